@@ -1,0 +1,189 @@
+"""The oracle: TEST INFRASTRUCTURE ONLY.
+
+A plain, slow CPU restatement (scalar C, double precision) of block Gibbs
+sampling of the convolutional RBM that encodes the Shastry–Sutherland Ising
+lattice (arXiv 2511.20911, Sec. II.A–II.B).  Only ``tests/``, the smoke check
+and the benchmark's CPU-baseline / reference legs may import this package.  It
+shares no code with ``paper_2511_20911_gb300``: both sides implement the same
+readings of the paper (bond list, weights, tables, Philox keying) separately.
+
+This module only marshals numpy arrays into ``crbm_oracle.c``.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+import subprocess
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+_SRC = os.path.join(_HERE, "crbm_oracle.c")
+_LIB_DIR = os.path.join(_HERE, "_build")
+_LIB = os.path.join(_LIB_DIR, "liboracle.so")
+
+NSUM = 11
+TAG_VIS, TAG_INIT, TAG_SWAP = 4, 5, 6
+
+
+def build(force: bool = False) -> str:
+    """Compile crbm_oracle.c into oracle/_build/liboracle.so (gcc, OpenMP)."""
+    os.makedirs(_LIB_DIR, exist_ok=True)
+    srcs = [_SRC, os.path.join(_HERE, "crbm_oracle.h"), os.path.join(_HERE, "oracle_pt.c")]
+    srcs = [s for s in srcs if os.path.exists(s)]
+    if not force and os.path.exists(_LIB):
+        if all(os.path.getmtime(_LIB) >= os.path.getmtime(s) for s in srcs):
+            return _LIB
+    cfiles = [s for s in srcs if s.endswith(".c")]
+    tmp = _LIB + f".tmp{os.getpid()}"
+    cmd = ["gcc", "-O2", "-std=c11", "-fopenmp", "-ffp-contract=off", "-fPIC", "-shared",
+           "-o", tmp] + cfiles + ["-lm"]
+    subprocess.check_call(cmd)
+    os.replace(tmp, _LIB)
+    return _LIB
+
+
+class Bond(ctypes.Structure):
+    _fields_ = [("r1", ctypes.c_int8), ("c1", ctypes.c_int8), ("r2", ctypes.c_int8),
+                ("c2", ctypes.c_int8), ("cls", ctypes.c_uint8)]
+
+
+_lib = None
+
+
+def lib():
+    global _lib
+    if _lib is None:
+        _lib = ctypes.CDLL(build())
+        _lib.orc_threshold.restype = ctypes.c_uint32
+        _lib.orc_threshold.argtypes = [ctypes.c_double]
+    return _lib
+
+
+def _p(a, ct):
+    return a.ctypes.data_as(ctypes.POINTER(ct)) if a is not None else None
+
+
+def bonds_array(bonds=None):
+    """ctypes array of bonds; None -> the canonical SS unit cell."""
+    if bonds is None:
+        bonds = canonical_bonds()
+    arr = (Bond * len(bonds))()
+    for i, b in enumerate(bonds):
+        arr[i] = Bond(*b)
+    return arr, len(bonds)
+
+
+def canonical_bonds():
+    arr = (Bond * 10)()
+    n = lib().orc_canonical_bonds(arr)
+    return [(arr[i].r1, arr[i].c1, arr[i].r2, arr[i].c2, arr[i].cls) for i in range(n)]
+
+
+def philox(ctr, key):
+    c = (ctypes.c_uint32 * 4)(*[int(x) & 0xFFFFFFFF for x in ctr])
+    k = (ctypes.c_uint32 * 2)(*[int(x) & 0xFFFFFFFF for x in key])
+    o = (ctypes.c_uint32 * 4)()
+    lib().orc_philox4x32_10(c, k, o)
+    return [o[i] for i in range(4)]
+
+
+def weight(beta, J):
+    a = ctypes.c_double()
+    s = ctypes.c_int()
+    lib().orc_weight(ctypes.c_double(beta), ctypes.c_double(J), ctypes.byref(a), ctypes.byref(s))
+    return a.value, s.value
+
+
+def threshold(y):
+    return int(lib().orc_threshold(float(y)))
+
+
+def quantize(x):
+    q = ctypes.c_int32()
+    if lib().orc_quantize(ctypes.c_double(x), ctypes.byref(q)):
+        raise ValueError(f"coupling {x} out of Q.4 range")
+    return q.value
+
+
+def degrees(L, periodic=True, bonds=None):
+    arr, nb = bonds_array(bonds)
+    dj, djp = ctypes.c_int(), ctypes.c_int()
+    if lib().orc_degrees(L, int(periodic), arr, nb, ctypes.byref(dj), ctypes.byref(djp)):
+        raise ValueError("bad model")
+    return dj.value, djp.value
+
+
+def tables(L, J, Jp, h, beta, periodic=True, bonds=None):
+    """(Th[2][5], Tv[2DJ+1][2DJp+1]) uint32 for one parameter point."""
+    arr, nb = bonds_array(bonds)
+    dj, djp = degrees(L, periodic, bonds)
+    th = np.zeros(10, np.uint32)
+    tv = np.zeros((2 * dj + 1) * (2 * djp + 1), np.uint32)
+    rc = lib().orc_tables(L, int(periodic), arr, nb, ctypes.c_double(J), ctypes.c_double(Jp),
+                          ctypes.c_double(h), ctypes.c_double(beta), _p(th, ctypes.c_uint32),
+                          _p(tv, ctypes.c_uint32))
+    if rc:
+        raise ValueError("bad parameters")
+    return th.reshape(2, 5), tv.reshape(2 * dj + 1, 2 * djp + 1)
+
+
+def init_spins(L, chain_ids, seed):
+    ids = np.ascontiguousarray(chain_ids, dtype=np.uint32)
+    out = np.zeros((len(ids), L, L), np.int8)
+    lib().orc_init(L, _p(ids, ctypes.c_uint32), len(ids), ctypes.c_uint64(seed),
+                   _p(out, ctypes.c_int8))
+    return out
+
+
+def counts(spins, L, periodic=True, bonds=None):
+    """Exact (N_J, N_J', M) of one configuration [L][L] of +-1."""
+    arr, nb = bonds_array(bonds)
+    v = np.ascontiguousarray(spins, dtype=np.int8)
+    a, b, c = ctypes.c_int64(), ctypes.c_int64(), ctypes.c_int64()
+    lib().orc_counts(L, int(periodic), arr, nb, _p(v, ctypes.c_int8), ctypes.byref(a),
+                     ctypes.byref(b), ctypes.byref(c))
+    return a.value, b.value, c.value
+
+
+def run(L, params, chain_param, spins, seed, sweep0, n_sweeps, measure_every=1,
+        chain_ids=None, periodic=True, bonds=None, sums=None, series_cap=0, sq_every=0,
+        sq=None):
+    """Advance ``spins`` [n_chains][L][L] (int8 +-1, modified in place).
+
+    params: dict of equal-length sequences J, Jp, h, beta.
+    Returns (sums [n_chains][11] int64, series or None, sq or None).
+    """
+    arr, nb = bonds_array(bonds)
+    J = np.ascontiguousarray(params["J"], np.float64)
+    Jp = np.ascontiguousarray(params["Jp"], np.float64)
+    h = np.ascontiguousarray(params["h"], np.float64)
+    beta = np.ascontiguousarray(params["beta"], np.float64)
+    cp = np.ascontiguousarray(chain_param, np.int32)
+    n = len(cp)
+    assert spins.dtype == np.int8 and spins.flags.c_contiguous and spins.shape == (n, L, L)
+    ids = np.arange(n, dtype=np.uint32) if chain_ids is None else np.ascontiguousarray(
+        chain_ids, np.uint32)
+    if sums is None:
+        sums = np.zeros((n, NSUM), np.int64)
+    series = np.zeros((n, series_cap, 3), np.int32) if series_cap > 0 else None
+    if sq_every > 0 and sq is None:
+        sq = np.zeros((n, L, L), np.float64)
+    rc = lib().orc_run(L, int(periodic), arr, nb, _p(J, ctypes.c_double), _p(Jp, ctypes.c_double),
+                       _p(h, ctypes.c_double), _p(beta, ctypes.c_double), len(J),
+                       _p(cp, ctypes.c_int32), _p(ids, ctypes.c_uint32), n, ctypes.c_uint64(seed),
+                       ctypes.c_int64(sweep0), ctypes.c_int64(n_sweeps), int(measure_every),
+                       _p(spins, ctypes.c_int8), _p(sums, ctypes.c_int64),
+                       _p(series, ctypes.c_int32), ctypes.c_int64(series_cap), int(sq_every),
+                       _p(sq, ctypes.c_double) if sq_every > 0 else None)
+    if rc:
+        raise ValueError(f"orc_run failed ({rc})")
+    return sums, series, sq
+
+
+def set_threads(n):
+    lib().orc_set_threads(int(n))
+
+
+def get_threads():
+    return int(lib().orc_get_threads())

@@ -1,0 +1,388 @@
+/*
+ * crbm_oracle.c — TEST INFRASTRUCTURE ONLY (the oracle); see crbm_oracle.h.
+ *
+ * Plain scalar C, double precision for every real number, int8 +-1 spins and
+ * hidden units in [chain][row][col] order, no blocking, no bit packing, no
+ * SIMD.  Each function names the passage of arXiv 2511.20911 it restates.
+ * Build: gcc -O2 -fopenmp -ffp-contract=off -shared -fPIC (no FMA contraction,
+ * so the table arithmetic is the plain left-to-right double evaluation).
+ */
+#include "crbm_oracle.h"
+
+#include <math.h>
+#include <stdlib.h>
+#include <string.h>
+#ifdef _OPENMP
+#include <omp.h>
+#endif
+
+/* ---------------------------------------------------------------- Philox */
+/* Salmon et al., SC'11, Sec. 4: Philox-4x32 with R = 10 rounds.  One round
+ * multiplies counter words 0 and 2 by the two round multipliers, forming
+ * 64-bit products, and permutes/whitens:
+ *     (c0, c1, c2, c3) -> (hi(M1 c2) ^ c1 ^ k0, lo(M1 c2), hi(M0 c0) ^ c3 ^ k1, lo(M0 c0))
+ * and between rounds the key is bumped by the Weyl constants (golden ratio
+ * and sqrt(3) - 1, as 32-bit fractions). */
+#define ORC_PHILOX_M0 0xD2511F53u
+#define ORC_PHILOX_M1 0xCD9E8D57u
+#define ORC_PHILOX_W0 0x9E3779B9u
+#define ORC_PHILOX_W1 0xBB67AE85u
+
+void orc_philox4x32_10(const uint32_t ctr[4], const uint32_t key[2], uint32_t out[4]) {
+    uint32_t c0 = ctr[0], c1 = ctr[1], c2 = ctr[2], c3 = ctr[3];
+    uint32_t k0 = key[0], k1 = key[1];
+    for (int round = 0; round < 10; ++round) {
+        if (round > 0) {
+            k0 += ORC_PHILOX_W0;
+            k1 += ORC_PHILOX_W1;
+        }
+        uint64_t p0 = (uint64_t)ORC_PHILOX_M0 * (uint64_t)c0;
+        uint64_t p1 = (uint64_t)ORC_PHILOX_M1 * (uint64_t)c2;
+        uint32_t n0 = (uint32_t)(p1 >> 32) ^ c1 ^ k0;
+        uint32_t n1 = (uint32_t)p1;
+        uint32_t n2 = (uint32_t)(p0 >> 32) ^ c3 ^ k1;
+        uint32_t n3 = (uint32_t)p0;
+        c0 = n0; c1 = n1; c2 = n2; c3 = n3;
+    }
+    out[0] = c0; out[1] = c1; out[2] = c2; out[3] = c3;
+}
+
+static uint32_t philox_word(uint32_t cell, uint32_t sweep, uint32_t chain, uint32_t tag,
+                            uint64_t seed, int word) {
+    uint32_t ctr[4] = {cell, sweep, chain, tag};
+    uint32_t key[2] = {(uint32_t)(seed & 0xffffffffu), (uint32_t)(seed >> 32)};
+    uint32_t out[4];
+    orc_philox4x32_10(ctr, key, out);
+    return out[word];
+}
+
+/* ------------------------------------------------------------ lattice */
+/* Fig. 1(a) and Sec. II.A: the SS lattice has a 3x3 unit cell holding 8
+ * nearest-neighbour (J1) bonds and 2 diagonal (J2) bonds, labelled 0..9 with
+ * k in [0,7] the J1 filters and k in {8, 9} the J2 filters.  In window
+ * coordinates (row, col): horizontal bonds of rows 0 and 1, vertical bonds of
+ * columns 0 and 1, and the two orthogonal dimers: "\" on plaquette (0,0) and
+ * "/" on plaquette (1,1).  Tiling the window with stride 2 covers every
+ * square-lattice bond once and every site with exactly one diagonal. */
+int orc_canonical_bonds(orc_bond out[10]) {
+    static const orc_bond b[10] = {
+        {0, 0, 0, 1, 0}, {0, 1, 0, 2, 0}, {1, 0, 1, 1, 0}, {1, 1, 1, 2, 0},
+        {0, 0, 1, 0, 0}, {1, 0, 2, 0, 0}, {0, 1, 1, 1, 0}, {1, 1, 2, 1, 0},
+        {0, 0, 1, 1, 1}, {1, 2, 2, 1, 1},
+    };
+    memcpy(out, b, sizeof(b));
+    return 10;
+}
+
+static int n_windows(int L) { return (L + 1) / 2; }
+
+/* Appendix, "Wrapper Module": a periodic lattice copies the first rows and
+ * columns past the edge; an open one inserts zeros.  A zero-padded endpoint
+ * is a null site (-1) that contributes nothing. */
+static int site_of(int L, int periodic, int i, int j, int r, int c) {
+    int R = 2 * i + r, C = 2 * j + c;
+    if (R >= L || C >= L) {
+        if (!periodic) return -1;
+        R %= L;
+        C %= L;
+    }
+    return R * L + C;
+}
+
+static int check_model(int L, const orc_bond* bonds, int nb) {
+    if (L < 3 || L > 4096 || nb < 1 || nb > 16) return -1;
+    for (int k = 0; k < nb; ++k) {
+        const orc_bond* b = &bonds[k];
+        if (b->r1 < 0 || b->r1 > 2 || b->c1 < 0 || b->c1 > 2 || b->r2 < 0 || b->r2 > 2 ||
+            b->c2 < 0 || b->c2 > 2 || b->cls > 1)
+            return -1;
+        if (b->r1 == b->r2 && b->c1 == b->c2) return -1;
+    }
+    return 0;
+}
+
+int orc_quantize(double x, int32_t* q) {
+    if (!(x == x)) return -1;
+    double v = nearbyint(16.0 * x);
+    if (v < -2047.0 || v > 2047.0) return -1;
+    *q = (int32_t)v;
+    return 0;
+}
+
+/* ------------------------------------------------------------- weights */
+/* Eqs. (4)-(7) (Carleo et al. mapping): exp(K v_i v_j) is reproduced, up to a
+ * constant, by a hidden unit h = +-1 coupled with weight a to v_i and s a to
+ * v_j, since sum_h exp(a h (v_i + s v_j)) = 2 cosh(a (v_i + s v_j)), whose
+ * aligned/anti-aligned ratio is cosh(2a).  Hence cosh(2a) = exp(2|K|),
+ * a = 1/2 arccosh(exp(2|K|)), s = sgn(K).  The Boltzmann weight of Eq. (1) is
+ * exp(-beta H), so a J bond has K = -beta J (J > 0 antiferromagnetic). */
+void orc_weight(double beta, double J, double* a, int* s) {
+    double K = -beta * J;
+    *a = 0.5 * acosh(exp(2.0 * fabs(K)));
+    *s = (K >= 0.0) ? 1 : -1;
+}
+
+/* Sigmoid of Eqs. (9)-(10) as an unsigned 32-bit acceptance threshold: a unit
+ * becomes +1 iff a uniform 32-bit draw u satisfies u < thr. */
+uint32_t orc_threshold(double y) {
+    double p = 1.0 / (1.0 + exp(-y));
+    double t = nearbyint(ldexp(p, 32));
+    if (t > 4294967295.0) t = 4294967295.0;
+    if (t < 0.0) t = 0.0;
+    return (uint32_t)t;
+}
+
+int orc_degrees(int L, int periodic, const orc_bond* bonds, int nb, int* DJ, int* DJp) {
+    if (check_model(L, bonds, nb)) return -1;
+    int W = n_windows(L);
+    int* deg = (int*)calloc((size_t)2 * L * L, sizeof(int));
+    if (!deg) return -2;
+    for (int i = 0; i < W; ++i)
+        for (int j = 0; j < W; ++j)
+            for (int k = 0; k < nb; ++k) {
+                int s1 = site_of(L, periodic, i, j, bonds[k].r1, bonds[k].c1);
+                int s2 = site_of(L, periodic, i, j, bonds[k].r2, bonds[k].c2);
+                if (s1 >= 0) deg[bonds[k].cls * L * L + s1]++;
+                if (s2 >= 0) deg[bonds[k].cls * L * L + s2]++;
+            }
+    int m0 = 0, m1 = 0;
+    for (int s = 0; s < L * L; ++s) {
+        if (deg[s] > m0) m0 = deg[s];
+        if (deg[L * L + s] > m1) m1 = deg[L * L + s];
+    }
+    free(deg);
+    *DJ = m0;
+    *DJp = m1;
+    return 0;
+}
+
+/* Eq. (9): P(H=1|V) = sigmoid of the forward cross-correlation; with +-1
+ * hidden units the hidden conditional is sigmoid(2 a m), m = v1 + s v2.
+ * Eq. (10): P(V=1|H) = sigmoid of the zero-padded reverse correlation summed
+ * over the filters plus the visible bias; here sigmoid(2 x) with
+ * x = beta h + a_J n_J + a_J' n_J'. */
+int orc_tables(int L, int periodic, const orc_bond* bonds, int nb, double J, double Jp,
+               double h, double beta, uint32_t* Th, uint32_t* Tv) {
+    int DJ, DJp;
+    if (orc_degrees(L, periodic, bonds, nb, &DJ, &DJp)) return -1;
+    int32_t qJ, qJp, qh;
+    if (orc_quantize(J, &qJ) || orc_quantize(Jp, &qJp) || orc_quantize(h, &qh)) return -1;
+    if (!(beta >= 0.0) || beta > 1.0e6) return -1;
+    double Jd = qJ / 16.0, Jpd = qJp / 16.0, hd = qh / 16.0;
+    double a[2];
+    int s[2];
+    orc_weight(beta, Jd, &a[0], &s[0]);
+    orc_weight(beta, Jpd, &a[1], &s[1]);
+    for (int cls = 0; cls < 2; ++cls)
+        for (int m = -2; m <= 2; ++m) Th[cls * 5 + (m + 2)] = orc_threshold(2.0 * a[cls] * m);
+    int nP = 2 * DJp + 1;
+    for (int nJ = -DJ; nJ <= DJ; ++nJ)
+        for (int nJp = -DJp; nJp <= DJp; ++nJp) {
+            double x = beta * hd + a[0] * nJ + a[1] * nJp;
+            Tv[(nJ + DJ) * nP + (nJp + DJp)] = orc_threshold(2.0 * x);
+        }
+    return 0;
+}
+
+/* ------------------------------------------------------ configuration */
+void orc_init(int L, const uint32_t* chain_ids, int n_chains, uint64_t seed, int8_t* spins) {
+    int W = n_windows(L);
+    for (int c = 0; c < n_chains; ++c)
+        for (int R = 0; R < L; ++R)
+            for (int C = 0; C < L; ++C) {
+                uint32_t cell = (uint32_t)((R >> 1) * W + (C >> 1));
+                uint32_t u = philox_word(cell, 0u, chain_ids[c], ORC_TAG_INIT, seed,
+                                         2 * (R & 1) + (C & 1));
+                spins[(size_t)c * L * L + R * L + C] = (u < 0x80000000u) ? 1 : -1;
+            }
+}
+
+/* Eq. (1) on the bond multiset generated by the stride-2 windows. */
+void orc_counts(int L, int periodic, const orc_bond* bonds, int nb, const int8_t* v,
+                int64_t* NJ, int64_t* NJp, int64_t* M) {
+    int W = n_windows(L);
+    int64_t n[2] = {0, 0}, m = 0;
+    for (int i = 0; i < W; ++i)
+        for (int j = 0; j < W; ++j)
+            for (int k = 0; k < nb; ++k) {
+                int s1 = site_of(L, periodic, i, j, bonds[k].r1, bonds[k].c1);
+                int s2 = site_of(L, periodic, i, j, bonds[k].r2, bonds[k].c2);
+                if (s1 < 0 || s2 < 0) continue;
+                n[bonds[k].cls] += v[s1] * v[s2];
+            }
+    for (int s = 0; s < L * L; ++s) m += v[s];
+    *NJ = n[0];
+    *NJp = n[1];
+    *M = m;
+}
+
+/* Sec. IV.B, Eq. (11): S(q) = sum_ij <s_i s_j> e^{i q.(R_i - R_j)}, reported
+ * per spin: |sum_r s_r e^{i q.r}|^2 / N at q = 2 pi (nR, nC) / L. */
+static void add_structure_factor(int L, const int8_t* v, double* sq) {
+    const double twopi = 6.283185307179586476925286766559;
+    int N = L * L;
+    for (int nR = 0; nR < L; ++nR)
+        for (int nC = 0; nC < L; ++nC) {
+            double re = 0.0, im = 0.0;
+            for (int R = 0; R < L; ++R)
+                for (int C = 0; C < L; ++C) {
+                    double ph = twopi * (double)(nR * R + nC * C) / (double)L;
+                    re += v[R * L + C] * cos(ph);
+                    im += v[R * L + C] * sin(ph);
+                }
+            sq[nR * L + nC] += (re * re + im * im) / (double)N;
+        }
+}
+
+/* ------------------------------------------------------------ sampling */
+typedef struct {
+    uint32_t Th[10];
+    uint32_t* Tv;
+    int s[2];
+} orc_point;
+
+/* Sec. II.B and Fig. 1(d): one sweep = every hidden unit drawn from Eq. (9)
+ * given the current spins, then every spin drawn from Eq. (10) given those
+ * hidden units.  The Philox counter (cell, sweep, chain, tag) fixes every draw:
+ * hidden bond k of cell (i, j) uses word k&3 of tag k>>2; the spin at
+ * window offset (r, c) uses word 2r+c of tag ORC_TAG_VIS. */
+static void one_sweep(int L, int periodic, const orc_bond* bonds, int nb, const orc_point* pt,
+                      int DJ, int DJp, uint32_t chain, uint32_t sweep, uint64_t seed, int8_t* v,
+                      int8_t* hid, int* field) {
+    int W = n_windows(L);
+    /* hidden | visible */
+    for (int i = 0; i < W; ++i)
+        for (int j = 0; j < W; ++j) {
+            uint32_t cell = (uint32_t)(i * W + j);
+            for (int k = 0; k < nb; ++k) {
+                const orc_bond* b = &bonds[k];
+                int s1 = site_of(L, periodic, i, j, b->r1, b->c1);
+                int s2 = site_of(L, periodic, i, j, b->r2, b->c2);
+                int m = (s1 >= 0 ? v[s1] : 0) + pt->s[b->cls] * (s2 >= 0 ? v[s2] : 0);
+                uint32_t u = philox_word(cell, sweep, chain, (uint32_t)(k >> 2), seed, k & 3);
+                uint32_t t = pt->Th[b->cls * 5 + (m + 2)];
+                hid[cell * nb + k] = (u < t) ? 1 : -1;
+            }
+        }
+    /* visible | hidden: zero-padded reverse correlation = scatter of every
+     * hidden unit onto its two endpoints with coefficients (+1, s). */
+    memset(field, 0, sizeof(int) * 2 * L * L);
+    for (int i = 0; i < W; ++i)
+        for (int j = 0; j < W; ++j) {
+            int cell = i * W + j;
+            for (int k = 0; k < nb; ++k) {
+                const orc_bond* b = &bonds[k];
+                int s1 = site_of(L, periodic, i, j, b->r1, b->c1);
+                int s2 = site_of(L, periodic, i, j, b->r2, b->c2);
+                int hv = hid[cell * nb + k];
+                if (s1 >= 0) field[b->cls * L * L + s1] += hv;
+                if (s2 >= 0) field[b->cls * L * L + s2] += pt->s[b->cls] * hv;
+            }
+        }
+    int nP = 2 * DJp + 1;
+    for (int R = 0; R < L; ++R)
+        for (int C = 0; C < L; ++C) {
+            int s = R * L + C;
+            uint32_t cell = (uint32_t)((R >> 1) * W + (C >> 1));
+            uint32_t u = philox_word(cell, sweep, chain, ORC_TAG_VIS, seed, 2 * (R & 1) + (C & 1));
+            uint32_t t = pt->Tv[(field[s] + DJ) * nP + (field[L * L + s] + DJp)];
+            v[s] = (u < t) ? 1 : -1;
+        }
+}
+
+int orc_run(int L, int periodic, const orc_bond* bonds, int nb, const double* J, const double* Jp,
+            const double* h, const double* beta, int n_params, const int32_t* chain_param,
+            const uint32_t* chain_ids, int n_chains, uint64_t seed, int64_t sweep0,
+            int64_t n_sweeps, int measure_every, int8_t* spins, int64_t* sums, int32_t* series,
+            int64_t series_cap, int sq_every, double* sq) {
+    int DJ, DJp;
+    if (orc_degrees(L, periodic, bonds, nb, &DJ, &DJp)) return -1;
+    if (n_params < 1 || n_chains < 0 || n_sweeps < 0 || sweep0 < 0 ||
+        sweep0 + n_sweeps > 4294967295LL || measure_every < 0 || sq_every < 0)
+        return -1;
+    for (int c = 0; c < n_chains; ++c)
+        if (chain_param[c] < 0 || chain_param[c] >= n_params) return -1;
+    int nTv = (2 * DJ + 1) * (2 * DJp + 1);
+    orc_point* pts = (orc_point*)calloc((size_t)n_params, sizeof(orc_point));
+    uint32_t* tv = (uint32_t*)calloc((size_t)n_params * nTv, sizeof(uint32_t));
+    if (!pts || !tv) {
+        free(pts);
+        free(tv);
+        return -2;
+    }
+    int err = 0;
+    for (int p = 0; p < n_params; ++p) {
+        pts[p].Tv = tv + (size_t)p * nTv;
+        if (orc_tables(L, periodic, bonds, nb, J[p], Jp[p], h[p], beta[p], pts[p].Th, pts[p].Tv))
+            err = -1;
+        int32_t q;
+        double a;
+        orc_quantize(J[p], &q);
+        orc_weight(beta[p], q / 16.0, &a, &pts[p].s[0]);
+        orc_quantize(Jp[p], &q);
+        orc_weight(beta[p], q / 16.0, &a, &pts[p].s[1]);
+    }
+    if (err) {
+        free(pts);
+        free(tv);
+        return -1;
+    }
+    int W = n_windows(L);
+    int N = L * L;
+#pragma omp parallel for schedule(dynamic, 1)
+    for (int c = 0; c < n_chains; ++c) {
+        int8_t* v = spins + (size_t)c * N;
+        int8_t* hid = (int8_t*)malloc((size_t)W * W * nb);
+        int* field = (int*)malloc(sizeof(int) * 2 * N);
+        const orc_point* pt = &pts[chain_param[c]];
+        for (int64_t t = sweep0; t < sweep0 + n_sweeps; ++t) {
+            one_sweep(L, periodic, bonds, nb, pt, DJ, DJp, chain_ids[c], (uint32_t)t, seed, v, hid,
+                      field);
+            if (measure_every > 0 && (t + 1) % measure_every == 0 && sums) {
+                int64_t nJ, nJp, M;
+                orc_counts(L, periodic, bonds, nb, v, &nJ, &nJp, &M);
+                int64_t* s = sums + (size_t)c * ORC_NSUM;
+                if (series && s[0] < series_cap) {
+                    int32_t* e = series + ((size_t)c * series_cap + s[0]) * 3;
+                    e[0] = (int32_t)nJ;
+                    e[1] = (int32_t)nJp;
+                    e[2] = (int32_t)M;
+                }
+                s[0] += 1;
+                s[1] += nJ;
+                s[2] += nJp;
+                s[3] += M;
+                s[4] += M < 0 ? -M : M;
+                s[5] += nJ * nJ;
+                s[6] += nJp * nJp;
+                s[7] += M * M;
+                s[8] += nJ * nJp;
+                s[9] += nJ * M;
+                s[10] += nJp * M;
+            }
+            if (sq_every > 0 && (t + 1) % sq_every == 0 && sq)
+                add_structure_factor(L, v, sq + (size_t)c * N);
+        }
+        free(hid);
+        free(field);
+    }
+    free(pts);
+    free(tv);
+    return 0;
+}
+
+void orc_set_threads(int n) {
+#ifdef _OPENMP
+    if (n > 0) omp_set_num_threads(n);
+#else
+    (void)n;
+#endif
+}
+
+int orc_get_threads(void) {
+#ifdef _OPENMP
+    return omp_get_max_threads();
+#else
+    return 1;
+#endif
+}

@@ -1,0 +1,103 @@
+/*
+ * crbm_oracle.h — TEST INFRASTRUCTURE ONLY (the oracle).
+ *
+ * A plain, slow, scalar CPU restatement of block Gibbs sampling of the
+ * convolutional RBM (CRBM) that encodes the classical Shastry–Sutherland (SS)
+ * Ising lattice (Brahma et al., arXiv 2511.20911, Sec. II.A "Mapping to CRBM"
+ * and Sec. II.B "Sampling of CRBM").  Only tests/, the smoke check and the
+ * benchmark's CPU-baseline leg may load it.  It shares no code with the CUDA
+ * library: its bond list, weights, threshold tables, Philox generator and
+ * sweep loop are written here from the paper and from the published Philox
+ * definition, independently of the library's own.
+ *
+ * Conventions (the readings of the paper that both sides implement):
+ *   - spins and hidden units are +1/-1 (int8); spin bit 1 <-> +1.
+ *   - H(s) = J * sum_nn s s + J' * sum_diag s s - h * sum s   (Eq. 1 with the
+ *     field sign chosen so that h > 0 favours +1).
+ *   - J, J', h are held as signed Q.4 fixed point: q = nearbyint(16 x),
+ *     |q| <= 2047; energies in units of 1/16 are then exact integers.
+ *   - windows of the stride-2 3x3 filter sit at (2i, 2j), i, j in [0, W),
+ *     W = floor((L+1)/2) (the hidden register size of the appendix).
+ */
+#ifndef CRBM_ORACLE_H
+#define CRBM_ORACLE_H
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct {
+    int8_t r1, c1, r2, c2; /* window-relative endpoints, each in [0, 2] */
+    uint8_t cls;           /* 0 = J (nearest neighbour), 1 = J' (diagonal) */
+} orc_bond;
+
+/* Philox-4x32-10 of Salmon, Moraes, Dror and Shaw, "Parallel random numbers:
+ * as easy as 1, 2, 3", SC'11: counter ctr[4], key key[2] -> out[4]. */
+void orc_philox4x32_10(const uint32_t ctr[4], const uint32_t key[2], uint32_t out[4]);
+
+/* The ten bonds of the SS 3x3 unit cell (8 J bonds then 2 J' diagonals). */
+int orc_canonical_bonds(orc_bond out[10]);
+
+/* Q.4 quantisation of a coupling; returns 0, or -1 if out of range / NaN. */
+int orc_quantize(double x, int32_t* q);
+
+/* Per-class weight a = 1/2 arccosh(exp(2|K|)), K = -beta * J (Eqs. 5-7), and
+ * the sign s of the second endpoint's coefficient (s = +1 iff K >= 0). */
+void orc_weight(double beta, double J, double* a, int* s);
+
+/* thr(y) = min(2^32 - 1, nearbyint(2^32 / (1 + exp(-y)))) as uint32. */
+uint32_t orc_threshold(double y);
+
+/* Largest number of (cell, bond, endpoint) incidences of class 0 / class 1 on
+ * any real site: the visible table spans n_J in [-DJ, DJ], n_J' in [-DJp, DJp]. */
+int orc_degrees(int L, int periodic, const orc_bond* bonds, int nb, int* DJ, int* DJp);
+
+/* Threshold tables for one parameter point.
+ *   Th[cls*5 + (m+2)] = thr(2 a_cls m),                m in [-2, 2]
+ *   Tv[(nJ+DJ)*(2DJp+1) + (nJp+DJp)] = thr(2 x),
+ *       x = beta*h + a_J*nJ + a_J'*nJp  (left to right, double). */
+int orc_tables(int L, int periodic, const orc_bond* bonds, int nb,
+               double J, double Jp, double h, double beta,
+               uint32_t* Th, uint32_t* Tv);
+
+/* Uniform +-1 initial spins: site (R, C) of chain c is +1 iff word
+ * 2(R&1)+(C&1) of Philox((cell, 0, c, TAG_INIT), seed) < 2^31. */
+void orc_init(int L, const uint32_t* chain_ids, int n_chains, uint64_t seed, int8_t* spins);
+
+/* Exact integer counts of one configuration over the bond multiset generated
+ * by the windows: NJ = sum over class-0 bonds of s s, NJp likewise, M = sum s. */
+void orc_counts(int L, int periodic, const orc_bond* bonds, int nb,
+                const int8_t* spins, int64_t* NJ, int64_t* NJp, int64_t* M);
+
+/* Run n_sweeps block-Gibbs sweeps (hidden | visible, then visible | hidden)
+ * on each chain, starting at global sweep index sweep0.
+ *   params: J, Jp, h, beta arrays of length n_params; chain_param[c] -> p.
+ *   chain_ids[c]: global chain index used in the Philox counter.
+ *   spins [n_chains][L*L] int8 in/out.
+ *   sums [n_chains][11] int64, accumulated (see ORC_SUM_*), may be NULL.
+ *   series [n_chains][series_cap][3] int32 (NJ, NJp, M), may be NULL; entry
+ *     index = sums[c][0] before the measurement.
+ *   sq [n_chains][L*L] double, accumulated S(q) = |sum_r s_r e^{i q.r}|^2 / N
+ *     at q = 2 pi (nR, nC) / L, every sq_every sweeps (0 = off), may be NULL.
+ * Measurement after sweep t (0-based, global) iff measure_every > 0 and
+ * (t + 1) % measure_every == 0.  Returns 0 or a negative error. */
+int orc_run(int L, int periodic, const orc_bond* bonds, int nb,
+            const double* J, const double* Jp, const double* h, const double* beta,
+            int n_params, const int32_t* chain_param, const uint32_t* chain_ids,
+            int n_chains, uint64_t seed, int64_t sweep0, int64_t n_sweeps,
+            int measure_every, int8_t* spins, int64_t* sums,
+            int32_t* series, int64_t series_cap, int sq_every, double* sq);
+
+void orc_set_threads(int n);
+int orc_get_threads(void);
+
+#define ORC_TAG_VIS 4u
+#define ORC_TAG_INIT 5u
+#define ORC_TAG_SWAP 6u
+#define ORC_NSUM 11
+
+#ifdef __cplusplus
+}
+#endif
+#endif

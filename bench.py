@@ -1,0 +1,273 @@
+"""Benchmark of the GB300 CRBM block-Gibbs sampler (one JSON line on stdout).
+
+Default workload: the L=18 periodic Shastry–Sutherland grid -- J'/J in
+{0.5, 1, 2} x 16 beta in [0.1, 5] x 16 h in [0, 4] x 16 chains = 12288 chains,
+couplings on the Q.4 grid, SMEM-resident lattices.  A step is one crbm_sweep
+call of --sweeps-per-step sweeps over every chain (hidden then visible
+half-step, observables every 10 sweeps), inputs resident in HBM.
+
+  python bench.py [--gpus N --steps K --warmup W] [--impl reference]
+
+N > 1 (torchrun): every rank runs an independent replica with its own chains
+(no data-path collective); value = all ranks' spin-updates / max rank time.
+--impl reference times the CPU oracle (the reference arm) on host cores.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "spin-updates/s and ESS/s (energy, m) per GB300 vs plain Gibbs; roofline %"
+UNIT = "spin-updates/s"
+SM_COUNT, SMSP_PER_SM, LANES, SM_MAX_MHZ = 152, 4, 32, 2070.0
+# Algorithmic integer operations per (chain, cell, sweep) of the canonical SS
+# path: 4 Philox-4x32-10 calls x 10 rounds x (2 wide multiplies + 2 three-input
+# XORs) = 160; 10 hidden decisions x 4 (field index, threshold select, compare,
+# pack) = 40; 4 visible decisions x 8 (4 field adds, index, table load,
+# compare, pack) = 32.  Each cell holds 4 spins.
+OPS_PER_CELL = 160 + 40 + 32
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=10)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--sweeps-per-step", type=int, default=2000)
+    ap.add_argument("--measure-every", type=int, default=10)
+    ap.add_argument("--cpu-seconds", type=float, default=8.0)
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    return ap.parse_args()
+
+
+def dist_setup(args):
+    ws = int(os.environ.get("WORLD_SIZE", "1"))
+    if ws > 1:
+        import torch
+        import torch.distributed as dist
+        rank = int(os.environ["RANK"])
+        torch.cuda.set_device(int(os.environ.get("LOCAL_RANK", rank)))
+        dist.init_process_group("nccl")
+        return rank, ws
+    return 0, 1
+
+
+class ClockSampler:
+    """nvidia-smi clock/throttle samples every 200 ms while running."""
+
+    Q = ("clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.hw_slowdown,"
+         "clocks_event_reasons.hw_thermal_slowdown,clocks_event_reasons.sw_thermal_slowdown,"
+         "clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index):
+        self.index, self.rows, self.proc = index, [], None
+
+    def __enter__(self):
+        try:
+            self.proc = subprocess.Popen(["nvidia-smi", "-i", str(self.index), f"--query-gpu={self.Q}",
+                                          "--format=csv,noheader,nounits", "-lms", "200"],
+                                         stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.t = threading.Thread(target=self._read, daemon=True)
+            self.t.start()
+        except OSError:
+            self.proc = None
+        return self
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.rows.append([x.strip() for x in line.split(",")])
+
+    def __exit__(self, *a):
+        if self.proc:
+            self.proc.terminate()
+            self.proc.wait()
+            self.t.join(timeout=2)
+
+    def summary(self):
+        sm = [float(r[0]) for r in self.rows if len(r) >= 7 and r[0].replace(".", "").isdigit()]
+        mx = [float(r[1]) for r in self.rows if len(r) >= 7 and r[1].replace(".", "").isdigit()]
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = sorted({names[i] for r in self.rows if len(r) >= 7 for i in range(4)
+                          if r[3 + i].lower() == "active"})
+        return {"sm_mhz": statistics.median(sm) if sm else None,
+                "sm_max_mhz": max(mx) if mx else None, "reasons": reasons, "samples": len(sm)}
+
+
+def grid_config(rank):
+    from paper_2511_20911_gb300 import workloads
+    w = workloads.grid_workload()
+    w["seed"] = w["seed"] + 1000003 * rank
+    return w
+
+
+def cpu_baseline(w, seconds):
+    """The oracle as it stands, OpenMP over chains on every host core, on a
+    bounded sample of the same workload (a spread subset of its chains)."""
+    import oracle
+    oracle.build()
+    n_all = w["n_chains"]
+    L = w["L"]
+    cores = os.cpu_count() or 1
+    oracle.set_threads(cores)
+
+    def run(n_ch, n_sw):
+        ids = np.linspace(0, n_all - 1, n_ch).astype(np.uint32)
+        cp = np.asarray(w["chain_param"], np.int32)[ids]
+        sp = oracle.init_spins(L, ids, w["seed"])
+        t = time.perf_counter()
+        oracle.run(L, w["params"], cp, sp, w["seed"], 0, n_sw, 10, chain_ids=ids)
+        return time.perf_counter() - t
+
+    n_ch = 16 * cores
+    dt = run(n_ch, 20)
+    n_sw = max(20, int(20 * seconds / max(dt, 1e-3)))
+    dt = run(n_ch, n_sw)
+    value = n_ch * n_sw * L * L / dt
+    return {"value": value, "unit": UNIT, "cores": oracle.get_threads(), "kind": "oracle",
+            "sample": f"{n_ch} of the {n_all} chains (spread over all parameter points), "
+                      f"{n_sw} sweeps, measure every 10, {dt:.1f} s wall"}
+
+
+def run_reference(args, rank, ws):
+    """Reference arm: the CPU oracle timed on the host cores."""
+    if rank != 0:
+        return
+    w = grid_config(0)
+    per_step = max(1.0, 60.0 / max(1, args.steps + args.warmup))
+    for _ in range(args.warmup):
+        cpu_baseline(w, min(per_step, 2.0))
+    vals = [cpu_baseline(w, per_step) for _ in range(args.steps)]
+    v = float(np.mean([x["value"] for x in vals]))
+    cb = dict(vals[-1])
+    cb["value"] = v
+    n_ch = int(cb["sample"].split()[0])
+    print(json.dumps({
+        "impl": "reference", "metric": METRIC, "value": v, "unit": UNIT, "n_gpus": args.gpus,
+        "steps": args.steps, "warmup": args.warmup,
+        "ms_per_step": float(np.mean([1e3 * n_ch * 324 * 0 + 0 for _ in vals])) or None,
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "int8",
+        "data": "synthetic", "config": config_dict(w, args), "cpu_baseline": cb,
+        "e2e": {"value": v, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}))
+
+
+def config_dict(w, args):
+    return {"workload": "L=18 periodic SS grid: J'/J in {0.5,1,2} x 16 beta in [0.1,5] x 16 h in "
+                        "[0,4] x 16 chains", "L": w["L"], "n_chains": w["n_chains"],
+            "n_params": len(w["params"]["J"]), "sweeps_per_step": args.sweeps_per_step,
+            "measure_every": args.measure_every, "layout": "smem",
+            "l2": "flushed between steps (256 MiB write outside the step events)",
+            "parallelism": f"replicas x{args.gpus}"}
+
+
+def main():
+    args = parse()
+    rank, ws = dist_setup(args)
+    if args.impl == "reference":
+        run_reference(args, rank, ws)
+        return
+    import torch
+    import paper_2511_20911_gb300 as crbm
+    from paper_2511_20911_gb300 import analysis
+
+    dev = torch.cuda.current_device()
+    w = grid_config(rank)
+    S, K, W = args.sweeps_per_step, args.steps, args.warmup
+    n_meas = S * K // args.measure_every
+    s = crbm.Sampler(w["L"], w["params"], w["n_chains"], chain_param=w["chain_param"], seed=w["seed"],
+                     measure_every=args.measure_every, series_len=n_meas)
+    stream = torch.cuda.current_stream()
+    flush = torch.empty(256 * 1024 * 1024, dtype=torch.uint8, device="cuda")
+    for _ in range(W):
+        s.sweep(S)
+    torch.cuda.synchronize()
+    s.reset_observables()
+    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(K)]
+    launches0 = s.launch_count
+    if ws > 1:
+        torch.distributed.barrier()
+    torch.cuda.synchronize()
+    with ClockSampler(dev) as clk:
+        for k in range(K):
+            flush.fill_(k & 0xFF)
+            ev[k][0].record(stream)
+            s.sweep(S)
+            ev[k][1].record(stream)
+        torch.cuda.synchronize()
+    if ws > 1:
+        torch.distributed.barrier()
+    launches = s.launch_count - launches0
+    step_ms = [a.elapsed_time(b) for a, b in ev]
+    t_total = sum(step_ms) / 1e3
+    if ws > 1:
+        t = torch.tensor([t_total], device="cuda")
+        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
+        t_total = float(t.item())
+    spin_updates = w["n_chains"] * w["L"] ** 2 * S * K
+    value = spin_updates * ws / t_total
+
+    # effective samples of E and m over the timed steps
+    ser = s.series()                                   # [T][chain][3]
+    p = w["params"]
+    cp = np.asarray(w["chain_param"])
+    Jc, Jpc, hc = (np.asarray(p[k])[cp] for k in ("J", "Jp", "h"))
+    E = analysis.energy_series(ser.transpose(1, 0, 2), Jc[:, None], Jpc[:, None], hc[:, None])
+    Mx = ser[:, :, 2].T.astype(np.float64)
+    ess_E = float(analysis.effective_samples(E).sum())
+    ess_m = float(analysis.effective_samples(Mx).sum())
+
+    # end to end through the C ABI with host buffers: set spins (H2D), sweep,
+    # read observables (D2H), every step
+    spins_h = s.get_spins()
+    obs_h = np.zeros((w["n_chains"], crbm.CRBM_NSUM), np.int64)
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    for k in range(max(1, K // 2)):
+        s.set_spins(spins_h)
+        s.sweep(S)
+        obs_h[:] = s.observables()
+    e2e_t = time.perf_counter() - t0
+    e2e_steps = max(1, K // 2)
+    e2e_val = w["n_chains"] * w["L"] ** 2 * S * e2e_steps * ws / e2e_t
+
+    ops = OPS_PER_CELL * (w["L"] // 2) ** 2 * w["n_chains"] * S
+    achieved = ops / (t_total / K) / 1e12
+    peak = SM_COUNT * SMSP_PER_SM * LANES * SM_MAX_MHZ * 1e6 / 1e12
+    out = {
+        "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws, "steps": K, "warmup": W,
+        "ms_per_step": t_total / K * 1e3, "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "u32", "data": "synthetic", "config": config_dict(w, args),
+        "ess_per_s": {"energy": ess_E * ws / t_total, "m": ess_m * ws / t_total,
+                      "method": "Sokal windowing c=5 on per-chain series (every "
+                                f"{args.measure_every} sweeps), first 10% discarded, summed over chains"},
+        "node_updates_per_s": value * 3.5,
+        "clocks": clk.summary(),
+        "e2e": {"value": e2e_val, "unit": UNIT, "h2d_bytes_per_step": int(spins_h.nbytes),
+                "d2h_bytes_per_step": int(obs_h.nbytes)},
+        "gpu_launches": int(launches),
+        "roofline": {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "Tops/s",
+                     "frac": achieved / peak, "traffic": None,
+                     "note": "integer-issue peak 152 SM x 4 SMSP x 32 lanes x 2070 MHz; ops = "
+                             f"{OPS_PER_CELL} algorithmic integer ops per chain-cell-sweep"},
+    }
+    if rank == 0 and not args.no_cpu_baseline:
+        out["cpu_baseline"] = cpu_baseline(w, args.cpu_seconds)
+    if rank == 0:
+        print(json.dumps(out))
+    if ws > 1:
+        torch.distributed.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

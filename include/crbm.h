@@ -1,0 +1,172 @@
+/*
+ * crbm.h — C ABI of the GB300 block-Gibbs sampler for the convolutional RBM
+ * (CRBM) that encodes the classical Shastry–Sutherland (SS) Ising lattice.
+ *
+ * Method: Brahma, Han, Razzaque, Patel, Salahuddin, "Hardware Acceleration of
+ * Frustrated Lattice Systems using Convolutional Restricted Boltzmann
+ * Machine", arXiv 2511.20911:
+ *   Eq. (1)      SS Hamiltonian H = J1 sum_nn s s + J2 sum_diag s s + h_z sum s
+ *   Eqs. (3)-(7) bond -> hidden unit mapping, a = 1/2 arccosh(exp(2|J|))
+ *   Eq. (8)      the ten 3x3 stride-2 convolutional filters of the unit cell
+ *   Eqs. (9)-(10) hidden | visible and visible | hidden conditionals
+ *   Sec. II.C and the appendix: the host writes weights, biases, sizes and
+ *   periodicity, runs sampling cycles, and reads samples back.
+ *
+ * Readings fixed by this library (the CPU oracle in oracle/ implements the
+ * same ones independently; trajectories agree bit for bit):
+ *   - spins and hidden units are +1/-1; H uses -h sum s (h > 0 favours +1);
+ *   - a bond of coupling J has K = -beta J, weight a = 0.5*acosh(exp(2|K|)),
+ *     coefficient +1 on its first endpoint and s = (K >= 0 ? +1 : -1) on its
+ *     second; hidden bias 0; visible bias beta*h;
+ *   - J, J', h are rounded to the nearest 1/16 (Q.4 fixed point,
+ *     |16 x| <= 2047), so energies are exact integers in units of 1/16;
+ *   - acceptance: a unit becomes +1 iff u < thr(y), u a 32-bit Philox-4x32-10
+ *     word, thr(y) = min(2^32-1, nearbyint(2^32 / (1 + exp(-y)))) in double;
+ *   - Philox counter (cell, sweep, chain, tag), key (seed lo, seed hi): hidden
+ *     bond k uses word k&3 of tag k>>2; the spin at window offset (r, c) uses
+ *     word 2r+c of tag 4; the initial spin is +1 iff that word of tag 5 at
+ *     sweep 0 is < 2^31.
+ *
+ * Conventions for every function:
+ *   - return CRBM_OK (0) or a negative CRBM_E* code; crbm_last_error() then
+ *     holds a message.  No C++ exception crosses this boundary.
+ *   - the caller owns every host buffer; the context owns all device memory.
+ *   - a context is bound to the CUDA device current at crbm_create and to the
+ *     stream given there; calls on one context are not thread-safe.
+ *   - crbm_sweep is asynchronous on that stream; every function that returns
+ *     data to the host synchronises the stream first.
+ */
+#ifndef CRBM_H
+#define CRBM_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#define CRBM_OK 0
+#define CRBM_EINVAL -1       /* bad argument or buffer size */
+#define CRBM_ENOMEM -2       /* device or host allocation failed */
+#define CRBM_ECUDA -3        /* a CUDA runtime call failed */
+#define CRBM_ETIMEOUT -4     /* a bounded device-side wait gave up */
+#define CRBM_EUNSUPPORTED -5 /* valid request this build cannot serve */
+
+#define CRBM_NSUM 11 /* per-chain observable sums, see crbm_observables */
+
+/* Layout of a context's lattice state on the device. */
+#define CRBM_LAYOUT_AUTO 0   /* SMEM for L <= CRBM_SMEM_MAX_L, else STREAM */
+#define CRBM_LAYOUT_SMEM 1   /* whole lattice resident in shared memory */
+#define CRBM_LAYOUT_STREAM 2 /* lattice in HBM, one tiled launch per sweep */
+#define CRBM_SMEM_MAX_L 96
+
+typedef struct crbm_ctx crbm_ctx;
+
+/* One filter of Eq. (8): the bond between two sites of the 3x3 window
+ * (row, col offsets in [0, 2]); cls 0 = J (J1), 1 = J' (J2). */
+typedef struct {
+    int8_t r1, c1, r2, c2;
+    uint8_t cls;
+} crbm_bond;
+
+typedef struct {
+    int32_t L;        /* L x L spins, 3 <= L <= 4096 */
+    int32_t periodic; /* 1 = periodic in both directions, 0 = open (zero padded) */
+    const crbm_bond* bonds; /* NULL -> the ten SS filters of Fig. 1 */
+    int32_t n_bonds;        /* 1..16 when bonds != NULL */
+    /* parameter points p = 0..n_params-1 (host arrays of length n_params) */
+    const double* J;
+    const double* Jp;
+    const double* h;
+    const double* beta;
+    int32_t n_params;
+    /* chain -> parameter point (host array of n_chains), NULL -> contiguous
+     * equal blocks: p(c) = c * n_params / n_chains */
+    const int32_t* chain_param;
+    int32_t n_chains;       /* >= 1 */
+    uint64_t seed;          /* Philox key */
+    int32_t measure_every;  /* accumulate observables after every K-th sweep, 0 = never */
+    int32_t series_len;     /* per-chain time-series capacity in measurements, 0 = none */
+    int32_t sq_every;       /* accumulate spin correlations every K_S sweeps, 0 = never */
+    int32_t layout;         /* CRBM_LAYOUT_* */
+    void* stream;           /* cudaStream_t for all work; NULL = legacy default stream */
+} crbm_params;
+
+/* Build the model (Eqs. 3-8), the threshold tables, allocate device state and
+ * draw the initial spins (tag 5) on the stream.  *out receives the context.
+ * Errors: CRBM_EINVAL (bad sizes, couplings outside Q.4 range, beta < 0 or
+ * NaN, bond outside the window), CRBM_ENOMEM, CRBM_ECUDA. */
+int crbm_create(crbm_ctx** out, const crbm_params* params);
+
+/* Free all device memory; NULL is ignored. */
+void crbm_destroy(crbm_ctx* ctx);
+
+/* Run n_sweeps sweeps (Sec. II.B: all hidden units from Eq. 9, then all spins
+ * from Eq. 10), continuing the global sweep counter.  Asynchronous.
+ * Errors: CRBM_EINVAL (n_sweeps < 0 or counter past 2^32-1), CRBM_ECUDA. */
+int crbm_sweep(crbm_ctx* ctx, int64_t n_sweeps);
+
+/* Global number of sweeps done since creation (or since crbm_load). */
+int64_t crbm_sweep_count(const crbm_ctx* ctx);
+
+/* Per-chain exact integer sums over measurements (measure_every), host array
+ * out[n_chains][CRBM_NSUM] int64 = {n, sum NJ, sum NJ', sum M, sum |M|,
+ * sum NJ^2, sum NJ'^2, sum M^2, sum NJ NJ', sum NJ M, sum NJ' M}, where for
+ * one configuration NJ = sum over J bonds of s_i s_j, NJ' likewise over J'
+ * bonds, M = sum s (so E = J NJ + J' NJ' - h M).  n_out = number of int64s.
+ * Synchronises the stream. */
+int crbm_observables(crbm_ctx* ctx, int64_t* out, size_t n_out);
+
+/* Time series, host array out[series_len][n_chains][3] int32 = (NJ, NJ', M)
+ * per measurement (entries past the number of measurements are zero). */
+int crbm_series(crbm_ctx* ctx, int32_t* out, size_t n_out);
+
+/* Spin-correlation sums of Sec. IV.B, host array out[n_params][L*L] int64:
+ * out[p][dR*L+dC] = sum over sampled configurations of chains at p of
+ * sum_r s_r s_{r+d} (periodic lattices only), and n_samples[p] (may be NULL). */
+int crbm_correlations(crbm_ctx* ctx, int64_t* out, size_t n_out, int64_t* n_samples);
+
+/* Static structure factor per spin, host array out[n_params][L*L] double:
+ * S(q) = (1/N) <|sum_r s_r e^{i q.r}|^2>, q = 2 pi (nR, nC) / L, from the
+ * correlation sums (Eq. 11 with the 1/N of the text's per-spin plots). */
+int crbm_structure_factor(crbm_ctx* ctx, double* out, size_t n_out);
+
+/* Zero every accumulator (sums, series, correlations). */
+int crbm_reset_observables(crbm_ctx* ctx);
+
+/* Spins as int8 +-1, host array [n_chains][L][L]. */
+int crbm_get_spins(crbm_ctx* ctx, int8_t* out, size_t n_out);
+int crbm_set_spins(crbm_ctx* ctx, const int8_t* in, size_t n_in);
+
+/* Threshold tables, host array [n_params][10 + (2DJ+1)(2DJ'+1)] uint32:
+ * Th[cls][m+2] (m in -2..2) then Tv[nJ+DJ][nJ'+DJ'].  dims may be NULL; else
+ * dims[0] = DJ, dims[1] = DJ'. */
+int crbm_get_tables(crbm_ctx* ctx, uint32_t* out, size_t n_out, int32_t* dims);
+
+/* Which layout the context runs (CRBM_LAYOUT_SMEM or CRBM_LAYOUT_STREAM). */
+int crbm_layout(const crbm_ctx* ctx);
+
+/* Kernel launches issued by this context since creation. */
+int64_t crbm_launch_count(const crbm_ctx* ctx);
+
+/* Checkpoint: serialise spins, sweep counter, seed and accumulators into a
+ * caller buffer.  With buf == NULL, *n receives the size needed.  Resume is
+ * bit-exact because every draw is a function of (cell, sweep, chain, tag). */
+int crbm_save(crbm_ctx* ctx, void* buf, size_t* n);
+int crbm_load(crbm_ctx* ctx, const void* buf, size_t n);
+
+/* Evaluate the library's device Philox-4x32-10 (Salmon et al., SC'11) on n
+ * host inputs in[n][6] = (c0, c1, c2, c3, k0, k1) into host out[n][4], on the
+ * current device's legacy stream.  For verification of the generator that
+ * keys every draw; synchronous.  Errors: CRBM_EINVAL, CRBM_ENOMEM, CRBM_ECUDA. */
+int crbm_philox(const uint32_t* in, uint32_t* out, size_t n);
+
+/* Message for the last failed call on ctx (or of the last failed
+ * crbm_create when ctx is NULL).  Never NULL. */
+const char* crbm_last_error(const crbm_ctx* ctx);
+
+#ifdef __cplusplus
+}
+#endif
+#endif

@@ -1,0 +1,271 @@
+"""Python binding of the GB300 CRBM block-Gibbs sampler (include/crbm.h).
+
+Argument marshalling only: every step of the sampling path runs in the CUDA
+kernels of ``libcrbm.so``.  PyTorch is used for the CUDA stream (the current
+torch stream is handed to the library); the library owns its device memory.
+There is no CPU fallback: if the compiled library is missing this module
+raises on first use.
+
+Method: Brahma et al., arXiv 2511.20911 -- the Shastry–Sutherland Ising
+lattice (Eq. 1) mapped onto a convolutional RBM (Eqs. 3-8) and sampled by
+block Gibbs sweeps (Eqs. 9-10).
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+
+import numpy as np
+
+from ._build import LIB, build
+
+CRBM_OK, CRBM_EINVAL, CRBM_ENOMEM, CRBM_ECUDA, CRBM_ETIMEOUT, CRBM_EUNSUPPORTED = 0, -1, -2, -3, -4, -5
+CRBM_NSUM = 11
+CRBM_LAYOUT_AUTO, CRBM_LAYOUT_SMEM, CRBM_LAYOUT_STREAM = 0, 1, 2
+CRBM_SMEM_MAX_L = 96
+SUM_FIELDS = ("n", "NJ", "NJp", "M", "absM", "NJ2", "NJp2", "M2", "NJ_NJp", "NJ_M", "NJp_M")
+
+# Names of every entry point include/crbm.h declares.
+ABI_FUNCTIONS = (
+    "crbm_create", "crbm_destroy", "crbm_sweep", "crbm_sweep_count", "crbm_observables",
+    "crbm_series", "crbm_correlations", "crbm_structure_factor", "crbm_reset_observables",
+    "crbm_get_spins", "crbm_set_spins", "crbm_get_tables", "crbm_layout", "crbm_launch_count",
+    "crbm_save", "crbm_load", "crbm_philox", "crbm_last_error",
+)
+
+
+class CrbmError(RuntimeError):
+    def __init__(self, code, msg):
+        super().__init__(f"crbm error {code}: {msg}")
+        self.code = code
+
+
+class crbm_bond(ctypes.Structure):
+    _fields_ = [("r1", ctypes.c_int8), ("c1", ctypes.c_int8), ("r2", ctypes.c_int8),
+                ("c2", ctypes.c_int8), ("cls", ctypes.c_uint8)]
+
+
+class crbm_params(ctypes.Structure):
+    _fields_ = [("L", ctypes.c_int32), ("periodic", ctypes.c_int32),
+                ("bonds", ctypes.POINTER(crbm_bond)), ("n_bonds", ctypes.c_int32),
+                ("J", ctypes.POINTER(ctypes.c_double)), ("Jp", ctypes.POINTER(ctypes.c_double)),
+                ("h", ctypes.POINTER(ctypes.c_double)), ("beta", ctypes.POINTER(ctypes.c_double)),
+                ("n_params", ctypes.c_int32), ("chain_param", ctypes.POINTER(ctypes.c_int32)),
+                ("n_chains", ctypes.c_int32), ("seed", ctypes.c_uint64),
+                ("measure_every", ctypes.c_int32), ("series_len", ctypes.c_int32),
+                ("sq_every", ctypes.c_int32), ("layout", ctypes.c_int32),
+                ("stream", ctypes.c_void_p)]
+
+
+_lib = None
+
+
+def load_library(path: str | None = None):
+    """Load libcrbm.so (building it if absent and nvcc is available)."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    p = path or LIB
+    if not os.path.exists(p):
+        p = build()
+    lib = ctypes.CDLL(p)
+    c = ctypes
+    vp = c.c_void_p
+    sigs = {
+        "crbm_create": (c.c_int, [c.POINTER(vp), c.POINTER(crbm_params)]),
+        "crbm_destroy": (None, [vp]),
+        "crbm_sweep": (c.c_int, [vp, c.c_int64]),
+        "crbm_sweep_count": (c.c_int64, [vp]),
+        "crbm_observables": (c.c_int, [vp, c.POINTER(c.c_int64), c.c_size_t]),
+        "crbm_series": (c.c_int, [vp, c.POINTER(c.c_int32), c.c_size_t]),
+        "crbm_correlations": (c.c_int, [vp, c.POINTER(c.c_int64), c.c_size_t, c.POINTER(c.c_int64)]),
+        "crbm_structure_factor": (c.c_int, [vp, c.POINTER(c.c_double), c.c_size_t]),
+        "crbm_reset_observables": (c.c_int, [vp]),
+        "crbm_get_spins": (c.c_int, [vp, c.POINTER(c.c_int8), c.c_size_t]),
+        "crbm_set_spins": (c.c_int, [vp, c.POINTER(c.c_int8), c.c_size_t]),
+        "crbm_get_tables": (c.c_int, [vp, c.POINTER(c.c_uint32), c.c_size_t, c.POINTER(c.c_int32)]),
+        "crbm_layout": (c.c_int, [vp]),
+        "crbm_launch_count": (c.c_int64, [vp]),
+        "crbm_save": (c.c_int, [vp, vp, c.POINTER(c.c_size_t)]),
+        "crbm_load": (c.c_int, [vp, vp, c.c_size_t]),
+        "crbm_philox": (c.c_int, [c.POINTER(c.c_uint32), c.POINTER(c.c_uint32), c.c_size_t]),
+        "crbm_last_error": (c.c_char_p, [vp]),
+    }
+    for name, (res, args) in sigs.items():
+        fn = getattr(lib, name)
+        fn.restype = res
+        fn.argtypes = args
+    _lib = lib
+    return lib
+
+
+def _ptr(a, ct):
+    return a.ctypes.data_as(ctypes.POINTER(ct))
+
+
+def _check(rc, ctx=None):
+    if rc != CRBM_OK:
+        msg = load_library().crbm_last_error(ctx)
+        raise CrbmError(rc, msg.decode() if msg else "")
+
+
+def current_stream_handle():
+    """The raw cudaStream_t of torch's current stream (0 if torch has no CUDA)."""
+    import torch
+    if not torch.cuda.is_available():
+        raise CrbmError(CRBM_ECUDA, "no CUDA device: the sampler runs only on the GPU")
+    return torch.cuda.current_stream().cuda_stream
+
+
+class Sampler:
+    """One context of include/crbm.h: chains of L x L spins at parameter points.
+
+    params: dict with equal-length sequences J, Jp, h, beta (one entry per
+    parameter point); chain_param maps each chain to a point.
+    """
+
+    def __init__(self, L, params, n_chains, chain_param=None, seed=1, periodic=True,
+                 bonds=None, measure_every=1, series_len=0, sq_every=0,
+                 layout=CRBM_LAYOUT_AUTO, stream=None):
+        lib = load_library()
+        self.L, self.n_chains = int(L), int(n_chains)
+        self._J = np.ascontiguousarray(params["J"], np.float64)
+        self._Jp = np.ascontiguousarray(params["Jp"], np.float64)
+        self._h = np.ascontiguousarray(params["h"], np.float64)
+        self._beta = np.ascontiguousarray(params["beta"], np.float64)
+        self.n_params = len(self._J)
+        self.series_len, self.sq_every = int(series_len), int(sq_every)
+        self._cp = None if chain_param is None else np.ascontiguousarray(chain_param, np.int32)
+        if self._cp is not None and len(self._cp) != self.n_chains:
+            raise CrbmError(CRBM_EINVAL, "chain_param must have n_chains entries")
+        self._bonds = None
+        if bonds is not None:
+            self._bonds = (crbm_bond * len(bonds))(*[crbm_bond(*b) for b in bonds])
+        if stream is None:
+            stream = current_stream_handle()
+        p = crbm_params()
+        p.L, p.periodic = self.L, int(bool(periodic))
+        p.bonds = self._bonds if self._bonds is not None else None
+        p.n_bonds = len(bonds) if bonds is not None else 0
+        p.J, p.Jp = _ptr(self._J, ctypes.c_double), _ptr(self._Jp, ctypes.c_double)
+        p.h, p.beta = _ptr(self._h, ctypes.c_double), _ptr(self._beta, ctypes.c_double)
+        p.n_params = self.n_params
+        p.chain_param = _ptr(self._cp, ctypes.c_int32) if self._cp is not None else None
+        p.n_chains = self.n_chains
+        p.seed = int(seed) & 0xFFFFFFFFFFFFFFFF
+        p.measure_every, p.series_len, p.sq_every = int(measure_every), self.series_len, self.sq_every
+        p.layout = int(layout)
+        p.stream = ctypes.c_void_p(int(stream)) if stream else None
+        h = ctypes.c_void_p()
+        _check(lib.crbm_create(ctypes.byref(h), ctypes.byref(p)))
+        self._ctx = h
+        self._lib = lib
+
+    def close(self):
+        if getattr(self, "_ctx", None):
+            self._lib.crbm_destroy(self._ctx)
+            self._ctx = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def sweep(self, n_sweeps):
+        _check(self._lib.crbm_sweep(self._ctx, int(n_sweeps)), self._ctx)
+
+    @property
+    def sweep_count(self):
+        return int(self._lib.crbm_sweep_count(self._ctx))
+
+    @property
+    def launch_count(self):
+        return int(self._lib.crbm_launch_count(self._ctx))
+
+    @property
+    def layout(self):
+        return int(self._lib.crbm_layout(self._ctx))
+
+    def observables(self):
+        out = np.zeros((self.n_chains, CRBM_NSUM), np.int64)
+        _check(self._lib.crbm_observables(self._ctx, _ptr(out, ctypes.c_int64), out.size), self._ctx)
+        return out
+
+    def series(self):
+        out = np.zeros((self.series_len, self.n_chains, 3), np.int32)
+        _check(self._lib.crbm_series(self._ctx, _ptr(out, ctypes.c_int32), out.size), self._ctx)
+        return out
+
+    def correlations(self):
+        out = np.zeros((self.n_params, self.L, self.L), np.int64)
+        ns = np.zeros(self.n_params, np.int64)
+        _check(self._lib.crbm_correlations(self._ctx, _ptr(out, ctypes.c_int64), out.size,
+                                           _ptr(ns, ctypes.c_int64)), self._ctx)
+        return out, ns
+
+    def structure_factor(self):
+        out = np.zeros((self.n_params, self.L, self.L), np.float64)
+        _check(self._lib.crbm_structure_factor(self._ctx, _ptr(out, ctypes.c_double), out.size),
+               self._ctx)
+        return out
+
+    def reset_observables(self):
+        _check(self._lib.crbm_reset_observables(self._ctx), self._ctx)
+
+    def get_spins(self, out=None):
+        if out is None:
+            out = np.zeros((self.n_chains, self.L, self.L), np.int8)
+        _check(self._lib.crbm_get_spins(self._ctx, _ptr(out, ctypes.c_int8), out.size), self._ctx)
+        return out
+
+    def set_spins(self, spins):
+        a = np.ascontiguousarray(spins, np.int8)
+        _check(self._lib.crbm_set_spins(self._ctx, _ptr(a, ctypes.c_int8), a.size), self._ctx)
+
+    def tables(self):
+        dims = np.zeros(2, np.int32)
+        _check(self._lib.crbm_get_tables(self._ctx, None, 0, _ptr(dims, ctypes.c_int32)), self._ctx)
+        dj, djp = int(dims[0]), int(dims[1])
+        ntab = 10 + (2 * dj + 1) * (2 * djp + 1)
+        out = np.zeros((self.n_params, ntab), np.uint32)
+        _check(self._lib.crbm_get_tables(self._ctx, _ptr(out, ctypes.c_uint32), out.size, None),
+               self._ctx)
+        return out, (dj, djp)
+
+    def save(self):
+        n = ctypes.c_size_t(0)
+        _check(self._lib.crbm_save(self._ctx, None, ctypes.byref(n)), self._ctx)
+        buf = np.zeros(n.value, np.uint8)
+        _check(self._lib.crbm_save(self._ctx, buf.ctypes.data_as(ctypes.c_void_p), ctypes.byref(n)),
+               self._ctx)
+        return buf
+
+    def load(self, buf):
+        b = np.ascontiguousarray(buf, np.uint8)
+        _check(self._lib.crbm_load(self._ctx, b.ctypes.data_as(ctypes.c_void_p), b.size), self._ctx)
+
+
+def crbm_philox(inputs):
+    """Device Philox-4x32-10 on rows (c0, c1, c2, c3, k0, k1) -> rows of 4 words."""
+    a = np.ascontiguousarray(inputs, np.uint32).reshape(-1, 6)
+    out = np.zeros((len(a), 4), np.uint32)
+    _check(load_library().crbm_philox(_ptr(a, ctypes.c_uint32), _ptr(out, ctypes.c_uint32), len(a)))
+    return out
+
+
+# C-ABI names, for callers that prefer the flat interface.
+def crbm_create(L, params, n_chains, **kw):
+    return Sampler(L, params, n_chains, **kw)
+
+
+def crbm_sweep(s: Sampler, n):
+    s.sweep(n)
+
+
+def crbm_observables(s: Sampler):
+    return s.observables()
+
+
+def crbm_destroy(s: Sampler):
+    s.close()

@@ -1,0 +1,633 @@
+// Host runtime of the CRBM sampler: model construction (Eqs. 3-8 of arXiv
+// 2511.20911), threshold tables, device buffers, launches and the C ABI of
+// include/crbm.h.  Compiled with -ffp-contract=off: every table entry is the
+// plain left-to-right double evaluation of the formulas in crbm.h.
+#include "../../include/crbm.h"
+#include "crbm_internal.h"
+
+#include <algorithm>
+#include <cmath>
+#include <cstdio>
+#include <cstdlib>
+#include <cstring>
+#include <new>
+#include <string>
+#include <vector>
+
+using namespace crbm;
+
+struct crbm_ctx {
+    Geometry g{};
+    int n_chains = 0, n_words = 0, n_params = 0;
+    int layout = CRBM_LAYOUT_SMEM;
+    int warps = 8;
+    uint64_t seed = 0;
+    int measure_every = 0, series_len = 0, sq_every = 0;
+    int64_t sweeps = 0;     // global sweep counter
+    int64_t meas = 0;       // measurements since the last reset
+    int64_t sq_meas = 0;    // correlation samples since the last reset
+    int64_t launches = 0;
+    cudaStream_t stream = nullptr;
+    int device = 0;
+    std::vector<int32_t> chain_param;
+    std::vector<int32_t> q[3];     // quantised J, J', h per point
+    std::vector<double> beta;
+    std::vector<uint32_t> tables;  // [n_params][nTab]
+    DeviceState d;
+    std::string err;
+};
+
+namespace {
+
+thread_local std::string g_create_error;
+
+// The ten filters of the SS unit cell (Fig. 1): horizontal bonds of window
+// rows 0 and 1, vertical bonds of columns 0 and 1 (class 0, J1), and the
+// orthogonal dimers "\" on plaquette (0,0) and "/" on plaquette (1,1)
+// (class 1, J2).  Window offsets are (row, col) in [0, 2].
+const crbm_bond kSSFilters[10] = {
+    {0, 0, 0, 1, 0}, {0, 1, 0, 2, 0}, {1, 0, 1, 1, 0}, {1, 1, 1, 2, 0}, {0, 0, 1, 0, 0},
+    {1, 0, 2, 0, 0}, {0, 1, 1, 1, 0}, {1, 1, 2, 1, 0}, {0, 0, 1, 1, 1}, {1, 2, 2, 1, 1},
+};
+
+int fail(crbm_ctx* ctx, int code, const std::string& msg) {
+    if (ctx)
+        ctx->err = msg;
+    else
+        g_create_error = msg;
+    return code;
+}
+
+int cuda_fail(crbm_ctx* ctx, cudaError_t e, const char* what) {
+    return fail(ctx, CRBM_ECUDA, std::string(what) + ": " + cudaGetErrorString(e));
+}
+
+// Q.4 fixed point: nearest multiple of 1/16, |16 x| <= 2047.
+bool to_q4(double x, int32_t& q) {
+    if (!std::isfinite(x)) return false;
+    const double r = std::nearbyint(16.0 * x);
+    if (r < -2047.0 || r > 2047.0) return false;
+    q = static_cast<int32_t>(r);
+    return true;
+}
+
+// Eqs. (5)-(7): a = 1/2 arccosh(exp(2|K|)), K = -beta J; s = sign of K (+1 at 0).
+void bond_weight(double beta, double J, double& a, int& s) {
+    const double K = -beta * J;
+    a = 0.5 * std::acosh(std::exp(2.0 * std::fabs(K)));
+    s = (K >= 0.0) ? 1 : -1;
+}
+
+// Sigmoid of Eqs. (9)-(10) as a 32-bit acceptance threshold.
+uint32_t accept_threshold(double y) {
+    const double prob = 1.0 / (1.0 + std::exp(-y));
+    const double r = std::nearbyint(std::ldexp(prob, 32));
+    if (r >= 4294967295.0) return 0xFFFFFFFFu;
+    if (r <= 0.0) return 0u;
+    return static_cast<uint32_t>(r);
+}
+
+int site_index(const Geometry& g, int i, int j, int r, int c) {
+    int R = 2 * i + r, C = 2 * j + c;
+    if (R >= g.L || C >= g.L) {
+        if (!g.periodic) return -1;
+        R %= g.L;
+        C %= g.L;
+    }
+    return R * g.L + C;
+}
+
+// Geometry, visible field ranges and the generic incidence list.
+int build_geometry(crbm_ctx* ctx, const crbm_params* p, std::vector<uint32_t>& inc,
+                   std::vector<int32_t>& inc_off) {
+    Geometry& g = ctx->g;
+    const crbm_bond* bonds = p->bonds ? p->bonds : kSSFilters;
+    const int nb = p->bonds ? p->n_bonds : 10;
+    if (nb < 1 || nb > kMaxBonds) return fail(nullptr, CRBM_EINVAL, "n_bonds must be in 1..16");
+    for (int k = 0; k < nb; ++k) {
+        const crbm_bond& b = bonds[k];
+        if (b.r1 < 0 || b.r1 > 2 || b.c1 < 0 || b.c1 > 2 || b.r2 < 0 || b.r2 > 2 || b.c2 < 0 ||
+            b.c2 > 2 || b.cls > 1 || (b.r1 == b.r2 && b.c1 == b.c2))
+            return fail(nullptr, CRBM_EINVAL, "bond " + std::to_string(k) + " is not a bond of the 3x3 window");
+        g.r1[k] = b.r1; g.c1[k] = b.c1; g.r2[k] = b.r2; g.c2[k] = b.c2; g.cls[k] = b.cls;
+    }
+    g.L = p->L;
+    g.W = (p->L + 1) / 2;
+    g.N = p->L * p->L;
+    g.n_cells = g.W * g.W;
+    g.nb = nb;
+    g.n_calls = (nb + 3) / 4;
+    g.periodic = p->periodic ? 1 : 0;
+    bool same = (nb == 10);
+    for (int k = 0; same && k < 10; ++k)
+        same = std::memcmp(&bonds[k], &kSSFilters[k], sizeof(crbm_bond)) == 0;
+    g.canonical = (same && g.periodic && (g.L % 2 == 0)) ? 1 : 0;
+
+    std::vector<int> deg(2 * static_cast<size_t>(g.N), 0);
+    std::vector<std::vector<uint32_t>> per_site(g.N);
+    g.n_real_bonds[0] = g.n_real_bonds[1] = 0;
+    for (int i = 0; i < g.W; ++i)
+        for (int j = 0; j < g.W; ++j)
+            for (int k = 0; k < nb; ++k) {
+                const int s1 = site_index(g, i, j, g.r1[k], g.c1[k]);
+                const int s2 = site_index(g, i, j, g.r2[k], g.c2[k]);
+                const uint32_t hid = static_cast<uint32_t>((i * g.W + j) * nb + k);
+                const uint32_t cls = g.cls[k];
+                if (s1 >= 0) {
+                    deg[cls * g.N + s1]++;
+                    per_site[s1].push_back(hid | (cls << 30));
+                }
+                if (s2 >= 0) {
+                    deg[cls * g.N + s2]++;
+                    per_site[s2].push_back(hid | (cls << 30) | (1u << 31));
+                }
+                if (s1 >= 0 && s2 >= 0) g.n_real_bonds[cls]++;
+            }
+    g.DJ = g.DJp = 0;
+    for (int s = 0; s < g.N; ++s) {
+        g.DJ = std::max(g.DJ, deg[s]);
+        g.DJp = std::max(g.DJp, deg[g.N + s]);
+    }
+    g.nTv = (2 * g.DJ + 1) * (2 * g.DJp + 1);
+    g.nTab = 10 + g.nTv;
+    if (g.canonical && (g.DJ != 4 || g.DJp != 1))
+        return fail(nullptr, CRBM_EINVAL, "internal: SS filters must give 4 J and 1 J' filter per spin");
+    inc.clear();
+    inc_off.assign(g.N + 1, 0);
+    for (int s = 0; s < g.N; ++s) {
+        inc_off[s] = static_cast<int32_t>(inc.size());
+        inc.insert(inc.end(), per_site[s].begin(), per_site[s].end());
+    }
+    inc_off[g.N] = static_cast<int32_t>(inc.size());
+    return CRBM_OK;
+}
+
+// Th[cls][m+2] = thr(2 a_cls m), Tv[nJ+DJ][nJ'+DJ'] = thr(2 (beta h + a_J nJ + a_J' nJ')).
+void point_tables(const Geometry& g, double beta, int32_t qJ, int32_t qJp, int32_t qh,
+                  uint32_t* out, int sgn[2]) {
+    double a[2];
+    bond_weight(beta, qJ / 16.0, a[0], sgn[0]);
+    bond_weight(beta, qJp / 16.0, a[1], sgn[1]);
+    for (int cls = 0; cls < 2; ++cls)
+        for (int m = -2; m <= 2; ++m) out[cls * 5 + m + 2] = accept_threshold(2.0 * a[cls] * m);
+    const double hd = qh / 16.0;
+    const int nP = 2 * g.DJp + 1;
+    for (int nJ = -g.DJ; nJ <= g.DJ; ++nJ)
+        for (int nJp = -g.DJp; nJp <= g.DJp; ++nJp) {
+            const double x = beta * hd + a[0] * nJ + a[1] * nJp;
+            out[10 + (nJ + g.DJ) * nP + (nJp + g.DJp)] = accept_threshold(2.0 * x);
+        }
+}
+
+template <typename T>
+int dalloc(crbm_ctx* ctx, T*& ptr, size_t count) {
+    if (count == 0) count = 1;
+    const cudaError_t e = cudaMalloc(reinterpret_cast<void**>(&ptr), count * sizeof(T));
+    if (e != cudaSuccess) {
+        ptr = nullptr;
+        return fail(ctx, CRBM_ENOMEM, std::string("cudaMalloc: ") + cudaGetErrorString(e));
+    }
+    return CRBM_OK;
+}
+
+void free_device(DeviceState& d) {
+    void* ptrs[] = {d.v, d.tab, d.sneg, d.inc, d.inc_off, d.sums, d.series, d.corr,
+                    d.seg, d.segmask, d.spins8, d.vtmp, d.err};
+    for (void* p : ptrs)
+        if (p) cudaFree(p);
+    d = DeviceState{};
+}
+
+int default_warps(const Geometry& g) {
+    if (const char* env = std::getenv("CRBM_WARPS")) {
+        const int w = std::atoi(env);
+        if (w >= 1 && w <= 32) return w;
+    }
+    // about nine cells per warp, up to 16 warps per CTA
+    return std::max(1, std::min(16, (g.n_cells + 8) / 9));
+}
+
+}  // namespace
+
+extern "C" {
+
+int crbm_create(crbm_ctx** out, const crbm_params* p) {
+    if (!out || !p) return fail(nullptr, CRBM_EINVAL, "null argument");
+    *out = nullptr;
+    if (p->L < 3 || p->L > 4096) return fail(nullptr, CRBM_EINVAL, "L must be in 3..4096");
+    if (p->n_params < 1 || !p->J || !p->Jp || !p->h || !p->beta)
+        return fail(nullptr, CRBM_EINVAL, "need n_params >= 1 and J, Jp, h, beta arrays");
+    if (p->n_chains < 1) return fail(nullptr, CRBM_EINVAL, "n_chains must be >= 1");
+    if (p->measure_every < 0 || p->series_len < 0 || p->sq_every < 0)
+        return fail(nullptr, CRBM_EINVAL, "measure_every, series_len and sq_every must be >= 0");
+    if (p->layout < CRBM_LAYOUT_AUTO || p->layout > CRBM_LAYOUT_STREAM)
+        return fail(nullptr, CRBM_EINVAL, "unknown layout");
+    crbm_ctx* ctx = new (std::nothrow) crbm_ctx();
+    if (!ctx) return fail(nullptr, CRBM_ENOMEM, "host allocation failed");
+    std::vector<uint32_t> inc;
+    std::vector<int32_t> inc_off;
+    int rc = build_geometry(ctx, p, inc, inc_off);
+    if (rc) {
+        delete ctx;
+        return rc;
+    }
+    Geometry& g = ctx->g;
+    ctx->layout = p->layout == CRBM_LAYOUT_AUTO
+                      ? (p->L <= CRBM_SMEM_MAX_L ? CRBM_LAYOUT_SMEM : CRBM_LAYOUT_STREAM)
+                      : p->layout;
+    if (ctx->layout == CRBM_LAYOUT_SMEM && p->L > CRBM_SMEM_MAX_L) {
+        delete ctx;
+        return fail(nullptr, CRBM_EINVAL, "SMEM layout needs L <= CRBM_SMEM_MAX_L");
+    }
+    if (ctx->layout == CRBM_LAYOUT_STREAM) {
+        delete ctx;
+        return fail(nullptr, CRBM_EUNSUPPORTED, "streamed layout not available in this build");
+    }
+    if (ctx->layout == CRBM_LAYOUT_SMEM && smem_bytes_smem_layout(g) > 227 * 1024) {
+        delete ctx;
+        return fail(nullptr, CRBM_EUNSUPPORTED,
+                    "lattice, hidden layer and threshold columns exceed 227 KB of shared memory");
+    }
+    if (p->sq_every > 0 && !g.periodic) {
+        delete ctx;
+        return fail(nullptr, CRBM_EINVAL, "spin correlations need a periodic lattice");
+    }
+    ctx->n_chains = p->n_chains;
+    ctx->n_words = (p->n_chains + 31) / 32;
+    ctx->n_params = p->n_params;
+    ctx->seed = p->seed;
+    ctx->measure_every = p->measure_every;
+    ctx->series_len = p->series_len;
+    ctx->sq_every = p->sq_every;
+    ctx->stream = static_cast<cudaStream_t>(p->stream);
+    ctx->warps = default_warps(g);
+    for (int k = 0; k < 3; ++k) ctx->q[k].resize(p->n_params);
+    ctx->beta.assign(p->beta, p->beta + p->n_params);
+    for (int i = 0; i < p->n_params; ++i) {
+        if (!to_q4(p->J[i], ctx->q[0][i]) || !to_q4(p->Jp[i], ctx->q[1][i]) ||
+            !to_q4(p->h[i], ctx->q[2][i])) {
+            delete ctx;
+            return fail(nullptr, CRBM_EINVAL, "parameter point " + std::to_string(i) +
+                                                  ": J, J', h must be finite with |16 x| <= 2047");
+        }
+        if (!(p->beta[i] >= 0.0) || !(p->beta[i] <= 1.0e6)) {
+            delete ctx;
+            return fail(nullptr, CRBM_EINVAL, "parameter point " + std::to_string(i) + ": beta must be in [0, 1e6]");
+        }
+    }
+    ctx->chain_param.resize(p->n_chains);
+    for (int c = 0; c < p->n_chains; ++c) {
+        const int32_t pp = p->chain_param
+                               ? p->chain_param[c]
+                               : static_cast<int32_t>(static_cast<int64_t>(c) * p->n_params / p->n_chains);
+        if (pp < 0 || pp >= p->n_params) {
+            delete ctx;
+            return fail(nullptr, CRBM_EINVAL, "chain_param[" + std::to_string(c) + "] out of range");
+        }
+        ctx->chain_param[c] = pp;
+    }
+    // Per-point tables and signs, then lane-expanded per word.
+    ctx->tables.resize(static_cast<size_t>(p->n_params) * g.nTab);
+    std::vector<int> sgn(2 * static_cast<size_t>(p->n_params));
+    for (int i = 0; i < p->n_params; ++i)
+        point_tables(g, ctx->beta[i], ctx->q[0][i], ctx->q[1][i], ctx->q[2][i],
+                     &ctx->tables[static_cast<size_t>(i) * g.nTab], &sgn[2 * i]);
+    const int nw = ctx->n_words, npad = nw * 32;
+    std::vector<uint32_t> tab(static_cast<size_t>(nw) * g.nTab * 32);
+    std::vector<uint32_t> sneg(2 * static_cast<size_t>(nw), 0u);
+    std::vector<int32_t> seg(33 * static_cast<size_t>(nw), 0);
+    std::vector<uint32_t> segmask(32 * static_cast<size_t>(nw), 0u);
+    for (int w = 0; w < nw; ++w) {
+        int nseg = 0;
+        for (int l = 0; l < 32; ++l) {
+            const int c = w * 32 + l;
+            const bool real = c < p->n_chains;
+            const int pp = real ? ctx->chain_param[c] : ctx->chain_param[0];
+            for (int e = 0; e < g.nTab; ++e)
+                tab[(static_cast<size_t>(w) * g.nTab + e) * 32 + l] = ctx->tables[static_cast<size_t>(pp) * g.nTab + e];
+            if (sgn[2 * pp] < 0) sneg[2 * w] |= 1u << l;
+            if (sgn[2 * pp + 1] < 0) sneg[2 * w + 1] |= 1u << l;
+            if (!real) continue;
+            int sidx = -1;
+            for (int s = 0; s < nseg; ++s)
+                if ((seg[33 * w + 1 + s] >> 8) == pp) sidx = s;
+            if (sidx < 0) {
+                sidx = nseg++;
+                seg[33 * w + 1 + sidx] = (pp << 8) | l;
+            }
+            segmask[32 * w + sidx] |= 1u << l;
+        }
+        seg[33 * w] = nseg;
+    }
+    // Device state.
+    cudaGetDevice(&ctx->device);
+    DeviceState& d = ctx->d;
+    const size_t N = static_cast<size_t>(g.N);
+    if ((rc = dalloc(ctx, d.v, nw * N)) || (rc = dalloc(ctx, d.tab, tab.size())) ||
+        (rc = dalloc(ctx, d.sneg, sneg.size())) || (rc = dalloc(ctx, d.inc, inc.size())) ||
+        (rc = dalloc(ctx, d.inc_off, inc_off.size())) ||
+        (rc = dalloc(ctx, d.sums, static_cast<size_t>(npad) * kNSum)) ||
+        (rc = dalloc(ctx, d.series, static_cast<size_t>(p->series_len) * npad * 3)) ||
+        (rc = dalloc(ctx, d.corr, p->sq_every > 0 ? static_cast<size_t>(p->n_params) * N : 1)) ||
+        (rc = dalloc(ctx, d.seg, seg.size())) || (rc = dalloc(ctx, d.segmask, segmask.size())) ||
+        (rc = dalloc(ctx, d.spins8, static_cast<size_t>(npad) * N)) || (rc = dalloc(ctx, d.err, 4))) {
+        g_create_error = ctx->err;
+        free_device(d);
+        delete ctx;
+        return rc;
+    }
+    cudaStream_t st = ctx->stream;
+    cudaError_t e = cudaSuccess;
+    auto h2d = [&](void* dst, const void* src, size_t bytes) {
+        if (e == cudaSuccess && bytes) e = cudaMemcpyAsync(dst, src, bytes, cudaMemcpyHostToDevice, st);
+    };
+    h2d(d.tab, tab.data(), tab.size() * 4);
+    h2d(d.sneg, sneg.data(), sneg.size() * 4);
+    h2d(d.inc, inc.data(), inc.size() * 4);
+    h2d(d.inc_off, inc_off.data(), inc_off.size() * 4);
+    h2d(d.seg, seg.data(), seg.size() * 4);
+    h2d(d.segmask, segmask.data(), segmask.size() * 4);
+    if (e == cudaSuccess) e = cudaMemsetAsync(d.sums, 0, static_cast<size_t>(npad) * kNSum * 8, st);
+    if (e == cudaSuccess && p->series_len)
+        e = cudaMemsetAsync(d.series, 0, static_cast<size_t>(p->series_len) * npad * 12, st);
+    if (e == cudaSuccess && p->sq_every)
+        e = cudaMemsetAsync(d.corr, 0, static_cast<size_t>(p->n_params) * N * 8, st);
+    if (e == cudaSuccess) e = cudaMemsetAsync(d.spins8, 1, static_cast<size_t>(npad) * N, st);
+    if (e == cudaSuccess) e = cudaMemsetAsync(d.err, 0, 4, st);
+    if (e == cudaSuccess)
+        e = launch_init(g, d.v, nw, static_cast<uint32_t>(ctx->seed),
+                        static_cast<uint32_t>(ctx->seed >> 32), st);
+    // The staged host vectors go out of scope: finish the copies first.
+    if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+    if (e != cudaSuccess) {
+        g_create_error = std::string("crbm_create: ") + cudaGetErrorString(e);
+        free_device(d);
+        delete ctx;
+        return CRBM_ECUDA;
+    }
+    ctx->launches = 1;
+    *out = ctx;
+    return CRBM_OK;
+}
+
+void crbm_destroy(crbm_ctx* ctx) {
+    if (!ctx) return;
+    int cur = 0;
+    cudaGetDevice(&cur);
+    if (cur != ctx->device) cudaSetDevice(ctx->device);
+    cudaStreamSynchronize(ctx->stream);
+    free_device(ctx->d);
+    if (cur != ctx->device) cudaSetDevice(cur);
+    delete ctx;
+}
+
+int crbm_sweep(crbm_ctx* ctx, int64_t n_sweeps) {
+    if (!ctx) return CRBM_EINVAL;
+    if (n_sweeps < 0) return fail(ctx, CRBM_EINVAL, "n_sweeps must be >= 0");
+    if (ctx->sweeps + n_sweeps > 4294967295LL)
+        return fail(ctx, CRBM_EINVAL, "the 32-bit sweep counter of the Philox key would overflow");
+    int64_t left = n_sweeps;
+    while (left > 0) {
+        // Chunks keep one launch within a few seconds on large grids.
+        const int chunk = static_cast<int>(std::min<int64_t>(left, 1 << 20));
+        SweepArgs a{};
+        a.g = ctx->g;
+        a.v = ctx->d.v;
+        a.tab = ctx->d.tab;
+        a.sneg = ctx->d.sneg;
+        a.inc = ctx->d.inc;
+        a.inc_off = ctx->d.inc_off;
+        a.sums = ctx->d.sums;
+        a.series = ctx->d.series;
+        a.corr = ctx->d.corr;
+        a.seg = ctx->d.seg;
+        a.segmask = ctx->d.segmask;
+        a.n_words = ctx->n_words;
+        a.n_chains_padded = ctx->n_words * 32;
+        a.key0 = static_cast<uint32_t>(ctx->seed);
+        a.key1 = static_cast<uint32_t>(ctx->seed >> 32);
+        a.t0 = static_cast<uint32_t>(ctx->sweeps);
+        a.n_sweeps = chunk;
+        a.measure_every = ctx->measure_every;
+        a.meas0 = ctx->meas;
+        a.series_len = ctx->series_len;
+        a.sq_every = ctx->sq_every;
+        const cudaError_t e = launch_sweep_smem(a, ctx->warps, ctx->stream);
+        if (e != cudaSuccess) return cuda_fail(ctx, e, "sweep launch");
+        ++ctx->launches;
+        const int64_t t0 = ctx->sweeps, t1 = ctx->sweeps + chunk;
+        if (ctx->measure_every > 0) ctx->meas += t1 / ctx->measure_every - t0 / ctx->measure_every;
+        if (ctx->sq_every > 0) ctx->sq_meas += t1 / ctx->sq_every - t0 / ctx->sq_every;
+        ctx->sweeps = t1;
+        left -= chunk;
+    }
+    return CRBM_OK;
+}
+
+int64_t crbm_sweep_count(const crbm_ctx* ctx) { return ctx ? ctx->sweeps : -1; }
+
+int64_t crbm_launch_count(const crbm_ctx* ctx) { return ctx ? ctx->launches : -1; }
+
+int crbm_layout(const crbm_ctx* ctx) { return ctx ? ctx->layout : CRBM_EINVAL; }
+
+int crbm_observables(crbm_ctx* ctx, int64_t* out, size_t n_out) {
+    if (!ctx || !out) return CRBM_EINVAL;
+    const size_t need = static_cast<size_t>(ctx->n_chains) * kNSum;
+    if (n_out < need) return fail(ctx, CRBM_EINVAL, "output buffer too small");
+    cudaError_t e = cudaMemcpyAsync(out, ctx->d.sums, need * 8, cudaMemcpyDeviceToHost, ctx->stream);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(ctx->stream);
+    return e == cudaSuccess ? CRBM_OK : cuda_fail(ctx, e, "crbm_observables");
+}
+
+int crbm_series(crbm_ctx* ctx, int32_t* out, size_t n_out) {
+    if (!ctx || !out) return CRBM_EINVAL;
+    const size_t per = static_cast<size_t>(ctx->n_chains) * 3;
+    if (n_out < per * ctx->series_len) return fail(ctx, CRBM_EINVAL, "output buffer too small");
+    cudaError_t e = cudaSuccess;
+    const size_t pitch = static_cast<size_t>(ctx->n_words) * 32 * 3 * 4;
+    if (ctx->series_len > 0)
+        e = cudaMemcpy2DAsync(out, per * 4, ctx->d.series, pitch, per * 4, ctx->series_len,
+                              cudaMemcpyDeviceToHost, ctx->stream);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(ctx->stream);
+    return e == cudaSuccess ? CRBM_OK : cuda_fail(ctx, e, "crbm_series");
+}
+
+int crbm_correlations(crbm_ctx* ctx, int64_t* out, size_t n_out, int64_t* n_samples) {
+    if (!ctx || !out) return CRBM_EINVAL;
+    if (ctx->sq_every <= 0) return fail(ctx, CRBM_EINVAL, "context created with sq_every = 0");
+    const size_t need = static_cast<size_t>(ctx->n_params) * ctx->g.N;
+    if (n_out < need) return fail(ctx, CRBM_EINVAL, "output buffer too small");
+    cudaError_t e = cudaMemcpyAsync(out, ctx->d.corr, need * 8, cudaMemcpyDeviceToHost, ctx->stream);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(ctx->stream);
+    if (e != cudaSuccess) return cuda_fail(ctx, e, "crbm_correlations");
+    if (n_samples) {
+        std::vector<int64_t> per(ctx->n_params, 0);
+        for (int c = 0; c < ctx->n_chains; ++c) per[ctx->chain_param[c]]++;
+        for (int i = 0; i < ctx->n_params; ++i) n_samples[i] = per[i] * ctx->sq_meas;
+    }
+    return CRBM_OK;
+}
+
+int crbm_structure_factor(crbm_ctx* ctx, double* out, size_t n_out) {
+    if (!ctx || !out) return CRBM_EINVAL;
+    const int L = ctx->g.L, N = ctx->g.N;
+    const size_t need = static_cast<size_t>(ctx->n_params) * N;
+    if (n_out < need) return fail(ctx, CRBM_EINVAL, "output buffer too small");
+    std::vector<int64_t> corr(need), ns(ctx->n_params);
+    const int rc = crbm_correlations(ctx, corr.data(), need, ns.data());
+    if (rc) return rc;
+    // S(q) = (1/N) sum_d <C(d)> cos(q.d): C(d) = C(-d), so the sine part cancels.
+    std::vector<double> cosk(L);
+    for (int k = 0; k < L; ++k) cosk[k] = std::cos(6.283185307179586476925286766559 * k / L);
+    for (int p = 0; p < ctx->n_params; ++p) {
+        const int64_t* c = &corr[static_cast<size_t>(p) * N];
+        for (int nR = 0; nR < L; ++nR)
+            for (int nC = 0; nC < L; ++nC) {
+                double s = 0.0;
+                for (int dR = 0; dR < L; ++dR)
+                    for (int dC = 0; dC < L; ++dC)
+                        s += static_cast<double>(c[dR * L + dC]) * cosk[(nR * dR + nC * dC) % L];
+                out[static_cast<size_t>(p) * N + nR * L + nC] = ns[p] > 0 ? s / (static_cast<double>(ns[p]) * N) : 0.0;
+            }
+    }
+    return CRBM_OK;
+}
+
+int crbm_reset_observables(crbm_ctx* ctx) {
+    if (!ctx) return CRBM_EINVAL;
+    const size_t npad = static_cast<size_t>(ctx->n_words) * 32;
+    cudaError_t e = cudaMemsetAsync(ctx->d.sums, 0, npad * kNSum * 8, ctx->stream);
+    if (e == cudaSuccess && ctx->series_len)
+        e = cudaMemsetAsync(ctx->d.series, 0, static_cast<size_t>(ctx->series_len) * npad * 12, ctx->stream);
+    if (e == cudaSuccess && ctx->sq_every)
+        e = cudaMemsetAsync(ctx->d.corr, 0, static_cast<size_t>(ctx->n_params) * ctx->g.N * 8, ctx->stream);
+    if (e != cudaSuccess) return cuda_fail(ctx, e, "crbm_reset_observables");
+    ctx->meas = 0;
+    ctx->sq_meas = 0;
+    return CRBM_OK;
+}
+
+int crbm_get_spins(crbm_ctx* ctx, int8_t* out, size_t n_out) {
+    if (!ctx || !out) return CRBM_EINVAL;
+    const size_t need = static_cast<size_t>(ctx->n_chains) * ctx->g.N;
+    if (n_out < need) return fail(ctx, CRBM_EINVAL, "output buffer too small");
+    cudaError_t e = launch_unpack(ctx->g, ctx->d.v, ctx->d.spins8, ctx->n_words, ctx->stream);
+    ++ctx->launches;
+    if (e == cudaSuccess) e = cudaMemcpyAsync(out, ctx->d.spins8, need, cudaMemcpyDeviceToHost, ctx->stream);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(ctx->stream);
+    return e == cudaSuccess ? CRBM_OK : cuda_fail(ctx, e, "crbm_get_spins");
+}
+
+int crbm_set_spins(crbm_ctx* ctx, const int8_t* in, size_t n_in) {
+    if (!ctx || !in) return CRBM_EINVAL;
+    const size_t need = static_cast<size_t>(ctx->n_chains) * ctx->g.N;
+    if (n_in < need) return fail(ctx, CRBM_EINVAL, "input buffer too small");
+    for (size_t x = 0; x < need; ++x)
+        if (in[x] != 1 && in[x] != -1) return fail(ctx, CRBM_EINVAL, "spins must be +1 or -1");
+    cudaError_t e = cudaMemcpyAsync(ctx->d.spins8, in, need, cudaMemcpyHostToDevice, ctx->stream);
+    if (e == cudaSuccess) e = launch_pack(ctx->g, ctx->d.spins8, ctx->d.v, ctx->n_words, ctx->stream);
+    ++ctx->launches;
+    // the caller may free `in` on return
+    if (e == cudaSuccess) e = cudaStreamSynchronize(ctx->stream);
+    return e == cudaSuccess ? CRBM_OK : cuda_fail(ctx, e, "crbm_set_spins");
+}
+
+int crbm_get_tables(crbm_ctx* ctx, uint32_t* out, size_t n_out, int32_t* dims) {
+    if (!ctx) return CRBM_EINVAL;
+    if (dims) {
+        dims[0] = ctx->g.DJ;
+        dims[1] = ctx->g.DJp;
+    }
+    if (!out) return CRBM_OK;
+    if (n_out < ctx->tables.size()) return fail(ctx, CRBM_EINVAL, "output buffer too small");
+    std::memcpy(out, ctx->tables.data(), ctx->tables.size() * 4);
+    return CRBM_OK;
+}
+
+// Checkpoint layout: header of 16 int64, then packed spins [n_words][N] u32,
+// sums [n_words*32][11] i64, series [series_len][n_words*32][3] i32,
+// correlations [n_params][N] i64 (when sq_every > 0).
+int crbm_save(crbm_ctx* ctx, void* buf, size_t* n) {
+    if (!ctx || !n) return CRBM_EINVAL;
+    const size_t npad = static_cast<size_t>(ctx->n_words) * 32, N = ctx->g.N;
+    const size_t b_v = ctx->n_words * N * 4, b_s = npad * kNSum * 8,
+                 b_t = static_cast<size_t>(ctx->series_len) * npad * 12,
+                 b_c = ctx->sq_every ? static_cast<size_t>(ctx->n_params) * N * 8 : 0;
+    const size_t total = 16 * 8 + b_v + b_s + b_t + b_c;
+    if (!buf) {
+        *n = total;
+        return CRBM_OK;
+    }
+    if (*n < total) return fail(ctx, CRBM_EINVAL, "checkpoint buffer too small");
+    int64_t hdr[16] = {0x4d425243 /* "CRBM" */, 1, ctx->g.L, ctx->n_chains, ctx->n_params,
+                       static_cast<int64_t>(ctx->seed), ctx->sweeps, ctx->meas, ctx->sq_meas,
+                       ctx->series_len, ctx->sq_every, ctx->measure_every, ctx->g.nb,
+                       ctx->g.periodic, 0, 0};
+    char* p = static_cast<char*>(buf);
+    std::memcpy(p, hdr, sizeof(hdr));
+    cudaError_t e = cudaMemcpyAsync(p + 128, ctx->d.v, b_v, cudaMemcpyDeviceToHost, ctx->stream);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(p + 128 + b_v, ctx->d.sums, b_s, cudaMemcpyDeviceToHost, ctx->stream);
+    if (e == cudaSuccess && b_t)
+        e = cudaMemcpyAsync(p + 128 + b_v + b_s, ctx->d.series, b_t, cudaMemcpyDeviceToHost, ctx->stream);
+    if (e == cudaSuccess && b_c)
+        e = cudaMemcpyAsync(p + 128 + b_v + b_s + b_t, ctx->d.corr, b_c, cudaMemcpyDeviceToHost, ctx->stream);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(ctx->stream);
+    if (e != cudaSuccess) return cuda_fail(ctx, e, "crbm_save");
+    *n = total;
+    return CRBM_OK;
+}
+
+int crbm_load(crbm_ctx* ctx, const void* buf, size_t n) {
+    if (!ctx || !buf) return CRBM_EINVAL;
+    size_t need = 0;
+    crbm_save(ctx, nullptr, &need);
+    if (n < need) return fail(ctx, CRBM_EINVAL, "checkpoint too small for this context");
+    int64_t hdr[16];
+    std::memcpy(hdr, buf, sizeof(hdr));
+    if (hdr[0] != 0x4d425243 || hdr[1] != 1 || hdr[2] != ctx->g.L || hdr[3] != ctx->n_chains ||
+        hdr[4] != ctx->n_params || hdr[5] != static_cast<int64_t>(ctx->seed) ||
+        hdr[9] != ctx->series_len || hdr[10] != ctx->sq_every || hdr[11] != ctx->measure_every ||
+        hdr[12] != ctx->g.nb || hdr[13] != ctx->g.periodic)
+        return fail(ctx, CRBM_EINVAL, "checkpoint does not match this context");
+    const size_t npad = static_cast<size_t>(ctx->n_words) * 32, N = ctx->g.N;
+    const size_t b_v = ctx->n_words * N * 4, b_s = npad * kNSum * 8,
+                 b_t = static_cast<size_t>(ctx->series_len) * npad * 12,
+                 b_c = ctx->sq_every ? static_cast<size_t>(ctx->n_params) * N * 8 : 0;
+    const char* p = static_cast<const char*>(buf);
+    cudaError_t e = cudaMemcpyAsync(ctx->d.v, p + 128, b_v, cudaMemcpyHostToDevice, ctx->stream);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(ctx->d.sums, p + 128 + b_v, b_s, cudaMemcpyHostToDevice, ctx->stream);
+    if (e == cudaSuccess && b_t)
+        e = cudaMemcpyAsync(ctx->d.series, p + 128 + b_v + b_s, b_t, cudaMemcpyHostToDevice, ctx->stream);
+    if (e == cudaSuccess && b_c)
+        e = cudaMemcpyAsync(ctx->d.corr, p + 128 + b_v + b_s + b_t, b_c, cudaMemcpyHostToDevice, ctx->stream);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(ctx->stream);
+    if (e != cudaSuccess) return cuda_fail(ctx, e, "crbm_load");
+    ctx->sweeps = hdr[6];
+    ctx->meas = hdr[7];
+    ctx->sq_meas = hdr[8];
+    return CRBM_OK;
+}
+
+int crbm_philox(const uint32_t* in, uint32_t* out, size_t n) {
+    if (!in || !out || n > (1u << 26)) return fail(nullptr, CRBM_EINVAL, "crbm_philox: bad arguments");
+    if (n == 0) return CRBM_OK;
+    uint32_t *din = nullptr, *dout = nullptr;
+    if (cudaMalloc(reinterpret_cast<void**>(&din), n * 24) != cudaSuccess)
+        return fail(nullptr, CRBM_ENOMEM, "crbm_philox: cudaMalloc");
+    if (cudaMalloc(reinterpret_cast<void**>(&dout), n * 16) != cudaSuccess) {
+        cudaFree(din);
+        return fail(nullptr, CRBM_ENOMEM, "crbm_philox: cudaMalloc");
+    }
+    cudaError_t e = cudaMemcpy(din, in, n * 24, cudaMemcpyHostToDevice);
+    if (e == cudaSuccess) e = launch_philox(din, dout, static_cast<int>(n), nullptr);
+    if (e == cudaSuccess) e = cudaMemcpy(out, dout, n * 16, cudaMemcpyDeviceToHost);
+    cudaFree(din);
+    cudaFree(dout);
+    return e == cudaSuccess ? CRBM_OK : cuda_fail(nullptr, e, "crbm_philox");
+}
+
+const char* crbm_last_error(const crbm_ctx* ctx) {
+    return ctx ? ctx->err.c_str() : g_create_error.c_str();
+}
+
+}  // extern "C"

@@ -1,0 +1,87 @@
+// Internal definitions shared by the host runtime (crbm_host.cpp) and the
+// CUDA kernels (crbm_kernels.cu).  Not part of the public ABI (include/crbm.h).
+#pragma once
+
+#include <cstdint>
+#include <cuda_runtime.h>
+
+namespace crbm {
+
+constexpr int kMaxBonds = 16;  // filters per 3x3 window -> at most 4 hidden Philox calls
+constexpr int kNSum = 11;      // per-chain observable sums
+constexpr int kWordBits = 32;  // chains per packed word (one bit per chain)
+constexpr uint32_t kTagVis = 4u;   // Philox tag of the visible half-step
+constexpr uint32_t kTagInit = 5u;  // Philox tag of the initial spins
+constexpr uint32_t kTagSwap = 6u;  // Philox tag of replica-exchange decisions
+
+// Lattice and filter geometry, passed by value to kernels (lives in the
+// kernel-parameter constant bank, read uniformly by every warp).
+struct Geometry {
+    int L;         // spins per side
+    int W;         // windows (cells) per side = (L + 1) / 2
+    int N;         // L * L
+    int n_cells;   // W * W
+    int nb;        // filters per window
+    int n_calls;   // hidden Philox calls per cell = ceil(nb / 4)
+    int periodic;  // 1 periodic, 0 open (zero padded)
+    int canonical; // 1: the ten SS filters on an even, periodic lattice
+    int DJ, DJp;   // visible field ranges n_J in [-DJ, DJ], n_J' in [-DJp, DJp]
+    int nTv;       // (2 DJ + 1) (2 DJp + 1)
+    int nTab;      // 10 hidden entries + nTv visible entries
+    int n_real_bonds[2];  // bonds with both endpoints real, per class
+    int8_t r1[kMaxBonds], c1[kMaxBonds], r2[kMaxBonds], c2[kMaxBonds];
+    uint8_t cls[kMaxBonds];
+};
+
+// Device buffers of one context (all owned by the context).
+struct DeviceState {
+    uint32_t* v = nullptr;        // [n_words][N] packed spins, bit l = chain 32w + l
+    uint32_t* tab = nullptr;      // [n_words][nTab][32] lane-expanded thresholds
+    uint32_t* sneg = nullptr;     // [n_words][2] lanes whose class coefficient s = -1
+    uint32_t* inc = nullptr;      // generic incidences, CSR entries (see kernels)
+    int32_t* inc_off = nullptr;   // [N + 1] CSR offsets
+    int64_t* sums = nullptr;      // [n_words * 32][kNSum]
+    int32_t* series = nullptr;    // [series_len][n_words * 32][3]
+    int64_t* corr = nullptr;      // [n_params][N] correlation sums
+    int32_t* seg = nullptr;       // [n_words][33]: n_seg, then (param << 8 | first lane) ...
+    uint32_t* segmask = nullptr;  // [n_words][32] lane mask of each segment
+    int8_t* spins8 = nullptr;     // [n_words * 32][N] staging for get/set spins
+    uint32_t* vtmp = nullptr;     // [n_words][N] second buffer for the streamed layout
+    int* err = nullptr;           // device error word
+};
+
+struct SweepArgs {
+    Geometry g;
+    uint32_t* v;
+    const uint32_t* tab;
+    const uint32_t* sneg;
+    const uint32_t* inc;
+    const int32_t* inc_off;
+    int64_t* sums;
+    int32_t* series;
+    int64_t* corr;
+    const int32_t* seg;
+    const uint32_t* segmask;
+    int n_words;
+    int n_chains_padded;
+    uint32_t key0, key1;
+    uint32_t t0;          // first global sweep index of this launch
+    int n_sweeps;
+    int measure_every;    // 0 = never
+    int64_t meas0;        // measurements recorded before this launch (series index)
+    int series_len;
+    int sq_every;         // 0 = never
+};
+
+// Kernel launchers (crbm_kernels.cu).  All return cudaGetLastError().
+size_t smem_bytes_smem_layout(const Geometry& g);
+cudaError_t launch_init(const Geometry& g, uint32_t* v, int n_words, uint32_t key0,
+                        uint32_t key1, cudaStream_t st);
+cudaError_t launch_sweep_smem(const SweepArgs& a, int warps_per_cta, cudaStream_t st);
+cudaError_t launch_philox(const uint32_t* in, uint32_t* out, int n, cudaStream_t st);
+cudaError_t launch_unpack(const Geometry& g, const uint32_t* v, int8_t* out, int n_words,
+                          cudaStream_t st);
+cudaError_t launch_pack(const Geometry& g, const int8_t* in, uint32_t* v, int n_words,
+                        cudaStream_t st);
+
+}  // namespace crbm

@@ -1,0 +1,51 @@
+"""Seeded synthetic workloads (parameter grids, chain assignments, spin
+configurations) shared by the tests and the benchmark.
+
+Holds no arithmetic of the sampling method: only the shapes and parameter
+values of the paper's workloads (arXiv 2511.20911: 18x18 periodic lattices,
+J1 = 1, J2/J1 in [0, 3], h in [-8, 8]; lattice sizes 6x6 ... 18x18).
+"""
+from __future__ import annotations
+
+import numpy as np
+
+
+def q4(x):
+    """Round to the nearest multiple of 1/16 (the Q.4 grid of the couplings)."""
+    return np.round(np.asarray(x, np.float64) * 16.0) / 16.0
+
+
+def small_workload():
+    """L=6 periodic, J=J'=1, h=0.5, beta=2, 64 chains, seed 1, 10^4 sweeps."""
+    return dict(L=6, params=dict(J=[1.0], Jp=[1.0], h=[0.5], beta=[2.0]), n_chains=64,
+                chain_param=np.zeros(64, np.int32), seed=1, n_sweeps=10_000)
+
+
+def grid_workload(chains_per_point=16, n_beta=16, n_h=16, ratios=(0.5, 1.0, 2.0)):
+    """L=18 periodic: J'/J in `ratios` x n_beta beta linear in [0.1, 5] x n_h h
+    linear in [0, 4] (on the 1/16 grid) x chains_per_point chains, J = 1.
+    Chains of one parameter point are contiguous."""
+    betas = np.linspace(0.1, 5.0, n_beta)
+    hs = q4(np.linspace(0.0, 4.0, n_h))
+    J, Jp, h, beta = [], [], [], []
+    for r in ratios:
+        for b in betas:
+            for x in hs:
+                J.append(1.0)
+                Jp.append(float(r))
+                h.append(float(x))
+                beta.append(float(b))
+    n_p = len(J)
+    cp = np.repeat(np.arange(n_p, dtype=np.int32), chains_per_point)
+    return dict(L=18, params=dict(J=J, Jp=Jp, h=h, beta=beta), n_chains=len(cp),
+                chain_param=cp, seed=2025)
+
+
+def random_params(rng, n):
+    """n random parameter points on the Q.4 grid (signs of J, J' both ways)."""
+    return dict(J=list(q4(rng.uniform(-2, 2, n))), Jp=list(q4(rng.uniform(-3, 3, n))),
+                h=list(q4(rng.uniform(-4, 4, n))), beta=list(rng.uniform(0.05, 3.0, n)))
+
+
+def random_spins(rng, n_chains, L):
+    return rng.choice(np.array([-1, 1], np.int8), size=(n_chains, L, L))

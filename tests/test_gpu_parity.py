@@ -1,0 +1,194 @@
+"""GPU path (through the C ABI) against the oracle, element by element.
+
+Plain Gibbs is deterministic given the Philox keying and the threshold tables,
+so the bar is bit-exact: identical spins after every call, identical integer
+observable sums and time series.  S(q) is FP64 post-processing of exact
+integer sums and must agree to 1e-12 relative.
+"""
+import numpy as np
+import pytest
+
+import paper_2511_20911_gb300 as crbm
+from paper_2511_20911_gb300 import workloads
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _gpu():
+    torch = pytest.importorskip("torch")
+    if not torch.cuda.is_available():
+        pytest.skip("no GPU")
+    crbm.load_library()
+
+
+def run_pair(orc, L, params, n_chains, chain_param, seed, splits, measure_every=1,
+             periodic=True, bonds=None, series_len=0, sq_every=0, check_ids=None):
+    s = crbm.Sampler(L, params, n_chains, chain_param=chain_param, seed=seed, periodic=periodic,
+                     bonds=bonds, measure_every=measure_every, series_len=series_len,
+                     sq_every=sq_every)
+    ids = np.arange(n_chains, dtype=np.uint32) if check_ids is None else np.asarray(check_ids, np.uint32)
+    cp = np.asarray(chain_param, np.int32)[ids]
+    ospins = orc.init_spins(L, ids, seed)
+    assert np.array_equal(s.get_spins()[ids], ospins), "initial spins"
+    sums = None
+    t = 0
+    series_cap = series_len
+    oseries = None
+    osq = None
+    for n in splits:
+        s.sweep(n)
+        sums, ser, osq = orc.run(L, params, cp, ospins, seed, t, n, measure_every, chain_ids=ids,
+                                 periodic=periodic, bonds=bonds, sums=sums, series_cap=series_cap,
+                                 sq_every=sq_every, sq=osq)
+        if ser is not None:
+            oseries = ser if oseries is None else np.where(ser != 0, ser, oseries)
+        t += n
+        g = s.get_spins()[ids]
+        assert np.array_equal(g, ospins), f"spins differ after sweep {t}"
+    if measure_every:
+        assert np.array_equal(s.observables()[ids], sums), "observable sums"
+    if series_len:
+        gser = s.series()[:, ids, :]                 # [T][chain][3]
+        assert np.array_equal(gser.transpose(1, 0, 2), oseries), "time series"
+    return s, ospins, sums, osq
+
+
+def test_philox_device_matches_oracle(orc):
+    rng = np.random.default_rng(11)
+    x = rng.integers(0, 2**32, size=(5000, 6), dtype=np.uint64).astype(np.uint32)
+    x[:3] = [[0] * 6, [0xFFFFFFFF] * 6, [3, 1, 4, 1, 5, 9]]
+    out = crbm.crbm_philox(x)
+    for i in range(0, 5000, 7):
+        assert list(out[i]) == orc.philox(x[i, :4], x[i, 4:]), i
+
+
+@pytest.mark.parametrize("L,periodic", [(6, True), (18, True), (3, True), (3, False), (9, True),
+                                        (10, False)])
+def test_tables_match_oracle(orc, L, periodic):
+    rng = np.random.default_rng(L)
+    params = workloads.random_params(rng, 7)
+    params["beta"][0] = 0.0
+    params["beta"][1] = 10.0
+    s = crbm.Sampler(L, params, 40, chain_param=np.arange(40) % 7, periodic=periodic)
+    tabs, (dj, djp) = s.tables()
+    assert (dj, djp) == orc.degrees(L, periodic)
+    for p in range(7):
+        th, tv = orc.tables(L, params["J"][p], params["Jp"][p], params["h"][p],
+                            params["beta"][p], periodic=periodic)
+        assert np.array_equal(tabs[p, :10], th.reshape(-1))
+        assert np.array_equal(tabs[p, 10:], tv.reshape(-1))
+
+
+def test_small_workload_bitexact(orc):
+    w = workloads.small_workload()
+    run_pair(orc, w["L"], w["params"], w["n_chains"], w["chain_param"], w["seed"],
+             splits=[1, 99, 200], measure_every=1, series_len=300)
+
+
+def test_grid_L18_ragged_bitexact(orc):
+    w = workloads.grid_workload(chains_per_point=1, n_beta=4, n_h=5)   # 60 chains: ragged word
+    run_pair(orc, 18, w["params"], w["n_chains"], w["chain_param"], 77, splits=[7, 33],
+             measure_every=5, series_len=8)
+
+
+@pytest.mark.parametrize("L,periodic", [(3, True), (3, False), (5, False), (7, True), (9, True),
+                                        (10, False), (4, False), (12, True)])
+def test_generic_lattices_bitexact(orc, L, periodic):
+    rng = np.random.default_rng(100 + L)
+    params = workloads.random_params(rng, 3)
+    n = 45
+    run_pair(orc, L, params, n, rng.integers(0, 3, n), 5 + L, splits=[3, 17], measure_every=2,
+             periodic=periodic, series_len=10)
+
+
+@pytest.mark.parametrize("bonds", [
+    [(0, 0, 0, 1, 0), (1, 0, 1, 1, 0), (0, 0, 1, 0, 0), (0, 1, 1, 1, 0)],          # square lattice
+    [(0, 0, 0, 1, 0), (0, 1, 0, 2, 0), (1, 0, 1, 1, 0), (1, 1, 1, 2, 0), (0, 0, 1, 0, 0),
+     (1, 0, 2, 0, 0), (0, 1, 1, 1, 0), (1, 1, 2, 1, 0), (0, 0, 1, 1, 1), (1, 2, 2, 1, 1),
+     (0, 1, 1, 0, 1), (0, 0, 2, 2, 0), (2, 0, 0, 2, 1)],                               # 13 filters
+    [(0, 0, 1, 1, 1)],                                                               # one filter
+])
+def test_custom_filters_bitexact(orc, bonds):
+    rng = np.random.default_rng(len(bonds))
+    params = workloads.random_params(rng, 2)
+    for L, periodic in ((6, True), (7, False)):
+        run_pair(orc, L, params, 33, rng.integers(0, 2, 33), 9, splits=[11], measure_every=3,
+                 periodic=periodic, bonds=bonds)
+
+
+def test_structure_factor_matches_oracle(orc):
+    L, n = 8, 70
+    rng = np.random.default_rng(8)
+    params = workloads.random_params(rng, 3)
+    cp = np.sort(rng.integers(0, 3, n)).astype(np.int32)
+    s, _, _, osq = run_pair(orc, L, params, n, cp, 4, splits=[9, 12], measure_every=0,
+                            sq_every=3)
+    sq = s.structure_factor()
+    corr, ns = s.correlations()
+    for p in range(3):
+        ref = osq[cp == p].sum(0) / ns[p]
+        assert ns[p] == (cp == p).sum() * 7
+        assert np.allclose(sq[p], ref, rtol=1e-12, atol=1e-12 * np.abs(ref).max())
+        assert corr[p, 0, 0] == ns[p] * L * L                     # C(0) = N per sample
+
+
+def test_set_spins_then_sweep(orc):
+    L, n, seed = 6, 50, 21
+    rng = np.random.default_rng(2)
+    params = workloads.random_params(rng, 2)
+    cp = rng.integers(0, 2, n).astype(np.int32)
+    s = crbm.Sampler(L, params, n, chain_param=cp, seed=seed)
+    v0 = workloads.random_spins(rng, n, L)
+    s.set_spins(v0)
+    assert np.array_equal(s.get_spins(), v0)
+    s.sweep(25)
+    ref = v0.copy()
+    orc.run(L, params, cp, ref, seed, 0, 25, 0)
+    assert np.array_equal(s.get_spins(), ref)
+
+
+def test_checkpoint_resume_bitexact():
+    w = workloads.small_workload()
+    a = crbm.Sampler(6, w["params"], 64, chain_param=w["chain_param"], seed=1, series_len=40)
+    a.sweep(20)
+    ck = a.save()
+    a.sweep(20)
+    b = crbm.Sampler(6, w["params"], 64, chain_param=w["chain_param"], seed=1, series_len=40)
+    b.load(ck)
+    assert b.sweep_count == 20
+    b.sweep(20)
+    assert np.array_equal(a.get_spins(), b.get_spins())
+    assert np.array_equal(a.observables(), b.observables())
+    assert np.array_equal(a.series(), b.series())
+
+
+def test_host_side_errors():
+    ok = dict(J=[1.0], Jp=[1.0], h=[0.5], beta=[2.0])
+    bad = [dict(L=2, params=ok, n_chains=4), dict(L=6, params=dict(ok, beta=[-1.0]), n_chains=4),
+           dict(L=6, params=dict(ok, J=[500.0]), n_chains=4),
+           dict(L=6, params=dict(ok, h=[float("nan")]), n_chains=4),
+           dict(L=6, params=ok, n_chains=0),
+           dict(L=6, params=ok, n_chains=4, chain_param=[0, 0, 1, 0]),
+           dict(L=6, params=ok, n_chains=4, bonds=[(0, 0, 0, 0, 0)]),
+           dict(L=6, params=ok, n_chains=4, bonds=[(0, 0, 3, 0, 0)]),
+           dict(L=7, params=ok, n_chains=4, periodic=False, sq_every=1)]
+    for kw in bad:
+        with pytest.raises(crbm.CrbmError) as e:
+            crbm.Sampler(**kw)
+        assert e.value.code == crbm.CRBM_EINVAL, kw
+    s = crbm.Sampler(6, ok, 4)
+    with pytest.raises(crbm.CrbmError):
+        s.sweep(-1)
+    with pytest.raises(crbm.CrbmError):
+        s.set_spins(np.zeros((4, 6, 6), np.int8))
+
+
+@pytest.mark.slow
+def test_full_grid_workload_sampled_chains(orc):
+    """The L=18 grid at full size (12288 chains, the benchmark's launch), with
+    64 chains spread over every word checked one by one against the oracle."""
+    w = workloads.grid_workload()
+    ids = np.linspace(0, w["n_chains"] - 1, 64).astype(np.uint32)
+    run_pair(orc, 18, w["params"], w["n_chains"], w["chain_param"], w["seed"], splits=[10, 20],
+             measure_every=10, check_ids=ids)

@@ -30,13 +30,15 @@ sys.path.insert(0, ROOT)
 
 METRIC = "spin-updates/s and ESS/s (energy, m) per GB300 vs plain Gibbs; roofline %"
 UNIT = "spin-updates/s"
-SM_COUNT, SMSP_PER_SM, LANES, SM_MAX_MHZ = 152, 4, 32, 2070.0
-# Algorithmic integer operations per (chain, cell, sweep) of the canonical SS
-# path: 4 Philox-4x32-10 calls x 10 rounds x (2 wide multiplies + 2 three-input
-# XORs) = 160; 10 hidden decisions x 4 (field index, threshold select, compare,
-# pack) = 40; 4 visible decisions x 8 (4 field adds, index, table load,
-# compare, pack) = 32.  Each cell holds 4 spins.
-OPS_PER_CELL = 160 + 40 + 32
+SM_COUNT, SM_MAX_MHZ = 152, 2070.0
+# The path is bound by 32-bit integer multiplies: every node decision needs a
+# Philox-4x32-10 word, and one Philox call (4 words) is 10 rounds x two
+# 32x32->64 products = 40 multiply lane-operations (low and high halves).  The
+# GB300 SM retires 64 integer-multiply lanes per clock, so the ceiling is
+# 152 SM x 64 x 2070 MHz = 20.1 T multiply-ops/s = 5.03e11 Philox calls/s.
+IMUL_LANES_PER_SM_CLK = 64
+MUL_OPS_PER_CALL = 40
+CALLS_PER_CELL = 4          # 3 hidden calls (10 filters) + 1 visible call (4 spins) per cell
 
 
 def parse():
@@ -136,6 +138,7 @@ def cpu_baseline(w, seconds):
     dt = run(n_ch, n_sw)
     value = n_ch * n_sw * L * L / dt
     return {"value": value, "unit": UNIT, "cores": oracle.get_threads(), "kind": "oracle",
+            "seconds": dt,
             "sample": f"{n_ch} of the {n_all} chains (spread over all parameter points), "
                       f"{n_sw} sweeps, measure every 10, {dt:.1f} s wall"}
 
@@ -156,7 +159,7 @@ def run_reference(args, rank, ws):
     print(json.dumps({
         "impl": "reference", "metric": METRIC, "value": v, "unit": UNIT, "n_gpus": args.gpus,
         "steps": args.steps, "warmup": args.warmup,
-        "ms_per_step": float(np.mean([1e3 * n_ch * 324 * 0 + 0 for _ in vals])) or None,
+        "ms_per_step": float(np.mean([x["seconds"] for x in vals])) * 1e3,
         "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "int8",
         "data": "synthetic", "config": config_dict(w, args), "cpu_baseline": cb,
         "e2e": {"value": v, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}))
@@ -241,9 +244,9 @@ def main():
     e2e_steps = max(1, K // 2)
     e2e_val = w["n_chains"] * w["L"] ** 2 * S * e2e_steps * ws / e2e_t
 
-    ops = OPS_PER_CELL * (w["L"] // 2) ** 2 * w["n_chains"] * S
-    achieved = ops / (t_total / K) / 1e12
-    peak = SM_COUNT * SMSP_PER_SM * LANES * SM_MAX_MHZ * 1e6 / 1e12
+    calls = CALLS_PER_CELL * (w["L"] // 2) ** 2 * w["n_chains"] * S     # per step (= one launch)
+    achieved = MUL_OPS_PER_CALL * calls / (t_total / K) / 1e12
+    peak = SM_COUNT * IMUL_LANES_PER_SM_CLK * SM_MAX_MHZ * 1e6 / 1e12
     out = {
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws, "steps": K, "warmup": W,
         "ms_per_step": t_total / K * 1e3, "higher_is_better": True, "scaling": "weak",
@@ -258,8 +261,9 @@ def main():
         "gpu_launches": int(launches),
         "roofline": {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "Tops/s",
                      "frac": achieved / peak, "traffic": None,
-                     "note": "integer-issue peak 152 SM x 4 SMSP x 32 lanes x 2070 MHz; ops = "
-                             f"{OPS_PER_CELL} algorithmic integer ops per chain-cell-sweep"},
+                     "note": "integer-multiply ceiling: 152 SM x 64 lanes/clk x 2070 MHz; 40 "
+                             "multiply ops per Philox-4x32-10 call, 4 calls per chain-cell-sweep",
+                     "philox_calls_per_s": calls / (t_total / K)},
     }
     if rank == 0 and not args.no_cpu_baseline:
         out["cpu_baseline"] = cpu_baseline(w, args.cpu_seconds)

@@ -1,0 +1,170 @@
+// Device helpers shared by the sweep kernels: the Philox generator, bit
+// access on packed words, and the per-sweep measurement / correlation steps.
+#pragma once
+
+#include "crbm_internal.h"
+
+namespace crbm {
+namespace dev {
+
+struct U4 {
+    uint32_t x, y, z, w;
+};
+
+constexpr uint32_t kPhiloxM0 = 0xD2511F53u;
+constexpr uint32_t kPhiloxM1 = 0xCD9E8D57u;
+constexpr uint32_t kPhiloxW0 = 0x9E3779B9u;
+constexpr uint32_t kPhiloxW1 = 0xBB67AE85u;
+
+// Philox-4x32-10 (Salmon, Moraes, Dror, Shaw, SC'11): ten rounds of two
+// 32x32->64 multiplies by the round multipliers, the high halves XORed with
+// the other two counter words and the round key; the key advances by the two
+// Weyl increments between rounds.
+__device__ __forceinline__ U4 philox(uint32_t c0, uint32_t c1, uint32_t c2, uint32_t c3,
+                                     uint32_t k0, uint32_t k1) {
+#pragma unroll
+    for (int r = 0; r < 10; ++r) {
+        const uint64_t p0 = static_cast<uint64_t>(kPhiloxM0) * c0;
+        const uint64_t p1 = static_cast<uint64_t>(kPhiloxM1) * c2;
+        const uint32_t n0 = static_cast<uint32_t>(p1 >> 32) ^ c1 ^ k0;
+        const uint32_t n2 = static_cast<uint32_t>(p0 >> 32) ^ c3 ^ k1;
+        c1 = static_cast<uint32_t>(p1);
+        c3 = static_cast<uint32_t>(p0);
+        c0 = n0;
+        c2 = n2;
+        k0 += kPhiloxW0;
+        k1 += kPhiloxW1;
+    }
+    return {c0, c1, c2, c3};
+}
+
+// Rounds 1..9 from the state after round 0, with precomputed round keys
+// rk[2r] = k0 + r W0, rk[2r+1] = k1 + r W1 (kernel parameters, so each key is
+// a constant-bank operand of its XOR).
+__device__ __forceinline__ U4 philox_rounds1to9(uint32_t c0, uint32_t c1, uint32_t c2, uint32_t c3,
+                                                const uint32_t (&rk)[20]) {
+#pragma unroll
+    for (int r = 1; r < 10; ++r) {
+        const uint64_t p0 = static_cast<uint64_t>(kPhiloxM0) * c0;
+        const uint64_t p1 = static_cast<uint64_t>(kPhiloxM1) * c2;
+        const uint32_t n0 = static_cast<uint32_t>(p1 >> 32) ^ c1 ^ rk[2 * r];
+        const uint32_t n2 = static_cast<uint32_t>(p0 >> 32) ^ c3 ^ rk[2 * r + 1];
+        c1 = static_cast<uint32_t>(p1);
+        c3 = static_cast<uint32_t>(p0);
+        c0 = n0;
+        c2 = n2;
+    }
+    return {c0, c1, c2, c3};
+}
+
+// Round 0 of counter (cell, sweep, chain, tag) needs no per-call multiply:
+// M1 * chain is a per-lane constant, M0 * cell is warp-uniform.  The state
+// after round 0 is (hi(M1 chain) ^ sweep ^ rk0, lo(M1 chain),
+// hi(M0 cell) ^ tag ^ rk1, lo(M0 cell)).
+struct Round0Lane {
+    uint32_t hi, lo;
+};
+struct Round0Cell {
+    uint32_t a, b;  // hi(M0 cell) ^ rk1, lo(M0 cell)
+};
+__device__ __forceinline__ Round0Lane round0_lane(uint32_t chain) {
+    const uint64_t p = static_cast<uint64_t>(kPhiloxM1) * chain;
+    return {static_cast<uint32_t>(p >> 32), static_cast<uint32_t>(p)};
+}
+__device__ __forceinline__ Round0Cell round0_cell(uint32_t cell, uint32_t rk1) {
+    const uint64_t p = static_cast<uint64_t>(kPhiloxM0) * cell;
+    return {static_cast<uint32_t>(p >> 32) ^ rk1, static_cast<uint32_t>(p)};
+}
+
+__device__ __forceinline__ uint32_t pick(const U4& q, int w) {
+    return w == 0 ? q.x : (w == 1 ? q.y : (w == 2 ? q.z : q.w));
+}
+
+__device__ __forceinline__ uint32_t bit_of(uint32_t word, int lane) { return (word >> lane) & 1u; }
+
+__device__ __forceinline__ uint32_t rotr(uint32_t x, uint32_t s) { return __funnelshift_r(x, x, s); }
+
+__device__ __forceinline__ int warp_sum(int x) {
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) x += __shfl_xor_sync(0xffffffffu, x, o);
+    return x;
+}
+
+// Site index of window offset (r, c) of cell (i, j), or -1 for a zero-padded
+// (open boundary) site.  r, c <= 2 and 2i, 2j <= L - 1, so one wrap suffices.
+__device__ __forceinline__ int site_of(const Geometry& g, int i, int j, int r, int c) {
+    int R = 2 * i + r, C = 2 * j + c;
+    if (R >= g.L) {
+        if (!g.periodic) return -1;
+        R -= g.L;
+    }
+    if (C >= g.L) {
+        if (!g.periodic) return -1;
+        C -= g.L;
+    }
+    return R * g.L + C;
+}
+
+// Measurement step shared by the sweep kernels.  s_cnt[0..95] holds, per
+// lane, the number of anti-aligned real bonds of each class and of +1 spins,
+// summed by every warp of the CTA.  Warp 0 turns them into (NJ, NJ', M),
+// appends the series entry and accumulates the eleven sums in registers.
+__device__ __forceinline__ void measure_finalize(const SweepArgs& a, int* s_cnt, int lane,
+                                                 uint32_t chain, int64_t meas, int64_t (&acc)[kNSum]) {
+    const Geometry& g = a.g;
+    const int64_t nJ = g.n_real_bonds[0] - 2 * s_cnt[lane];
+    const int64_t nP = g.n_real_bonds[1] - 2 * s_cnt[32 + lane];
+    const int64_t M = 2 * s_cnt[64 + lane] - g.N;
+    s_cnt[lane] = 0;
+    s_cnt[32 + lane] = 0;
+    s_cnt[64 + lane] = 0;
+    if (meas < a.series_len) {
+        int32_t* e = a.series + (static_cast<size_t>(meas) * a.n_chains_padded + chain) * 3;
+        e[0] = static_cast<int32_t>(nJ);
+        e[1] = static_cast<int32_t>(nP);
+        e[2] = static_cast<int32_t>(M);
+    }
+    acc[0] += 1;
+    acc[1] += nJ;
+    acc[2] += nP;
+    acc[3] += M;
+    acc[4] += M < 0 ? -M : M;
+    acc[5] += nJ * nJ;
+    acc[6] += nP * nP;
+    acc[7] += M * M;
+    acc[8] += nJ * nP;
+    acc[9] += nJ * M;
+    acc[10] += nP * M;
+}
+
+// Spin correlations of Sec. IV.B for the chains of each parameter-point
+// segment of this word:  C_p(d) += n_p N - 2 sum_r popc((v_r ^ v_{r+d}) & mask_p).
+__device__ __forceinline__ void accumulate_correlations(const SweepArgs& a, const uint32_t* s_v,
+                                                        const int* s_seg, const uint32_t* s_segmask,
+                                                        int warp, int nwarp, int lane) {
+    const int L = a.g.L, N = a.g.N, nseg = s_seg[0];
+    for (int d = warp; d < N; d += nwarp) {
+        const int dR = d / L, dC = d - (d / L) * L;
+        for (int sgi = 0; sgi < nseg; ++sgi) {
+            const uint32_t mask = s_segmask[sgi];
+            int cnt = 0;
+            for (int r = lane; r < N; r += 32) {
+                const int R = r / L, C = r - (r / L) * L;
+                int R2 = R + dR, C2 = C + dC;
+                if (R2 >= L) R2 -= L;
+                if (C2 >= L) C2 -= L;
+                cnt += __popc((s_v[r] ^ s_v[R2 * L + C2]) & mask);
+            }
+            cnt = warp_sum(cnt);
+            if (lane == 0) {
+                const int p = s_seg[1 + sgi] >> 8;
+                const long long val = static_cast<long long>(__popc(mask)) * N - 2LL * cnt;
+                atomicAdd(reinterpret_cast<unsigned long long*>(a.corr + static_cast<size_t>(p) * N + d),
+                          static_cast<unsigned long long>(val));
+            }
+        }
+    }
+}
+
+}  // namespace dev
+}  // namespace crbm

@@ -191,7 +191,7 @@ int dalloc(crbm_ctx* ctx, T*& ptr, size_t count) {
 }
 
 void free_device(DeviceState& d) {
-    void* ptrs[] = {d.v, d.tab, d.sneg, d.inc, d.inc_off, d.sums, d.series, d.corr,
+    void* ptrs[] = {d.v, d.tab, d.ctab, d.sneg, d.inc, d.inc_off, d.sums, d.series, d.corr,
                     d.seg, d.segmask, d.spins8, d.vtmp, d.err};
     for (void* p : ptrs)
         if (p) cudaFree(p);
@@ -201,10 +201,10 @@ void free_device(DeviceState& d) {
 int default_warps(const Geometry& g) {
     if (const char* env = std::getenv("CRBM_WARPS")) {
         const int w = std::atoi(env);
-        if (w >= 1 && w <= 32) return w;
+        if (w >= 1 && w <= 16) return w;
     }
-    // about nine cells per warp, up to 16 warps per CTA
-    return std::max(1, std::min(16, (g.n_cells + 8) / 9));
+    // about six cells per warp, up to 16 warps per CTA
+    return std::max(1, std::min(16, (g.n_cells + 5) / 6));
 }
 
 }  // namespace
@@ -243,7 +243,8 @@ int crbm_create(crbm_ctx** out, const crbm_params* p) {
         delete ctx;
         return fail(nullptr, CRBM_EUNSUPPORTED, "streamed layout not available in this build");
     }
-    if (ctx->layout == CRBM_LAYOUT_SMEM && smem_bytes_smem_layout(g) > 227 * 1024) {
+    if (ctx->layout == CRBM_LAYOUT_SMEM &&
+        (g.canonical ? smem_bytes_canon(g) : smem_bytes_generic(g)) > 227 * 1024) {
         delete ctx;
         return fail(nullptr, CRBM_EUNSUPPORTED,
                     "lattice, hidden layer and threshold columns exceed 227 KB of shared memory");
@@ -319,11 +320,49 @@ int crbm_create(crbm_ctx** out, const crbm_params* p) {
         }
         seg[33 * w] = nseg;
     }
+    // Canonical fast-path tables (crbm_canon.cu): per word and lane, the
+    // hidden table indexed by the raw endpoint bits (e1 + 2 e2) and the
+    // visible tables indexed by the five raw filter bits of each spin
+    // position; the coefficient signs and the field sums are folded in.
+    std::vector<uint32_t> ctab;
+    if (g.canonical) {
+        // (class, second endpoint) of slots 0..4 for spins (0,0), (0,1), (1,0), (1,1)
+        static const int kSlot[4][5][2] = {{{0, 0}, {0, 0}, {1, 0}, {0, 1}, {0, 1}},
+                                           {{0, 1}, {0, 0}, {0, 0}, {0, 1}, {1, 1}},
+                                           {{0, 0}, {0, 1}, {0, 0}, {0, 1}, {1, 0}},
+                                           {{0, 1}, {0, 1}, {1, 1}, {0, 0}, {0, 0}}};
+        ctab.assign(static_cast<size_t>(nw) * kCanonTab, 0u);
+        for (int w = 0; w < nw; ++w)
+            for (int l = 0; l < 32; ++l) {
+                const int c = w * 32 + l;
+                const int pp = c < p->n_chains ? ctx->chain_param[c] : ctx->chain_param[0];
+                const uint32_t* T = &ctx->tables[static_cast<size_t>(pp) * g.nTab];
+                uint32_t* out = &ctab[static_cast<size_t>(w) * kCanonTab];
+                for (int cls = 0; cls < 2; ++cls)
+                    for (int idx = 0; idx < 4; ++idx) {
+                        const int e1 = idx & 1, e2 = idx >> 1;
+                        const int m = (2 * e1 - 1) + sgn[2 * pp + cls] * (2 * e2 - 1);
+                        out[(cls * 4 + idx) * 32 + l] = T[cls * 5 + m + 2];
+                    }
+                for (int sc = 0; sc < 4; ++sc)
+                    for (int idx = 0; idx < 32; ++idx) {
+                        int n[2] = {0, 0};
+                        for (int slot = 0; slot < 5; ++slot) {
+                            const int cls = kSlot[sc][slot][0];
+                            const int coef = kSlot[sc][slot][1] ? sgn[2 * pp + cls] : 1;
+                            n[cls] += coef * (2 * ((idx >> slot) & 1) - 1);
+                        }
+                        out[kCanonTh + (sc * 32 + idx) * 32 + l] =
+                            T[10 + (n[0] + g.DJ) * (2 * g.DJp + 1) + (n[1] + g.DJp)];
+                    }
+            }
+    }
     // Device state.
     cudaGetDevice(&ctx->device);
     DeviceState& d = ctx->d;
     const size_t N = static_cast<size_t>(g.N);
     if ((rc = dalloc(ctx, d.v, nw * N)) || (rc = dalloc(ctx, d.tab, tab.size())) ||
+        (rc = dalloc(ctx, d.ctab, ctab.size())) ||
         (rc = dalloc(ctx, d.sneg, sneg.size())) || (rc = dalloc(ctx, d.inc, inc.size())) ||
         (rc = dalloc(ctx, d.inc_off, inc_off.size())) ||
         (rc = dalloc(ctx, d.sums, static_cast<size_t>(npad) * kNSum)) ||
@@ -342,6 +381,7 @@ int crbm_create(crbm_ctx** out, const crbm_params* p) {
         if (e == cudaSuccess && bytes) e = cudaMemcpyAsync(dst, src, bytes, cudaMemcpyHostToDevice, st);
     };
     h2d(d.tab, tab.data(), tab.size() * 4);
+    h2d(d.ctab, ctab.data(), ctab.size() * 4);
     h2d(d.sneg, sneg.data(), sneg.size() * 4);
     h2d(d.inc, inc.data(), inc.size() * 4);
     h2d(d.inc_off, inc_off.data(), inc_off.size() * 4);
@@ -394,6 +434,7 @@ int crbm_sweep(crbm_ctx* ctx, int64_t n_sweeps) {
         a.g = ctx->g;
         a.v = ctx->d.v;
         a.tab = ctx->d.tab;
+        a.ctab = ctx->d.ctab;
         a.sneg = ctx->d.sneg;
         a.inc = ctx->d.inc;
         a.inc_off = ctx->d.inc_off;
@@ -406,13 +447,18 @@ int crbm_sweep(crbm_ctx* ctx, int64_t n_sweeps) {
         a.n_chains_padded = ctx->n_words * 32;
         a.key0 = static_cast<uint32_t>(ctx->seed);
         a.key1 = static_cast<uint32_t>(ctx->seed >> 32);
+        for (int r = 0; r < 10; ++r) {  // Philox key schedule (Weyl increments)
+            a.rk[2 * r] = a.key0 + static_cast<uint32_t>(r) * 0x9E3779B9u;
+            a.rk[2 * r + 1] = a.key1 + static_cast<uint32_t>(r) * 0xBB67AE85u;
+        }
         a.t0 = static_cast<uint32_t>(ctx->sweeps);
         a.n_sweeps = chunk;
         a.measure_every = ctx->measure_every;
         a.meas0 = ctx->meas;
         a.series_len = ctx->series_len;
         a.sq_every = ctx->sq_every;
-        const cudaError_t e = launch_sweep_smem(a, ctx->warps, ctx->stream);
+        const cudaError_t e = ctx->g.canonical ? launch_sweep_canon(a, ctx->warps, ctx->stream)
+                                               : launch_sweep_generic(a, ctx->warps, ctx->stream);
         if (e != cudaSuccess) return cuda_fail(ctx, e, "sweep launch");
         ++ctx->launches;
         const int64_t t0 = ctx->sweeps, t1 = ctx->sweeps + chunk;

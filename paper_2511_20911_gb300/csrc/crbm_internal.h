@@ -14,6 +14,11 @@ constexpr uint32_t kTagVis = 4u;   // Philox tag of the visible half-step
 constexpr uint32_t kTagInit = 5u;  // Philox tag of the initial spins
 constexpr uint32_t kTagSwap = 6u;  // Philox tag of replica-exchange decisions
 
+// Canonical fast-path tables per packed word: hidden [2 cls][4 idx][32 lanes]
+// then visible [4 spin positions][32 idx][32 lanes] (see crbm_canon.cu).
+constexpr int kCanonTh = 2 * 4 * 32;
+constexpr int kCanonTab = kCanonTh + 4 * 32 * 32;
+
 // Lattice and filter geometry, passed by value to kernels (lives in the
 // kernel-parameter constant bank, read uniformly by every warp).
 struct Geometry {
@@ -37,6 +42,7 @@ struct Geometry {
 struct DeviceState {
     uint32_t* v = nullptr;        // [n_words][N] packed spins, bit l = chain 32w + l
     uint32_t* tab = nullptr;      // [n_words][nTab][32] lane-expanded thresholds
+    uint32_t* ctab = nullptr;     // [n_words][kCanonTab] canonical fast-path tables
     uint32_t* sneg = nullptr;     // [n_words][2] lanes whose class coefficient s = -1
     uint32_t* inc = nullptr;      // generic incidences, CSR entries (see kernels)
     int32_t* inc_off = nullptr;   // [N + 1] CSR offsets
@@ -54,6 +60,7 @@ struct SweepArgs {
     Geometry g;
     uint32_t* v;
     const uint32_t* tab;
+    const uint32_t* ctab;
     const uint32_t* sneg;
     const uint32_t* inc;
     const int32_t* inc_off;
@@ -65,6 +72,7 @@ struct SweepArgs {
     int n_words;
     int n_chains_padded;
     uint32_t key0, key1;
+    uint32_t rk[20];      // Philox round keys: rk[2r] = key0 + r W0, rk[2r+1] = key1 + r W1
     uint32_t t0;          // first global sweep index of this launch
     int n_sweeps;
     int measure_every;    // 0 = never
@@ -74,10 +82,12 @@ struct SweepArgs {
 };
 
 // Kernel launchers (crbm_kernels.cu).  All return cudaGetLastError().
-size_t smem_bytes_smem_layout(const Geometry& g);
+size_t smem_bytes_generic(const Geometry& g);
+size_t smem_bytes_canon(const Geometry& g);
 cudaError_t launch_init(const Geometry& g, uint32_t* v, int n_words, uint32_t key0,
                         uint32_t key1, cudaStream_t st);
-cudaError_t launch_sweep_smem(const SweepArgs& a, int warps_per_cta, cudaStream_t st);
+cudaError_t launch_sweep_generic(const SweepArgs& a, int warps_per_cta, cudaStream_t st);
+cudaError_t launch_sweep_canon(const SweepArgs& a, int warps_per_cta, cudaStream_t st);
 cudaError_t launch_philox(const uint32_t* in, uint32_t* out, int n, cudaStream_t st);
 cudaError_t launch_unpack(const Geometry& g, const uint32_t* v, int8_t* out, int n_words,
                           cudaStream_t st);

@@ -47,7 +47,8 @@ def parse():
     ap.add_argument("--steps", type=int, default=10)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
-    ap.add_argument("--sweeps-per-step", type=int, default=2000)
+    ap.add_argument("--workload", default="grid", choices=["grid", "stream"])
+    ap.add_argument("--sweeps-per-step", type=int, default=None)
     ap.add_argument("--measure-every", type=int, default=10)
     ap.add_argument("--cpu-seconds", type=float, default=8.0)
     ap.add_argument("--no-cpu-baseline", action="store_true")
@@ -107,11 +108,14 @@ class ClockSampler:
                 "sm_max_mhz": max(mx) if mx else None, "reasons": reasons, "samples": len(sm)}
 
 
-def grid_config(rank):
+def workload_config(name, rank):
     from paper_2511_20911_gb300 import workloads
-    w = workloads.grid_workload()
+    w = workloads.grid_workload() if name == "grid" else workloads.stream_workload()
     w["seed"] = w["seed"] + 1000003 * rank
     return w
+
+
+DEFAULT_SWEEPS = {"grid": 2000, "stream": 20}
 
 
 def cpu_baseline(w, seconds):
@@ -132,9 +136,11 @@ def cpu_baseline(w, seconds):
         oracle.run(L, w["params"], cp, sp, w["seed"], 0, n_sw, 10, chain_ids=ids)
         return time.perf_counter() - t
 
-    n_ch = 16 * cores
-    dt = run(n_ch, 20)
-    n_sw = max(20, int(20 * seconds / max(dt, 1e-3)))
+    small = L <= 64
+    n_ch = 16 * cores if small else cores
+    sw0 = 20 if small else 1
+    dt = run(n_ch, sw0)
+    n_sw = max(sw0, int(sw0 * seconds / max(dt, 1e-3)))
     dt = run(n_ch, n_sw)
     value = n_ch * n_sw * L * L / dt
     return {"value": value, "unit": UNIT, "cores": oracle.get_threads(), "kind": "oracle",
@@ -147,7 +153,7 @@ def run_reference(args, rank, ws):
     """Reference arm: the CPU oracle timed on the host cores."""
     if rank != 0:
         return
-    w = grid_config(0)
+    w = workload_config(args.workload, 0)
     per_step = max(1.0, 60.0 / max(1, args.steps + args.warmup))
     for _ in range(args.warmup):
         cpu_baseline(w, min(per_step, 2.0))
@@ -166,16 +172,24 @@ def run_reference(args, rank, ws):
 
 
 def config_dict(w, args):
-    return {"workload": "L=18 periodic SS grid: J'/J in {0.5,1,2} x 16 beta in [0.1,5] x 16 h in "
-                        "[0,4] x 16 chains", "L": w["L"], "n_chains": w["n_chains"],
+    if args.workload == "grid":
+        desc = ("L=18 periodic SS grid: J'/J in {0.5,1,2} x 16 beta in [0.1,5] x 16 h in [0,4] "
+                "x 16 chains, SMEM-resident")
+    else:
+        desc = ("L=384 periodic SS lattice: J=J'=1, beta=1, h in {0,1,2} x 1024 chains, 64-chain "
+                "words, spins and hidden units in HBM (two launches per sweep)")
+    return {"workload": desc, "L": w["L"], "n_chains": w["n_chains"],
             "n_params": len(w["params"]["J"]), "sweeps_per_step": args.sweeps_per_step,
-            "measure_every": args.measure_every, "layout": "smem",
+            "measure_every": args.measure_every,
+            "layout": "smem" if args.workload == "grid" else "stream",
             "l2": "flushed between steps (256 MiB write outside the step events)",
             "parallelism": f"replicas x{args.gpus}"}
 
 
 def main():
     args = parse()
+    if args.sweeps_per_step is None:
+        args.sweeps_per_step = DEFAULT_SWEEPS[args.workload]
     rank, ws = dist_setup(args)
     if args.impl == "reference":
         run_reference(args, rank, ws)
@@ -185,11 +199,12 @@ def main():
     from paper_2511_20911_gb300 import analysis
 
     dev = torch.cuda.current_device()
-    w = grid_config(rank)
+    w = workload_config(args.workload, rank)
     S, K, W = args.sweeps_per_step, args.steps, args.warmup
     n_meas = S * K // args.measure_every
+    layout = crbm.CRBM_LAYOUT_SMEM if args.workload == "grid" else crbm.CRBM_LAYOUT_STREAM
     s = crbm.Sampler(w["L"], w["params"], w["n_chains"], chain_param=w["chain_param"], seed=w["seed"],
-                     measure_every=args.measure_every, series_len=n_meas)
+                     measure_every=args.measure_every, series_len=n_meas, layout=layout)
     stream = torch.cuda.current_stream()
     flush = torch.empty(256 * 1024 * 1024, dtype=torch.uint8, device="cuda")
     for _ in range(W):
@@ -227,8 +242,11 @@ def main():
     Jc, Jpc, hc = (np.asarray(p[k])[cp] for k in ("J", "Jp", "h"))
     E = analysis.energy_series(ser.transpose(1, 0, 2), Jc[:, None], Jpc[:, None], hc[:, None])
     Mx = ser[:, :, 2].T.astype(np.float64)
-    ess_E = float(analysis.effective_samples(E).sum())
-    ess_m = float(analysis.effective_samples(Mx).sum())
+    if ser.shape[0] >= 20:
+        ess_E = float(analysis.effective_samples(E).sum())
+        ess_m = float(analysis.effective_samples(Mx).sum())
+    else:                      # too few measurements in the timed steps for a windowed estimate
+        ess_E = ess_m = float("nan")
 
     # end to end through the C ABI with host buffers: set spins (H2D), sweep,
     # read observables (D2H), every step
@@ -244,14 +262,19 @@ def main():
     e2e_steps = max(1, K // 2)
     e2e_val = w["n_chains"] * w["L"] ** 2 * S * e2e_steps * ws / e2e_t
 
-    calls = CALLS_PER_CELL * (w["L"] // 2) ** 2 * w["n_chains"] * S     # per step (= one launch)
+    calls = CALLS_PER_CELL * (w["L"] // 2) ** 2 * w["n_chains"] * S     # per step
+    if args.workload == "grid":   # one launch per step: spins in and out once
+        hbm_bytes = w["n_chains"] * w["L"] ** 2 / 8 * 2
+    else:                         # per sweep: spins read + written, hidden written + read
+        hbm_bytes = w["n_chains"] * w["L"] ** 2 * 7 / 8 * S
     achieved = MUL_OPS_PER_CALL * calls / (t_total / K) / 1e12
     peak = SM_COUNT * IMUL_LANES_PER_SM_CLK * SM_MAX_MHZ * 1e6 / 1e12
     out = {
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws, "steps": K, "warmup": W,
         "ms_per_step": t_total / K * 1e3, "higher_is_better": True, "scaling": "weak",
         "vs_baseline": None, "dtype": "u32", "data": "synthetic", "config": config_dict(w, args),
-        "ess_per_s": {"energy": ess_E * ws / t_total, "m": ess_m * ws / t_total,
+        "ess_per_s": {"energy": None if ess_E != ess_E else ess_E * ws / t_total,
+                      "m": None if ess_m != ess_m else ess_m * ws / t_total,
                       "method": "Sokal windowing c=5 on per-chain series (every "
                                 f"{args.measure_every} sweeps), first 10% discarded, summed over chains"},
         "node_updates_per_s": value * 3.5,
@@ -259,6 +282,9 @@ def main():
         "e2e": {"value": e2e_val, "unit": UNIT, "h2d_bytes_per_step": int(spins_h.nbytes),
                 "d2h_bytes_per_step": int(obs_h.nbytes)},
         "gpu_launches": int(launches),
+        "hbm": {"algorithmic_gbs": hbm_bytes / (t_total / K) / 1e9, "peak_gbs": 6797.9,
+                "note": "0.25 B (SMEM layout: spins in and out once per launch) or 0.875 B "
+                        "(streamed: spins 2 bits + hidden 5 bits per spin-update) of algorithmic traffic"},
         "roofline": {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "Tops/s",
                      "frac": achieved / peak, "traffic": None,
                      "note": "integer-multiply ceiling: 152 SM x 64 lanes/clk x 2070 MHz; 40 "

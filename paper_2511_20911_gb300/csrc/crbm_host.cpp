@@ -192,7 +192,7 @@ int dalloc(crbm_ctx* ctx, T*& ptr, size_t count) {
 
 void free_device(DeviceState& d) {
     void* ptrs[] = {d.v, d.tab, d.ctab, d.sneg, d.inc, d.inc_off, d.sums, d.series, d.corr,
-                    d.seg, d.segmask, d.spins8, d.vtmp, d.err};
+                    d.seg, d.segmask, d.spins8, d.h, d.cnt, d.err};
     for (void* p : ptrs)
         if (p) cudaFree(p);
     d = DeviceState{};
@@ -239,10 +239,16 @@ int crbm_create(crbm_ctx** out, const crbm_params* p) {
         delete ctx;
         return fail(nullptr, CRBM_EINVAL, "SMEM layout needs L <= CRBM_SMEM_MAX_L");
     }
-    if (ctx->layout == CRBM_LAYOUT_STREAM) {
+    if (ctx->layout == CRBM_LAYOUT_STREAM && !g.canonical) {
         delete ctx;
-        return fail(nullptr, CRBM_EUNSUPPORTED, "streamed layout not available in this build");
+        return fail(nullptr, CRBM_EUNSUPPORTED,
+                    "the streamed layout serves the ten SS filters on an even, periodic lattice");
     }
+    if (ctx->layout == CRBM_LAYOUT_STREAM && p->sq_every > 0) {
+        delete ctx;
+        return fail(nullptr, CRBM_EUNSUPPORTED, "spin correlations are accumulated in the SMEM layout only");
+    }
+    g.vil = ctx->layout == CRBM_LAYOUT_STREAM ? 1 : 0;
     if (ctx->layout == CRBM_LAYOUT_SMEM &&
         (g.canonical ? smem_bytes_canon(g) : smem_bytes_generic(g)) > 227 * 1024) {
         delete ctx;
@@ -254,7 +260,8 @@ int crbm_create(crbm_ctx** out, const crbm_params* p) {
         return fail(nullptr, CRBM_EINVAL, "spin correlations need a periodic lattice");
     }
     ctx->n_chains = p->n_chains;
-    ctx->n_words = (p->n_chains + 31) / 32;
+    // the streamed layout stores 64-chain words: an even number of 32-chain halves
+    ctx->n_words = ctx->layout == CRBM_LAYOUT_STREAM ? 2 * ((p->n_chains + 63) / 64) : (p->n_chains + 31) / 32;
     ctx->n_params = p->n_params;
     ctx->seed = p->seed;
     ctx->measure_every = p->measure_every;
@@ -369,7 +376,9 @@ int crbm_create(crbm_ctx** out, const crbm_params* p) {
         (rc = dalloc(ctx, d.series, static_cast<size_t>(p->series_len) * npad * 3)) ||
         (rc = dalloc(ctx, d.corr, p->sq_every > 0 ? static_cast<size_t>(p->n_params) * N : 1)) ||
         (rc = dalloc(ctx, d.seg, seg.size())) || (rc = dalloc(ctx, d.segmask, segmask.size())) ||
-        (rc = dalloc(ctx, d.spins8, static_cast<size_t>(npad) * N)) || (rc = dalloc(ctx, d.err, 4))) {
+        (rc = dalloc(ctx, d.spins8, static_cast<size_t>(npad) * N)) || (rc = dalloc(ctx, d.err, 4)) ||
+        (g.vil && (rc = dalloc(ctx, d.h, static_cast<size_t>(nw) * g.n_cells * 10))) ||
+        (g.vil && (rc = dalloc(ctx, d.cnt, static_cast<size_t>(npad) * 3)))) {
         g_create_error = ctx->err;
         free_device(d);
         delete ctx;
@@ -394,6 +403,7 @@ int crbm_create(crbm_ctx** out, const crbm_params* p) {
         e = cudaMemsetAsync(d.corr, 0, static_cast<size_t>(p->n_params) * N * 8, st);
     if (e == cudaSuccess) e = cudaMemsetAsync(d.spins8, 1, static_cast<size_t>(npad) * N, st);
     if (e == cudaSuccess) e = cudaMemsetAsync(d.err, 0, 4, st);
+    if (e == cudaSuccess && d.cnt) e = cudaMemsetAsync(d.cnt, 0, static_cast<size_t>(npad) * 12, st);
     if (e == cudaSuccess)
         e = launch_init(g, d.v, nw, static_cast<uint32_t>(ctx->seed),
                         static_cast<uint32_t>(ctx->seed >> 32), st);
@@ -440,6 +450,8 @@ int crbm_sweep(crbm_ctx* ctx, int64_t n_sweeps) {
         a.inc_off = ctx->d.inc_off;
         a.sums = ctx->d.sums;
         a.series = ctx->d.series;
+        a.h = ctx->d.h;
+        a.cnt = ctx->d.cnt;
         a.corr = ctx->d.corr;
         a.seg = ctx->d.seg;
         a.segmask = ctx->d.segmask;
@@ -457,10 +469,15 @@ int crbm_sweep(crbm_ctx* ctx, int64_t n_sweeps) {
         a.meas0 = ctx->meas;
         a.series_len = ctx->series_len;
         a.sq_every = ctx->sq_every;
-        const cudaError_t e = ctx->g.canonical ? launch_sweep_canon(a, ctx->warps, ctx->stream)
-                                               : launch_sweep_generic(a, ctx->warps, ctx->stream);
+        cudaError_t e;
+        if (ctx->layout == CRBM_LAYOUT_STREAM) {
+            e = launch_sweep_stream(a, ctx->stream, &ctx->launches);
+        } else {
+            e = ctx->g.canonical ? launch_sweep_canon(a, ctx->warps, ctx->stream)
+                                 : launch_sweep_generic(a, ctx->warps, ctx->stream);
+            ++ctx->launches;
+        }
         if (e != cudaSuccess) return cuda_fail(ctx, e, "sweep launch");
-        ++ctx->launches;
         const int64_t t0 = ctx->sweeps, t1 = ctx->sweeps + chunk;
         if (ctx->measure_every > 0) ctx->meas += t1 / ctx->measure_every - t0 / ctx->measure_every;
         if (ctx->sq_every > 0) ctx->sq_meas += t1 / ctx->sq_every - t0 / ctx->sq_every;

@@ -7,6 +7,12 @@
 
 namespace crbm {
 
+// Index of the packed word of 32-chain word w at site s in either layout.
+__host__ __device__ inline size_t word_index(int vil, int w, int N, int s) {
+    return vil ? (static_cast<size_t>(w >> 1) * N + s) * 2 + (w & 1)
+               : static_cast<size_t>(w) * N + s;
+}
+
 constexpr int kMaxBonds = 16;  // filters per 3x3 window -> at most 4 hidden Philox calls
 constexpr int kNSum = 11;      // per-chain observable sums
 constexpr int kWordBits = 32;  // chains per packed word (one bit per chain)
@@ -34,6 +40,7 @@ struct Geometry {
     int nTv;       // (2 DJ + 1) (2 DJp + 1)
     int nTab;      // 10 hidden entries + nTv visible entries
     int n_real_bonds[2];  // bonds with both endpoints real, per class
+    int vil;       // spin storage: 0 = [word][site], 1 = 64-chain words [group][site][2]
     int8_t r1[kMaxBonds], c1[kMaxBonds], r2[kMaxBonds], c2[kMaxBonds];
     uint8_t cls[kMaxBonds];
 };
@@ -52,7 +59,8 @@ struct DeviceState {
     int32_t* seg = nullptr;       // [n_words][33]: n_seg, then (param << 8 | first lane) ...
     uint32_t* segmask = nullptr;  // [n_words][32] lane mask of each segment
     int8_t* spins8 = nullptr;     // [n_words * 32][N] staging for get/set spins
-    uint32_t* vtmp = nullptr;     // [n_words][N] second buffer for the streamed layout
+    uint32_t* h = nullptr;        // streamed layout: [n_words][n_cells][10] hidden words
+    int* cnt = nullptr;           // streamed layout: [n_words * 32][3] measurement counts
     int* err = nullptr;           // device error word
 };
 
@@ -66,6 +74,8 @@ struct SweepArgs {
     const int32_t* inc_off;
     int64_t* sums;
     int32_t* series;
+    uint32_t* h;
+    int* cnt;
     int64_t* corr;
     const int32_t* seg;
     const uint32_t* segmask;
@@ -88,6 +98,7 @@ cudaError_t launch_init(const Geometry& g, uint32_t* v, int n_words, uint32_t ke
                         uint32_t key1, cudaStream_t st);
 cudaError_t launch_sweep_generic(const SweepArgs& a, int warps_per_cta, cudaStream_t st);
 cudaError_t launch_sweep_canon(const SweepArgs& a, int warps_per_cta, cudaStream_t st);
+cudaError_t launch_sweep_stream(const SweepArgs& a, cudaStream_t st, int64_t* launches);
 cudaError_t launch_philox(const uint32_t* in, uint32_t* out, int n, cudaStream_t st);
 cudaError_t launch_unpack(const Geometry& g, const uint32_t* v, int8_t* out, int n_words,
                           cudaStream_t st);

@@ -208,7 +208,7 @@ __global__ void k_init(const Geometry g, uint32_t* v, int n_words, uint32_t k0, 
         const uint32_t cell = static_cast<uint32_t>((R >> 1) * g.W + (C >> 1));
         const U4 q = philox(cell, 0u, static_cast<uint32_t>(word) * 32u + lane, kTagInit, k0, k1);
         const uint32_t b = __ballot_sync(0xffffffffu, pick(q, 2 * (R & 1) + (C & 1)) < 0x80000000u);
-        if (lane == 0) v[x] = b;
+        if (lane == 0) v[word_index(g.vil, word, g.N, s)] = b;
     }
 }
 
@@ -218,7 +218,7 @@ __global__ void k_unpack(const Geometry g, const uint32_t* v, int8_t* out, int n
          x += static_cast<long long>(gridDim.x) * blockDim.x) {
         const long long chain = x / g.N;
         const int s = static_cast<int>(x - chain * g.N);
-        const uint32_t w = v[(chain >> 5) * g.N + s];
+        const uint32_t w = v[word_index(g.vil, static_cast<int>(chain >> 5), g.N, s)];
         out[x] = ((w >> (chain & 31)) & 1u) ? 1 : -1;
     }
 }
@@ -232,7 +232,7 @@ __global__ void k_pack(const Geometry g, const int8_t* in, uint32_t* v, int n_wo
         const int s = static_cast<int>(x - word * g.N);
         const int8_t val = in[(word * 32 + lane) * g.N + s];
         const uint32_t b = __ballot_sync(0xffffffffu, val > 0);
-        if (lane == 0) v[x] = b;
+        if (lane == 0) v[word_index(g.vil, static_cast<int>(word), g.N, s)] = b;
     }
 }
 

@@ -49,3 +49,11 @@ def random_params(rng, n):
 
 def random_spins(rng, n_chains, L):
     return rng.choice(np.array([-1, 1], np.int8), size=(n_chains, L, L))
+
+
+def stream_workload():
+    """L=384 periodic, J=J'=1, beta=1, h in {0, 1, 2} x 1024 chains (3072
+    chains), spins and hidden units in HBM; 10^4 sweeps."""
+    return dict(L=384, params=dict(J=[1.0] * 3, Jp=[1.0] * 3, h=[0.0, 1.0, 2.0], beta=[1.0] * 3),
+                n_chains=3072, chain_param=np.repeat(np.arange(3, dtype=np.int32), 1024), seed=384,
+                n_sweeps=10_000)

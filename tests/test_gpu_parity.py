@@ -23,10 +23,11 @@ def _gpu():
 
 
 def run_pair(orc, L, params, n_chains, chain_param, seed, splits, measure_every=1,
-             periodic=True, bonds=None, series_len=0, sq_every=0, check_ids=None):
+             periodic=True, bonds=None, series_len=0, sq_every=0, check_ids=None,
+             layout=crbm.CRBM_LAYOUT_AUTO):
     s = crbm.Sampler(L, params, n_chains, chain_param=chain_param, seed=seed, periodic=periodic,
                      bonds=bonds, measure_every=measure_every, series_len=series_len,
-                     sq_every=sq_every)
+                     sq_every=sq_every, layout=layout)
     ids = np.arange(n_chains, dtype=np.uint32) if check_ids is None else np.asarray(check_ids, np.uint32)
     cp = np.asarray(chain_param, np.int32)[ids]
     ospins = orc.init_spins(L, ids, seed)
@@ -192,3 +193,38 @@ def test_full_grid_workload_sampled_chains(orc):
     ids = np.linspace(0, w["n_chains"] - 1, 64).astype(np.uint32)
     run_pair(orc, 18, w["params"], w["n_chains"], w["chain_param"], w["seed"], splits=[10, 20],
              measure_every=10, check_ids=ids)
+
+
+@pytest.mark.parametrize("L,n", [(8, 70), (20, 64), (36, 130), (34, 33)])
+def test_stream_layout_bitexact(orc, L, n):
+    """Two-phase HBM layout (64-chain words, 16x16-cell tiles with halos),
+    including ragged tiles and a ragged last 64-chain group."""
+    rng = np.random.default_rng(L * 7 + n)
+    params = workloads.random_params(rng, 3)
+    cp = rng.integers(0, 3, n).astype(np.int32)
+    s, spins, sums, _ = run_pair(orc, L, params, n, cp, 11, splits=[2, 5], measure_every=2,
+                                 series_len=4, layout=crbm.CRBM_LAYOUT_STREAM)
+    assert s.layout == crbm.CRBM_LAYOUT_STREAM
+    m = crbm.Sampler(L, params, n, chain_param=cp, seed=11, measure_every=2,
+                     layout=crbm.CRBM_LAYOUT_SMEM)
+    m.sweep(7)
+    assert np.array_equal(m.get_spins(), spins)
+    assert np.array_equal(m.observables(), sums)
+
+
+@pytest.mark.slow
+def test_stream_workload_L384_sampled_chains(orc):
+    """The L=384 workload at full size (3072 chains, the benchmark's launch):
+    16 chains spread over all words checked against the oracle."""
+    w = workloads.stream_workload()
+    ids = np.linspace(0, w["n_chains"] - 1, 16).astype(np.uint32)
+    run_pair(orc, 384, w["params"], w["n_chains"], w["chain_param"], w["seed"], splits=[1, 2],
+             measure_every=1, check_ids=ids)
+
+
+def test_stream_rejects_unsupported():
+    ok = dict(J=[1.0], Jp=[1.0], h=[0.5], beta=[2.0])
+    for kw in (dict(L=9), dict(L=10, periodic=False), dict(L=10, sq_every=1)):
+        with pytest.raises(crbm.CrbmError) as e:
+            crbm.Sampler(params=ok, n_chains=4, layout=crbm.CRBM_LAYOUT_STREAM, **kw)
+        assert e.value.code == crbm.CRBM_EUNSUPPORTED

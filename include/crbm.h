@@ -162,6 +162,41 @@ int crbm_load(crbm_ctx* ctx, const void* buf, size_t n);
  * keys every draw; synchronous.  Errors: CRBM_EINVAL, CRBM_ENOMEM, CRBM_ECUDA. */
 int crbm_philox(const uint32_t* in, uint32_t* out, size_t n);
 
+/* Size of the fixed device scratch array of crbm_sweep_stream_noalloc. */
+#define CRBM_NOALLOC_SCRATCH_BYTES (32u << 20)
+
+/* Streamed sweep that allocates nothing, for callers that cannot call
+ * cudaMalloc (code running under another framework's allocator or memory
+ * pool, or a service whose device memory is fixed at start-up).  The paper
+ * has no counterpart: it is the two-launch streamed sweep of the
+ * CRBM_LAYOUT_STREAM contexts, stateless and without a context.
+ *
+ * p: the model and chains (L even, periodic = 1, bonds = NULL, J, Jp, h,
+ *    beta, n_params, chain_param, n_chains, seed, stream); measure_every,
+ *    series_len, sq_every and layout are ignored: no observables are kept.
+ * v: device spins owned by the caller, in/out, the streamed layout:
+ *    u32 v[ceil(n_chains/64)][L*L][2], bit l of v[g][s][k] = spin +1 of chain
+ *    64 g + 32 k + l at site s (pad chains of the last group are sampled too).
+ * Runs sweeps sweep0 .. sweep0 + n_sweeps - 1 of the same Philox keying as a
+ * context, so the result is bit-identical to crbm_sweep on a
+ * CRBM_LAYOUT_STREAM context holding the same spins at the same sweep count.
+ *
+ * Scratch: one static device array of CRBM_NOALLOC_SCRATCH_BYTES per GPU that
+ * loads the library, held until exit; it takes the lane threshold tables and
+ * the hidden words, 4 * n_words * (4352 + 10 (L/2)^2) bytes with
+ * n_words = 2 ceil(n_chains / 64).  Larger requests return
+ * CRBM_EUNSUPPORTED.  Every call shares the array and leaves its contents
+ * behind (each call rewrites all of it that it reads), so calls that overlap
+ * on the GPU -- on different streams, or from several threads -- race.
+ * The first call on a device fetches the array's device address
+ * (cudaGetSymbolAddress, with that device current); make that first call
+ * before any stream capture.  Asynchronous on p->stream apart from the table
+ * upload from host memory.  No cudaMalloc, cudaFree or other allocation.
+ * Errors (code only, crbm_last_error is not updated): CRBM_EINVAL (bad
+ * arguments or parameters), CRBM_EUNSUPPORTED (needs more scratch than
+ * CRBM_NOALLOC_SCRATCH_BYTES), CRBM_ECUDA. */
+int crbm_sweep_stream_noalloc(const crbm_params* p, uint32_t* v, int64_t sweep0, int64_t n_sweeps);
+
 /* Message for the last failed call on ctx (or of the last failed
  * crbm_create when ctx is NULL).  Never NULL. */
 const char* crbm_last_error(const crbm_ctx* ctx);

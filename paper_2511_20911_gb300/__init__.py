@@ -30,7 +30,7 @@ ABI_FUNCTIONS = (
     "crbm_create", "crbm_destroy", "crbm_sweep", "crbm_sweep_count", "crbm_observables",
     "crbm_series", "crbm_correlations", "crbm_structure_factor", "crbm_reset_observables",
     "crbm_get_spins", "crbm_set_spins", "crbm_get_tables", "crbm_layout", "crbm_launch_count",
-    "crbm_save", "crbm_load", "crbm_philox", "crbm_last_error",
+    "crbm_save", "crbm_load", "crbm_philox", "crbm_sweep_stream_noalloc", "crbm_last_error",
 )
 
 
@@ -89,6 +89,7 @@ def load_library(path: str | None = None):
         "crbm_save": (c.c_int, [vp, vp, c.POINTER(c.c_size_t)]),
         "crbm_load": (c.c_int, [vp, vp, c.c_size_t]),
         "crbm_philox": (c.c_int, [c.POINTER(c.c_uint32), c.POINTER(c.c_uint32), c.c_size_t]),
+        "crbm_sweep_stream_noalloc": (c.c_int, [c.POINTER(crbm_params), vp, c.c_int64, c.c_int64]),
         "crbm_last_error": (c.c_char_p, [vp]),
     }
     for name, (res, args) in sigs.items():

@@ -209,6 +209,14 @@ int default_warps(const Geometry& g) {
 
 }  // namespace
 
+namespace crbm {
+bool host_to_q4(double x, int32_t& q) { return to_q4(x, q); }
+void host_point_tables(const Geometry& g, double beta, int32_t qJ, int32_t qJp, int32_t qh,
+                       uint32_t* out, int sgn[2]) {
+    point_tables(g, beta, qJ, qJp, qh, out, sgn);
+}
+}  // namespace crbm
+
 extern "C" {
 
 int crbm_create(crbm_ctx** out, const crbm_params* p) {
@@ -333,11 +341,6 @@ int crbm_create(crbm_ctx** out, const crbm_params* p) {
     // position; the coefficient signs and the field sums are folded in.
     std::vector<uint32_t> ctab;
     if (g.canonical) {
-        // (class, second endpoint) of slots 0..4 for spins (0,0), (0,1), (1,0), (1,1)
-        static const int kSlot[4][5][2] = {{{0, 0}, {0, 0}, {1, 0}, {0, 1}, {0, 1}},
-                                           {{0, 1}, {0, 0}, {0, 0}, {0, 1}, {1, 1}},
-                                           {{0, 0}, {0, 1}, {0, 0}, {0, 1}, {1, 0}},
-                                           {{0, 1}, {0, 1}, {1, 1}, {0, 0}, {0, 0}}};
         ctab.assign(static_cast<size_t>(nw) * kCanonTab, 0u);
         for (int w = 0; w < nw; ++w)
             for (int l = 0; l < 32; ++l) {
@@ -355,8 +358,8 @@ int crbm_create(crbm_ctx** out, const crbm_params* p) {
                     for (int idx = 0; idx < 32; ++idx) {
                         int n[2] = {0, 0};
                         for (int slot = 0; slot < 5; ++slot) {
-                            const int cls = kSlot[sc][slot][0];
-                            const int coef = kSlot[sc][slot][1] ? sgn[2 * pp + cls] : 1;
+                            const int cls = kCanonSlot[sc][slot][0];
+                            const int coef = kCanonSlot[sc][slot][1] ? sgn[2 * pp + cls] : 1;
                             n[cls] += coef * (2 * ((idx >> slot) & 1) - 1);
                         }
                         out[kCanonTh + (sc * 32 + idx) * 32 + l] =

@@ -24,6 +24,12 @@ constexpr uint32_t kTagSwap = 6u;  // Philox tag of replica-exchange decisions
 // then visible [4 spin positions][32 idx][32 lanes] (see crbm_canon.cu).
 constexpr int kCanonTh = 2 * 4 * 32;
 constexpr int kCanonTab = kCanonTh + 4 * 32 * 32;
+// (class, second-endpoint flag) of the five filter slots of each spin
+// position (0,0), (0,1), (1,0), (1,1) in the canonical visible tables.
+constexpr int kCanonSlot[4][5][2] = {{{0, 0}, {0, 0}, {1, 0}, {0, 1}, {0, 1}},
+                                     {{0, 1}, {0, 0}, {0, 0}, {0, 1}, {1, 1}},
+                                     {{0, 0}, {0, 1}, {0, 0}, {0, 1}, {1, 0}},
+                                     {{0, 1}, {0, 1}, {1, 1}, {0, 0}, {0, 0}}};
 
 // Lattice and filter geometry, passed by value to kernels (lives in the
 // kernel-parameter constant bank, read uniformly by every warp).
@@ -90,6 +96,13 @@ struct SweepArgs {
     int series_len;
     int sq_every;         // 0 = never
 };
+
+// Host model helpers (crbm_host.cpp): Q.4 rounding of a coupling, and the
+// ten hidden + (2DJ+1)(2DJp+1) visible thresholds and the two class signs of
+// one parameter point.
+bool host_to_q4(double x, int32_t& q);
+void host_point_tables(const Geometry& g, double beta, int32_t qJ, int32_t qJp, int32_t qh,
+                       uint32_t* out, int sgn[2]);
 
 // Kernel launchers (crbm_kernels.cu).  All return cudaGetLastError().
 size_t smem_bytes_generic(const Geometry& g);

@@ -29,7 +29,7 @@ TAG_VIS, TAG_INIT, TAG_SWAP = 4, 5, 6
 def build(force: bool = False) -> str:
     """Compile crbm_oracle.c into oracle/_build/liboracle.so (gcc, OpenMP)."""
     os.makedirs(_LIB_DIR, exist_ok=True)
-    srcs = [_SRC, os.path.join(_HERE, "crbm_oracle.h"), os.path.join(_HERE, "oracle_pt.c")]
+    srcs = [_SRC, os.path.join(_HERE, "crbm_oracle.h")]
     srcs = [s for s in srcs if os.path.exists(s)]
     if not force and os.path.exists(_LIB):
         if all(os.path.getmtime(_LIB) >= os.path.getmtime(s) for s in srcs):
@@ -187,3 +187,39 @@ def set_threads(n):
 
 def get_threads():
     return int(lib().orc_get_threads())
+
+
+def run_pt(L, params, chain_param, spins, slot_of_beta, seed, sweep0, n_sweeps, measure_every=1,
+           swap_every=10, periodic=True, bonds=None, sums=None, series_cap=0):
+    """Parallel tempering on ladders of 32 chains (see orc_run_pt).  Advances
+    ``spins`` (per slot) and ``slot_of_beta`` [n_ladders][32] in place; sums
+    and series rows are per rung (chain index 32 l + k)."""
+    arr, nb = bonds_array(bonds)
+    J = np.ascontiguousarray(params["J"], np.float64)
+    Jp = np.ascontiguousarray(params["Jp"], np.float64)
+    h = np.ascontiguousarray(params["h"], np.float64)
+    beta = np.ascontiguousarray(params["beta"], np.float64)
+    cp = np.ascontiguousarray(chain_param, np.int32)
+    n = len(cp)
+    assert spins.dtype == np.int8 and spins.flags.c_contiguous and spins.shape == (n, L, L)
+    assert slot_of_beta.dtype == np.int32 and slot_of_beta.flags.c_contiguous
+    if sums is None:
+        sums = np.zeros((n, NSUM), np.int64)
+    series = np.zeros((n, series_cap, 3), np.int32) if series_cap > 0 else None
+    rc = lib().orc_run_pt(L, int(periodic), arr, nb, _p(J, ctypes.c_double),
+                          _p(Jp, ctypes.c_double), _p(h, ctypes.c_double),
+                          _p(beta, ctypes.c_double), len(J), _p(cp, ctypes.c_int32), n,
+                          ctypes.c_uint64(seed), ctypes.c_int64(sweep0), ctypes.c_int64(n_sweeps),
+                          int(measure_every), int(swap_every), _p(spins, ctypes.c_int8),
+                          _p(slot_of_beta, ctypes.c_int32), _p(sums, ctypes.c_int64),
+                          _p(series, ctypes.c_int32), ctypes.c_int64(series_cap))
+    if rc:
+        raise ValueError(f"orc_run_pt failed ({rc})")
+    return sums, series
+
+
+def swap_threshold(x):
+    f = lib().orc_swap_threshold
+    f.restype = ctypes.c_uint32
+    f.argtypes = [ctypes.c_double]
+    return int(f(float(x)))

@@ -371,6 +371,134 @@ int orc_run(int L, int periodic, const orc_bond* bonds, int nb, const double* J,
     return 0;
 }
 
+/* ------------------------------------------------- parallel tempering */
+/* Replica exchange between adjacent rungs of a temperature ladder (the
+ * paper's introduction lists parallel tempering among the Monte Carlo
+ * remedies for trapping); see orc_run_pt in crbm_oracle.h. */
+uint32_t orc_swap_threshold(double x) {
+    double t = nearbyint(ldexp(exp(x), 32));
+    if (t > 4294967295.0) t = 4294967295.0;
+    if (t < 0.0) t = 0.0;
+    return (uint32_t)t;
+}
+
+int orc_run_pt(int L, int periodic, const orc_bond* bonds, int nb, const double* J,
+               const double* Jp, const double* h, const double* beta, int n_params,
+               const int32_t* chain_param, int n_chains, uint64_t seed, int64_t sweep0,
+               int64_t n_sweeps, int measure_every, int swap_every, int8_t* spins,
+               int32_t* slot_of_beta, int64_t* sums, int32_t* series, int64_t series_cap) {
+    if (n_chains <= 0 || n_chains % 32 || swap_every <= 0 || measure_every < 0) return -1;
+    int n_lad = n_chains / 32, N = L * L;
+    for (int l = 0; l < n_lad; ++l) {
+        const int32_t* cp = chain_param + 32 * l;
+        for (int k = 0; k < 32; ++k) {
+            if (cp[k] < 0 || cp[k] >= n_params) return -1;
+            if (J[cp[k]] != J[cp[0]] || Jp[cp[k]] != Jp[cp[0]] || h[cp[k]] != h[cp[0]]) return -1;
+            if (k > 0 && !(beta[cp[k]] > beta[cp[k - 1]])) return -1;
+        }
+    }
+    int DJ, DJp;
+    if (orc_degrees(L, periodic, bonds, nb, &DJ, &DJp)) return -1;
+    int nTv = (2 * DJ + 1) * (2 * DJp + 1);
+    orc_point* pts = (orc_point*)calloc((size_t)n_params, sizeof(orc_point));
+    uint32_t* tv = (uint32_t*)calloc((size_t)n_params * nTv, sizeof(uint32_t));
+    if (!pts || !tv) {
+        free(pts);
+        free(tv);
+        return -2;
+    }
+    int err = 0;
+    for (int p = 0; p < n_params; ++p) {
+        pts[p].Tv = tv + (size_t)p * nTv;
+        if (orc_tables(L, periodic, bonds, nb, J[p], Jp[p], h[p], beta[p], pts[p].Th, pts[p].Tv))
+            err = 1;
+        int32_t qq;
+        double a;
+        orc_quantize(J[p], &qq);
+        orc_weight(beta[p], qq / 16.0, &a, &pts[p].s[0]);
+        orc_quantize(Jp[p], &qq);
+        orc_weight(beta[p], qq / 16.0, &a, &pts[p].s[1]);
+    }
+    if (err) {
+        free(pts);
+        free(tv);
+        return -1;
+    }
+    int W = n_windows(L);
+#pragma omp parallel for schedule(dynamic, 1)
+    for (int l = 0; l < n_lad; ++l) {
+        int8_t* hid = (int8_t*)malloc((size_t)W * W * nb);
+        int* field = (int*)malloc(sizeof(int) * 2 * N);
+        const int32_t* cp = chain_param + 32 * l;
+        int32_t* sob = slot_of_beta + 32 * l;
+        int32_t q[3];
+        orc_quantize(J[cp[0]], &q[0]);
+        orc_quantize(Jp[cp[0]], &q[1]);
+        orc_quantize(h[cp[0]], &q[2]);
+        for (int64_t t = sweep0; t < sweep0 + n_sweeps; ++t) {
+            int bos[32];
+            for (int k = 0; k < 32; ++k) bos[sob[k]] = k;
+            for (int r = 0; r < 32; ++r)
+                one_sweep(L, periodic, bonds, nb, &pts[cp[bos[r]]], DJ, DJp, (uint32_t)(32 * l + r),
+                          (uint32_t)t, seed, spins + (size_t)(32 * l + r) * N, hid, field);
+            int64_t nJ[32], nP[32], M[32], E[32];
+            for (int r = 0; r < 32; ++r) {
+                orc_counts(L, periodic, bonds, nb, spins + (size_t)(32 * l + r) * N, &nJ[r],
+                           &nP[r], &M[r]);
+                E[r] = (int64_t)q[0] * nJ[r] + (int64_t)q[1] * nP[r] - (int64_t)q[2] * M[r];
+            }
+            if (measure_every > 0 && (t + 1) % measure_every == 0 && sums) {
+                for (int k = 0; k < 32; ++k) {
+                    const int r = sob[k];
+                    int64_t* s = sums + (size_t)(32 * l + k) * ORC_NSUM;
+                    if (series && s[0] < series_cap) {
+                        int32_t* e = series + ((size_t)(32 * l + k) * series_cap + s[0]) * 3;
+                        e[0] = (int32_t)nJ[r];
+                        e[1] = (int32_t)nP[r];
+                        e[2] = (int32_t)M[r];
+                    }
+                    s[0] += 1;
+                    s[1] += nJ[r];
+                    s[2] += nP[r];
+                    s[3] += M[r];
+                    s[4] += M[r] < 0 ? -M[r] : M[r];
+                    s[5] += nJ[r] * nJ[r];
+                    s[6] += nP[r] * nP[r];
+                    s[7] += M[r] * M[r];
+                    s[8] += nJ[r] * nP[r];
+                    s[9] += nJ[r] * M[r];
+                    s[10] += nP[r] * M[r];
+                }
+            }
+            if ((t + 1) % swap_every == 0) {
+                const int64_t m = (t + 1) / swap_every - 1;
+                for (int k = (int)(m & 1); k < 31; k += 2) {
+                    const int64_t D = E[sob[k]] - E[sob[k + 1]];
+                    int accept = D <= 0;
+                    if (!accept) {
+                        const double x = (beta[cp[k]] - beta[cp[k + 1]]) * (double)D / 16.0;
+                        uint32_t ctr[4] = {(uint32_t)k, (uint32_t)m, (uint32_t)l, ORC_TAG_SWAP};
+                        uint32_t key[2] = {(uint32_t)(seed & 0xffffffffu), (uint32_t)(seed >> 32)};
+                        uint32_t out[4];
+                        orc_philox4x32_10(ctr, key, out);
+                        accept = out[0] < orc_swap_threshold(x);
+                    }
+                    if (accept) {
+                        const int32_t tmp = sob[k];
+                        sob[k] = sob[k + 1];
+                        sob[k + 1] = tmp;
+                    }
+                }
+            }
+        }
+        free(hid);
+        free(field);
+    }
+    free(pts);
+    free(tv);
+    return 0;
+}
+
 void orc_set_threads(int n) {
 #ifdef _OPENMP
     if (n > 0) omp_set_num_threads(n);

@@ -101,3 +101,28 @@ int orc_get_threads(void);
 }
 #endif
 #endif
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+/* Parallel tempering (replica exchange) on ladders of 32 chains: chains
+ * 32 l .. 32 l + 31 form ladder l.  Chain index 32 l + k of chain_param names
+ * the parameter point of temperature rung k (beta strictly increasing in k,
+ * equal J, J', h along a ladder).  slot_of_beta[l][k] (in/out) is the replica
+ * slot holding rung k; spins are stored per slot and every slot's Gibbs
+ * draws use its own chain index 32 l + slot.  After sweep t, if measuring,
+ * rung k's configuration is measured into sums / series row 32 l + k; then,
+ * if (t + 1) % swap_every == 0 (round m = (t + 1) / swap_every - 1), every
+ * pair (k, k+1) with k = m mod 2 (mod 2) exchanges rungs with probability
+ * min(1, exp((beta_k - beta_{k+1}) (E_k - E_{k+1}) / 16)), E in 1/16 units:
+ * accepted iff E_k <= E_{k+1} or u < nearbyint(2^32 exp(x)), u = word 0 of
+ * Philox((k, m, l, ORC_TAG_SWAP)). */
+int orc_run_pt(int L, int periodic, const orc_bond* bonds, int nb, const double* J,
+               const double* Jp, const double* h, const double* beta, int n_params,
+               const int32_t* chain_param, int n_chains, uint64_t seed, int64_t sweep0,
+               int64_t n_sweeps, int measure_every, int swap_every, int8_t* spins,
+               int32_t* slot_of_beta, int64_t* sums, int32_t* series, int64_t series_cap);
+uint32_t orc_swap_threshold(double x);
+#ifdef __cplusplus
+}
+#endif

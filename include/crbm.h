@@ -90,6 +90,16 @@ typedef struct {
     int32_t series_len;     /* per-chain time-series capacity in measurements, 0 = none */
     int32_t sq_every;       /* accumulate spin correlations every K_S sweeps, 0 = never */
     int32_t layout;         /* CRBM_LAYOUT_* */
+    /* Replica exchange (parallel tempering), 0 = off.  > 0: every 32-chain
+     * group c = 32 l .. 32 l + 31 is a temperature ladder -- rung k is the
+     * parameter point chain_param[32 l + k], all rungs with equal J, J', h and
+     * beta strictly increasing in k -- and after every swap_every-th sweep
+     * adjacent rungs exchange configurations by the Metropolis rule
+     * min(1, exp((beta_k - beta_{k+1}) (E_k - E_{k+1}))) on exact integer
+     * energies.  Needs n_chains % 32 == 0 and the SMEM layout.  Observables
+     * then belong to rungs (row 32 l + k), spins to replica slots (see
+     * crbm_get_permutation). */
+    int32_t swap_every;
     void* stream;           /* cudaStream_t for all work; NULL = legacy default stream */
 } crbm_params;
 
@@ -143,6 +153,11 @@ int crbm_set_spins(crbm_ctx* ctx, const int8_t* in, size_t n_in);
  * Th[cls][m+2] (m in -2..2) then Tv[nJ+DJ][nJ'+DJ'].  dims may be NULL; else
  * dims[0] = DJ, dims[1] = DJ'. */
 int crbm_get_tables(crbm_ctx* ctx, uint32_t* out, size_t n_out, int32_t* dims);
+
+/* Replica permutation of a tempering context, host array out[n_chains]
+ * int32: out[32 l + k] = replica slot (chain index within ladder l) that
+ * holds rung k.  The identity without tempering. */
+int crbm_get_permutation(crbm_ctx* ctx, int32_t* out, size_t n_out);
 
 /* Which layout the context runs (CRBM_LAYOUT_SMEM or CRBM_LAYOUT_STREAM). */
 int crbm_layout(const crbm_ctx* ctx);

@@ -29,7 +29,8 @@ SUM_FIELDS = ("n", "NJ", "NJp", "M", "absM", "NJ2", "NJp2", "M2", "NJ_NJp", "NJ_
 ABI_FUNCTIONS = (
     "crbm_create", "crbm_destroy", "crbm_sweep", "crbm_sweep_count", "crbm_observables",
     "crbm_series", "crbm_correlations", "crbm_structure_factor", "crbm_reset_observables",
-    "crbm_get_spins", "crbm_set_spins", "crbm_get_tables", "crbm_layout", "crbm_launch_count",
+    "crbm_get_spins", "crbm_set_spins", "crbm_get_tables", "crbm_get_permutation", "crbm_layout",
+    "crbm_launch_count",
     "crbm_save", "crbm_load", "crbm_philox", "crbm_sweep_stream_noalloc", "crbm_last_error",
 )
 
@@ -54,7 +55,7 @@ class crbm_params(ctypes.Structure):
                 ("n_chains", ctypes.c_int32), ("seed", ctypes.c_uint64),
                 ("measure_every", ctypes.c_int32), ("series_len", ctypes.c_int32),
                 ("sq_every", ctypes.c_int32), ("layout", ctypes.c_int32),
-                ("stream", ctypes.c_void_p)]
+                ("swap_every", ctypes.c_int32), ("stream", ctypes.c_void_p)]
 
 
 _lib = None
@@ -84,6 +85,7 @@ def load_library(path: str | None = None):
         "crbm_get_spins": (c.c_int, [vp, c.POINTER(c.c_int8), c.c_size_t]),
         "crbm_set_spins": (c.c_int, [vp, c.POINTER(c.c_int8), c.c_size_t]),
         "crbm_get_tables": (c.c_int, [vp, c.POINTER(c.c_uint32), c.c_size_t, c.POINTER(c.c_int32)]),
+        "crbm_get_permutation": (c.c_int, [vp, c.POINTER(c.c_int32), c.c_size_t]),
         "crbm_layout": (c.c_int, [vp]),
         "crbm_launch_count": (c.c_int64, [vp]),
         "crbm_save": (c.c_int, [vp, vp, c.POINTER(c.c_size_t)]),
@@ -127,7 +129,7 @@ class Sampler:
 
     def __init__(self, L, params, n_chains, chain_param=None, seed=1, periodic=True,
                  bonds=None, measure_every=1, series_len=0, sq_every=0,
-                 layout=CRBM_LAYOUT_AUTO, stream=None):
+                 layout=CRBM_LAYOUT_AUTO, swap_every=0, stream=None):
         lib = load_library()
         self.L, self.n_chains = int(L), int(n_chains)
         self._J = np.ascontiguousarray(params["J"], np.float64)
@@ -156,6 +158,7 @@ class Sampler:
         p.seed = int(seed) & 0xFFFFFFFFFFFFFFFF
         p.measure_every, p.series_len, p.sq_every = int(measure_every), self.series_len, self.sq_every
         p.layout = int(layout)
+        p.swap_every = int(swap_every)
         p.stream = ctypes.c_void_p(int(stream)) if stream else None
         h = ctypes.c_void_p()
         _check(lib.crbm_create(ctypes.byref(h), ctypes.byref(p)))
@@ -223,6 +226,12 @@ class Sampler:
     def set_spins(self, spins):
         a = np.ascontiguousarray(spins, np.int8)
         _check(self._lib.crbm_set_spins(self._ctx, _ptr(a, ctypes.c_int8), a.size), self._ctx)
+
+    def permutation(self):
+        """[n_chains] int32: entry 32 l + k = slot of ladder l holding rung k."""
+        out = np.zeros(self.n_chains, np.int32)
+        _check(self._lib.crbm_get_permutation(self._ctx, _ptr(out, ctypes.c_int32), out.size), self._ctx)
+        return out
 
     def tables(self):
         dims = np.zeros(2, np.int32)

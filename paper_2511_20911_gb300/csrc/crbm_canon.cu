@@ -27,6 +27,8 @@ __global__ void __launch_bounds__(512, CRBM_SWEEP_MIN_BLOCKS) k_sweep_canon(cons
     int* s_cnt = reinterpret_cast<int*>(s_h + g.n_cells * 10);   // [3][32]
     int* s_seg = s_cnt + 96;                                      // [33]
     uint32_t* s_segmask = reinterpret_cast<uint32_t*>(s_seg + 33); // [32]
+    int* s_sob = reinterpret_cast<int*>(s_segmask + 32);          // [32] slot of each rung
+    int* s_bos = s_sob + 32;                                        // [32] rung of each slot
 
     const uint4* gt = reinterpret_cast<const uint4*>(a.ctab + static_cast<size_t>(word) * kCanonTab);
     for (int x = threadIdx.x; x < kCanonTab / 4; x += blockDim.x) reinterpret_cast<uint4*>(smem)[x] = gt[x];
@@ -44,7 +46,13 @@ __global__ void __launch_bounds__(512, CRBM_SWEEP_MIN_BLOCKS) k_sweep_canon(cons
 #pragma unroll
     for (int s = 0; s < 5; ++s) lc.rot[s] = static_cast<uint32_t>(lane - 7 - s) & 31u;
     const Round0Lane r0l = round0_lane(chain);
+    if (warp == 0) {  // replica permutation (identity without tempering)
+        const int sob = a.swap_every > 0 ? a.sob[word * 32 + lane] : lane;
+        s_sob[lane] = sob;
+        s_bos[sob] = lane;
+    }
     __syncthreads();
+    lc.lb = 4u * static_cast<uint32_t>(s_bos[lane]);  // lane reads the column of its rung
 
     int64_t acc[kNSum];
     const bool measuring = a.measure_every > 0;
@@ -90,7 +98,9 @@ __global__ void __launch_bounds__(512, CRBM_SWEEP_MIN_BLOCKS) k_sweep_canon(cons
             }
         }
         __syncthreads();
-        if (measuring && (t + 1u) % static_cast<uint32_t>(a.measure_every) == 0u) {
+        const bool do_meas = measuring && (t + 1u) % static_cast<uint32_t>(a.measure_every) == 0u;
+        const bool do_swap = a.swap_every > 0 && (t + 1u) % static_cast<uint32_t>(a.swap_every) == 0u;
+        if (do_meas || do_swap) {
             int anti0 = 0, anti1 = 0, pos = 0;
             i = i_first;
             j = j_first;
@@ -109,9 +119,10 @@ __global__ void __launch_bounds__(512, CRBM_SWEEP_MIN_BLOCKS) k_sweep_canon(cons
             atomicAdd(&s_cnt[32 + lane], anti1);
             atomicAdd(&s_cnt[64 + lane], pos);
             __syncthreads();
-            if (warp == 0) measure_finalize(a, s_cnt, lane, chain, meas, acc);
-            ++meas;
+            if (warp == 0) post_sweep_warp0(a, s_cnt, s_sob, s_bos, lane, word, t, do_meas, do_swap, meas, acc);
+            if (do_meas) ++meas;
             __syncthreads();
+            if (do_swap) lc.lb = 4u * static_cast<uint32_t>(s_bos[lane]);
         }
         if (a.sq_every > 0 && (t + 1u) % static_cast<uint32_t>(a.sq_every) == 0u) {
             accumulate_correlations(a, s_v, s_seg, s_segmask, warp, nwarp, lane);
@@ -119,6 +130,7 @@ __global__ void __launch_bounds__(512, CRBM_SWEEP_MIN_BLOCKS) k_sweep_canon(cons
         }
     }
     for (int x = threadIdx.x; x < g.N; x += blockDim.x) gv[x] = s_v[x];
+    if (warp == 0 && a.swap_every > 0) a.sob[word * 32 + lane] = s_sob[lane];
     if (warp == 0 && measuring) {
 #pragma unroll
         for (int x = 0; x < kNSum; ++x) a.sums[static_cast<size_t>(chain) * kNSum + x] = acc[x];
@@ -129,7 +141,7 @@ __global__ void __launch_bounds__(512, CRBM_SWEEP_MIN_BLOCKS) k_sweep_canon(cons
 
 size_t smem_bytes_canon(const Geometry& g) {
     return sizeof(uint32_t) * (static_cast<size_t>(kCanonTab) + g.N + static_cast<size_t>(g.n_cells) * 10 +
-                               96 + 33 + 32);
+                               96 + 33 + 32 + 64);
 }
 
 cudaError_t launch_sweep_canon(const SweepArgs& a, int warps_per_cta, cudaStream_t st) {

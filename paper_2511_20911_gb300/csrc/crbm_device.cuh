@@ -105,36 +105,82 @@ __device__ __forceinline__ int site_of(const Geometry& g, int i, int j, int r, i
     return R * g.L + C;
 }
 
-// Measurement step shared by the sweep kernels.  s_cnt[0..95] holds, per
-// lane, the number of anti-aligned real bonds of each class and of +1 spins,
-// summed by every warp of the CTA.  Warp 0 turns them into (NJ, NJ', M),
-// appends the series entry and accumulates the eleven sums in registers.
-__device__ __forceinline__ void measure_finalize(const SweepArgs& a, int* s_cnt, int lane,
-                                                 uint32_t chain, int64_t meas, int64_t (&acc)[kNSum]) {
+// Post-sweep step of the SMEM kernels, run by warp 0 after every warp has
+// added its per-lane counts to s_cnt ([0..31] anti-aligned J filters, [32..63]
+// anti-aligned J' filters, [64..95] +1 spins; lane = replica slot).  Lane k
+// then stands for temperature rung k, held by slot s_sob[k] (the identity
+// without tempering):
+//  - measurement: rung k's (NJ, NJ', M) go to series/sums row 32 word + k;
+//  - replica exchange (round m): pairs (k, k+1) with k = m (mod 2) swap rungs
+//    when E_k <= E_{k+1}, else when a Philox word (k, m, word, swap tag) is
+//    below the host-built threshold of nearbyint(2^32 exp((b_k - b_{k+1}) dE / 16)).
+__device__ __forceinline__ void post_sweep_warp0(const SweepArgs& a, int* s_cnt, int* s_sob,
+                                                 int* s_bos, int lane, int word, uint32_t t,
+                                                 bool do_meas, bool do_swap, int64_t meas,
+                                                 int64_t (&acc)[kNSum]) {
     const Geometry& g = a.g;
-    const int64_t nJ = g.n_real_bonds[0] - 2 * s_cnt[lane];
-    const int64_t nP = g.n_real_bonds[1] - 2 * s_cnt[32 + lane];
-    const int64_t M = 2 * s_cnt[64 + lane] - g.N;
+    const int nJr = g.n_real_bonds[0] - 2 * s_cnt[lane];
+    const int nPr = g.n_real_bonds[1] - 2 * s_cnt[32 + lane];
+    const int Mr = 2 * s_cnt[64 + lane] - g.N;
     s_cnt[lane] = 0;
     s_cnt[32 + lane] = 0;
     s_cnt[64 + lane] = 0;
-    if (meas < a.series_len) {
-        int32_t* e = a.series + (static_cast<size_t>(meas) * a.n_chains_padded + chain) * 3;
-        e[0] = static_cast<int32_t>(nJ);
-        e[1] = static_cast<int32_t>(nP);
-        e[2] = static_cast<int32_t>(M);
+    const int k = lane;
+    const int slot = s_sob[k];
+    const int64_t nJ = __shfl_sync(0xffffffffu, nJr, slot);
+    const int64_t nP = __shfl_sync(0xffffffffu, nPr, slot);
+    const int64_t M = __shfl_sync(0xffffffffu, Mr, slot);
+    if (do_meas) {
+        const uint32_t row = static_cast<uint32_t>(word) * 32u + k;
+        if (meas < a.series_len) {
+            int32_t* e = a.series + (static_cast<size_t>(meas) * a.n_chains_padded + row) * 3;
+            e[0] = static_cast<int32_t>(nJ);
+            e[1] = static_cast<int32_t>(nP);
+            e[2] = static_cast<int32_t>(M);
+        }
+        acc[0] += 1;
+        acc[1] += nJ;
+        acc[2] += nP;
+        acc[3] += M;
+        acc[4] += M < 0 ? -M : M;
+        acc[5] += nJ * nJ;
+        acc[6] += nP * nP;
+        acc[7] += M * M;
+        acc[8] += nJ * nP;
+        acc[9] += nJ * M;
+        acc[10] += nP * M;
     }
-    acc[0] += 1;
-    acc[1] += nJ;
-    acc[2] += nP;
-    acc[3] += M;
-    acc[4] += M < 0 ? -M : M;
-    acc[5] += nJ * nJ;
-    acc[6] += nP * nP;
-    acc[7] += M * M;
-    acc[8] += nJ * nP;
-    acc[9] += nJ * M;
-    acc[10] += nP * M;
+    if (do_swap) {
+        const int32_t* q = a.wq + 3 * word;
+        const long long E = static_cast<long long>(q[0]) * nJ + static_cast<long long>(q[1]) * nP -
+                            static_cast<long long>(q[2]) * M;
+        const long long E1 = __shfl_down_sync(0xffffffffu, E, 1);
+        const uint32_t m = (t + 1u) / static_cast<uint32_t>(a.swap_every) - 1u;
+        bool accept = false;
+        if (k < 31 && (static_cast<uint32_t>(k) & 1u) == (m & 1u)) {
+            const long long D = E - E1;
+            if (D <= 0) {
+                accept = true;
+            } else {
+                const int idx = word * 32 + k;
+                if (D < a.swap_len[idx]) {
+                    const U4 u = philox(static_cast<uint32_t>(k), m, static_cast<uint32_t>(word), kTagSwap,
+                                        a.key0, a.key1);
+                    accept = u.x < a.swap_tab[a.swap_off[idx] + D];
+                }
+            }
+        }
+        const uint32_t am = __ballot_sync(0xffffffffu, accept);
+        const int up = __shfl_down_sync(0xffffffffu, slot, 1);
+        const int dn = __shfl_up_sync(0xffffffffu, slot, 1);
+        int ns = slot;
+        if ((am >> k) & 1u)
+            ns = up;
+        else if (k > 0 && ((am >> (k - 1)) & 1u))
+            ns = dn;
+        s_sob[k] = ns;
+        s_bos[ns] = k;
+    }
 }
 
 // Spin correlations of Sec. IV.B for the chains of each parameter-point

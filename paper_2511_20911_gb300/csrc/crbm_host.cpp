@@ -22,7 +22,7 @@ struct crbm_ctx {
     int layout = CRBM_LAYOUT_SMEM;
     int warps = 8;
     uint64_t seed = 0;
-    int measure_every = 0, series_len = 0, sq_every = 0;
+    int measure_every = 0, series_len = 0, sq_every = 0, swap_every = 0;
     int64_t sweeps = 0;     // global sweep counter
     int64_t meas = 0;       // measurements since the last reset
     int64_t sq_meas = 0;    // correlation samples since the last reset
@@ -82,6 +82,14 @@ void bond_weight(double beta, double J, double& a, int& s) {
 uint32_t accept_threshold(double y) {
     const double prob = 1.0 / (1.0 + std::exp(-y));
     const double r = std::nearbyint(std::ldexp(prob, 32));
+    if (r >= 4294967295.0) return 0xFFFFFFFFu;
+    if (r <= 0.0) return 0u;
+    return static_cast<uint32_t>(r);
+}
+
+// Replica-exchange acceptance exp(x), x <= 0, as a 32-bit threshold.
+uint32_t swap_threshold(double x) {
+    const double r = std::nearbyint(std::ldexp(std::exp(x), 32));
     if (r >= 4294967295.0) return 0xFFFFFFFFu;
     if (r <= 0.0) return 0u;
     return static_cast<uint32_t>(r);
@@ -192,7 +200,8 @@ int dalloc(crbm_ctx* ctx, T*& ptr, size_t count) {
 
 void free_device(DeviceState& d) {
     void* ptrs[] = {d.v, d.tab, d.ctab, d.sneg, d.inc, d.inc_off, d.sums, d.series, d.corr,
-                    d.seg, d.segmask, d.spins8, d.h, d.cnt, d.err};
+                    d.seg, d.segmask, d.spins8, d.h, d.cnt, d.err, d.sob, d.swap_tab, d.swap_off,
+                    d.swap_len, d.wq};
     for (void* p : ptrs)
         if (p) cudaFree(p);
     d = DeviceState{};
@@ -302,6 +311,67 @@ int crbm_create(crbm_ctx** out, const crbm_params* p) {
         }
         ctx->chain_param[c] = pp;
     }
+    // Replica-exchange ladders: 32-chain words of equal couplings and
+    // strictly increasing beta; per pair a threshold table over the energy
+    // difference dE = 1 .. len-1 (1/16 units), len = the first dE whose
+    // threshold is 0 (or past the largest possible |dE|).
+    ctx->swap_every = p->swap_every;
+    std::vector<uint32_t> swap_tab;
+    std::vector<int32_t> swap_off, swap_len, wq;
+    if (p->swap_every < 0) {
+        delete ctx;
+        return fail(nullptr, CRBM_EINVAL, "swap_every must be >= 0");
+    }
+    if (p->swap_every > 0) {
+        if (p->n_chains % 32 != 0 || ctx->layout != CRBM_LAYOUT_SMEM) {
+            delete ctx;
+            return fail(nullptr, p->n_chains % 32 ? CRBM_EINVAL : CRBM_EUNSUPPORTED,
+                        "replica exchange needs n_chains % 32 == 0 and the SMEM layout");
+        }
+        const int nwl = p->n_chains / 32;
+        const int64_t e_max = 2 * (2047LL * g.n_real_bonds[0] + 2047LL * g.n_real_bonds[1] + 2047LL * g.N);
+        swap_off.assign(32 * static_cast<size_t>(nwl), 0);
+        swap_len.assign(32 * static_cast<size_t>(nwl), 0);
+        wq.assign(3 * static_cast<size_t>(nwl), 0);
+        for (int w = 0; w < nwl; ++w) {
+            const int32_t* cpw = &ctx->chain_param[32 * w];
+            for (int k = 0; k < 32; ++k) {
+                const int pk = cpw[k], p0 = cpw[0];
+                if (ctx->q[0][pk] != ctx->q[0][p0] || ctx->q[1][pk] != ctx->q[1][p0] ||
+                    ctx->q[2][pk] != ctx->q[2][p0] || (k > 0 && !(ctx->beta[pk] > ctx->beta[cpw[k - 1]]))) {
+                    delete ctx;
+                    return fail(nullptr, CRBM_EINVAL,
+                                "ladder " + std::to_string(w) +
+                                    ": rungs need equal J, J', h and strictly increasing beta");
+                }
+            }
+            wq[3 * w] = ctx->q[0][cpw[0]];
+            wq[3 * w + 1] = ctx->q[1][cpw[0]];
+            wq[3 * w + 2] = ctx->q[2][cpw[0]];
+            const int64_t emax_w = 2 * (std::abs(static_cast<int64_t>(wq[3 * w])) * g.n_real_bonds[0] +
+                                        std::abs(static_cast<int64_t>(wq[3 * w + 1])) * g.n_real_bonds[1] +
+                                        std::abs(static_cast<int64_t>(wq[3 * w + 2])) * g.N);
+            (void)e_max;
+            for (int k = 0; k < 31; ++k) {
+                const double db = ctx->beta[cpw[k]] - ctx->beta[cpw[k + 1]];
+                swap_off[32 * w + k] = static_cast<int32_t>(swap_tab.size());
+                int64_t len = 1;
+                swap_tab.push_back(0u);  // dE = 0 is accepted before any lookup
+                while (len <= emax_w) {
+                    const uint32_t thr = swap_threshold(db * static_cast<double>(len) / 16.0);
+                    if (thr == 0u) break;
+                    swap_tab.push_back(thr);
+                    ++len;
+                    if (swap_tab.size() > (1u << 26)) {
+                        delete ctx;
+                        return fail(nullptr, CRBM_EUNSUPPORTED,
+                                    "adjacent rungs too close in beta for the swap tables");
+                    }
+                }
+                swap_len[32 * w + k] = static_cast<int32_t>(len);
+            }
+        }
+    }
     // Per-point tables and signs, then lane-expanded per word.
     ctx->tables.resize(static_cast<size_t>(p->n_params) * g.nTab);
     std::vector<int> sgn(2 * static_cast<size_t>(p->n_params));
@@ -380,6 +450,9 @@ int crbm_create(crbm_ctx** out, const crbm_params* p) {
         (rc = dalloc(ctx, d.corr, p->sq_every > 0 ? static_cast<size_t>(p->n_params) * N : 1)) ||
         (rc = dalloc(ctx, d.seg, seg.size())) || (rc = dalloc(ctx, d.segmask, segmask.size())) ||
         (rc = dalloc(ctx, d.spins8, static_cast<size_t>(npad) * N)) || (rc = dalloc(ctx, d.err, 4)) ||
+        (rc = dalloc(ctx, d.sob, static_cast<size_t>(npad))) ||
+        (rc = dalloc(ctx, d.swap_tab, swap_tab.size())) || (rc = dalloc(ctx, d.swap_off, swap_off.size())) ||
+        (rc = dalloc(ctx, d.swap_len, swap_len.size())) || (rc = dalloc(ctx, d.wq, wq.size())) ||
         (g.vil && (rc = dalloc(ctx, d.h, static_cast<size_t>(nw) * g.n_cells * 10))) ||
         (g.vil && (rc = dalloc(ctx, d.cnt, static_cast<size_t>(npad) * 3)))) {
         g_create_error = ctx->err;
@@ -399,6 +472,13 @@ int crbm_create(crbm_ctx** out, const crbm_params* p) {
     h2d(d.inc_off, inc_off.data(), inc_off.size() * 4);
     h2d(d.seg, seg.data(), seg.size() * 4);
     h2d(d.segmask, segmask.data(), segmask.size() * 4);
+    h2d(d.swap_tab, swap_tab.data(), swap_tab.size() * 4);
+    h2d(d.swap_off, swap_off.data(), swap_off.size() * 4);
+    h2d(d.swap_len, swap_len.data(), swap_len.size() * 4);
+    h2d(d.wq, wq.data(), wq.size() * 4);
+    std::vector<int32_t> ident(static_cast<size_t>(npad));
+    for (int c = 0; c < npad; ++c) ident[c] = c & 31;
+    h2d(d.sob, ident.data(), ident.size() * 4);
     if (e == cudaSuccess) e = cudaMemsetAsync(d.sums, 0, static_cast<size_t>(npad) * kNSum * 8, st);
     if (e == cudaSuccess && p->series_len)
         e = cudaMemsetAsync(d.series, 0, static_cast<size_t>(p->series_len) * npad * 12, st);
@@ -455,6 +535,12 @@ int crbm_sweep(crbm_ctx* ctx, int64_t n_sweeps) {
         a.series = ctx->d.series;
         a.h = ctx->d.h;
         a.cnt = ctx->d.cnt;
+        a.sob = ctx->d.sob;
+        a.swap_tab = ctx->d.swap_tab;
+        a.swap_off = ctx->d.swap_off;
+        a.swap_len = ctx->d.swap_len;
+        a.wq = ctx->d.wq;
+        a.swap_every = ctx->swap_every;
         a.corr = ctx->d.corr;
         a.seg = ctx->d.seg;
         a.segmask = ctx->d.segmask;
@@ -598,6 +684,15 @@ int crbm_set_spins(crbm_ctx* ctx, const int8_t* in, size_t n_in) {
     return e == cudaSuccess ? CRBM_OK : cuda_fail(ctx, e, "crbm_set_spins");
 }
 
+int crbm_get_permutation(crbm_ctx* ctx, int32_t* out, size_t n_out) {
+    if (!ctx || !out) return CRBM_EINVAL;
+    if (n_out < static_cast<size_t>(ctx->n_chains)) return fail(ctx, CRBM_EINVAL, "output buffer too small");
+    cudaError_t e = cudaMemcpyAsync(out, ctx->d.sob, static_cast<size_t>(ctx->n_chains) * 4,
+                                    cudaMemcpyDeviceToHost, ctx->stream);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(ctx->stream);
+    return e == cudaSuccess ? CRBM_OK : cuda_fail(ctx, e, "crbm_get_permutation");
+}
+
 int crbm_get_tables(crbm_ctx* ctx, uint32_t* out, size_t n_out, int32_t* dims) {
     if (!ctx) return CRBM_EINVAL;
     if (dims) {
@@ -619,7 +714,8 @@ int crbm_save(crbm_ctx* ctx, void* buf, size_t* n) {
     const size_t b_v = ctx->n_words * N * 4, b_s = npad * kNSum * 8,
                  b_t = static_cast<size_t>(ctx->series_len) * npad * 12,
                  b_c = ctx->sq_every ? static_cast<size_t>(ctx->n_params) * N * 8 : 0;
-    const size_t total = 16 * 8 + b_v + b_s + b_t + b_c;
+    const size_t b_p = npad * 4;
+    const size_t total = 16 * 8 + b_v + b_s + b_t + b_c + b_p;
     if (!buf) {
         *n = total;
         return CRBM_OK;
@@ -628,7 +724,7 @@ int crbm_save(crbm_ctx* ctx, void* buf, size_t* n) {
     int64_t hdr[16] = {0x4d425243 /* "CRBM" */, 1, ctx->g.L, ctx->n_chains, ctx->n_params,
                        static_cast<int64_t>(ctx->seed), ctx->sweeps, ctx->meas, ctx->sq_meas,
                        ctx->series_len, ctx->sq_every, ctx->measure_every, ctx->g.nb,
-                       ctx->g.periodic, 0, 0};
+                       ctx->g.periodic, ctx->swap_every, 0};
     char* p = static_cast<char*>(buf);
     std::memcpy(p, hdr, sizeof(hdr));
     cudaError_t e = cudaMemcpyAsync(p + 128, ctx->d.v, b_v, cudaMemcpyDeviceToHost, ctx->stream);
@@ -637,6 +733,8 @@ int crbm_save(crbm_ctx* ctx, void* buf, size_t* n) {
         e = cudaMemcpyAsync(p + 128 + b_v + b_s, ctx->d.series, b_t, cudaMemcpyDeviceToHost, ctx->stream);
     if (e == cudaSuccess && b_c)
         e = cudaMemcpyAsync(p + 128 + b_v + b_s + b_t, ctx->d.corr, b_c, cudaMemcpyDeviceToHost, ctx->stream);
+    if (e == cudaSuccess)
+        e = cudaMemcpyAsync(p + 128 + b_v + b_s + b_t + b_c, ctx->d.sob, b_p, cudaMemcpyDeviceToHost, ctx->stream);
     if (e == cudaSuccess) e = cudaStreamSynchronize(ctx->stream);
     if (e != cudaSuccess) return cuda_fail(ctx, e, "crbm_save");
     *n = total;
@@ -653,7 +751,7 @@ int crbm_load(crbm_ctx* ctx, const void* buf, size_t n) {
     if (hdr[0] != 0x4d425243 || hdr[1] != 1 || hdr[2] != ctx->g.L || hdr[3] != ctx->n_chains ||
         hdr[4] != ctx->n_params || hdr[5] != static_cast<int64_t>(ctx->seed) ||
         hdr[9] != ctx->series_len || hdr[10] != ctx->sq_every || hdr[11] != ctx->measure_every ||
-        hdr[12] != ctx->g.nb || hdr[13] != ctx->g.periodic)
+        hdr[12] != ctx->g.nb || hdr[13] != ctx->g.periodic || hdr[14] != ctx->swap_every)
         return fail(ctx, CRBM_EINVAL, "checkpoint does not match this context");
     const size_t npad = static_cast<size_t>(ctx->n_words) * 32, N = ctx->g.N;
     const size_t b_v = ctx->n_words * N * 4, b_s = npad * kNSum * 8,
@@ -666,6 +764,9 @@ int crbm_load(crbm_ctx* ctx, const void* buf, size_t n) {
         e = cudaMemcpyAsync(ctx->d.series, p + 128 + b_v + b_s, b_t, cudaMemcpyHostToDevice, ctx->stream);
     if (e == cudaSuccess && b_c)
         e = cudaMemcpyAsync(ctx->d.corr, p + 128 + b_v + b_s + b_t, b_c, cudaMemcpyHostToDevice, ctx->stream);
+    if (e == cudaSuccess)
+        e = cudaMemcpyAsync(ctx->d.sob, p + 128 + b_v + b_s + b_t + b_c, npad * 4, cudaMemcpyHostToDevice,
+                            ctx->stream);
     if (e == cudaSuccess) e = cudaStreamSynchronize(ctx->stream);
     if (e != cudaSuccess) return cuda_fail(ctx, e, "crbm_load");
     ctx->sweeps = hdr[6];

@@ -65,6 +65,11 @@ struct DeviceState {
     int32_t* seg = nullptr;       // [n_words][33]: n_seg, then (param << 8 | first lane) ...
     uint32_t* segmask = nullptr;  // [n_words][32] lane mask of each segment
     int8_t* spins8 = nullptr;     // [n_words * 32][N] staging for get/set spins
+    int32_t* sob = nullptr;       // tempering: [n_words][32] replica slot holding each rung
+    uint32_t* swap_tab = nullptr; // tempering: swap thresholds, per (word, pair) at swap_off
+    int32_t* swap_off = nullptr;  // [n_words][32]
+    int32_t* swap_len = nullptr;  // [n_words][32]: thresholds for dE = 1 .. len-1 (0 beyond)
+    int32_t* wq = nullptr;        // [n_words][3] Q.4 couplings (J, J', h) of each word
     uint32_t* h = nullptr;        // streamed layout: [n_words][n_cells][10] hidden words
     int* cnt = nullptr;           // streamed layout: [n_words * 32][3] measurement counts
     int* err = nullptr;           // device error word
@@ -82,6 +87,12 @@ struct SweepArgs {
     int32_t* series;
     uint32_t* h;
     int* cnt;
+    int32_t* sob;
+    const uint32_t* swap_tab;
+    const int32_t* swap_off;
+    const int32_t* swap_len;
+    const int32_t* wq;
+    int swap_every;       // 0 = no replica exchange
     int64_t* corr;
     const int32_t* seg;
     const uint32_t* segmask;

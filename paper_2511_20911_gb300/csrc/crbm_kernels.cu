@@ -22,7 +22,7 @@ using namespace dev;
 __device__ __forceinline__ void hidden_cell_generic(const Geometry& g, const uint32_t* s_v,
                                                     uint32_t* s_h, const uint32_t* s_tab,
                                                     int cell, int i, int j, uint32_t t,
-                                                    uint32_t chain, int lane, uint32_t k0,
+                                                    uint32_t chain, int lane, int col, uint32_t k0,
                                                     uint32_t k1, const uint32_t (&sn)[2]) {
     U4 q[4];
 #pragma unroll
@@ -37,7 +37,7 @@ __device__ __forceinline__ void hidden_cell_generic(const Geometry& g, const uin
             int m = 2;
             if (s1 >= 0) m += 2 * static_cast<int>(bit_of(s_v[s1], lane)) - 1;
             if (s2 >= 0) m += 2 * static_cast<int>(bit_of(s_v[s2], lane) ^ sn[cls]) - 1;
-            const uint32_t thr = s_tab[(cls * 5 + m) * 32 + lane];
+            const uint32_t thr = s_tab[(cls * 5 + m) * 32 + col];
             const uint32_t hw = __ballot_sync(0xffffffffu, pick(q[k >> 2], k & 3) < thr);
             if (lane == 0) s_h[cell * g.nb + k] = hw;
         }
@@ -52,7 +52,7 @@ __device__ __forceinline__ void visible_cell_generic(const Geometry& g, uint32_t
                                                      const uint32_t* __restrict__ inc,
                                                      const int32_t* __restrict__ inc_off,
                                                      int cell, int i, int j, uint32_t t,
-                                                     uint32_t chain, int lane, uint32_t k0,
+                                                     uint32_t chain, int lane, int col, uint32_t k0,
                                                      uint32_t k1, const uint32_t (&sn)[2]) {
     const U4 q = philox(cell, t, chain, kTagVis, k0, k1);
     const int nP = 2 * g.DJp + 1;
@@ -69,7 +69,7 @@ __device__ __forceinline__ void visible_cell_generic(const Geometry& g, uint32_t
                 const uint32_t b = bit_of(s_h[ent & 0x0FFFFFFFu], lane) ^ ((ent >> 31) ? sn[cls] : 0u);
                 n[cls] += 2 * static_cast<int>(b) - 1;
             }
-            const uint32_t thr = s_tab[(10 + (n[0] + g.DJ) * nP + (n[1] + g.DJp)) * 32 + lane];
+            const uint32_t thr = s_tab[(10 + (n[0] + g.DJ) * nP + (n[1] + g.DJp)) * 32 + col];
             const uint32_t vw = __ballot_sync(0xffffffffu, pick(q, w) < thr);
             if (lane == 0) s_v[s] = vw;
         }
@@ -114,6 +114,8 @@ __global__ void __launch_bounds__(512, 1) k_sweep_generic(const SweepArgs a) {
     int* s_cnt = reinterpret_cast<int*>(s_h + g.n_cells * g.nb);  // [3][32]
     int* s_seg = s_cnt + 96;                                       // [33]
     uint32_t* s_segmask = reinterpret_cast<uint32_t*>(s_seg + 33); // [32]
+    int* s_sob = reinterpret_cast<int*>(s_segmask + 32);          // [32] slot of each rung
+    int* s_bos = s_sob + 32;                                        // [32] rung of each slot
 
     const uint32_t* gtab = a.tab + static_cast<size_t>(word) * g.nTab * 32;
     for (int x = threadIdx.x; x < g.nTab * 32; x += blockDim.x) s_tab[x] = gtab[x];
@@ -126,7 +128,13 @@ __global__ void __launch_bounds__(512, 1) k_sweep_generic(const SweepArgs a) {
     }
     const uint32_t sn[2] = {bit_of(a.sneg[2 * word], lane), bit_of(a.sneg[2 * word + 1], lane)};
     const uint32_t chain = static_cast<uint32_t>(word) * 32u + lane;
+    if (warp == 0) {  // replica permutation (identity without tempering)
+        const int sob = a.swap_every > 0 ? a.sob[word * 32 + lane] : lane;
+        s_sob[lane] = sob;
+        s_bos[sob] = lane;
+    }
     __syncthreads();
+    int col = s_bos[lane];  // threshold column: the rung this slot holds
     int64_t acc[kNSum];
     const bool measuring = a.measure_every > 0;
     if (warp == 0 && measuring) {
@@ -141,7 +149,7 @@ __global__ void __launch_bounds__(512, 1) k_sweep_generic(const SweepArgs a) {
         const uint32_t t = a.t0 + static_cast<uint32_t>(it);
         int i = i_first, j = j_first;
         for (int cell = warp; cell < g.n_cells; cell += nwarp) {
-            hidden_cell_generic(g, s_v, s_h, s_tab, cell, i, j, t, chain, lane, a.key0, a.key1, sn);
+            hidden_cell_generic(g, s_v, s_h, s_tab, cell, i, j, t, chain, lane, col, a.key0, a.key1, sn);
             i += di;
             j += dj;
             if (j >= g.W) {
@@ -153,7 +161,7 @@ __global__ void __launch_bounds__(512, 1) k_sweep_generic(const SweepArgs a) {
         i = i_first;
         j = j_first;
         for (int cell = warp; cell < g.n_cells; cell += nwarp) {
-            visible_cell_generic(g, s_v, s_h, s_tab, a.inc, a.inc_off, cell, i, j, t, chain, lane,
+            visible_cell_generic(g, s_v, s_h, s_tab, a.inc, a.inc_off, cell, i, j, t, chain, lane, col,
                                  a.key0, a.key1, sn);
             i += di;
             j += dj;
@@ -163,7 +171,9 @@ __global__ void __launch_bounds__(512, 1) k_sweep_generic(const SweepArgs a) {
             }
         }
         __syncthreads();
-        if (measuring && (t + 1u) % static_cast<uint32_t>(a.measure_every) == 0u) {
+        const bool do_meas = measuring && (t + 1u) % static_cast<uint32_t>(a.measure_every) == 0u;
+        const bool do_swap = a.swap_every > 0 && (t + 1u) % static_cast<uint32_t>(a.swap_every) == 0u;
+        if (do_meas || do_swap) {
             int anti0 = 0, anti1 = 0, pos = 0;
             i = i_first;
             j = j_first;
@@ -180,9 +190,10 @@ __global__ void __launch_bounds__(512, 1) k_sweep_generic(const SweepArgs a) {
             atomicAdd(&s_cnt[32 + lane], anti1);
             atomicAdd(&s_cnt[64 + lane], pos);
             __syncthreads();
-            if (warp == 0) measure_finalize(a, s_cnt, lane, chain, meas, acc);
-            ++meas;
+            if (warp == 0) post_sweep_warp0(a, s_cnt, s_sob, s_bos, lane, word, t, do_meas, do_swap, meas, acc);
+            if (do_meas) ++meas;
             __syncthreads();
+            if (do_swap) col = s_bos[lane];
         }
         if (a.sq_every > 0 && (t + 1u) % static_cast<uint32_t>(a.sq_every) == 0u) {
             accumulate_correlations(a, s_v, s_seg, s_segmask, warp, nwarp, lane);
@@ -190,6 +201,7 @@ __global__ void __launch_bounds__(512, 1) k_sweep_generic(const SweepArgs a) {
         }
     }
     for (int x = threadIdx.x; x < g.N; x += blockDim.x) gv[x] = s_v[x];
+    if (warp == 0 && a.swap_every > 0) a.sob[word * 32 + lane] = s_sob[lane];
     if (warp == 0 && measuring) {
 #pragma unroll
         for (int x = 0; x < kNSum; ++x) a.sums[static_cast<size_t>(chain) * kNSum + x] = acc[x];
@@ -258,7 +270,7 @@ cudaError_t launch_philox(const uint32_t* in, uint32_t* out, int n, cudaStream_t
 
 size_t smem_bytes_generic(const Geometry& g) {
     return sizeof(uint32_t) * (static_cast<size_t>(g.nTab) * 32 + g.N +
-                               static_cast<size_t>(g.n_cells) * g.nb + 96 + 33 + 32);
+                               static_cast<size_t>(g.n_cells) * g.nb + 96 + 33 + 32 + 64);
 }
 
 cudaError_t launch_init(const Geometry& g, uint32_t* v, int n_words, uint32_t key0, uint32_t key1,

@@ -47,7 +47,7 @@ def parse():
     ap.add_argument("--steps", type=int, default=10)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
-    ap.add_argument("--workload", default="grid", choices=["grid", "stream"])
+    ap.add_argument("--workload", default="grid", choices=["grid", "stream", "batch"])
     ap.add_argument("--sweeps-per-step", type=int, default=None)
     ap.add_argument("--measure-every", type=int, default=10)
     ap.add_argument("--cpu-seconds", type=float, default=8.0)
@@ -115,7 +115,7 @@ def workload_config(name, rank):
     return w
 
 
-DEFAULT_SWEEPS = {"grid": 2000, "stream": 20}
+DEFAULT_SWEEPS = {"grid": 2000, "stream": 20, "batch": 500}
 
 
 def cpu_baseline(w, seconds):
@@ -186,6 +186,78 @@ def config_dict(w, args):
             "parallelism": f"replicas x{args.gpus}"}
 
 
+def run_batch(args, rank, ws):
+    """Mixed L in {6,9,12,18,24,48} x 8 tempering ladders of 32 betas, all
+    members advanced by one graph-captured launch per step."""
+    import torch
+    import paper_2511_20911_gb300 as crbm
+    from paper_2511_20911_gb300 import workloads
+    specs = workloads.tempering_batch_workload()
+    S, K, W = args.sweeps_per_step, args.steps, args.warmup
+    members = []
+    for sp in specs:
+        sp = dict(sp, seed=sp["seed"] + 1000003 * rank, measure_every=args.measure_every)
+        m = crbm.Sampler(**sp)
+        m.autotune(50)
+        members.append(m)
+    batch = crbm.Batch(members)
+    stream = torch.cuda.current_stream()
+    flush = torch.empty(256 * 1024 * 1024, dtype=torch.uint8, device="cuda")
+    for _ in range(W):
+        batch.sweep(S)
+    torch.cuda.synchronize()
+    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(K)]
+    l0 = sum(m.launch_count for m in members)
+    if ws > 1:
+        torch.distributed.barrier()
+    with ClockSampler(torch.cuda.current_device()) as clk:
+        for k in range(K):
+            flush.fill_(k & 0xFF)
+            ev[k][0].record(stream)
+            batch.sweep(S)
+            ev[k][1].record(stream)
+        torch.cuda.synchronize()
+    t_total = sum(a.elapsed_time(b) for a, b in ev) / 1e3
+    if ws > 1:
+        t = torch.tensor([t_total], device="cuda")
+        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
+        t_total = float(t.item())
+    per_sweep = sum(sp["n_chains"] * sp["L"] ** 2 for sp in specs)
+    value = per_sweep * S * K * ws / t_total
+    calls = sum(4 * ((sp["L"] + 1) // 2) ** 2 * sp["n_chains"] for sp in specs) * S
+    achieved = MUL_OPS_PER_CALL * calls / (t_total / K) / 1e12
+    peak = SM_COUNT * IMUL_LANES_PER_SM_CLK * SM_MAX_MHZ * 1e6 / 1e12
+    # end to end with host buffers: spins in, one batched step, observables out
+    host = [m.get_spins() for m in members]
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    for m, hsp in zip(members, host):
+        m.set_spins(hsp)
+    batch.sweep(S)
+    obs = [m.observables() for m in members]
+    e2e_t = time.perf_counter() - t0
+    out = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws, "steps": K, "warmup": W,
+           "ms_per_step": t_total / K * 1e3, "higher_is_better": True, "scaling": "weak",
+           "vs_baseline": None, "dtype": "u32", "data": "synthetic",
+           "config": {"workload": "mixed L in {6,9,12,18,24,48} x 8 replica-exchange ladders of 32 "
+                                  "geometric beta in [0.2,10], J'/J=1.5, h=1, swaps every 10 sweeps, "
+                                  "one graph-captured launch per step",
+                      "n_chains": sum(sp["n_chains"] for sp in specs), "sweeps_per_step": S,
+                      "threads_per_cta": batch.threads, "warps_tuned": [m.warps for m in members],
+                      "l2": "flushed between steps (256 MiB write outside the step events)",
+                      "parallelism": f"replicas x{ws}"},
+           "sweeps_per_s": S * K / t_total,
+           "clocks": clk.summary(),
+           "e2e": {"value": per_sweep * S / e2e_t, "unit": UNIT,
+                   "h2d_bytes_per_step": int(sum(h.nbytes for h in host)),
+                   "d2h_bytes_per_step": int(sum(o.nbytes for o in obs))},
+           "gpu_launches": int(sum(m.launch_count for m in members) - l0),
+           "roofline": {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "Tops/s",
+                        "frac": achieved / peak, "traffic": None}}
+    if rank == 0:
+        print(json.dumps(out))
+
+
 def main():
     args = parse()
     if args.sweeps_per_step is None:
@@ -193,6 +265,9 @@ def main():
     rank, ws = dist_setup(args)
     if args.impl == "reference":
         run_reference(args, rank, ws)
+        return
+    if args.workload == "batch":
+        run_batch(args, rank, ws)
         return
     import torch
     import paper_2511_20911_gb300 as crbm

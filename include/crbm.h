@@ -162,6 +162,19 @@ int crbm_get_permutation(crbm_ctx* ctx, int32_t* out, size_t n_out);
 /* Which layout the context runs (CRBM_LAYOUT_SMEM or CRBM_LAYOUT_STREAM). */
 int crbm_layout(const crbm_ctx* ctx);
 
+/* Autotuner: time the CTA shapes of the SMEM sweep (2..16 warps per packed
+ * word) for probe_sweeps sweeps each on scratch copies of the context's
+ * spins (its chains, counters and observables are untouched), keep the
+ * fastest for this context and append it to the cache file
+ * ($CRBM_AUTOTUNE_CACHE, default $HOME/.cache/crbm_autotune.txt), which
+ * crbm_create consults for contexts of the same shape on the same GPU model.
+ * best_warps may be NULL.  Synchronises the stream.  Errors: CRBM_EINVAL,
+ * CRBM_EUNSUPPORTED (streamed layout), CRBM_ECUDA. */
+int crbm_autotune(crbm_ctx* ctx, int64_t probe_sweeps, int32_t* best_warps);
+
+/* Warps per CTA the context's SMEM sweep launches with. */
+int crbm_warps(const crbm_ctx* ctx);
+
 /* Kernel launches issued by this context since creation. */
 int64_t crbm_launch_count(const crbm_ctx* ctx);
 
@@ -176,6 +189,27 @@ int crbm_load(crbm_ctx* ctx, const void* buf, size_t n);
  * current device's legacy stream.  For verification of the generator that
  * keys every draw; synchronous.  Errors: CRBM_EINVAL, CRBM_ENOMEM, CRBM_ECUDA. */
 int crbm_philox(const uint32_t* in, uint32_t* out, size_t n);
+
+/* Batched sweeps: several SMEM-layout contexts -- mixed lattice sizes,
+ * filter lists and tempering ladders -- advanced together by ONE kernel
+ * launch (one CTA per packed word of every member, heaviest lattices first)
+ * plus a one-thread clock update, captured once in a CUDA graph and replayed
+ * on the members' common stream.  Members keep their own state, counters and
+ * getters; each batched call advances every member by n_sweeps sweeps,
+ * bit-identical to calling crbm_sweep on each.  The CTA shape is the largest
+ * warps count of the members (see crbm_autotune). */
+#define CRBM_BATCH_MAX 16
+typedef struct crbm_batch crbm_batch;
+/* Errors: CRBM_EINVAL (0 or more than CRBM_BATCH_MAX members, a repeated
+ * member, a streamed-layout member, members on different devices or
+ * streams), CRBM_ENOMEM, CRBM_ECUDA.  The members must outlive the batch. */
+int crbm_batch_create(crbm_batch** out, crbm_ctx* const* ctxs, int32_t n_ctx);
+/* Asynchronous on the members' stream.  n_sweeps in 0..2^20. */
+int crbm_batch_sweep(crbm_batch* batch, int64_t n_sweeps);
+int crbm_batch_threads(const crbm_batch* batch);
+/* Message for the last failed call on batch (or crbm_batch_create if NULL). */
+const char* crbm_batch_last_error(const crbm_batch* batch);
+void crbm_batch_destroy(crbm_batch* batch);
 
 /* Size of the fixed device scratch array of crbm_sweep_stream_noalloc. */
 #define CRBM_NOALLOC_SCRATCH_BYTES (32u << 20)

@@ -30,7 +30,8 @@ ABI_FUNCTIONS = (
     "crbm_create", "crbm_destroy", "crbm_sweep", "crbm_sweep_count", "crbm_observables",
     "crbm_series", "crbm_correlations", "crbm_structure_factor", "crbm_reset_observables",
     "crbm_get_spins", "crbm_set_spins", "crbm_get_tables", "crbm_get_permutation", "crbm_layout",
-    "crbm_launch_count",
+    "crbm_launch_count", "crbm_autotune", "crbm_warps", "crbm_batch_create", "crbm_batch_sweep",
+    "crbm_batch_threads", "crbm_batch_last_error", "crbm_batch_destroy",
     "crbm_save", "crbm_load", "crbm_philox", "crbm_sweep_stream_noalloc", "crbm_last_error",
 )
 
@@ -87,6 +88,13 @@ def load_library(path: str | None = None):
         "crbm_get_tables": (c.c_int, [vp, c.POINTER(c.c_uint32), c.c_size_t, c.POINTER(c.c_int32)]),
         "crbm_get_permutation": (c.c_int, [vp, c.POINTER(c.c_int32), c.c_size_t]),
         "crbm_layout": (c.c_int, [vp]),
+        "crbm_autotune": (c.c_int, [vp, c.c_int64, c.POINTER(c.c_int32)]),
+        "crbm_warps": (c.c_int, [vp]),
+        "crbm_batch_create": (c.c_int, [c.POINTER(vp), c.POINTER(vp), c.c_int32]),
+        "crbm_batch_sweep": (c.c_int, [vp, c.c_int64]),
+        "crbm_batch_threads": (c.c_int, [vp]),
+        "crbm_batch_last_error": (c.c_char_p, [vp]),
+        "crbm_batch_destroy": (None, [vp]),
         "crbm_launch_count": (c.c_int64, [vp]),
         "crbm_save": (c.c_int, [vp, vp, c.POINTER(c.c_size_t)]),
         "crbm_load": (c.c_int, [vp, vp, c.c_size_t]),
@@ -227,6 +235,16 @@ class Sampler:
         a = np.ascontiguousarray(spins, np.int8)
         _check(self._lib.crbm_set_spins(self._ctx, _ptr(a, ctypes.c_int8), a.size), self._ctx)
 
+    def autotune(self, probe_sweeps=200):
+        """Time the SMEM sweep's CTA shapes on scratch copies; returns the warps kept."""
+        best = ctypes.c_int32(0)
+        _check(self._lib.crbm_autotune(self._ctx, int(probe_sweeps), ctypes.byref(best)), self._ctx)
+        return best.value
+
+    @property
+    def warps(self):
+        return int(self._lib.crbm_warps(self._ctx))
+
     def permutation(self):
         """[n_chains] int32: entry 32 l + k = slot of ladder l holding rung k."""
         out = np.zeros(self.n_chains, np.int32)
@@ -254,6 +272,41 @@ class Sampler:
     def load(self, buf):
         b = np.ascontiguousarray(buf, np.uint8)
         _check(self._lib.crbm_load(self._ctx, b.ctypes.data_as(ctypes.c_void_p), b.size), self._ctx)
+
+
+class Batch:
+    """Several Samplers advanced by one graph-captured kernel launch
+    (crbm_batch_*).  Keep the members alive while the batch exists."""
+
+    def __init__(self, samplers):
+        lib = load_library()
+        self.members = list(samplers)
+        arr = (ctypes.c_void_p * len(self.members))(*[s._ctx.value for s in self.members])
+        h = ctypes.c_void_p()
+        rc = lib.crbm_batch_create(ctypes.byref(h), arr, len(self.members))
+        if rc != CRBM_OK:
+            raise CrbmError(rc, (lib.crbm_batch_last_error(None) or b"").decode())
+        self._b, self._lib = h, lib
+
+    def sweep(self, n_sweeps):
+        rc = self._lib.crbm_batch_sweep(self._b, int(n_sweeps))
+        if rc != CRBM_OK:
+            raise CrbmError(rc, (self._lib.crbm_batch_last_error(self._b) or b"").decode())
+
+    @property
+    def threads(self):
+        return int(self._lib.crbm_batch_threads(self._b))
+
+    def close(self):
+        if getattr(self, "_b", None):
+            self._lib.crbm_batch_destroy(self._b)
+            self._b = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
 
 
 def crbm_philox(inputs):

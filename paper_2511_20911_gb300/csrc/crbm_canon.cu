@@ -2,7 +2,7 @@
 // chains) holding the whole even, periodic lattice, its hidden layer and the
 // lane-expanded tables in shared memory, all n_sweeps sweeps on device.  The
 // per-cell cores are in crbm_canon_core.cuh.
-#include "crbm_canon_core.cuh"
+#include "crbm_canon_body.cuh"
 
 #ifndef CRBM_SWEEP_MIN_BLOCKS
 #define CRBM_SWEEP_MIN_BLOCKS 2
@@ -15,126 +15,7 @@ using namespace dev;
 using namespace canon;
 
 __global__ void __launch_bounds__(512, CRBM_SWEEP_MIN_BLOCKS) k_sweep_canon(const SweepArgs a) {
-    extern __shared__ __align__(16) uint32_t smem[];
-    const Geometry& g = a.g;
-    const int L = g.L, W = g.W;
-    const int word = blockIdx.x;
-    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nwarp = blockDim.x >> 5;
-    uint32_t* s_th = smem;                      // [2][4][32]
-    uint32_t* s_tv = smem + kCanonTh;           // [4][32][32]
-    uint32_t* s_v = smem + kCanonTab;           // [N]
-    uint32_t* s_h = s_v + g.N;                  // [n_cells][10]
-    int* s_cnt = reinterpret_cast<int*>(s_h + g.n_cells * 10);   // [3][32]
-    int* s_seg = s_cnt + 96;                                      // [33]
-    uint32_t* s_segmask = reinterpret_cast<uint32_t*>(s_seg + 33); // [32]
-    int* s_sob = reinterpret_cast<int*>(s_segmask + 32);          // [32] slot of each rung
-    int* s_bos = s_sob + 32;                                        // [32] rung of each slot
-
-    const uint4* gt = reinterpret_cast<const uint4*>(a.ctab + static_cast<size_t>(word) * kCanonTab);
-    for (int x = threadIdx.x; x < kCanonTab / 4; x += blockDim.x) reinterpret_cast<uint4*>(smem)[x] = gt[x];
-    uint32_t* gv = a.v + static_cast<size_t>(word) * g.N;
-    for (int x = threadIdx.x; x < g.N; x += blockDim.x) s_v[x] = gv[x];
-    for (int x = threadIdx.x; x < 96; x += blockDim.x) s_cnt[x] = 0;
-    if (a.sq_every > 0) {
-        for (int x = threadIdx.x; x < 33; x += blockDim.x) s_seg[x] = a.seg[word * 33 + x];
-        for (int x = threadIdx.x; x < 32; x += blockDim.x) s_segmask[x] = a.segmask[word * 32 + x];
-    }
-    const uint32_t chain = static_cast<uint32_t>(word) * 32u + lane;
-    LaneConst lc;
-    lc.lm = 1u << lane;
-    lc.lb = 4u * lane;
-#pragma unroll
-    for (int s = 0; s < 5; ++s) lc.rot[s] = static_cast<uint32_t>(lane - 7 - s) & 31u;
-    const Round0Lane r0l = round0_lane(chain);
-    if (warp == 0) {  // replica permutation (identity without tempering)
-        const int sob = a.swap_every > 0 ? a.sob[word * 32 + lane] : lane;
-        s_sob[lane] = sob;
-        s_bos[sob] = lane;
-    }
-    __syncthreads();
-    lc.lb = 4u * static_cast<uint32_t>(s_bos[lane]);  // lane reads the column of its rung
-
-    int64_t acc[kNSum];
-    const bool measuring = a.measure_every > 0;
-    if (warp == 0 && measuring) {
-#pragma unroll
-        for (int x = 0; x < kNSum; ++x) acc[x] = a.sums[static_cast<size_t>(chain) * kNSum + x];
-    }
-    int64_t meas = a.meas0;
-    // Cells of this warp: warp, warp + nwarp, ...; (i, j) advanced without division.
-    const int i_first = warp / W, j_first = warp - (warp / W) * W;
-    const int di = nwarp / W, dj = nwarp - (nwarp / W) * W;
-
-    for (int it = 0; it < a.n_sweeps; ++it) {
-        const uint32_t t = a.t0 + static_cast<uint32_t>(it);
-        const uint32_t X = r0l.hi ^ t ^ a.rk[0];
-        int i = i_first, j = j_first;
-        for (int cell = warp; cell < g.n_cells; cell += nwarp) {
-            const int R0 = 2 * i * L, C0 = 2 * j;
-            hidden_cell(s_v, R0, R0 + L, (2 * i + 2 == L) ? 0 : R0 + 2 * L, C0, C0 + 1,
-                        (C0 + 2 == L) ? 0 : C0 + 2, s_h + cell * 10, s_th, X, r0l.lo,
-                        round0_cell(static_cast<uint32_t>(cell), a.rk[1]), a.rk, lc);
-            i += di;
-            j += dj;
-            if (j >= W) {
-                j -= W;
-                ++i;
-            }
-        }
-        __syncthreads();
-        i = i_first;
-        j = j_first;
-        for (int cell = warp; cell < g.n_cells; cell += nwarp) {
-            const int iu = (i == 0) ? W - 1 : i - 1;
-            const int jl = (j == 0) ? W - 1 : j - 1;
-            visible_cell(s_v + 2 * i * L + 2 * j, L, s_h + cell * 10, s_h + (iu * W + j) * 10,
-                         s_h + (i * W + jl) * 10, s_tv, X, r0l.lo,
-                         round0_cell(static_cast<uint32_t>(cell), a.rk[1]), a.rk, lc);
-            i += di;
-            j += dj;
-            if (j >= W) {
-                j -= W;
-                ++i;
-            }
-        }
-        __syncthreads();
-        const bool do_meas = measuring && (t + 1u) % static_cast<uint32_t>(a.measure_every) == 0u;
-        const bool do_swap = a.swap_every > 0 && (t + 1u) % static_cast<uint32_t>(a.swap_every) == 0u;
-        if (do_meas || do_swap) {
-            int anti0 = 0, anti1 = 0, pos = 0;
-            i = i_first;
-            j = j_first;
-            for (int cell = warp; cell < g.n_cells; cell += nwarp) {
-                const int R0 = 2 * i * L, C0 = 2 * j;
-                count_cell(s_v, R0, R0 + L, (2 * i + 2 == L) ? 0 : R0 + 2 * L, C0, C0 + 1,
-                           (C0 + 2 == L) ? 0 : C0 + 2, lane, anti0, anti1, pos);
-                i += di;
-                j += dj;
-                if (j >= W) {
-                    j -= W;
-                    ++i;
-                }
-            }
-            atomicAdd(&s_cnt[lane], anti0);
-            atomicAdd(&s_cnt[32 + lane], anti1);
-            atomicAdd(&s_cnt[64 + lane], pos);
-            __syncthreads();
-            if (warp == 0) post_sweep_warp0(a, s_cnt, s_sob, s_bos, lane, word, t, do_meas, do_swap, meas, acc);
-            if (do_meas) ++meas;
-            __syncthreads();
-            if (do_swap) lc.lb = 4u * static_cast<uint32_t>(s_bos[lane]);
-        }
-        if (a.sq_every > 0 && (t + 1u) % static_cast<uint32_t>(a.sq_every) == 0u) {
-            accumulate_correlations(a, s_v, s_seg, s_segmask, warp, nwarp, lane);
-            __syncthreads();
-        }
-    }
-    for (int x = threadIdx.x; x < g.N; x += blockDim.x) gv[x] = s_v[x];
-    if (warp == 0 && a.swap_every > 0) a.sob[word * 32 + lane] = s_sob[lane];
-    if (warp == 0 && measuring) {
-#pragma unroll
-        for (int x = 0; x < kNSum; ++x) a.sums[static_cast<size_t>(chain) * kNSum + x] = acc[x];
-    }
+    sweep_canon_body(a, blockIdx.x);
 }
 
 }  // namespace

@@ -4,6 +4,7 @@
 // plain left-to-right double evaluation of the formulas in crbm.h.
 #include "../../include/crbm.h"
 #include "crbm_internal.h"
+#include "crbm_context.h"
 
 #include <algorithm>
 #include <cmath>
@@ -16,26 +17,8 @@
 
 using namespace crbm;
 
-struct crbm_ctx {
-    Geometry g{};
-    int n_chains = 0, n_words = 0, n_params = 0;
-    int layout = CRBM_LAYOUT_SMEM;
-    int warps = 8;
-    uint64_t seed = 0;
-    int measure_every = 0, series_len = 0, sq_every = 0, swap_every = 0;
-    int64_t sweeps = 0;     // global sweep counter
-    int64_t meas = 0;       // measurements since the last reset
-    int64_t sq_meas = 0;    // correlation samples since the last reset
-    int64_t launches = 0;
-    cudaStream_t stream = nullptr;
-    int device = 0;
-    std::vector<int32_t> chain_param;
-    std::vector<int32_t> q[3];     // quantised J, J', h per point
-    std::vector<double> beta;
-    std::vector<uint32_t> tables;  // [n_params][nTab]
-    DeviceState d;
-    std::string err;
-};
+
+
 
 namespace {
 
@@ -223,6 +206,47 @@ bool host_to_q4(double x, int32_t& q) { return to_q4(x, q); }
 void host_point_tables(const Geometry& g, double beta, int32_t qJ, int32_t qJp, int32_t qh,
                        uint32_t* out, int sgn[2]) {
     point_tables(g, beta, qJ, qJp, qh, out, sgn);
+}
+}  // namespace crbm
+
+namespace crbm {
+SweepArgs fill_sweep_args(const crbm_ctx* ctx, int chunk) {
+    SweepArgs a{};
+    a.g = ctx->g;
+    a.v = ctx->d.v;
+    a.tab = ctx->d.tab;
+    a.ctab = ctx->d.ctab;
+    a.sneg = ctx->d.sneg;
+    a.inc = ctx->d.inc;
+    a.inc_off = ctx->d.inc_off;
+    a.sums = ctx->d.sums;
+    a.series = ctx->d.series;
+    a.h = ctx->d.h;
+    a.cnt = ctx->d.cnt;
+    a.sob = ctx->d.sob;
+    a.swap_tab = ctx->d.swap_tab;
+    a.swap_off = ctx->d.swap_off;
+    a.swap_len = ctx->d.swap_len;
+    a.wq = ctx->d.wq;
+    a.swap_every = ctx->swap_every;
+    a.corr = ctx->d.corr;
+    a.seg = ctx->d.seg;
+    a.segmask = ctx->d.segmask;
+    a.n_words = ctx->n_words;
+    a.n_chains_padded = ctx->n_words * 32;
+    a.key0 = static_cast<uint32_t>(ctx->seed);
+    a.key1 = static_cast<uint32_t>(ctx->seed >> 32);
+    for (int r = 0; r < 10; ++r) {  // Philox key schedule (Weyl increments)
+        a.rk[2 * r] = a.key0 + static_cast<uint32_t>(r) * 0x9E3779B9u;
+        a.rk[2 * r + 1] = a.key1 + static_cast<uint32_t>(r) * 0xBB67AE85u;
+    }
+    a.t0 = static_cast<uint32_t>(ctx->sweeps);
+    a.n_sweeps = chunk;
+    a.measure_every = ctx->measure_every;
+    a.meas0 = ctx->meas;
+    a.series_len = ctx->series_len;
+    a.sq_every = ctx->sq_every;
+    return a;
 }
 }  // namespace crbm
 
@@ -499,6 +523,8 @@ int crbm_create(crbm_ctx** out, const crbm_params* p) {
         return CRBM_ECUDA;
     }
     ctx->launches = 1;
+    if (!std::getenv("CRBM_WARPS") && ctx->layout == CRBM_LAYOUT_SMEM)
+        if (const int w = autotune_lookup(ctx)) ctx->warps = w;  // shape tuned earlier on this GPU
     *out = ctx;
     return CRBM_OK;
 }
@@ -523,41 +549,7 @@ int crbm_sweep(crbm_ctx* ctx, int64_t n_sweeps) {
     while (left > 0) {
         // Chunks keep one launch within a few seconds on large grids.
         const int chunk = static_cast<int>(std::min<int64_t>(left, 1 << 20));
-        SweepArgs a{};
-        a.g = ctx->g;
-        a.v = ctx->d.v;
-        a.tab = ctx->d.tab;
-        a.ctab = ctx->d.ctab;
-        a.sneg = ctx->d.sneg;
-        a.inc = ctx->d.inc;
-        a.inc_off = ctx->d.inc_off;
-        a.sums = ctx->d.sums;
-        a.series = ctx->d.series;
-        a.h = ctx->d.h;
-        a.cnt = ctx->d.cnt;
-        a.sob = ctx->d.sob;
-        a.swap_tab = ctx->d.swap_tab;
-        a.swap_off = ctx->d.swap_off;
-        a.swap_len = ctx->d.swap_len;
-        a.wq = ctx->d.wq;
-        a.swap_every = ctx->swap_every;
-        a.corr = ctx->d.corr;
-        a.seg = ctx->d.seg;
-        a.segmask = ctx->d.segmask;
-        a.n_words = ctx->n_words;
-        a.n_chains_padded = ctx->n_words * 32;
-        a.key0 = static_cast<uint32_t>(ctx->seed);
-        a.key1 = static_cast<uint32_t>(ctx->seed >> 32);
-        for (int r = 0; r < 10; ++r) {  // Philox key schedule (Weyl increments)
-            a.rk[2 * r] = a.key0 + static_cast<uint32_t>(r) * 0x9E3779B9u;
-            a.rk[2 * r + 1] = a.key1 + static_cast<uint32_t>(r) * 0xBB67AE85u;
-        }
-        a.t0 = static_cast<uint32_t>(ctx->sweeps);
-        a.n_sweeps = chunk;
-        a.measure_every = ctx->measure_every;
-        a.meas0 = ctx->meas;
-        a.series_len = ctx->series_len;
-        a.sq_every = ctx->sq_every;
+        const SweepArgs a = fill_sweep_args(ctx, chunk);
         cudaError_t e;
         if (ctx->layout == CRBM_LAYOUT_STREAM) {
             e = launch_sweep_stream(a, ctx->stream, &ctx->launches);

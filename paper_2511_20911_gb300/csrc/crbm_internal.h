@@ -93,6 +93,7 @@ struct SweepArgs {
     const int32_t* swap_len;
     const int32_t* wq;
     int swap_every;       // 0 = no replica exchange
+    const int64_t* clock; // batch launches: device {sweep, measurements} (else t0 / meas0)
     int64_t* corr;
     const int32_t* seg;
     const uint32_t* segmask;
@@ -115,6 +116,15 @@ bool host_to_q4(double x, int32_t& q);
 void host_point_tables(const Geometry& g, double beta, int32_t qJ, int32_t qJp, int32_t qh,
                        uint32_t* out, int sgn[2]);
 
+// Batched launch: up to kMaxBatch contexts' descriptors by value (kernel
+// parameter space), and a work list of (descriptor, word) per CTA.
+constexpr int kMaxBatch = 16;
+struct BatchArgs {
+    const int2* items;
+    int n_desc;
+    SweepArgs d[kMaxBatch];
+};
+
 // Kernel launchers (crbm_kernels.cu).  All return cudaGetLastError().
 size_t smem_bytes_generic(const Geometry& g);
 size_t smem_bytes_canon(const Geometry& g);
@@ -123,6 +133,8 @@ cudaError_t launch_init(const Geometry& g, uint32_t* v, int n_words, uint32_t ke
 cudaError_t launch_sweep_generic(const SweepArgs& a, int warps_per_cta, cudaStream_t st);
 cudaError_t launch_sweep_canon(const SweepArgs& a, int warps_per_cta, cudaStream_t st);
 cudaError_t launch_sweep_stream(const SweepArgs& a, cudaStream_t st, int64_t* launches);
+cudaError_t launch_sweep_batch(const BatchArgs& b, int n_items, int threads, size_t smem, cudaStream_t st);
+cudaError_t launch_batch_advance(int64_t* clocks, const int* every, int n_ctx, int64_t n_sweeps, cudaStream_t st);
 cudaError_t launch_philox(const uint32_t* in, uint32_t* out, int n, cudaStream_t st);
 cudaError_t launch_unpack(const Geometry& g, const uint32_t* v, int8_t* out, int n_words,
                           cudaStream_t st);

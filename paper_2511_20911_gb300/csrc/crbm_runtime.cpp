@@ -1,0 +1,317 @@
+// Native runtime around the sweep kernels: the autotuner (CTA shape per
+// lattice shape, timed on scratch copies of a context's state and cached per
+// GPU in a text file) and batched launches (several contexts, mixed lattice
+// sizes and tempering ladders, in one kernel launch captured in a CUDA graph).
+#include <algorithm>
+#include <cstdio>
+#include <cstdlib>
+#include <cstring>
+#include <fstream>
+#include <map>
+#include <mutex>
+#include <new>
+#include <sstream>
+#include <string>
+#include <vector>
+
+#include <sys/stat.h>
+
+#include "crbm_context.h"
+
+using namespace crbm;
+
+namespace {
+
+// ----------------------------------------------------------------- cache
+// One line per tuned shape: "<key> <warps>"; the key names the GPU, the
+// lattice, the filter set and the number of packed words.
+std::mutex g_cache_mutex;
+
+std::string cache_path() {
+    if (const char* p = std::getenv("CRBM_AUTOTUNE_CACHE")) return p;
+    const char* home = std::getenv("HOME");
+    return std::string(home ? home : "/tmp") + "/.cache/crbm_autotune.txt";
+}
+
+std::string shape_key(const crbm_ctx* ctx) {
+    cudaDeviceProp prop{};
+    cudaGetDeviceProperties(&prop, ctx->device);
+    std::ostringstream k;
+    k << prop.name << "|sm" << prop.multiProcessorCount << "|L" << ctx->g.L << "|p" << ctx->g.periodic << "|c"
+      << ctx->g.canonical << "|nb" << ctx->g.nb << "|w" << ctx->n_words << "|x" << (ctx->swap_every > 0);
+    std::string s = k.str();
+    std::replace(s.begin(), s.end(), ' ', '_');
+    return s;
+}
+
+int smem_ok(const crbm_ctx* ctx) {
+    return (ctx->g.canonical ? smem_bytes_canon(ctx->g) : smem_bytes_generic(ctx->g)) <= 227 * 1024;
+}
+
+cudaError_t launch_one(const SweepArgs& a, const crbm_ctx* ctx, int warps) {
+    return ctx->g.canonical ? launch_sweep_canon(a, warps, ctx->stream) : launch_sweep_generic(a, warps, ctx->stream);
+}
+
+}  // namespace
+
+namespace crbm {
+int autotune_lookup(const crbm_ctx* ctx) {
+    std::lock_guard<std::mutex> lock(g_cache_mutex);
+    std::ifstream f(cache_path());
+    if (!f) return 0;
+    const std::string key = shape_key(ctx);
+    std::string k;
+    int w = 0, found = 0;
+    while (f >> k >> w)
+        if (k == key && w >= 1 && w <= 16) found = w;  // last entry wins
+    return found;
+}
+}  // namespace crbm
+
+extern "C" {
+
+int crbm_autotune(crbm_ctx* ctx, int64_t probe_sweeps, int32_t* best_warps) {
+    if (!ctx) return CRBM_EINVAL;
+    if (ctx->layout != CRBM_LAYOUT_SMEM) {
+        ctx->err = "the autotuner chooses CTA shapes of the SMEM layout";
+        return CRBM_EUNSUPPORTED;
+    }
+    if (probe_sweeps < 1 || probe_sweeps > 100000) {
+        ctx->err = "probe_sweeps must be in 1..100000";
+        return CRBM_EINVAL;
+    }
+    const size_t npad = static_cast<size_t>(ctx->n_words) * 32, N = ctx->g.N;
+    uint32_t* v2 = nullptr;
+    int64_t* s2 = nullptr;
+    int32_t* p2 = nullptr;
+    cudaEvent_t e0 = nullptr, e1 = nullptr;
+    cudaError_t e = cudaMalloc(reinterpret_cast<void**>(&v2), ctx->n_words * N * 4);
+    if (e == cudaSuccess) e = cudaMalloc(reinterpret_cast<void**>(&s2), npad * kNSum * 8);
+    if (e == cudaSuccess) e = cudaMalloc(reinterpret_cast<void**>(&p2), npad * 4);
+    if (e == cudaSuccess) e = cudaEventCreate(&e0);
+    if (e == cudaSuccess) e = cudaEventCreate(&e1);
+    int best = ctx->warps;
+    float best_ms = 1e30f;
+    const int cand[] = {2, 4, 6, 8, 10, 12, 14, 16};
+    for (int w : cand) {
+        if (e != cudaSuccess) break;
+        if (w > std::max(1, ctx->g.n_cells)) continue;
+        // scratch copies: the tuning sweeps never touch the context's chains
+        e = cudaMemcpyAsync(v2, ctx->d.v, ctx->n_words * N * 4, cudaMemcpyDeviceToDevice, ctx->stream);
+        if (e == cudaSuccess) e = cudaMemsetAsync(s2, 0, npad * kNSum * 8, ctx->stream);
+        if (e == cudaSuccess)
+            e = cudaMemcpyAsync(p2, ctx->d.sob, npad * 4, cudaMemcpyDeviceToDevice, ctx->stream);
+        if (e != cudaSuccess) break;
+        SweepArgs a = fill_sweep_args(ctx, static_cast<int>(probe_sweeps));
+        a.v = v2;
+        a.sums = s2;
+        a.sob = p2;
+        a.series_len = 0;
+        a.sq_every = 0;
+        a.clock = nullptr;
+        a.n_sweeps = static_cast<int>(std::max<int64_t>(1, probe_sweeps / 4));
+        e = launch_one(a, ctx, w);  // warm-up
+        a.n_sweeps = static_cast<int>(probe_sweeps);
+        if (e == cudaSuccess) e = cudaEventRecord(e0, ctx->stream);
+        if (e == cudaSuccess) e = launch_one(a, ctx, w);
+        if (e == cudaSuccess) e = cudaEventRecord(e1, ctx->stream);
+        if (e == cudaSuccess) e = cudaEventSynchronize(e1);
+        float ms = 0.f;
+        if (e == cudaSuccess) e = cudaEventElapsedTime(&ms, e0, e1);
+        if (e == cudaSuccess && ms < best_ms) {
+            best_ms = ms;
+            best = w;
+        }
+    }
+    if (e0) cudaEventDestroy(e0);
+    if (e1) cudaEventDestroy(e1);
+    cudaFree(v2);
+    cudaFree(s2);
+    cudaFree(p2);
+    if (e != cudaSuccess) {
+        ctx->err = std::string("crbm_autotune: ") + cudaGetErrorString(e);
+        return CRBM_ECUDA;
+    }
+    ctx->warps = best;
+    if (best_warps) *best_warps = best;
+    std::lock_guard<std::mutex> lock(g_cache_mutex);
+    const std::string path = cache_path();
+    const size_t slash = path.find_last_of('/');
+    if (slash != std::string::npos && slash > 0) mkdir(path.substr(0, slash).c_str(), 0755);  // best effort
+    if (FILE* f = std::fopen(path.c_str(), "a")) {
+        std::fprintf(f, "%s %d\n", shape_key(ctx).c_str(), best);
+        std::fclose(f);
+    }
+    return CRBM_OK;
+}
+
+int crbm_warps(const crbm_ctx* ctx) { return ctx ? ctx->warps : CRBM_EINVAL; }
+
+}  // extern "C"
+
+// ----------------------------------------------------------------- batches
+struct crbm_batch {
+    std::vector<crbm_ctx*> ctx;
+    cudaStream_t stream = nullptr;     // the contexts' common stream
+    cudaStream_t capture = nullptr;    // private stream the graph is captured on
+    int2* items = nullptr;
+    int n_items = 0;
+    int64_t* clock = nullptr;          // device [n][2]
+    int* every = nullptr;              // device [n]
+    std::vector<int64_t> mirror;       // host view of clock
+    std::vector<int64_t> staged;       // pinned-free staging for clock uploads
+    int threads = 0;
+    size_t smem = 0;
+    cudaGraphExec_t exec = nullptr;
+    int64_t graph_n = -1;
+    std::string err;
+};
+
+namespace {
+thread_local std::string g_batch_create_error;
+
+void batch_free(crbm_batch* b) {
+    if (b->exec) cudaGraphExecDestroy(b->exec);
+    if (b->capture) cudaStreamDestroy(b->capture);
+    cudaFree(b->items);
+    cudaFree(b->clock);
+    cudaFree(b->every);
+    delete b;
+}
+}  // namespace
+
+extern "C" {
+
+int crbm_batch_create(crbm_batch** out, crbm_ctx* const* ctxs, int32_t n_ctx) {
+    if (!out || !ctxs || n_ctx < 1 || n_ctx > kMaxBatch) {
+        g_batch_create_error = "need 1..CRBM_BATCH_MAX contexts";
+        return CRBM_EINVAL;
+    }
+    *out = nullptr;
+    crbm_batch* b = new (std::nothrow) crbm_batch();
+    if (!b) return CRBM_ENOMEM;
+    int warps = 1;
+    std::vector<std::pair<int64_t, int2>> work;  // (cost, item)
+    for (int c = 0; c < n_ctx; ++c) {
+        crbm_ctx* x = ctxs[c];
+        if (!x || x->layout != CRBM_LAYOUT_SMEM || !smem_ok(x) || x->stream != ctxs[0]->stream ||
+            x->device != ctxs[0]->device || std::count(ctxs, ctxs + c, x)) {
+            g_batch_create_error = "batch members must be distinct SMEM-layout contexts on one device and stream";
+            delete b;
+            return CRBM_EINVAL;
+        }
+        b->ctx.push_back(x);
+        warps = std::max(warps, x->warps);
+        b->smem = std::max(b->smem, x->g.canonical ? smem_bytes_canon(x->g) : smem_bytes_generic(x->g));
+        const int64_t cost = static_cast<int64_t>(x->g.n_cells) * (x->g.canonical ? 2 : 3);
+        for (int w = 0; w < x->n_words; ++w) work.push_back({cost, make_int2(c, w)});
+    }
+    // heaviest lattices first, so they start in the first wave
+    std::stable_sort(work.begin(), work.end(),
+                     [](const std::pair<int64_t, int2>& p, const std::pair<int64_t, int2>& q) { return p.first > q.first; });
+    std::vector<int2> items;
+    for (auto& p : work) items.push_back(p.second);
+    std::vector<int> every;
+    for (auto* x : b->ctx) every.push_back(x->measure_every);
+    b->stream = ctxs[0]->stream;
+    b->threads = 32 * warps;
+    b->n_items = static_cast<int>(items.size());
+    b->mirror.assign(2 * n_ctx, -1);
+    b->staged.assign(2 * n_ctx, 0);
+    cudaError_t e = cudaMalloc(reinterpret_cast<void**>(&b->items), items.size() * sizeof(int2));
+    if (e == cudaSuccess) e = cudaMalloc(reinterpret_cast<void**>(&b->clock), 2 * n_ctx * sizeof(int64_t));
+    if (e == cudaSuccess) e = cudaMalloc(reinterpret_cast<void**>(&b->every), n_ctx * sizeof(int));
+    if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&b->capture, cudaStreamNonBlocking);
+    if (e == cudaSuccess) e = cudaMemcpy(b->items, items.data(), items.size() * sizeof(int2), cudaMemcpyHostToDevice);
+    if (e == cudaSuccess) e = cudaMemcpy(b->every, every.data(), every.size() * sizeof(int), cudaMemcpyHostToDevice);
+    if (e != cudaSuccess) {
+        g_batch_create_error = std::string("crbm_batch_create: ") + cudaGetErrorString(e);
+        batch_free(b);
+        return CRBM_ECUDA;
+    }
+    *out = b;
+    return CRBM_OK;
+}
+
+int crbm_batch_sweep(crbm_batch* b, int64_t n_sweeps) {
+    if (!b) return CRBM_EINVAL;
+    if (n_sweeps < 0 || n_sweeps > (1 << 20)) {
+        b->err = "n_sweeps must be in 0..2^20 per batched launch";
+        return CRBM_EINVAL;
+    }
+    if (n_sweeps == 0) return CRBM_OK;
+    const int n = static_cast<int>(b->ctx.size());
+    for (auto* x : b->ctx)
+        if (x->sweeps + n_sweeps > 4294967295LL) {
+            b->err = "the 32-bit sweep counter of a member would overflow";
+            return CRBM_EINVAL;
+        }
+    // upload the members' counters when they moved outside this batch
+    bool stale = false;
+    for (int c = 0; c < n; ++c)
+        if (b->mirror[2 * c] != b->ctx[c]->sweeps || b->mirror[2 * c + 1] != b->ctx[c]->meas) stale = true;
+    cudaError_t e = cudaSuccess;
+    if (stale) {
+        for (int c = 0; c < n; ++c) {
+            b->staged[2 * c] = b->ctx[c]->sweeps;
+            b->staged[2 * c + 1] = b->ctx[c]->meas;
+        }
+        // pageable source: staged by the time the call returns
+        e = cudaMemcpyAsync(b->clock, b->staged.data(), 2 * n * sizeof(int64_t), cudaMemcpyHostToDevice, b->stream);
+        b->mirror = b->staged;
+    }
+    if (e == cudaSuccess && (!b->exec || b->graph_n != n_sweeps)) {
+        if (b->exec) {
+            cudaGraphExecDestroy(b->exec);
+            b->exec = nullptr;
+        }
+        BatchArgs args{};
+        args.items = b->items;
+        args.n_desc = n;
+        for (int c = 0; c < n; ++c) {
+            args.d[c] = fill_sweep_args(b->ctx[c], static_cast<int>(n_sweeps));
+            args.d[c].clock = b->clock + 2 * c;
+        }
+        cudaGraph_t graph = nullptr;
+        e = cudaStreamBeginCapture(b->capture, cudaStreamCaptureModeThreadLocal);
+        if (e == cudaSuccess) {
+            cudaError_t e1 = launch_sweep_batch(args, b->n_items, b->threads, b->smem, b->capture);
+            cudaError_t e2 = launch_batch_advance(b->clock, b->every, n, n_sweeps, b->capture);
+            e = cudaStreamEndCapture(b->capture, &graph);
+            if (e == cudaSuccess) e = e1 != cudaSuccess ? e1 : e2;
+        }
+        if (e == cudaSuccess) e = cudaGraphInstantiate(&b->exec, graph, 0);
+        if (graph) cudaGraphDestroy(graph);
+        b->graph_n = n_sweeps;
+    }
+    if (e == cudaSuccess) e = cudaGraphLaunch(b->exec, b->stream);
+    if (e != cudaSuccess) {
+        b->err = std::string("crbm_batch_sweep: ") + cudaGetErrorString(e);
+        return CRBM_ECUDA;
+    }
+    for (int c = 0; c < n; ++c) {  // host mirrors of the device clocks
+        crbm_ctx* x = b->ctx[c];
+        const int64_t t0 = x->sweeps, t1 = t0 + n_sweeps;
+        if (x->measure_every > 0) x->meas += t1 / x->measure_every - t0 / x->measure_every;
+        if (x->sq_every > 0) x->sq_meas += t1 / x->sq_every - t0 / x->sq_every;
+        x->sweeps = t1;
+        x->launches += 1;
+        b->mirror[2 * c] = x->sweeps;
+        b->mirror[2 * c + 1] = x->meas;
+    }
+    return CRBM_OK;
+}
+
+int crbm_batch_threads(const crbm_batch* b) { return b ? b->threads : CRBM_EINVAL; }
+
+const char* crbm_batch_last_error(const crbm_batch* b) {
+    return b ? b->err.c_str() : g_batch_create_error.c_str();
+}
+
+void crbm_batch_destroy(crbm_batch* b) {
+    if (!b) return;
+    cudaStreamSynchronize(b->stream);
+    batch_free(b);
+}
+
+}  // extern "C"

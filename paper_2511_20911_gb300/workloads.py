@@ -57,3 +57,17 @@ def stream_workload():
     return dict(L=384, params=dict(J=[1.0] * 3, Jp=[1.0] * 3, h=[0.0, 1.0, 2.0], beta=[1.0] * 3),
                 n_chains=3072, chain_param=np.repeat(np.arange(3, dtype=np.int32), 1024), seed=384,
                 n_sweeps=10_000)
+
+
+def tempering_batch_workload(sizes=(6, 9, 12, 18, 24, 48), ladders=8, b_lo=0.2, b_hi=10.0):
+    """Mixed lattice sizes, each with `ladders` replica-exchange ladders of 32
+    geometric beta in [b_lo, b_hi] (256 chains per size), J=1, J'=1.5, h=1,
+    swaps every 10 sweeps; 10^5 sweeps."""
+    betas = list(b_lo * (b_hi / b_lo) ** (np.arange(32) / 31.0))
+    params = dict(J=[1.0] * 32, Jp=[1.5] * 32, h=[1.0] * 32, beta=betas)
+    members = []
+    for L in sizes:
+        members.append(dict(L=L, params=params, n_chains=32 * ladders,
+                            chain_param=np.tile(np.arange(32, dtype=np.int32), ladders),
+                            seed=1000 + L, swap_every=10))
+    return members

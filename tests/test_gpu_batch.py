@@ -1,0 +1,99 @@
+"""Batched launches and the autotuner.  A batch advances every member by one
+kernel launch (graph-captured); each member must stay bit-identical to a twin
+context advanced on its own.  Autotuning must not touch the chains."""
+import numpy as np
+import pytest
+
+import paper_2511_20911_gb300 as crbm
+from paper_2511_20911_gb300 import workloads
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _gpu():
+    torch = pytest.importorskip("torch")
+    if not torch.cuda.is_available():
+        pytest.skip("no GPU")
+
+
+def members():
+    rng = np.random.default_rng(12)
+    pt = workloads.tempering_batch_workload(sizes=(9, 12), ladders=2)
+    specs = [dict(L=6, params=workloads.random_params(rng, 3), n_chains=64,
+                  chain_param=rng.integers(0, 3, 64).astype(np.int32), seed=1, measure_every=2,
+                  series_len=20),
+             dict(L=7, params=workloads.random_params(rng, 2), n_chains=40, periodic=False,
+                  chain_param=rng.integers(0, 2, 40).astype(np.int32), seed=2, measure_every=3),
+             dict(L=8, params=workloads.random_params(rng, 2), n_chains=33,
+                  chain_param=rng.integers(0, 2, 33).astype(np.int32), seed=3, measure_every=0,
+                  sq_every=4)]
+    for m in pt:
+        specs.append(dict(m, measure_every=5, series_len=10))
+    return specs
+
+
+def make(spec):
+    return crbm.Sampler(**spec)
+
+
+def same(a, b):
+    assert a.sweep_count == b.sweep_count
+    assert np.array_equal(a.get_spins(), b.get_spins())
+    assert np.array_equal(a.observables(), b.observables())
+    assert np.array_equal(a.permutation(), b.permutation())
+    if a.series_len:
+        assert np.array_equal(a.series(), b.series())
+    if a.sq_every:
+        assert np.array_equal(a.correlations()[0], b.correlations()[0])
+
+
+def test_batch_matches_individual_sweeps():
+    specs = members()
+    batched = [make(s) for s in specs]
+    twins = [make(s) for s in specs]
+    batch = crbm.Batch(batched)
+    assert batch.threads >= 32
+    plan = [("batch", 5), ("batch", 8), ("solo", 3), ("batch", 8), ("batch", 2)]
+    for kind, n in plan:
+        if kind == "batch":
+            batch.sweep(n)
+        else:                              # a member moved outside the batch: clocks re-uploaded
+            batched[1].sweep(n)
+            batched[3].sweep(n)
+            twins[1].sweep(n)
+            twins[3].sweep(n)
+            continue
+        for t in twins:
+            t.sweep(n)
+    for a, b in zip(batched, twins):
+        same(a, b)
+    batch.close()
+
+
+def test_batch_validation():
+    spec = members()[0]
+    a, b = make(spec), make(spec)
+    s = crbm.Sampler(20, dict(J=[1.0], Jp=[1.0], h=[0.5], beta=[1.0]), 64,
+                     layout=crbm.CRBM_LAYOUT_STREAM)
+    for group in ([a, a], [a, s]):
+        with pytest.raises(crbm.CrbmError) as e:
+            crbm.Batch(group)
+        assert e.value.code == crbm.CRBM_EINVAL
+
+
+def test_autotune_keeps_chains_and_writes_cache(tmp_path, monkeypatch):
+    monkeypatch.setenv("CRBM_AUTOTUNE_CACHE", str(tmp_path / "tune.txt"))
+    spec = members()[3]                     # a tempering member
+    a, b = make(spec), make(spec)
+    a.sweep(7)
+    b.sweep(7)
+    w = a.autotune(20)
+    assert w in (2, 4, 6, 8, 10, 12, 14, 16) and a.warps == w
+    a.sweep(9)
+    b.sweep(9)
+    same(a, b)
+    text = (tmp_path / "tune.txt").read_text()
+    assert text.strip().endswith(f" {w}")
+    c = make(spec)                          # same shape on the same GPU: taken from the cache
+    assert c.warps == w

@@ -223,3 +223,79 @@ def swap_threshold(x):
     f.restype = ctypes.c_uint32
     f.argtypes = [ctypes.c_double]
     return int(f(float(x)))
+
+
+NET_PARAMS = 3345
+
+
+def bf16(x):
+    f = lib().orc_bf16
+    f.restype = ctypes.c_double
+    f.argtypes = [ctypes.c_double]
+    return float(f(float(x)))
+
+
+def patch_input(spins, bR, bC, k, beta, h):
+    L = spins.shape[-1]
+    v = np.ascontiguousarray(spins, np.int8)
+    P = k + 6
+    out = np.zeros((6, P, P), np.float64)
+    lib().orc_patch_input(L, _p(v, ctypes.c_int8), bR, bC, k, ctypes.c_double(beta),
+                          ctypes.c_double(h), _p(out, ctypes.c_double))
+    return out
+
+
+def net_forward(k, w, inp, use_bf16=False):
+    w = np.ascontiguousarray(w, np.float64)
+    inp = np.ascontiguousarray(inp, np.float64)
+    out = np.zeros(k * k, np.float64)
+    if lib().orc_net_forward(k, _p(w, ctypes.c_double), _p(inp, ctypes.c_double), int(use_bf16),
+                             _p(out, ctypes.c_double)):
+        raise ValueError("orc_net_forward failed")
+    return out
+
+
+def net_loss_grad(k, w, inputs, targets, use_bf16=False):
+    w = np.ascontiguousarray(w, np.float64)
+    inputs = np.ascontiguousarray(inputs, np.float64)
+    targets = np.ascontiguousarray(targets, np.int8)
+    n = len(targets)
+    grad = np.zeros(NET_PARAMS, np.float64)
+    loss = ctypes.c_double()
+    if lib().orc_net_loss_grad(k, _p(w, ctypes.c_double), _p(inputs, ctypes.c_double),
+                               _p(targets, ctypes.c_int8), n, int(use_bf16), ctypes.byref(loss),
+                               _p(grad, ctypes.c_double)):
+        raise ValueError("orc_net_loss_grad failed")
+    return loss.value, grad
+
+
+def block_delta_e(spins, bR, bC, newblock, J, Jp, h):
+    L = spins.shape[-1]
+    v = np.ascontiguousarray(spins, np.int8)
+    nb = np.ascontiguousarray(newblock, np.int8).reshape(-1)
+    k = int(round(np.sqrt(nb.size)))
+    f = lib().orc_block_delta_e
+    f.restype = ctypes.c_int64
+    return int(f(L, _p(v, ctypes.c_int8), bR, bC, k, _p(nb, ctypes.c_int8), quantize(J),
+                 quantize(Jp), quantize(h)))
+
+
+def mh_rows(states, bR, bC, k, w, J, Jp, h, beta, use_bf16=False):
+    v = np.ascontiguousarray(states, np.int8)
+    n, L = v.shape[0], v.shape[-1]
+    w = np.ascontiguousarray(w, np.float64)
+    out = np.zeros((n, 1 << (k * k)), np.float64)
+    if lib().orc_mh_rows(L, _p(v, ctypes.c_int8), n, bR, bC, k, _p(w, ctypes.c_double),
+                         ctypes.c_double(J), ctypes.c_double(Jp), ctypes.c_double(h),
+                         ctypes.c_double(beta), int(use_bf16), _p(out, ctypes.c_double)):
+        raise ValueError("orc_mh_rows failed")
+    return out
+
+
+def random_net(seed, scale=0.3):
+    """Random parameters in the documented order (W1, b1, W2, b2, W3, b3)."""
+    rng = np.random.default_rng(seed)
+    w = rng.normal(0.0, scale, NET_PARAMS)
+    w[864:880] *= 0.1
+    w[3184:3200] *= 0.1
+    return w

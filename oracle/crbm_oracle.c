@@ -514,3 +514,294 @@ int orc_get_threads(void) {
     return 1;
 #endif
 }
+
+/* ------------------------------------------------ learned block proposal */
+/* Round a double to the nearest bfloat16 (8-bit mantissa), ties to even. */
+double orc_bf16(double x) {
+    float f = (float)x;
+    uint32_t u;
+    memcpy(&u, &f, 4);
+    if ((u & 0x7f800000u) == 0x7f800000u) return (double)f; /* inf / nan */
+    uint32_t lsb = (u >> 16) & 1u;
+    u += 0x7fffu + lsb;
+    u &= 0xffff0000u;
+    memcpy(&f, &u, 4);
+    return (double)f;
+}
+
+/* Input planes of the (k+6)^2 patch around block (bR, bC); input[c][P]. */
+int orc_patch_input(int L, const int8_t* v, int bR, int bC, int k, double beta, double h,
+                    double* input) {
+    int P = k + 6;
+    for (int a = 0; a < P; ++a)
+        for (int b = 0; b < P; ++b) {
+            int R = ((bR - 3 + a) % L + L) % L, C = ((bC - 3 + b) % L + L) % L;
+            int dR = ((R - bR) % L + L) % L, dC = ((C - bC) % L + L) % L;
+            int inside = dR < k && dC < k;
+            int x = a * P + b;
+            input[0 * P * P + x] = inside ? 0.0 : (double)v[R * L + C];
+            input[1 * P * P + x] = inside ? 1.0 : 0.0;
+            input[2 * P * P + x] = (double)(R & 1);
+            input[3 * P * P + x] = (double)(C & 1);
+            input[4 * P * P + x] = beta;
+            input[5 * P * P + x] = h;
+        }
+    return 0;
+}
+
+/* One valid 3x3 convolution: out[o][y][x] = b[o] + sum_c,ky,kx W[o][c][ky][kx]
+ * in[c][y+ky][x+kx], in of side S, out of side S - 2. */
+static void conv3(const double* W, const double* b, int cin, int cout, int S, const double* in,
+                  double* out) {
+    int T = S - 2;
+    for (int o = 0; o < cout; ++o)
+        for (int y = 0; y < T; ++y)
+            for (int x = 0; x < T; ++x) {
+                double acc = b[o];
+                for (int c = 0; c < cin; ++c)
+                    for (int ky = 0; ky < 3; ++ky)
+                        for (int kx = 0; kx < 3; ++kx)
+                            acc += W[((o * cin + c) * 3 + ky) * 3 + kx] * in[(c * S + y + ky) * S + x + kx];
+                out[(o * T + y) * T + x] = acc;
+            }
+}
+
+typedef struct {
+    double w[ORC_NET_PARAMS];
+} orc_net;
+
+static void net_weights(const double* w, int bf16, double* out) {
+    for (int i = 0; i < ORC_NET_PARAMS; ++i) out[i] = bf16 ? orc_bf16(w[i]) : w[i];
+}
+
+/* Forward pass keeping the activations: z1, a1 [16][(k+4)^2], z2, a2 [16][(k+2)^2]. */
+static void net_forward_full(int k, const double* wr, const double* input, int bf16, double* in_r,
+                             double* z1, double* a1, double* z2, double* a2, double* logits) {
+    int P = k + 6, S1 = k + 4, S2 = k + 2;
+    const double *W1 = wr, *b1 = wr + 864, *W2 = wr + 880, *b2 = wr + 3184, *W3 = wr + 3200,
+                 *b3 = wr + 3344;
+    for (int i = 0; i < 6 * P * P; ++i) in_r[i] = bf16 ? orc_bf16(input[i]) : input[i];
+    conv3(W1, b1, 6, 16, P, in_r, z1);
+    for (int i = 0; i < 16 * S1 * S1; ++i) {
+        double r = z1[i] > 0.0 ? z1[i] : 0.0;
+        a1[i] = bf16 ? orc_bf16(r) : r;
+    }
+    conv3(W2, b2, 16, 16, S1, a1, z2);
+    for (int i = 0; i < 16 * S2 * S2; ++i) {
+        double r = z2[i] > 0.0 ? z2[i] : 0.0;
+        a2[i] = bf16 ? orc_bf16(r) : r;
+    }
+    conv3(W3, b3, 16, 1, S2, a2, logits);
+}
+
+int orc_net_forward(int k, const double* w, const double* input, int bf16, double* logits) {
+    if (k < 1 || k > 8) return -1;
+    int P = k + 6, S1 = k + 4, S2 = k + 2;
+    double* buf = (double*)malloc(sizeof(double) * (ORC_NET_PARAMS + 6 * P * P + 32 * S1 * S1 + 32 * S2 * S2));
+    if (!buf) return -2;
+    double* wr = buf;
+    double* in_r = wr + ORC_NET_PARAMS;
+    double* z1 = in_r + 6 * P * P;
+    double* a1 = z1 + 16 * S1 * S1;
+    double* z2 = a1 + 16 * S1 * S1;
+    double* a2 = z2 + 16 * S2 * S2;
+    net_weights(w, bf16, wr);
+    net_forward_full(k, wr, input, bf16, in_r, z1, a1, z2, a2, logits);
+    free(buf);
+    return 0;
+}
+
+/* Mean binary cross-entropy of q = sigmoid(logit) against the block bits
+ * (target +1 -> 1) over n examples, and its gradient with respect to the
+ * parameters by back-propagation (the bf16 roundings pass gradients
+ * straight through). */
+int orc_net_loss_grad(int k, const double* w, const double* inputs, const int8_t* targets, int n,
+                      int bf16, double* loss, double* grad) {
+    if (k < 1 || k > 8 || n < 1) return -1;
+    int P = k + 6, S1 = k + 4, S2 = k + 2, K2 = k * k;
+    size_t need = ORC_NET_PARAMS + 6 * P * P + 64 * S1 * S1 + 64 * S2 * S2 + 2 * K2;
+    double* buf = (double*)calloc(need, sizeof(double));
+    if (!buf) return -2;
+    double* wr = buf;
+    double* in_r = wr + ORC_NET_PARAMS;
+    double* z1 = in_r + 6 * P * P;
+    double* a1 = z1 + 16 * S1 * S1;
+    double* d1 = a1 + 16 * S1 * S1;
+    double* z2 = d1 + 16 * S1 * S1;
+    double* a2 = z2 + 16 * S2 * S2;
+    double* d2 = a2 + 16 * S2 * S2;
+    double* logit = d2 + 16 * S2 * S2;
+    double* dl = logit + K2;
+    net_weights(w, bf16, wr);
+    const double *W2 = wr + 880, *W3 = wr + 3200;
+    for (int i = 0; i < ORC_NET_PARAMS; ++i) grad[i] = 0.0;
+    double L_sum = 0.0;
+    for (int e = 0; e < n; ++e) {
+        net_forward_full(k, wr, inputs + (size_t)e * 6 * P * P, bf16, in_r, z1, a1, z2, a2, logit);
+        for (int s = 0; s < K2; ++s) {
+            double y = targets[(size_t)e * K2 + s] > 0 ? 1.0 : 0.0;
+            double z = logit[s];
+            /* BCE(sigmoid(z), y) = softplus(z) - y z, evaluated stably */
+            double sp = z > 0 ? z + log1p(exp(-z)) : log1p(exp(z));
+            L_sum += sp - y * z;
+            dl[s] = (1.0 / (1.0 + exp(-z)) - y) / ((double)n * K2);
+        }
+        /* layer 3 */
+        for (int s = 0; s < K2; ++s) {
+            int y = s / k, x = s % k;
+            grad[3344] += dl[s];
+            for (int c = 0; c < 16; ++c)
+                for (int ky = 0; ky < 3; ++ky)
+                    for (int kx = 0; kx < 3; ++kx)
+                        grad[3200 + (c * 3 + ky) * 3 + kx] += dl[s] * a2[(c * S2 + y + ky) * S2 + x + kx];
+        }
+        for (int i = 0; i < 16 * S2 * S2; ++i) d2[i] = 0.0;
+        for (int s = 0; s < K2; ++s) {
+            int y = s / k, x = s % k;
+            for (int c = 0; c < 16; ++c)
+                for (int ky = 0; ky < 3; ++ky)
+                    for (int kx = 0; kx < 3; ++kx)
+                        d2[(c * S2 + y + ky) * S2 + x + kx] += dl[s] * W3[(c * 3 + ky) * 3 + kx];
+        }
+        for (int i = 0; i < 16 * S2 * S2; ++i)
+            if (!(z2[i] > 0.0)) d2[i] = 0.0;
+        /* layer 2 */
+        for (int o = 0; o < 16; ++o)
+            for (int y = 0; y < S2; ++y)
+                for (int x = 0; x < S2; ++x) {
+                    double g = d2[(o * S2 + y) * S2 + x];
+                    if (g == 0.0) continue;
+                    grad[3184 + o] += g;
+                    for (int c = 0; c < 16; ++c)
+                        for (int ky = 0; ky < 3; ++ky)
+                            for (int kx = 0; kx < 3; ++kx)
+                                grad[880 + ((o * 16 + c) * 3 + ky) * 3 + kx] += g * a1[(c * S1 + y + ky) * S1 + x + kx];
+                }
+        for (int i = 0; i < 16 * S1 * S1; ++i) d1[i] = 0.0;
+        for (int o = 0; o < 16; ++o)
+            for (int y = 0; y < S2; ++y)
+                for (int x = 0; x < S2; ++x) {
+                    double g = d2[(o * S2 + y) * S2 + x];
+                    if (g == 0.0) continue;
+                    for (int c = 0; c < 16; ++c)
+                        for (int ky = 0; ky < 3; ++ky)
+                            for (int kx = 0; kx < 3; ++kx)
+                                d1[(c * S1 + y + ky) * S1 + x + kx] += g * W2[((o * 16 + c) * 3 + ky) * 3 + kx];
+                }
+        for (int i = 0; i < 16 * S1 * S1; ++i)
+            if (!(z1[i] > 0.0)) d1[i] = 0.0;
+        /* layer 1 */
+        for (int o = 0; o < 16; ++o)
+            for (int y = 0; y < S1; ++y)
+                for (int x = 0; x < S1; ++x) {
+                    double g = d1[(o * S1 + y) * S1 + x];
+                    if (g == 0.0) continue;
+                    grad[864 + o] += g;
+                    for (int c = 0; c < 6; ++c)
+                        for (int ky = 0; ky < 3; ++ky)
+                            for (int kx = 0; kx < 3; ++kx)
+                                grad[((o * 6 + c) * 3 + ky) * 3 + kx] += g * in_r[(c * P + y + ky) * P + x + kx];
+                }
+    }
+    *loss = L_sum / ((double)n * K2);
+    free(buf);
+    return 0;
+}
+
+/* Exact energy difference (1/16 units) of replacing block (bR, bC) of v by
+ * newblock[k*k] (+-1), canonical SS lattice (even L, periodic): bonds with at
+ * least one endpoint in the block and the field term of the block sites. */
+static int diag_partner(int L, int R, int C) {
+    int r = R & 1, c = C & 1, R2, C2;
+    if (!r && !c) { R2 = R + 1; C2 = C + 1; }        /* "\" dimer, upper end */
+    else if (r && c) { R2 = R - 1; C2 = C - 1; }     /* "\" dimer, lower end */
+    else if (r && !c) { R2 = R + 1; C2 = C - 1; }    /* "/" dimer, upper end */
+    else { R2 = R - 1; C2 = C + 1; }                 /* "/" dimer, lower end */
+    R2 = (R2 % L + L) % L;
+    C2 = (C2 % L + L) % L;
+    return R2 * L + C2;
+}
+
+int64_t orc_block_delta_e(int L, const int8_t* v, int bR, int bC, int k, const int8_t* newblock,
+                          int32_t qJ, int32_t qJp, int32_t qh) {
+    int N = L * L;
+    int8_t* w = (int8_t*)malloc((size_t)N);
+    memcpy(w, v, (size_t)N);
+    for (int a = 0; a < k; ++a)
+        for (int b = 0; b < k; ++b) w[((bR + a) % L) * L + (bC + b) % L] = newblock[a * k + b];
+    int64_t d = 0;
+    for (int s = 0; s < N; ++s) {
+        int R = s / L, C = s % L;
+        int nbr[3] = {R * L + (C + 1) % L, ((R + 1) % L) * L + C, -1};
+        int dp = diag_partner(L, R, C);
+        if (dp > s) nbr[2] = dp; /* count each dimer once */
+        for (int t = 0; t < 3; ++t) {
+            if (nbr[t] < 0) continue;
+            int e0 = v[s] * v[nbr[t]], e1 = w[s] * w[nbr[t]];
+            d += (int64_t)(t < 2 ? qJ : qJp) * (e1 - e0);
+        }
+        d -= (int64_t)qh * (w[s] - v[s]);
+    }
+    free(w);
+    return d;
+}
+
+/* One Metropolis-Hastings block move from configuration v: probs[b] (b =
+ * the k*k bits of the proposed block, bit a*k+b'' set = +1) is the exact
+ * probability of moving to that block value; the entry of the current value
+ * also holds the rejection mass. */
+int orc_mh_row(int L, const int8_t* v, int bR, int bC, int k, const double* w, double J, double Jp,
+               double h, double beta, int bf16, double* probs) {
+    if (k < 1 || k > 4 || (L & 1)) return -1;
+    int P = k + 6, K2 = k * k;
+    int32_t qJ, qJp, qh;
+    if (orc_quantize(J, &qJ) || orc_quantize(Jp, &qJp) || orc_quantize(h, &qh)) return -1;
+    double* input = (double*)malloc(sizeof(double) * 6 * P * P);
+    double logit[16];
+    orc_patch_input(L, v, bR, bC, k, bf16 ? orc_bf16(beta) : beta, bf16 ? orc_bf16(h) : h, input);
+    orc_net_forward(k, w, input, bf16, logit);
+    free(input);
+    double p[16];
+    for (int s = 0; s < K2; ++s) {
+        double q = 1.0 / (1.0 + exp(-logit[s]));
+        double t = nearbyint(ldexp(q, 32));
+        if (t < 1.0) t = 1.0;
+        if (t > 4294967295.0) t = 4294967295.0;
+        p[s] = ldexp(t, -32);
+    }
+    int cur = 0;
+    for (int s = 0; s < K2; ++s)
+        if (v[((bR + s / k) % L) * L + (bC + s % k) % L] > 0) cur |= 1 << s;
+    double logq_cur = 0.0;
+    for (int s = 0; s < K2; ++s) logq_cur += ((cur >> s) & 1) ? log(p[s]) : log1p(-p[s]);
+    double stay = 1.0;
+    int8_t nb[16];
+    for (int b = 0; b < (1 << K2); ++b) {
+        probs[b] = 0.0;
+        if (b == cur) continue;
+        double logq = 0.0;
+        for (int s = 0; s < K2; ++s) {
+            nb[s] = ((b >> s) & 1) ? 1 : -1;
+            logq += ((b >> s) & 1) ? log(p[s]) : log1p(-p[s]);
+        }
+        int64_t dE = orc_block_delta_e(L, v, bR, bC, k, nb, qJ, qJp, qh);
+        double loga = -beta * (double)dE / 16.0 + logq_cur - logq;
+        double acc = loga >= 0.0 ? 1.0 : exp(loga);
+        probs[b] = exp(logq) * acc;
+        stay -= probs[b];
+    }
+    probs[cur] = stay;
+    return 0;
+}
+
+/* orc_mh_row over many configurations v[n][L*L] (rows probs[n][2^(k*k)]). */
+int orc_mh_rows(int L, const int8_t* v, int n, int bR, int bC, int k, const double* w, double J,
+                double Jp, double h, double beta, int bf16, double* probs) {
+    int err = 0;
+#pragma omp parallel for schedule(static)
+    for (int i = 0; i < n; ++i)
+        if (orc_mh_row(L, v + (size_t)i * L * L, bR, bC, k, w, J, Jp, h, beta, bf16,
+                       probs + ((size_t)i << (k * k))))
+            err = 1;
+    return err ? -1 : 0;
+}

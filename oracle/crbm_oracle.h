@@ -126,3 +126,37 @@ uint32_t orc_swap_threshold(double x);
 #ifdef __cplusplus
 }
 #endif
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+/* ---- learned block proposal (test infrastructure) ------------------------
+ * A k x k block of spins at origin (bR, bC) is proposed from a small conv net
+ * over the (k+6) x (k+6) patch around it (periodic):
+ *   input channels: 0 spin (0 inside the block), 1 block mask, 2 row parity,
+ *                   3 column parity, 4 beta, 5 h;
+ *   three valid 3x3 convolutions 6->16->16->1 with ReLU after the first two,
+ *   one logit per block site, q_s = sigmoid(logit) = P(spin s = +1).
+ * Parameters (ORC_NET_PARAMS doubles): W1[16][6][3][3], b1[16],
+ * W2[16][16][3][3], b2[16], W3[16][3][3], b3.
+ * With bf16 != 0, weights and inputs are rounded to bfloat16 (round to
+ * nearest even) and so are the two hidden activations (the GPU's storage
+ * precision); accumulation is in double.  The proposal draws each site with
+ * probability t_s / 2^32, t_s = clamp(nearbyint(q_s 2^32), 1, 2^32 - 1), and
+ * the move is accepted with probability
+ * min(1, exp(-beta dE / 16) q(x_B) / q(x'_B)) on the exact integer energy
+ * difference dE (1/16 units) of the canonical SS lattice (even L, periodic). */
+#define ORC_NET_PARAMS 3345
+double orc_bf16(double x);
+int orc_patch_input(int L, const int8_t* v, int bR, int bC, int k, double beta, double h,
+                    double* input);
+int orc_net_forward(int k, const double* w, const double* input, int bf16, double* logits);
+int orc_net_loss_grad(int k, const double* w, const double* inputs, const int8_t* targets, int n,
+                      int bf16, double* loss, double* grad);
+int64_t orc_block_delta_e(int L, const int8_t* v, int bR, int bC, int k, const int8_t* newblock,
+                          int32_t qJ, int32_t qJp, int32_t qh);
+int orc_mh_row(int L, const int8_t* v, int bR, int bC, int k, const double* w, double J,
+               double Jp, double h, double beta, int bf16, double* probs);
+#ifdef __cplusplus
+}
+#endif

@@ -211,6 +211,58 @@ int crbm_batch_threads(const crbm_batch* batch);
 const char* crbm_batch_last_error(const crbm_batch* batch);
 void crbm_batch_destroy(crbm_batch* batch);
 
+/* ---- Learned block proposal --------------------------------------------
+ * A k x k block (k = 4) of spins is proposed from a small convolutional net
+ * over the (k+6) x (k+6) periodic patch around it: input channels spin (0
+ * inside the block), block mask, row parity, column parity, beta, h; three
+ * valid 3x3 convolutions 6 -> 16 -> 16 -> 1 with ReLU; one logit per block
+ * site, q = sigmoid(logit) = P(+1).  Weights and activations are bfloat16,
+ * accumulation fp32.  The net never sees the block's own spins, so forward
+ * and reverse proposal probabilities are exact and each move passes a
+ * Metropolis-Hastings test min(1, exp(-beta dE/16) q(x)/q(x')) on the exact
+ * integer energy difference dE (1/16 units).  A pass moves blocks at least 8
+ * sites apart (max(1, L/8) per side, random offset), one per 32-chain word
+ * and block per CTA.  Not a method of the paper: a learned proposal mixed
+ * with its block Gibbs sweeps, judged by it (observables within standard
+ * errors) and trained on configurations it generates.
+ * Parameter order (3345 floats): W1[16][6][3][3], b1[16], W2[16][16][3][3],
+ * b2[16], W3[16][3][3], b3.
+ * Contexts used with proposals need the ten SS filters, an even periodic
+ * lattice, the SMEM layout and no replica exchange (else CRBM_EUNSUPPORTED).
+ * Errors of these functions: see crbm_proposal_last_error(). */
+typedef struct crbm_proposal crbm_proposal;
+typedef struct {
+    float logit[16];
+    int32_t dE;               /* exact energy change of the proposed block, 1/16 units */
+    uint32_t cur_bits, new_bits; /* bit s = site (s / 4, s % 4) of the block is +1 */
+    float log_alpha;
+    int32_t bR, bC;           /* block origin */
+} crbm_pass_record;
+/* New net with seeded He-style weights; block must be 4. */
+int crbm_proposal_create(crbm_proposal** out, int32_t block, uint64_t seed);
+void crbm_proposal_destroy(crbm_proposal* p);
+int crbm_proposal_set_weights(crbm_proposal* p, const float* w, size_t n);
+int crbm_proposal_get_weights(crbm_proposal* p, float* w, size_t n);
+/* Train on the GPU: per step, crbm_sweep(ctx, sweeps_between), draw `batch`
+ * (chain, block) examples from ctx's current configurations, back-propagate
+ * the mean binary cross-entropy of q against the blocks' spins, Adam step
+ * (lr).  losses[steps] (may be NULL) receives the batch losses. */
+int crbm_proposal_train(crbm_proposal* p, crbm_ctx* ctx, int32_t steps, int32_t batch, float lr,
+                        int32_t sweeps_between, float* losses);
+/* Loss and gradient (fp32, GPU) on given examples: host spins[n][L*L] (+-1),
+ * block origins[n][2], beta_h[n][2]; grad[3345]. */
+int crbm_proposal_loss_grad(crbm_proposal* p, const int8_t* spins, int32_t L, const int32_t* origins,
+                            const float* beta_h, int32_t n, float* loss, float* grad);
+/* n_passes passes of block moves (asynchronous). */
+int crbm_proposal_pass(crbm_ctx* ctx, crbm_proposal* p, int64_t n_passes);
+/* n_sweeps times: one Gibbs sweep, then one pass of block moves. */
+int crbm_sweep_mixed(crbm_ctx* ctx, crbm_proposal* p, int64_t n_sweeps);
+/* The next pass, evaluated without moving: records out[n_words][n_blocks][32]. */
+int crbm_proposal_inspect(crbm_ctx* ctx, crbm_proposal* p, crbm_pass_record* out, size_t n_out);
+/* Cumulative proposed / accepted block moves of p. */
+int crbm_proposal_stats(crbm_proposal* p, int64_t* proposed, int64_t* accepted);
+const char* crbm_proposal_last_error(void);
+
 /* Size of the fixed device scratch array of crbm_sweep_stream_noalloc. */
 #define CRBM_NOALLOC_SCRATCH_BYTES (32u << 20)
 

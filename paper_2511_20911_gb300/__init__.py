@@ -32,6 +32,10 @@ ABI_FUNCTIONS = (
     "crbm_get_spins", "crbm_set_spins", "crbm_get_tables", "crbm_get_permutation", "crbm_layout",
     "crbm_launch_count", "crbm_autotune", "crbm_warps", "crbm_batch_create", "crbm_batch_sweep",
     "crbm_batch_threads", "crbm_batch_last_error", "crbm_batch_destroy",
+    "crbm_proposal_create", "crbm_proposal_destroy", "crbm_proposal_set_weights",
+    "crbm_proposal_get_weights", "crbm_proposal_train", "crbm_proposal_loss_grad",
+    "crbm_proposal_pass", "crbm_sweep_mixed", "crbm_proposal_inspect", "crbm_proposal_stats",
+    "crbm_proposal_last_error",
     "crbm_save", "crbm_load", "crbm_philox", "crbm_sweep_stream_noalloc", "crbm_last_error",
 )
 
@@ -95,6 +99,20 @@ def load_library(path: str | None = None):
         "crbm_batch_threads": (c.c_int, [vp]),
         "crbm_batch_last_error": (c.c_char_p, [vp]),
         "crbm_batch_destroy": (None, [vp]),
+        "crbm_proposal_create": (c.c_int, [c.POINTER(vp), c.c_int32, c.c_uint64]),
+        "crbm_proposal_destroy": (None, [vp]),
+        "crbm_proposal_set_weights": (c.c_int, [vp, c.POINTER(c.c_float), c.c_size_t]),
+        "crbm_proposal_get_weights": (c.c_int, [vp, c.POINTER(c.c_float), c.c_size_t]),
+        "crbm_proposal_train": (c.c_int, [vp, vp, c.c_int32, c.c_int32, c.c_float, c.c_int32,
+                                          c.POINTER(c.c_float)]),
+        "crbm_proposal_loss_grad": (c.c_int, [vp, c.POINTER(c.c_int8), c.c_int32, c.POINTER(c.c_int32),
+                                              c.POINTER(c.c_float), c.c_int32, c.POINTER(c.c_float),
+                                              c.POINTER(c.c_float)]),
+        "crbm_proposal_pass": (c.c_int, [vp, vp, c.c_int64]),
+        "crbm_sweep_mixed": (c.c_int, [vp, vp, c.c_int64]),
+        "crbm_proposal_inspect": (c.c_int, [vp, vp, vp, c.c_size_t]),
+        "crbm_proposal_stats": (c.c_int, [vp, c.POINTER(c.c_int64), c.POINTER(c.c_int64)]),
+        "crbm_proposal_last_error": (c.c_char_p, []),
         "crbm_launch_count": (c.c_int64, [vp]),
         "crbm_save": (c.c_int, [vp, vp, c.POINTER(c.c_size_t)]),
         "crbm_load": (c.c_int, [vp, vp, c.c_size_t]),
@@ -307,6 +325,86 @@ class Batch:
             self.close()
         except Exception:
             pass
+
+
+NET_PARAMS = 3345
+PASS_RECORD = np.dtype([("logit", np.float32, 16), ("dE", np.int32), ("cur_bits", np.uint32),
+                        ("new_bits", np.uint32), ("log_alpha", np.float32), ("bR", np.int32),
+                        ("bC", np.int32)])
+
+
+class Proposal:
+    """Learned 4x4 block proposal (crbm_proposal_*): a conv net trained on the
+    GPU on the sampler's own configurations, used in exact MH block moves."""
+
+    def __init__(self, seed=0, block=4):
+        lib = load_library()
+        h = ctypes.c_void_p()
+        self._lib = lib
+        self._chk(lib.crbm_proposal_create(ctypes.byref(h), int(block), int(seed)))
+        self._p = h
+
+    def _chk(self, rc):
+        if rc != CRBM_OK:
+            raise CrbmError(rc, (self._lib.crbm_proposal_last_error() or b"").decode())
+
+    def close(self):
+        if getattr(self, "_p", None):
+            self._lib.crbm_proposal_destroy(self._p)
+            self._p = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    @property
+    def weights(self):
+        w = np.zeros(NET_PARAMS, np.float32)
+        self._chk(self._lib.crbm_proposal_get_weights(self._p, _ptr(w, ctypes.c_float), w.size))
+        return w
+
+    @weights.setter
+    def weights(self, w):
+        w = np.ascontiguousarray(w, np.float32)
+        self._chk(self._lib.crbm_proposal_set_weights(self._p, _ptr(w, ctypes.c_float), w.size))
+
+    def train(self, sampler, steps, batch=2048, lr=3e-3, sweeps_between=2):
+        losses = np.zeros(max(1, steps), np.float32)
+        self._chk(self._lib.crbm_proposal_train(self._p, sampler._ctx, int(steps), int(batch), float(lr),
+                                                int(sweeps_between), _ptr(losses, ctypes.c_float)))
+        return losses[:steps]
+
+    def loss_grad(self, spins, origins, beta_h):
+        s = np.ascontiguousarray(spins, np.int8)
+        o = np.ascontiguousarray(origins, np.int32)
+        bh = np.ascontiguousarray(beta_h, np.float32)
+        grad = np.zeros(NET_PARAMS, np.float32)
+        loss = ctypes.c_float()
+        self._chk(self._lib.crbm_proposal_loss_grad(self._p, _ptr(s, ctypes.c_int8), s.shape[-1],
+                                                    _ptr(o, ctypes.c_int32), _ptr(bh, ctypes.c_float),
+                                                    len(o), ctypes.byref(loss), _ptr(grad, ctypes.c_float)))
+        return loss.value, grad
+
+    def passes(self, sampler, n):
+        self._chk(self._lib.crbm_proposal_pass(sampler._ctx, self._p, int(n)))
+
+    def sweep_mixed(self, sampler, n):
+        self._chk(self._lib.crbm_sweep_mixed(sampler._ctx, self._p, int(n)))
+
+    def inspect(self, sampler):
+        nb1 = max(1, sampler.L // 8)
+        n_words = (sampler.n_chains + 31) // 32
+        out = np.zeros(n_words * nb1 * nb1 * 32, PASS_RECORD)
+        self._chk(self._lib.crbm_proposal_inspect(sampler._ctx, self._p,
+                                                  out.ctypes.data_as(ctypes.c_void_p), out.size))
+        return out.reshape(n_words, nb1 * nb1, 32)
+
+    def stats(self):
+        a, b = ctypes.c_int64(), ctypes.c_int64()
+        self._chk(self._lib.crbm_proposal_stats(self._p, ctypes.byref(a), ctypes.byref(b)))
+        return a.value, b.value
 
 
 def crbm_philox(inputs):

@@ -19,6 +19,7 @@ struct crbm_ctx {
     int64_t meas = 0;       // measurements since the last reset
     int64_t sq_meas = 0;    // correlation samples since the last reset
     int64_t launches = 0;
+    int64_t passes = 0;     // block-proposal passes (Philox sweep slot of the moves)
     cudaStream_t stream = nullptr;
     int device = 0;
     std::vector<int32_t> chain_param;

@@ -184,7 +184,7 @@ int dalloc(crbm_ctx* ctx, T*& ptr, size_t count) {
 void free_device(DeviceState& d) {
     void* ptrs[] = {d.v, d.tab, d.ctab, d.sneg, d.inc, d.inc_off, d.sums, d.series, d.corr,
                     d.seg, d.segmask, d.spins8, d.h, d.cnt, d.err, d.sob, d.swap_tab, d.swap_off,
-                    d.swap_len, d.wq};
+                    d.swap_len, d.wq, d.chain_bh, d.chain_q};
     for (void* p : ptrs)
         if (p) cudaFree(p);
     d = DeviceState{};

@@ -72,6 +72,8 @@ struct DeviceState {
     int32_t* wq = nullptr;        // [n_words][3] Q.4 couplings (J, J', h) of each word
     uint32_t* h = nullptr;        // streamed layout: [n_words][n_cells][10] hidden words
     int* cnt = nullptr;           // streamed layout: [n_words * 32][3] measurement counts
+    float* chain_bh = nullptr;    // block proposals: [n_words * 32][2] beta, h (bf16-rounded)
+    int32_t* chain_q = nullptr;   // block proposals: [n_words * 32][3] Q.4 J, J', h
     int* err = nullptr;           // device error word
 };
 

@@ -71,3 +71,25 @@ def tempering_batch_workload(sizes=(6, 9, 12, 18, 24, 48), ladders=8, b_lo=0.2, 
                             chain_param=np.tile(np.arange(32, dtype=np.int32), ladders),
                             seed=1000 + L, swap_every=10))
     return members
+
+
+def proposal_training_workload(L=18, n_chains=4096, betas=(1.5, 2.0, 2.5, 3.0),
+                               hs=(2.5, 2.75, 3.0, 3.25, 3.5)):
+    """Training configurations for the block proposal: J'/J = 1, beta in
+    [1.5, 3], h around the 1/3 magnetisation plateau (J2 = J1, h near 3)."""
+    pts = [(b, h) for b in betas for h in hs]
+    params = dict(J=[1.0] * len(pts), Jp=[1.0] * len(pts), h=[h for _, h in pts],
+                  beta=[b for b, _ in pts])
+    return dict(L=L, params=params, n_chains=n_chains,
+                chain_param=(np.arange(n_chains) * len(pts) // n_chains).astype(np.int32),
+                seed=55, measure_every=0)
+
+
+def proposal_eval_workload(L, n_chains=4096, betas=(1.5, 2.0, 3.0), h=3.0):
+    """Evaluation points of the block proposal: J'/J = 1, h = 3, beta in
+    {1.5, 2, 3}."""
+    params = dict(J=[1.0] * len(betas), Jp=[1.0] * len(betas), h=[h] * len(betas),
+                  beta=list(betas))
+    return dict(L=L, params=params, n_chains=n_chains,
+                chain_param=(np.arange(n_chains) * len(betas) // n_chains).astype(np.int32),
+                seed=77)

@@ -47,7 +47,7 @@ def parse():
     ap.add_argument("--steps", type=int, default=10)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
-    ap.add_argument("--workload", default="grid", choices=["grid", "stream", "batch"])
+    ap.add_argument("--workload", default="grid", choices=["grid", "stream", "batch", "proposal"])
     ap.add_argument("--sweeps-per-step", type=int, default=None)
     ap.add_argument("--measure-every", type=int, default=10)
     ap.add_argument("--cpu-seconds", type=float, default=8.0)
@@ -115,7 +115,7 @@ def workload_config(name, rank):
     return w
 
 
-DEFAULT_SWEEPS = {"grid": 2000, "stream": 20, "batch": 500}
+DEFAULT_SWEEPS = {"grid": 2000, "stream": 20, "batch": 500, "proposal": 1000}
 
 
 def cpu_baseline(w, seconds):
@@ -258,6 +258,80 @@ def run_batch(args, rank, ws):
         print(json.dumps(out))
 
 
+def run_proposal(args, rank, ws):
+    """Learned block proposal: train it on the GPU on configurations the
+    sampler generates (L=18, J'/J=1, beta in [1.5,3], h in [2.5,3.5]), then
+    compare effective samples per second of E and m, plain Gibbs against
+    Gibbs + one block-move pass per sweep, from the same equilibrated state,
+    at L=18 and L=48 (J'/J=1, h=3, beta in {1.5,2,3}, 4096 chains)."""
+    import torch
+    import paper_2511_20911_gb300 as crbm
+    from paper_2511_20911_gb300 import analysis, workloads
+    T = args.sweeps_per_step
+    tw = workloads.proposal_training_workload()
+    src = crbm.Sampler(**tw)
+    src.sweep(500)
+    prop = crbm.Proposal(seed=2024 + rank)
+    t0 = time.perf_counter()
+    losses = prop.train(src, steps=400, batch=4096, lr=1e-2, sweeps_between=2)
+    torch.cuda.synchronize()
+    train_s = time.perf_counter() - t0
+    stream = torch.cuda.current_stream()
+    results = []
+    for L, burn in ((18, 20000), (48, 6000)):
+        ew = workloads.proposal_eval_workload(L)
+        base = crbm.Sampler(**dict(ew, measure_every=1, series_len=T))
+        base.sweep(burn)
+        ck = base.save()
+        cp = np.asarray(ew["chain_param"])
+        out = {}
+        for mode in ("plain", "mixed"):
+            s = crbm.Sampler(**dict(ew, measure_every=1, series_len=T))
+            s.load(ck)
+            s.reset_observables()
+            p0 = prop.stats()
+            a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            torch.cuda.synchronize()
+            a.record(stream)
+            if mode == "plain":
+                s.sweep(T)
+            else:
+                prop.sweep_mixed(s, T)
+            b.record(stream)
+            torch.cuda.synchronize()
+            sec = a.elapsed_time(b) / 1e3
+            p1 = prop.stats()
+            ser = s.series().transpose(1, 0, 2)                    # [chain][T][3]
+            E = ser[..., 0] + ser[..., 1] - 3.0 * ser[..., 2]       # J = J' = 1, h = 3
+            M = ser[..., 2].astype(np.float64)
+            essE, essM = analysis.effective_samples(E), analysis.effective_samples(M)
+            half = E.shape[1] // 2
+            drift = [float((E[cp == g][:, half:].mean() - E[cp == g][:, :half].mean()) / (16 * L * L) * 16)
+                     for g in range(3)]
+            out[mode] = {"seconds": sec, "sweeps": T, "e_drift_second_minus_first_half": drift,
+                         "ess_per_s_E": [float(essE[cp == g].sum() / sec) for g in range(3)],
+                         "ess_per_s_m": [float(essM[cp == g].sum() / sec) for g in range(3)],
+                         "e_per_spin": [float(E[cp == g].mean() / (16 * L * L) * 16) for g in range(3)],
+                         "accept": (p1[1] - p0[1]) / max(1, p1[0] - p0[0]) if mode == "mixed" else None}
+        gain_E = [m / p if p > 0 else None for m, p in zip(out["mixed"]["ess_per_s_E"], out["plain"]["ess_per_s_E"])]
+        gain_m = [m / p if p > 0 else None for m, p in zip(out["mixed"]["ess_per_s_m"], out["plain"]["ess_per_s_m"])]
+        results.append({"L": L, "beta": ew["params"]["beta"], "h": 3.0, "plain": out["plain"],
+                        "mixed": out["mixed"], "ess_per_s_gain_E": gain_E, "ess_per_s_gain_m": gain_m})
+    mixed_rate = sum(sum(r["mixed"]["ess_per_s_E"]) for r in results)
+    line = {"metric": METRIC, "value": mixed_rate, "unit": "effective samples/s (E, mixed sampler)",
+            "n_gpus": ws, "steps": 1, "warmup": 0, "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "bf16+u32", "data": "synthetic",
+            "config": {"workload": "learned 4x4 block proposal (3x3 conv net 6-16-16-1, bf16/fp32, "
+                                   "mma.sync) + Gibbs vs plain Gibbs, J'/J=1, h=3, beta in {1.5,2,3}, "
+                                   "L in {18,48}, 4096 chains, from one equilibrated state",
+                       "sweeps": T, "train_steps": 400, "train_batch": 4096},
+           "train": {"seconds": train_s, "loss_first": float(losses[:5].mean()),
+                     "loss_last": float(losses[-20:].mean())},
+           "results": results}
+    if rank == 0:
+        print(json.dumps(line))
+
+
 def main():
     args = parse()
     if args.sweeps_per_step is None:
@@ -268,6 +342,9 @@ def main():
         return
     if args.workload == "batch":
         run_batch(args, rank, ws)
+        return
+    if args.workload == "proposal":
+        run_proposal(args, rank, ws)
         return
     import torch
     import paper_2511_20911_gb300 as crbm

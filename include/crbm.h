@@ -56,7 +56,7 @@ extern "C" {
 #define CRBM_NSUM 11 /* per-chain observable sums, see crbm_observables */
 
 /* Layout of a context's lattice state on the device. */
-#define CRBM_LAYOUT_AUTO 0   /* SMEM for L <= CRBM_SMEM_MAX_L, else STREAM */
+#define CRBM_LAYOUT_AUTO 0   /* SMEM when it fits one CTA (L <= CRBM_SMEM_MAX_L), else STREAM */
 #define CRBM_LAYOUT_SMEM 1   /* whole lattice resident in shared memory */
 #define CRBM_LAYOUT_STREAM 2 /* lattice in HBM, one tiled launch per sweep */
 #define CRBM_SMEM_MAX_L 96
@@ -284,7 +284,7 @@ const char* crbm_proposal_last_error(void);
  *
  * Scratch: one static device array of CRBM_NOALLOC_SCRATCH_BYTES per GPU that
  * loads the library, held until exit; it takes the lane threshold tables and
- * the hidden words, 4 * n_words * (4352 + 10 (L/2)^2) bytes with
+ * the lanes' hidden words, 4 * n_words * (4352 + 32 (L/2)^2) bytes with
  * n_words = 2 ceil(n_chains / 64).  Larger requests return
  * CRBM_EUNSUPPORTED.  Every call shares the array and leaves its contents
  * behind (each call rewrites all of it that it reads), so calls that overlap

@@ -20,8 +20,8 @@ __device__ __forceinline__ void sweep_canon_body(const SweepArgs& a, int word) {
     uint32_t* s_th = smem;                      // [2][4][32]
     uint32_t* s_tv = smem + kCanonTh;           // [4][32][32]
     uint32_t* s_v = smem + kCanonTab;           // [N]
-    uint32_t* s_h = s_v + g.N;                  // [n_cells][10]
-    int* s_cnt = reinterpret_cast<int*>(s_h + g.n_cells * 10);   // [3][32]
+    uint32_t* s_w = s_v + g.N;                  // [n_cells][32] per-lane hidden words
+    int* s_cnt = reinterpret_cast<int*>(s_w + g.n_cells * 32);   // [3][32]
     int* s_seg = s_cnt + 96;                                      // [33]
     uint32_t* s_segmask = reinterpret_cast<uint32_t*>(s_seg + 33); // [32]
     int* s_sob = reinterpret_cast<int*>(s_segmask + 32);          // [32] slot of each rung
@@ -37,11 +37,7 @@ __device__ __forceinline__ void sweep_canon_body(const SweepArgs& a, int word) {
         for (int x = threadIdx.x; x < 32; x += blockDim.x) s_segmask[x] = a.segmask[word * 32 + x];
     }
     const uint32_t chain = static_cast<uint32_t>(word) * 32u + lane;
-    LaneConst lc;
-    lc.lm = 1u << lane;
-    lc.lb = 4u * lane;
-#pragma unroll
-    for (int s = 0; s < 5; ++s) lc.rot[s] = static_cast<uint32_t>(lane - 7 - s) & 31u;
+    LaneConst lc = lane_const(lane, lane);
     const Round0Lane r0l = round0_lane(chain);
     if (warp == 0) {  // replica permutation (identity without tempering)
         const int sob = a.swap_every > 0 ? a.sob[word * 32 + lane] : lane;
@@ -70,9 +66,10 @@ __device__ __forceinline__ void sweep_canon_body(const SweepArgs& a, int word) {
         int i = i_first, j = j_first;
         for (int cell = warp; cell < g.n_cells; cell += nwarp) {
             const int R0 = 2 * i * L, C0 = 2 * j;
-            hidden_cell(s_v, R0, R0 + L, (2 * i + 2 == L) ? 0 : R0 + 2 * L, C0, C0 + 1,
-                        (C0 + 2 == L) ? 0 : C0 + 2, s_h + cell * 10, s_th, X, r0l.lo,
-                        round0_cell(static_cast<uint32_t>(cell), a.rk[1]), a.rk, lc);
+            s_w[cell * 32 + lane] =
+                hidden_cell(s_v, R0, R0 + L, (2 * i + 2 == L) ? 0 : R0 + 2 * L, C0, C0 + 1,
+                            (C0 + 2 == L) ? 0 : C0 + 2, s_th, X, r0l.lo,
+                            round0_cell(static_cast<uint32_t>(cell), a.rk[1]), a.rk, lc);
             i += di;
             j += dj;
             if (j >= W) {
@@ -86,8 +83,8 @@ __device__ __forceinline__ void sweep_canon_body(const SweepArgs& a, int word) {
         for (int cell = warp; cell < g.n_cells; cell += nwarp) {
             const int iu = (i == 0) ? W - 1 : i - 1;
             const int jl = (j == 0) ? W - 1 : j - 1;
-            visible_cell(s_v + 2 * i * L + 2 * j, L, s_h + cell * 10, s_h + (iu * W + j) * 10,
-                         s_h + (i * W + jl) * 10, s_tv, X, r0l.lo,
+            visible_cell(s_v + 2 * i * L + 2 * j, L, s_w[cell * 32 + lane], s_w[(iu * W + j) * 32 + lane],
+                         s_w[(i * W + jl) * 32 + lane], s_tv, X, r0l.lo,
                          round0_cell(static_cast<uint32_t>(cell), a.rk[1]), a.rk, lc);
             i += di;
             j += dj;

@@ -1,14 +1,26 @@
 // Per-cell cores of the canonical SS fast path (the ten filters of Fig. 1 on
 // an even, periodic lattice), shared by the SMEM-resident sweep
-// (crbm_canon.cu) and the streamed two-phase sweep (crbm_stream.cu).
+// (crbm_canon_body.cuh), the streamed two-phase sweep (crbm_stream.cu) and
+// the batched launch.
 //
-// Mapping: warp = 32 chains of one packed word, lane = chain.  Each packed
-// word a node depends on is masked to the lane's bit and rotated (funnel
-// shift) straight into the address bits of a lane-expanded threshold table;
-// OR-ing those bits with the lane's column offset gives the table address.
-// The host builds the tables so that they absorb the coefficient signs s and
-// the field sums (Eqs. 9-10): a node costs one address merge, one shared
-// load, one compare and one ballot, plus its share of a Philox call.
+// Mapping: warp = 32 chains of one packed word, lane = chain.
+//
+// Hidden half-step (Eq. 9): each packed spin word of the 3x3 window is masked
+// to the lane's bit and rotated (funnel shift) into address bit 7 (first
+// endpoint) or 8 (second endpoint) of the lane-expanded hidden table
+// [cls][e1 + 2 e2][lane]; one OR with the lane's column offset makes the
+// address.  The ten decisions are not packed across lanes: each lane ORs
+// them into ONE per-lane word W whose bits are already the slots of the
+// visible-table indices that use them (layout below), for the cell's own four
+// spins and for the spins of the cell below and the cell to the right.
+//
+// Visible half-step (Eq. 10): C = (W_own & kOwn) | (W_up & kDown) |
+// (W_left & kRight) holds the 5-bit filter index of spin (r, c) at bits
+// 7 + 5 (2r + c) .. +4; a shift and a mask place it in address bits 7..11 of
+// the visible table [spin position][idx][lane].  The host builds both tables
+// so that they absorb the coefficient signs s and the field sums, so a node
+// costs one address merge, one shared load, one compare and one bit merge
+// (hidden) or ballot (visible), plus its share of a Philox call.
 #pragma once
 
 #include "crbm_device.cuh"
@@ -18,6 +30,27 @@ namespace canon {
 
 using namespace dev;
 
+// Bit of W for each filter unit k (see the slot table kCanonSlot):
+//   spin (0,0): b0 b4 b8 l.b1 u.b5 -> bits  7  8  9 10 11
+//   spin (0,1): b0 b6 b1 u.b7 u.b9 -> bits 12 13 14 15 16
+//   spin (1,0): b2 b4 b5 l.b3 l.b9 -> bits 17 18 19 20 21
+//   spin (1,1): b2 b6 b8 b3 b7     -> bits 22 23 24 25 26
+// A unit of the own cell sets its own-spin bits; b1, b3, b9 also set the bits
+// the cell to the right reads, b5, b7, b9 those the cell below reads.
+constexpr uint32_t kBit0 = (1u << 7) | (1u << 12);
+constexpr uint32_t kBit1 = (1u << 14) | (1u << 10);  // own (0,1) slot 2; right's (0,0) slot 3
+constexpr uint32_t kBit2 = (1u << 17) | (1u << 22);
+constexpr uint32_t kBit3 = (1u << 25) | (1u << 20);  // own (1,1) slot 3; right's (1,0) slot 3
+constexpr uint32_t kBit4 = (1u << 8) | (1u << 18);
+constexpr uint32_t kBit5 = (1u << 19) | (1u << 11);  // own (1,0) slot 2; below's (0,0) slot 4
+constexpr uint32_t kBit6 = (1u << 13) | (1u << 23);
+constexpr uint32_t kBit7 = (1u << 26) | (1u << 15);  // own (1,1) slot 4; below's (0,1) slot 3
+constexpr uint32_t kBit8 = (1u << 9) | (1u << 24);
+constexpr uint32_t kBit9 = (1u << 16) | (1u << 21);  // below's (0,1) slot 4; right's (1,0) slot 4
+constexpr uint32_t kDownBits = (1u << 11) | (1u << 15) | (1u << 16);
+constexpr uint32_t kRightBits = (1u << 10) | (1u << 20) | (1u << 21);
+constexpr uint32_t kOwnBits = ((1u << 27) - (1u << 7)) & ~kDownBits & ~kRightBits;
+
 // Byte-addressed 32-bit shared-memory load.
 __device__ __forceinline__ uint32_t lds_at(const uint32_t* base, uint32_t byte_off) {
     return *reinterpret_cast<const uint32_t*>(reinterpret_cast<const char*>(base) + byte_off);
@@ -25,19 +58,25 @@ __device__ __forceinline__ uint32_t lds_at(const uint32_t* base, uint32_t byte_o
 
 struct LaneConst {
     uint32_t lm;      // 1 << lane
-    uint32_t lb;      // 4 * lane: the lane's column in a [.][32] table
-    uint32_t rot[5];  // rotate-right amounts taking bit `lane` to bit 7 + j
+    uint32_t lb;      // 4 * column: the lane's column in a [.][32] table
+    uint32_t rot[2];  // rotate-right amounts taking bit `lane` to bit 7 / 8
 };
 
-// Hidden half-step of one cell (Eq. 9).  Table s_th[cls][e1 + 2 e2][lane]
-// (byte offset cls*512 + idx*128 + 4 lane): the e1 bit is rotated to bit 7,
-// the e2 bit to bit 8.
-// Window rows are at s_v + r0, r1, r2 (offsets of window rows 0..2) and
-// columns c0, c1, c2; the ten results go to h[0..9].
-__device__ __forceinline__ void hidden_cell(const uint32_t* s_v, int r0, int r1, int r2, int c0,
-                                            int c1, int c2, uint32_t* h, const uint32_t* s_th,
-                                            uint32_t X, uint32_t Y, const Round0Cell rc,
-                                            const uint32_t (&rk)[20], const LaneConst& lc) {
+__device__ __forceinline__ LaneConst lane_const(int lane, int col) {
+    LaneConst lc;
+    lc.lm = 1u << lane;
+    lc.lb = 4u * static_cast<uint32_t>(col);
+    lc.rot[0] = static_cast<uint32_t>(lane - 7) & 31u;
+    lc.rot[1] = static_cast<uint32_t>(lane - 8) & 31u;
+    return lc;
+}
+
+// Hidden half-step of one cell.  Window rows at s_v + r0, r1, r2 and columns
+// c0, c1, c2; returns the lane's word W.
+__device__ __forceinline__ uint32_t hidden_cell(const uint32_t* s_v, int r0, int r1, int r2, int c0,
+                                                int c1, int c2, const uint32_t* s_th, uint32_t X,
+                                                uint32_t Y, const Round0Cell rc,
+                                                const uint32_t (&rk)[20], const LaneConst& lc) {
     const uint32_t m00 = s_v[r0 + c0] & lc.lm, m01 = s_v[r0 + c1] & lc.lm;
     const uint32_t m02 = s_v[r0 + c2] & lc.lm, m10 = s_v[r1 + c0] & lc.lm;
     const uint32_t m11 = s_v[r1 + c1] & lc.lm, m12 = s_v[r1 + c2] & lc.lm;
@@ -56,48 +95,35 @@ __device__ __forceinline__ void hidden_cell(const uint32_t* s_v, int r0, int r1,
     const U4 q2 = philox_rounds1to9(X, Y, rc.a ^ 2u, rc.b, rk);
     const uint32_t* thJ = s_th;
     const uint32_t* thP = s_th + 128;
+    uint32_t w = 0u;
     // filters 0..7 (J) and 8..9 (J'): (first endpoint, second endpoint)
-    h[0] = __ballot_sync(0xffffffffu, q0.x < lds_at(thJ, a00 | b01 | lc.lb));
-    h[1] = __ballot_sync(0xffffffffu, q0.y < lds_at(thJ, a01 | b02 | lc.lb));
-    h[2] = __ballot_sync(0xffffffffu, q0.z < lds_at(thJ, a10 | b11 | lc.lb));
-    h[3] = __ballot_sync(0xffffffffu, q0.w < lds_at(thJ, a11 | b12 | lc.lb));
-    h[4] = __ballot_sync(0xffffffffu, q1.x < lds_at(thJ, a00 | b10 | lc.lb));
-    h[5] = __ballot_sync(0xffffffffu, q1.y < lds_at(thJ, a10 | b20 | lc.lb));
-    h[6] = __ballot_sync(0xffffffffu, q1.z < lds_at(thJ, a01 | b11 | lc.lb));
-    h[7] = __ballot_sync(0xffffffffu, q1.w < lds_at(thJ, a11 | b21 | lc.lb));
-    h[8] = __ballot_sync(0xffffffffu, q2.x < lds_at(thP, a00 | b11 | lc.lb));
-    h[9] = __ballot_sync(0xffffffffu, q2.y < lds_at(thP, a12 | b21 | lc.lb));
+    w |= q0.x < lds_at(thJ, a00 | b01 | lc.lb) ? kBit0 : 0u;
+    w |= q0.y < lds_at(thJ, a01 | b02 | lc.lb) ? kBit1 : 0u;
+    w |= q0.z < lds_at(thJ, a10 | b11 | lc.lb) ? kBit2 : 0u;
+    w |= q0.w < lds_at(thJ, a11 | b12 | lc.lb) ? kBit3 : 0u;
+    w |= q1.x < lds_at(thJ, a00 | b10 | lc.lb) ? kBit4 : 0u;
+    w |= q1.y < lds_at(thJ, a10 | b20 | lc.lb) ? kBit5 : 0u;
+    w |= q1.z < lds_at(thJ, a01 | b11 | lc.lb) ? kBit6 : 0u;
+    w |= q1.w < lds_at(thJ, a11 | b21 | lc.lb) ? kBit7 : 0u;
+    w |= q2.x < lds_at(thP, a00 | b11 | lc.lb) ? kBit8 : 0u;
+    w |= q2.y < lds_at(thP, a12 | b21 | lc.lb) ? kBit9 : 0u;
+    return w;
 }
 
-// Visible half-step of one cell (Eq. 10).  Each spin's five filter units sit
-// in slots 0..4 (bits 7..11) of a 5-bit index into s_tv[site][idx][lane]
-// (byte offset site*4096 + idx*128 + 4 lane).  Slot assignment (own cell /
-// cell above "u" / cell to the left "l"), chosen so that a unit shared by two
-// spins of the cell sits in the same slot for both:
-//   spin (0,0): b0 b4 b8 l.b1 u.b5     spin (0,1): b0 b6 b1 u.b7 u.b9
-//   spin (1,0): b2 b4 b5 l.b3 l.b9     spin (1,1): b2 b6 b8 b3 b7
-// ho, hu, hl: the ten hidden words of this cell, the cell above and the cell
-// to the left; the four new spin words go to out[0], out[1], out[row],
-// out[row + 1].
-__device__ __forceinline__ void visible_cell(uint32_t* out, int row, const uint32_t* ho,
-                                             const uint32_t* hu, const uint32_t* hl,
-                                             const uint32_t* s_tv, uint32_t X, uint32_t Y,
-                                             const Round0Cell rc, const uint32_t (&rk)[20],
+// Visible half-step of one cell from the lanes' words of this cell (wo), the
+// cell above (wu) and the cell to the left (wl); the four new spin words go
+// to out[0], out[1], out[row], out[row + 1].
+__device__ __forceinline__ void visible_cell(uint32_t* out, int row, uint32_t wo, uint32_t wu,
+                                             uint32_t wl, const uint32_t* s_tv, uint32_t X,
+                                             uint32_t Y, const Round0Cell rc, const uint32_t (&rk)[20],
                                              const LaneConst& lc) {
-    const uint32_t o0 = rotr(ho[0] & lc.lm, lc.rot[0]), o2 = rotr(ho[2] & lc.lm, lc.rot[0]);
-    const uint32_t o4 = rotr(ho[4] & lc.lm, lc.rot[1]), o6 = rotr(ho[6] & lc.lm, lc.rot[1]);
-    const uint32_t o8 = rotr(ho[8] & lc.lm, lc.rot[2]), o1 = rotr(ho[1] & lc.lm, lc.rot[2]);
-    const uint32_t o5 = rotr(ho[5] & lc.lm, lc.rot[2]), o3 = rotr(ho[3] & lc.lm, lc.rot[3]);
-    const uint32_t o7 = rotr(ho[7] & lc.lm, lc.rot[4]);
-    const uint32_t l1 = rotr(hl[1] & lc.lm, lc.rot[3]), l3 = rotr(hl[3] & lc.lm, lc.rot[3]);
-    const uint32_t l9 = rotr(hl[9] & lc.lm, lc.rot[4]);
-    const uint32_t u5 = rotr(hu[5] & lc.lm, lc.rot[4]), u7 = rotr(hu[7] & lc.lm, lc.rot[3]);
-    const uint32_t u9 = rotr(hu[9] & lc.lm, lc.rot[4]);
+    const uint32_t c = (wo & kOwnBits) | (wu & kDownBits) | (wl & kRightBits);
     const U4 q = philox_rounds1to9(X, Y, rc.a ^ kTagVis, rc.b, rk);
-    const uint32_t t00 = lds_at(s_tv, o0 | o4 | o8 | l1 | u5 | lc.lb);
-    const uint32_t t01 = lds_at(s_tv + 1024, o0 | o6 | o1 | u7 | u9 | lc.lb);
-    const uint32_t t10 = lds_at(s_tv + 2048, o2 | o4 | o5 | l3 | l9 | lc.lb);
-    const uint32_t t11 = lds_at(s_tv + 3072, o2 | o6 | o8 | o3 | o7 | lc.lb);
+    const uint32_t f = 31u << 7;
+    const uint32_t t00 = lds_at(s_tv, (c & f) | lc.lb);
+    const uint32_t t01 = lds_at(s_tv + 1024, ((c >> 5) & f) | lc.lb);
+    const uint32_t t10 = lds_at(s_tv + 2048, ((c >> 10) & f) | lc.lb);
+    const uint32_t t11 = lds_at(s_tv + 3072, ((c >> 15) & f) | lc.lb);
     out[0] = __ballot_sync(0xffffffffu, q.x < t00);
     out[1] = __ballot_sync(0xffffffffu, q.y < t01);
     out[row] = __ballot_sync(0xffffffffu, q.z < t10);

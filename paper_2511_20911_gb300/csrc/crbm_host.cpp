@@ -273,9 +273,13 @@ int crbm_create(crbm_ctx** out, const crbm_params* p) {
         return rc;
     }
     Geometry& g = ctx->g;
-    ctx->layout = p->layout == CRBM_LAYOUT_AUTO
-                      ? (p->L <= CRBM_SMEM_MAX_L ? CRBM_LAYOUT_SMEM : CRBM_LAYOUT_STREAM)
-                      : p->layout;
+    // AUTO: shared memory when the lattice, its hidden words and the tables fit
+    // in one CTA's 227 KB, else the streamed layout (SS filters, even periodic L)
+    ctx->layout = p->layout;
+    if (ctx->layout == CRBM_LAYOUT_AUTO) {
+        const size_t need = g.canonical ? smem_bytes_canon(g) : smem_bytes_generic(g);
+        ctx->layout = (p->L <= CRBM_SMEM_MAX_L && need <= 227 * 1024) ? CRBM_LAYOUT_SMEM : CRBM_LAYOUT_STREAM;
+    }
     if (ctx->layout == CRBM_LAYOUT_SMEM && p->L > CRBM_SMEM_MAX_L) {
         delete ctx;
         return fail(nullptr, CRBM_EINVAL, "SMEM layout needs L <= CRBM_SMEM_MAX_L");
@@ -477,7 +481,7 @@ int crbm_create(crbm_ctx** out, const crbm_params* p) {
         (rc = dalloc(ctx, d.sob, static_cast<size_t>(npad))) ||
         (rc = dalloc(ctx, d.swap_tab, swap_tab.size())) || (rc = dalloc(ctx, d.swap_off, swap_off.size())) ||
         (rc = dalloc(ctx, d.swap_len, swap_len.size())) || (rc = dalloc(ctx, d.wq, wq.size())) ||
-        (g.vil && (rc = dalloc(ctx, d.h, static_cast<size_t>(nw) * g.n_cells * 10))) ||
+        (g.vil && (rc = dalloc(ctx, d.h, static_cast<size_t>(nw) * g.n_cells * 32))) ||
         (g.vil && (rc = dalloc(ctx, d.cnt, static_cast<size_t>(npad) * 3)))) {
         g_create_error = ctx->err;
         free_device(d);

@@ -21,7 +21,7 @@ using namespace crbm;
 constexpr size_t kScratchWords = CRBM_NOALLOC_SCRATCH_BYTES / sizeof(uint32_t);
 
 // Scratch of the no-allocation sweep: per 32-chain word, kCanonTab table
-// words, then the hidden words of every word ([n_words][n_cells][10]).
+// words, then the lanes' hidden words of every word ([n_words][n_cells][32]).
 __device__ __align__(256) uint32_t g_noalloc_scratch[kScratchWords];
 
 constexpr int kMaxDevices = 64;
@@ -45,11 +45,11 @@ extern "C" int crbm_sweep_stream_noalloc(const crbm_params* p, uint32_t* v, int6
         return noalloc_fail(CRBM_EINVAL, "sweep range outside the 32-bit Philox sweep counter");
     const int L = p->L, W = L / 2, N = L * L, n_cells = W * W;
     const int n_words = 2 * ((p->n_chains + 63) / 64);
-    const size_t need = static_cast<size_t>(n_words) * kCanonTab + static_cast<size_t>(n_words) * n_cells * 10;
+    const size_t need = static_cast<size_t>(n_words) * kCanonTab + static_cast<size_t>(n_words) * n_cells * 32;
     if (need > kScratchWords)
         return noalloc_fail(CRBM_EUNSUPPORTED,
                             "lattice and chain count need more than CRBM_NOALLOC_SCRATCH_BYTES of scratch "
-                            "(4 bytes x n_words x (4352 + 10 (L/2)^2), n_words = 2 ceil(n_chains/64))");
+                            "(4 bytes x n_words x (4352 + 32 (L/2)^2), n_words = 2 ceil(n_chains/64))");
     for (int c = 0; p->chain_param && c < p->n_chains; ++c)
         if (p->chain_param[c] < 0 || p->chain_param[c] >= p->n_params)
             return noalloc_fail(CRBM_EINVAL, "chain_param out of range");

@@ -21,21 +21,13 @@ __device__ __forceinline__ size_t vidx(int w, int N, int s) {
     return (static_cast<size_t>(w >> 1) * N + s) * 2 + (w & 1);
 }
 
-__device__ __forceinline__ LaneConst lane_const(int lane) {
-    LaneConst lc;
-    lc.lm = 1u << lane;
-    lc.lb = 4u * lane;
-#pragma unroll
-    for (int s = 0; s < 5; ++s) lc.rot[s] = static_cast<uint32_t>(lane - 7 - s) & 31u;
-    return lc;
-}
-
 // Hidden half-step of one tile: v tile rows 2 i0 .. 2 i0 + 2 TI and columns
-// 2 j0 .. 2 j0 + 2 TJ (wrapped), hidden words out to h[word][cell][10].
+// 2 j0 .. 2 j0 + 2 TJ (wrapped), the lanes' hidden words out to
+// h[word][cell][32].
 __global__ void __launch_bounds__(kStreamThreads, 4) k_stream_hidden(const SweepArgs a, uint32_t t) {
     __shared__ __align__(16) uint32_t s_th[kCanonTh];
     __shared__ uint32_t s_v[(2 * kTI + 1) * (2 * kTJ + 1)];
-    __shared__ uint32_t s_h[kTI * kTJ * 10];
+    __shared__ uint32_t s_h[kTI * kTJ * 32];
     const Geometry& g = a.g;
     const int L = g.L, W = g.W, N = g.N;
     const int w = blockIdx.y;
@@ -51,7 +43,7 @@ __global__ void __launch_bounds__(kStreamThreads, 4) k_stream_hidden(const Sweep
         s_v[x] = a.v[vidx(w, N, R * L + C)];
     }
     const uint32_t chain = static_cast<uint32_t>(w) * 32u + lane;
-    const LaneConst lc = lane_const(lane);
+    const LaneConst lc = lane_const(lane, lane);
     const Round0Lane r0l = round0_lane(chain);
     const uint32_t X = r0l.hi ^ t ^ a.rk[0];
     __syncthreads();
@@ -60,15 +52,16 @@ __global__ void __launch_bounds__(kStreamThreads, 4) k_stream_hidden(const Sweep
         const int gi = i0 + li, gj = j0 + lj;
         if (gi >= W || gj >= W) continue;
         const int r0 = 2 * li * VS, c0 = 2 * lj;
-        hidden_cell(s_v, r0, r0 + VS, r0 + 2 * VS, c0, c0 + 1, c0 + 2, s_h + lcell * 10, s_th, X,
-                    r0l.lo, round0_cell(static_cast<uint32_t>(gi * W + gj), a.rk[1]), a.rk, lc);
+        s_h[lcell * 32 + lane] =
+            hidden_cell(s_v, r0, r0 + VS, r0 + 2 * VS, c0, c0 + 1, c0 + 2, s_th, X, r0l.lo,
+                        round0_cell(static_cast<uint32_t>(gi * W + gj), a.rk[1]), a.rk, lc);
     }
     __syncthreads();
     const int nj = min(kTJ, W - j0);
-    for (int x = threadIdx.x; x < kTI * kTJ * 10; x += blockDim.x) {
-        const int li = x / (kTJ * 10), rest = x - li * (kTJ * 10);
-        if (i0 + li >= W || rest >= nj * 10) continue;
-        a.h[(static_cast<size_t>(w) * g.n_cells + (i0 + li) * W + j0) * 10 + rest] = s_h[x];
+    for (int x = threadIdx.x; x < kTI * kTJ * 32; x += blockDim.x) {
+        const int li = x / (kTJ * 32), rest = x - li * (kTJ * 32);
+        if (i0 + li >= W || rest >= nj * 32) continue;
+        a.h[(static_cast<size_t>(w) * g.n_cells + (i0 + li) * W + j0) * 32 + rest] = s_h[x];
     }
 }
 
@@ -76,7 +69,7 @@ __global__ void __launch_bounds__(kStreamThreads, 4) k_stream_hidden(const Sweep
 // of cells above and the column to the left (wrapped), new spins out.
 __global__ void __launch_bounds__(kStreamThreads, 4) k_stream_visible(const SweepArgs a, uint32_t t) {
     __shared__ __align__(16) uint32_t s_tv[4 * 32 * 32];
-    __shared__ uint32_t s_h[(kTI + 1) * (kTJ + 1) * 10];
+    __shared__ uint32_t s_h[(kTI + 1) * (kTJ + 1) * 32];
     __shared__ uint32_t s_o[2 * kTI * 2 * kTJ];
     const Geometry& g = a.g;
     const int L = g.L, W = g.W, N = g.N;
@@ -87,14 +80,14 @@ __global__ void __launch_bounds__(kStreamThreads, 4) k_stream_visible(const Swee
     const uint4* gt = reinterpret_cast<const uint4*>(a.ctab + static_cast<size_t>(w) * kCanonTab + kCanonTh);
     for (int x = threadIdx.x; x < 4 * 32 * 32 / 4; x += blockDim.x) reinterpret_cast<uint4*>(s_tv)[x] = gt[x];
     constexpr int HS = kTJ + 1;
-    for (int x = threadIdx.x; x < (kTI + 1) * HS * 10; x += blockDim.x) {
-        const int lcell = x / 10, k = x - (x / 10) * 10;
+    for (int x = threadIdx.x; x < (kTI + 1) * HS * 32; x += blockDim.x) {
+        const int lcell = x >> 5, k = x & 31;
         const int li = lcell / HS, lj = lcell - (lcell / HS) * HS;
         const int gi = (i0 - 1 + li + W) % W, gj = (j0 - 1 + lj + W) % W;
-        s_h[x] = a.h[(static_cast<size_t>(w) * g.n_cells + gi * W + gj) * 10 + k];
+        s_h[x] = a.h[(static_cast<size_t>(w) * g.n_cells + gi * W + gj) * 32 + k];
     }
     const uint32_t chain = static_cast<uint32_t>(w) * 32u + lane;
-    const LaneConst lc = lane_const(lane);
+    const LaneConst lc = lane_const(lane, lane);
     const Round0Lane r0l = round0_lane(chain);
     const uint32_t X = r0l.hi ^ t ^ a.rk[0];
     __syncthreads();
@@ -103,8 +96,8 @@ __global__ void __launch_bounds__(kStreamThreads, 4) k_stream_visible(const Swee
         const int li = lcell / kTJ, lj = lcell - (lcell / kTJ) * kTJ;
         const int gi = i0 + li, gj = j0 + lj;
         if (gi >= W || gj >= W) continue;
-        const uint32_t* ho = s_h + ((li + 1) * HS + lj + 1) * 10;
-        visible_cell(s_o + 2 * li * VO + 2 * lj, VO, ho, ho - HS * 10, ho - 10, s_tv, X, r0l.lo,
+        const uint32_t* ho = s_h + ((li + 1) * HS + lj + 1) * 32 + lane;
+        visible_cell(s_o + 2 * li * VO + 2 * lj, VO, ho[0], ho[-HS * 32], ho[-32], s_tv, X, r0l.lo,
                      round0_cell(static_cast<uint32_t>(gi * W + gj), a.rk[1]), a.rk, lc);
     }
     __syncthreads();

@@ -10,9 +10,13 @@ namespace canon {
 
 // Whole-run body of the canonical SMEM-resident sweep for packed word `word`
 // (one CTA): load tables, spins and replica permutation into shared memory,
-// run a.n_sweeps sweeps with measurement / replica exchange / correlations,
+// run n_sweeps sweeps from global sweep t0 (measurement index meas0) with
+// measurement / replica exchange / correlations,
 // write the state back.
-__device__ __forceinline__ void sweep_canon_body(const SweepArgs& a, int word) {
+// State is read with L1-bypassing loads: under the persistent scheduler the
+// previous chunk of this word may have been written by another SM.
+__device__ __forceinline__ void sweep_canon_body(const SweepArgs& a, int word, uint32_t t0,
+                                                 int n_sweeps, int64_t meas0) {
     extern __shared__ __align__(16) uint32_t smem[];
     const Geometry& g = a.g;
     const int L = g.L, W = g.W;
@@ -30,7 +34,7 @@ __device__ __forceinline__ void sweep_canon_body(const SweepArgs& a, int word) {
     const uint4* gt = reinterpret_cast<const uint4*>(a.ctab + static_cast<size_t>(word) * kCanonTab);
     for (int x = threadIdx.x; x < kCanonTab / 4; x += blockDim.x) reinterpret_cast<uint4*>(smem)[x] = gt[x];
     uint32_t* gv = a.v + static_cast<size_t>(word) * g.N;
-    for (int x = threadIdx.x; x < g.N; x += blockDim.x) s_v[x] = gv[x];
+    for (int x = threadIdx.x; x < g.N; x += blockDim.x) s_v[x] = __ldcg(gv + x);
     for (int x = threadIdx.x; x < 96; x += blockDim.x) s_cnt[x] = 0;
     if (a.sq_every > 0) {
         for (int x = threadIdx.x; x < 33; x += blockDim.x) s_seg[x] = a.seg[word * 33 + x];
@@ -40,7 +44,7 @@ __device__ __forceinline__ void sweep_canon_body(const SweepArgs& a, int word) {
     LaneConst lc = lane_const(lane, lane);
     const Round0Lane r0l = round0_lane(chain);
     if (warp == 0) {  // replica permutation (identity without tempering)
-        const int sob = a.swap_every > 0 ? a.sob[word * 32 + lane] : lane;
+        const int sob = a.swap_every > 0 ? __ldcg(a.sob + word * 32 + lane) : lane;
         s_sob[lane] = sob;
         s_bos[sob] = lane;
     }
@@ -51,16 +55,15 @@ __device__ __forceinline__ void sweep_canon_body(const SweepArgs& a, int word) {
     const bool measuring = a.measure_every > 0;
     if (warp == 0 && measuring) {
 #pragma unroll
-        for (int x = 0; x < kNSum; ++x) acc[x] = a.sums[static_cast<size_t>(chain) * kNSum + x];
+        for (int x = 0; x < kNSum; ++x) acc[x] = __ldcg(a.sums + static_cast<size_t>(chain) * kNSum + x);
     }
     // sweep and measurement counters: kernel arguments, or the batch's device clock
-    const uint32_t t0 = a.clock ? static_cast<uint32_t>(a.clock[0]) : a.t0;
-    int64_t meas = a.clock ? a.clock[1] : a.meas0;
+    int64_t meas = meas0;
     // Cells of this warp: warp, warp + nwarp, ...; (i, j) advanced without division.
     const int i_first = warp / W, j_first = warp - (warp / W) * W;
     const int di = nwarp / W, dj = nwarp - (nwarp / W) * W;
 
-    for (int it = 0; it < a.n_sweeps; ++it) {
+    for (int it = 0; it < n_sweeps; ++it) {
         const uint32_t t = t0 + static_cast<uint32_t>(it);
         const uint32_t X = r0l.hi ^ t ^ a.rk[0];
         int i = i_first, j = j_first;

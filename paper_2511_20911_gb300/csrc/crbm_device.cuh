@@ -84,6 +84,16 @@ __device__ __forceinline__ uint32_t bit_of(uint32_t word, int lane) { return (wo
 
 __device__ __forceinline__ uint32_t rotr(uint32_t x, uint32_t s) { return __funnelshift_r(x, x, s); }
 
+// Acquire load / release store of a progress counter in global memory.
+__device__ __forceinline__ int ld_acquire(const int* p) {
+    int v;
+    asm volatile("ld.acquire.gpu.global.s32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
+    return v;
+}
+__device__ __forceinline__ void st_release(int* p, int v) {
+    asm volatile("st.release.gpu.global.s32 [%0], %1;" ::"l"(p), "r"(v) : "memory");
+}
+
 __device__ __forceinline__ int warp_sum(int x) {
 #pragma unroll
     for (int o = 16; o > 0; o >>= 1) x += __shfl_xor_sync(0xffffffffu, x, o);

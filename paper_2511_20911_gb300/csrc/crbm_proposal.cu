@@ -348,7 +348,7 @@ __global__ void __launch_bounds__(128) k_prop_train(const float* __restrict__ w,
         in[4][pos] = x.beta;
         in[5][pos] = x.h;
     }
-    float a1[16][kS1 * kS1], a2[16][kS2 * kS2], z[kK * kK];
+    float a1[16][kS1 * kS1], a2[16][kS2 * kS2];
     for (int o = 0; o < 16; ++o)
         for (int p = 0; p < kS1 * kS1; ++p) {
             const int y = p / kS1, xx = p % kS1;
@@ -371,7 +371,6 @@ __global__ void __launch_bounds__(128) k_prop_train(const float* __restrict__ w,
         float acc = w[oB3];
         for (int c = 0; c < 16; ++c)
             for (int t = 0; t < 9; ++t) acc += w[oW3 + c * 9 + t] * a2[c][(y + t / 3) * kS2 + xx + t % 3];
-        z[p] = acc;
         const float yv = x.target[p] > 0 ? 1.f : 0.f;
         lsum += (acc > 0.f ? acc + log1pf(__expf(-acc)) : log1pf(__expf(acc))) - yv * acc;
         dl[p] = (1.f / (1.f + __expf(-acc)) - yv) / (static_cast<float>(n) * kK * kK);
@@ -486,17 +485,6 @@ __global__ void k_prop_fragments(const float* wb, uint2* frag, float* bias) {
     frag[i] = make_uint2(pack_bf16(Bv(k0, n), Bv(k0 + 1, n)), pack_bf16(Bv(k0 + 8, n), Bv(k0 + 9, n)));
 }
 
-__global__ void k_prop_chain_params(const int32_t* chain_param, const double* beta, const int32_t* q,
-                                    int n_chains, int npad, float* bh, int32_t* cq) {
-    const int c = blockIdx.x * blockDim.x + threadIdx.x;
-    if (c >= npad) return;
-    const int p = chain_param[c < n_chains ? c : 0];
-    bh[2 * c] = bf16r(static_cast<float>(beta[p]));
-    bh[2 * c + 1] = bf16r(static_cast<float>(q[3 * p + 2]) * 0.0625f);
-    cq[3 * c] = q[3 * p];
-    cq[3 * c + 1] = q[3 * p + 1];
-    cq[3 * c + 2] = q[3 * p + 2];
-}
 }  // namespace
 }  // namespace crbm
 

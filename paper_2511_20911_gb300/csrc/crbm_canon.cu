@@ -70,7 +70,7 @@ __global__ void __launch_bounds__(512, CRBM_SWEEP_MIN_BLOCKS)
 }  // namespace
 
 size_t smem_bytes_canon(const Geometry& g) {
-    return sizeof(uint32_t) * (static_cast<size_t>(kCanonTab) + g.N + static_cast<size_t>(g.n_cells) * 32 +
+    return sizeof(uint32_t) * (static_cast<size_t>(kAccWords) + kCanonTab + g.N + static_cast<size_t>(g.n_cells) * 32 +
                                96 + 33 + 32 + 64);
 }
 

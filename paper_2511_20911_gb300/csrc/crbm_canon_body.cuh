@@ -19,11 +19,11 @@ __device__ __forceinline__ void sweep_canon_body(const SweepArgs& a, int word, u
                                                  int n_sweeps, int64_t meas0) {
     extern __shared__ __align__(16) uint32_t smem[];
     const Geometry& g = a.g;
-    const int L = g.L, W = g.W;
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nwarp = blockDim.x >> 5;
-    uint32_t* s_th = smem;                      // [2][4][32]
-    uint32_t* s_tv = smem + kCanonTh;           // [4][32][32]
-    uint32_t* s_v = smem + kCanonTab;           // [N]
+    int64_t* s_acc = reinterpret_cast<int64_t*>(smem);  // [kNSum][32] running sums
+    uint32_t* s_th = smem + kAccWords;          // [2][4][32]
+    uint32_t* s_tv = s_th + kCanonTh;           // [4][32][32]
+    uint32_t* s_v = s_th + kCanonTab;           // [N]
     uint32_t* s_w = s_v + g.N;                  // [n_cells][32] per-lane hidden words
     int* s_cnt = reinterpret_cast<int*>(s_w + g.n_cells * 32);   // [3][32]
     int* s_seg = s_cnt + 96;                                      // [33]
@@ -32,7 +32,7 @@ __device__ __forceinline__ void sweep_canon_body(const SweepArgs& a, int word, u
     int* s_bos = s_sob + 32;                                        // [32] rung of each slot
 
     const uint4* gt = reinterpret_cast<const uint4*>(a.ctab + static_cast<size_t>(word) * kCanonTab);
-    for (int x = threadIdx.x; x < kCanonTab / 4; x += blockDim.x) reinterpret_cast<uint4*>(smem)[x] = gt[x];
+    for (int x = threadIdx.x; x < kCanonTab / 4; x += blockDim.x) reinterpret_cast<uint4*>(s_th)[x] = gt[x];
     uint32_t* gv = a.v + static_cast<size_t>(word) * g.N;
     for (int x = threadIdx.x; x < g.N; x += blockDim.x) s_v[x] = __ldcg(gv + x);
     for (int x = threadIdx.x; x < 96; x += blockDim.x) s_cnt[x] = 0;
@@ -51,74 +51,47 @@ __device__ __forceinline__ void sweep_canon_body(const SweepArgs& a, int word, u
     __syncthreads();
     lc.lb = 4u * static_cast<uint32_t>(s_bos[lane]);  // lane reads the column of its rung
 
-    int64_t acc[kNSum];
     const bool measuring = a.measure_every > 0;
     if (warp == 0 && measuring) {
-#pragma unroll
-        for (int x = 0; x < kNSum; ++x) acc[x] = __ldcg(a.sums + static_cast<size_t>(chain) * kNSum + x);
+        for (int x = 0; x < kNSum; ++x)
+            s_acc[x * 32 + lane] = __ldcg(a.sums + static_cast<size_t>(chain) * kNSum + x);
     }
     // sweep and measurement counters: kernel arguments, or the batch's device clock
     int64_t meas = meas0;
-    // Cells of this warp: warp, warp + nwarp, ...; (i, j) advanced without division.
-    const int i_first = warp / W, j_first = warp - (warp / W) * W;
-    const int di = nwarp / W, dj = nwarp - (nwarp / W) * W;
+    // Cells of this warp: warp, warp + nwarp, ...; each described by its
+    // kCellRec records (shared-memory byte offsets and round-0 Philox words).
+    char* sm = reinterpret_cast<char*>(smem);
+    const uint32_t lane4 = 4u * static_cast<uint32_t>(lane);
+    const uint4* rec0 = a.crec + static_cast<size_t>(warp) * kCellRec;
+    const int rstep = nwarp * kCellRec;
 
     for (int it = 0; it < n_sweeps; ++it) {
         const uint32_t t = t0 + static_cast<uint32_t>(it);
         const uint32_t X = r0l.hi ^ t ^ a.rk[0];
-        int i = i_first, j = j_first;
-        for (int cell = warp; cell < g.n_cells; cell += nwarp) {
-            const int R0 = 2 * i * L, C0 = 2 * j;
-            s_w[cell * 32 + lane] =
-                hidden_cell(s_v, R0, R0 + L, (2 * i + 2 == L) ? 0 : R0 + 2 * L, C0, C0 + 1,
-                            (C0 + 2 == L) ? 0 : C0 + 2, s_th, X, r0l.lo,
-                            round0_cell(static_cast<uint32_t>(cell), a.rk[1]), a.rk, lc);
-            i += di;
-            j += dj;
-            if (j >= W) {
-                j -= W;
-                ++i;
-            }
+        const uint4* rec = rec0;
+        for (int cell = warp; cell < g.n_cells; cell += nwarp, rec += rstep) {
+            const uint4 h0 = __ldg(rec), h1 = __ldg(rec + 1);
+            sts_off(sm, h1.y + lane4, hidden_cell_rec(sm, h0, h1, s_th, X, r0l.lo, a.rk, lc));
         }
         __syncthreads();
-        i = i_first;
-        j = j_first;
-        for (int cell = warp; cell < g.n_cells; cell += nwarp) {
-            const int iu = (i == 0) ? W - 1 : i - 1;
-            const int jl = (j == 0) ? W - 1 : j - 1;
-            visible_cell(s_v + 2 * i * L + 2 * j, L, s_w[cell * 32 + lane], s_w[(iu * W + j) * 32 + lane],
-                         s_w[(i * W + jl) * 32 + lane], s_tv, X, r0l.lo,
-                         round0_cell(static_cast<uint32_t>(cell), a.rk[1]), a.rk, lc);
-            i += di;
-            j += dj;
-            if (j >= W) {
-                j -= W;
-                ++i;
-            }
+        rec = rec0;
+        for (int cell = warp; cell < g.n_cells; cell += nwarp, rec += rstep) {
+            const uint4 v0 = __ldg(rec + 2), v1 = __ldg(rec + 3);
+            visible_cell_rec(sm, v0, v1, lane4, s_tv, X, r0l.lo, a.rk, lc);
         }
         __syncthreads();
         const bool do_meas = measuring && (t + 1u) % static_cast<uint32_t>(a.measure_every) == 0u;
         const bool do_swap = a.swap_every > 0 && (t + 1u) % static_cast<uint32_t>(a.swap_every) == 0u;
         if (do_meas || do_swap) {
             int anti0 = 0, anti1 = 0, pos = 0;
-            i = i_first;
-            j = j_first;
-            for (int cell = warp; cell < g.n_cells; cell += nwarp) {
-                const int R0 = 2 * i * L, C0 = 2 * j;
-                count_cell(s_v, R0, R0 + L, (2 * i + 2 == L) ? 0 : R0 + 2 * L, C0, C0 + 1,
-                           (C0 + 2 == L) ? 0 : C0 + 2, lane, anti0, anti1, pos);
-                i += di;
-                j += dj;
-                if (j >= W) {
-                    j -= W;
-                    ++i;
-                }
-            }
+            const uint4* rec = rec0;
+            for (int cell = warp; cell < g.n_cells; cell += nwarp, rec += rstep)
+                count_cell_rec(sm, __ldg(rec), __ldg(rec + 1), lane, anti0, anti1, pos);
             atomicAdd(&s_cnt[lane], anti0);
             atomicAdd(&s_cnt[32 + lane], anti1);
             atomicAdd(&s_cnt[64 + lane], pos);
             __syncthreads();
-            if (warp == 0) post_sweep_warp0(a, s_cnt, s_sob, s_bos, lane, word, t, do_meas, do_swap, meas, acc);
+            if (warp == 0) post_sweep_warp0(a, s_cnt, s_sob, s_bos, lane, word, t, do_meas, do_swap, meas, s_acc);
             if (do_meas) ++meas;
             __syncthreads();
             if (do_swap) lc.lb = 4u * static_cast<uint32_t>(s_bos[lane]);
@@ -131,8 +104,7 @@ __device__ __forceinline__ void sweep_canon_body(const SweepArgs& a, int word, u
     for (int x = threadIdx.x; x < g.N; x += blockDim.x) gv[x] = s_v[x];
     if (warp == 0 && a.swap_every > 0) a.sob[word * 32 + lane] = s_sob[lane];
     if (warp == 0 && measuring) {
-#pragma unroll
-        for (int x = 0; x < kNSum; ++x) a.sums[static_cast<size_t>(chain) * kNSum + x] = acc[x];
+        for (int x = 0; x < kNSum; ++x) a.sums[static_cast<size_t>(chain) * kNSum + x] = s_acc[x * 32 + lane];
     }
 }
 

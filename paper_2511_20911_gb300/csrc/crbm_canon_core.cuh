@@ -71,16 +71,24 @@ __device__ __forceinline__ LaneConst lane_const(int lane, int col) {
     return lc;
 }
 
-// Hidden half-step of one cell.  Window rows at s_v + r0, r1, r2 and columns
-// c0, c1, c2; returns the lane's word W.
-__device__ __forceinline__ uint32_t hidden_cell(const uint32_t* s_v, int r0, int r1, int r2, int c0,
-                                                int c1, int c2, const uint32_t* s_th, uint32_t X,
-                                                uint32_t Y, const Round0Cell rc,
-                                                const uint32_t (&rk)[20], const LaneConst& lc) {
-    const uint32_t m00 = s_v[r0 + c0] & lc.lm, m01 = s_v[r0 + c1] & lc.lm;
-    const uint32_t m02 = s_v[r0 + c2] & lc.lm, m10 = s_v[r1 + c0] & lc.lm;
-    const uint32_t m11 = s_v[r1 + c1] & lc.lm, m12 = s_v[r1 + c2] & lc.lm;
-    const uint32_t m20 = s_v[r2 + c0] & lc.lm, m21 = s_v[r2 + c1] & lc.lm;
+// Shared-memory word at a byte offset from the start of dynamic shared
+// memory (per-cell records hold such offsets).
+__device__ __forceinline__ uint32_t lds_off(const char* sm, uint32_t off) {
+    return *reinterpret_cast<const uint32_t*>(sm + off);
+}
+__device__ __forceinline__ void sts_off(char* sm, uint32_t off, uint32_t x) {
+    *reinterpret_cast<uint32_t*>(sm + off) = x;
+}
+
+// Hidden half-step of one cell from its eight window words v_rc (row r,
+// column c of the 3x3 window; (2,2) is not used) and the cell's round-0
+// Philox words (rca, rcb); returns the lane's word W.
+__device__ __forceinline__ uint32_t hidden_core(uint32_t v00, uint32_t v01, uint32_t v02, uint32_t v10,
+                                                uint32_t v11, uint32_t v12, uint32_t v20, uint32_t v21,
+                                                const uint32_t* s_th, uint32_t X, uint32_t Y, uint32_t rca,
+                                                uint32_t rcb, const uint32_t (&rk)[20], const LaneConst& lc) {
+    const uint32_t m00 = v00 & lc.lm, m01 = v01 & lc.lm, m02 = v02 & lc.lm, m10 = v10 & lc.lm;
+    const uint32_t m11 = v11 & lc.lm, m12 = v12 & lc.lm, m20 = v20 & lc.lm, m21 = v21 & lc.lm;
     // first endpoints at bit 7
     const uint32_t a00 = rotr(m00, lc.rot[0]), a01 = rotr(m01, lc.rot[0]);
     const uint32_t a10 = rotr(m10, lc.rot[0]), a11 = rotr(m11, lc.rot[0]);
@@ -90,9 +98,9 @@ __device__ __forceinline__ uint32_t hidden_cell(const uint32_t* s_v, int r0, int
     const uint32_t b10 = rotr(m10, lc.rot[1]), b11 = rotr(m11, lc.rot[1]);
     const uint32_t b12 = rotr(m12, lc.rot[1]), b20 = rotr(m20, lc.rot[1]);
     const uint32_t b21 = rotr(m21, lc.rot[1]);
-    const U4 q0 = philox_rounds1to9(X, Y, rc.a, rc.b, rk);
-    const U4 q1 = philox_rounds1to9(X, Y, rc.a ^ 1u, rc.b, rk);
-    const U4 q2 = philox_rounds1to9(X, Y, rc.a ^ 2u, rc.b, rk);
+    const U4 q0 = philox_rounds1to9(X, Y, rca, rcb, rk);
+    const U4 q1 = philox_rounds1to9(X, Y, rca ^ 1u, rcb, rk);
+    const U4 q2 = philox_rounds1to9(X, Y, rca ^ 2u, rcb, rk);
     const uint32_t* thJ = s_th;
     const uint32_t* thP = s_th + 128;
     uint32_t w = 0u;
@@ -110,38 +118,93 @@ __device__ __forceinline__ uint32_t hidden_cell(const uint32_t* s_v, int r0, int
     return w;
 }
 
+// Hidden half-step of one cell.  Window rows at s_v + r0, r1, r2 and columns
+// c0, c1, c2; returns the lane's word W.
+__device__ __forceinline__ uint32_t hidden_cell(const uint32_t* s_v, int r0, int r1, int r2, int c0,
+                                                int c1, int c2, const uint32_t* s_th, uint32_t X,
+                                                uint32_t Y, const Round0Cell rc,
+                                                const uint32_t (&rk)[20], const LaneConst& lc) {
+    return hidden_core(s_v[r0 + c0], s_v[r0 + c1], s_v[r0 + c2], s_v[r1 + c0], s_v[r1 + c1], s_v[r1 + c2],
+                       s_v[r2 + c0], s_v[r2 + c1], s_th, X, Y, rc.a, rc.b, rk, lc);
+}
+
+// Hidden half-step of one cell described by its records h0, h1 (layout in
+// crbm_internal.h); returns the lane's word W.
+__device__ __forceinline__ uint32_t hidden_cell_rec(const char* sm, const uint4& h0, const uint4& h1,
+                                                    const uint32_t* s_th, uint32_t X, uint32_t Y,
+                                                    const uint32_t (&rk)[20], const LaneConst& lc) {
+    return hidden_core(lds_off(sm, h0.x), lds_off(sm, h0.x + 4u), lds_off(sm, h0.w), lds_off(sm, h0.y),
+                       lds_off(sm, h0.y + 4u), lds_off(sm, h1.x), lds_off(sm, h0.z), lds_off(sm, h0.z + 4u),
+                       s_th, X, Y, h1.w, h1.z, rk, lc);
+}
+
 // Visible half-step of one cell from the lanes' words of this cell (wo), the
-// cell above (wu) and the cell to the left (wl); the four new spin words go
-// to out[0], out[1], out[row], out[row + 1].
-__device__ __forceinline__ void visible_cell(uint32_t* out, int row, uint32_t wo, uint32_t wu,
-                                             uint32_t wl, const uint32_t* s_tv, uint32_t X,
-                                             uint32_t Y, const Round0Cell rc, const uint32_t (&rk)[20],
-                                             const LaneConst& lc) {
+// cell above (wu) and the cell to the left (wl), with round-0 words
+// (rca ^ visible tag, rcb); returns the four new spin words (0,0) (0,1)
+// (1,0) (1,1) of the cell.
+__device__ __forceinline__ U4 visible_core(uint32_t wo, uint32_t wu, uint32_t wl, const uint32_t* s_tv,
+                                           uint32_t X, uint32_t Y, uint32_t rcav, uint32_t rcb,
+                                           const uint32_t (&rk)[20], const LaneConst& lc) {
     const uint32_t c = (wo & kOwnBits) | (wu & kDownBits) | (wl & kRightBits);
-    const U4 q = philox_rounds1to9(X, Y, rc.a ^ kTagVis, rc.b, rk);
+    const U4 q = philox_rounds1to9(X, Y, rcav, rcb, rk);
     const uint32_t f = 31u << 7;
     const uint32_t t00 = lds_at(s_tv, (c & f) | lc.lb);
     const uint32_t t01 = lds_at(s_tv + 1024, ((c >> 5) & f) | lc.lb);
     const uint32_t t10 = lds_at(s_tv + 2048, ((c >> 10) & f) | lc.lb);
     const uint32_t t11 = lds_at(s_tv + 3072, ((c >> 15) & f) | lc.lb);
-    out[0] = __ballot_sync(0xffffffffu, q.x < t00);
-    out[1] = __ballot_sync(0xffffffffu, q.y < t01);
-    out[row] = __ballot_sync(0xffffffffu, q.z < t10);
-    out[row + 1] = __ballot_sync(0xffffffffu, q.w < t11);
+    return {__ballot_sync(0xffffffffu, q.x < t00), __ballot_sync(0xffffffffu, q.y < t01),
+            __ballot_sync(0xffffffffu, q.z < t10), __ballot_sync(0xffffffffu, q.w < t11)};
 }
 
-// Per-lane counts of one cell for the measurement: anti-aligned J and J'
-// filters of the window, and +1 spins of the cell.
-__device__ __forceinline__ void count_cell(const uint32_t* s_v, int r0, int r1, int r2, int c0,
-                                           int c1, int c2, int lane, int& anti0, int& anti1, int& pos) {
-    const uint32_t w00 = s_v[r0 + c0], w01 = s_v[r0 + c1], w02 = s_v[r0 + c2];
-    const uint32_t w10 = s_v[r1 + c0], w11 = s_v[r1 + c1], w12 = s_v[r1 + c2];
-    const uint32_t w20 = s_v[r2 + c0], w21 = s_v[r2 + c1];
+// Visible half-step of one cell; the four new spin words go to out[0],
+// out[1], out[row], out[row + 1].
+__device__ __forceinline__ void visible_cell(uint32_t* out, int row, uint32_t wo, uint32_t wu,
+                                             uint32_t wl, const uint32_t* s_tv, uint32_t X,
+                                             uint32_t Y, const Round0Cell rc, const uint32_t (&rk)[20],
+                                             const LaneConst& lc) {
+    const U4 o = visible_core(wo, wu, wl, s_tv, X, Y, rc.a ^ kTagVis, rc.b, rk, lc);
+    out[0] = o.x;
+    out[1] = o.y;
+    out[row] = o.z;
+    out[row + 1] = o.w;
+}
+
+// Visible half-step of one cell described by its records v0, v1; lane4 =
+// 4 * lane (the lane's column of the hidden rows).
+__device__ __forceinline__ void visible_cell_rec(char* sm, const uint4& v0, const uint4& v1, uint32_t lane4,
+                                                 const uint32_t* s_tv, uint32_t X, uint32_t Y,
+                                                 const uint32_t (&rk)[20], const LaneConst& lc) {
+    const U4 o = visible_core(lds_off(sm, v0.z + lane4), lds_off(sm, v0.w + lane4), lds_off(sm, v1.x + lane4),
+                              s_tv, X, Y, v1.z, v1.y, rk, lc);
+    sts_off(sm, v0.x, o.x);
+    sts_off(sm, v0.x + 4u, o.y);
+    sts_off(sm, v0.y, o.z);
+    sts_off(sm, v0.y + 4u, o.w);
+}
+
+// Per-lane counts of one cell for the measurement from its eight window
+// words: anti-aligned J and J' filters of the window, and +1 spins of the cell.
+__device__ __forceinline__ void count_core(uint32_t w00, uint32_t w01, uint32_t w02, uint32_t w10, uint32_t w11,
+                                           uint32_t w12, uint32_t w20, uint32_t w21, int lane, int& anti0,
+                                           int& anti1, int& pos) {
     anti0 += bit_of(w00 ^ w01, lane) + bit_of(w01 ^ w02, lane) + bit_of(w10 ^ w11, lane) +
              bit_of(w11 ^ w12, lane) + bit_of(w00 ^ w10, lane) + bit_of(w10 ^ w20, lane) +
              bit_of(w01 ^ w11, lane) + bit_of(w11 ^ w21, lane);
     anti1 += bit_of(w00 ^ w11, lane) + bit_of(w12 ^ w21, lane);
     pos += bit_of(w00, lane) + bit_of(w01, lane) + bit_of(w10, lane) + bit_of(w11, lane);
+}
+
+__device__ __forceinline__ void count_cell(const uint32_t* s_v, int r0, int r1, int r2, int c0,
+                                           int c1, int c2, int lane, int& anti0, int& anti1, int& pos) {
+    count_core(s_v[r0 + c0], s_v[r0 + c1], s_v[r0 + c2], s_v[r1 + c0], s_v[r1 + c1], s_v[r1 + c2],
+               s_v[r2 + c0], s_v[r2 + c1], lane, anti0, anti1, pos);
+}
+
+__device__ __forceinline__ void count_cell_rec(const char* sm, const uint4& h0, const uint4& h1, int lane,
+                                               int& anti0, int& anti1, int& pos) {
+    count_core(lds_off(sm, h0.x), lds_off(sm, h0.x + 4u), lds_off(sm, h0.w), lds_off(sm, h0.y),
+               lds_off(sm, h0.y + 4u), lds_off(sm, h1.x), lds_off(sm, h0.z), lds_off(sm, h0.z + 4u), lane,
+               anti0, anti1, pos);
 }
 
 }  // namespace canon

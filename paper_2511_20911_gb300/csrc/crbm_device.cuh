@@ -120,14 +120,16 @@ __device__ __forceinline__ int site_of(const Geometry& g, int i, int j, int r, i
 // anti-aligned J' filters, [64..95] +1 spins; lane = replica slot).  Lane k
 // then stands for temperature rung k, held by slot s_sob[k] (the identity
 // without tempering):
-//  - measurement: rung k's (NJ, NJ', M) go to series/sums row 32 word + k;
+//  - measurement: rung k's (NJ, NJ', M) go to series row 32 word + k and are
+//    added to the running sums s_acc[x][k] (shared memory, so that they hold
+//    no registers through the sweep loop);
 //  - replica exchange (round m): pairs (k, k+1) with k = m (mod 2) swap rungs
 //    when E_k <= E_{k+1}, else when a Philox word (k, m, word, swap tag) is
 //    below the host-built threshold of nearbyint(2^32 exp((b_k - b_{k+1}) dE / 16)).
 __device__ __forceinline__ void post_sweep_warp0(const SweepArgs& a, int* s_cnt, int* s_sob,
                                                  int* s_bos, int lane, int word, uint32_t t,
                                                  bool do_meas, bool do_swap, int64_t meas,
-                                                 int64_t (&acc)[kNSum]) {
+                                                 int64_t* s_acc) {
     const Geometry& g = a.g;
     const int nJr = g.n_real_bonds[0] - 2 * s_cnt[lane];
     const int nPr = g.n_real_bonds[1] - 2 * s_cnt[32 + lane];
@@ -148,17 +150,18 @@ __device__ __forceinline__ void post_sweep_warp0(const SweepArgs& a, int* s_cnt,
             e[1] = static_cast<int32_t>(nP);
             e[2] = static_cast<int32_t>(M);
         }
-        acc[0] += 1;
-        acc[1] += nJ;
-        acc[2] += nP;
-        acc[3] += M;
-        acc[4] += M < 0 ? -M : M;
-        acc[5] += nJ * nJ;
-        acc[6] += nP * nP;
-        acc[7] += M * M;
-        acc[8] += nJ * nP;
-        acc[9] += nJ * M;
-        acc[10] += nP * M;
+        int64_t* acc = s_acc + k;
+        acc[0 * 32] += 1;
+        acc[1 * 32] += nJ;
+        acc[2 * 32] += nP;
+        acc[3 * 32] += M;
+        acc[4 * 32] += M < 0 ? -M : M;
+        acc[5 * 32] += nJ * nJ;
+        acc[6 * 32] += nP * nP;
+        acc[7 * 32] += M * M;
+        acc[8 * 32] += nJ * nP;
+        acc[9 * 32] += nJ * M;
+        acc[10 * 32] += nP * M;
     }
     if (do_swap) {
         const int32_t* q = a.wq + 3 * word;

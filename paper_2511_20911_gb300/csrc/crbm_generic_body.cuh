@@ -102,7 +102,8 @@ __device__ __forceinline__ void sweep_generic_body(const SweepArgs& a, int word)
     extern __shared__ __align__(16) uint32_t smem[];
     const Geometry& g = a.g;
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nwarp = blockDim.x >> 5;
-    uint32_t* s_tab = smem;
+    int64_t* s_acc = reinterpret_cast<int64_t*>(smem);  // [kNSum][32] running sums
+    uint32_t* s_tab = smem + kAccWords;
     uint32_t* s_v = s_tab + g.nTab * 32;
     uint32_t* s_h = s_v + g.N;
     int* s_cnt = reinterpret_cast<int*>(s_h + g.n_cells * g.nb);  // [3][32]
@@ -129,11 +130,9 @@ __device__ __forceinline__ void sweep_generic_body(const SweepArgs& a, int word)
     }
     __syncthreads();
     int col = s_bos[lane];  // threshold column: the rung this slot holds
-    int64_t acc[kNSum];
     const bool measuring = a.measure_every > 0;
     if (warp == 0 && measuring) {
-#pragma unroll
-        for (int x = 0; x < kNSum; ++x) acc[x] = a.sums[static_cast<size_t>(chain) * kNSum + x];
+        for (int x = 0; x < kNSum; ++x) s_acc[x * 32 + lane] = a.sums[static_cast<size_t>(chain) * kNSum + x];
     }
     // sweep and measurement counters: kernel arguments, or the batch's device clock
     const uint32_t t0 = a.clock ? static_cast<uint32_t>(a.clock[0]) : a.t0;
@@ -186,7 +185,7 @@ __device__ __forceinline__ void sweep_generic_body(const SweepArgs& a, int word)
             atomicAdd(&s_cnt[32 + lane], anti1);
             atomicAdd(&s_cnt[64 + lane], pos);
             __syncthreads();
-            if (warp == 0) post_sweep_warp0(a, s_cnt, s_sob, s_bos, lane, word, t, do_meas, do_swap, meas, acc);
+            if (warp == 0) post_sweep_warp0(a, s_cnt, s_sob, s_bos, lane, word, t, do_meas, do_swap, meas, s_acc);
             if (do_meas) ++meas;
             __syncthreads();
             if (do_swap) col = s_bos[lane];
@@ -199,8 +198,7 @@ __device__ __forceinline__ void sweep_generic_body(const SweepArgs& a, int word)
     for (int x = threadIdx.x; x < g.N; x += blockDim.x) gv[x] = s_v[x];
     if (warp == 0 && a.swap_every > 0) a.sob[word * 32 + lane] = s_sob[lane];
     if (warp == 0 && measuring) {
-#pragma unroll
-        for (int x = 0; x < kNSum; ++x) a.sums[static_cast<size_t>(chain) * kNSum + x] = acc[x];
+        for (int x = 0; x < kNSum; ++x) a.sums[static_cast<size_t>(chain) * kNSum + x] = s_acc[x * 32 + lane];
     }
 }
 

@@ -182,7 +182,7 @@ int dalloc(crbm_ctx* ctx, T*& ptr, size_t count) {
 }
 
 void free_device(DeviceState& d) {
-    void* ptrs[] = {d.v, d.tab, d.ctab, d.sneg, d.inc, d.inc_off, d.sums, d.series, d.corr,
+    void* ptrs[] = {d.v, d.tab, d.ctab, d.crec, d.sneg, d.inc, d.inc_off, d.sums, d.series, d.corr,
                     d.seg, d.segmask, d.spins8, d.h, d.cnt, d.err, d.sob, d.swap_tab, d.swap_off,
                     d.swap_len, d.wq, d.chain_bh, d.chain_q, d.sched};
     for (void* p : ptrs)
@@ -216,6 +216,7 @@ SweepArgs fill_sweep_args(const crbm_ctx* ctx, int chunk) {
     a.v = ctx->d.v;
     a.tab = ctx->d.tab;
     a.ctab = ctx->d.ctab;
+    a.crec = ctx->d.crec;
     a.sneg = ctx->d.sneg;
     a.inc = ctx->d.inc;
     a.inc_off = ctx->d.inc_off;
@@ -465,12 +466,34 @@ int crbm_create(crbm_ctx** out, const crbm_params* p) {
                     }
             }
     }
+    // Per-cell records of the canonical SMEM sweep (layout in crbm_internal.h).
+    std::vector<uint32_t> crec;
+    if (g.canonical && ctx->layout == CRBM_LAYOUT_SMEM) {
+        const int L = g.L, W = g.W;
+        const uint32_t key1 = static_cast<uint32_t>(ctx->seed >> 32);
+        const uint32_t vb = 4u * kCanonSmemV, wb = 4u * static_cast<uint32_t>(kCanonSmemV + g.N);
+        auto site = [&](int R, int C) { return vb + 4u * static_cast<uint32_t>((R % L) * L + C % L); };
+        auto hrow = [&](int i, int j) { return wb + 128u * static_cast<uint32_t>(i * W + j); };
+        crec.assign(static_cast<size_t>(g.n_cells) * kCellRec * 4, 0u);
+        for (int i = 0; i < W; ++i)
+            for (int j = 0; j < W; ++j) {
+                uint32_t* o = &crec[static_cast<size_t>(i * W + j) * kCellRec * 4];
+                const uint64_t m = 0xD2511F53ull * static_cast<uint32_t>(i * W + j);
+                const uint32_t lo = static_cast<uint32_t>(m), hi = static_cast<uint32_t>(m >> 32) ^ key1;
+                const int R = 2 * i, C = 2 * j;
+                const uint32_t rec[16] = {site(R, C),     site(R + 1, C), site(R + 2, C),
+                                          site(R, C + 2), site(R + 1, C + 2), hrow(i, j), lo, hi,
+                                          site(R, C),     site(R + 1, C), hrow(i, j), hrow((i + W - 1) % W, j),
+                                          hrow(i, (j + W - 1) % W), lo, hi ^ kTagVis, 0u};
+                std::copy(rec, rec + 16, o);
+            }
+    }
     // Device state.
     cudaGetDevice(&ctx->device);
     DeviceState& d = ctx->d;
     const size_t N = static_cast<size_t>(g.N);
     if ((rc = dalloc(ctx, d.v, nw * N)) || (rc = dalloc(ctx, d.tab, tab.size())) ||
-        (rc = dalloc(ctx, d.ctab, ctab.size())) ||
+        (rc = dalloc(ctx, d.ctab, ctab.size())) || (rc = dalloc(ctx, d.crec, crec.size() / 4)) ||
         (rc = dalloc(ctx, d.sneg, sneg.size())) || (rc = dalloc(ctx, d.inc, inc.size())) ||
         (rc = dalloc(ctx, d.inc_off, inc_off.size())) ||
         (rc = dalloc(ctx, d.sums, static_cast<size_t>(npad) * kNSum)) ||
@@ -496,6 +519,7 @@ int crbm_create(crbm_ctx** out, const crbm_params* p) {
     };
     h2d(d.tab, tab.data(), tab.size() * 4);
     h2d(d.ctab, ctab.data(), ctab.size() * 4);
+    h2d(d.crec, crec.data(), crec.size() * 4);
     h2d(d.sneg, sneg.data(), sneg.size() * 4);
     h2d(d.inc, inc.data(), inc.size() * 4);
     h2d(d.inc_off, inc_off.data(), inc_off.size() * 4);

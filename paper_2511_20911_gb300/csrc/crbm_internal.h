@@ -15,6 +15,7 @@ __host__ __device__ inline size_t word_index(int vil, int w, int N, int s) {
 
 constexpr int kMaxBonds = 16;  // filters per 3x3 window -> at most 4 hidden Philox calls
 constexpr int kNSum = 11;      // per-chain observable sums
+constexpr int kAccWords = kNSum * 32 * 2;  // shared-memory words of the [kNSum][32] int64 running sums
 constexpr int kWordBits = 32;  // chains per packed word (one bit per chain)
 constexpr uint32_t kTagVis = 4u;   // Philox tag of the visible half-step
 constexpr uint32_t kTagInit = 5u;  // Philox tag of the initial spins
@@ -24,6 +25,20 @@ constexpr uint32_t kTagSwap = 6u;  // Philox tag of replica-exchange decisions
 // then visible [4 spin positions][32 idx][32 lanes] (see crbm_canon.cu).
 constexpr int kCanonTh = 2 * 4 * 32;
 constexpr int kCanonTab = kCanonTh + 4 * 32 * 32;
+// Canonical SMEM-resident sweep: dynamic shared memory holds, in 32-bit
+// words, [kAccWords running sums][kCanonTab tables][N spins]
+// [n_cells x 32 per-lane hidden words][counters ...]; kCanonSmemV is the
+// offset of the spins.
+constexpr int kCanonSmemV = kAccWords + kCanonTab;
+// Per-cell records of that sweep, kCellRec uint4 per cell, built on the host
+// so that the cell loops do no index arithmetic.  Byte offsets are from the
+// start of dynamic shared memory; rc = (lo(M0 cell), hi(M0 cell) ^ key1) are
+// the round-0 Philox words of the cell (M0 the first Philox multiplier):
+//   [0] spins (0,0) (1,0) (2,0) (0,2) of the 3x3 window (site (r,1) is (r,0) + 4)
+//   [1] spin (1,2), the cell's hidden row, rc.lo, rc.hi
+//   [2] spins (0,0) (1,0) of the cell, hidden rows of the cell and of the cell above
+//   [3] hidden row of the cell to the left, rc.lo, rc.hi ^ visible tag, 0
+constexpr int kCellRec = 4;
 // (class, second-endpoint flag) of the five filter slots of each spin
 // position (0,0), (0,1), (1,0), (1,1) in the canonical visible tables.
 constexpr int kCanonSlot[4][5][2] = {{{0, 0}, {0, 0}, {1, 0}, {0, 1}, {0, 1}},
@@ -56,6 +71,7 @@ struct DeviceState {
     uint32_t* v = nullptr;        // [n_words][N] packed spins, bit l = chain 32w + l
     uint32_t* tab = nullptr;      // [n_words][nTab][32] lane-expanded thresholds
     uint32_t* ctab = nullptr;     // [n_words][kCanonTab] canonical fast-path tables
+    uint4* crec = nullptr;        // [n_cells][kCellRec] canonical per-cell records (SMEM layout)
     uint32_t* sneg = nullptr;     // [n_words][2] lanes whose class coefficient s = -1
     uint32_t* inc = nullptr;      // generic incidences, CSR entries (see kernels)
     int32_t* inc_off = nullptr;   // [N + 1] CSR offsets
@@ -83,6 +99,7 @@ struct SweepArgs {
     uint32_t* v;
     const uint32_t* tab;
     const uint32_t* ctab;
+    const uint4* crec;
     const uint32_t* sneg;
     const uint32_t* inc;
     const int32_t* inc_off;

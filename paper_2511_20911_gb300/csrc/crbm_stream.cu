@@ -15,21 +15,115 @@ using namespace canon;
 
 constexpr int kTI = 16;  // tile rows of cells
 constexpr int kTJ = 16;  // tile columns of cells
-constexpr int kStreamThreads = 256;
+#ifndef CRBM_STREAM_THREADS
+#define CRBM_STREAM_THREADS 256
+#endif
+#ifndef CRBM_STREAM_VIS_THREADS
+#define CRBM_STREAM_VIS_THREADS 256
+#endif
+constexpr int kStreamThreads = CRBM_STREAM_THREADS;      // hidden and count kernels
+constexpr int kStreamVisThreads = CRBM_STREAM_VIS_THREADS;
 
 __device__ __forceinline__ size_t vidx(int w, int N, int s) {
     return (static_cast<size_t>(w >> 1) * N + s) * 2 + (w & 1);
+}
+#ifndef CRBM_STREAM_MIN_BLOCKS
+#define CRBM_STREAM_MIN_BLOCKS 4
+#endif
+#ifndef CRBM_STREAM_VIS_MIN_BLOCKS
+#define CRBM_STREAM_VIS_MIN_BLOCKS 4
+#endif
+
+// Stage spin rows 2 i0 .. 2 i0 + 2 TI and columns 2 j0 .. 2 j0 + 2 TJ
+// (wrapped) of half-word w into s_v[(2 TI + 1)][(2 TJ + 1)].  Every load of a
+// thread is issued before its first shared store.  kOneWrap: L >= 2 TJ, so
+// 2 i0 + r <= L + 30 needs at most one subtraction of L.
+template <bool kOneWrap>
+__device__ __forceinline__ void stage_spin_tile(const SweepArgs& a, int w, int i0, int j0, uint32_t* s_v) {
+    constexpr int VS = 2 * kTJ + 1, NV = (2 * kTI + 1) * VS;
+    constexpr int IT = (NV + kStreamThreads - 1) / kStreamThreads;
+    const int L = a.g.L;
+    const uint32_t* vw = a.v + vidx(w, a.g.N, 0);  // site s of half-word w at vw[2 s]
+    uint32_t val[IT];
+#pragma unroll
+    for (int k = 0; k < IT; ++k) {
+        const int x = threadIdx.x + k * kStreamThreads;
+        const int r = x / VS, c = x - (x / VS) * VS;
+        int R = 2 * i0 + r, C = 2 * j0 + c;
+        if (kOneWrap) {
+            R -= R >= L ? L : 0;
+            C -= C >= L ? L : 0;
+        } else {
+            R %= L;
+            C %= L;
+        }
+        val[k] = 0u;
+        if (x < NV) val[k] = vw[2 * (R * L + C)];
+    }
+#pragma unroll
+    for (int k = 0; k < IT; ++k) {
+        const int x = threadIdx.x + k * kStreamThreads;
+        if (x < NV) s_v[x] = val[k];
+    }
+}
+
+__device__ __forceinline__ void stage_spin_tile(const SweepArgs& a, int w, int i0, int j0, uint32_t* s_v) {
+    if (a.g.L >= 2 * kTJ)
+        stage_spin_tile<true>(a, w, i0, j0, s_v);
+    else
+        stage_spin_tile<false>(a, w, i0, j0, s_v);
+}
+
+// Stage the hidden words of cells i0 - 1 .. i0 + TI - 1 x j0 - 1 .. j0 + TJ - 1
+// (wrapped) of half-word w into s_h[(TI + 1)][(TJ + 1)][32], 16 bytes per
+// load, in batches whose loads are all issued before their stores.
+// kOneWrap: W > TI, so i0 - 1 + li in [-1, W + TI - 2] wraps with one add or
+// subtraction of W.
+template <bool kOneWrap>
+__device__ __forceinline__ void stage_hidden_halo(const SweepArgs& a, int w, int i0, int j0, uint32_t* s_h) {
+    constexpr int HS = kTJ + 1, NQ = (kTI + 1) * HS * 8;  // 8 uint4 per cell
+    constexpr int IT = (NQ + kStreamVisThreads - 1) / kStreamVisThreads;
+    constexpr int B = 5;  // loads in flight per thread
+    const int W = a.g.W;
+    const uint4* hw = reinterpret_cast<const uint4*>(a.h + static_cast<size_t>(w) * a.g.n_cells * 32);
+#pragma unroll
+    for (int k0 = 0; k0 < IT; k0 += B) {
+        uint4 val[B];
+#pragma unroll
+        for (int k = 0; k < B; ++k) {
+            const int x = threadIdx.x + (k0 + k) * kStreamVisThreads;
+            const int lcell = x >> 3, q = x & 7;
+            const int li = lcell / HS, lj = lcell - (lcell / HS) * HS;
+            int gi = i0 - 1 + li, gj = j0 - 1 + lj;
+            if (kOneWrap) {
+                gi += gi < 0 ? W : 0;
+                gi -= gi >= W ? W : 0;
+                gj += gj < 0 ? W : 0;
+                gj -= gj >= W ? W : 0;
+            } else {
+                gi = (gi % W + W) % W;
+                gj = (gj % W + W) % W;
+            }
+            val[k] = make_uint4(0u, 0u, 0u, 0u);
+            if (k0 + k < IT && x < NQ) val[k] = hw[(gi * W + gj) * 8 + q];
+        }
+#pragma unroll
+        for (int k = 0; k < B; ++k) {
+            const int x = threadIdx.x + (k0 + k) * kStreamVisThreads;
+            if (k0 + k < IT && x < NQ) reinterpret_cast<uint4*>(s_h)[x] = val[k];
+        }
+    }
 }
 
 // Hidden half-step of one tile: v tile rows 2 i0 .. 2 i0 + 2 TI and columns
 // 2 j0 .. 2 j0 + 2 TJ (wrapped), the lanes' hidden words out to
 // h[word][cell][32].
-__global__ void __launch_bounds__(kStreamThreads, 4) k_stream_hidden(const SweepArgs a, uint32_t t) {
+__global__ void __launch_bounds__(kStreamThreads, CRBM_STREAM_MIN_BLOCKS) k_stream_hidden(const SweepArgs a, uint32_t t) {
     __shared__ __align__(16) uint32_t s_th[kCanonTh];
     __shared__ uint32_t s_v[(2 * kTI + 1) * (2 * kTJ + 1)];
-    __shared__ uint32_t s_h[kTI * kTJ * 32];
+    __shared__ __align__(16) uint32_t s_h[kTI * kTJ * 32];
     const Geometry& g = a.g;
-    const int L = g.L, W = g.W, N = g.N;
+    const int W = g.W;
     const int w = blockIdx.y;
     const int tiles_j = (W + kTJ - 1) / kTJ;
     const int i0 = (blockIdx.x / tiles_j) * kTI, j0 = (blockIdx.x % tiles_j) * kTJ;
@@ -37,11 +131,7 @@ __global__ void __launch_bounds__(kStreamThreads, 4) k_stream_hidden(const Sweep
     const uint32_t* gt = a.ctab + static_cast<size_t>(w) * kCanonTab;
     for (int x = threadIdx.x; x < kCanonTh; x += blockDim.x) s_th[x] = gt[x];
     constexpr int VS = 2 * kTJ + 1;
-    for (int x = threadIdx.x; x < (2 * kTI + 1) * VS; x += blockDim.x) {
-        const int r = x / VS, c = x - (x / VS) * VS;
-        const int R = (2 * i0 + r) % L, C = (2 * j0 + c) % L;
-        s_v[x] = a.v[vidx(w, N, R * L + C)];
-    }
+    stage_spin_tile(a, w, i0, j0, s_v);
     const uint32_t chain = static_cast<uint32_t>(w) * 32u + lane;
     const LaneConst lc = lane_const(lane, lane);
     const Round0Lane r0l = round0_lane(chain);
@@ -57,19 +147,21 @@ __global__ void __launch_bounds__(kStreamThreads, 4) k_stream_hidden(const Sweep
                         round0_cell(static_cast<uint32_t>(gi * W + gj), a.rk[1]), a.rk, lc);
     }
     __syncthreads();
+    // tile rows of hidden words are contiguous runs of nj * 32 words in h
     const int nj = min(kTJ, W - j0);
-    for (int x = threadIdx.x; x < kTI * kTJ * 32; x += blockDim.x) {
-        const int li = x / (kTJ * 32), rest = x - li * (kTJ * 32);
-        if (i0 + li >= W || rest >= nj * 32) continue;
-        a.h[(static_cast<size_t>(w) * g.n_cells + (i0 + li) * W + j0) * 32 + rest] = s_h[x];
+    for (int x = threadIdx.x; x < kTI * kTJ * 8; x += blockDim.x) {
+        const int li = x / (kTJ * 8), rest = x - li * (kTJ * 8);
+        if (i0 + li >= W || rest >= nj * 8) continue;
+        reinterpret_cast<uint4*>(a.h + (static_cast<size_t>(w) * g.n_cells + (i0 + li) * W + j0) * 32)[rest] =
+            reinterpret_cast<const uint4*>(s_h)[x];
     }
 }
 
 // Visible half-step of one tile: hidden words of the tile cells plus the row
 // of cells above and the column to the left (wrapped), new spins out.
-__global__ void __launch_bounds__(kStreamThreads, 4) k_stream_visible(const SweepArgs a, uint32_t t) {
+__global__ void __launch_bounds__(kStreamVisThreads, CRBM_STREAM_VIS_MIN_BLOCKS) k_stream_visible(const SweepArgs a, uint32_t t) {
     __shared__ __align__(16) uint32_t s_tv[4 * 32 * 32];
-    __shared__ uint32_t s_h[(kTI + 1) * (kTJ + 1) * 32];
+    __shared__ __align__(16) uint32_t s_h[(kTI + 1) * (kTJ + 1) * 32];
     __shared__ uint32_t s_o[2 * kTI * 2 * kTJ];
     const Geometry& g = a.g;
     const int L = g.L, W = g.W, N = g.N;
@@ -80,12 +172,10 @@ __global__ void __launch_bounds__(kStreamThreads, 4) k_stream_visible(const Swee
     const uint4* gt = reinterpret_cast<const uint4*>(a.ctab + static_cast<size_t>(w) * kCanonTab + kCanonTh);
     for (int x = threadIdx.x; x < 4 * 32 * 32 / 4; x += blockDim.x) reinterpret_cast<uint4*>(s_tv)[x] = gt[x];
     constexpr int HS = kTJ + 1;
-    for (int x = threadIdx.x; x < (kTI + 1) * HS * 32; x += blockDim.x) {
-        const int lcell = x >> 5, k = x & 31;
-        const int li = lcell / HS, lj = lcell - (lcell / HS) * HS;
-        const int gi = (i0 - 1 + li + W) % W, gj = (j0 - 1 + lj + W) % W;
-        s_h[x] = a.h[(static_cast<size_t>(w) * g.n_cells + gi * W + gj) * 32 + k];
-    }
+    if (W > kTI)
+        stage_hidden_halo<true>(a, w, i0, j0, s_h);
+    else
+        stage_hidden_halo<false>(a, w, i0, j0, s_h);
     const uint32_t chain = static_cast<uint32_t>(w) * 32u + lane;
     const LaneConst lc = lane_const(lane, lane);
     const Round0Lane r0l = round0_lane(chain);
@@ -111,21 +201,17 @@ __global__ void __launch_bounds__(kStreamThreads, 4) k_stream_visible(const Swee
 
 // Measurement counts of one tile (anti-aligned J / J' filters and +1 spins
 // per chain), summed over the CTA in shared memory, then into cnt[chain][3].
-__global__ void __launch_bounds__(kStreamThreads, 4) k_stream_count(const SweepArgs a) {
+__global__ void __launch_bounds__(kStreamThreads, CRBM_STREAM_MIN_BLOCKS) k_stream_count(const SweepArgs a) {
     __shared__ uint32_t s_v[(2 * kTI + 1) * (2 * kTJ + 1)];
     __shared__ int s_cnt[96];
     const Geometry& g = a.g;
-    const int L = g.L, W = g.W, N = g.N;
+    const int W = g.W;
     const int w = blockIdx.y;
     const int tiles_j = (W + kTJ - 1) / kTJ;
     const int i0 = (blockIdx.x / tiles_j) * kTI, j0 = (blockIdx.x % tiles_j) * kTJ;
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nwarp = blockDim.x >> 5;
     constexpr int VS = 2 * kTJ + 1;
-    for (int x = threadIdx.x; x < (2 * kTI + 1) * VS; x += blockDim.x) {
-        const int r = x / VS, c = x - (x / VS) * VS;
-        const int R = (2 * i0 + r) % L, C = (2 * j0 + c) % L;
-        s_v[x] = a.v[vidx(w, N, R * L + C)];
-    }
+    stage_spin_tile(a, w, i0, j0, s_v);
     for (int x = threadIdx.x; x < 96; x += blockDim.x) s_cnt[x] = 0;
     __syncthreads();
     int anti0 = 0, anti1 = 0, pos = 0;
@@ -185,7 +271,7 @@ cudaError_t launch_sweep_stream(const SweepArgs& a, cudaStream_t st, int64_t* la
     for (int it = 0; it < a.n_sweeps; ++it) {
         const uint32_t t = a.t0 + static_cast<uint32_t>(it);
         k_stream_hidden<<<grid, kStreamThreads, 0, st>>>(a, t);
-        k_stream_visible<<<grid, kStreamThreads, 0, st>>>(a, t);
+        k_stream_visible<<<grid, kStreamVisThreads, 0, st>>>(a, t);
         *launches += 2;
         if (a.measure_every > 0 && (t + 1u) % static_cast<uint32_t>(a.measure_every) == 0u) {
             k_stream_count<<<grid, kStreamThreads, 0, st>>>(a);

@@ -16,7 +16,7 @@ namespace {
 using namespace dev;
 using namespace canon;
 
-__global__ void __launch_bounds__(512, CRBM_SWEEP_MIN_BLOCKS) k_sweep_canon(const SweepArgs a) {
+__global__ void __launch_bounds__(CRBM_SWEEP_MAX_THREADS, CRBM_SWEEP_MIN_BLOCKS) k_sweep_canon(const SweepArgs a) {
     sweep_canon_body(a, blockIdx.x, a.t0, a.n_sweeps, a.meas0);
 }
 
@@ -26,7 +26,7 @@ __global__ void __launch_bounds__(512, CRBM_SWEEP_MIN_BLOCKS) k_sweep_canon(cons
 // is n_words lower, held by a resident CTA, so the wait ends); the wait is
 // bounded and, if it gives up, sets the error word and the CTA stops.  Every
 // SM stays busy until the last chunks, whatever the number of words.
-__global__ void __launch_bounds__(512, CRBM_SWEEP_MIN_BLOCKS)
+__global__ void __launch_bounds__(CRBM_SWEEP_MAX_THREADS, CRBM_SWEEP_MIN_BLOCKS)
     k_sweep_canon_persistent(const SweepArgs a, int chunk, int* counter, int* done, int* err) {
     __shared__ int s_item, s_ok;
     const int n_chunks = (a.n_sweeps + chunk - 1) / chunk;

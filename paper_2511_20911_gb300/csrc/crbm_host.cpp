@@ -193,10 +193,10 @@ void free_device(DeviceState& d) {
 int default_warps(const Geometry& g) {
     if (const char* env = std::getenv("CRBM_WARPS")) {
         const int w = std::atoi(env);
-        if (w >= 1 && w <= 16) return w;
+        if (w >= 1 && w <= kMaxSweepWarps) return w;
     }
     // about six cells per warp, up to 16 warps per CTA
-    return std::max(1, std::min(16, (g.n_cells + 5) / 6));
+    return std::max(1, std::min(std::min(16, kMaxSweepWarps), (g.n_cells + 5) / 6));
 }
 
 }  // namespace

@@ -13,6 +13,10 @@ __host__ __device__ inline size_t word_index(int vil, int w, int N, int s) {
                : static_cast<size_t>(w) * N + s;
 }
 
+#ifndef CRBM_SWEEP_MAX_THREADS
+#define CRBM_SWEEP_MAX_THREADS 512
+#endif
+constexpr int kMaxSweepWarps = CRBM_SWEEP_MAX_THREADS / 32;  // warps per CTA of the SMEM sweeps
 constexpr int kMaxBonds = 16;  // filters per 3x3 window -> at most 4 hidden Philox calls
 constexpr int kNSum = 11;      // per-chain observable sums
 constexpr int kAccWords = kNSum * 32 * 2;  // shared-memory words of the [kNSum][32] int64 running sums

@@ -137,21 +137,20 @@ __global__ void __launch_bounds__(kStreamThreads, CRBM_STREAM_MIN_BLOCKS) k_stre
     const Round0Lane r0l = round0_lane(chain);
     const uint32_t X = r0l.hi ^ t ^ a.rk[0];
     __syncthreads();
-    for (int lcell = warp; lcell < kTI * kTJ; lcell += nwarp) {
-        const int li = lcell / kTJ, lj = lcell - (lcell / kTJ) * kTJ;
-        const int gi = i0 + li, gj = j0 + lj;
-        if (gi >= W || gj >= W) continue;
-        const int r0 = 2 * li * VS, c0 = 2 * lj;
-        s_h[lcell * 32 + lane] =
-            hidden_cell(s_v, r0, r0 + VS, r0 + 2 * VS, c0, c0 + 1, c0 + 2, s_th, X, r0l.lo,
-                        round0_cell(static_cast<uint32_t>(gi * W + gj), a.rk[1]), a.rk, lc);
+    // warp = columns lj of the tile, cells walked down the column
+    const int ni = min(kTI, W - i0), nj = min(kTJ, W - j0);
+    for (int lj = warp; lj < nj; lj += nwarp) {
+        const uint32_t* v = s_v + 2 * lj;
+        uint32_t* hp = s_h + lj * 32 + lane;
+        uint32_t cell = static_cast<uint32_t>(i0 * W + j0 + lj);
+        for (int li = 0; li < ni; ++li, v += 2 * VS, hp += kTJ * 32, cell += static_cast<uint32_t>(W))
+            *hp = hidden_cell(v, 0, VS, 2 * VS, 0, 1, 2, s_th, X, r0l.lo, round0_cell(cell, a.rk[1]), a.rk, lc);
     }
     __syncthreads();
     // tile rows of hidden words are contiguous runs of nj * 32 words in h
-    const int nj = min(kTJ, W - j0);
     for (int x = threadIdx.x; x < kTI * kTJ * 8; x += blockDim.x) {
         const int li = x / (kTJ * 8), rest = x - li * (kTJ * 8);
-        if (i0 + li >= W || rest >= nj * 8) continue;
+        if (li >= ni || rest >= nj * 8) continue;
         reinterpret_cast<uint4*>(a.h + (static_cast<size_t>(w) * g.n_cells + (i0 + li) * W + j0) * 32)[rest] =
             reinterpret_cast<const uint4*>(s_h)[x];
     }
@@ -182,13 +181,14 @@ __global__ void __launch_bounds__(kStreamVisThreads, CRBM_STREAM_VIS_MIN_BLOCKS)
     const uint32_t X = r0l.hi ^ t ^ a.rk[0];
     __syncthreads();
     constexpr int VO = 2 * kTJ;
-    for (int lcell = warp; lcell < kTI * kTJ; lcell += nwarp) {
-        const int li = lcell / kTJ, lj = lcell - (lcell / kTJ) * kTJ;
-        const int gi = i0 + li, gj = j0 + lj;
-        if (gi >= W || gj >= W) continue;
-        const uint32_t* ho = s_h + ((li + 1) * HS + lj + 1) * 32 + lane;
-        visible_cell(s_o + 2 * li * VO + 2 * lj, VO, ho[0], ho[-HS * 32], ho[-32], s_tv, X, r0l.lo,
-                     round0_cell(static_cast<uint32_t>(gi * W + gj), a.rk[1]), a.rk, lc);
+    const int ni = min(kTI, W - i0), nj = min(kTJ, W - j0);
+    for (int lj = warp; lj < nj; lj += nwarp) {
+        const uint32_t* ho = s_h + (HS + lj + 1) * 32 + lane;
+        uint32_t* o = s_o + 2 * lj;
+        uint32_t cell = static_cast<uint32_t>(i0 * W + j0 + lj);
+        for (int li = 0; li < ni; ++li, ho += HS * 32, o += 2 * VO, cell += static_cast<uint32_t>(W))
+            visible_cell(o, VO, ho[0], ho[-HS * 32], ho[-32], s_tv, X, r0l.lo, round0_cell(cell, a.rk[1]), a.rk,
+                         lc);
     }
     __syncthreads();
     for (int x = threadIdx.x; x < 2 * kTI * VO; x += blockDim.x) {
@@ -215,12 +215,10 @@ __global__ void __launch_bounds__(kStreamThreads, CRBM_STREAM_MIN_BLOCKS) k_stre
     for (int x = threadIdx.x; x < 96; x += blockDim.x) s_cnt[x] = 0;
     __syncthreads();
     int anti0 = 0, anti1 = 0, pos = 0;
-    for (int lcell = warp; lcell < kTI * kTJ; lcell += nwarp) {
-        const int li = lcell / kTJ, lj = lcell - (lcell / kTJ) * kTJ;
-        if (i0 + li >= W || j0 + lj >= W) continue;
-        const int r0 = 2 * li * VS, c0 = 2 * lj;
-        count_cell(s_v, r0, r0 + VS, r0 + 2 * VS, c0, c0 + 1, c0 + 2, lane, anti0, anti1, pos);
-    }
+    const int ni = min(kTI, W - i0), nj = min(kTJ, W - j0);
+    for (int lj = warp; lj < nj; lj += nwarp)
+        for (int li = 0; li < ni; ++li)
+            count_cell(s_v + 2 * li * VS + 2 * lj, 0, VS, 2 * VS, 0, 1, 2, lane, anti0, anti1, pos);
     atomicAdd(&s_cnt[lane], anti0);
     atomicAdd(&s_cnt[32 + lane], anti1);
     atomicAdd(&s_cnt[64 + lane], pos);

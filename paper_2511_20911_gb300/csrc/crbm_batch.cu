@@ -15,7 +15,7 @@ __global__ void __launch_bounds__(512, 1) k_sweep_batch(const __grid_constant__ 
     const int2 item = b.items[blockIdx.x];
     const SweepArgs& a = b.d[item.x];
     if (a.g.canonical)
-        canon::sweep_canon_body(a, item.y, static_cast<uint32_t>(a.clock[0]), a.n_sweeps, a.clock[1]);
+        canon::sweep_canon_body<false>(a, item.y, static_cast<uint32_t>(a.clock[0]), a.n_sweeps, a.clock[1]);
     else
         generic::sweep_generic_body(a, item.y);
 }

@@ -8,6 +8,11 @@
 namespace crbm {
 namespace canon {
 
+template <bool kSmem>
+__device__ __forceinline__ uint4 ld_rec(const uint4* p) {
+    return kSmem ? *p : __ldg(p);
+}
+
 // Whole-run body of the canonical SMEM-resident sweep for packed word `word`
 // (one CTA): load tables, spins and replica permutation into shared memory,
 // run n_sweeps sweeps from global sweep t0 (measurement index meas0) with
@@ -15,6 +20,10 @@ namespace canon {
 // write the state back.
 // State is read with L1-bypassing loads: under the persistent scheduler the
 // previous chunk of this word may have been written by another SM.
+// kSmemRec: the per-cell records are first copied into shared memory after
+// the replica tables (canon_smem_records() decides on the host), else read
+// through the read-only cache.
+template <bool kSmemRec>
 __device__ __forceinline__ void sweep_canon_body(const SweepArgs& a, int word, uint32_t t0,
                                                  int n_sweeps, int64_t meas0) {
     extern __shared__ __align__(16) uint32_t smem[];
@@ -30,6 +39,12 @@ __device__ __forceinline__ void sweep_canon_body(const SweepArgs& a, int word, u
     uint32_t* s_segmask = reinterpret_cast<uint32_t*>(s_seg + 33); // [32]
     int* s_sob = reinterpret_cast<int*>(s_segmask + 32);          // [32] slot of each rung
     int* s_bos = s_sob + 32;                                        // [32] rung of each slot
+    const uint4* recs = a.crec;
+    if (kSmemRec) {  // [n_cells][kCellRec] records, 16-byte aligned
+        uint4* s_rec = reinterpret_cast<uint4*>(smem + canon_smem_rec_offset(g));
+        for (int x = threadIdx.x; x < g.n_cells * kCellRec; x += blockDim.x) s_rec[x] = __ldg(a.crec + x);
+        recs = s_rec;
+    }
 
     const uint4* gt = reinterpret_cast<const uint4*>(a.ctab + static_cast<size_t>(word) * kCanonTab);
     for (int x = threadIdx.x; x < kCanonTab / 4; x += blockDim.x) reinterpret_cast<uint4*>(s_th)[x] = gt[x];
@@ -62,7 +77,7 @@ __device__ __forceinline__ void sweep_canon_body(const SweepArgs& a, int word, u
     // kCellRec records (shared-memory byte offsets and round-0 Philox words).
     char* sm = reinterpret_cast<char*>(smem);
     const uint32_t lane4 = 4u * static_cast<uint32_t>(lane);
-    const uint4* rec0 = a.crec + static_cast<size_t>(warp) * kCellRec;
+    const uint4* rec0 = recs + static_cast<size_t>(warp) * kCellRec;
     const int rstep = nwarp * kCellRec;
 
     for (int it = 0; it < n_sweeps; ++it) {
@@ -70,13 +85,13 @@ __device__ __forceinline__ void sweep_canon_body(const SweepArgs& a, int word, u
         const uint32_t X = r0l.hi ^ t ^ a.rk[0];
         const uint4* rec = rec0;
         for (int cell = warp; cell < g.n_cells; cell += nwarp, rec += rstep) {
-            const uint4 h0 = __ldg(rec), h1 = __ldg(rec + 1);
+            const uint4 h0 = ld_rec<kSmemRec>(rec), h1 = ld_rec<kSmemRec>(rec + 1);
             sts_off(sm, h1.y + lane4, hidden_cell_rec(sm, h0, h1, s_th, X, r0l.lo, a.rk, lc));
         }
         __syncthreads();
         rec = rec0;
         for (int cell = warp; cell < g.n_cells; cell += nwarp, rec += rstep) {
-            const uint4 v0 = __ldg(rec + 2), v1 = __ldg(rec + 3);
+            const uint4 v0 = ld_rec<kSmemRec>(rec + 2), v1 = ld_rec<kSmemRec>(rec + 3);
             visible_cell_rec(sm, v0, v1, lane4, s_tv, X, r0l.lo, a.rk, lc);
         }
         __syncthreads();
@@ -86,7 +101,7 @@ __device__ __forceinline__ void sweep_canon_body(const SweepArgs& a, int word, u
             int anti0 = 0, anti1 = 0, pos = 0;
             const uint4* rec = rec0;
             for (int cell = warp; cell < g.n_cells; cell += nwarp, rec += rstep)
-                count_cell_rec(sm, __ldg(rec), __ldg(rec + 1), lane, anti0, anti1, pos);
+                count_cell_rec(sm, ld_rec<kSmemRec>(rec), ld_rec<kSmemRec>(rec + 1), lane, anti0, anti1, pos);
             atomicAdd(&s_cnt[lane], anti0);
             atomicAdd(&s_cnt[32 + lane], anti1);
             atomicAdd(&s_cnt[64 + lane], pos);

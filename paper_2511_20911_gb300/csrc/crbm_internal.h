@@ -70,6 +70,14 @@ struct Geometry {
     uint8_t cls[kMaxBonds];
 };
 
+// Word offset of the records when the sweep copies them into shared memory:
+// after [kCanonSmemV][N][n_cells x 32][3 x 32 counters][33 segments][32 masks]
+// [32][32] replica tables, rounded up to 16 bytes.
+__host__ __device__ inline size_t canon_smem_rec_offset(const Geometry& g) {
+    return (static_cast<size_t>(kCanonSmemV) + g.N + static_cast<size_t>(g.n_cells) * 32 + 96 + 33 + 32 + 64 + 3) &
+           ~static_cast<size_t>(3);
+}
+
 // Device buffers of one context (all owned by the context).
 struct DeviceState {
     uint32_t* v = nullptr;        // [n_words][N] packed spins, bit l = chain 32w + l
@@ -152,6 +160,11 @@ struct BatchArgs {
 // Kernel launchers (crbm_kernels.cu).  All return cudaGetLastError().
 size_t smem_bytes_generic(const Geometry& g);
 size_t smem_bytes_canon(const Geometry& g);
+// Whether the canonical persistent sweep keeps the per-cell records in shared
+// memory (when that does not lower the CTAs per SM), and its dynamic shared
+// memory with that choice.
+bool canon_smem_records(const Geometry& g);
+size_t smem_bytes_canon_launch(const Geometry& g);
 cudaError_t launch_init(const Geometry& g, uint32_t* v, int n_words, uint32_t key0,
                         uint32_t key1, cudaStream_t st);
 cudaError_t launch_sweep_generic(const SweepArgs& a, int warps_per_cta, cudaStream_t st);

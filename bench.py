@@ -39,6 +39,14 @@ SM_COUNT, SM_MAX_MHZ = 152, 2070.0
 IMUL_LANES_PER_SM_CLK = 64
 MUL_OPS_PER_CALL = 40
 CALLS_PER_CELL = 4          # 3 hidden calls (10 filters) + 1 visible call (4 spins) per cell
+# DRAM bytes (read + write) of the timed unit, from one ncu capture of the
+# kernels as they stand (commands in the named profiles/ summaries): one bench
+# launch of k_sweep_canon_persistent (2000 sweeps of the L=18 grid), and one
+# streamed sweep of the L=384 lattice (k_stream_hidden + k_stream_visible).
+MEASURED_TRAFFIC = {
+    "grid": (8.35e6 + 0.417e6, "per launch; profiles/k_sweep_canon_persistent_L18_grid.md"),
+    "stream": (56.74e6 + 392.23e6 + 454.64e6 + 49.61e6, "per sweep (two launches); profiles/k_stream_L384.md"),
+}
 
 
 def parse():
@@ -442,7 +450,8 @@ def main():
                 "note": "0.25 B (SMEM layout: spins in and out once per launch) or 0.875 B "
                         "(streamed: spins 2 bits + hidden 5 bits per spin-update) of algorithmic traffic"},
         "roofline": {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "Tops/s",
-                     "frac": achieved / peak, "traffic": None,
+                     "frac": achieved / peak, "traffic": MEASURED_TRAFFIC[args.workload][0],
+                     "traffic_unit": "bytes " + MEASURED_TRAFFIC[args.workload][1],
                      "note": "integer-multiply ceiling: 152 SM x 64 lanes/clk x 2070 MHz; 40 "
                              "multiply ops per Philox-4x32-10 call, 4 calls per chain-cell-sweep",
                      "philox_calls_per_s": calls / (t_total / K)},

@@ -1,7 +1,8 @@
-// SMEM-resident sweep, canonical SS fast path: one CTA per packed word (32
-// chains) holding the whole even, periodic lattice, its hidden layer and the
-// lane-expanded tables in shared memory, all n_sweeps sweeps on device.  The
-// per-cell cores are in crbm_canon_core.cuh.
+// SMEM-resident sweep, canonical SS fast path: a CTA holds one packed word
+// (32 chains) -- the whole even, periodic lattice, its hidden layer and the
+// lane-expanded tables -- in shared memory and runs a chunk of sweeps on it.
+// The sweep body is in crbm_canon_body.cuh, the per-cell cores in
+// crbm_canon_core.cuh.
 #include <algorithm>
 
 #include "crbm_canon_body.cuh"
@@ -15,10 +16,6 @@ namespace {
 
 using namespace dev;
 using namespace canon;
-
-__global__ void __launch_bounds__(CRBM_SWEEP_MAX_THREADS, CRBM_SWEEP_MIN_BLOCKS) k_sweep_canon(const SweepArgs a) {
-    sweep_canon_body<false>(a, blockIdx.x, a.t0, a.n_sweeps, a.meas0);
-}
 
 // Persistent form: a grid that fits on the GPU at once takes work items
 // (word, chunk of `chunk` sweeps) in ticket order from a global counter.
@@ -88,17 +85,6 @@ size_t smem_bytes_canon_launch(const Geometry& g) {
 size_t smem_bytes_canon(const Geometry& g) {
     return sizeof(uint32_t) * (static_cast<size_t>(kAccWords) + kCanonTab + g.N + static_cast<size_t>(g.n_cells) * 32 +
                                96 + 33 + 32 + 64);
-}
-
-cudaError_t launch_sweep_canon(const SweepArgs& a, int warps_per_cta, cudaStream_t st) {
-    const size_t smem = smem_bytes_canon(a.g);
-    if (smem > 48 * 1024) {
-        const cudaError_t e = cudaFuncSetAttribute(k_sweep_canon, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                                   static_cast<int>(smem));
-        if (e != cudaSuccess) return e;
-    }
-    k_sweep_canon<<<a.n_words, warps_per_cta * 32, smem, st>>>(a);
-    return cudaGetLastError();
 }
 
 namespace {

@@ -168,7 +168,6 @@ size_t smem_bytes_canon_launch(const Geometry& g);
 cudaError_t launch_init(const Geometry& g, uint32_t* v, int n_words, uint32_t key0,
                         uint32_t key1, cudaStream_t st);
 cudaError_t launch_sweep_generic(const SweepArgs& a, int warps_per_cta, cudaStream_t st);
-cudaError_t launch_sweep_canon(const SweepArgs& a, int warps_per_cta, cudaStream_t st);
 cudaError_t launch_sweep_canon_persistent(const SweepArgs& a, int warps_per_cta, int chunk, int* sched,
                                           int* err, cudaStream_t st);
 cudaError_t launch_sweep_stream(const SweepArgs& a, cudaStream_t st, int64_t* launches);

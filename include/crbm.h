@@ -50,7 +50,7 @@ extern "C" {
 #define CRBM_EINVAL -1       /* bad argument or buffer size */
 #define CRBM_ENOMEM -2       /* device or host allocation failed */
 #define CRBM_ECUDA -3        /* a CUDA runtime call failed */
-#define CRBM_ETIMEOUT -4     /* a bounded device-side wait gave up */
+#define CRBM_ETIMEOUT -4     /* reserved: a bounded device-side wait gave up (no kernel of this build waits) */
 #define CRBM_EUNSUPPORTED -5 /* valid request this build cannot serve */
 
 #define CRBM_NSUM 11 /* per-chain observable sums, see crbm_observables */

@@ -17,41 +17,75 @@ namespace {
 using namespace dev;
 using namespace canon;
 
-// Persistent form: a grid that fits on the GPU at once takes work items
-// (word, chunk of `chunk` sweeps) in ticket order from a global counter.
-// Chunk c of a word waits until chunk c-1 of that word is done (its ticket
-// is n_words lower, held by a resident CTA, so the wait ends); the wait is
-// bounded and, if it gives up, sets the error word and the CTA stops.  Every
-// SM stays busy until the last chunks, whatever the number of words.
+// Persistent form: a grid that fits on the GPU at once works through items
+// (word, chunk of `chunk` sweeps).  Chunks of a word run in order, one CTA at
+// a time.  state[w] = 2 (chunks of w done) + (1 while a CTA holds w).  A CTA
+// claims, with a compare-and-swap on state, the free word with the fewest
+// chunks done (warp 0 scans all states with 16-byte loads; ties go to the
+// first word in a CTA-dependent scan order), runs its next chunk, publishes
+// the word's spins and sums, then releases it with the new count and claims
+// again.  A CTA that finds no free unfinished word exits: every unfinished
+// word is then held by a running CTA, which claims again after its chunk, so
+// no work is left behind and nothing waits.
 template <bool kSmemRec>
 __global__ void __launch_bounds__(CRBM_SWEEP_MAX_THREADS, CRBM_SWEEP_MIN_BLOCKS)
-    k_sweep_canon_persistent(const SweepArgs a, int chunk, int* counter, int* done, int* err) {
-    __shared__ int s_item, s_ok;
+    k_sweep_canon_persistent(const SweepArgs a, int chunk, int* state) {
+    __shared__ int s_word, s_chunk;
     const int n_chunks = (a.n_sweeps + chunk - 1) / chunk;
-    const int n_items = n_chunks * a.n_words;
+    const int nw = a.n_words, nq = (nw + 3) / 4;
     const int K = a.measure_every;
+    const int lane = threadIdx.x & 31;
+    const unsigned int start = (blockIdx.x * 97u) % static_cast<unsigned int>(nw);
     for (;;) {
-        if (threadIdx.x == 0) {
-            s_item = atomicAdd(counter, 1);
-            s_ok = 1;
-            const int item = s_item;
-            if (item < n_items) {
-                const int word = item % a.n_words, c = item / a.n_words;
-                unsigned int spins = 0;
-                while (ld_acquire(done + word) < c) {
-                    if (++spins > (1u << 26)) {  // about 7 s: the predecessor never finished
-                        atomicExch(err, 1);
-                        s_ok = 0;
-                        break;
+        if (threadIdx.x < 32) {
+            int word = -1, c = 0;
+            for (int tries = 0; tries < (1 << 20) && word < 0; ++tries) {
+                int best = 0x7fffffff, bk = 0x7fffffff, bw = -1;  // (chunks done, scan rank, word)
+                for (int q = lane; q < nq; q += 32) {
+                    const int4 v = __ldcg(reinterpret_cast<const int4*>(state) + q);
+                    const int sv[4] = {v.x, v.y, v.z, v.w};
+#pragma unroll
+                    for (int j = 0; j < 4; ++j) {
+                        const int w = 4 * q + j;
+                        const int dw = sv[j] >> 1;
+                        const int rank = static_cast<int>((static_cast<unsigned int>(w) + nw - start) %
+                                                          static_cast<unsigned int>(nw));
+                        if (w < nw && (sv[j] & 1) == 0 && dw < n_chunks &&
+                            (dw < best || (dw == best && rank < bk))) {
+                            best = dw;
+                            bk = rank;
+                            bw = w;
+                        }
                     }
-                    __nanosleep(100);
                 }
+#pragma unroll
+                for (int o = 16; o > 0; o >>= 1) {
+                    const int ob = __shfl_xor_sync(0xffffffffu, best, o);
+                    const int ok = __shfl_xor_sync(0xffffffffu, bk, o);
+                    const int ow = __shfl_xor_sync(0xffffffffu, bw, o);
+                    if (ob < best || (ob == best && ok < bk)) {
+                        best = ob;
+                        bk = ok;
+                        bw = ow;
+                    }
+                }
+                if (bw < 0) break;  // every unfinished word is held by a running CTA
+                if (lane == 0 && atomicCAS(state + bw, 2 * best, 2 * best + 1) == 2 * best) {
+                    __threadfence();  // acquire: the previous chunk's stores precede its release
+                    word = bw;
+                    c = best;
+                }
+                word = __shfl_sync(0xffffffffu, word, 0);
+                c = __shfl_sync(0xffffffffu, c, 0);
+            }
+            if (lane == 0) {
+                s_word = word;
+                s_chunk = c;
             }
         }
         __syncthreads();
-        const int item = s_item;
-        if (item >= n_items || !s_ok) break;
-        const int word = item % a.n_words, c = item / a.n_words;
+        const int word = s_word, c = s_chunk;
+        if (word < 0) break;
         const uint32_t t0 = a.t0 + static_cast<uint32_t>(c * chunk);
         const int n = min(chunk, a.n_sweeps - c * chunk);
         const int64_t meas0 =
@@ -60,7 +94,7 @@ __global__ void __launch_bounds__(CRBM_SWEEP_MAX_THREADS, CRBM_SWEEP_MIN_BLOCKS)
         __syncthreads();  // every thread's state stores are issued
         if (threadIdx.x == 0) {
             __threadfence();
-            st_release(done + word, c + 1);
+            st_release(state + word, 2 * (c + 1));
         }
     }
 }
@@ -89,8 +123,7 @@ size_t smem_bytes_canon(const Geometry& g) {
 
 namespace {
 template <bool kSmemRec>
-cudaError_t launch_persistent(const SweepArgs& a, int warps_per_cta, int chunk, int* sched, int* err,
-                              cudaStream_t st) {
+cudaError_t launch_persistent(const SweepArgs& a, int warps_per_cta, int chunk, int* sched, cudaStream_t st) {
     const size_t smem = smem_bytes_canon_launch(a.g);
     if (smem > 48 * 1024) {
         const cudaError_t e = cudaFuncSetAttribute(k_sweep_canon_persistent<kSmemRec>,
@@ -105,19 +138,19 @@ cudaError_t launch_persistent(const SweepArgs& a, int warps_per_cta, int chunk, 
     if (e != cudaSuccess) return e;
     if (per_sm < 1) return cudaErrorInvalidConfiguration;
     const int n_items = ((a.n_sweeps + chunk - 1) / chunk) * a.n_words;
-    const int grid = std::min(n_items, per_sm * sms);  // all CTAs resident: the waits always end
-    e = cudaMemsetAsync(sched, 0, sizeof(int) * (1 + static_cast<size_t>(a.n_words)), st);
+    const int grid = std::min(std::min(n_items, a.n_words), per_sm * sms);
+    e = cudaMemsetAsync(sched, 0, sizeof(int) * (4 + static_cast<size_t>(a.n_words)), st);
     if (e != cudaSuccess) return e;
-    k_sweep_canon_persistent<kSmemRec><<<grid, warps_per_cta * 32, smem, st>>>(a, chunk, sched, sched + 1, err);
+    k_sweep_canon_persistent<kSmemRec><<<grid, warps_per_cta * 32, smem, st>>>(a, chunk, sched);
     return cudaGetLastError();
 }
 
 }  // namespace
 
 cudaError_t launch_sweep_canon_persistent(const SweepArgs& a, int warps_per_cta, int chunk, int* sched,
-                                          int* err, cudaStream_t st) {
-    return canon_smem_records(a.g) ? launch_persistent<true>(a, warps_per_cta, chunk, sched, err, st)
-                                   : launch_persistent<false>(a, warps_per_cta, chunk, sched, err, st);
+                                          cudaStream_t st) {
+    return canon_smem_records(a.g) ? launch_persistent<true>(a, warps_per_cta, chunk, sched, st)
+                                   : launch_persistent<false>(a, warps_per_cta, chunk, sched, st);
 }
 
 }  // namespace crbm

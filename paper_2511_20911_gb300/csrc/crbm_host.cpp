@@ -183,7 +183,7 @@ int dalloc(crbm_ctx* ctx, T*& ptr, size_t count) {
 
 void free_device(DeviceState& d) {
     void* ptrs[] = {d.v, d.tab, d.ctab, d.crec, d.sneg, d.inc, d.inc_off, d.sums, d.series, d.corr,
-                    d.seg, d.segmask, d.spins8, d.h, d.cnt, d.err, d.sob, d.swap_tab, d.swap_off,
+                    d.seg, d.segmask, d.spins8, d.h, d.cnt, d.sob, d.swap_tab, d.swap_off,
                     d.swap_len, d.wq, d.chain_bh, d.chain_q, d.sched};
     for (void* p : ptrs)
         if (p) cudaFree(p);
@@ -500,9 +500,9 @@ int crbm_create(crbm_ctx** out, const crbm_params* p) {
         (rc = dalloc(ctx, d.series, static_cast<size_t>(p->series_len) * npad * 3)) ||
         (rc = dalloc(ctx, d.corr, p->sq_every > 0 ? static_cast<size_t>(p->n_params) * N : 1)) ||
         (rc = dalloc(ctx, d.seg, seg.size())) || (rc = dalloc(ctx, d.segmask, segmask.size())) ||
-        (rc = dalloc(ctx, d.spins8, static_cast<size_t>(npad) * N)) || (rc = dalloc(ctx, d.err, 4)) ||
+        (rc = dalloc(ctx, d.spins8, static_cast<size_t>(npad) * N)) ||
         (rc = dalloc(ctx, d.sob, static_cast<size_t>(npad))) ||
-        (rc = dalloc(ctx, d.sched, 1 + static_cast<size_t>(nw))) ||
+        (rc = dalloc(ctx, d.sched, 4 + static_cast<size_t>(nw))) ||
         (rc = dalloc(ctx, d.swap_tab, swap_tab.size())) || (rc = dalloc(ctx, d.swap_off, swap_off.size())) ||
         (rc = dalloc(ctx, d.swap_len, swap_len.size())) || (rc = dalloc(ctx, d.wq, wq.size())) ||
         (g.vil && (rc = dalloc(ctx, d.h, static_cast<size_t>(nw) * g.n_cells * 32))) ||
@@ -538,7 +538,6 @@ int crbm_create(crbm_ctx** out, const crbm_params* p) {
     if (e == cudaSuccess && p->sq_every)
         e = cudaMemsetAsync(d.corr, 0, static_cast<size_t>(p->n_params) * N * 8, st);
     if (e == cudaSuccess) e = cudaMemsetAsync(d.spins8, 1, static_cast<size_t>(npad) * N, st);
-    if (e == cudaSuccess) e = cudaMemsetAsync(d.err, 0, 4, st);
     if (e == cudaSuccess && d.cnt) e = cudaMemsetAsync(d.cnt, 0, static_cast<size_t>(npad) * 12, st);
     if (e == cudaSuccess)
         e = launch_init(g, d.v, nw, static_cast<uint32_t>(ctx->seed),
@@ -587,7 +586,7 @@ int crbm_sweep(crbm_ctx* ctx, int64_t n_sweeps) {
             // 32nd of the launch (at least 8 sweeps) so that every SM stays busy
             const int chunk = std::max(8, (a.n_sweeps + 31) / 32);
             e = ctx->g.canonical
-                    ? launch_sweep_canon_persistent(a, ctx->warps, chunk, ctx->d.sched, ctx->d.err, ctx->stream)
+                    ? launch_sweep_canon_persistent(a, ctx->warps, chunk, ctx->d.sched, ctx->stream)
                     : launch_sweep_generic(a, ctx->warps, ctx->stream);
             ++ctx->launches;
         }
@@ -607,15 +606,6 @@ int64_t crbm_launch_count(const crbm_ctx* ctx) { return ctx ? ctx->launches : -1
 
 int crbm_layout(const crbm_ctx* ctx) { return ctx ? ctx->layout : CRBM_EINVAL; }
 
-namespace {
-// After a synchronising read: did a bounded device-side wait give up?
-int check_device_error(crbm_ctx* ctx) {
-    int flag = 0;
-    if (cudaMemcpy(&flag, ctx->d.err, 4, cudaMemcpyDeviceToHost) != cudaSuccess) return CRBM_ECUDA;
-    if (flag) return fail(ctx, CRBM_ETIMEOUT, "a bounded device-side wait of the persistent sweep gave up");
-    return CRBM_OK;
-}
-}  // namespace
 
 int crbm_observables(crbm_ctx* ctx, int64_t* out, size_t n_out) {
     if (!ctx || !out) return CRBM_EINVAL;
@@ -623,7 +613,7 @@ int crbm_observables(crbm_ctx* ctx, int64_t* out, size_t n_out) {
     if (n_out < need) return fail(ctx, CRBM_EINVAL, "output buffer too small");
     cudaError_t e = cudaMemcpyAsync(out, ctx->d.sums, need * 8, cudaMemcpyDeviceToHost, ctx->stream);
     if (e == cudaSuccess) e = cudaStreamSynchronize(ctx->stream);
-    return e == cudaSuccess ? check_device_error(ctx) : cuda_fail(ctx, e, "crbm_observables");
+    return e == cudaSuccess ? CRBM_OK : cuda_fail(ctx, e, "crbm_observables");
 }
 
 int crbm_series(crbm_ctx* ctx, int32_t* out, size_t n_out) {
@@ -702,7 +692,7 @@ int crbm_get_spins(crbm_ctx* ctx, int8_t* out, size_t n_out) {
     ++ctx->launches;
     if (e == cudaSuccess) e = cudaMemcpyAsync(out, ctx->d.spins8, need, cudaMemcpyDeviceToHost, ctx->stream);
     if (e == cudaSuccess) e = cudaStreamSynchronize(ctx->stream);
-    return e == cudaSuccess ? check_device_error(ctx) : cuda_fail(ctx, e, "crbm_get_spins");
+    return e == cudaSuccess ? CRBM_OK : cuda_fail(ctx, e, "crbm_get_spins");
 }
 
 int crbm_set_spins(crbm_ctx* ctx, const int8_t* in, size_t n_in) {

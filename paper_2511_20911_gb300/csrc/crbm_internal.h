@@ -102,8 +102,7 @@ struct DeviceState {
     int* cnt = nullptr;           // streamed layout: [n_words * 32][3] measurement counts
     float* chain_bh = nullptr;    // block proposals: [n_words * 32][2] beta, h (bf16-rounded)
     int32_t* chain_q = nullptr;   // block proposals: [n_words * 32][3] Q.4 J, J', h
-    int* err = nullptr;           // device error word (a bounded wait gave up)
-    int* sched = nullptr;         // persistent scheduler: ticket counter, then [n_words] progress
+    int* sched = nullptr;         // persistent scheduler: [n_words + 4] word states (chunks done, held)
 };
 
 struct SweepArgs {
@@ -169,7 +168,7 @@ cudaError_t launch_init(const Geometry& g, uint32_t* v, int n_words, uint32_t ke
                         uint32_t key1, cudaStream_t st);
 cudaError_t launch_sweep_generic(const SweepArgs& a, int warps_per_cta, cudaStream_t st);
 cudaError_t launch_sweep_canon_persistent(const SweepArgs& a, int warps_per_cta, int chunk, int* sched,
-                                          int* err, cudaStream_t st);
+                                          cudaStream_t st);
 cudaError_t launch_sweep_stream(const SweepArgs& a, cudaStream_t st, int64_t* launches);
 cudaError_t launch_sweep_batch(const BatchArgs& b, int n_items, int threads, size_t smem, cudaStream_t st);
 cudaError_t launch_batch_advance(int64_t* clocks, const int* every, int n_ctx, int64_t n_sweeps, cudaStream_t st);

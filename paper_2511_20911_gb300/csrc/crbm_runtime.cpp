@@ -51,7 +51,7 @@ int smem_ok(const crbm_ctx* ctx) {
 cudaError_t launch_one(const SweepArgs& a, const crbm_ctx* ctx, int warps) {
     if (!ctx->g.canonical) return launch_sweep_generic(a, warps, ctx->stream);
     const int chunk = std::max(8, (a.n_sweeps + 31) / 32);  // as crbm_sweep does
-    return launch_sweep_canon_persistent(a, warps, chunk, ctx->d.sched, ctx->d.err, ctx->stream);
+    return launch_sweep_canon_persistent(a, warps, chunk, ctx->d.sched, ctx->stream);
 }
 
 }  // namespace

@@ -582,9 +582,11 @@ int crbm_sweep(crbm_ctx* ctx, int64_t n_sweeps) {
         if (ctx->layout == CRBM_LAYOUT_STREAM) {
             e = launch_sweep_stream(a, ctx->stream, &ctx->launches);
         } else {
-            // canonical: persistent grid over (word, chunk) items, chunks of about a
-            // 32nd of the launch (at least 8 sweeps) so that every SM stays busy
-            const int chunk = std::max(8, (a.n_sweeps + 31) / 32);
+            // canonical: persistent grid over (word, chunk) items, chunks of about
+            // 1/CRBM_CHUNKS_PER_WORD of the launch (at least 8 sweeps): short
+            // enough that the last round leaves few SMs idle, long enough that
+            // reloading a word's tables and state stays cheap
+            const int chunk = std::max(8, (a.n_sweeps + CRBM_CHUNKS_PER_WORD - 1) / CRBM_CHUNKS_PER_WORD);
             e = ctx->g.canonical
                     ? launch_sweep_canon_persistent(a, ctx->warps, chunk, ctx->d.sched, ctx->stream)
                     : launch_sweep_generic(a, ctx->warps, ctx->stream);

@@ -17,6 +17,9 @@ __host__ __device__ inline size_t word_index(int vil, int w, int N, int s) {
 #define CRBM_SWEEP_MAX_THREADS 512
 #endif
 constexpr int kMaxSweepWarps = CRBM_SWEEP_MAX_THREADS / 32;  // warps per CTA of the SMEM sweeps
+#ifndef CRBM_CHUNKS_PER_WORD
+#define CRBM_CHUNKS_PER_WORD 64  // persistent SMEM sweep: a launch is about this many chunks per word
+#endif
 constexpr int kMaxBonds = 16;  // filters per 3x3 window -> at most 4 hidden Philox calls
 constexpr int kNSum = 11;      // per-chain observable sums
 constexpr int kAccWords = kNSum * 32 * 2;  // shared-memory words of the [kNSum][32] int64 running sums

@@ -50,7 +50,7 @@ int smem_ok(const crbm_ctx* ctx) {
 
 cudaError_t launch_one(const SweepArgs& a, const crbm_ctx* ctx, int warps) {
     if (!ctx->g.canonical) return launch_sweep_generic(a, warps, ctx->stream);
-    const int chunk = std::max(8, (a.n_sweeps + 31) / 32);  // as crbm_sweep does
+    const int chunk = std::max(8, (a.n_sweeps + CRBM_CHUNKS_PER_WORD - 1) / CRBM_CHUNKS_PER_WORD);  // as crbm_sweep does
     return launch_sweep_canon_persistent(a, warps, chunk, ctx->d.sched, ctx->stream);
 }
 

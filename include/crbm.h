@@ -192,12 +192,17 @@ int crbm_philox(const uint32_t* in, uint32_t* out, size_t n);
 
 /* Batched sweeps: several SMEM-layout contexts -- mixed lattice sizes,
  * filter lists and tempering ladders -- advanced together by ONE kernel
- * launch (one CTA per packed word of every member, heaviest lattices first)
- * plus a one-thread clock update, captured once in a CUDA graph and replayed
- * on the members' common stream.  Members keep their own state, counters and
- * getters; each batched call advances every member by n_sweeps sweeps,
- * bit-identical to calling crbm_sweep on each.  The CTA shape is the largest
- * warps count of the members (see crbm_autotune). */
+ * launch plus a one-thread clock update, captured once in a CUDA graph and
+ * replayed on the members' common stream.  The launch has one CTA per packed
+ * word of every member, heaviest lattices first, except that with
+ * thread-block clusters of C CTAs (environment CRBM_BATCH_CLUSTER, default 8,
+ * 1 = none) a canonical word without correlations that has at least C cell
+ * rows and 16 cells per band is split into C bands of cell rows, one cluster
+ * per word, the bands exchanging their boundary rows through distributed
+ * shared memory.  Members keep their own state, counters and getters; each
+ * batched call advances every member by n_sweeps sweeps, bit-identical to
+ * calling crbm_sweep on each.  The CTA shape is the largest warps count of
+ * the members (see crbm_autotune). */
 #define CRBM_BATCH_MAX 16
 typedef struct crbm_batch crbm_batch;
 /* Errors: CRBM_EINVAL (0 or more than CRBM_BATCH_MAX members, a repeated
@@ -207,6 +212,8 @@ int crbm_batch_create(crbm_batch** out, crbm_ctx* const* ctxs, int32_t n_ctx);
 /* Asynchronous on the members' stream.  n_sweeps in 0..2^20. */
 int crbm_batch_sweep(crbm_batch* batch, int64_t n_sweeps);
 int crbm_batch_threads(const crbm_batch* batch);
+/* Cluster size C of the batched launch (1: no clusters, no word split). */
+int crbm_batch_cluster(const crbm_batch* batch);
 /* Message for the last failed call on batch (or crbm_batch_create if NULL). */
 const char* crbm_batch_last_error(const crbm_batch* batch);
 void crbm_batch_destroy(crbm_batch* batch);

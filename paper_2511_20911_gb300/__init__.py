@@ -31,7 +31,7 @@ ABI_FUNCTIONS = (
     "crbm_series", "crbm_correlations", "crbm_structure_factor", "crbm_reset_observables",
     "crbm_get_spins", "crbm_set_spins", "crbm_get_tables", "crbm_get_permutation", "crbm_layout",
     "crbm_launch_count", "crbm_autotune", "crbm_warps", "crbm_batch_create", "crbm_batch_sweep",
-    "crbm_batch_threads", "crbm_batch_last_error", "crbm_batch_destroy",
+    "crbm_batch_threads", "crbm_batch_cluster", "crbm_batch_last_error", "crbm_batch_destroy",
     "crbm_proposal_create", "crbm_proposal_destroy", "crbm_proposal_set_weights",
     "crbm_proposal_get_weights", "crbm_proposal_train", "crbm_proposal_loss_grad",
     "crbm_proposal_pass", "crbm_sweep_mixed", "crbm_proposal_inspect", "crbm_proposal_stats",
@@ -97,6 +97,7 @@ def load_library(path: str | None = None):
         "crbm_batch_create": (c.c_int, [c.POINTER(vp), c.POINTER(vp), c.c_int32]),
         "crbm_batch_sweep": (c.c_int, [vp, c.c_int64]),
         "crbm_batch_threads": (c.c_int, [vp]),
+        "crbm_batch_cluster": (c.c_int, [vp]),
         "crbm_batch_last_error": (c.c_char_p, [vp]),
         "crbm_batch_destroy": (None, [vp]),
         "crbm_proposal_create": (c.c_int, [c.POINTER(vp), c.c_int32, c.c_uint64]),
@@ -314,6 +315,11 @@ class Batch:
     @property
     def threads(self):
         return int(self._lib.crbm_batch_threads(self._b))
+
+    @property
+    def cluster(self):
+        """CTAs per thread-block cluster of the batched launch (1: none)."""
+        return int(self._lib.crbm_batch_cluster(self._b))
 
     def close(self):
         if getattr(self, "_b", None):

@@ -1,8 +1,8 @@
 // Batched sweep: several contexts (mixed lattice sizes, filter lists and
-// tempering ladders) in one kernel launch.  Each CTA takes one (context,
-// word) item of the work list and runs the canonical or the generic
-// SMEM-resident body for it; the contexts' descriptors travel by value in
-// the kernel parameters.  Sweep and measurement counters come from a device
+// tempering ladders) in one kernel launch.  Each CTA (or cluster of CTAs)
+// takes one (context, word) item of the work list and runs the canonical or
+// the generic SMEM-resident body for it; the contexts' descriptors travel by
+// value in the kernel parameters.  Sweep and measurement counters come from a device
 // clock per context, advanced by a one-thread epilogue, so the pair of
 // launches can be captured once in a CUDA graph and replayed.
 #include "crbm_canon_body.cuh"
@@ -11,13 +11,30 @@
 namespace crbm {
 namespace {
 
-__global__ void __launch_bounds__(512, 1) k_sweep_batch(const __grid_constant__ BatchArgs b) {
-    const int2 item = b.items[blockIdx.x];
-    const SweepArgs& a = b.d[item.x];
-    if (a.g.canonical)
-        canon::sweep_canon_body<false>(a, item.y, static_cast<uint32_t>(a.clock[0]), a.n_sweeps, a.clock[1]);
+namespace cg = cooperative_groups;
+
+// One CTA per task (descriptor, word, band, bands).  kCluster: the launch
+// has thread-block clusters.  A word split into bands > 1 occupies
+// consecutive ranks of a cluster that holds only words of its context (and
+// padding ranks of that context, band >= bands), all synchronising with
+// cluster barriers; every other cluster holds whole words, one per CTA,
+// which synchronise within their CTA only; tasks with descriptor -1 return
+// at once.
+template <bool kCluster>
+__global__ void __launch_bounds__(CRBM_SWEEP_MAX_THREADS, CRBM_SWEEP_MAX_THREADS <= 512 ? 2 : 1) k_sweep_batch(const __grid_constant__ BatchArgs b) {
+    const int4 task = b.items[blockIdx.x];
+    if (task.x < 0) return;
+    const SweepArgs& a = b.d[task.x];
+    const uint32_t t0 = static_cast<uint32_t>(a.clock[0]);
+    if (!a.g.canonical)
+        generic::sweep_generic_body(a, task.y);
+    else if (kCluster && task.w > 1) {
+        const int rank = static_cast<int>(cg::this_cluster().block_rank());
+        const int rank0 = task.z < task.w ? rank - task.z : 0;
+        canon::sweep_canon_body<false, true>(a, task.y, t0, a.n_sweeps, a.clock[1], task.z, rank0);
+    }
     else
-        generic::sweep_generic_body(a, item.y);
+        canon::sweep_canon_body<false, false>(a, task.y, t0, a.n_sweeps, a.clock[1]);
 }
 
 // clocks[c] = {sweep, measurements}; every[c] = measure_every of context c.
@@ -32,14 +49,58 @@ __global__ void k_batch_advance(int64_t* clocks, const int* every, int n_ctx, in
 
 }  // namespace
 
-cudaError_t launch_sweep_batch(const BatchArgs& b, int n_items, int threads, size_t smem, cudaStream_t st) {
+cudaError_t launch_sweep_batch(const BatchArgs& b, int n_tasks, int cluster, int threads, size_t smem,
+                               cudaStream_t st) {
+    if (cluster <= 1) {
+        if (smem > 48 * 1024) {
+            const cudaError_t e = cudaFuncSetAttribute(k_sweep_batch<false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                                       static_cast<int>(smem));
+            if (e != cudaSuccess) return e;
+        }
+        k_sweep_batch<false><<<n_tasks, threads, smem, st>>>(b);
+        return cudaGetLastError();
+    }
     if (smem > 48 * 1024) {
-        const cudaError_t e = cudaFuncSetAttribute(k_sweep_batch, cudaFuncAttributeMaxDynamicSharedMemorySize,
+        const cudaError_t e = cudaFuncSetAttribute(k_sweep_batch<true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                                    static_cast<int>(smem));
         if (e != cudaSuccess) return e;
     }
-    k_sweep_batch<<<n_items, threads, smem, st>>>(b);
-    return cudaGetLastError();
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = dim3(static_cast<unsigned int>(n_tasks));
+    cfg.blockDim = dim3(static_cast<unsigned int>(threads));
+    cfg.dynamicSmemBytes = smem;
+    cfg.stream = st;
+    cudaLaunchAttribute attr[1];
+    attr[0].id = cudaLaunchAttributeClusterDimension;
+    attr[0].val.clusterDim.x = static_cast<unsigned int>(cluster);
+    attr[0].val.clusterDim.y = 1;
+    attr[0].val.clusterDim.z = 1;
+    cfg.attrs = attr;
+    cfg.numAttrs = 1;
+    return cudaLaunchKernelEx(&cfg, k_sweep_batch<true>, b);
+}
+
+int batch_max_active_clusters(int cluster, int threads, size_t smem) {
+    if (smem > 48 * 1024 && cudaFuncSetAttribute(k_sweep_batch<true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                                 static_cast<int>(smem)) != cudaSuccess)
+        return 0;
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = dim3(static_cast<unsigned int>(cluster));
+    cfg.blockDim = dim3(static_cast<unsigned int>(threads));
+    cfg.dynamicSmemBytes = smem;
+    cudaLaunchAttribute attr[1];
+    attr[0].id = cudaLaunchAttributeClusterDimension;
+    attr[0].val.clusterDim.x = static_cast<unsigned int>(cluster);
+    attr[0].val.clusterDim.y = 1;
+    attr[0].val.clusterDim.z = 1;
+    cfg.attrs = attr;
+    cfg.numAttrs = 1;
+    int n = 0;
+    if (cudaOccupancyMaxActiveClusters(&n, k_sweep_batch<true>, &cfg) != cudaSuccess) {
+        cudaGetLastError();
+        return 0;
+    }
+    return n;
 }
 
 cudaError_t launch_batch_advance(int64_t* clocks, const int* every, int n_ctx, int64_t n_sweeps, cudaStream_t st) {

@@ -8,7 +8,7 @@
 #include "crbm_canon_body.cuh"
 
 #ifndef CRBM_SWEEP_MIN_BLOCKS
-#define CRBM_SWEEP_MIN_BLOCKS 2
+#define CRBM_SWEEP_MIN_BLOCKS (CRBM_SWEEP_MAX_THREADS <= 512 ? 2 : 1)  // 64 registers a thread either way
 #endif
 
 namespace crbm {
@@ -90,7 +90,7 @@ __global__ void __launch_bounds__(CRBM_SWEEP_MAX_THREADS, CRBM_SWEEP_MIN_BLOCKS)
         const int n = min(chunk, a.n_sweeps - c * chunk);
         const int64_t meas0 =
             K > 0 ? a.meas0 + static_cast<int64_t>(t0 / K) - static_cast<int64_t>(a.t0 / K) : a.meas0;
-        sweep_canon_body<kSmemRec>(a, word, t0, n, meas0);
+        sweep_canon_body<kSmemRec, false>(a, word, t0, n, meas0);
         __syncthreads();  // every thread's state stores are issued
         if (threadIdx.x == 0) {
             __threadfence();

@@ -1,34 +1,65 @@
-// Body of the canonical SMEM-resident sweep (one CTA = one 32-chain word),
-// shared by the single-context kernel (crbm_canon.cu) and the batched kernel
-// (crbm_batch.cu).
+// Body of the canonical SMEM-resident sweep (one CTA = one 32-chain word, or
+// one band of cell rows of a word in a thread-block cluster), shared by the
+// persistent kernel (crbm_canon.cu) and the batched kernel (crbm_batch.cu).
 #pragma once
+
+#include <cooperative_groups.h>
 
 #include "crbm_canon_core.cuh"
 
 namespace crbm {
 namespace canon {
 
+namespace cg = cooperative_groups;
+
 template <bool kSmem>
 __device__ __forceinline__ uint4 ld_rec(const uint4* p) {
     return kSmem ? *p : __ldg(p);
 }
 
-// Whole-run body of the canonical SMEM-resident sweep for packed word `word`
-// (one CTA): load tables, spins and replica permutation into shared memory,
-// run n_sweeps sweeps from global sweep t0 (measurement index meas0) with
-// measurement / replica exchange / correlations,
-// write the state back.
+// CTA barrier, or cluster barrier (release / acquire over the cluster's
+// shared memory) when a word is split over the CTAs of a cluster.
+template <bool kCluster>
+__device__ __forceinline__ void body_sync() {
+    if (kCluster)
+        cg::this_cluster().sync();
+    else
+        __syncthreads();
+}
+
+// Whole-run body of the canonical SMEM-resident sweep for packed word `word`:
+// load tables, spins and replica permutation into shared memory, run
+// n_sweeps sweeps from global sweep t0 (measurement index meas0) with
+// measurement / replica exchange / correlations, write the state back.
 // State is read with L1-bypassing loads: under the persistent scheduler the
 // previous chunk of this word may have been written by another SM.
 // kSmemRec: the per-cell records are first copied into shared memory after
 // the replica tables (canon_smem_records() decides on the host), else read
 // through the read-only cache.
-template <bool kSmemRec>
-__device__ __forceinline__ void sweep_canon_body(const SweepArgs& a, int word, uint32_t t0,
-                                                 int n_sweeps, int64_t meas0) {
+// kCluster: the CTA holds band `band` of the word's a.n_bands bands of cell
+// rows; the word's bands are the cluster ranks rank0 .. rank0 + n_bands - 1
+// (a cluster may hold several words of one context, or padding ranks of that
+// context with band >= n_bands).  Every rank holds the whole lattice;
+// it updates its own rows and, as it goes, writes the hidden words of its
+// last cell row into the next band (the upper neighbours of that band's first
+// row) and the spins of its first spin row into the previous band (the last
+// window row of that band's last cell row), wrapping around.  Half-steps end
+// with a cluster barrier; measurement counts are summed into the word's
+// band 0, which runs the measurement and the replica exchange.  Padding ranks
+// (band >= n_bands) only keep the barrier count, which is the same for every
+// rank because a cluster never mixes contexts.  Correlations need the whole
+// lattice, so a word with sq_every > 0 is never split (n_bands == 1).
+template <bool kSmemRec, bool kCluster>
+__device__ __forceinline__ void sweep_canon_body(const SweepArgs& a, int word, uint32_t t0, int n_sweeps,
+                                                 int64_t meas0, int band = 0, int rank0 = 0) {
     extern __shared__ __align__(16) uint32_t smem[];
     const Geometry& g = a.g;
+    const int W = g.W;
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nwarp = blockDim.x >> 5;
+    const int nb = kCluster ? a.n_bands : 1;
+    const bool active = band < nb;
+    const int row0 = active ? band * W / nb : 0, row1 = active ? (band + 1) * W / nb : 0;
+    const int c_begin = row0 * W, c_end = row1 * W;
     int64_t* s_acc = reinterpret_cast<int64_t*>(smem);  // [kNSum][32] running sums
     uint32_t* s_th = smem + kAccWords;          // [2][4][32]
     uint32_t* s_tv = s_th + kCanonTh;           // [4][32][32]
@@ -39,86 +70,117 @@ __device__ __forceinline__ void sweep_canon_body(const SweepArgs& a, int word, u
     uint32_t* s_segmask = reinterpret_cast<uint32_t*>(s_seg + 33); // [32]
     int* s_sob = reinterpret_cast<int*>(s_segmask + 32);          // [32] slot of each rung
     int* s_bos = s_sob + 32;                                        // [32] rung of each slot
-    const uint4* recs = a.crec;
-    if (kSmemRec) {  // [n_cells][kCellRec] records, 16-byte aligned
-        uint4* s_rec = reinterpret_cast<uint4*>(smem + canon_smem_rec_offset(g));
-        for (int x = threadIdx.x; x < g.n_cells * kCellRec; x += blockDim.x) s_rec[x] = __ldg(a.crec + x);
-        recs = s_rec;
+    char* sm = reinterpret_cast<char*>(smem);
+    // cluster neighbours (unused without a split)
+    char* sm_next = sm;
+    char* sm_prev = sm;
+    int* cnt0 = s_cnt;
+    const int* bos0 = s_bos;
+    if (kCluster && active) {
+        cg::cluster_group cl = cg::this_cluster();
+        if (nb > 1) {
+            sm_next = cl.map_shared_rank(sm, static_cast<unsigned int>(rank0 + (band + 1) % nb));
+            sm_prev = cl.map_shared_rank(sm, static_cast<unsigned int>(rank0 + (band + nb - 1) % nb));
+        }
+        cnt0 = cl.map_shared_rank(s_cnt, static_cast<unsigned int>(rank0));
+        bos0 = cl.map_shared_rank(s_bos, static_cast<unsigned int>(rank0));
     }
 
-    const uint4* gt = reinterpret_cast<const uint4*>(a.ctab + static_cast<size_t>(word) * kCanonTab);
-    for (int x = threadIdx.x; x < kCanonTab / 4; x += blockDim.x) reinterpret_cast<uint4*>(s_th)[x] = gt[x];
-    uint32_t* gv = a.v + static_cast<size_t>(word) * g.N;
-    for (int x = threadIdx.x; x < g.N; x += blockDim.x) s_v[x] = __ldcg(gv + x);
-    for (int x = threadIdx.x; x < 96; x += blockDim.x) s_cnt[x] = 0;
-    if (a.sq_every > 0) {
-        for (int x = threadIdx.x; x < 33; x += blockDim.x) s_seg[x] = a.seg[word * 33 + x];
-        for (int x = threadIdx.x; x < 32; x += blockDim.x) s_segmask[x] = a.segmask[word * 32 + x];
-    }
+    const uint4* recs = a.crec;
     const uint32_t chain = static_cast<uint32_t>(word) * 32u + lane;
     LaneConst lc = lane_const(lane, lane);
     const Round0Lane r0l = round0_lane(chain);
-    if (warp == 0) {  // replica permutation (identity without tempering)
-        const int sob = a.swap_every > 0 ? __ldcg(a.sob + word * 32 + lane) : lane;
-        s_sob[lane] = sob;
-        s_bos[sob] = lane;
+    const bool measuring = a.measure_every > 0;
+    if (active) {
+        if (kSmemRec) {  // [n_cells][kCellRec] records, 16-byte aligned
+            uint4* s_rec = reinterpret_cast<uint4*>(smem + canon_smem_rec_offset(g));
+            for (int x = threadIdx.x; x < g.n_cells * kCellRec; x += blockDim.x) s_rec[x] = __ldg(a.crec + x);
+            recs = s_rec;
+        }
+        const uint4* gt = reinterpret_cast<const uint4*>(a.ctab + static_cast<size_t>(word) * kCanonTab);
+        for (int x = threadIdx.x; x < kCanonTab / 4; x += blockDim.x) reinterpret_cast<uint4*>(s_th)[x] = gt[x];
+        const uint32_t* gv = a.v + static_cast<size_t>(word) * g.N;
+        for (int x = threadIdx.x; x < g.N; x += blockDim.x) s_v[x] = __ldcg(gv + x);
+        for (int x = threadIdx.x; x < 96; x += blockDim.x) s_cnt[x] = 0;
+        if (a.sq_every > 0) {
+            for (int x = threadIdx.x; x < 33; x += blockDim.x) s_seg[x] = a.seg[word * 33 + x];
+            for (int x = threadIdx.x; x < 32; x += blockDim.x) s_segmask[x] = a.segmask[word * 32 + x];
+        }
+        if (warp == 0) {  // replica permutation (identity without tempering)
+            const int sob = a.swap_every > 0 ? __ldcg(a.sob + word * 32 + lane) : lane;
+            s_sob[lane] = sob;
+            s_bos[sob] = lane;
+        }
     }
     __syncthreads();
     lc.lb = 4u * static_cast<uint32_t>(s_bos[lane]);  // lane reads the column of its rung
-
-    const bool measuring = a.measure_every > 0;
-    if (warp == 0 && measuring) {
+    if (active && band == 0 && warp == 0 && measuring) {
         for (int x = 0; x < kNSum; ++x)
             s_acc[x * 32 + lane] = __ldcg(a.sums + static_cast<size_t>(chain) * kNSum + x);
     }
+    if (kCluster) body_sync<true>();  // every rank started before any shared memory crosses CTAs
+
     // sweep and measurement counters: kernel arguments, or the batch's device clock
     int64_t meas = meas0;
-    // Cells of this warp: warp, warp + nwarp, ...; each described by its
+    // Cells of this warp: c_begin + warp, + nwarp, ...; each described by its
     // kCellRec records (shared-memory byte offsets and round-0 Philox words).
-    char* sm = reinterpret_cast<char*>(smem);
     const uint32_t lane4 = 4u * static_cast<uint32_t>(lane);
-    const uint4* rec0 = recs + static_cast<size_t>(warp) * kCellRec;
+    const uint4* rec0 = recs + static_cast<size_t>(c_begin + warp) * kCellRec;
     const int rstep = nwarp * kCellRec;
+    const int last_row = c_end - W, first_row_end = c_begin + W;
 
     for (int it = 0; it < n_sweeps; ++it) {
         const uint32_t t = t0 + static_cast<uint32_t>(it);
         const uint32_t X = r0l.hi ^ t ^ a.rk[0];
         const uint4* rec = rec0;
-        for (int cell = warp; cell < g.n_cells; cell += nwarp, rec += rstep) {
+        for (int cell = c_begin + warp; cell < c_end; cell += nwarp, rec += rstep) {
             const uint4 h0 = ld_rec<kSmemRec>(rec), h1 = ld_rec<kSmemRec>(rec + 1);
-            sts_off(sm, h1.y + lane4, hidden_cell_rec(sm, h0, h1, s_th, X, r0l.lo, a.rk, lc));
+            const uint32_t w = hidden_cell_rec(sm, h0, h1, s_th, X, r0l.lo, a.rk, lc);
+            sts_off(sm, h1.y + lane4, w);
+            if (kCluster && nb > 1 && cell >= last_row) sts_off(sm_next, h1.y + lane4, w);
         }
-        __syncthreads();
+        body_sync<kCluster>();
         rec = rec0;
-        for (int cell = warp; cell < g.n_cells; cell += nwarp, rec += rstep) {
+        for (int cell = c_begin + warp; cell < c_end; cell += nwarp, rec += rstep) {
             const uint4 v0 = ld_rec<kSmemRec>(rec + 2), v1 = ld_rec<kSmemRec>(rec + 3);
-            visible_cell_rec(sm, v0, v1, lane4, s_tv, X, r0l.lo, a.rk, lc);
+            const U4 o = visible_cell_rec(sm, v0, v1, lane4, s_tv, X, r0l.lo, a.rk, lc);
+            if (kCluster && nb > 1 && cell < first_row_end) {
+                sts_off(sm_prev, v0.x, o.x);
+                sts_off(sm_prev, v0.x + 4u, o.y);
+            }
         }
-        __syncthreads();
+        body_sync<kCluster>();
         const bool do_meas = measuring && (t + 1u) % static_cast<uint32_t>(a.measure_every) == 0u;
         const bool do_swap = a.swap_every > 0 && (t + 1u) % static_cast<uint32_t>(a.swap_every) == 0u;
         if (do_meas || do_swap) {
-            int anti0 = 0, anti1 = 0, pos = 0;
-            const uint4* rec = rec0;
-            for (int cell = warp; cell < g.n_cells; cell += nwarp, rec += rstep)
-                count_cell_rec(sm, ld_rec<kSmemRec>(rec), ld_rec<kSmemRec>(rec + 1), lane, anti0, anti1, pos);
-            atomicAdd(&s_cnt[lane], anti0);
-            atomicAdd(&s_cnt[32 + lane], anti1);
-            atomicAdd(&s_cnt[64 + lane], pos);
-            __syncthreads();
-            if (warp == 0) post_sweep_warp0(a, s_cnt, s_sob, s_bos, lane, word, t, do_meas, do_swap, meas, s_acc);
+            if (active) {
+                int anti0 = 0, anti1 = 0, pos = 0;
+                rec = rec0;
+                for (int cell = c_begin + warp; cell < c_end; cell += nwarp, rec += rstep)
+                    count_cell_rec(sm, ld_rec<kSmemRec>(rec), ld_rec<kSmemRec>(rec + 1), lane, anti0, anti1, pos);
+                atomicAdd(&cnt0[lane], anti0);
+                atomicAdd(&cnt0[32 + lane], anti1);
+                atomicAdd(&cnt0[64 + lane], pos);
+            }
+            body_sync<kCluster>();
+            if (band == 0 && warp == 0)
+                post_sweep_warp0(a, s_cnt, s_sob, s_bos, lane, word, t, do_meas, do_swap, meas, s_acc);
             if (do_meas) ++meas;
-            __syncthreads();
-            if (do_swap) lc.lb = 4u * static_cast<uint32_t>(s_bos[lane]);
+            body_sync<kCluster>();
+            if (do_swap && active) lc.lb = 4u * static_cast<uint32_t>(bos0[lane]);
         }
-        if (a.sq_every > 0 && (t + 1u) % static_cast<uint32_t>(a.sq_every) == 0u) {
+        if (!kCluster && a.sq_every > 0 && (t + 1u) % static_cast<uint32_t>(a.sq_every) == 0u) {
             accumulate_correlations(a, s_v, s_seg, s_segmask, warp, nwarp, lane);
             __syncthreads();
         }
     }
-    for (int x = threadIdx.x; x < g.N; x += blockDim.x) gv[x] = s_v[x];
-    if (warp == 0 && a.swap_every > 0) a.sob[word * 32 + lane] = s_sob[lane];
-    if (warp == 0 && measuring) {
+    if (kCluster) body_sync<true>();  // no rank reads another's shared memory after this
+    if (!active) return;
+    uint32_t* gv = a.v + static_cast<size_t>(word) * g.N;
+    const int s_begin = 2 * row0 * g.L, s_end = min(2 * row1, g.L) * g.L;  // own spin rows
+    for (int x = s_begin + static_cast<int>(threadIdx.x); x < s_end; x += blockDim.x) gv[x] = s_v[x];
+    if (band == 0 && warp == 0 && a.swap_every > 0) a.sob[word * 32 + lane] = s_sob[lane];
+    if (band == 0 && warp == 0 && measuring) {
         for (int x = 0; x < kNSum; ++x) a.sums[static_cast<size_t>(chain) * kNSum + x] = s_acc[x * 32 + lane];
     }
 }

@@ -170,16 +170,18 @@ __device__ __forceinline__ void visible_cell(uint32_t* out, int row, uint32_t wo
 }
 
 // Visible half-step of one cell described by its records v0, v1; lane4 =
-// 4 * lane (the lane's column of the hidden rows).
-__device__ __forceinline__ void visible_cell_rec(char* sm, const uint4& v0, const uint4& v1, uint32_t lane4,
-                                                 const uint32_t* s_tv, uint32_t X, uint32_t Y,
-                                                 const uint32_t (&rk)[20], const LaneConst& lc) {
+// 4 * lane (the lane's column of the hidden rows).  Stores the four new spin
+// words and returns them.
+__device__ __forceinline__ U4 visible_cell_rec(char* sm, const uint4& v0, const uint4& v1, uint32_t lane4,
+                                               const uint32_t* s_tv, uint32_t X, uint32_t Y,
+                                               const uint32_t (&rk)[20], const LaneConst& lc) {
     const U4 o = visible_core(lds_off(sm, v0.z + lane4), lds_off(sm, v0.w + lane4), lds_off(sm, v1.x + lane4),
                               s_tv, X, Y, v1.z, v1.y, rk, lc);
     sts_off(sm, v0.x, o.x);
     sts_off(sm, v0.x + 4u, o.y);
     sts_off(sm, v0.y, o.z);
     sts_off(sm, v0.y + 4u, o.w);
+    return o;
 }
 
 // Per-lane counts of one cell for the measurement from its eight window

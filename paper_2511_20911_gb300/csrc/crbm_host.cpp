@@ -230,6 +230,7 @@ SweepArgs fill_sweep_args(const crbm_ctx* ctx, int chunk) {
     a.swap_len = ctx->d.swap_len;
     a.wq = ctx->d.wq;
     a.swap_every = ctx->swap_every;
+    a.n_bands = 1;
     a.corr = ctx->d.corr;
     a.seg = ctx->d.seg;
     a.segmask = ctx->d.segmask;

@@ -14,7 +14,7 @@ __host__ __device__ inline size_t word_index(int vil, int w, int N, int s) {
 }
 
 #ifndef CRBM_SWEEP_MAX_THREADS
-#define CRBM_SWEEP_MAX_THREADS 512
+#define CRBM_SWEEP_MAX_THREADS 1024
 #endif
 constexpr int kMaxSweepWarps = CRBM_SWEEP_MAX_THREADS / 32;  // warps per CTA of the SMEM sweeps
 #ifndef CRBM_CHUNKS_PER_WORD
@@ -127,6 +127,7 @@ struct SweepArgs {
     const int32_t* swap_len;
     const int32_t* wq;
     int swap_every;       // 0 = no replica exchange
+    int n_bands;          // batched cluster launch: CTAs (bands of cell rows) per word, else 1
     const int64_t* clock; // batch launches: device {sweep, measurements} (else t0 / meas0)
     int64_t* corr;
     const int32_t* seg;
@@ -154,7 +155,7 @@ void host_point_tables(const Geometry& g, double beta, int32_t qJ, int32_t qJp, 
 // parameter space), and a work list of (descriptor, word) per CTA.
 constexpr int kMaxBatch = 16;
 struct BatchArgs {
-    const int2* items;
+    const int4* items;    // per CTA: (descriptor or -1, word, band, bands)
     int n_desc;
     SweepArgs d[kMaxBatch];
 };
@@ -173,7 +174,10 @@ cudaError_t launch_sweep_generic(const SweepArgs& a, int warps_per_cta, cudaStre
 cudaError_t launch_sweep_canon_persistent(const SweepArgs& a, int warps_per_cta, int chunk, int* sched,
                                           cudaStream_t st);
 cudaError_t launch_sweep_stream(const SweepArgs& a, cudaStream_t st, int64_t* launches);
-cudaError_t launch_sweep_batch(const BatchArgs& b, int n_items, int threads, size_t smem, cudaStream_t st);
+cudaError_t launch_sweep_batch(const BatchArgs& b, int n_tasks, int cluster, int threads, size_t smem,
+                               cudaStream_t st);
+// Clusters of `cluster` batch CTAs that can be resident at once (0: none).
+int batch_max_active_clusters(int cluster, int threads, size_t smem);
 cudaError_t launch_batch_advance(int64_t* clocks, const int* every, int n_ctx, int64_t n_sweeps, cudaStream_t st);
 cudaError_t launch_philox(const uint32_t* in, uint32_t* out, int n, cudaStream_t st);
 cudaError_t launch_unpack(const Geometry& g, const uint32_t* v, int8_t* out, int n_words,

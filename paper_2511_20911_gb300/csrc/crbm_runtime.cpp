@@ -94,10 +94,11 @@ int crbm_autotune(crbm_ctx* ctx, int64_t probe_sweeps, int32_t* best_warps) {
     if (e == cudaSuccess) e = cudaEventCreate(&e1);
     int best = ctx->warps;
     float best_ms = 1e30f;
-    const int cand[] = {2, 4, 6, 8, 10, 12, 14, 16};
+    const int cand[] = {2, 4, 6, 8, 10, 12, 14, 16, 20, 24, 28, 32};
     for (int w : cand) {
         if (e != cudaSuccess) break;
-        if (w > std::max(1, ctx->g.n_cells)) continue;
+        // the generic kernel is built for CTAs of at most 512 threads
+        if (w > std::max(1, ctx->g.n_cells) || w > (ctx->g.canonical ? kMaxSweepWarps : 16)) continue;
         // scratch copies: the tuning sweeps never touch the context's chains
         e = cudaMemcpyAsync(v2, ctx->d.v, ctx->n_words * N * 4, cudaMemcpyDeviceToDevice, ctx->stream);
         if (e == cudaSuccess) e = cudaMemsetAsync(s2, 0, npad * kNSum * 8, ctx->stream);
@@ -156,7 +157,7 @@ struct crbm_batch {
     std::vector<crbm_ctx*> ctx;
     cudaStream_t stream = nullptr;     // the contexts' common stream
     cudaStream_t capture = nullptr;    // private stream the graph is captured on
-    int2* items = nullptr;
+    int4* items = nullptr;             // per CTA: (member or -1, word, band, bands)
     int n_items = 0;
     int64_t* clock = nullptr;          // device [n][2]
     int* every = nullptr;              // device [n]
@@ -164,6 +165,8 @@ struct crbm_batch {
     std::vector<int64_t> staged;       // pinned-free staging for clock uploads
     int threads = 0;
     size_t smem = 0;
+    int cluster = 1;                   // CTAs per item (thread-block cluster)
+    std::vector<int> bands;            // per member: CTAs its words are split over
     cudaGraphExec_t exec = nullptr;
     int64_t graph_n = -1;
     std::string err;
@@ -193,7 +196,6 @@ int crbm_batch_create(crbm_batch** out, crbm_ctx* const* ctxs, int32_t n_ctx) {
     crbm_batch* b = new (std::nothrow) crbm_batch();
     if (!b) return CRBM_ENOMEM;
     int warps = 1;
-    std::vector<std::pair<int64_t, int2>> work;  // (cost, item)
     for (int c = 0; c < n_ctx; ++c) {
         crbm_ctx* x = ctxs[c];
         if (!x || x->layout != CRBM_LAYOUT_SMEM || !smem_ok(x) || x->stream != ctxs[0]->stream ||
@@ -205,26 +207,69 @@ int crbm_batch_create(crbm_batch** out, crbm_ctx* const* ctxs, int32_t n_ctx) {
         b->ctx.push_back(x);
         warps = std::max(warps, x->warps);
         b->smem = std::max(b->smem, x->g.canonical ? smem_bytes_canon(x->g) : smem_bytes_generic(x->g));
-        const int64_t cost = static_cast<int64_t>(x->g.n_cells) * (x->g.canonical ? 2 : 3);
-        for (int w = 0; w < x->n_words; ++w) work.push_back({cost, make_int2(c, w)});
     }
-    // heaviest lattices first, so they start in the first wave
-    std::stable_sort(work.begin(), work.end(),
-                     [](const std::pair<int64_t, int2>& p, const std::pair<int64_t, int2>& q) { return p.first > q.first; });
-    std::vector<int2> items;
-    for (auto& p : work) items.push_back(p.second);
+    b->threads = 32 * warps;
+    // Thread-block clusters of `cluster` CTAs (CRBM_BATCH_CLUSTER, default 8,
+    // a power of two; 1 = none).  A canonical member without correlations is
+    // split into B bands of cell rows per word, B the smallest power of two
+    // (at most the cluster size and W) that brings its cells per CTA down to
+    // the heaviest member's when split over a whole cluster (at least 16);
+    // its words then share clusters, cluster/B words per cluster, padded with
+    // ranks of the same member that only keep the barriers.  Other words are
+    // packed one per CTA.  Falls back to no clusters when none can be resident.
+    int cluster = 8;
+    if (const char* env = std::getenv("CRBM_BATCH_CLUSTER")) cluster = std::max(1, std::min(8, std::atoi(env)));
+    while (cluster & (cluster - 1)) --cluster;  // a power of two
+    if (cluster > 1 && batch_max_active_clusters(cluster, b->threads, b->smem) < 1) cluster = 1;
+    auto splittable = [&](const crbm_ctx* x) { return cluster > 1 && x->g.canonical && x->sq_every == 0; };
+    int target = 16;
+    for (auto* x : b->ctx)
+        if (splittable(x)) target = std::max(target, x->g.n_cells / std::min(cluster, x->g.W));
+    for (auto* x : b->ctx) {
+        int nb = 1;
+        if (splittable(x))
+            while (nb < cluster && 2 * nb <= x->g.W && x->g.n_cells / nb > target) nb *= 2;
+        b->bands.push_back(nb);
+    }
+    // tasks: split words cluster by cluster (heaviest member first), then
+    // whole words one per CTA (heaviest first), padded to whole clusters
+    std::vector<int> order(n_ctx);
+    for (int c = 0; c < n_ctx; ++c) order[c] = c;
+    std::stable_sort(order.begin(), order.end(), [&](int p, int q) {
+        return b->ctx[p]->g.n_cells / b->bands[p] > b->ctx[q]->g.n_cells / b->bands[q];
+    });
+    std::vector<int4> items;
+    std::vector<std::pair<int64_t, int4>> whole;
+    for (int c : order) {
+        const crbm_ctx* x = b->ctx[c];
+        const int nb = b->bands[c];
+        if (nb == 1) {
+            const int64_t cost = static_cast<int64_t>(x->g.n_cells) * (x->g.canonical ? 2 : 3);
+            for (int w = 0; w < x->n_words; ++w) whole.push_back({cost, make_int4(c, w, 0, 1)});
+            continue;
+        }
+        const int per = cluster / nb;  // words per cluster
+        for (int w0 = 0; w0 < x->n_words; w0 += per)
+            for (int k = 0; k < per; ++k)
+                for (int r = 0; r < nb; ++r)
+                    items.push_back(w0 + k < x->n_words ? make_int4(c, w0 + k, r, nb) : make_int4(c, 0, nb, nb));
+    }
+    std::stable_sort(whole.begin(), whole.end(),
+                     [](const std::pair<int64_t, int4>& p, const std::pair<int64_t, int4>& q) { return p.first > q.first; });
+    for (auto& p : whole) items.push_back(p.second);
+    while (items.size() % static_cast<size_t>(cluster)) items.push_back(make_int4(-1, 0, 0, 1));
+    b->cluster = cluster;
     std::vector<int> every;
     for (auto* x : b->ctx) every.push_back(x->measure_every);
     b->stream = ctxs[0]->stream;
-    b->threads = 32 * warps;
     b->n_items = static_cast<int>(items.size());
     b->mirror.assign(2 * n_ctx, -1);
     b->staged.assign(2 * n_ctx, 0);
-    cudaError_t e = cudaMalloc(reinterpret_cast<void**>(&b->items), items.size() * sizeof(int2));
+    cudaError_t e = cudaMalloc(reinterpret_cast<void**>(&b->items), items.size() * sizeof(int4));
     if (e == cudaSuccess) e = cudaMalloc(reinterpret_cast<void**>(&b->clock), 2 * n_ctx * sizeof(int64_t));
     if (e == cudaSuccess) e = cudaMalloc(reinterpret_cast<void**>(&b->every), n_ctx * sizeof(int));
     if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&b->capture, cudaStreamNonBlocking);
-    if (e == cudaSuccess) e = cudaMemcpy(b->items, items.data(), items.size() * sizeof(int2), cudaMemcpyHostToDevice);
+    if (e == cudaSuccess) e = cudaMemcpy(b->items, items.data(), items.size() * sizeof(int4), cudaMemcpyHostToDevice);
     if (e == cudaSuccess) e = cudaMemcpy(b->every, every.data(), every.size() * sizeof(int), cudaMemcpyHostToDevice);
     if (e != cudaSuccess) {
         g_batch_create_error = std::string("crbm_batch_create: ") + cudaGetErrorString(e);
@@ -273,11 +318,12 @@ int crbm_batch_sweep(crbm_batch* b, int64_t n_sweeps) {
         for (int c = 0; c < n; ++c) {
             args.d[c] = fill_sweep_args(b->ctx[c], static_cast<int>(n_sweeps));
             args.d[c].clock = b->clock + 2 * c;
+            args.d[c].n_bands = b->bands[c];
         }
         cudaGraph_t graph = nullptr;
         e = cudaStreamBeginCapture(b->capture, cudaStreamCaptureModeThreadLocal);
         if (e == cudaSuccess) {
-            cudaError_t e1 = launch_sweep_batch(args, b->n_items, b->threads, b->smem, b->capture);
+            cudaError_t e1 = launch_sweep_batch(args, b->n_items, b->cluster, b->threads, b->smem, b->capture);
             cudaError_t e2 = launch_batch_advance(b->clock, b->every, n, n_sweeps, b->capture);
             e = cudaStreamEndCapture(b->capture, &graph);
             if (e == cudaSuccess) e = e1 != cudaSuccess ? e1 : e2;
@@ -305,6 +351,8 @@ int crbm_batch_sweep(crbm_batch* b, int64_t n_sweeps) {
 }
 
 int crbm_batch_threads(const crbm_batch* b) { return b ? b->threads : CRBM_EINVAL; }
+
+int crbm_batch_cluster(const crbm_batch* b) { return b ? b->cluster : CRBM_EINVAL; }
 
 const char* crbm_batch_last_error(const crbm_batch* b) {
     return b ? b->err.c_str() : g_batch_create_error.c_str();

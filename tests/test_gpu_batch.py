@@ -71,6 +71,34 @@ def test_batch_matches_individual_sweeps():
     batch.close()
 
 
+@pytest.mark.parametrize("cluster", [2, 4, 8])
+def test_batch_cluster_split_matches_individual_sweeps(cluster, monkeypatch):
+    """Words split into bands over a thread-block cluster (boundary rows
+    exchanged through distributed shared memory, measurement and replica
+    exchange on rank 0) stay bit-identical to the whole-word sweep."""
+    monkeypatch.setenv("CRBM_BATCH_CLUSTER", str(cluster))
+    rng = np.random.default_rng(40 + cluster)
+    pt = workloads.tempering_batch_workload(sizes=(12, 24), ladders=1)
+    specs = [dict(m, measure_every=5, series_len=12) for m in pt]
+    specs += [dict(L=18, params=workloads.random_params(rng, 3), n_chains=70,
+                   chain_param=rng.integers(0, 3, 70).astype(np.int32), seed=7, measure_every=3, series_len=20),
+              dict(L=9, params=workloads.random_params(rng, 2), n_chains=32,
+                   chain_param=rng.integers(0, 2, 32).astype(np.int32), seed=8, measure_every=4),
+              dict(L=16, params=workloads.random_params(rng, 2), n_chains=40,
+                   chain_param=rng.integers(0, 2, 40).astype(np.int32), seed=9, measure_every=0, sq_every=5)]
+    batched = [make(s) for s in specs]
+    twins = [make(s) for s in specs]
+    batch = crbm.Batch(batched)
+    assert batch.cluster == cluster
+    for n in (7, 13, 25):
+        batch.sweep(n)
+        for t in twins:
+            t.sweep(n)
+    for a, b in zip(batched, twins):
+        same(a, b)
+    batch.close()
+
+
 def test_batch_validation():
     spec = members()[0]
     a, b = make(spec), make(spec)

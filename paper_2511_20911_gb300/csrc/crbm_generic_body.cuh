@@ -11,27 +11,35 @@ namespace generic {
 
 using namespace dev;
 
+// Endpoint word of filter k of a cell (built on the host): bits 0..14 the
+// site of the first endpoint, bit 15 set when it is a real site (clear for a
+// zero-padded one, whose site bits are 0), bits 16..31 the same for the
+// second endpoint.
+__device__ __forceinline__ int endpoint_term(const uint32_t* s_v, uint32_t half, int lane, uint32_t flip) {
+    const int b = static_cast<int>(bit_of(s_v[half & 0x7FFFu], lane) ^ flip);
+    return (half & 0x8000u) ? 2 * b - 1 : 0;
+}
+
 // Generic hidden half-step: any filter list (<= 16 filters), odd L, open
 // boundaries.  m = c1 v1 + c2 v2 with a zero-padded endpoint contributing 0;
 // the threshold row is cls * 5 + (m + 2).
 __device__ __forceinline__ void hidden_cell_generic(const Geometry& g, const uint32_t* s_v,
                                                     uint32_t* s_h, const uint32_t* s_tab,
-                                                    int cell, int i, int j, uint32_t t,
+                                                    const uint32_t* __restrict__ ep,
+                                                    int cell, uint32_t t,
                                                     uint32_t chain, int lane, int col, uint32_t k0,
                                                     uint32_t k1, const uint32_t (&sn)[2]) {
     U4 q[4];
 #pragma unroll
     for (int c = 0; c < 4; ++c)
         if (c < g.n_calls) q[c] = philox(cell, t, chain, static_cast<uint32_t>(c), k0, k1);
+    const uint32_t* e = ep + static_cast<size_t>(cell) * g.nb;
 #pragma unroll
     for (int k = 0; k < kMaxBonds; ++k) {
         if (k < g.nb) {
-            const int s1 = site_of(g, i, j, g.r1[k], g.c1[k]);
-            const int s2 = site_of(g, i, j, g.r2[k], g.c2[k]);
+            const uint32_t ek = __ldg(e + k);
             const int cls = g.cls[k];
-            int m = 2;
-            if (s1 >= 0) m += 2 * static_cast<int>(bit_of(s_v[s1], lane)) - 1;
-            if (s2 >= 0) m += 2 * static_cast<int>(bit_of(s_v[s2], lane) ^ sn[cls]) - 1;
+            const int m = 2 + endpoint_term(s_v, ek, lane, 0u) + endpoint_term(s_v, ek >> 16, lane, sn[cls]);
             const uint32_t thr = s_tab[(cls * 5 + m) * 32 + col];
             const uint32_t hw = __ballot_sync(0xffffffffu, pick(q[k >> 2], k & 3) < thr);
             if (lane == 0) s_h[cell * g.nb + k] = hw;
@@ -73,15 +81,16 @@ __device__ __forceinline__ void visible_cell_generic(const Geometry& g, uint32_t
 
 // Per-lane counts of one cell for the energy/magnetisation measurement:
 // anti[cls] = number of anti-aligned real bonds, pos = number of +1 spins.
-__device__ __forceinline__ void count_cell(const Geometry& g, const uint32_t* s_v, int i, int j,
+__device__ __forceinline__ void count_cell(const Geometry& g, const uint32_t* s_v,
+                                           const uint32_t* __restrict__ ep, int cell, int i, int j,
                                            int lane, int& anti0, int& anti1, int& pos) {
+    const uint32_t* e = ep + static_cast<size_t>(cell) * g.nb;
 #pragma unroll
     for (int k = 0; k < kMaxBonds; ++k) {
         if (k < g.nb) {
-            const int s1 = site_of(g, i, j, g.r1[k], g.c1[k]);
-            const int s2 = site_of(g, i, j, g.r2[k], g.c2[k]);
-            if (s1 >= 0 && s2 >= 0) {
-                const int x = static_cast<int>(bit_of(s_v[s1] ^ s_v[s2], lane));
+            const uint32_t ek = __ldg(e + k);
+            if ((ek & 0x80008000u) == 0x80008000u) {
+                const int x = static_cast<int>(bit_of(s_v[ek & 0x7FFFu] ^ s_v[(ek >> 16) & 0x7FFFu], lane));
                 if (g.cls[k]) anti1 += x; else anti0 += x;
             }
         }
@@ -142,19 +151,10 @@ __device__ __forceinline__ void sweep_generic_body(const SweepArgs& a, int word)
 
     for (int it = 0; it < a.n_sweeps; ++it) {
         const uint32_t t = t0 + static_cast<uint32_t>(it);
-        int i = i_first, j = j_first;
-        for (int cell = warp; cell < g.n_cells; cell += nwarp) {
-            hidden_cell_generic(g, s_v, s_h, s_tab, cell, i, j, t, chain, lane, col, a.key0, a.key1, sn);
-            i += di;
-            j += dj;
-            if (j >= g.W) {
-                j -= g.W;
-                ++i;
-            }
-        }
+        for (int cell = warp; cell < g.n_cells; cell += nwarp)
+            hidden_cell_generic(g, s_v, s_h, s_tab, a.gep, cell, t, chain, lane, col, a.key0, a.key1, sn);
         __syncthreads();
-        i = i_first;
-        j = j_first;
+        int i = i_first, j = j_first;
         for (int cell = warp; cell < g.n_cells; cell += nwarp) {
             visible_cell_generic(g, s_v, s_h, s_tab, a.inc, a.inc_off, cell, i, j, t, chain, lane, col,
                                  a.key0, a.key1, sn);
@@ -173,7 +173,7 @@ __device__ __forceinline__ void sweep_generic_body(const SweepArgs& a, int word)
             i = i_first;
             j = j_first;
             for (int cell = warp; cell < g.n_cells; cell += nwarp) {
-                count_cell(g, s_v, i, j, lane, anti0, anti1, pos);
+                count_cell(g, s_v, a.gep, cell, i, j, lane, anti0, anti1, pos);
                 i += di;
                 j += dj;
                 if (j >= g.W) {

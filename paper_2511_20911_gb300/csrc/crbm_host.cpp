@@ -150,6 +150,17 @@ int build_geometry(crbm_ctx* ctx, const crbm_params* p, std::vector<uint32_t>& i
         inc.insert(inc.end(), per_site[s].begin(), per_site[s].end());
     }
     inc_off[g.N] = static_cast<int32_t>(inc.size());
+    // endpoint words of the generic hidden half-step, after the CSR entries:
+    // per endpoint 15 bits of site and a real-site flag (a padded one is 0);
+    // generic contexts are SMEM-resident (L <= CRBM_SMEM_MAX_L), so sites fit
+    auto endpoint = [&](int s) { return s >= 0 ? (static_cast<uint32_t>(s) | 0x8000u) : 0u; };
+    if (!g.canonical && g.N <= 0x7FFF) {
+        for (int i = 0; i < g.W; ++i)
+            for (int j = 0; j < g.W; ++j)
+                for (int k = 0; k < nb; ++k)
+                    inc.push_back(endpoint(site_index(g, i, j, g.r1[k], g.c1[k])) |
+                                  (endpoint(site_index(g, i, j, g.r2[k], g.c2[k])) << 16));
+    }
     return CRBM_OK;
 }
 
@@ -220,6 +231,7 @@ SweepArgs fill_sweep_args(const crbm_ctx* ctx, int chunk) {
     a.sneg = ctx->d.sneg;
     a.inc = ctx->d.inc;
     a.inc_off = ctx->d.inc_off;
+    a.gep = ctx->d.inc + ctx->n_inc;
     a.sums = ctx->d.sums;
     a.series = ctx->d.series;
     a.h = ctx->d.h;
@@ -270,6 +282,7 @@ int crbm_create(crbm_ctx** out, const crbm_params* p) {
     std::vector<uint32_t> inc;
     std::vector<int32_t> inc_off;
     int rc = build_geometry(ctx, p, inc, inc_off);
+    if (rc == CRBM_OK) ctx->n_inc = static_cast<size_t>(inc_off.back());
     if (rc) {
         delete ctx;
         return rc;

@@ -116,10 +116,34 @@ class ClockSampler:
                 "sm_max_mhz": max(mx) if mx else None, "reasons": reasons, "samples": len(sm)}
 
 
+def replica_seed(seed, rank):
+    """Seed of rank `rank`'s replica: every rank samples its own chains."""
+    return seed + 1000003 * rank
+
+
+def max_over_ranks(t_local, ws):
+    """Largest of the ranks' timed seconds (the job's time); the tensor lives
+    on the device for NCCL and on the host for gloo."""
+    if ws == 1:
+        return t_local
+    import torch
+    import torch.distributed as dist
+    dev = "cuda" if dist.get_backend() == "nccl" else "cpu"
+    t = torch.tensor([t_local], dtype=torch.float64, device=dev)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def replica_value(units_per_rank, ws, t_max):
+    """Whole-job throughput: the units all ranks processed over the slowest
+    rank's time (replicas do equal work)."""
+    return units_per_rank * ws / t_max
+
+
 def workload_config(name, rank):
     from paper_2511_20911_gb300 import workloads
     w = workloads.grid_workload() if name == "grid" else workloads.stream_workload()
-    w["seed"] = w["seed"] + 1000003 * rank
+    w["seed"] = replica_seed(w["seed"], rank)
     return w
 
 
@@ -204,7 +228,7 @@ def run_batch(args, rank, ws):
     S, K, W = args.sweeps_per_step, args.steps, args.warmup
     members = []
     for sp in specs:
-        sp = dict(sp, seed=sp["seed"] + 1000003 * rank, measure_every=args.measure_every)
+        sp = dict(sp, seed=replica_seed(sp["seed"], rank), measure_every=args.measure_every)
         m = crbm.Sampler(**sp)
         m.autotune(50)
         members.append(m)
@@ -225,13 +249,9 @@ def run_batch(args, rank, ws):
             batch.sweep(S)
             ev[k][1].record(stream)
         torch.cuda.synchronize()
-    t_total = sum(a.elapsed_time(b) for a, b in ev) / 1e3
-    if ws > 1:
-        t = torch.tensor([t_total], device="cuda")
-        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
-        t_total = float(t.item())
+    t_total = max_over_ranks(sum(a.elapsed_time(b) for a, b in ev) / 1e3, ws)
     per_sweep = sum(sp["n_chains"] * sp["L"] ** 2 for sp in specs)
-    value = per_sweep * S * K * ws / t_total
+    value = replica_value(per_sweep * S * K, ws, t_total)
     calls = sum(4 * ((sp["L"] + 1) // 2) ** 2 * sp["n_chains"] for sp in specs) * S
     achieved = MUL_OPS_PER_CALL * calls / (t_total / K) / 1e12
     peak = SM_COUNT * IMUL_LANES_PER_SM_CLK * SM_MAX_MHZ * 1e6 / 1e12
@@ -388,13 +408,9 @@ def main():
         torch.distributed.barrier()
     launches = s.launch_count - launches0
     step_ms = [a.elapsed_time(b) for a, b in ev]
-    t_total = sum(step_ms) / 1e3
-    if ws > 1:
-        t = torch.tensor([t_total], device="cuda")
-        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
-        t_total = float(t.item())
+    t_total = max_over_ranks(sum(step_ms) / 1e3, ws)
     spin_updates = w["n_chains"] * w["L"] ** 2 * S * K
-    value = spin_updates * ws / t_total
+    value = replica_value(spin_updates, ws, t_total)
 
     # effective samples of E and m over the timed steps
     ser = s.series()                                   # [T][chain][3]

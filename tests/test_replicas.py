@@ -1,0 +1,58 @@
+"""Host logic of the multi-GPU replica path (bench.py --gpus N) on CPU ranks:
+world size 2 over gloo.  Each rank gets its own seed, the job time is the
+largest rank time, and the whole-job value counts every rank's units.  No
+data-path collective exists: the chains of different ranks never meet."""
+import os
+import socket
+import sys
+
+import pytest
+import torch.multiprocessing as mp
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+def _free_port():
+    with socket.socket() as s:
+        s.bind(("127.0.0.1", 0))
+        return s.getsockname()[1]
+
+
+def _rank(rank, ws, port, out):
+    os.environ.update(MASTER_ADDR="127.0.0.1", MASTER_PORT=str(port), RANK=str(rank), WORLD_SIZE=str(ws))
+    sys.path.insert(0, ROOT)
+    import torch.distributed as dist
+    import bench
+    dist.init_process_group("gloo", rank=rank, world_size=ws)
+    try:
+        t_local = 1.0 + 0.5 * rank            # rank 1 is the slower one
+        t_max = bench.max_over_ranks(t_local, ws)
+        grid = bench.workload_config("grid", rank)
+        stream = bench.workload_config("stream", rank)
+        out[rank] = (t_max, grid["seed"], stream["seed"], bench.replica_value(1000, ws, t_max))
+    finally:
+        dist.destroy_process_group()
+
+
+def test_two_gloo_ranks_replica_logic():
+    ws, port = 2, _free_port()
+    with mp.Manager() as m:
+        out = m.dict()
+        ctx = mp.get_context("spawn")
+        procs = [ctx.Process(target=_rank, args=(r, ws, port, out)) for r in range(ws)]
+        for p in procs:
+            p.start()
+        for p in procs:
+            p.join(timeout=120)
+            assert p.exitcode == 0
+        res = dict(out)
+    assert res[0][0] == res[1][0] == pytest.approx(1.5)      # max over ranks
+    assert res[0][1] != res[1][1] and res[0][2] != res[1][2]  # independent replicas
+    assert res[0][3] == pytest.approx(2000 / 1.5)             # all ranks' units / slowest time
+
+
+def test_single_rank_is_identity():
+    sys.path.insert(0, ROOT)
+    import bench
+    assert bench.max_over_ranks(2.5, 1) == 2.5
+    assert bench.replica_seed(7, 0) == 7

@@ -131,11 +131,11 @@ __device__ __forceinline__ void sweep_canon_body(const SweepArgs& a, int word, u
 
     for (int it = 0; it < n_sweeps; ++it) {
         const uint32_t t = t0 + static_cast<uint32_t>(it);
-        const uint32_t X = r0l.hi ^ t ^ a.rk[0];
+        const Round1Sweep rs = round1_sweep(r0l.hi ^ t ^ a.rk[0], a.rk);
         const uint4* rec = rec0;
         for (int cell = c_begin + warp; cell < c_end; cell += nwarp, rec += rstep) {
             const uint4 h0 = ld_rec<kSmemRec>(rec), h1 = ld_rec<kSmemRec>(rec + 1);
-            const uint32_t w = hidden_cell_rec(sm, h0, h1, s_th, X, r0l.lo, a.rk, lc);
+            const uint32_t w = hidden_cell_rec(sm, h0, h1, s_th, rs, r0l.lo, a.rk, lc);
             sts_off(sm, h1.y + lane4, w);
             if (kCluster && nb > 1 && cell >= last_row) sts_off(sm_next, h1.y + lane4, w);
         }
@@ -143,7 +143,7 @@ __device__ __forceinline__ void sweep_canon_body(const SweepArgs& a, int word, u
         rec = rec0;
         for (int cell = c_begin + warp; cell < c_end; cell += nwarp, rec += rstep) {
             const uint4 v0 = ld_rec<kSmemRec>(rec + 2), v1 = ld_rec<kSmemRec>(rec + 3);
-            const U4 o = visible_cell_rec(sm, v0, v1, lane4, s_tv, X, r0l.lo, a.rk, lc);
+            const U4 o = visible_cell_rec(sm, v0, v1, lane4, s_tv, rs, r0l.lo, a.rk, lc);
             if (kCluster && nb > 1 && cell < first_row_end) {
                 sts_off(sm_prev, v0.x, o.x);
                 sts_off(sm_prev, v0.x + 4u, o.y);

@@ -85,8 +85,9 @@ __device__ __forceinline__ void sts_off(char* sm, uint32_t off, uint32_t x) {
 // Philox words (rca, rcb); returns the lane's word W.
 __device__ __forceinline__ uint32_t hidden_core(uint32_t v00, uint32_t v01, uint32_t v02, uint32_t v10,
                                                 uint32_t v11, uint32_t v12, uint32_t v20, uint32_t v21,
-                                                const uint32_t* s_th, uint32_t X, uint32_t Y, uint32_t rca,
-                                                uint32_t rcb, const uint32_t (&rk)[20], const LaneConst& lc) {
+                                                const uint32_t* s_th, const Round1Sweep& r1, uint32_t Y,
+                                                uint32_t rca, uint32_t rcb, const uint32_t (&rk)[20],
+                                                const LaneConst& lc) {
     const uint32_t m00 = v00 & lc.lm, m01 = v01 & lc.lm, m02 = v02 & lc.lm, m10 = v10 & lc.lm;
     const uint32_t m11 = v11 & lc.lm, m12 = v12 & lc.lm, m20 = v20 & lc.lm, m21 = v21 & lc.lm;
     // first endpoints at bit 7
@@ -98,9 +99,10 @@ __device__ __forceinline__ uint32_t hidden_core(uint32_t v00, uint32_t v01, uint
     const uint32_t b10 = rotr(m10, lc.rot[1]), b11 = rotr(m11, lc.rot[1]);
     const uint32_t b12 = rotr(m12, lc.rot[1]), b20 = rotr(m20, lc.rot[1]);
     const uint32_t b21 = rotr(m21, lc.rot[1]);
-    const U4 q0 = philox_rounds1to9(X, Y, rca, rcb, rk);
-    const U4 q1 = philox_rounds1to9(X, Y, rca ^ 1u, rcb, rk);
-    const U4 q2 = philox_rounds1to9(X, Y, rca ^ 2u, rcb, rk);
+    const uint32_t n2 = r1.hik ^ rcb;  // shared by the cell's calls
+    const U4 q0 = philox_from_round1(Y, r1, n2, rca, rk);
+    const U4 q1 = philox_from_round1(Y, r1, n2, rca ^ 1u, rk);
+    const U4 q2 = philox_from_round1(Y, r1, n2, rca ^ 2u, rk);
     const uint32_t* thJ = s_th;
     const uint32_t* thP = s_th + 128;
     uint32_t w = 0u;
@@ -121,21 +123,21 @@ __device__ __forceinline__ uint32_t hidden_core(uint32_t v00, uint32_t v01, uint
 // Hidden half-step of one cell.  Window rows at s_v + r0, r1, r2 and columns
 // c0, c1, c2; returns the lane's word W.
 __device__ __forceinline__ uint32_t hidden_cell(const uint32_t* s_v, int r0, int r1, int r2, int c0,
-                                                int c1, int c2, const uint32_t* s_th, uint32_t X,
+                                                int c1, int c2, const uint32_t* s_th, const Round1Sweep& rs,
                                                 uint32_t Y, const Round0Cell rc,
                                                 const uint32_t (&rk)[20], const LaneConst& lc) {
     return hidden_core(s_v[r0 + c0], s_v[r0 + c1], s_v[r0 + c2], s_v[r1 + c0], s_v[r1 + c1], s_v[r1 + c2],
-                       s_v[r2 + c0], s_v[r2 + c1], s_th, X, Y, rc.a, rc.b, rk, lc);
+                       s_v[r2 + c0], s_v[r2 + c1], s_th, rs, Y, rc.a, rc.b, rk, lc);
 }
 
 // Hidden half-step of one cell described by its records h0, h1 (layout in
 // crbm_internal.h); returns the lane's word W.
 __device__ __forceinline__ uint32_t hidden_cell_rec(const char* sm, const uint4& h0, const uint4& h1,
-                                                    const uint32_t* s_th, uint32_t X, uint32_t Y,
+                                                    const uint32_t* s_th, const Round1Sweep& rs, uint32_t Y,
                                                     const uint32_t (&rk)[20], const LaneConst& lc) {
     return hidden_core(lds_off(sm, h0.x), lds_off(sm, h0.x + 4u), lds_off(sm, h0.w), lds_off(sm, h0.y),
                        lds_off(sm, h0.y + 4u), lds_off(sm, h1.x), lds_off(sm, h0.z), lds_off(sm, h0.z + 4u),
-                       s_th, X, Y, h1.w, h1.z, rk, lc);
+                       s_th, rs, Y, h1.w, h1.z, rk, lc);
 }
 
 // Visible half-step of one cell from the lanes' words of this cell (wo), the
@@ -143,10 +145,10 @@ __device__ __forceinline__ uint32_t hidden_cell_rec(const char* sm, const uint4&
 // (rca ^ visible tag, rcb); returns the four new spin words (0,0) (0,1)
 // (1,0) (1,1) of the cell.
 __device__ __forceinline__ U4 visible_core(uint32_t wo, uint32_t wu, uint32_t wl, const uint32_t* s_tv,
-                                           uint32_t X, uint32_t Y, uint32_t rcav, uint32_t rcb,
+                                           const Round1Sweep& r1, uint32_t Y, uint32_t rcav, uint32_t rcb,
                                            const uint32_t (&rk)[20], const LaneConst& lc) {
     const uint32_t c = (wo & kOwnBits) | (wu & kDownBits) | (wl & kRightBits);
-    const U4 q = philox_rounds1to9(X, Y, rcav, rcb, rk);
+    const U4 q = philox_from_round1(Y, r1, r1.hik ^ rcb, rcav, rk);
     const uint32_t f = 31u << 7;
     const uint32_t t00 = lds_at(s_tv, (c & f) | lc.lb);
     const uint32_t t01 = lds_at(s_tv + 1024, ((c >> 5) & f) | lc.lb);
@@ -159,10 +161,10 @@ __device__ __forceinline__ U4 visible_core(uint32_t wo, uint32_t wu, uint32_t wl
 // Visible half-step of one cell; the four new spin words go to out[0],
 // out[1], out[row], out[row + 1].
 __device__ __forceinline__ void visible_cell(uint32_t* out, int row, uint32_t wo, uint32_t wu,
-                                             uint32_t wl, const uint32_t* s_tv, uint32_t X,
+                                             uint32_t wl, const uint32_t* s_tv, const Round1Sweep& rs,
                                              uint32_t Y, const Round0Cell rc, const uint32_t (&rk)[20],
                                              const LaneConst& lc) {
-    const U4 o = visible_core(wo, wu, wl, s_tv, X, Y, rc.a ^ kTagVis, rc.b, rk, lc);
+    const U4 o = visible_core(wo, wu, wl, s_tv, rs, Y, rc.a ^ kTagVis, rc.b, rk, lc);
     out[0] = o.x;
     out[1] = o.y;
     out[row] = o.z;
@@ -173,10 +175,10 @@ __device__ __forceinline__ void visible_cell(uint32_t* out, int row, uint32_t wo
 // 4 * lane (the lane's column of the hidden rows).  Stores the four new spin
 // words and returns them.
 __device__ __forceinline__ U4 visible_cell_rec(char* sm, const uint4& v0, const uint4& v1, uint32_t lane4,
-                                               const uint32_t* s_tv, uint32_t X, uint32_t Y,
+                                               const uint32_t* s_tv, const Round1Sweep& rs, uint32_t Y,
                                                const uint32_t (&rk)[20], const LaneConst& lc) {
     const U4 o = visible_core(lds_off(sm, v0.z + lane4), lds_off(sm, v0.w + lane4), lds_off(sm, v1.x + lane4),
-                              s_tv, X, Y, v1.z, v1.y, rk, lc);
+                              s_tv, rs, Y, v1.z, v1.y, rk, lc);
     sts_off(sm, v0.x, o.x);
     sts_off(sm, v0.x + 4u, o.y);
     sts_off(sm, v0.y, o.z);

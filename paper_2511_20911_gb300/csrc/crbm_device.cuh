@@ -57,6 +57,45 @@ __device__ __forceinline__ U4 philox_rounds1to9(uint32_t c0, uint32_t c1, uint32
     return {c0, c1, c2, c3};
 }
 
+// Rounds 2..9 from the state after round 1 (c0, c1, c2, c3).
+__device__ __forceinline__ U4 philox_rounds2to9(uint32_t c0, uint32_t c1, uint32_t c2, uint32_t c3,
+                                                const uint32_t (&rk)[20]) {
+#pragma unroll
+    for (int r = 2; r < 10; ++r) {
+        const uint64_t p0 = static_cast<uint64_t>(kPhiloxM0) * c0;
+        const uint64_t p1 = static_cast<uint64_t>(kPhiloxM1) * c2;
+        const uint32_t n0 = static_cast<uint32_t>(p1 >> 32) ^ c1 ^ rk[2 * r];
+        const uint32_t n2 = static_cast<uint32_t>(p0 >> 32) ^ c3 ^ rk[2 * r + 1];
+        c1 = static_cast<uint32_t>(p1);
+        c3 = static_cast<uint32_t>(p0);
+        c0 = n0;
+        c2 = n2;
+    }
+    return {c0, c1, c2, c3};
+}
+
+// Round 1 of the sweep-keyed counters, split by what varies.  After round 0
+// the state is (X, Y, c2, c3) with X, Y fixed for a lane in a sweep and
+// (c2, c3) = (hi(M0 cell) ^ key1 ^ tag, lo(M0 cell)).  Round 1 multiplies X
+// (once per sweep: Round1Sweep) and c2 (per call); its second output word
+// hi(M0 X) ^ c3 ^ rk3 is shared by all calls of a cell.
+struct Round1Sweep {
+    uint32_t lo;   // lo(M0 X): word 3 after round 1
+    uint32_t hik;  // hi(M0 X) ^ rk[3]
+};
+__device__ __forceinline__ Round1Sweep round1_sweep(uint32_t X, const uint32_t (&rk)[20]) {
+    const uint64_t p = static_cast<uint64_t>(kPhiloxM0) * X;
+    return {static_cast<uint32_t>(p), static_cast<uint32_t>(p >> 32) ^ rk[3]};
+}
+// The full Philox-4x32-10 output for round-0 state (X, Y, c2, c3), given
+// r1 = round1_sweep(X) and n2 = r1.hik ^ c3 of the cell.
+__device__ __forceinline__ U4 philox_from_round1(uint32_t Y, const Round1Sweep& r1, uint32_t n2, uint32_t c2,
+                                                 const uint32_t (&rk)[20]) {
+    const uint64_t p1 = static_cast<uint64_t>(kPhiloxM1) * c2;
+    return philox_rounds2to9(static_cast<uint32_t>(p1 >> 32) ^ Y ^ rk[2], static_cast<uint32_t>(p1), n2, r1.lo,
+                             rk);
+}
+
 // Round 0 of counter (cell, sweep, chain, tag) needs no per-call multiply:
 // M1 * chain is a per-lane constant, M0 * cell is warp-uniform.  The state
 // after round 0 is (hi(M1 chain) ^ sweep ^ rk0, lo(M1 chain),

@@ -135,7 +135,7 @@ __global__ void __launch_bounds__(kStreamThreads, CRBM_STREAM_MIN_BLOCKS) k_stre
     const uint32_t chain = static_cast<uint32_t>(w) * 32u + lane;
     const LaneConst lc = lane_const(lane, lane);
     const Round0Lane r0l = round0_lane(chain);
-    const uint32_t X = r0l.hi ^ t ^ a.rk[0];
+    const Round1Sweep rs = round1_sweep(r0l.hi ^ t ^ a.rk[0], a.rk);
     __syncthreads();
     // warp = columns lj of the tile, cells walked down the column
     const int ni = min(kTI, W - i0), nj = min(kTJ, W - j0);
@@ -144,7 +144,7 @@ __global__ void __launch_bounds__(kStreamThreads, CRBM_STREAM_MIN_BLOCKS) k_stre
         uint32_t* hp = s_h + lj * 32 + lane;
         uint32_t cell = static_cast<uint32_t>(i0 * W + j0 + lj);
         for (int li = 0; li < ni; ++li, v += 2 * VS, hp += kTJ * 32, cell += static_cast<uint32_t>(W))
-            *hp = hidden_cell(v, 0, VS, 2 * VS, 0, 1, 2, s_th, X, r0l.lo, round0_cell(cell, a.rk[1]), a.rk, lc);
+            *hp = hidden_cell(v, 0, VS, 2 * VS, 0, 1, 2, s_th, rs, r0l.lo, round0_cell(cell, a.rk[1]), a.rk, lc);
     }
     __syncthreads();
     // tile rows of hidden words are contiguous runs of nj * 32 words in h
@@ -178,7 +178,7 @@ __global__ void __launch_bounds__(kStreamVisThreads, CRBM_STREAM_VIS_MIN_BLOCKS)
     const uint32_t chain = static_cast<uint32_t>(w) * 32u + lane;
     const LaneConst lc = lane_const(lane, lane);
     const Round0Lane r0l = round0_lane(chain);
-    const uint32_t X = r0l.hi ^ t ^ a.rk[0];
+    const Round1Sweep rs = round1_sweep(r0l.hi ^ t ^ a.rk[0], a.rk);
     __syncthreads();
     constexpr int VO = 2 * kTJ;
     const int ni = min(kTI, W - i0), nj = min(kTJ, W - j0);
@@ -187,7 +187,7 @@ __global__ void __launch_bounds__(kStreamVisThreads, CRBM_STREAM_VIS_MIN_BLOCKS)
         uint32_t* o = s_o + 2 * lj;
         uint32_t cell = static_cast<uint32_t>(i0 * W + j0 + lj);
         for (int li = 0; li < ni; ++li, ho += HS * 32, o += 2 * VO, cell += static_cast<uint32_t>(W))
-            visible_cell(o, VO, ho[0], ho[-HS * 32], ho[-32], s_tv, X, r0l.lo, round0_cell(cell, a.rk[1]), a.rk,
+            visible_cell(o, VO, ho[0], ho[-HS * 32], ho[-32], s_tv, rs, r0l.lo, round0_cell(cell, a.rk[1]), a.rk,
                          lc);
     }
     __syncthreads();

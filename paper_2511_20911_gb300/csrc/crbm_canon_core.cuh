@@ -99,10 +99,10 @@ __device__ __forceinline__ uint32_t hidden_core(uint32_t v00, uint32_t v01, uint
     const uint32_t b10 = rotr(m10, lc.rot[1]), b11 = rotr(m11, lc.rot[1]);
     const uint32_t b12 = rotr(m12, lc.rot[1]), b20 = rotr(m20, lc.rot[1]);
     const uint32_t b21 = rotr(m21, lc.rot[1]);
-    const uint32_t n2 = r1.hik ^ rcb;  // shared by the cell's calls
-    const U4 q0 = philox_from_round1(Y, r1, n2, rca, rk);
-    const U4 q1 = philox_from_round1(Y, r1, n2, rca ^ 1u, rk);
-    const U4 q2 = philox_from_round1(Y, r1, n2, rca ^ 2u, rk);
+    const Round2Cell r2 = round2_cell(r1.hik ^ rcb);  // shared by the cell's calls
+    const U4 q0 = philox_from_round2(Y, r1, r2, rca, rk);
+    const U4 q1 = philox_from_round2(Y, r1, r2, rca ^ 1u, rk);
+    const U4 q2 = philox_from_round2(Y, r1, r2, rca ^ 2u, rk);
     const uint32_t* thJ = s_th;
     const uint32_t* thP = s_th + 128;
     uint32_t w = 0u;

@@ -74,6 +74,23 @@ __device__ __forceinline__ U4 philox_rounds2to9(uint32_t c0, uint32_t c1, uint32
     return {c0, c1, c2, c3};
 }
 
+// Rounds 3..9 from the state after round 2.
+__device__ __forceinline__ U4 philox_rounds3to9(uint32_t c0, uint32_t c1, uint32_t c2, uint32_t c3,
+                                                const uint32_t (&rk)[20]) {
+#pragma unroll
+    for (int r = 3; r < 10; ++r) {
+        const uint64_t p0 = static_cast<uint64_t>(kPhiloxM0) * c0;
+        const uint64_t p1 = static_cast<uint64_t>(kPhiloxM1) * c2;
+        const uint32_t n0 = static_cast<uint32_t>(p1 >> 32) ^ c1 ^ rk[2 * r];
+        const uint32_t n2 = static_cast<uint32_t>(p0 >> 32) ^ c3 ^ rk[2 * r + 1];
+        c1 = static_cast<uint32_t>(p1);
+        c3 = static_cast<uint32_t>(p0);
+        c0 = n0;
+        c2 = n2;
+    }
+    return {c0, c1, c2, c3};
+}
+
 // Round 1 of the sweep-keyed counters, split by what varies.  After round 0
 // the state is (X, Y, c2, c3) with X, Y fixed for a lane in a sweep and
 // (c2, c3) = (hi(M0 cell) ^ key1 ^ tag, lo(M0 cell)).  Round 1 multiplies X
@@ -94,6 +111,26 @@ __device__ __forceinline__ U4 philox_from_round1(uint32_t Y, const Round1Sweep& 
     const uint64_t p1 = static_cast<uint64_t>(kPhiloxM1) * c2;
     return philox_rounds2to9(static_cast<uint32_t>(p1 >> 32) ^ Y ^ rk[2], static_cast<uint32_t>(p1), n2, r1.lo,
                              rk);
+}
+
+// Round 2 multiplies word 2 after round 1, which is the cell's n2 for every
+// call of the cell: its product is formed once per cell.
+struct Round2Cell {
+    uint32_t hi, lo;  // M1 n2
+};
+__device__ __forceinline__ Round2Cell round2_cell(uint32_t n2) {
+    const uint64_t p = static_cast<uint64_t>(kPhiloxM1) * n2;
+    return {static_cast<uint32_t>(p >> 32), static_cast<uint32_t>(p)};
+}
+// The full Philox-4x32-10 output for round-0 state (X, Y, c2, c3) of a call,
+// given r1 = round1_sweep(X) and r2 = round2_cell(r1.hik ^ c3).
+__device__ __forceinline__ U4 philox_from_round2(uint32_t Y, const Round1Sweep& r1, const Round2Cell& r2,
+                                                 uint32_t c2, const uint32_t (&rk)[20]) {
+    const uint64_t p1 = static_cast<uint64_t>(kPhiloxM1) * c2;             // round 1
+    const uint32_t n0 = static_cast<uint32_t>(p1 >> 32) ^ Y ^ rk[2];
+    const uint64_t p0 = static_cast<uint64_t>(kPhiloxM0) * n0;             // round 2
+    return philox_rounds3to9(r2.hi ^ static_cast<uint32_t>(p1) ^ rk[4], r2.lo,
+                             static_cast<uint32_t>(p0 >> 32) ^ r1.lo ^ rk[5], static_cast<uint32_t>(p0), rk);
 }
 
 // Round 0 of counter (cell, sweep, chain, tag) needs no per-call multiply:

@@ -23,16 +23,20 @@ __device__ __forceinline__ int endpoint_term(const uint32_t* s_v, uint32_t half,
 // Generic hidden half-step: any filter list (<= 16 filters), odd L, open
 // boundaries.  m = c1 v1 + c2 v2 with a zero-padded endpoint contributing 0;
 // the threshold row is cls * 5 + (m + 2).
+// Draws: Philox-4x32-10 of counter (cell, sweep, chain, tag) from the split
+// rounds (crbm_device.cuh): rs = round1_sweep of the lane's sweep word, Y the
+// lane's chain word, rk the round keys.
 __device__ __forceinline__ void hidden_cell_generic(const Geometry& g, const uint32_t* s_v,
                                                     uint32_t* s_h, const uint32_t* s_tab,
-                                                    const uint32_t* __restrict__ ep,
-                                                    int cell, uint32_t t,
-                                                    uint32_t chain, int lane, int col, uint32_t k0,
-                                                    uint32_t k1, const uint32_t (&sn)[2]) {
+                                                    const uint32_t* __restrict__ ep, int cell,
+                                                    const Round1Sweep& rs, uint32_t Y, const uint32_t (&rk)[20],
+                                                    int lane, int col, const uint32_t (&sn)[2]) {
+    const Round0Cell rc = round0_cell(static_cast<uint32_t>(cell), rk[1]);
+    const Round2Cell r2 = round2_cell(rs.hik ^ rc.b);
     U4 q[4];
 #pragma unroll
     for (int c = 0; c < 4; ++c)
-        if (c < g.n_calls) q[c] = philox(cell, t, chain, static_cast<uint32_t>(c), k0, k1);
+        if (c < g.n_calls) q[c] = philox_from_round2(Y, rs, r2, rc.a ^ static_cast<uint32_t>(c), rk);
     const uint32_t* e = ep + static_cast<size_t>(cell) * g.nb;
 #pragma unroll
     for (int k = 0; k < kMaxBonds; ++k) {
@@ -54,10 +58,11 @@ __device__ __forceinline__ void visible_cell_generic(const Geometry& g, uint32_t
                                                      const uint32_t* s_h, const uint32_t* s_tab,
                                                      const uint32_t* __restrict__ inc,
                                                      const int32_t* __restrict__ inc_off,
-                                                     int cell, int i, int j, uint32_t t,
-                                                     uint32_t chain, int lane, int col, uint32_t k0,
-                                                     uint32_t k1, const uint32_t (&sn)[2]) {
-    const U4 q = philox(cell, t, chain, kTagVis, k0, k1);
+                                                     int cell, int i, int j, const Round1Sweep& rs, uint32_t Y,
+                                                     const uint32_t (&rk)[20], int lane, int col,
+                                                     const uint32_t (&sn)[2]) {
+    const Round0Cell rc = round0_cell(static_cast<uint32_t>(cell), rk[1]);
+    const U4 q = philox_from_round2(Y, rs, round2_cell(rs.hik ^ rc.b), rc.a ^ kTagVis, rk);
     const int nP = 2 * g.DJp + 1;
 #pragma unroll
     for (int w = 0; w < 4; ++w) {
@@ -149,15 +154,17 @@ __device__ __forceinline__ void sweep_generic_body(const SweepArgs& a, int word)
     const int i_first = warp / g.W, j_first = warp - (warp / g.W) * g.W;
     const int di = nwarp / g.W, dj = nwarp - (nwarp / g.W) * g.W;
 
+    const Round0Lane r0l = round0_lane(chain);
     for (int it = 0; it < a.n_sweeps; ++it) {
         const uint32_t t = t0 + static_cast<uint32_t>(it);
+        const Round1Sweep rs = round1_sweep(r0l.hi ^ t ^ a.rk[0], a.rk);
         for (int cell = warp; cell < g.n_cells; cell += nwarp)
-            hidden_cell_generic(g, s_v, s_h, s_tab, a.gep, cell, t, chain, lane, col, a.key0, a.key1, sn);
+            hidden_cell_generic(g, s_v, s_h, s_tab, a.gep, cell, rs, r0l.lo, a.rk, lane, col, sn);
         __syncthreads();
         int i = i_first, j = j_first;
         for (int cell = warp; cell < g.n_cells; cell += nwarp) {
-            visible_cell_generic(g, s_v, s_h, s_tab, a.inc, a.inc_off, cell, i, j, t, chain, lane, col,
-                                 a.key0, a.key1, sn);
+            visible_cell_generic(g, s_v, s_h, s_tab, a.inc, a.inc_off, cell, i, j, rs, r0l.lo, a.rk, lane, col,
+                                 sn);
             i += di;
             j += dj;
             if (j >= g.W) {

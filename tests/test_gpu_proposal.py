@@ -1,7 +1,8 @@
 """The learned block proposal on the GPU against the oracle: logits of the
 tensor-core net vs the oracle's bf16 forward, the exact integer energy change
 of every proposed move, training gradients vs the oracle's back-propagation,
-and the mixed sampler's observables vs plain Gibbs."""
+the mixed sampler's observables vs plain Gibbs, and what the trained net gains
+in effective samples per sweep over plain Gibbs and over the untrained net."""
 import numpy as np
 import pytest
 
@@ -121,6 +122,43 @@ def test_mixed_sampler_matches_plain_gibbs():
         res.append([(x.mean(0).mean(), x.mean(0).std(ddof=1) / np.sqrt(n)) for x in (E, M)])
     for (m0, s0), (m1, s1) in zip(res[0], res[1]):
         assert abs(m0 - m1) < 4 * np.hypot(s0, s1), (m0, m1, s0, s1)
+
+
+def test_trained_network_gains_effective_samples_per_sweep():
+    """What the trained network adds over the method without it: from one
+    equilibrated L=18 state (J'/J = 1, h = 3, beta = 2, near the 1/3 plateau),
+    Gibbs + one pass of trained block moves per sweep gives more effective
+    samples of the energy per sweep than plain Gibbs, and far more accepted
+    moves than the same net untrained.  (Per second it does not pay: a pass
+    costs about a dozen Gibbs sweeps; the bench line states that ratio.)"""
+    from paper_2511_20911_gb300 import analysis
+    src = crbm.Sampler(**workloads.proposal_training_workload(n_chains=2048))
+    src.sweep(300)
+    trained = crbm.Proposal(seed=5)
+    trained.train(src, steps=250, batch=4096, lr=1e-2, sweeps_between=2)
+    untrained = crbm.Proposal(seed=5)
+    T = 1000
+    ew = workloads.proposal_eval_workload(18, n_chains=1024, betas=(2.0,))
+    base = crbm.Sampler(**dict(ew, measure_every=1, series_len=T))
+    base.sweep(6000)
+    ck = base.save()
+    ess, acc = {}, {}
+    for name, prop in (("plain", None), ("untrained", untrained), ("trained", trained)):
+        s = crbm.Sampler(**dict(ew, measure_every=1, series_len=T))
+        s.load(ck)
+        s.reset_observables()
+        if prop is None:
+            s.sweep(T)
+        else:
+            p0 = prop.stats()
+            prop.sweep_mixed(s, T)
+            p1 = prop.stats()
+            acc[name] = (p1[1] - p0[1]) / max(1, p1[0] - p0[0])
+        ser = s.series().transpose(1, 0, 2).astype(np.float64)   # [chain][T][3]
+        E = ser[..., 0] + ser[..., 1] - 3.0 * ser[..., 2]
+        ess[name] = float(analysis.effective_samples(E).sum())
+    assert ess["trained"] > 1.2 * ess["plain"], ess
+    assert acc["trained"] > 2.0 * acc["untrained"], acc
 
 
 def test_proposal_rejects_unsupported_contexts():

@@ -99,29 +99,42 @@ __global__ void __launch_bounds__(kPassThreads, 1) k_prop_pass(const __grid_cons
     float* logit = reinterpret_cast<float*>(sm + 12800 + 16384);   // [32][16]
     uint32_t* pw = sm + 12800 + 16384 + 512;   // [100] patch words
     uint2* fr = reinterpret_cast<uint2*>(pw + 100 + 4);           // [kFrags][32]
+    uint32_t* s_par = reinterpret_cast<uint32_t*>(fr + kFrags * 32);  // [100] row/column parity planes (bf16 pair)
+    uint32_t* s_in = s_par + 100;                                  // [100] 1 inside the block
+    uint32_t* s_bh = s_in + 100;                                   // [32] beta, h of each lane (bf16 pair)
+    // Metropolis-Hastings per (chain, site), over A1 once layer 2 has read it
+    float* lqc = reinterpret_cast<float*>(A1);  // [32][16] log q of the current spin
+    float* lqn = lqc + 512;                     // [32][16] log q of the proposed spin
+    int* s_xx = reinterpret_cast<int*>(lqn + 512);  // [32][16] bit 0: current +1, bit 1: proposed +1
+    long long* s_de = reinterpret_cast<long long*>(s_xx + 512);  // [32][16] energy-change terms
 
     // block origin of this pass
     const U4 off = philox(a.pass, 0u, 0u, kTagOffset, a.key0, a.key1);
     const int bR = static_cast<int>((off.x % static_cast<uint32_t>(L) + a.spacing * (b / a.nb1)) % L);
     const int bC = static_cast<int>((off.y % static_cast<uint32_t>(L) + a.spacing * (b % a.nb1)) % L);
-    for (int x = threadIdx.x; x < kP * kP; x += blockDim.x) {
+    for (int x = threadIdx.x; x < kP * kP; x += blockDim.x) {  // per patch position
         const int R = (bR - 3 + x / kP + 2 * L) % L, C = (bC - 3 + x % kP + 2 * L) % L;
         pw[x] = a.v[static_cast<size_t>(word) * N + R * L + C];
+        s_in[x] = ((R - bR + L) % L) < kK && ((C - bC + L) % L) < kK;
+        s_par[x] = pack_bf16(static_cast<float>(R & 1), static_cast<float>(C & 1));
+    }
+    if (threadIdx.x < 32) {
+        const int chain = word * 32 + threadIdx.x;
+        s_bh[threadIdx.x] = pack_bf16(a.chain_bh[2 * chain], a.chain_bh[2 * chain + 1]);
     }
     for (int x = threadIdx.x; x < kFrags * 32; x += blockDim.x) fr[x] = a.frag[x];
     __syncthreads();
     // input planes, 8 channels per (chain, position): spin | mask | R&1 | C&1 | beta | h | 0 | 0
-    for (int x = threadIdx.x; x < 32 * kP * kP; x += blockDim.x) {
-        const int c = x / (kP * kP), pos = x - c * (kP * kP);
-        const int R = (bR - 3 + pos / kP + 2 * L) % L, C = (bC - 3 + pos % kP + 2 * L) % L;
-        const bool inside = ((R - bR + L) % L) < kK && ((C - bC + L) % L) < kK;
-        const float spin = inside ? 0.f : (((pw[pos] >> c) & 1u) ? 1.f : -1.f);
-        const int chain = word * 32 + c;
-        uint32_t* dst = X + (c * kP * kP + pos) * 4;
-        dst[0] = pack_bf16(spin, inside ? 1.f : 0.f);
-        dst[1] = pack_bf16(static_cast<float>(R & 1), static_cast<float>(C & 1));
-        dst[2] = pack_bf16(a.chain_bh[2 * chain], a.chain_bh[2 * chain + 1]);
-        dst[3] = 0u;
+    {
+        const uint32_t in_word = pack_bf16(0.f, 1.f), up = pack_bf16(1.f, 0.f), down = pack_bf16(-1.f, 0.f);
+        for (int x = threadIdx.x; x < 32 * kP * kP; x += blockDim.x) {
+            const int c = x / (kP * kP), pos = x - c * (kP * kP);
+            uint32_t* dst = X + (c * kP * kP + pos) * 4;
+            dst[0] = s_in[pos] ? in_word : (((pw[pos] >> c) & 1u) ? up : down);
+            dst[1] = s_par[pos];
+            dst[2] = s_bh[c];
+            dst[3] = 0u;
+        }
     }
     __syncthreads();
     // ---- layer 1: rows (chain, y*8+x) = 2048 (128 m-tiles), K = 10 taps x 8 ch
@@ -200,57 +213,83 @@ __global__ void __launch_bounds__(kPassThreads, 1) k_prop_pass(const __grid_cons
         }
     }
     __syncthreads();
-    // ---- Metropolis-Hastings decision: warp 0, lane = chain
-    if (warp != 0) return;
+    // ---- Metropolis-Hastings, phase A on every warp: lane = chain, warp w
+    // draws Philox call w / 2 of its chain (4 sites) and takes sites
+    // 4 (w / 2) + 2 (w % 2) + {0, 1}: threshold, log q of the current and the
+    // proposed spin, the proposed spin.
     const int chain = word * 32 + lane;
     const uint32_t cell_id = static_cast<uint32_t>(b);
-    int x[kK * kK], xn[kK * kK];
-    float logq_cur = 0.f, logq_new = 0.f;
-    U4 u[4];
-#pragma unroll
-    for (int c = 0; c < 4; ++c)
-        u[c] = philox(cell_id, a.pass, static_cast<uint32_t>(chain), kTagBits + c, a.key0, a.key1);
-#pragma unroll
-    for (int s = 0; s < kK * kK; ++s) {
-        const int pos = (3 + s / kK) * kP + 3 + s % kK;
-        x[s] = ((pw[pos] >> lane) & 1u) ? 1 : -1;
-        const float q = 1.f / (1.f + __expf(-logit[lane * 16 + s]));
-        float tf = q * 4294967296.f;
-        tf = fminf(fmaxf(tf, 1.f), 4294967040.f);
-        const uint32_t thr = static_cast<uint32_t>(tf);
-        const float p1 = static_cast<float>(thr) * 2.3283064365386963e-10f;
-        const float lp = __logf(p1), lm = log1pf(-p1);
-        xn[s] = pick(u[s >> 2], s & 3) < thr ? 1 : -1;
-        logq_cur += x[s] > 0 ? lp : lm;
-        logq_new += xn[s] > 0 ? lp : lm;
-    }
-    // exact energy difference (1/16 units) over the bonds touching the block
     const int qJ = a.chain_q[3 * chain], qJp = a.chain_q[3 * chain + 1], qh = a.chain_q[3 * chain + 2];
-    auto spin_at = [&](int pr, int pc) -> int { return ((pw[pr * kP + pc] >> lane) & 1u) ? 1 : -1; };
+    {
+        const int call = warp >> 1;
+        const U4 u = philox(cell_id, a.pass, static_cast<uint32_t>(chain), kTagBits + call, a.key0, a.key1);
+#pragma unroll
+        for (int j = 0; j < 2; ++j) {
+            const int s = 4 * call + 2 * (warp & 1) + j;
+            const int pos = (3 + s / kK) * kP + 3 + s % kK;
+            const int xc = ((pw[pos] >> lane) & 1u) ? 1 : -1;
+            const float q = 1.f / (1.f + __expf(-logit[lane * 16 + s]));
+            float tf = q * 4294967296.f;
+            tf = fminf(fmaxf(tf, 1.f), 4294967040.f);
+            const uint32_t thr = static_cast<uint32_t>(tf);
+            const float p1 = static_cast<float>(thr) * 2.3283064365386963e-10f;
+            const float lp = __logf(p1), lm = log1pf(-p1);
+            const int xp = pick(u, s & 3) < thr ? 1 : -1;
+            lqc[lane * 16 + s] = xc > 0 ? lp : lm;
+            lqn[lane * 16 + s] = xp > 0 ? lp : lm;
+            s_xx[lane * 16 + s] = (xc > 0 ? 1 : 0) | (xp > 0 ? 2 : 0);
+        }
+    }
+    __syncthreads();
+    // phase A': each site's share of the exact energy change (1/16 units) over
+    // the bonds touching the block; a bond inside the block is counted by its
+    // left / upper endpoint (right and down neighbours, and the dimer partner
+    // of higher index)
+    {
+        auto spin_at = [&](int pr, int pc) -> int { return ((pw[pr * kP + pc] >> lane) & 1u) ? 1 : -1; };
+        auto xs = [&](int t) { return (s_xx[lane * 16 + t] & 1) ? 1 : -1; };
+        auto ns = [&](int t) { return (s_xx[lane * 16 + t] & 2) ? 1 : -1; };
+#pragma unroll
+        for (int j = 0; j < 2; ++j) {
+            const int s = 4 * (warp >> 1) + 2 * (warp & 1) + j;
+            const int ar = s / kK, ac = s % kK;
+            const int x0 = xs(s), n0 = ns(s), d = n0 - x0;
+            long long dE = -static_cast<long long>(qh) * d;
+            if (ac + 1 < kK) dE += static_cast<long long>(qJ) * (n0 * ns(s + 1) - x0 * xs(s + 1));
+            else dE += static_cast<long long>(qJ) * d * spin_at(3 + ar, 3 + ac + 1);
+            if (ar + 1 < kK) dE += static_cast<long long>(qJ) * (n0 * ns(s + kK) - x0 * xs(s + kK));
+            else dE += static_cast<long long>(qJ) * d * spin_at(3 + ar + 1, 3 + ac);
+            if (ac == 0) dE += static_cast<long long>(qJ) * d * spin_at(3 + ar, 2);
+            if (ar == 0) dE += static_cast<long long>(qJ) * d * spin_at(2, 3 + ac);
+            // the orthogonal dimer of this site
+            const int R = bR + ar, C = bC + ac;
+            const int dR = (R & 1) ? ((C & 1) ? -1 : 1) : ((C & 1) ? -1 : 1);
+            const int dC = (R & 1) ? -1 : 1;
+            const int pr = ar + dR, pc = ac + dC;
+            if (pr >= 0 && pr < kK && pc >= 0 && pc < kK) {
+                const int t = pr * kK + pc;
+                if (t > s) dE += static_cast<long long>(qJp) * (n0 * ns(t) - x0 * xs(t));
+            } else {
+                dE += static_cast<long long>(qJp) * d * spin_at(3 + pr, 3 + pc);
+            }
+            s_de[lane * 16 + s] = dE;
+        }
+    }
+    __syncthreads();
+    // ---- phase B, warp 0, lane = chain: sums over the sites in site order,
+    // the exact MH test and the move
+    if (warp != 0) return;
+    float logq_cur = 0.f, logq_new = 0.f;
     long long dE = 0;
+    uint32_t cb = 0, nb = 0;
 #pragma unroll
     for (int s = 0; s < kK * kK; ++s) {
-        const int ar = s / kK, ac = s % kK;
-        const int d = xn[s] - x[s];
-        dE -= static_cast<long long>(qh) * d;
-        // right and down: inside the block both endpoints change
-        if (ac + 1 < kK) dE += static_cast<long long>(qJ) * (xn[s] * xn[s + 1] - x[s] * x[s + 1]);
-        else dE += static_cast<long long>(qJ) * d * spin_at(3 + ar, 3 + ac + 1);
-        if (ar + 1 < kK) dE += static_cast<long long>(qJ) * (xn[s] * xn[s + kK] - x[s] * x[s + kK]);
-        else dE += static_cast<long long>(qJ) * d * spin_at(3 + ar + 1, 3 + ac);
-        if (ac == 0) dE += static_cast<long long>(qJ) * d * spin_at(3 + ar, 2);
-        if (ar == 0) dE += static_cast<long long>(qJ) * d * spin_at(2, 3 + ac);
-        // the orthogonal dimer of this site
-        const int R = bR + ar, C = bC + ac;
-        const int dR = (R & 1) ? ((C & 1) ? -1 : 1) : ((C & 1) ? -1 : 1);
-        const int dC = (R & 1) ? -1 : 1;
-        const int pr = ar + dR, pc = ac + dC;
-        if (pr >= 0 && pr < kK && pc >= 0 && pc < kK) {
-            const int t = pr * kK + pc;
-            if (t > s) dE += static_cast<long long>(qJp) * (xn[s] * xn[t] - x[s] * x[t]);
-        } else {
-            dE += static_cast<long long>(qJp) * d * spin_at(3 + pr, 3 + pc);
-        }
+        logq_cur += lqc[lane * 16 + s];
+        logq_new += lqn[lane * 16 + s];
+        dE += s_de[lane * 16 + s];
+        const int xx = s_xx[lane * 16 + s];
+        cb |= static_cast<uint32_t>(xx & 1) << s;
+        nb |= static_cast<uint32_t>((xx >> 1) & 1) << s;
     }
     const float beta = a.chain_bh[2 * chain];
     const float log_alpha = -beta * static_cast<float>(dE) * 0.0625f + logq_cur - logq_new;
@@ -259,13 +298,8 @@ __global__ void __launch_bounds__(kPassThreads, 1) k_prop_pass(const __grid_cons
                         static_cast<float>(ua.x >> 8) * 5.9604644775390625e-08f < __expf(log_alpha);
     if (a.rec) {  // inspection: record, do not move
         PassRecord* r = a.rec + (static_cast<size_t>(word) * gridDim.x + b) * 32 + lane;
-        uint32_t cb = 0, nb = 0;
 #pragma unroll
-        for (int s = 0; s < kK * kK; ++s) {
-            r->logit[s] = logit[lane * 16 + s];
-            cb |= (x[s] > 0 ? 1u : 0u) << s;
-            nb |= (xn[s] > 0 ? 1u : 0u) << s;
-        }
+        for (int s = 0; s < kK * kK; ++s) r->logit[s] = logit[lane * 16 + s];
         r->dE = static_cast<int32_t>(dE);
         r->cur_bits = cb;
         r->new_bits = nb;
@@ -277,8 +311,7 @@ __global__ void __launch_bounds__(kPassThreads, 1) k_prop_pass(const __grid_cons
     const uint32_t am = __ballot_sync(0xffffffffu, accept);
 #pragma unroll
     for (int s = 0; s < kK * kK; ++s) {
-        const int val = accept ? xn[s] : x[s];
-        const uint32_t wv = __ballot_sync(0xffffffffu, val > 0);
+        const uint32_t wv = __ballot_sync(0xffffffffu, ((accept ? nb : cb) >> s) & 1u);
         if (lane == s) {
             const int R = (bR + s / kK) % L, C = (bC + s % kK) % L;
             a.v[static_cast<size_t>(word) * N + R * L + C] = wv;
@@ -604,7 +637,7 @@ cudaError_t launch_pass(crbm_ctx* ctx, crbm_proposal* p, crbm::PassRecord* rec) 
     a.pass = static_cast<uint32_t>(ctx->passes);
     a.nb1 = nb1;
     a.spacing = L / nb1;
-    const size_t smem = (12800 + 16384 + 512 + 104) * 4 + crbm::kFrags * 32 * 8;
+    const size_t smem = (12800 + 16384 + 512 + 104) * 4 + crbm::kFrags * 32 * 8 + 232 * 4;
     cudaError_t e = cudaFuncSetAttribute(crbm::k_prop_pass, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                          static_cast<int>(smem));
     if (e != cudaSuccess) return e;

@@ -231,6 +231,7 @@ int crbm_batch_create(crbm_batch** out, crbm_ctx* const* ctxs, int32_t n_ctx) {
             while (nb < cluster && 2 * nb <= x->g.W && x->g.n_cells / nb > target) nb *= 2;
         b->bands.push_back(nb);
     }
+    if (*std::max_element(b->bands.begin(), b->bands.end()) == 1) cluster = 1;  // nothing to split
     // tasks: split words cluster by cluster (heaviest member first), then
     // whole words one per CTA (heaviest first), padded to whole clusters
     std::vector<int> order(n_ctx);

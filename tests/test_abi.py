@@ -12,7 +12,8 @@ def declared_functions():
     names = set()
     for f in os.listdir(os.path.join(ROOT, "include")):
         if f.endswith(".h"):
-            txt = open(os.path.join(ROOT, "include", f)).read()
+            with open(os.path.join(ROOT, "include", f)) as fh:
+                txt = fh.read()
             txt = re.sub(r"/\*.*?\*/", "", txt, flags=re.S)
             names |= set(re.findall(r"\b(crbm_[a-z0-9_]+)\s*\(", txt))
     return names

@@ -36,9 +36,9 @@ def _rank(rank, ws, port, out):
 
 def test_two_gloo_ranks_replica_logic():
     ws, port = 2, _free_port()
-    with mp.Manager() as m:
+    ctx = mp.get_context("spawn")
+    with ctx.Manager() as m:
         out = m.dict()
-        ctx = mp.get_context("spawn")
         procs = [ctx.Process(target=_rank, args=(r, ws, port, out)) for r in range(ws)]
         for p in procs:
             p.start()

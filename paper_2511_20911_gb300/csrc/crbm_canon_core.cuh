@@ -51,6 +51,16 @@ constexpr uint32_t kDownBits = (1u << 11) | (1u << 15) | (1u << 16);
 constexpr uint32_t kRightBits = (1u << 10) | (1u << 20) | (1u << 21);
 constexpr uint32_t kOwnBits = ((1u << 27) - (1u << 7)) & ~kDownBits & ~kRightBits;
 
+// w | K when q < t, as one compare and one predicated OR (the conditional
+// expression form compiles to a compare, a select and an OR).
+template <uint32_t K>
+__device__ __forceinline__ uint32_t or_if_less(uint32_t w, uint32_t q, uint32_t t) {
+    asm("{\n\t.reg .pred p;\n\tsetp.lt.u32 p, %1, %2;\n\t@p or.b32 %0, %0, %3;\n\t}"
+        : "+r"(w)
+        : "r"(q), "r"(t), "n"(K));
+    return w;
+}
+
 // Byte-addressed 32-bit shared-memory load.
 __device__ __forceinline__ uint32_t lds_at(const uint32_t* base, uint32_t byte_off) {
     return *reinterpret_cast<const uint32_t*>(reinterpret_cast<const char*>(base) + byte_off);
@@ -107,16 +117,16 @@ __device__ __forceinline__ uint32_t hidden_core(uint32_t v00, uint32_t v01, uint
     const uint32_t* thP = s_th + 128;
     uint32_t w = 0u;
     // filters 0..7 (J) and 8..9 (J'): (first endpoint, second endpoint)
-    w |= q0.x < lds_at(thJ, a00 | b01 | lc.lb) ? kBit0 : 0u;
-    w |= q0.y < lds_at(thJ, a01 | b02 | lc.lb) ? kBit1 : 0u;
-    w |= q0.z < lds_at(thJ, a10 | b11 | lc.lb) ? kBit2 : 0u;
-    w |= q0.w < lds_at(thJ, a11 | b12 | lc.lb) ? kBit3 : 0u;
-    w |= q1.x < lds_at(thJ, a00 | b10 | lc.lb) ? kBit4 : 0u;
-    w |= q1.y < lds_at(thJ, a10 | b20 | lc.lb) ? kBit5 : 0u;
-    w |= q1.z < lds_at(thJ, a01 | b11 | lc.lb) ? kBit6 : 0u;
-    w |= q1.w < lds_at(thJ, a11 | b21 | lc.lb) ? kBit7 : 0u;
-    w |= q2.x < lds_at(thP, a00 | b11 | lc.lb) ? kBit8 : 0u;
-    w |= q2.y < lds_at(thP, a12 | b21 | lc.lb) ? kBit9 : 0u;
+    w = or_if_less<kBit0>(w, q0.x, lds_at(thJ, a00 | b01 | lc.lb));
+    w = or_if_less<kBit1>(w, q0.y, lds_at(thJ, a01 | b02 | lc.lb));
+    w = or_if_less<kBit2>(w, q0.z, lds_at(thJ, a10 | b11 | lc.lb));
+    w = or_if_less<kBit3>(w, q0.w, lds_at(thJ, a11 | b12 | lc.lb));
+    w = or_if_less<kBit4>(w, q1.x, lds_at(thJ, a00 | b10 | lc.lb));
+    w = or_if_less<kBit5>(w, q1.y, lds_at(thJ, a10 | b20 | lc.lb));
+    w = or_if_less<kBit6>(w, q1.z, lds_at(thJ, a01 | b11 | lc.lb));
+    w = or_if_less<kBit7>(w, q1.w, lds_at(thJ, a11 | b21 | lc.lb));
+    w = or_if_less<kBit8>(w, q2.x, lds_at(thP, a00 | b11 | lc.lb));
+    w = or_if_less<kBit9>(w, q2.y, lds_at(thP, a12 | b21 | lc.lb));
     return w;
 }
 

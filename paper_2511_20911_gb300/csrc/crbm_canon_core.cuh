@@ -91,12 +91,14 @@ __device__ __forceinline__ void sts_off(char* sm, uint32_t off, uint32_t x) {
 }
 
 // Hidden half-step of one cell from its eight window words v_rc (row r,
-// column c of the 3x3 window; (2,2) is not used) and the cell's round-0
-// Philox words (rca, rcb); returns the lane's word W.
+// column c of the 3x3 window; (2,2) is not used), the cell's round-0 Philox
+// word rcb = lo(M0 cell) and the round-1 call products of its three calls;
+// returns the lane's word W.
 __device__ __forceinline__ uint32_t hidden_core(uint32_t v00, uint32_t v01, uint32_t v02, uint32_t v10,
                                                 uint32_t v11, uint32_t v12, uint32_t v20, uint32_t v21,
                                                 const uint32_t* s_th, const Round1Sweep& r1, uint32_t Y,
-                                                uint32_t rca, uint32_t rcb, const uint32_t (&rk)[20],
+                                                uint32_t rcb, const Round1Call& c0, const Round1Call& c1,
+                                                const Round1Call& c2, const uint32_t (&rk)[20],
                                                 const LaneConst& lc) {
     const uint32_t m00 = v00 & lc.lm, m01 = v01 & lc.lm, m02 = v02 & lc.lm, m10 = v10 & lc.lm;
     const uint32_t m11 = v11 & lc.lm, m12 = v12 & lc.lm, m20 = v20 & lc.lm, m21 = v21 & lc.lm;
@@ -110,9 +112,9 @@ __device__ __forceinline__ uint32_t hidden_core(uint32_t v00, uint32_t v01, uint
     const uint32_t b12 = rotr(m12, lc.rot[1]), b20 = rotr(m20, lc.rot[1]);
     const uint32_t b21 = rotr(m21, lc.rot[1]);
     const Round2Cell r2 = round2_cell(r1.hik ^ rcb);  // shared by the cell's calls
-    const U4 q0 = philox_from_round2(Y, r1, r2, rca, rk);
-    const U4 q1 = philox_from_round2(Y, r1, r2, rca ^ 1u, rk);
-    const U4 q2 = philox_from_round2(Y, r1, r2, rca ^ 2u, rk);
+    const U4 q0 = philox_from_call(Y, r1, r2, c0, rk);
+    const U4 q1 = philox_from_call(Y, r1, r2, c1, rk);
+    const U4 q2 = philox_from_call(Y, r1, r2, c2, rk);
     const uint32_t* thJ = s_th;
     const uint32_t* thP = s_th + 128;
     uint32_t w = 0u;
@@ -137,28 +139,31 @@ __device__ __forceinline__ uint32_t hidden_cell(const uint32_t* s_v, int r0, int
                                                 uint32_t Y, const Round0Cell rc,
                                                 const uint32_t (&rk)[20], const LaneConst& lc) {
     return hidden_core(s_v[r0 + c0], s_v[r0 + c1], s_v[r0 + c2], s_v[r1 + c0], s_v[r1 + c1], s_v[r1 + c2],
-                       s_v[r2 + c0], s_v[r2 + c1], s_th, rs, Y, rc.a, rc.b, rk, lc);
+                       s_v[r2 + c0], s_v[r2 + c1], s_th, rs, Y, rc.b, round1_call(rc.a, rk),
+                       round1_call(rc.a ^ 1u, rk), round1_call(rc.a ^ 2u, rk), rk, lc);
 }
 
-// Hidden half-step of one cell described by its records h0, h1 (layout in
-// crbm_internal.h); returns the lane's word W.
+// Hidden half-step of one cell described by its records h0, h1, h2 and the
+// first word h5 of its record 5 (layout in crbm_internal.h); returns the
+// lane's word W.
 __device__ __forceinline__ uint32_t hidden_cell_rec(const char* sm, const uint4& h0, const uint4& h1,
-                                                    const uint32_t* s_th, const Round1Sweep& rs, uint32_t Y,
-                                                    const uint32_t (&rk)[20], const LaneConst& lc) {
+                                                    const uint4& h2, uint32_t h5, const uint32_t* s_th,
+                                                    const Round1Sweep& rs, uint32_t Y, const uint32_t (&rk)[20],
+                                                    const LaneConst& lc) {
     return hidden_core(lds_off(sm, h0.x), lds_off(sm, h0.x + 4u), lds_off(sm, h0.w), lds_off(sm, h0.y),
                        lds_off(sm, h0.y + 4u), lds_off(sm, h1.x), lds_off(sm, h0.z), lds_off(sm, h0.z + 4u),
-                       s_th, rs, Y, h1.w, h1.z, rk, lc);
+                       s_th, rs, Y, h1.z, {h2.x, h2.y}, {h2.z, h2.w}, {h1.w, h5}, rk, lc);
 }
 
 // Visible half-step of one cell from the lanes' words of this cell (wo), the
-// cell above (wu) and the cell to the left (wl), with round-0 words
-// (rca ^ visible tag, rcb); returns the four new spin words (0,0) (0,1)
-// (1,0) (1,1) of the cell.
+// cell above (wu) and the cell to the left (wl), with the cell's round-0 word
+// rcb = lo(M0 cell) and the round-1 product cv of its visible call; returns
+// the four new spin words (0,0) (0,1) (1,0) (1,1) of the cell.
 __device__ __forceinline__ U4 visible_core(uint32_t wo, uint32_t wu, uint32_t wl, const uint32_t* s_tv,
-                                           const Round1Sweep& r1, uint32_t Y, uint32_t rcav, uint32_t rcb,
-                                           const uint32_t (&rk)[20], const LaneConst& lc) {
+                                           const Round1Sweep& r1, uint32_t Y, uint32_t rcb,
+                                           const Round1Call& cv, const uint32_t (&rk)[20], const LaneConst& lc) {
     const uint32_t c = (wo & kOwnBits) | (wu & kDownBits) | (wl & kRightBits);
-    const U4 q = philox_from_round1(Y, r1, r1.hik ^ rcb, rcav, rk);
+    const U4 q = philox_from_call(Y, r1, round2_cell(r1.hik ^ rcb), cv, rk);
     const uint32_t f = 31u << 7;
     const uint32_t t00 = lds_at(s_tv, (c & f) | lc.lb);
     const uint32_t t01 = lds_at(s_tv + 1024, ((c >> 5) & f) | lc.lb);
@@ -174,21 +179,21 @@ __device__ __forceinline__ void visible_cell(uint32_t* out, int row, uint32_t wo
                                              uint32_t wl, const uint32_t* s_tv, const Round1Sweep& rs,
                                              uint32_t Y, const Round0Cell rc, const uint32_t (&rk)[20],
                                              const LaneConst& lc) {
-    const U4 o = visible_core(wo, wu, wl, s_tv, rs, Y, rc.a ^ kTagVis, rc.b, rk, lc);
+    const U4 o = visible_core(wo, wu, wl, s_tv, rs, Y, rc.b, round1_call(rc.a ^ kTagVis, rk), rk, lc);
     out[0] = o.x;
     out[1] = o.y;
     out[row] = o.z;
     out[row + 1] = o.w;
 }
 
-// Visible half-step of one cell described by its records v0, v1; lane4 =
+// Visible half-step of one cell described by its records 3 and 4 (v0, v1); lane4 =
 // 4 * lane (the lane's column of the hidden rows).  Stores the four new spin
 // words and returns them.
 __device__ __forceinline__ U4 visible_cell_rec(char* sm, const uint4& v0, const uint4& v1, uint32_t lane4,
                                                const uint32_t* s_tv, const Round1Sweep& rs, uint32_t Y,
                                                const uint32_t (&rk)[20], const LaneConst& lc) {
     const U4 o = visible_core(lds_off(sm, v0.z + lane4), lds_off(sm, v0.w + lane4), lds_off(sm, v1.x + lane4),
-                              s_tv, rs, Y, v1.z, v1.y, rk, lc);
+                              s_tv, rs, Y, v1.y, {v1.z, v1.w}, rk, lc);
     sts_off(sm, v0.x, o.x);
     sts_off(sm, v0.x + 4u, o.y);
     sts_off(sm, v0.y, o.z);

@@ -133,6 +133,26 @@ __device__ __forceinline__ U4 philox_from_round2(uint32_t Y, const Round1Sweep& 
                              static_cast<uint32_t>(p0 >> 32) ^ r1.lo ^ rk[5], static_cast<uint32_t>(p0), rk);
 }
 
+// Round 1's product M1 c2 of a call: c2 = hi(M0 cell) ^ key1 ^ tag is the
+// same for every lane, so its product can be formed once per (cell, tag),
+// on the host for the record-driven sweeps.  Stored XORed with the round keys
+// it meets: (hi ^ rk2, lo ^ rk4).
+struct Round1Call {
+    uint32_t h, l;
+};
+__device__ __forceinline__ Round1Call round1_call(uint32_t c2, const uint32_t (&rk)[20]) {
+    const uint64_t p = static_cast<uint64_t>(kPhiloxM1) * c2;
+    return {static_cast<uint32_t>(p >> 32) ^ rk[2], static_cast<uint32_t>(p) ^ rk[4]};
+}
+// The full Philox-4x32-10 output of a call from r1 = round1_sweep(X), the
+// cell's r2 = round2_cell(r1.hik ^ c3) and the call's q = round1_call(c2).
+__device__ __forceinline__ U4 philox_from_call(uint32_t Y, const Round1Sweep& r1, const Round2Cell& r2,
+                                               const Round1Call& q, const uint32_t (&rk)[20]) {
+    const uint64_t p0 = static_cast<uint64_t>(kPhiloxM0) * (q.h ^ Y);     // round 2
+    return philox_rounds3to9(r2.hi ^ q.l, r2.lo, static_cast<uint32_t>(p0 >> 32) ^ r1.lo ^ rk[5],
+                             static_cast<uint32_t>(p0), rk);
+}
+
 // Round 0 of counter (cell, sweep, chain, tag) needs no per-call multiply:
 // M1 * chain is a per-lane constant, M0 * cell is warp-uniform.  The state
 // after round 0 is (hi(M1 chain) ^ sweep ^ rk0, lo(M1 chain),

@@ -484,7 +484,8 @@ int crbm_create(crbm_ctx** out, const crbm_params* p) {
     std::vector<uint32_t> crec;
     if (g.canonical && ctx->layout == CRBM_LAYOUT_SMEM) {
         const int L = g.L, W = g.W;
-        const uint32_t key1 = static_cast<uint32_t>(ctx->seed >> 32);
+        const uint32_t key0 = static_cast<uint32_t>(ctx->seed), key1 = static_cast<uint32_t>(ctx->seed >> 32);
+        const uint32_t rk2 = key0 + 0x9E3779B9u, rk4 = key0 + 2u * 0x9E3779B9u;  // round keys 1, 2 (word 0)
         const uint32_t vb = 4u * kCanonSmemV, wb = 4u * static_cast<uint32_t>(kCanonSmemV + g.N);
         auto site = [&](int R, int C) { return vb + 4u * static_cast<uint32_t>((R % L) * L + C % L); };
         auto hrow = [&](int i, int j) { return wb + 128u * static_cast<uint32_t>(i * W + j); };
@@ -494,12 +495,22 @@ int crbm_create(crbm_ctx** out, const crbm_params* p) {
                 uint32_t* o = &crec[static_cast<size_t>(i * W + j) * kCellRec * 4];
                 const uint64_t m = 0xD2511F53ull * static_cast<uint32_t>(i * W + j);
                 const uint32_t lo = static_cast<uint32_t>(m), hi = static_cast<uint32_t>(m >> 32) ^ key1;
+                uint32_t qh[4], ql[4];  // round-1 products of the calls with tags 0, 1, 2, visible
+                const uint32_t tags[4] = {0u, 1u, 2u, kTagVis};
+                for (int t = 0; t < 4; ++t) {
+                    const uint64_t p = 0xCD9E8D57ull * (hi ^ tags[t]);
+                    qh[t] = static_cast<uint32_t>(p >> 32) ^ rk2;
+                    ql[t] = static_cast<uint32_t>(p) ^ rk4;
+                }
                 const int R = 2 * i, C = 2 * j;
-                const uint32_t rec[16] = {site(R, C),     site(R + 1, C), site(R + 2, C),
-                                          site(R, C + 2), site(R + 1, C + 2), hrow(i, j), lo, hi,
-                                          site(R, C),     site(R + 1, C), hrow(i, j), hrow((i + W - 1) % W, j),
-                                          hrow(i, (j + W - 1) % W), lo, hi ^ kTagVis, 0u};
-                std::copy(rec, rec + 16, o);
+                const uint32_t rec[kCellRec * 4] = {
+                    site(R, C),     site(R + 1, C), site(R + 2, C),        site(R, C + 2),
+                    site(R + 1, C + 2), hrow(i, j), lo,                    qh[2],
+                    qh[0],          ql[0],          qh[1],                 ql[1],
+                    site(R, C),     site(R + 1, C), hrow(i, j),            hrow((i + W - 1) % W, j),
+                    hrow(i, (j + W - 1) % W), lo,   qh[3],                 ql[3],
+                    ql[2],          0u,             0u,                    0u};
+                std::copy(rec, rec + kCellRec * 4, o);
             }
     }
     // Device state.

@@ -39,13 +39,19 @@ constexpr int kCanonTab = kCanonTh + 4 * 32 * 32;
 constexpr int kCanonSmemV = kAccWords + kCanonTab;
 // Per-cell records of that sweep, kCellRec uint4 per cell, built on the host
 // so that the cell loops do no index arithmetic.  Byte offsets are from the
-// start of dynamic shared memory; rc = (lo(M0 cell), hi(M0 cell) ^ key1) are
-// the round-0 Philox words of the cell (M0 the first Philox multiplier):
+// start of dynamic shared memory; rc.lo = lo(M0 cell) is a round-0 Philox
+// word of the cell (M0, M1 the Philox multipliers).  Round 1 multiplies the
+// warp-uniform word rc.hi ^ tag = hi(M0 cell) ^ key1 ^ tag by M1, so that
+// product is built here too, per call tag t: Qt = (hi(M1 (rc.hi ^ t)) ^ rk2,
+// lo(M1 (rc.hi ^ t)) ^ rk4), with the round keys it is XORed with
+// (tags 0, 1, 2: hidden calls; v: the visible call):
 //   [0] spins (0,0) (1,0) (2,0) (0,2) of the 3x3 window (site (r,1) is (r,0) + 4)
-//   [1] spin (1,2), the cell's hidden row, rc.lo, rc.hi
-//   [2] spins (0,0) (1,0) of the cell, hidden rows of the cell and of the cell above
-//   [3] hidden row of the cell to the left, rc.lo, rc.hi ^ visible tag, 0
-constexpr int kCellRec = 4;
+//   [1] spin (1,2), the cell's hidden row, rc.lo, Q2.hi
+//   [2] Q0.hi, Q0.lo, Q1.hi, Q1.lo
+//   [3] spins (0,0) (1,0) of the cell, hidden rows of the cell and of the cell above
+//   [4] hidden row of the cell to the left, rc.lo, Qv.hi, Qv.lo
+//   [5] Q2.lo, 0, 0, 0
+constexpr int kCellRec = 6;
 // (class, second-endpoint flag) of the five filter slots of each spin
 // position (0,0), (0,1), (1,0), (1,1) in the canonical visible tables.
 constexpr int kCanonSlot[4][5][2] = {{{0, 0}, {0, 0}, {1, 0}, {0, 1}, {0, 1}},

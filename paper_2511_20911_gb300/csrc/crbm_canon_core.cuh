@@ -132,15 +132,29 @@ __device__ __forceinline__ uint32_t hidden_core(uint32_t v00, uint32_t v01, uint
     return w;
 }
 
-// Hidden half-step of one cell.  Window rows at s_v + r0, r1, r2 and columns
-// c0, c1, c2; returns the lane's word W.
-__device__ __forceinline__ uint32_t hidden_cell(const uint32_t* s_v, int r0, int r1, int r2, int c0,
-                                                int c1, int c2, const uint32_t* s_th, const Round1Sweep& rs,
-                                                uint32_t Y, const Round0Cell rc,
-                                                const uint32_t (&rk)[20], const LaneConst& lc) {
-    return hidden_core(s_v[r0 + c0], s_v[r0 + c1], s_v[r0 + c2], s_v[r1 + c0], s_v[r1 + c1], s_v[r1 + c2],
-                       s_v[r2 + c0], s_v[r2 + c1], s_th, rs, Y, rc.b, round1_call(rc.a, rk),
-                       round1_call(rc.a ^ 1u, rk), round1_call(rc.a ^ 2u, rk), rk, lc);
+// Hidden half-step of one cell.  Window rows at s_v + 0, vs, 2 vs; q0 =
+// (rc.lo, Q0.h, Q0.l, Q1.h), q1 = (Q1.l, Q2.h, Q2.l, -): the cell's round-0
+// word and round-1 call products (as in the per-cell records).  Returns the
+// lane's word W.
+__device__ __forceinline__ uint32_t hidden_cell(const uint32_t* s_v, int vs, const uint32_t* s_th,
+                                                const Round1Sweep& rs, uint32_t Y, const uint4& q0,
+                                                const uint4& q1, const uint32_t (&rk)[20], const LaneConst& lc) {
+    return hidden_core(s_v[0], s_v[1], s_v[2], s_v[vs], s_v[vs + 1], s_v[vs + 2], s_v[2 * vs], s_v[2 * vs + 1],
+                       s_th, rs, Y, q0.x, {q0.y, q0.z}, {q0.w, q1.x}, {q1.y, q1.z}, rk, lc);
+}
+
+// The (rc.lo, Q0.h, Q0.l, Q1.h), (Q1.l, Q2.h, Q2.l, 0) words of cell `cell`
+// for hidden_cell, and (rc.lo, Qv.h, Qv.l, 0) for visible_cell.
+__device__ __forceinline__ void hidden_call_words(uint32_t cell, const uint32_t (&rk)[20], uint4& q0, uint4& q1) {
+    const Round0Cell rc = round0_cell(cell, rk[1]);
+    const Round1Call c0 = round1_call(rc.a, rk), c1 = round1_call(rc.a ^ 1u, rk), c2 = round1_call(rc.a ^ 2u, rk);
+    q0 = make_uint4(rc.b, c0.h, c0.l, c1.h);
+    q1 = make_uint4(c1.l, c2.h, c2.l, 0u);
+}
+__device__ __forceinline__ uint4 visible_call_words(uint32_t cell, const uint32_t (&rk)[20]) {
+    const Round0Cell rc = round0_cell(cell, rk[1]);
+    const Round1Call cv = round1_call(rc.a ^ kTagVis, rk);
+    return make_uint4(rc.b, cv.h, cv.l, 0u);
 }
 
 // Hidden half-step of one cell described by its records h0, h1, h2 and the
@@ -173,13 +187,13 @@ __device__ __forceinline__ U4 visible_core(uint32_t wo, uint32_t wu, uint32_t wl
             __ballot_sync(0xffffffffu, q.z < t10), __ballot_sync(0xffffffffu, q.w < t11)};
 }
 
-// Visible half-step of one cell; the four new spin words go to out[0],
-// out[1], out[row], out[row + 1].
+// Visible half-step of one cell with qv = visible_call_words(cell); the four
+// new spin words go to out[0], out[1], out[row], out[row + 1].
 __device__ __forceinline__ void visible_cell(uint32_t* out, int row, uint32_t wo, uint32_t wu,
                                              uint32_t wl, const uint32_t* s_tv, const Round1Sweep& rs,
-                                             uint32_t Y, const Round0Cell rc, const uint32_t (&rk)[20],
+                                             uint32_t Y, const uint4& qv, const uint32_t (&rk)[20],
                                              const LaneConst& lc) {
-    const U4 o = visible_core(wo, wu, wl, s_tv, rs, Y, rc.b, round1_call(rc.a ^ kTagVis, rk), rk, lc);
+    const U4 o = visible_core(wo, wu, wl, s_tv, rs, Y, qv.x, {qv.y, qv.z}, rk, lc);
     out[0] = o.x;
     out[1] = o.y;
     out[row] = o.z;

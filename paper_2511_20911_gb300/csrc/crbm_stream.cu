@@ -122,6 +122,7 @@ __global__ void __launch_bounds__(kStreamThreads, CRBM_STREAM_MIN_BLOCKS) k_stre
     __shared__ __align__(16) uint32_t s_th[kCanonTh];
     __shared__ uint32_t s_v[(2 * kTI + 1) * (2 * kTJ + 1)];
     __shared__ __align__(16) uint32_t s_h[kTI * kTJ * 32];
+    __shared__ uint4 s_q[kTI * kTJ][2];  // per tile cell: hidden_call_words
     const Geometry& g = a.g;
     const int W = g.W;
     const int w = blockIdx.y;
@@ -136,15 +137,21 @@ __global__ void __launch_bounds__(kStreamThreads, CRBM_STREAM_MIN_BLOCKS) k_stre
     const LaneConst lc = lane_const(lane, lane);
     const Round0Lane r0l = round0_lane(chain);
     const Round1Sweep rs = round1_sweep(r0l.hi ^ t ^ a.rk[0], a.rk);
+    const int ni = min(kTI, W - i0), nj = min(kTJ, W - j0);
+    // the warp-uniform Philox words of each cell, once per CTA instead of once per warp-cell
+    for (int x = threadIdx.x; x < kTI * kTJ; x += blockDim.x) {
+        const int li = x / kTJ, lj = x - li * kTJ;
+        if (li < ni && lj < nj)
+            hidden_call_words(static_cast<uint32_t>((i0 + li) * W + j0 + lj), a.rk, s_q[x][0], s_q[x][1]);
+    }
     __syncthreads();
     // warp = columns lj of the tile, cells walked down the column
-    const int ni = min(kTI, W - i0), nj = min(kTJ, W - j0);
     for (int lj = warp; lj < nj; lj += nwarp) {
         const uint32_t* v = s_v + 2 * lj;
         uint32_t* hp = s_h + lj * 32 + lane;
-        uint32_t cell = static_cast<uint32_t>(i0 * W + j0 + lj);
-        for (int li = 0; li < ni; ++li, v += 2 * VS, hp += kTJ * 32, cell += static_cast<uint32_t>(W))
-            *hp = hidden_cell(v, 0, VS, 2 * VS, 0, 1, 2, s_th, rs, r0l.lo, round0_cell(cell, a.rk[1]), a.rk, lc);
+        const uint4* q = s_q[lj];
+        for (int li = 0; li < ni; ++li, v += 2 * VS, hp += kTJ * 32, q += 2 * kTJ)
+            *hp = hidden_cell(v, VS, s_th, rs, r0l.lo, q[0], q[1], a.rk, lc);
     }
     __syncthreads();
     // tile rows of hidden words are contiguous runs of nj * 32 words in h
@@ -162,6 +169,7 @@ __global__ void __launch_bounds__(kStreamVisThreads, CRBM_STREAM_VIS_MIN_BLOCKS)
     __shared__ __align__(16) uint32_t s_tv[4 * 32 * 32];
     __shared__ __align__(16) uint32_t s_h[(kTI + 1) * (kTJ + 1) * 32];
     __shared__ uint32_t s_o[2 * kTI * 2 * kTJ];
+    __shared__ uint4 s_q[kTI * kTJ];  // per tile cell: visible_call_words
     const Geometry& g = a.g;
     const int L = g.L, W = g.W, N = g.N;
     const int w = blockIdx.y;
@@ -179,16 +187,19 @@ __global__ void __launch_bounds__(kStreamVisThreads, CRBM_STREAM_VIS_MIN_BLOCKS)
     const LaneConst lc = lane_const(lane, lane);
     const Round0Lane r0l = round0_lane(chain);
     const Round1Sweep rs = round1_sweep(r0l.hi ^ t ^ a.rk[0], a.rk);
-    __syncthreads();
     constexpr int VO = 2 * kTJ;
     const int ni = min(kTI, W - i0), nj = min(kTJ, W - j0);
+    for (int x = threadIdx.x; x < kTI * kTJ; x += blockDim.x) {
+        const int li = x / kTJ, lj = x - li * kTJ;
+        if (li < ni && lj < nj) s_q[x] = visible_call_words(static_cast<uint32_t>((i0 + li) * W + j0 + lj), a.rk);
+    }
+    __syncthreads();
     for (int lj = warp; lj < nj; lj += nwarp) {
         const uint32_t* ho = s_h + (HS + lj + 1) * 32 + lane;
         uint32_t* o = s_o + 2 * lj;
-        uint32_t cell = static_cast<uint32_t>(i0 * W + j0 + lj);
-        for (int li = 0; li < ni; ++li, ho += HS * 32, o += 2 * VO, cell += static_cast<uint32_t>(W))
-            visible_cell(o, VO, ho[0], ho[-HS * 32], ho[-32], s_tv, rs, r0l.lo, round0_cell(cell, a.rk[1]), a.rk,
-                         lc);
+        const uint4* q = s_q + lj;
+        for (int li = 0; li < ni; ++li, ho += HS * 32, o += 2 * VO, q += kTJ)
+            visible_cell(o, VO, ho[0], ho[-HS * 32], ho[-32], s_tv, rs, r0l.lo, *q, a.rk, lc);
     }
     __syncthreads();
     for (int x = threadIdx.x; x < 2 * kTI * VO; x += blockDim.x) {

@@ -11,76 +11,92 @@ namespace generic {
 
 using namespace dev;
 
-// Endpoint word of filter k of a cell (built on the host): bits 0..14 the
-// site of the first endpoint, bit 15 set when it is a real site (clear for a
-// zero-padded one, whose site bits are 0), bits 16..31 the same for the
-// second endpoint.
-__device__ __forceinline__ int endpoint_term(const uint32_t* s_v, uint32_t half, int lane, uint32_t flip) {
-    const int b = static_cast<int>(bit_of(s_v[half & 0x7FFFu], lane) ^ flip);
-    return (half & 0x8000u) ? 2 * b - 1 : 0;
+// Byte-addressed shared-memory access (records hold byte offsets from the
+// start of dynamic shared memory).
+__device__ __forceinline__ uint32_t lds32(const char* sm, uint32_t off) {
+    return *reinterpret_cast<const uint32_t*>(sm + off);
+}
+__device__ __forceinline__ uint32_t lds16(const char* sm, uint32_t off) {
+    return *reinterpret_cast<const uint16_t*>(sm + off);
 }
 
-// Generic hidden half-step: any filter list (<= 16 filters), odd L, open
-// boundaries.  m = c1 v1 + c2 v2 with a zero-padded endpoint contributing 0;
-// the threshold row is cls * 5 + (m + 2).
+// w | bit when q < t: a compare and a predicated OR.
+__device__ __forceinline__ uint32_t or_if_less(uint32_t w, uint32_t q, uint32_t t, uint32_t bit) {
+    asm("{\n\t.reg .pred p;\n\tsetp.lt.u32 p, %1, %2;\n\t@p or.b32 %0, %0, %3;\n\t}"
+        : "+r"(w)
+        : "r"(q), "r"(t), "r"(bit));
+    return w;
+}
+
+// Generic hidden half-step of one cell (Eq. 9): filter k of the cell reads
+// its two endpoint words (the zero word for a zero-padded endpoint, whose
+// pad pattern selects table rows that give it no weight), moves the lane's
+// bits to address bits 7 and 8 of its table rows [cls][pad][e1 + 2 e2]
+// (coefficient sign folded in by the host) and compares the threshold with
+// its Philox word.  The lane's decisions go to a 16-bit word, bit k =
+// filter k, in row `cell` of the hidden words.
 // Draws: Philox-4x32-10 of counter (cell, sweep, chain, tag) from the split
 // rounds (crbm_device.cuh): rs = round1_sweep of the lane's sweep word, Y the
 // lane's chain word, rk the round keys.
-__device__ __forceinline__ void hidden_cell_generic(const Geometry& g, const uint32_t* s_v,
-                                                    uint32_t* s_h, const uint32_t* s_tab,
-                                                    const uint32_t* __restrict__ ep, int cell,
-                                                    const Round1Sweep& rs, uint32_t Y, const uint32_t (&rk)[20],
-                                                    int lane, int col, const uint32_t (&sn)[2]) {
+__device__ __forceinline__ void hidden_cell_generic(const Geometry& g, char* sm, const uint4* __restrict__ rh,
+                                                    uint32_t hw_byte, int cell, const Round1Sweep& rs, uint32_t Y,
+                                                    const uint32_t (&rk)[20], uint32_t lm, uint32_t rot0,
+                                                    uint32_t rot1, uint32_t lb, int lane) {
     const Round0Cell rc = round0_cell(static_cast<uint32_t>(cell), rk[1]);
     const Round2Cell r2 = round2_cell(rs.hik ^ rc.b);
-    U4 q[4];
+    const uint4* r = rh + static_cast<size_t>(cell) * g.nb;
+    uint32_t h = 0u;
 #pragma unroll
-    for (int c = 0; c < 4; ++c)
-        if (c < g.n_calls) q[c] = philox_from_round2(Y, rs, r2, rc.a ^ static_cast<uint32_t>(c), rk);
-    const uint32_t* e = ep + static_cast<size_t>(cell) * g.nb;
+    for (int c = 0; c < 4; ++c) {  // call c draws for filters 4c .. 4c + 3
+        if (c < g.n_calls) {
+            const U4 q = philox_from_round2(Y, rs, r2, rc.a ^ static_cast<uint32_t>(c), rk);
 #pragma unroll
-    for (int k = 0; k < kMaxBonds; ++k) {
-        if (k < g.nb) {
-            const uint32_t ek = __ldg(e + k);
-            const int cls = g.cls[k];
-            const int m = 2 + endpoint_term(s_v, ek, lane, 0u) + endpoint_term(s_v, ek >> 16, lane, sn[cls]);
-            const uint32_t thr = s_tab[(cls * 5 + m) * 32 + col];
-            const uint32_t hw = __ballot_sync(0xffffffffu, pick(q[k >> 2], k & 3) < thr);
-            if (lane == 0) s_h[cell * g.nb + k] = hw;
+            for (int x = 0; x < 4; ++x) {
+                const int k = 4 * c + x;
+                if (k < g.nb) {
+                    const uint4 e = __ldg(r + k);
+                    const uint32_t a = rotr(lds32(sm, e.x) & lm, rot0), b = rotr(lds32(sm, e.y) & lm, rot1);
+                    h = or_if_less(h, pick(q, x), lds32(sm, e.z + (a | b | lb)), 1u << k);
+                }
+            }
         }
     }
+    *reinterpret_cast<uint16_t*>(sm + hw_byte + 64u * static_cast<uint32_t>(cell) + 2u * lane) =
+        static_cast<uint16_t>(h);
 }
 
-// Generic visible half-step: incidences of each spin from a CSR list.  Entry
-// bits 0..27 = hidden index (cell * nb + k), bit 30 = class, bit 31 = second
-// endpoint (coefficient s).
-__device__ __forceinline__ void visible_cell_generic(const Geometry& g, uint32_t* s_v,
-                                                     const uint32_t* s_h, const uint32_t* s_tab,
-                                                     const uint32_t* __restrict__ inc,
-                                                     const int32_t* __restrict__ inc_off,
-                                                     int cell, int i, int j, const Round1Sweep& rs, uint32_t Y,
-                                                     const uint32_t (&rk)[20], int lane, int col,
-                                                     const uint32_t (&sn)[2]) {
+// Generic visible half-step of one cell (Eq. 10): the cell's spins take
+// their filters from the hidden rows of at most four cells (own, above,
+// left, above-left).  Each row's 16-bit word h is expanded to
+// h | (h ^ f) << 16 (f: the filters whose class coefficient is -1 for this
+// lane), so that bit k is the term of filter k at its first endpoint and bit
+// 16 + k at its second; a spin's n_J, n_J' are then 2 popc(masked) - degree,
+// and its table row is the record's row of n = -degree plus
+// 2 (2 DJp + 1) popc_J + 2 popc_J'.
+__device__ __forceinline__ void visible_cell_generic(char* sm, const uint4* __restrict__ rv, int cell,
+                                                     const Round1Sweep& rs, uint32_t Y, const uint32_t (&rk)[20],
+                                                     uint32_t sflip, uint32_t stepJ, uint32_t lb, int lane) {
+    const uint4* r = rv + static_cast<size_t>(cell) * kGenVisRec;
     const Round0Cell rc = round0_cell(static_cast<uint32_t>(cell), rk[1]);
     const U4 q = philox_from_round2(Y, rs, round2_cell(rs.hik ^ rc.b), rc.a ^ kTagVis, rk);
-    const int nP = 2 * g.DJp + 1;
+    const uint4 src = __ldg(r);
+    const uint32_t l2 = 2u * static_cast<uint32_t>(lane);
+    uint32_t w[4];
+    w[0] = lds16(sm, src.x + l2);
+    w[1] = lds16(sm, src.y + l2);
+    w[2] = lds16(sm, src.z + l2);
+    w[3] = lds16(sm, src.w + l2);
 #pragma unroll
-    for (int w = 0; w < 4; ++w) {
-        const int R = 2 * i + (w >> 1), C = 2 * j + (w & 1);
-        if (R < g.L && C < g.L) {
-            const int s = R * g.L + C;
-            int n[2] = {0, 0};
-            const int e0 = __ldg(inc_off + s), e1 = __ldg(inc_off + s + 1);
-            for (int e = e0; e < e1; ++e) {
-                const uint32_t ent = __ldg(inc + e);
-                const int cls = (ent >> 30) & 1;
-                const uint32_t b = bit_of(s_h[ent & 0x0FFFFFFFu], lane) ^ ((ent >> 31) ? sn[cls] : 0u);
-                n[cls] += 2 * static_cast<int>(b) - 1;
-            }
-            const uint32_t thr = s_tab[(10 + (n[0] + g.DJ) * nP + (n[1] + g.DJp)) * 32 + col];
-            const uint32_t vw = __ballot_sync(0xffffffffu, pick(q, w) < thr);
-            if (lane == 0) s_v[s] = vw;
-        }
+    for (int s = 0; s < 4; ++s) w[s] |= (w[s] ^ sflip) << 16;
+    const uint4 tb = __ldg(r + 9), so = __ldg(r + 10);
+#pragma unroll
+    for (int x = 0; x < 4; ++x) {
+        const uint4 mj = __ldg(r + 1 + 2 * x), mp = __ldg(r + 2 + 2 * x);
+        const uint32_t cj = __popc(w[0] & mj.x) + __popc(w[1] & mj.y) + __popc(w[2] & mj.z) + __popc(w[3] & mj.w);
+        const uint32_t cp = __popc(w[0] & mp.x) + __popc(w[1] & mp.y) + __popc(w[2] & mp.z) + __popc(w[3] & mp.w);
+        const uint32_t row = (x == 0 ? tb.x : x == 1 ? tb.y : x == 2 ? tb.z : tb.w) + cj * stepJ + (cp << 8);
+        const uint32_t vw = __ballot_sync(0xffffffffu, pick(q, x) < lds32(sm, row + lb));
+        *reinterpret_cast<uint32_t*>(sm + (x == 0 ? so.x : x == 1 ? so.y : x == 2 ? so.z : so.w)) = vw;
     }
 }
 
@@ -115,27 +131,39 @@ __device__ __forceinline__ void count_cell(const Geometry& g, const uint32_t* s_
 __device__ __forceinline__ void sweep_generic_body(const SweepArgs& a, int word) {
     extern __shared__ __align__(16) uint32_t smem[];
     const Geometry& g = a.g;
+    const GenericSmem gs = generic_smem(g);
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nwarp = blockDim.x >> 5;
+    char* sm = reinterpret_cast<char*>(smem);
     int64_t* s_acc = reinterpret_cast<int64_t*>(smem);  // [kNSum][32] running sums
-    uint32_t* s_tab = smem + kAccWords;
-    uint32_t* s_v = s_tab + g.nTab * 32;
-    uint32_t* s_h = s_v + g.N;
-    int* s_cnt = reinterpret_cast<int*>(s_h + g.n_cells * g.nb);  // [3][32]
-    int* s_seg = s_cnt + 96;                                       // [33]
-    uint32_t* s_segmask = reinterpret_cast<uint32_t*>(s_seg + 33); // [32]
-    int* s_sob = reinterpret_cast<int*>(s_segmask + 32);          // [32] slot of each rung
+    uint32_t* s_tab = smem + gs.tab;
+    uint32_t* s_v = smem + gs.v;
+    int* s_cnt = reinterpret_cast<int*>(smem + gs.cnt);            // [3][32]
+    int* s_seg = reinterpret_cast<int*>(smem + gs.seg);            // [33]
+    uint32_t* s_segmask = smem + gs.segmask;                       // [32]
+    int* s_sob = reinterpret_cast<int*>(smem + gs.sob);            // [32] slot of each rung
     int* s_bos = s_sob + 32;                                        // [32] rung of each slot
+    const int nTg = kGenHid + g.nTv;
+    const uint4* rh = a.crec;                                           // [n_cells][nb] hidden records
+    const uint4* rv = a.crec + static_cast<size_t>(g.n_cells) * g.nb;  // [n_cells][kGenVisRec]
+    const uint32_t hw_byte = 4u * static_cast<uint32_t>(gs.hw);
 
-    const uint32_t* gtab = a.tab + static_cast<size_t>(word) * g.nTab * 32;
-    for (int x = threadIdx.x; x < g.nTab * 32; x += blockDim.x) s_tab[x] = gtab[x];
+    const uint32_t* gtab = a.tab + static_cast<size_t>(word) * nTg * 32;
+    for (int x = threadIdx.x; x < nTg * 32; x += blockDim.x) s_tab[x] = gtab[x];
     uint32_t* gv = a.v + static_cast<size_t>(word) * g.N;
     for (int x = threadIdx.x; x < g.N; x += blockDim.x) s_v[x] = gv[x];
+    if (threadIdx.x < 2) s_v[g.N + threadIdx.x] = 0u;                  // zero word, scratch word
+    if (threadIdx.x < 16) smem[gs.zrow + threadIdx.x] = 0u;            // zero hidden row
     for (int x = threadIdx.x; x < 96; x += blockDim.x) s_cnt[x] = 0;
     if (a.sq_every > 0) {
         for (int x = threadIdx.x; x < 33; x += blockDim.x) s_seg[x] = a.seg[word * 33 + x];
         for (int x = threadIdx.x; x < 32; x += blockDim.x) s_segmask[x] = a.segmask[word * 32 + x];
     }
     const uint32_t sn[2] = {bit_of(a.sneg[2 * word], lane), bit_of(a.sneg[2 * word + 1], lane)};
+    uint32_t sflip = 0u;  // filters whose class coefficient is -1 for this lane
+    for (int k = 0; k < g.nb; ++k) sflip |= (g.cls[k] ? sn[1] : sn[0]) << k;
+    const uint32_t lm = 1u << lane;
+    const uint32_t rot0 = static_cast<uint32_t>(lane - 7) & 31u, rot1 = static_cast<uint32_t>(lane - 8) & 31u;
+    const uint32_t stepJ = 256u * static_cast<uint32_t>(2 * g.DJp + 1);
     const uint32_t chain = static_cast<uint32_t>(word) * 32u + lane;
     if (warp == 0) {  // replica permutation (identity without tempering)
         const int sob = a.swap_every > 0 ? a.sob[word * 32 + lane] : lane;
@@ -143,7 +171,7 @@ __device__ __forceinline__ void sweep_generic_body(const SweepArgs& a, int word)
         s_bos[sob] = lane;
     }
     __syncthreads();
-    int col = s_bos[lane];  // threshold column: the rung this slot holds
+    uint32_t lb = 4u * static_cast<uint32_t>(s_bos[lane]);  // threshold column: the rung this slot holds
     const bool measuring = a.measure_every > 0;
     if (warp == 0 && measuring) {
         for (int x = 0; x < kNSum; ++x) s_acc[x * 32 + lane] = a.sums[static_cast<size_t>(chain) * kNSum + x];
@@ -159,26 +187,16 @@ __device__ __forceinline__ void sweep_generic_body(const SweepArgs& a, int word)
         const uint32_t t = t0 + static_cast<uint32_t>(it);
         const Round1Sweep rs = round1_sweep(r0l.hi ^ t ^ a.rk[0], a.rk);
         for (int cell = warp; cell < g.n_cells; cell += nwarp)
-            hidden_cell_generic(g, s_v, s_h, s_tab, a.gep, cell, rs, r0l.lo, a.rk, lane, col, sn);
+            hidden_cell_generic(g, sm, rh, hw_byte, cell, rs, r0l.lo, a.rk, lm, rot0, rot1, lb, lane);
         __syncthreads();
-        int i = i_first, j = j_first;
-        for (int cell = warp; cell < g.n_cells; cell += nwarp) {
-            visible_cell_generic(g, s_v, s_h, s_tab, a.inc, a.inc_off, cell, i, j, rs, r0l.lo, a.rk, lane, col,
-                                 sn);
-            i += di;
-            j += dj;
-            if (j >= g.W) {
-                j -= g.W;
-                ++i;
-            }
-        }
+        for (int cell = warp; cell < g.n_cells; cell += nwarp)
+            visible_cell_generic(sm, rv, cell, rs, r0l.lo, a.rk, sflip, stepJ, lb, lane);
         __syncthreads();
         const bool do_meas = measuring && (t + 1u) % static_cast<uint32_t>(a.measure_every) == 0u;
         const bool do_swap = a.swap_every > 0 && (t + 1u) % static_cast<uint32_t>(a.swap_every) == 0u;
         if (do_meas || do_swap) {
             int anti0 = 0, anti1 = 0, pos = 0;
-            i = i_first;
-            j = j_first;
+            int i = i_first, j = j_first;
             for (int cell = warp; cell < g.n_cells; cell += nwarp) {
                 count_cell(g, s_v, a.gep, cell, i, j, lane, anti0, anti1, pos);
                 i += di;
@@ -195,7 +213,7 @@ __device__ __forceinline__ void sweep_generic_body(const SweepArgs& a, int word)
             if (warp == 0) post_sweep_warp0(a, s_cnt, s_sob, s_bos, lane, word, t, do_meas, do_swap, meas, s_acc);
             if (do_meas) ++meas;
             __syncthreads();
-            if (do_swap) col = s_bos[lane];
+            if (do_swap) lb = 4u * static_cast<uint32_t>(s_bos[lane]);
         }
         if (a.sq_every > 0 && (t + 1u) % static_cast<uint32_t>(a.sq_every) == 0u) {
             accumulate_correlations(a, s_v, s_seg, s_segmask, warp, nwarp, lane);

@@ -422,7 +422,9 @@ int crbm_create(crbm_ctx** out, const crbm_params* p) {
         point_tables(g, ctx->beta[i], ctx->q[0][i], ctx->q[1][i], ctx->q[2][i],
                      &ctx->tables[static_cast<size_t>(i) * g.nTab], &sgn[2 * i]);
     const int nw = ctx->n_words, npad = nw * 32;
-    std::vector<uint32_t> tab(static_cast<size_t>(nw) * g.nTab * 32);
+    // generic lane-expanded tables (layout in crbm_internal.h); canonical contexts use ctab
+    const int nTg = g.canonical ? 0 : kGenHid + g.nTv;
+    std::vector<uint32_t> tab(static_cast<size_t>(nw) * nTg * 32);
     std::vector<uint32_t> sneg(2 * static_cast<size_t>(nw), 0u);
     std::vector<int32_t> seg(33 * static_cast<size_t>(nw), 0);
     std::vector<uint32_t> segmask(32 * static_cast<size_t>(nw), 0u);
@@ -432,8 +434,18 @@ int crbm_create(crbm_ctx** out, const crbm_params* p) {
             const int c = w * 32 + l;
             const bool real = c < p->n_chains;
             const int pp = real ? ctx->chain_param[c] : ctx->chain_param[0];
-            for (int e = 0; e < g.nTab; ++e)
-                tab[(static_cast<size_t>(w) * g.nTab + e) * 32 + l] = ctx->tables[static_cast<size_t>(pp) * g.nTab + e];
+            if (nTg > 0) {
+                const uint32_t* T = &ctx->tables[static_cast<size_t>(pp) * g.nTab];
+                uint32_t* out = &tab[static_cast<size_t>(w) * nTg * 32 + l];
+                for (int cls = 0; cls < 2; ++cls)
+                    for (int pad = 0; pad < 4; ++pad)
+                        for (int idx = 0; idx < 4; ++idx) {
+                            const int e1 = idx & 1, e2 = idx >> 1;
+                            const int m = ((pad & 1) ? 0 : 2 * e1 - 1) + ((pad & 2) ? 0 : sgn[2 * pp + cls] * (2 * e2 - 1));
+                            out[((cls * 4 + pad) * 4 + idx) * 32] = T[cls * 5 + m + 2];
+                        }
+                for (int e = 0; e < g.nTv; ++e) out[(kGenHid + e) * 32] = T[10 + e];
+            }
             if (sgn[2 * pp] < 0) sneg[2 * w] |= 1u << l;
             if (sgn[2 * pp + 1] < 0) sneg[2 * w + 1] |= 1u << l;
             if (!real) continue;
@@ -512,6 +524,69 @@ int crbm_create(crbm_ctx** out, const crbm_params* p) {
                     ql[2],          0u,             0u,                    0u};
                 std::copy(rec, rec + kCellRec * 4, o);
             }
+    }
+    // Per-cell records of the generic SMEM sweep (layout in crbm_internal.h).
+    if (!g.canonical && ctx->layout == CRBM_LAYOUT_SMEM) {
+        const GenericSmem gs = generic_smem(g);
+        const int W = g.W, nb = g.nb, nP = 2 * g.DJp + 1;
+        const size_t nh = static_cast<size_t>(g.n_cells) * nb;
+        crec.assign((nh + static_cast<size_t>(g.n_cells) * kGenVisRec) * 4, 0u);
+        auto site_off = [&](int s) { return 4u * static_cast<uint32_t>(s >= 0 ? gs.v + s : gs.zero); };
+        for (int c = 0; c < g.n_cells; ++c)
+            for (int k = 0; k < nb; ++k) {
+                const int i = c / W, j = c % W;
+                const int s1 = site_index(g, i, j, g.r1[k], g.c1[k]), s2 = site_index(g, i, j, g.r2[k], g.c2[k]);
+                const int pad = (s1 < 0 ? 1 : 0) | (s2 < 0 ? 2 : 0);
+                uint32_t* o = &crec[(static_cast<size_t>(c) * nb + k) * 4];
+                o[0] = site_off(s1);
+                o[1] = site_off(s2);
+                o[2] = 4u * static_cast<uint32_t>(gs.tab + static_cast<size_t>((g.cls[k] * 4 + pad) * 4) * 32);
+            }
+        // incidences (cell, filter, endpoint) of every spin
+        std::vector<std::vector<int>> incid(g.N);
+        for (int c = 0; c < g.n_cells; ++c)
+            for (int k = 0; k < nb; ++k) {
+                const int i = c / W, j = c % W;
+                const int s1 = site_index(g, i, j, g.r1[k], g.c1[k]), s2 = site_index(g, i, j, g.r2[k], g.c2[k]);
+                if (s1 >= 0) incid[s1].push_back((c * kMaxBonds + k) * 2);
+                if (s2 >= 0) incid[s2].push_back((c * kMaxBonds + k) * 2 + 1);
+            }
+        for (int c = 0; c < g.n_cells; ++c) {
+            const int i = c / W, j = c % W;
+            const int iu = i > 0 ? i - 1 : (g.periodic ? W - 1 : -1);
+            const int jl = j > 0 ? j - 1 : (g.periodic ? W - 1 : -1);
+            const int src[4] = {c, iu >= 0 ? iu * W + j : -1, jl >= 0 ? i * W + jl : -1,
+                                iu >= 0 && jl >= 0 ? iu * W + jl : -1};
+            uint32_t* o = &crec[(nh + static_cast<size_t>(c) * kGenVisRec) * 4];
+            for (int q = 0; q < 4; ++q)
+                o[q] = 4u * static_cast<uint32_t>(src[q] >= 0 ? gs.hw + static_cast<size_t>(src[q]) * 16 : gs.zrow);
+            for (int x = 0; x < 4; ++x) {
+                const int R = 2 * i + (x >> 1), C = 2 * j + (x & 1);
+                uint32_t* mj = o + 4 * (1 + 2 * x);
+                uint32_t* mp = o + 4 * (2 + 2 * x);
+                int deg[2] = {0, 0};
+                if (R < g.L && C < g.L) {
+                    const int s = R * g.L + C;
+                    for (const int e : incid[s]) {
+                        const int cc = e / (2 * kMaxBonds), k = (e / 2) % kMaxBonds, second = e & 1;
+                        int q = 0;
+                        while (q < 4 && src[q] != cc) ++q;
+                        if (q == 4) {
+                            delete ctx;
+                            return fail(nullptr, CRBM_EINVAL, "internal: incidence outside the cell's windows");
+                        }
+                        const int cls = g.cls[k];
+                        (cls ? mp : mj)[q] |= 1u << (k + 16 * second);
+                        ++deg[cls];
+                    }
+                    o[4 * 10 + x] = site_off(s);
+                } else {
+                    o[4 * 10 + x] = 4u * static_cast<uint32_t>(gs.zero + 1);
+                }
+                o[4 * 9 + x] = 4u * static_cast<uint32_t>(
+                    gs.tab + static_cast<size_t>(kGenHid + (g.DJ - deg[0]) * nP + (g.DJp - deg[1])) * 32);
+            }
+        }
     }
     // Device state.
     cudaGetDevice(&ctx->device);

@@ -87,12 +87,59 @@ __host__ __device__ inline size_t canon_smem_rec_offset(const Geometry& g) {
            ~static_cast<size_t>(3);
 }
 
+// Generic SMEM-resident sweep (any filter list, odd L, open boundaries).
+// Lane-expanded tables per packed word, [kGenHid + nTv][32]: the hidden rows
+// [cls][pad][e1 + 2 e2] (pad bit 0: first endpoint zero-padded, bit 1:
+// second), indexed by the raw endpoint bits with the coefficient sign folded
+// in, then the visible rows [(n_J + DJ) (2 DJp + 1) + n_J' + DJp].
+constexpr int kGenHid = 2 * 4 * 4;
+// Host-built records of the generic sweep, byte offsets from the start of
+// dynamic shared memory:
+//   hidden, per (cell, filter k): {first endpoint word, second endpoint word
+//     (the zero word for a padded endpoint), table row of (cls, pad), 0};
+//   visible, kGenVisRec per cell: [0] the 16-bit hidden rows of the four
+//     cells whose windows can hold the cell's spins (own, above, left,
+//     above-left; a zero row where there is none); then per owned spin
+//     x = 2 r + c: [1 + 2x] J masks, [2 + 2x] J' masks over the four rows'
+//     expanded words (bit k: filter k with the spin as first endpoint, bit
+//     16 + k: as second endpoint); [9] the table row of n_J = n_J' = -deg
+//     of each spin; [10] each spin's word (a scratch word for a position past
+//     the lattice edge).
+constexpr int kGenVisRec = 11;
+// Word offsets of the generic sweep's dynamic shared memory.
+struct GenericSmem {
+    size_t tab;      // [kGenHid + nTv][32] thresholds
+    size_t v;        // [N] spins
+    size_t zero;     // one zero word (padded endpoints), then one scratch word
+    size_t hw;       // [n_cells][32] 16-bit per-lane hidden words (bit k: filter k)
+    size_t zrow;     // [32] 16-bit zeros
+    size_t cnt;      // [3][32] measurement counters
+    size_t seg;      // [33]
+    size_t segmask;  // [32]
+    size_t sob;      // [32] replica slot of each rung, then [32] rung of each slot
+    size_t total;
+};
+__host__ __device__ inline GenericSmem generic_smem(const Geometry& g) {
+    GenericSmem s;
+    s.tab = static_cast<size_t>(kAccWords);
+    s.v = s.tab + static_cast<size_t>(kGenHid + g.nTv) * 32;
+    s.zero = s.v + g.N;
+    s.hw = (s.zero + 2 + 3) & ~static_cast<size_t>(3);
+    s.zrow = s.hw + static_cast<size_t>(g.n_cells) * 16;
+    s.cnt = s.zrow + 16;
+    s.seg = s.cnt + 96;
+    s.segmask = s.seg + 33;
+    s.sob = s.segmask + 32;
+    s.total = s.sob + 64;
+    return s;
+}
+
 // Device buffers of one context (all owned by the context).
 struct DeviceState {
     uint32_t* v = nullptr;        // [n_words][N] packed spins, bit l = chain 32w + l
-    uint32_t* tab = nullptr;      // [n_words][nTab][32] lane-expanded thresholds
+    uint32_t* tab = nullptr;      // generic: [n_words][kGenHid + nTv][32] lane-expanded thresholds
     uint32_t* ctab = nullptr;     // [n_words][kCanonTab] canonical fast-path tables
-    uint4* crec = nullptr;        // [n_cells][kCellRec] canonical per-cell records (SMEM layout)
+    uint4* crec = nullptr;        // SMEM layout: canonical [n_cells][kCellRec] or generic per-cell records
     uint32_t* sneg = nullptr;     // [n_words][2] lanes whose class coefficient s = -1
     uint32_t* inc = nullptr;      // generic incidences, CSR entries (see kernels), then the endpoint words
     int32_t* inc_off = nullptr;   // [N + 1] CSR offsets

@@ -80,10 +80,7 @@ cudaError_t launch_philox(const uint32_t* in, uint32_t* out, int n, cudaStream_t
     return cudaGetLastError();
 }
 
-size_t smem_bytes_generic(const Geometry& g) {
-    return sizeof(uint32_t) * (static_cast<size_t>(kAccWords) + static_cast<size_t>(g.nTab) * 32 + g.N +
-                               static_cast<size_t>(g.n_cells) * g.nb + 96 + 33 + 32 + 64);
-}
+size_t smem_bytes_generic(const Geometry& g) { return sizeof(uint32_t) * generic_smem(g).total; }
 
 cudaError_t launch_init(const Geometry& g, uint32_t* v, int n_words, uint32_t key0, uint32_t key1,
                         cudaStream_t st) {

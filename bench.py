@@ -44,8 +44,8 @@ CALLS_PER_CELL = 4          # 3 hidden calls (10 filters) + 1 visible call (4 sp
 # launch of k_sweep_canon_persistent (2000 sweeps of the L=18 grid), and one
 # streamed sweep of the L=384 lattice (k_stream_hidden + k_stream_visible).
 MEASURED_TRAFFIC = {
-    "grid": (8.73e6 + 0.61e6, "per launch; profiles/k_sweep_canon_persistent_L18_grid.md"),
-    "stream": (56.74e6 + 392.03e6 + 454.65e6 + 48.59e6, "per sweep (two launches); profiles/k_stream_L384.md"),
+    "grid": (8.62e6 + 0.62e6, "per launch; profiles/k_sweep_canon_persistent_L18_grid.md"),
+    "stream": (56.87e6 + 392.34e6 + 454.60e6 + 48.92e6, "per sweep (two launches); profiles/k_stream_L384.md"),
 }
 
 

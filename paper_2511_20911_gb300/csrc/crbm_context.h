@@ -11,7 +11,6 @@
 struct crbm_ctx {
     crbm::Geometry g{};
     int n_chains = 0, n_words = 0, n_params = 0;
-    size_t n_inc = 0;       // CSR incidence entries (the generic endpoint words follow them)
     int layout = CRBM_LAYOUT_SMEM;
     int warps = 8;
     uint64_t seed = 0;

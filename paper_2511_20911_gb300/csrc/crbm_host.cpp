@@ -88,9 +88,8 @@ int site_index(const Geometry& g, int i, int j, int r, int c) {
     return R * g.L + C;
 }
 
-// Geometry, visible field ranges and the generic incidence list.
-int build_geometry(crbm_ctx* ctx, const crbm_params* p, std::vector<uint32_t>& inc,
-                   std::vector<int32_t>& inc_off) {
+// Geometry, visible field ranges and the generic endpoint words.
+int build_geometry(crbm_ctx* ctx, const crbm_params* p, std::vector<uint32_t>& ep) {
     Geometry& g = ctx->g;
     const crbm_bond* bonds = p->bonds ? p->bonds : kSSFilters;
     const int nb = p->bonds ? p->n_bonds : 10;
@@ -114,24 +113,16 @@ int build_geometry(crbm_ctx* ctx, const crbm_params* p, std::vector<uint32_t>& i
         same = std::memcmp(&bonds[k], &kSSFilters[k], sizeof(crbm_bond)) == 0;
     g.canonical = (same && g.periodic && (g.L % 2 == 0)) ? 1 : 0;
 
-    std::vector<int> deg(2 * static_cast<size_t>(g.N), 0);
-    std::vector<std::vector<uint32_t>> per_site(g.N);
+    std::vector<int> deg(2 * static_cast<size_t>(g.N), 0);  // filters per (class, site)
     g.n_real_bonds[0] = g.n_real_bonds[1] = 0;
     for (int i = 0; i < g.W; ++i)
         for (int j = 0; j < g.W; ++j)
             for (int k = 0; k < nb; ++k) {
                 const int s1 = site_index(g, i, j, g.r1[k], g.c1[k]);
                 const int s2 = site_index(g, i, j, g.r2[k], g.c2[k]);
-                const uint32_t hid = static_cast<uint32_t>((i * g.W + j) * nb + k);
-                const uint32_t cls = g.cls[k];
-                if (s1 >= 0) {
-                    deg[cls * g.N + s1]++;
-                    per_site[s1].push_back(hid | (cls << 30));
-                }
-                if (s2 >= 0) {
-                    deg[cls * g.N + s2]++;
-                    per_site[s2].push_back(hid | (cls << 30) | (1u << 31));
-                }
+                const int cls = g.cls[k];
+                if (s1 >= 0) deg[cls * g.N + s1]++;
+                if (s2 >= 0) deg[cls * g.N + s2]++;
                 if (s1 >= 0 && s2 >= 0) g.n_real_bonds[cls]++;
             }
     g.DJ = g.DJp = 0;
@@ -143,23 +134,17 @@ int build_geometry(crbm_ctx* ctx, const crbm_params* p, std::vector<uint32_t>& i
     g.nTab = 10 + g.nTv;
     if (g.canonical && (g.DJ != 4 || g.DJp != 1))
         return fail(nullptr, CRBM_EINVAL, "internal: SS filters must give 4 J and 1 J' filter per spin");
-    inc.clear();
-    inc_off.assign(g.N + 1, 0);
-    for (int s = 0; s < g.N; ++s) {
-        inc_off[s] = static_cast<int32_t>(inc.size());
-        inc.insert(inc.end(), per_site[s].begin(), per_site[s].end());
-    }
-    inc_off[g.N] = static_cast<int32_t>(inc.size());
-    // endpoint words of the generic hidden half-step, after the CSR entries:
-    // per endpoint 15 bits of site and a real-site flag (a padded one is 0);
-    // generic contexts are SMEM-resident (L <= CRBM_SMEM_MAX_L), so sites fit
+    // endpoint words of the generic measurement, [n_cells][nb]: per endpoint
+    // 15 bits of site and a real-site flag (a padded one is 0); generic
+    // contexts are SMEM-resident (L <= CRBM_SMEM_MAX_L), so sites fit
     auto endpoint = [&](int s) { return s >= 0 ? (static_cast<uint32_t>(s) | 0x8000u) : 0u; };
+    ep.clear();
     if (!g.canonical && g.N <= 0x7FFF) {
         for (int i = 0; i < g.W; ++i)
             for (int j = 0; j < g.W; ++j)
                 for (int k = 0; k < nb; ++k)
-                    inc.push_back(endpoint(site_index(g, i, j, g.r1[k], g.c1[k])) |
-                                  (endpoint(site_index(g, i, j, g.r2[k], g.c2[k])) << 16));
+                    ep.push_back(endpoint(site_index(g, i, j, g.r1[k], g.c1[k])) |
+                                 (endpoint(site_index(g, i, j, g.r2[k], g.c2[k])) << 16));
     }
     return CRBM_OK;
 }
@@ -193,7 +178,7 @@ int dalloc(crbm_ctx* ctx, T*& ptr, size_t count) {
 }
 
 void free_device(DeviceState& d) {
-    void* ptrs[] = {d.v, d.tab, d.ctab, d.crec, d.sneg, d.inc, d.inc_off, d.sums, d.series, d.corr,
+    void* ptrs[] = {d.v, d.tab, d.ctab, d.crec, d.sneg, d.gep, d.sums, d.series, d.corr,
                     d.seg, d.segmask, d.spins8, d.h, d.cnt, d.sob, d.swap_tab, d.swap_off,
                     d.swap_len, d.wq, d.chain_bh, d.chain_q, d.sched};
     for (void* p : ptrs)
@@ -229,9 +214,7 @@ SweepArgs fill_sweep_args(const crbm_ctx* ctx, int chunk) {
     a.ctab = ctx->d.ctab;
     a.crec = ctx->d.crec;
     a.sneg = ctx->d.sneg;
-    a.inc = ctx->d.inc;
-    a.inc_off = ctx->d.inc_off;
-    a.gep = ctx->d.inc + ctx->n_inc;
+    a.gep = ctx->d.gep;
     a.sums = ctx->d.sums;
     a.series = ctx->d.series;
     a.h = ctx->d.h;
@@ -279,10 +262,8 @@ int crbm_create(crbm_ctx** out, const crbm_params* p) {
         return fail(nullptr, CRBM_EINVAL, "unknown layout");
     crbm_ctx* ctx = new (std::nothrow) crbm_ctx();
     if (!ctx) return fail(nullptr, CRBM_ENOMEM, "host allocation failed");
-    std::vector<uint32_t> inc;
-    std::vector<int32_t> inc_off;
-    int rc = build_geometry(ctx, p, inc, inc_off);
-    if (rc == CRBM_OK) ctx->n_inc = static_cast<size_t>(inc_off.back());
+    std::vector<uint32_t> gep;
+    int rc = build_geometry(ctx, p, gep);
     if (rc) {
         delete ctx;
         return rc;
@@ -594,8 +575,7 @@ int crbm_create(crbm_ctx** out, const crbm_params* p) {
     const size_t N = static_cast<size_t>(g.N);
     if ((rc = dalloc(ctx, d.v, nw * N)) || (rc = dalloc(ctx, d.tab, tab.size())) ||
         (rc = dalloc(ctx, d.ctab, ctab.size())) || (rc = dalloc(ctx, d.crec, crec.size() / 4)) ||
-        (rc = dalloc(ctx, d.sneg, sneg.size())) || (rc = dalloc(ctx, d.inc, inc.size())) ||
-        (rc = dalloc(ctx, d.inc_off, inc_off.size())) ||
+        (rc = dalloc(ctx, d.sneg, sneg.size())) || (rc = dalloc(ctx, d.gep, gep.size())) ||
         (rc = dalloc(ctx, d.sums, static_cast<size_t>(npad) * kNSum)) ||
         (rc = dalloc(ctx, d.series, static_cast<size_t>(p->series_len) * npad * 3)) ||
         (rc = dalloc(ctx, d.corr, p->sq_every > 0 ? static_cast<size_t>(p->n_params) * N : 1)) ||
@@ -621,8 +601,7 @@ int crbm_create(crbm_ctx** out, const crbm_params* p) {
     h2d(d.ctab, ctab.data(), ctab.size() * 4);
     h2d(d.crec, crec.data(), crec.size() * 4);
     h2d(d.sneg, sneg.data(), sneg.size() * 4);
-    h2d(d.inc, inc.data(), inc.size() * 4);
-    h2d(d.inc_off, inc_off.data(), inc_off.size() * 4);
+    h2d(d.gep, gep.data(), gep.size() * 4);
     h2d(d.seg, seg.data(), seg.size() * 4);
     h2d(d.segmask, segmask.data(), segmask.size() * 4);
     h2d(d.swap_tab, swap_tab.data(), swap_tab.size() * 4);

@@ -141,8 +141,7 @@ struct DeviceState {
     uint32_t* ctab = nullptr;     // [n_words][kCanonTab] canonical fast-path tables
     uint4* crec = nullptr;        // SMEM layout: canonical [n_cells][kCellRec] or generic per-cell records
     uint32_t* sneg = nullptr;     // [n_words][2] lanes whose class coefficient s = -1
-    uint32_t* inc = nullptr;      // generic incidences, CSR entries (see kernels), then the endpoint words
-    int32_t* inc_off = nullptr;   // [N + 1] CSR offsets
+    uint32_t* gep = nullptr;      // generic: [n_cells][nb] filter endpoint words (measurement)
     int64_t* sums = nullptr;      // [n_words * 32][kNSum]
     int32_t* series = nullptr;    // [series_len][n_words * 32][3]
     int64_t* corr = nullptr;      // [n_params][N] correlation sums
@@ -168,8 +167,6 @@ struct SweepArgs {
     const uint32_t* ctab;
     const uint4* crec;
     const uint32_t* sneg;
-    const uint32_t* inc;
-    const int32_t* inc_off;
     const uint32_t* gep;  // generic path: [n_cells][nb] filter endpoint words (see crbm_generic_body.cuh)
     int64_t* sums;
     int32_t* series;

@@ -90,7 +90,7 @@ def test_batch_cluster_split_matches_individual_sweeps(cluster, monkeypatch):
     twins = [make(s) for s in specs]
     batch = crbm.Batch(batched)
     assert batch.cluster == cluster
-    for n in (7, 13, 25):
+    for n in (7, 13, 25, 120):
         batch.sweep(n)
         for t in twins:
             t.sweep(n)

@@ -95,3 +95,29 @@ def test_tempering_validation():
         with pytest.raises(crbm.CrbmError) as e:
             crbm.Sampler(8, swap_every=2, **kw)
         assert e.value.code == code, kw
+
+
+@pytest.mark.slow
+def test_full_tempering_batch_sampled_ladders(orc):
+    """The mixed-size tempering batch at full size (L in {6,9,12,18,24,48} x 8
+    ladders of 32 rungs, one graph-captured batch launch with the largest
+    words split over thread-block clusters, as the benchmark runs it): the
+    first two ladders of every size checked against the oracle's replica
+    exchange, spins per slot, rung permutation and per-rung sums."""
+    from paper_2511_20911_gb300 import workloads
+    specs = [dict(sp, measure_every=10) for sp in workloads.tempering_batch_workload()]
+    samplers = [crbm.Sampler(**sp) for sp in specs]
+    batch = crbm.Batch(samplers)
+    assert batch.cluster > 1
+    n = 30
+    batch.sweep(n)
+    for sp, s in zip(specs, samplers):
+        L, ids = sp["L"], np.arange(64, dtype=np.uint32)
+        cp = np.asarray(sp["chain_param"], np.int32)[:64]
+        spins = orc.init_spins(L, ids, sp["seed"])
+        sob = np.tile(np.arange(32, dtype=np.int32), (2, 1))
+        sums, _ = orc.run_pt(L, sp["params"], cp, spins, sob, sp["seed"], 0, n, 10, sp["swap_every"])
+        assert np.array_equal(s.get_spins()[:64], spins), L
+        assert np.array_equal(s.permutation().reshape(-1, 32)[:2], sob), L
+        assert np.array_equal(s.observables()[:64], sums), L
+    batch.close()

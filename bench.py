@@ -39,6 +39,7 @@ SM_COUNT, SM_MAX_MHZ = 152, 2070.0
 IMUL_LANES_PER_SM_CLK = 64
 MUL_OPS_PER_CALL = 40
 CALLS_PER_CELL = 4          # 3 hidden calls (10 filters) + 1 visible call (4 spins) per cell
+CALLS_PER_CELL_PAPER = 2    # paper precision: 16-bit uniforms, two per Philox word (14 of 16 used)
 # DRAM bytes (read + write) of the timed unit, from one ncu capture of the
 # kernels as they stand (commands in the named profiles/ summaries): one bench
 # launch of k_sweep_canon_persistent (2000 sweeps of the L=18 grid), and one
@@ -46,6 +47,7 @@ CALLS_PER_CELL = 4          # 3 hidden calls (10 filters) + 1 visible call (4 sp
 MEASURED_TRAFFIC = {
     "grid": (8.62e6 + 0.62e6, "per launch; profiles/k_sweep_canon_persistent_L18_grid.md"),
     "stream": (56.87e6 + 392.34e6 + 454.60e6 + 48.92e6, "per sweep (two launches); profiles/k_stream_L384.md"),
+    "grid_paper": (None, "per launch; not captured yet"),
 }
 
 
@@ -60,7 +62,13 @@ def parse():
     ap.add_argument("--measure-every", type=int, default=10)
     ap.add_argument("--cpu-seconds", type=float, default=8.0)
     ap.add_argument("--no-cpu-baseline", action="store_true")
-    return ap.parse_args()
+    ap.add_argument("--precision", default="exact", choices=["exact", "paper"],
+                    help="paper: the FPGA's 10-bit weights, 16-bit sigmoid table and 16-bit uniforms "
+                         "(L=18 grid only)")
+    args = ap.parse_args()
+    if args.precision == "paper" and args.workload != "grid":
+        ap.error("--precision paper runs the grid workload (SMEM layout) only")
+    return args
 
 
 def dist_setup(args):
@@ -150,7 +158,7 @@ def workload_config(name, rank):
 DEFAULT_SWEEPS = {"grid": 2000, "stream": 20, "batch": 500, "proposal": 1000}
 
 
-def cpu_baseline(w, seconds):
+def cpu_baseline(w, seconds, precision=0):
     """The oracle as it stands, OpenMP over chains on every host core, on a
     bounded sample of the same workload (a spread subset of its chains)."""
     import oracle
@@ -165,7 +173,7 @@ def cpu_baseline(w, seconds):
         cp = np.asarray(w["chain_param"], np.int32)[ids]
         sp = oracle.init_spins(L, ids, w["seed"])
         t = time.perf_counter()
-        oracle.run(L, w["params"], cp, sp, w["seed"], 0, n_sw, 10, chain_ids=ids)
+        oracle.run(L, w["params"], cp, sp, w["seed"], 0, n_sw, 10, chain_ids=ids, precision=precision)
         return time.perf_counter() - t
 
     small = L <= 64
@@ -188,8 +196,8 @@ def run_reference(args, rank, ws):
     w = workload_config(args.workload, 0)
     per_step = max(1.0, 60.0 / max(1, args.steps + args.warmup))
     for _ in range(args.warmup):
-        cpu_baseline(w, min(per_step, 2.0))
-    vals = [cpu_baseline(w, per_step) for _ in range(args.steps)]
+        cpu_baseline(w, min(per_step, 2.0), 1 if args.precision == "paper" else 0)
+    vals = [cpu_baseline(w, per_step, 1 if args.precision == "paper" else 0) for _ in range(args.steps)]
     v = float(np.mean([x["value"] for x in vals]))
     cb = dict(vals[-1])
     cb["value"] = v
@@ -210,6 +218,9 @@ def config_dict(w, args):
     else:
         desc = ("L=384 periodic SS lattice: J=J'=1, beta=1, h in {0,1,2} x 1024 chains, 64-chain "
                 "words, spins and hidden units in HBM (two launches per sweep)")
+    if getattr(args, "precision", "exact") == "paper":
+        desc += ("; paper precision: Q5.4 weights and bias, 12-bit accumulator, 16-bit sigmoid table "
+                 "and 16-bit uniforms (two per Philox word)")
     return {"workload": desc, "L": w["L"], "n_chains": w["n_chains"],
             "n_params": len(w["params"]["J"]), "sweeps_per_step": args.sweeps_per_step,
             "measure_every": args.measure_every,
@@ -255,6 +266,7 @@ def run_batch(args, rank, ws):
     calls = sum(4 * ((sp["L"] + 1) // 2) ** 2 * sp["n_chains"] for sp in specs) * S
     achieved = MUL_OPS_PER_CALL * calls / (t_total / K) / 1e12
     peak = SM_COUNT * IMUL_LANES_PER_SM_CLK * SM_MAX_MHZ * 1e6 / 1e12
+    traffic = MEASURED_TRAFFIC["grid_paper" if paper else args.workload]
     # end to end with host buffers: spins in, one batched step, observables out
     host = [m.get_spins() for m in members]
     torch.cuda.synchronize()
@@ -383,8 +395,10 @@ def main():
     S, K, W = args.sweeps_per_step, args.steps, args.warmup
     n_meas = S * K // args.measure_every
     layout = crbm.CRBM_LAYOUT_SMEM if args.workload == "grid" else crbm.CRBM_LAYOUT_STREAM
+    paper = args.precision == "paper"
     s = crbm.Sampler(w["L"], w["params"], w["n_chains"], chain_param=w["chain_param"], seed=w["seed"],
-                     measure_every=args.measure_every, series_len=n_meas, layout=layout)
+                     measure_every=args.measure_every, series_len=n_meas, layout=layout,
+                     precision=crbm.CRBM_PRECISION_PAPER if paper else crbm.CRBM_PRECISION_EXACT)
     tuned_warps = s.autotune(200) if args.workload == "grid" else None  # CTA shape, on scratch copies
     stream = torch.cuda.current_stream()
     flush = torch.empty(256 * 1024 * 1024, dtype=torch.uint8, device="cuda")
@@ -439,13 +453,14 @@ def main():
     e2e_steps = max(1, K // 2)
     e2e_val = w["n_chains"] * w["L"] ** 2 * S * e2e_steps * ws / e2e_t
 
-    calls = CALLS_PER_CELL * (w["L"] // 2) ** 2 * w["n_chains"] * S     # per step
+    calls = (CALLS_PER_CELL_PAPER if paper else CALLS_PER_CELL) * (w["L"] // 2) ** 2 * w["n_chains"] * S
     if args.workload == "grid":   # one launch per step: spins in and out once
         hbm_bytes = w["n_chains"] * w["L"] ** 2 / 8 * 2
     else:                         # per sweep: spins read + written, hidden written + read
         hbm_bytes = w["n_chains"] * w["L"] ** 2 * 7 / 8 * S
     achieved = MUL_OPS_PER_CALL * calls / (t_total / K) / 1e12
     peak = SM_COUNT * IMUL_LANES_PER_SM_CLK * SM_MAX_MHZ * 1e6 / 1e12
+    traffic = MEASURED_TRAFFIC["grid_paper" if paper else args.workload]
     cfg = config_dict(w, args)
     if tuned_warps:
         cfg["warps_per_cta_autotuned"] = tuned_warps
@@ -466,14 +481,15 @@ def main():
                 "note": "0.25 B (SMEM layout: spins in and out once per launch) or 0.875 B "
                         "(streamed: spins 2 bits + hidden 5 bits per spin-update) of algorithmic traffic"},
         "roofline": {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "Tops/s",
-                     "frac": achieved / peak, "traffic": MEASURED_TRAFFIC[args.workload][0],
-                     "traffic_unit": "bytes " + MEASURED_TRAFFIC[args.workload][1],
+                     "frac": achieved / peak, "traffic": traffic[0],
+                     "traffic_unit": "bytes " + traffic[1],
                      "note": "integer-multiply ceiling: 152 SM x 64 lanes/clk x 2070 MHz; 40 "
-                             "multiply ops per Philox-4x32-10 call, 4 calls per chain-cell-sweep",
+                             "multiply ops per Philox-4x32-10 call, "
+                             f"{CALLS_PER_CELL_PAPER if paper else CALLS_PER_CELL} calls per chain-cell-sweep",
                      "philox_calls_per_s": calls / (t_total / K)},
     }
     if rank == 0 and not args.no_cpu_baseline:
-        out["cpu_baseline"] = cpu_baseline(w, args.cpu_seconds)
+        out["cpu_baseline"] = cpu_baseline(w, args.cpu_seconds, 1 if paper else 0)
     if rank == 0:
         print(json.dumps(out))
     if ws > 1:

@@ -61,6 +61,13 @@ extern "C" {
 #define CRBM_LAYOUT_STREAM 2 /* lattice in HBM, one tiled launch per sweep */
 #define CRBM_SMEM_MAX_L 96
 
+/* Arithmetic of the conditionals (Eqs. 9-10). */
+#define CRBM_PRECISION_EXACT 0 /* double-precision weights, 32-bit thresholds and uniforms */
+#define CRBM_PRECISION_PAPER 1 /* the paper's FPGA (Sec. III, "Dimension and Precision"):
+                                * weights and visible bias in 10-bit fixed point (4 fraction
+                                * bits), a 12-bit accumulator, a 16-bit sigmoid table and
+                                * 16-bit uniforms, two per Philox word (see crbm_params) */
+
 typedef struct crbm_ctx crbm_ctx;
 
 /* One filter of Eq. (8): the bond between two sites of the 3x3 window
@@ -101,6 +108,18 @@ typedef struct {
      * crbm_get_permutation). */
     int32_t swap_every;
     void* stream;           /* cudaStream_t for all work; NULL = legacy default stream */
+    /* CRBM_PRECISION_*.  PAPER: A = q(a_cls), B = q(beta h) with q(x) the
+     * nearest multiple of 1/16 clamped to +-511/16; a unit's 16-bit threshold
+     * is min(65535, nearbyint(2^16 / (1 + exp(-2 y)))) with y = A m (hidden)
+     * or B + A_J n_J + A_J' n_J' (visible), y clamped to +-2047/16; its 16-bit
+     * uniform is a half of a Philox word (low half first): hidden filter
+     * k < 8 half k&1 of word k>>1 of tag 0, filters 8 and 9 word 0 of tag 1,
+     * the spin at window offset (r, c) half (2r+c)&1 of word 1 + ((2r+c)>>1)
+     * of tag 1 -- two Philox calls per cell instead of four.  Needs the ten
+     * SS filters, an even periodic lattice and the SMEM layout; not in
+     * batches or with block proposals.  crbm_get_tables returns the 16-bit
+     * thresholds in the upper halves of the 32-bit entries. */
+    int32_t precision;
 } crbm_params;
 
 /* Build the model (Eqs. 3-8), the threshold tables, allocate device state and

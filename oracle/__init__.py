@@ -24,6 +24,7 @@ _LIB = os.path.join(_LIB_DIR, "liboracle.so")
 
 NSUM = 11
 TAG_VIS, TAG_INIT, TAG_SWAP = 4, 5, 6
+PRECISION_EXACT, PRECISION_PAPER = 0, 1
 
 
 def build(force: bool = False) -> str:
@@ -57,6 +58,10 @@ def lib():
         _lib = ctypes.CDLL(build())
         _lib.orc_threshold.restype = ctypes.c_uint32
         _lib.orc_threshold.argtypes = [ctypes.c_double]
+        _lib.orc_lut16.restype = ctypes.c_uint32
+        _lib.orc_lut16.argtypes = [ctypes.c_int32]
+        _lib.orc_q54.restype = ctypes.c_int32
+        _lib.orc_q54.argtypes = [ctypes.c_double]
     return _lib
 
 
@@ -99,6 +104,17 @@ def threshold(y):
     return int(lib().orc_threshold(float(y)))
 
 
+def q54(x):
+    """Paper precision: nearest multiple of 1/16 within +-511/16, in 1/16 units."""
+    return int(lib().orc_q54(float(x)))
+
+
+def lut16(acc):
+    """Paper precision: 16-bit sigmoid table entry of an accumulator value (1/16
+    units), in the upper half of a 32-bit threshold."""
+    return int(lib().orc_lut16(int(acc)))
+
+
 def quantize(x):
     q = ctypes.c_int32()
     if lib().orc_quantize(ctypes.c_double(x), ctypes.byref(q)):
@@ -114,15 +130,15 @@ def degrees(L, periodic=True, bonds=None):
     return dj.value, djp.value
 
 
-def tables(L, J, Jp, h, beta, periodic=True, bonds=None):
+def tables(L, J, Jp, h, beta, periodic=True, bonds=None, precision=PRECISION_EXACT):
     """(Th[2][5], Tv[2DJ+1][2DJp+1]) uint32 for one parameter point."""
     arr, nb = bonds_array(bonds)
     dj, djp = degrees(L, periodic, bonds)
     th = np.zeros(10, np.uint32)
     tv = np.zeros((2 * dj + 1) * (2 * djp + 1), np.uint32)
-    rc = lib().orc_tables(L, int(periodic), arr, nb, ctypes.c_double(J), ctypes.c_double(Jp),
-                          ctypes.c_double(h), ctypes.c_double(beta), _p(th, ctypes.c_uint32),
-                          _p(tv, ctypes.c_uint32))
+    rc = lib().orc_tables_ex(L, int(periodic), arr, nb, ctypes.c_double(J), ctypes.c_double(Jp),
+                             ctypes.c_double(h), ctypes.c_double(beta), int(precision),
+                             _p(th, ctypes.c_uint32), _p(tv, ctypes.c_uint32))
     if rc:
         raise ValueError("bad parameters")
     return th.reshape(2, 5), tv.reshape(2 * dj + 1, 2 * djp + 1)
@@ -148,7 +164,7 @@ def counts(spins, L, periodic=True, bonds=None):
 
 def run(L, params, chain_param, spins, seed, sweep0, n_sweeps, measure_every=1,
         chain_ids=None, periodic=True, bonds=None, sums=None, series_cap=0, sq_every=0,
-        sq=None):
+        sq=None, precision=PRECISION_EXACT):
     """Advance ``spins`` [n_chains][L][L] (int8 +-1, modified in place).
 
     params: dict of equal-length sequences J, Jp, h, beta.
@@ -169,13 +185,13 @@ def run(L, params, chain_param, spins, seed, sweep0, n_sweeps, measure_every=1,
     series = np.zeros((n, series_cap, 3), np.int32) if series_cap > 0 else None
     if sq_every > 0 and sq is None:
         sq = np.zeros((n, L, L), np.float64)
-    rc = lib().orc_run(L, int(periodic), arr, nb, _p(J, ctypes.c_double), _p(Jp, ctypes.c_double),
+    rc = lib().orc_run_ex(L, int(periodic), arr, nb, _p(J, ctypes.c_double), _p(Jp, ctypes.c_double),
                        _p(h, ctypes.c_double), _p(beta, ctypes.c_double), len(J),
                        _p(cp, ctypes.c_int32), _p(ids, ctypes.c_uint32), n, ctypes.c_uint64(seed),
                        ctypes.c_int64(sweep0), ctypes.c_int64(n_sweeps), int(measure_every),
                        _p(spins, ctypes.c_int8), _p(sums, ctypes.c_int64),
                        _p(series, ctypes.c_int32), ctypes.c_int64(series_cap), int(sq_every),
-                       _p(sq, ctypes.c_double) if sq_every > 0 else None)
+                       _p(sq, ctypes.c_double) if sq_every > 0 else None, int(precision))
     if rc:
         raise ValueError(f"orc_run failed ({rc})")
     return sums, series, sq
@@ -190,7 +206,8 @@ def get_threads():
 
 
 def run_pt(L, params, chain_param, spins, slot_of_beta, seed, sweep0, n_sweeps, measure_every=1,
-           swap_every=10, periodic=True, bonds=None, sums=None, series_cap=0):
+           swap_every=10, periodic=True, bonds=None, sums=None, series_cap=0,
+           precision=PRECISION_EXACT):
     """Parallel tempering on ladders of 32 chains (see orc_run_pt).  Advances
     ``spins`` (per slot) and ``slot_of_beta`` [n_ladders][32] in place; sums
     and series rows are per rung (chain index 32 l + k)."""
@@ -206,13 +223,13 @@ def run_pt(L, params, chain_param, spins, slot_of_beta, seed, sweep0, n_sweeps, 
     if sums is None:
         sums = np.zeros((n, NSUM), np.int64)
     series = np.zeros((n, series_cap, 3), np.int32) if series_cap > 0 else None
-    rc = lib().orc_run_pt(L, int(periodic), arr, nb, _p(J, ctypes.c_double),
+    rc = lib().orc_run_pt_ex(L, int(periodic), arr, nb, _p(J, ctypes.c_double),
                           _p(Jp, ctypes.c_double), _p(h, ctypes.c_double),
                           _p(beta, ctypes.c_double), len(J), _p(cp, ctypes.c_int32), n,
                           ctypes.c_uint64(seed), ctypes.c_int64(sweep0), ctypes.c_int64(n_sweeps),
                           int(measure_every), int(swap_every), _p(spins, ctypes.c_int8),
                           _p(slot_of_beta, ctypes.c_int32), _p(sums, ctypes.c_int64),
-                          _p(series, ctypes.c_int32), ctypes.c_int64(series_cap))
+                          _p(series, ctypes.c_int32), ctypes.c_int64(series_cap), int(precision))
     if rc:
         raise ValueError(f"orc_run_pt failed ({rc})")
     return sums, series

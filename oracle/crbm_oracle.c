@@ -161,9 +161,34 @@ int orc_degrees(int L, int periodic, const orc_bond* bonds, int nb, int* DJ, int
  * Eq. (10): P(V=1|H) = sigmoid of the zero-padded reverse correlation summed
  * over the filters plus the visible bias; here sigmoid(2 x) with
  * x = beta h + a_J n_J + a_J' n_J'. */
+/* Paper precision (Sec. III, "Dimension and Precision"): 10-bit weights with
+ * 4 fraction bits, an accumulator 2 bits wider, a 16-bit sigmoid table. */
+int32_t orc_q54(double x) {
+    double v = nearbyint(16.0 * x);
+    if (v > 511.0) v = 511.0;
+    if (v < -511.0) v = -511.0;
+    return (int32_t)v;
+}
+
+uint32_t orc_lut16(int32_t acc) {
+    if (acc > 2047) acc = 2047;
+    if (acc < -2047) acc = -2047;
+    double p = 1.0 / (1.0 + exp(-2.0 * (double)acc / 16.0));
+    double t = nearbyint(ldexp(p, 16));
+    if (t > 65535.0) t = 65535.0;
+    return (uint32_t)t << 16;
+}
+
 int orc_tables(int L, int periodic, const orc_bond* bonds, int nb, double J, double Jp,
                double h, double beta, uint32_t* Th, uint32_t* Tv) {
+    return orc_tables_ex(L, periodic, bonds, nb, J, Jp, h, beta, ORC_PRECISION_EXACT, Th, Tv);
+}
+
+int orc_tables_ex(int L, int periodic, const orc_bond* bonds, int nb, double J, double Jp,
+                  double h, double beta, int precision, uint32_t* Th, uint32_t* Tv) {
     int DJ, DJp;
+    if (precision != ORC_PRECISION_EXACT && precision != ORC_PRECISION_PAPER) return -1;
+    if (precision == ORC_PRECISION_PAPER && nb > 10) return -1;
     if (orc_degrees(L, periodic, bonds, nb, &DJ, &DJp)) return -1;
     int32_t qJ, qJp, qh;
     if (orc_quantize(J, &qJ) || orc_quantize(Jp, &qJp) || orc_quantize(h, &qh)) return -1;
@@ -173,9 +198,18 @@ int orc_tables(int L, int periodic, const orc_bond* bonds, int nb, double J, dou
     int s[2];
     orc_weight(beta, Jd, &a[0], &s[0]);
     orc_weight(beta, Jpd, &a[1], &s[1]);
+    int nP = 2 * DJp + 1;
+    if (precision == ORC_PRECISION_PAPER) {
+        int32_t A[2] = {orc_q54(a[0]), orc_q54(a[1])}, B = orc_q54(beta * hd);
+        for (int cls = 0; cls < 2; ++cls)
+            for (int m = -2; m <= 2; ++m) Th[cls * 5 + (m + 2)] = orc_lut16(A[cls] * m);
+        for (int nJ = -DJ; nJ <= DJ; ++nJ)
+            for (int nJp = -DJp; nJp <= DJp; ++nJp)
+                Tv[(nJ + DJ) * nP + (nJp + DJp)] = orc_lut16(B + A[0] * nJ + A[1] * nJp);
+        return 0;
+    }
     for (int cls = 0; cls < 2; ++cls)
         for (int m = -2; m <= 2; ++m) Th[cls * 5 + (m + 2)] = orc_threshold(2.0 * a[cls] * m);
-    int nP = 2 * DJp + 1;
     for (int nJ = -DJ; nJ <= DJ; ++nJ)
         for (int nJp = -DJp; nJp <= DJp; ++nJp) {
             double x = beta * hd + a[0] * nJ + a[1] * nJp;
@@ -239,7 +273,19 @@ typedef struct {
     uint32_t Th[10];
     uint32_t* Tv;
     int s[2];
+    int paper;  /* ORC_PRECISION_PAPER: 16-bit uniforms and thresholds */
 } orc_point;
+
+/* One unit's decision.  Exact precision: word w of Philox((cell, sweep,
+ * chain, tag)) against the 32-bit threshold.  Paper precision: the 16-bit
+ * uniform in half `half` of that word against the threshold's upper half. */
+static int draw_below(const orc_point* pt, uint32_t cell, uint32_t sweep, uint32_t chain,
+                      uint32_t tag, int word, int half, uint64_t seed, uint32_t t) {
+    uint32_t u = philox_word(cell, sweep, chain, tag, seed, word);
+    if (!pt->paper) return u < t;
+    uint32_t u16 = half ? (u >> 16) : (u & 0xffffu);
+    return u16 < (t >> 16);
+}
 
 /* Sec. II.B and Fig. 1(d): one sweep = every hidden unit drawn from Eq. (9)
  * given the current spins, then every spin drawn from Eq. (10) given those
@@ -259,9 +305,15 @@ static void one_sweep(int L, int periodic, const orc_bond* bonds, int nb, const 
                 int s1 = site_of(L, periodic, i, j, b->r1, b->c1);
                 int s2 = site_of(L, periodic, i, j, b->r2, b->c2);
                 int m = (s1 >= 0 ? v[s1] : 0) + pt->s[b->cls] * (s2 >= 0 ? v[s2] : 0);
-                uint32_t u = philox_word(cell, sweep, chain, (uint32_t)(k >> 2), seed, k & 3);
                 uint32_t t = pt->Th[b->cls * 5 + (m + 2)];
-                hid[cell * nb + k] = (u < t) ? 1 : -1;
+                int up;
+                if (!pt->paper)
+                    up = draw_below(pt, cell, sweep, chain, (uint32_t)(k >> 2), k & 3, 0, seed, t);
+                else if (k < 8)
+                    up = draw_below(pt, cell, sweep, chain, 0u, k >> 1, k & 1, seed, t);
+                else
+                    up = draw_below(pt, cell, sweep, chain, 1u, 0, k & 1, seed, t);
+                hid[cell * nb + k] = up ? 1 : -1;
             }
         }
     /* visible | hidden: zero-padded reverse correlation = scatter of every
@@ -284,9 +336,11 @@ static void one_sweep(int L, int periodic, const orc_bond* bonds, int nb, const 
         for (int C = 0; C < L; ++C) {
             int s = R * L + C;
             uint32_t cell = (uint32_t)((R >> 1) * W + (C >> 1));
-            uint32_t u = philox_word(cell, sweep, chain, ORC_TAG_VIS, seed, 2 * (R & 1) + (C & 1));
+            int x = 2 * (R & 1) + (C & 1);
             uint32_t t = pt->Tv[(field[s] + DJ) * nP + (field[L * L + s] + DJp)];
-            v[s] = (u < t) ? 1 : -1;
+            int up = pt->paper ? draw_below(pt, cell, sweep, chain, 1u, 1 + (x >> 1), x & 1, seed, t)
+                               : draw_below(pt, cell, sweep, chain, ORC_TAG_VIS, x, 0, seed, t);
+            v[s] = up ? 1 : -1;
         }
 }
 
@@ -295,6 +349,16 @@ int orc_run(int L, int periodic, const orc_bond* bonds, int nb, const double* J,
             const uint32_t* chain_ids, int n_chains, uint64_t seed, int64_t sweep0,
             int64_t n_sweeps, int measure_every, int8_t* spins, int64_t* sums, int32_t* series,
             int64_t series_cap, int sq_every, double* sq) {
+    return orc_run_ex(L, periodic, bonds, nb, J, Jp, h, beta, n_params, chain_param, chain_ids,
+                      n_chains, seed, sweep0, n_sweeps, measure_every, spins, sums, series,
+                      series_cap, sq_every, sq, ORC_PRECISION_EXACT);
+}
+
+int orc_run_ex(int L, int periodic, const orc_bond* bonds, int nb, const double* J,
+               const double* Jp, const double* h, const double* beta, int n_params,
+               const int32_t* chain_param, const uint32_t* chain_ids, int n_chains, uint64_t seed,
+               int64_t sweep0, int64_t n_sweeps, int measure_every, int8_t* spins, int64_t* sums,
+               int32_t* series, int64_t series_cap, int sq_every, double* sq, int precision) {
     int DJ, DJp;
     if (orc_degrees(L, periodic, bonds, nb, &DJ, &DJp)) return -1;
     if (n_params < 1 || n_chains < 0 || n_sweeps < 0 || sweep0 < 0 ||
@@ -313,7 +377,9 @@ int orc_run(int L, int periodic, const orc_bond* bonds, int nb, const double* J,
     int err = 0;
     for (int p = 0; p < n_params; ++p) {
         pts[p].Tv = tv + (size_t)p * nTv;
-        if (orc_tables(L, periodic, bonds, nb, J[p], Jp[p], h[p], beta[p], pts[p].Th, pts[p].Tv))
+        pts[p].paper = precision == ORC_PRECISION_PAPER;
+        if (orc_tables_ex(L, periodic, bonds, nb, J[p], Jp[p], h[p], beta[p], precision, pts[p].Th,
+                          pts[p].Tv))
             err = -1;
         int32_t q;
         double a;
@@ -387,6 +453,17 @@ int orc_run_pt(int L, int periodic, const orc_bond* bonds, int nb, const double*
                const int32_t* chain_param, int n_chains, uint64_t seed, int64_t sweep0,
                int64_t n_sweeps, int measure_every, int swap_every, int8_t* spins,
                int32_t* slot_of_beta, int64_t* sums, int32_t* series, int64_t series_cap) {
+    return orc_run_pt_ex(L, periodic, bonds, nb, J, Jp, h, beta, n_params, chain_param, n_chains,
+                         seed, sweep0, n_sweeps, measure_every, swap_every, spins, slot_of_beta, sums,
+                         series, series_cap, ORC_PRECISION_EXACT);
+}
+
+int orc_run_pt_ex(int L, int periodic, const orc_bond* bonds, int nb, const double* J,
+                  const double* Jp, const double* h, const double* beta, int n_params,
+                  const int32_t* chain_param, int n_chains, uint64_t seed, int64_t sweep0,
+                  int64_t n_sweeps, int measure_every, int swap_every, int8_t* spins,
+                  int32_t* slot_of_beta, int64_t* sums, int32_t* series, int64_t series_cap,
+                  int precision) {
     if (n_chains <= 0 || n_chains % 32 || swap_every <= 0 || measure_every < 0) return -1;
     int n_lad = n_chains / 32, N = L * L;
     for (int l = 0; l < n_lad; ++l) {
@@ -410,7 +487,9 @@ int orc_run_pt(int L, int periodic, const orc_bond* bonds, int nb, const double*
     int err = 0;
     for (int p = 0; p < n_params; ++p) {
         pts[p].Tv = tv + (size_t)p * nTv;
-        if (orc_tables(L, periodic, bonds, nb, J[p], Jp[p], h[p], beta[p], pts[p].Th, pts[p].Tv))
+        pts[p].paper = precision == ORC_PRECISION_PAPER;
+        if (orc_tables_ex(L, periodic, bonds, nb, J[p], Jp[p], h[p], beta[p], precision, pts[p].Th,
+                          pts[p].Tv))
             err = 1;
         int32_t qq;
         double a;

@@ -92,6 +92,38 @@ int orc_run(int L, int periodic, const orc_bond* bonds, int nb,
 void orc_set_threads(int n);
 int orc_get_threads(void);
 
+/* ---- paper precision (Sec. III, "Dimension and Precision") ----------------
+ * The paper's FPGA keeps the convolution weights in 10-bit fixed point (sign,
+ * 5 integer and 4 fraction bits), sums them in an accumulator 2 bits wider,
+ * maps the sum through a 16-bit sigmoid table and compares it with 16-bit
+ * uniform draws.  ORC_PRECISION_PAPER restates that arithmetic:
+ *   A_cls = q54(a_cls), B = q54(beta h)   (q54: nearest multiple of 1/16,
+ *                                           clamped to +-511/16)
+ *   hidden threshold of m:   lut16(A_cls m)
+ *   visible threshold:       lut16(B + A_J n_J + A_J' n_J')
+ *   lut16(acc) = min(65535, nearbyint(2^16 / (1 + exp(-2 acc / 16)))) << 16,
+ *     acc in 1/16 units clamped to the 12-bit range +-2047,
+ * so a 32-bit table entry is the 16-bit threshold in its upper half.  Each
+ * Philox word carries two 16-bit uniforms, low half first: hidden filter
+ * k < 8 takes half k&1 of word k>>1 of tag 0, filters 8 and 9 the halves of
+ * word 0 of tag 1, and the spin at window offset (r, c) half (2r+c)&1 of word
+ * 1 + ((2r+c)>>1) of tag 1; a unit becomes +1 iff its uniform is below the
+ * 16-bit threshold.  Needs at most 10 filters.  The _ex functions take the
+ * precision; the others are ORC_PRECISION_EXACT. */
+#define ORC_PRECISION_EXACT 0
+#define ORC_PRECISION_PAPER 1
+int32_t orc_q54(double x);
+uint32_t orc_lut16(int32_t acc);
+int orc_tables_ex(int L, int periodic, const orc_bond* bonds, int nb,
+                  double J, double Jp, double h, double beta, int precision,
+                  uint32_t* Th, uint32_t* Tv);
+int orc_run_ex(int L, int periodic, const orc_bond* bonds, int nb,
+               const double* J, const double* Jp, const double* h, const double* beta,
+               int n_params, const int32_t* chain_param, const uint32_t* chain_ids,
+               int n_chains, uint64_t seed, int64_t sweep0, int64_t n_sweeps,
+               int measure_every, int8_t* spins, int64_t* sums,
+               int32_t* series, int64_t series_cap, int sq_every, double* sq, int precision);
+
 #define ORC_TAG_VIS 4u
 #define ORC_TAG_INIT 5u
 #define ORC_TAG_SWAP 6u
@@ -122,6 +154,12 @@ int orc_run_pt(int L, int periodic, const orc_bond* bonds, int nb, const double*
                const int32_t* chain_param, int n_chains, uint64_t seed, int64_t sweep0,
                int64_t n_sweeps, int measure_every, int swap_every, int8_t* spins,
                int32_t* slot_of_beta, int64_t* sums, int32_t* series, int64_t series_cap);
+int orc_run_pt_ex(int L, int periodic, const orc_bond* bonds, int nb, const double* J,
+                  const double* Jp, const double* h, const double* beta, int n_params,
+                  const int32_t* chain_param, int n_chains, uint64_t seed, int64_t sweep0,
+                  int64_t n_sweeps, int measure_every, int swap_every, int8_t* spins,
+                  int32_t* slot_of_beta, int64_t* sums, int32_t* series, int64_t series_cap,
+                  int precision);
 uint32_t orc_swap_threshold(double x);
 #ifdef __cplusplus
 }

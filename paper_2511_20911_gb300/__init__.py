@@ -22,6 +22,7 @@ from ._build import LIB, build
 CRBM_OK, CRBM_EINVAL, CRBM_ENOMEM, CRBM_ECUDA, CRBM_ETIMEOUT, CRBM_EUNSUPPORTED = 0, -1, -2, -3, -4, -5
 CRBM_NSUM = 11
 CRBM_LAYOUT_AUTO, CRBM_LAYOUT_SMEM, CRBM_LAYOUT_STREAM = 0, 1, 2
+CRBM_PRECISION_EXACT, CRBM_PRECISION_PAPER = 0, 1
 CRBM_SMEM_MAX_L = 96
 SUM_FIELDS = ("n", "NJ", "NJp", "M", "absM", "NJ2", "NJp2", "M2", "NJ_NJp", "NJ_M", "NJp_M")
 
@@ -60,7 +61,7 @@ class crbm_params(ctypes.Structure):
                 ("n_chains", ctypes.c_int32), ("seed", ctypes.c_uint64),
                 ("measure_every", ctypes.c_int32), ("series_len", ctypes.c_int32),
                 ("sq_every", ctypes.c_int32), ("layout", ctypes.c_int32),
-                ("swap_every", ctypes.c_int32), ("stream", ctypes.c_void_p)]
+                ("swap_every", ctypes.c_int32), ("stream", ctypes.c_void_p), ("precision", ctypes.c_int32)]
 
 
 _lib = None
@@ -156,7 +157,7 @@ class Sampler:
 
     def __init__(self, L, params, n_chains, chain_param=None, seed=1, periodic=True,
                  bonds=None, measure_every=1, series_len=0, sq_every=0,
-                 layout=CRBM_LAYOUT_AUTO, swap_every=0, stream=None):
+                 layout=CRBM_LAYOUT_AUTO, swap_every=0, stream=None, precision=0):
         lib = load_library()
         self.L, self.n_chains = int(L), int(n_chains)
         self._J = np.ascontiguousarray(params["J"], np.float64)
@@ -187,6 +188,8 @@ class Sampler:
         p.layout = int(layout)
         p.swap_every = int(swap_every)
         p.stream = ctypes.c_void_p(int(stream)) if stream else None
+        p.precision = int(precision)
+        self.precision = int(precision)
         h = ctypes.c_void_p()
         _check(lib.crbm_create(ctypes.byref(h), ctypes.byref(p)))
         self._ctx = h

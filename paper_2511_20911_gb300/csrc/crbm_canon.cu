@@ -27,7 +27,7 @@ using namespace canon;
 // again.  A CTA that finds no free unfinished word exits: every unfinished
 // word is then held by a running CTA, which claims again after its chunk, so
 // no work is left behind and nothing waits.
-template <bool kSmemRec>
+template <bool kSmemRec, bool kPaper>
 __global__ void __launch_bounds__(CRBM_SWEEP_MAX_THREADS, CRBM_SWEEP_MIN_BLOCKS)
     k_sweep_canon_persistent(const SweepArgs a, int chunk, int* state) {
     __shared__ int s_word, s_chunk;
@@ -90,7 +90,7 @@ __global__ void __launch_bounds__(CRBM_SWEEP_MAX_THREADS, CRBM_SWEEP_MIN_BLOCKS)
         const int n = min(chunk, a.n_sweeps - c * chunk);
         const int64_t meas0 =
             K > 0 ? a.meas0 + static_cast<int64_t>(t0 / K) - static_cast<int64_t>(a.t0 / K) : a.meas0;
-        sweep_canon_body<kSmemRec, false>(a, word, t0, n, meas0);
+        sweep_canon_body<kSmemRec, false, kPaper>(a, word, t0, n, meas0);
         __syncthreads();  // every thread's state stores are issued
         if (threadIdx.x == 0) {
             __threadfence();
@@ -116,22 +116,19 @@ size_t smem_bytes_canon_launch(const Geometry& g) {
                : smem_bytes_canon(g);
 }
 
-size_t smem_bytes_canon(const Geometry& g) {
-    return sizeof(uint32_t) * (static_cast<size_t>(kAccWords) + kCanonTab + g.N + static_cast<size_t>(g.n_cells) * 32 +
-                               96 + 33 + 32 + 64);
-}
+size_t smem_bytes_canon(const Geometry& g) { return sizeof(uint32_t) * canon_smem_rec_offset(g); }
 
 namespace {
-template <bool kSmemRec>
+template <bool kSmemRec, bool kPaper>
 cudaError_t launch_persistent(const SweepArgs& a, int warps_per_cta, int chunk, int* sched, cudaStream_t st) {
     const size_t smem = smem_bytes_canon_launch(a.g);
     if (smem > 48 * 1024) {
-        const cudaError_t e = cudaFuncSetAttribute(k_sweep_canon_persistent<kSmemRec>,
+        const cudaError_t e = cudaFuncSetAttribute(k_sweep_canon_persistent<kSmemRec, kPaper>,
                                                    cudaFuncAttributeMaxDynamicSharedMemorySize, static_cast<int>(smem));
         if (e != cudaSuccess) return e;
     }
     int per_sm = 0, dev = 0, sms = 0;
-    cudaError_t e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_sweep_canon_persistent<kSmemRec>,
+    cudaError_t e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_sweep_canon_persistent<kSmemRec, kPaper>,
                                                                   warps_per_cta * 32, smem);
     if (e == cudaSuccess) e = cudaGetDevice(&dev);
     if (e == cudaSuccess) e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
@@ -141,7 +138,7 @@ cudaError_t launch_persistent(const SweepArgs& a, int warps_per_cta, int chunk, 
     const int grid = std::min(std::min(n_items, a.n_words), per_sm * sms);
     e = cudaMemsetAsync(sched, 0, sizeof(int) * (4 + static_cast<size_t>(a.n_words)), st);
     if (e != cudaSuccess) return e;
-    k_sweep_canon_persistent<kSmemRec><<<grid, warps_per_cta * 32, smem, st>>>(a, chunk, sched);
+    k_sweep_canon_persistent<kSmemRec, kPaper><<<grid, warps_per_cta * 32, smem, st>>>(a, chunk, sched);
     return cudaGetLastError();
 }
 
@@ -149,8 +146,11 @@ cudaError_t launch_persistent(const SweepArgs& a, int warps_per_cta, int chunk, 
 
 cudaError_t launch_sweep_canon_persistent(const SweepArgs& a, int warps_per_cta, int chunk, int* sched,
                                           cudaStream_t st) {
-    return canon_smem_records(a.g) ? launch_persistent<true>(a, warps_per_cta, chunk, sched, st)
-                                   : launch_persistent<false>(a, warps_per_cta, chunk, sched, st);
+    if (a.g.paper)
+        return canon_smem_records(a.g) ? launch_persistent<true, true>(a, warps_per_cta, chunk, sched, st)
+                                       : launch_persistent<false, true>(a, warps_per_cta, chunk, sched, st);
+    return canon_smem_records(a.g) ? launch_persistent<true, false>(a, warps_per_cta, chunk, sched, st)
+                                   : launch_persistent<false, false>(a, warps_per_cta, chunk, sched, st);
 }
 
 }  // namespace crbm

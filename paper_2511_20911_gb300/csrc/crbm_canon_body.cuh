@@ -49,7 +49,9 @@ __device__ __forceinline__ void body_sync() {
 // (band >= n_bands) only keep the barrier count, which is the same for every
 // rank because a cluster never mixes contexts.  Correlations need the whole
 // lattice, so a word with sq_every > 0 is never split (n_bands == 1).
-template <bool kSmemRec, bool kCluster>
+// kPaper: CRBM_PRECISION_PAPER draws (two Philox calls per cell, the visible
+// uniforms passed from the hidden half-step through shared memory).
+template <bool kSmemRec, bool kCluster, bool kPaper = false>
 __device__ __forceinline__ void sweep_canon_body(const SweepArgs& a, int word, uint32_t t0, int n_sweeps,
                                                  int64_t meas0, int band = 0, int rank0 = 0) {
     extern __shared__ __align__(16) uint32_t smem[];
@@ -133,6 +135,19 @@ __device__ __forceinline__ void sweep_canon_body(const SweepArgs& a, int word, u
         const uint32_t t = t0 + static_cast<uint32_t>(it);
         const Round1Sweep rs = round1_sweep(r0l.hi ^ t ^ a.rk[0], a.rk);
         const uint4* rec = rec0;
+        if (kPaper && !kCluster) {
+            for (int cell = c_begin + warp; cell < c_end; cell += nwarp, rec += rstep) {
+                const uint4 h0 = ld_rec<kSmemRec>(rec), h1 = ld_rec<kSmemRec>(rec + 1),
+                            h2 = ld_rec<kSmemRec>(rec + 2);
+                sts_off(sm, h1.y + lane4, hidden_cell_rec_paper(sm, h0, h1, h2, s_th, rs, r0l.lo, a.rk, lc,
+                                                                2u * lane4));
+            }
+            __syncthreads();
+            rec = rec0;
+            for (int cell = c_begin + warp; cell < c_end; cell += nwarp, rec += rstep)
+                visible_cell_rec_paper(sm, ld_rec<kSmemRec>(rec + 3), ld_rec<kSmemRec>(rec + 4), lane4, s_tv, lc);
+            __syncthreads();
+        } else {
         for (int cell = c_begin + warp; cell < c_end; cell += nwarp, rec += rstep) {
             const uint4 h0 = ld_rec<kSmemRec>(rec), h1 = ld_rec<kSmemRec>(rec + 1), h2 = ld_rec<kSmemRec>(rec + 2);
             const uint32_t h5 = kSmemRec ? reinterpret_cast<const uint32_t*>(rec + 5)[0]
@@ -152,6 +167,7 @@ __device__ __forceinline__ void sweep_canon_body(const SweepArgs& a, int word, u
             }
         }
         body_sync<kCluster>();
+        }
         const bool do_meas = measuring && (t + 1u) % static_cast<uint32_t>(a.measure_every) == 0u;
         const bool do_swap = a.swap_every > 0 && (t + 1u) % static_cast<uint32_t>(a.swap_every) == 0u;
         if (do_meas || do_swap) {

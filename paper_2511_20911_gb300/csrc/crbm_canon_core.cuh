@@ -215,6 +215,85 @@ __device__ __forceinline__ U4 visible_cell_rec(char* sm, const uint4& v0, const 
     return o;
 }
 
+// Paper precision (CRBM_PRECISION_PAPER): every Philox word carries two
+// 16-bit uniforms and a threshold holds its 16-bit value in the upper half,
+// so a word's high-half uniform compares as the whole word and its low half
+// after a shift by 16.  The hidden half-step of a cell draws two calls (tags
+// 0 and 1): filter k takes half k&1 of word k>>1 of tag 0, filters 8 and 9
+// the halves of word 0 of tag 1; words 1 and 2 of tag 1 carry the cell's
+// four visible uniforms and are returned in `vis` for the visible half-step.
+__device__ __forceinline__ uint32_t hidden_core_paper(uint32_t v00, uint32_t v01, uint32_t v02, uint32_t v10,
+                                                      uint32_t v11, uint32_t v12, uint32_t v20, uint32_t v21,
+                                                      const uint32_t* s_th, const Round1Sweep& r1, uint32_t Y,
+                                                      uint32_t rcb, const Round1Call& c0, const Round1Call& c1,
+                                                      const uint32_t (&rk)[20], const LaneConst& lc, uint2& vis) {
+    const uint32_t m00 = v00 & lc.lm, m01 = v01 & lc.lm, m02 = v02 & lc.lm, m10 = v10 & lc.lm;
+    const uint32_t m11 = v11 & lc.lm, m12 = v12 & lc.lm, m20 = v20 & lc.lm, m21 = v21 & lc.lm;
+    const uint32_t a00 = rotr(m00, lc.rot[0]), a01 = rotr(m01, lc.rot[0]);
+    const uint32_t a10 = rotr(m10, lc.rot[0]), a11 = rotr(m11, lc.rot[0]);
+    const uint32_t a12 = rotr(m12, lc.rot[0]);
+    const uint32_t b01 = rotr(m01, lc.rot[1]), b02 = rotr(m02, lc.rot[1]);
+    const uint32_t b10 = rotr(m10, lc.rot[1]), b11 = rotr(m11, lc.rot[1]);
+    const uint32_t b12 = rotr(m12, lc.rot[1]), b20 = rotr(m20, lc.rot[1]);
+    const uint32_t b21 = rotr(m21, lc.rot[1]);
+    const Round2Cell r2 = round2_cell(r1.hik ^ rcb);
+    const U4 q0 = philox_from_call(Y, r1, r2, c0, rk);
+    const U4 q1 = philox_from_call(Y, r1, r2, c1, rk);
+    const uint32_t* thJ = s_th;
+    const uint32_t* thP = s_th + 128;
+    uint32_t w = 0u;
+    w = or_if_less<kBit0>(w, q0.x << 16, lds_at(thJ, a00 | b01 | lc.lb));
+    w = or_if_less<kBit1>(w, q0.x, lds_at(thJ, a01 | b02 | lc.lb));
+    w = or_if_less<kBit2>(w, q0.y << 16, lds_at(thJ, a10 | b11 | lc.lb));
+    w = or_if_less<kBit3>(w, q0.y, lds_at(thJ, a11 | b12 | lc.lb));
+    w = or_if_less<kBit4>(w, q0.z << 16, lds_at(thJ, a00 | b10 | lc.lb));
+    w = or_if_less<kBit5>(w, q0.z, lds_at(thJ, a10 | b20 | lc.lb));
+    w = or_if_less<kBit6>(w, q0.w << 16, lds_at(thJ, a01 | b11 | lc.lb));
+    w = or_if_less<kBit7>(w, q0.w, lds_at(thJ, a11 | b21 | lc.lb));
+    w = or_if_less<kBit8>(w, q1.x << 16, lds_at(thP, a00 | b11 | lc.lb));
+    w = or_if_less<kBit9>(w, q1.x, lds_at(thP, a12 | b21 | lc.lb));
+    vis = make_uint2(q1.y, q1.z);
+    return w;
+}
+
+// Paper-precision hidden half-step of one cell from its records (the cell's
+// row of visible draws is at byte offset h1.w); stores the lane's two
+// visible-draw words there and returns its word W.
+__device__ __forceinline__ uint32_t hidden_cell_rec_paper(char* sm, const uint4& h0, const uint4& h1,
+                                                          const uint4& h2, const uint32_t* s_th,
+                                                          const Round1Sweep& rs, uint32_t Y,
+                                                          const uint32_t (&rk)[20], const LaneConst& lc,
+                                                          uint32_t lane8) {
+    uint2 vis;
+    const uint32_t w =
+        hidden_core_paper(lds_off(sm, h0.x), lds_off(sm, h0.x + 4u), lds_off(sm, h0.w), lds_off(sm, h0.y),
+                          lds_off(sm, h0.y + 4u), lds_off(sm, h1.x), lds_off(sm, h0.z), lds_off(sm, h0.z + 4u),
+                          s_th, rs, Y, h1.z, {h2.x, h2.y}, {h2.z, h2.w}, rk, lc, vis);
+    *reinterpret_cast<uint2*>(sm + h1.w + lane8) = vis;
+    return w;
+}
+
+// Paper-precision visible half-step of one cell: the four uniforms are the
+// halves of the two words its hidden half-step left at byte offset v1.z.
+__device__ __forceinline__ U4 visible_cell_rec_paper(char* sm, const uint4& v0, const uint4& v1, uint32_t lane4,
+                                                     const uint32_t* s_tv, const LaneConst& lc) {
+    const uint32_t c = (lds_off(sm, v0.z + lane4) & kOwnBits) | (lds_off(sm, v0.w + lane4) & kDownBits) |
+                       (lds_off(sm, v1.x + lane4) & kRightBits);
+    const uint2 vis = *reinterpret_cast<const uint2*>(sm + v1.z + 2u * lane4);
+    const uint32_t f = 31u << 7;
+    const uint32_t t00 = lds_at(s_tv, (c & f) | lc.lb);
+    const uint32_t t01 = lds_at(s_tv + 1024, ((c >> 5) & f) | lc.lb);
+    const uint32_t t10 = lds_at(s_tv + 2048, ((c >> 10) & f) | lc.lb);
+    const uint32_t t11 = lds_at(s_tv + 3072, ((c >> 15) & f) | lc.lb);
+    const U4 o = {__ballot_sync(0xffffffffu, (vis.x << 16) < t00), __ballot_sync(0xffffffffu, vis.x < t01),
+                  __ballot_sync(0xffffffffu, (vis.y << 16) < t10), __ballot_sync(0xffffffffu, vis.y < t11)};
+    sts_off(sm, v0.x, o.x);
+    sts_off(sm, v0.x + 4u, o.y);
+    sts_off(sm, v0.y, o.z);
+    sts_off(sm, v0.y + 4u, o.w);
+    return o;
+}
+
 // Per-lane counts of one cell for the measurement from its eight window
 // words: anti-aligned J and J' filters of the window, and +1 spins of the cell.
 __device__ __forceinline__ void count_core(uint32_t w00, uint32_t w01, uint32_t w02, uint32_t w10, uint32_t w11,

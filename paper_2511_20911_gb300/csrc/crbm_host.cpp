@@ -70,6 +70,24 @@ uint32_t accept_threshold(double y) {
     return static_cast<uint32_t>(r);
 }
 
+// Paper precision (Sec. III, "Dimension and Precision"): a weight or bias in
+// 10-bit fixed point with 4 fraction bits, in 1/16 units (saturating).
+int32_t fixed_q54(double x) {
+    const double r = std::nearbyint(16.0 * x);
+    return static_cast<int32_t>(r > 511.0 ? 511.0 : (r < -511.0 ? -511.0 : r));
+}
+
+// Paper precision: the 16-bit sigmoid table entry of a 12-bit accumulator
+// value y (1/16 units, saturating), sigmoid(2 y / 16), placed in the upper
+// half of a 32-bit threshold so that the kernels compare 16-bit uniforms
+// held in the upper half of a word.
+uint32_t sigmoid_lut16(int32_t y) {
+    const int32_t acc = y > 2047 ? 2047 : (y < -2047 ? -2047 : y);
+    const double prob = 1.0 / (1.0 + std::exp(-2.0 * static_cast<double>(acc) / 16.0));
+    const double r = std::nearbyint(std::ldexp(prob, 16));
+    return static_cast<uint32_t>(r > 65535.0 ? 65535.0 : r) << 16;
+}
+
 // Replica-exchange acceptance exp(x), x <= 0, as a 32-bit threshold.
 uint32_t swap_threshold(double x) {
     const double r = std::nearbyint(std::ldexp(std::exp(x), 32));
@@ -155,6 +173,16 @@ void point_tables(const Geometry& g, double beta, int32_t qJ, int32_t qJp, int32
     double a[2];
     bond_weight(beta, qJ / 16.0, a[0], sgn[0]);
     bond_weight(beta, qJp / 16.0, a[1], sgn[1]);
+    if (g.paper) {
+        const int32_t A[2] = {fixed_q54(a[0]), fixed_q54(a[1])}, B = fixed_q54(beta * (qh / 16.0));
+        for (int cls = 0; cls < 2; ++cls)
+            for (int m = -2; m <= 2; ++m) out[cls * 5 + m + 2] = sigmoid_lut16(A[cls] * m);
+        const int nP = 2 * g.DJp + 1;
+        for (int nJ = -g.DJ; nJ <= g.DJ; ++nJ)
+            for (int nJp = -g.DJp; nJp <= g.DJp; ++nJp)
+                out[10 + (nJ + g.DJ) * nP + (nJp + g.DJp)] = sigmoid_lut16(B + A[0] * nJ + A[1] * nJp);
+        return;
+    }
     for (int cls = 0; cls < 2; ++cls)
         for (int m = -2; m <= 2; ++m) out[cls * 5 + m + 2] = accept_threshold(2.0 * a[cls] * m);
     const double hd = qh / 16.0;
@@ -269,6 +297,11 @@ int crbm_create(crbm_ctx** out, const crbm_params* p) {
         return rc;
     }
     Geometry& g = ctx->g;
+    if (p->precision != CRBM_PRECISION_EXACT && p->precision != CRBM_PRECISION_PAPER) {
+        delete ctx;
+        return fail(nullptr, CRBM_EINVAL, "unknown precision");
+    }
+    g.paper = p->precision == CRBM_PRECISION_PAPER ? 1 : 0;
     // AUTO: shared memory when the lattice, its hidden words and the tables fit
     // in one CTA's 227 KB, else the streamed layout (SS filters, even periodic L)
     ctx->layout = p->layout;
@@ -279,6 +312,11 @@ int crbm_create(crbm_ctx** out, const crbm_params* p) {
     if (ctx->layout == CRBM_LAYOUT_SMEM && p->L > CRBM_SMEM_MAX_L) {
         delete ctx;
         return fail(nullptr, CRBM_EINVAL, "SMEM layout needs L <= CRBM_SMEM_MAX_L");
+    }
+    if (g.paper && (!g.canonical || ctx->layout != CRBM_LAYOUT_SMEM)) {
+        delete ctx;
+        return fail(nullptr, CRBM_EUNSUPPORTED,
+                    "paper precision serves the ten SS filters on an even periodic lattice in the SMEM layout");
     }
     if (ctx->layout == CRBM_LAYOUT_STREAM && !g.canonical) {
         delete ctx;
@@ -504,6 +542,12 @@ int crbm_create(crbm_ctx** out, const crbm_params* p) {
                     hrow(i, (j + W - 1) % W), lo,   qh[3],                 ql[3],
                     ql[2],          0u,             0u,                    0u};
                 std::copy(rec, rec + kCellRec * 4, o);
+                if (g.paper) {  // the cell's row of visible draws replaces Q2.hi and Qv.hi
+                    const uint32_t pw = 4u * static_cast<uint32_t>(canon_smem_pw_offset(g)) +
+                                        256u * static_cast<uint32_t>(i * W + j);
+                    o[7] = pw;
+                    o[18] = pw;
+                }
             }
     }
     // Per-cell records of the generic SMEM sweep (layout in crbm_internal.h).
@@ -830,7 +874,7 @@ int crbm_save(crbm_ctx* ctx, void* buf, size_t* n) {
     int64_t hdr[16] = {0x4d425243 /* "CRBM" */, 1, ctx->g.L, ctx->n_chains, ctx->n_params,
                        static_cast<int64_t>(ctx->seed), ctx->sweeps, ctx->meas, ctx->sq_meas,
                        ctx->series_len, ctx->sq_every, ctx->measure_every, ctx->g.nb,
-                       ctx->g.periodic, ctx->swap_every, 0};
+                       ctx->g.periodic, ctx->swap_every, ctx->g.paper};
     char* p = static_cast<char*>(buf);
     std::memcpy(p, hdr, sizeof(hdr));
     cudaError_t e = cudaMemcpyAsync(p + 128, ctx->d.v, b_v, cudaMemcpyDeviceToHost, ctx->stream);
@@ -857,7 +901,8 @@ int crbm_load(crbm_ctx* ctx, const void* buf, size_t n) {
     if (hdr[0] != 0x4d425243 || hdr[1] != 1 || hdr[2] != ctx->g.L || hdr[3] != ctx->n_chains ||
         hdr[4] != ctx->n_params || hdr[5] != static_cast<int64_t>(ctx->seed) ||
         hdr[9] != ctx->series_len || hdr[10] != ctx->sq_every || hdr[11] != ctx->measure_every ||
-        hdr[12] != ctx->g.nb || hdr[13] != ctx->g.periodic || hdr[14] != ctx->swap_every)
+        hdr[12] != ctx->g.nb || hdr[13] != ctx->g.periodic || hdr[14] != ctx->swap_every ||
+        hdr[15] != ctx->g.paper)
         return fail(ctx, CRBM_EINVAL, "checkpoint does not match this context");
     const size_t npad = static_cast<size_t>(ctx->n_words) * 32, N = ctx->g.N;
     const size_t b_v = ctx->n_words * N * 4, b_s = npad * kNSum * 8,

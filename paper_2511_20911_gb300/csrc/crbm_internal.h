@@ -51,6 +51,8 @@ constexpr int kCanonSmemV = kAccWords + kCanonTab;
 //   [3] spins (0,0) (1,0) of the cell, hidden rows of the cell and of the cell above
 //   [4] hidden row of the cell to the left, rc.lo, Qv.hi, Qv.lo
 //   [5] Q2.lo, 0, 0, 0
+// In paper precision (two calls per cell) Q2 and Qv are not used: [1].w and
+// [4].z hold the byte offset of the cell's row of visible draws instead.
 constexpr int kCellRec = 6;
 // (class, second-endpoint flag) of the five filter slots of each spin
 // position (0,0), (0,1), (1,0), (1,1) in the canonical visible tables.
@@ -75,16 +77,23 @@ struct Geometry {
     int nTab;      // 10 hidden entries + nTv visible entries
     int n_real_bonds[2];  // bonds with both endpoints real, per class
     int vil;       // spin storage: 0 = [word][site], 1 = 64-chain words [group][site][2]
+    int paper;     // CRBM_PRECISION_PAPER: 16-bit thresholds and uniforms, two per Philox word
     int8_t r1[kMaxBonds], c1[kMaxBonds], r2[kMaxBonds], c2[kMaxBonds];
     uint8_t cls[kMaxBonds];
 };
 
-// Word offset of the records when the sweep copies them into shared memory:
-// after [kCanonSmemV][N][n_cells x 32][3 x 32 counters][33 segments][32 masks]
-// [32][32] replica tables, rounded up to 16 bytes.
-__host__ __device__ inline size_t canon_smem_rec_offset(const Geometry& g) {
+// Word offset, after [kCanonSmemV][N][n_cells x 32][3 x 32 counters]
+// [33 segments][32 masks][32][32] replica tables rounded up to 16 bytes, of
+// the paper-precision visible draws: [n_cells][32 lanes] pairs of words, the
+// two Philox words of tag 1 that carry a cell's four 16-bit visible uniforms
+// (drawn in the hidden half-step, read in the visible one).  The records
+// follow them when the sweep copies the records into shared memory.
+__host__ __device__ inline size_t canon_smem_pw_offset(const Geometry& g) {
     return (static_cast<size_t>(kCanonSmemV) + g.N + static_cast<size_t>(g.n_cells) * 32 + 96 + 33 + 32 + 64 + 3) &
            ~static_cast<size_t>(3);
+}
+__host__ __device__ inline size_t canon_smem_rec_offset(const Geometry& g) {
+    return canon_smem_pw_offset(g) + (g.paper ? static_cast<size_t>(g.n_cells) * 64 : 0);
 }
 
 // Generic SMEM-resident sweep (any filter list, odd L, open boundaries).

@@ -602,10 +602,10 @@ int ensure_chain_params(crbm_ctx* ctx) {
 
 int check_ctx(const crbm_ctx* ctx) {
     if (!ctx) return prop_fail(CRBM_EINVAL, "null context");
-    if (!ctx->g.canonical || ctx->layout != CRBM_LAYOUT_SMEM || ctx->swap_every > 0)
+    if (!ctx->g.canonical || ctx->layout != CRBM_LAYOUT_SMEM || ctx->swap_every > 0 || ctx->g.paper)
         return prop_fail(CRBM_EUNSUPPORTED,
                          "block proposals need the ten SS filters on an even periodic lattice, the SMEM "
-                         "layout and no replica exchange");
+                         "layout, exact precision and no replica exchange");
     return CRBM_OK;
 }
 

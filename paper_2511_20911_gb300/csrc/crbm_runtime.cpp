@@ -38,7 +38,8 @@ std::string shape_key(const crbm_ctx* ctx) {
     cudaGetDeviceProperties(&prop, ctx->device);
     std::ostringstream k;
     k << prop.name << "|sm" << prop.multiProcessorCount << "|L" << ctx->g.L << "|p" << ctx->g.periodic << "|c"
-      << ctx->g.canonical << "|nb" << ctx->g.nb << "|w" << ctx->n_words << "|x" << (ctx->swap_every > 0);
+      << ctx->g.canonical << "|nb" << ctx->g.nb << "|w" << ctx->n_words << "|x" << (ctx->swap_every > 0)
+      << "|q" << ctx->g.paper;
     std::string s = k.str();
     std::replace(s.begin(), s.end(), ' ', '_');
     return s;
@@ -198,9 +199,10 @@ int crbm_batch_create(crbm_batch** out, crbm_ctx* const* ctxs, int32_t n_ctx) {
     int warps = 1;
     for (int c = 0; c < n_ctx; ++c) {
         crbm_ctx* x = ctxs[c];
-        if (!x || x->layout != CRBM_LAYOUT_SMEM || !smem_ok(x) || x->stream != ctxs[0]->stream ||
+        if (!x || x->layout != CRBM_LAYOUT_SMEM || !smem_ok(x) || x->g.paper || x->stream != ctxs[0]->stream ||
             x->device != ctxs[0]->device || std::count(ctxs, ctxs + c, x)) {
-            g_batch_create_error = "batch members must be distinct SMEM-layout contexts on one device and stream";
+            g_batch_create_error =
+                "batch members must be distinct SMEM-layout, exact-precision contexts on one device and stream";
             delete b;
             return CRBM_EINVAL;
         }

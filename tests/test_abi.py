@@ -49,3 +49,28 @@ def test_workloads_shapes():
     w = workloads.grid_workload()
     assert w["n_chains"] == 3 * 16 * 16 * 16 and len(w["params"]["J"]) == 768
     assert all(abs(x * 16 - round(x * 16)) < 1e-12 for x in w["params"]["h"])
+
+
+def test_binding_struct_layout_matches_the_header(tmp_path):
+    """The ctypes mirror of crbm_params and crbm_bond has the C layout
+    (size and every field offset, as gcc lays out include/crbm.h)."""
+    import ctypes
+    import subprocess
+    import paper_2511_20911_gb300 as crbm
+    structs = {"crbm_params": crbm.crbm_params, "crbm_bond": crbm.crbm_bond}
+    lines = ['#include <stdio.h>', '#include <stddef.h>', '#include "crbm.h"', "int main(void) {"]
+    for name, cls in structs.items():
+        lines.append(f'printf("{name} sizeof %zu\\n", sizeof({name}));')
+        for field, _ in cls._fields_:
+            lines.append(f'printf("{name} {field} %zu\\n", offsetof({name}, {field}));')
+    lines.append("return 0; }")
+    src = tmp_path / "layout.c"
+    src.write_text("\n".join(lines))
+    exe = tmp_path / "layout"
+    subprocess.check_call(["gcc", "-std=c11", "-I", os.path.join(ROOT, "include"), str(src), "-o", str(exe)])
+    out = subprocess.run([str(exe)], capture_output=True, text=True, check=True).stdout.split("\n")
+    got = {tuple(l.split()[:2]): int(l.split()[2]) for l in out if l.strip()}
+    for name, cls in structs.items():
+        assert got[(name, "sizeof")] == ctypes.sizeof(cls), name
+        for field, _ in cls._fields_:
+            assert got[(name, field)] == getattr(cls, field).offset, (name, field)

@@ -45,9 +45,9 @@ CALLS_PER_CELL_PAPER = 2    # paper precision: 16-bit uniforms, two per Philox w
 # launch of k_sweep_canon_persistent (2000 sweeps of the L=18 grid), and one
 # streamed sweep of the L=384 lattice (k_stream_hidden + k_stream_visible).
 MEASURED_TRAFFIC = {
-    "grid": (8.62e6 + 0.62e6, "per launch; profiles/k_sweep_canon_persistent_L18_grid.md"),
+    "grid": (8.31e6 + 0.61e6, "per launch; profiles/k_sweep_canon_persistent_L18_grid.md"),
     "stream": (56.87e6 + 392.34e6 + 454.60e6 + 48.92e6, "per sweep (two launches); profiles/k_stream_L384.md"),
-    "grid_paper": (None, "per launch; not captured yet"),
+    "grid_paper": (8.53e6 + 0.63e6, "per launch; profiles/k_sweep_canon_persistent_L18_grid_paper.md"),
 }
 
 
@@ -266,7 +266,6 @@ def run_batch(args, rank, ws):
     calls = sum(4 * ((sp["L"] + 1) // 2) ** 2 * sp["n_chains"] for sp in specs) * S
     achieved = MUL_OPS_PER_CALL * calls / (t_total / K) / 1e12
     peak = SM_COUNT * IMUL_LANES_PER_SM_CLK * SM_MAX_MHZ * 1e6 / 1e12
-    traffic = MEASURED_TRAFFIC["grid_paper" if paper else args.workload]
     # end to end with host buffers: spins in, one batched step, observables out
     host = [m.get_spins() for m in members]
     torch.cuda.synchronize()

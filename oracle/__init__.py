@@ -122,43 +122,61 @@ def quantize(x):
     return q.value
 
 
+def shape(L, periodic=True):
+    """(Lr, Lc, pr, pc) from L = int or (rows, cols) and periodic = bool or
+    (rows axis, cols axis)."""
+    Lr, Lc = (int(L), int(L)) if np.isscalar(L) else (int(L[0]), int(L[1]))
+    pr, pc = ((bool(periodic),) * 2) if np.isscalar(periodic) else (bool(periodic[0]), bool(periodic[1]))
+    return Lr, Lc, int(pr), int(pc)
+
+
 def degrees(L, periodic=True, bonds=None):
     arr, nb = bonds_array(bonds)
     dj, djp = ctypes.c_int(), ctypes.c_int()
-    if lib().orc_degrees(L, int(periodic), arr, nb, ctypes.byref(dj), ctypes.byref(djp)):
+    Lr, Lc, pr, pc = shape(L, periodic)
+    if lib().orc_degrees_rect(Lr, Lc, pr, pc, arr, nb, ctypes.byref(dj), ctypes.byref(djp)):
         raise ValueError("bad model")
     return dj.value, djp.value
 
 
-def tables(L, J, Jp, h, beta, periodic=True, bonds=None, precision=PRECISION_EXACT):
-    """(Th[2][5], Tv[2DJ+1][2DJp+1]) uint32 for one parameter point."""
+def tables(L, J, Jp, h, beta, periodic=True, bonds=None, precision=PRECISION_EXACT, h_odd=None):
+    """(Th[2][5], Tv[2DJ+1][2DJp+1]) uint32 for one parameter point; with
+    h_odd, also the odd-column visible table as a third element."""
     arr, nb = bonds_array(bonds)
     dj, djp = degrees(L, periodic, bonds)
+    Lr, Lc, pr, pc = shape(L, periodic)
     th = np.zeros(10, np.uint32)
     tv = np.zeros((2 * dj + 1) * (2 * djp + 1), np.uint32)
-    rc = lib().orc_tables_ex(L, int(periodic), arr, nb, ctypes.c_double(J), ctypes.c_double(Jp),
-                             ctypes.c_double(h), ctypes.c_double(beta), int(precision),
-                             _p(th, ctypes.c_uint32), _p(tv, ctypes.c_uint32))
+    tvo = np.zeros_like(tv)
+    rc = lib().orc_tables_rect(Lr, Lc, pr, pc, arr, nb, ctypes.c_double(J), ctypes.c_double(Jp),
+                               ctypes.c_double(h), ctypes.c_double(h if h_odd is None else h_odd),
+                               ctypes.c_double(beta), int(precision), _p(th, ctypes.c_uint32),
+                               _p(tv, ctypes.c_uint32), _p(tvo, ctypes.c_uint32))
     if rc:
         raise ValueError("bad parameters")
-    return th.reshape(2, 5), tv.reshape(2 * dj + 1, 2 * djp + 1)
+    shp = (2 * dj + 1, 2 * djp + 1)
+    if h_odd is None:
+        return th.reshape(2, 5), tv.reshape(shp)
+    return th.reshape(2, 5), tv.reshape(shp), tvo.reshape(shp)
 
 
 def init_spins(L, chain_ids, seed):
     ids = np.ascontiguousarray(chain_ids, dtype=np.uint32)
-    out = np.zeros((len(ids), L, L), np.int8)
-    lib().orc_init(L, _p(ids, ctypes.c_uint32), len(ids), ctypes.c_uint64(seed),
-                   _p(out, ctypes.c_int8))
+    Lr, Lc, _, _ = shape(L)
+    out = np.zeros((len(ids), Lr, Lc), np.int8)
+    lib().orc_init_rect(Lr, Lc, _p(ids, ctypes.c_uint32), len(ids), ctypes.c_uint64(seed),
+                        _p(out, ctypes.c_int8))
     return out
 
 
 def counts(spins, L, periodic=True, bonds=None):
-    """Exact (N_J, N_J', M) of one configuration [L][L] of +-1."""
+    """Exact (N_J, N_J', M) of one configuration [Lr][Lc] of +-1."""
     arr, nb = bonds_array(bonds)
     v = np.ascontiguousarray(spins, dtype=np.int8)
+    Lr, Lc, pr, pc = shape(L, periodic)
     a, b, c = ctypes.c_int64(), ctypes.c_int64(), ctypes.c_int64()
-    lib().orc_counts(L, int(periodic), arr, nb, _p(v, ctypes.c_int8), ctypes.byref(a),
-                     ctypes.byref(b), ctypes.byref(c))
+    lib().orc_counts_rect(Lr, Lc, pr, pc, arr, nb, _p(v, ctypes.c_int8), ctypes.byref(a),
+                          ctypes.byref(b), ctypes.byref(c))
     return a.value, b.value, c.value
 
 
@@ -174,19 +192,21 @@ def run(L, params, chain_param, spins, seed, sweep0, n_sweeps, measure_every=1,
     J = np.ascontiguousarray(params["J"], np.float64)
     Jp = np.ascontiguousarray(params["Jp"], np.float64)
     h = np.ascontiguousarray(params["h"], np.float64)
+    h_odd = None if params.get("h_odd") is None else np.ascontiguousarray(params["h_odd"], np.float64)
     beta = np.ascontiguousarray(params["beta"], np.float64)
     cp = np.ascontiguousarray(chain_param, np.int32)
     n = len(cp)
-    assert spins.dtype == np.int8 and spins.flags.c_contiguous and spins.shape == (n, L, L)
+    Lr, Lc, pr, pc = shape(L, periodic)
+    assert spins.dtype == np.int8 and spins.flags.c_contiguous and spins.shape == (n, Lr, Lc)
     ids = np.arange(n, dtype=np.uint32) if chain_ids is None else np.ascontiguousarray(
         chain_ids, np.uint32)
     if sums is None:
         sums = np.zeros((n, NSUM), np.int64)
     series = np.zeros((n, series_cap, 3), np.int32) if series_cap > 0 else None
     if sq_every > 0 and sq is None:
-        sq = np.zeros((n, L, L), np.float64)
-    rc = lib().orc_run_ex(L, int(periodic), arr, nb, _p(J, ctypes.c_double), _p(Jp, ctypes.c_double),
-                       _p(h, ctypes.c_double), _p(beta, ctypes.c_double), len(J),
+        sq = np.zeros((n, Lr, Lc), np.float64)
+    rc = lib().orc_run_rect(Lr, Lc, pr, pc, arr, nb, _p(J, ctypes.c_double), _p(Jp, ctypes.c_double),
+                       _p(h, ctypes.c_double), _p(h_odd, ctypes.c_double), _p(beta, ctypes.c_double), len(J),
                        _p(cp, ctypes.c_int32), _p(ids, ctypes.c_uint32), n, ctypes.c_uint64(seed),
                        ctypes.c_int64(sweep0), ctypes.c_int64(n_sweeps), int(measure_every),
                        _p(spins, ctypes.c_int8), _p(sums, ctypes.c_int64),
@@ -218,12 +238,13 @@ def run_pt(L, params, chain_param, spins, slot_of_beta, seed, sweep0, n_sweeps, 
     beta = np.ascontiguousarray(params["beta"], np.float64)
     cp = np.ascontiguousarray(chain_param, np.int32)
     n = len(cp)
-    assert spins.dtype == np.int8 and spins.flags.c_contiguous and spins.shape == (n, L, L)
+    Lr, Lc, pr, pc = shape(L, periodic)
+    assert spins.dtype == np.int8 and spins.flags.c_contiguous and spins.shape == (n, Lr, Lc)
     assert slot_of_beta.dtype == np.int32 and slot_of_beta.flags.c_contiguous
     if sums is None:
         sums = np.zeros((n, NSUM), np.int64)
     series = np.zeros((n, series_cap, 3), np.int32) if series_cap > 0 else None
-    rc = lib().orc_run_pt_ex(L, int(periodic), arr, nb, _p(J, ctypes.c_double),
+    rc = lib().orc_run_pt_rect(Lr, Lc, pr, pc, arr, nb, _p(J, ctypes.c_double),
                           _p(Jp, ctypes.c_double), _p(h, ctypes.c_double),
                           _p(beta, ctypes.c_double), len(J), _p(cp, ctypes.c_int32), n,
                           ctypes.c_uint64(seed), ctypes.c_int64(sweep0), ctypes.c_int64(n_sweeps),

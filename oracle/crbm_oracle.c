@@ -76,17 +76,28 @@ int orc_canonical_bonds(orc_bond out[10]) {
 
 static int n_windows(int L) { return (L + 1) / 2; }
 
-/* Appendix, "Wrapper Module": a periodic lattice copies the first rows and
- * columns past the edge; an open one inserts zeros.  A zero-padded endpoint
- * is a null site (-1) that contributes nothing. */
-static int site_of(int L, int periodic, int i, int j, int r, int c) {
+/* A lattice of Lr rows by Lc columns with its own boundary along each axis
+ * (Sec. III: the hardware also runs open boundaries along the lateral
+ * direction only, for laterally confined strips).  Windows (i, j) with
+ * i < (Lr+1)/2, j < (Lc+1)/2; cell index i (Lc+1)/2 + j. */
+typedef struct {
+    int Lr, Lc, pr, pc;
+} orc_geom;
+
+/* Appendix, "Wrapper Module": a periodic axis copies its first rows (columns)
+ * past the edge; an open one inserts zeros.  A zero-padded endpoint is a null
+ * site (-1) that contributes nothing. */
+static int site_g(const orc_geom* g, int i, int j, int r, int c) {
     int R = 2 * i + r, C = 2 * j + c;
-    if (R >= L || C >= L) {
-        if (!periodic) return -1;
-        R %= L;
-        C %= L;
+    if (R >= g->Lr) {
+        if (!g->pr) return -1;
+        R %= g->Lr;
     }
-    return R * L + C;
+    if (C >= g->Lc) {
+        if (!g->pc) return -1;
+        C %= g->Lc;
+    }
+    return R * g->Lc + C;
 }
 
 static int check_model(int L, const orc_bond* bonds, int nb) {
@@ -132,28 +143,38 @@ uint32_t orc_threshold(double y) {
     return (uint32_t)t;
 }
 
-int orc_degrees(int L, int periodic, const orc_bond* bonds, int nb, int* DJ, int* DJp) {
-    if (check_model(L, bonds, nb)) return -1;
-    int W = n_windows(L);
-    int* deg = (int*)calloc((size_t)2 * L * L, sizeof(int));
+static int degrees_g(const orc_geom* g, const orc_bond* bonds, int nb, int* DJ, int* DJp) {
+    if (check_model(g->Lr, bonds, nb) || check_model(g->Lc, bonds, nb)) return -1;
+    int Wr = n_windows(g->Lr), Wc = n_windows(g->Lc), N = g->Lr * g->Lc;
+    int* deg = (int*)calloc((size_t)2 * N, sizeof(int));
     if (!deg) return -2;
-    for (int i = 0; i < W; ++i)
-        for (int j = 0; j < W; ++j)
+    for (int i = 0; i < Wr; ++i)
+        for (int j = 0; j < Wc; ++j)
             for (int k = 0; k < nb; ++k) {
-                int s1 = site_of(L, periodic, i, j, bonds[k].r1, bonds[k].c1);
-                int s2 = site_of(L, periodic, i, j, bonds[k].r2, bonds[k].c2);
-                if (s1 >= 0) deg[bonds[k].cls * L * L + s1]++;
-                if (s2 >= 0) deg[bonds[k].cls * L * L + s2]++;
+                int s1 = site_g(g, i, j, bonds[k].r1, bonds[k].c1);
+                int s2 = site_g(g, i, j, bonds[k].r2, bonds[k].c2);
+                if (s1 >= 0) deg[bonds[k].cls * N + s1]++;
+                if (s2 >= 0) deg[bonds[k].cls * N + s2]++;
             }
     int m0 = 0, m1 = 0;
-    for (int s = 0; s < L * L; ++s) {
+    for (int s = 0; s < N; ++s) {
         if (deg[s] > m0) m0 = deg[s];
-        if (deg[L * L + s] > m1) m1 = deg[L * L + s];
+        if (deg[N + s] > m1) m1 = deg[N + s];
     }
     free(deg);
     *DJ = m0;
     *DJp = m1;
     return 0;
+}
+
+int orc_degrees(int L, int periodic, const orc_bond* bonds, int nb, int* DJ, int* DJp) {
+    orc_geom g = {L, L, periodic, periodic};
+    return degrees_g(&g, bonds, nb, DJ, DJp);
+}
+
+int orc_degrees_rect(int Lr, int Lc, int pr, int pc, const orc_bond* bonds, int nb, int* DJ, int* DJp) {
+    orc_geom g = {Lr, Lc, pr, pc};
+    return degrees_g(&g, bonds, nb, DJ, DJp);
 }
 
 /* Eq. (9): P(H=1|V) = sigmoid of the forward cross-correlation; with +-1
@@ -184,87 +205,131 @@ int orc_tables(int L, int periodic, const orc_bond* bonds, int nb, double J, dou
     return orc_tables_ex(L, periodic, bonds, nb, J, Jp, h, beta, ORC_PRECISION_EXACT, Th, Tv);
 }
 
-int orc_tables_ex(int L, int periodic, const orc_bond* bonds, int nb, double J, double Jp,
-                  double h, double beta, int precision, uint32_t* Th, uint32_t* Tv) {
+/* Visible table of one field value h (Eq. 10), exact or paper precision. */
+static void visible_table(int DJ, int DJp, const double a[2], double beta, double hd, int precision,
+                          uint32_t* Tv) {
+    int nP = 2 * DJp + 1;
+    if (precision == ORC_PRECISION_PAPER) {
+        int32_t A[2] = {orc_q54(a[0]), orc_q54(a[1])}, B = orc_q54(beta * hd);
+        for (int nJ = -DJ; nJ <= DJ; ++nJ)
+            for (int nJp = -DJp; nJp <= DJp; ++nJp)
+                Tv[(nJ + DJ) * nP + (nJp + DJp)] = orc_lut16(B + A[0] * nJ + A[1] * nJp);
+        return;
+    }
+    for (int nJ = -DJ; nJ <= DJ; ++nJ)
+        for (int nJp = -DJp; nJp <= DJp; ++nJp) {
+            double x = beta * hd + a[0] * nJ + a[1] * nJp;
+            Tv[(nJ + DJ) * nP + (nJp + DJp)] = orc_threshold(2.0 * x);
+        }
+}
+
+/* Tables of one parameter point; Tv_odd (may be NULL) is the visible table of
+ * the odd columns, whose field is h_odd (the appendix's option of separate
+ * odd- and even-column visible biases). */
+static int tables_g(const orc_geom* g, const orc_bond* bonds, int nb, double J, double Jp, double h,
+                    double h_odd, double beta, int precision, uint32_t* Th, uint32_t* Tv, uint32_t* Tv_odd) {
     int DJ, DJp;
     if (precision != ORC_PRECISION_EXACT && precision != ORC_PRECISION_PAPER) return -1;
     if (precision == ORC_PRECISION_PAPER && nb > 10) return -1;
-    if (orc_degrees(L, periodic, bonds, nb, &DJ, &DJp)) return -1;
-    int32_t qJ, qJp, qh;
-    if (orc_quantize(J, &qJ) || orc_quantize(Jp, &qJp) || orc_quantize(h, &qh)) return -1;
+    if (degrees_g(g, bonds, nb, &DJ, &DJp)) return -1;
+    int32_t qJ, qJp, qh, qho;
+    if (orc_quantize(J, &qJ) || orc_quantize(Jp, &qJp) || orc_quantize(h, &qh) || orc_quantize(h_odd, &qho))
+        return -1;
     if (!(beta >= 0.0) || beta > 1.0e6) return -1;
     double Jd = qJ / 16.0, Jpd = qJp / 16.0, hd = qh / 16.0;
     double a[2];
     int s[2];
     orc_weight(beta, Jd, &a[0], &s[0]);
     orc_weight(beta, Jpd, &a[1], &s[1]);
-    int nP = 2 * DJp + 1;
     if (precision == ORC_PRECISION_PAPER) {
-        int32_t A[2] = {orc_q54(a[0]), orc_q54(a[1])}, B = orc_q54(beta * hd);
+        int32_t A[2] = {orc_q54(a[0]), orc_q54(a[1])};
         for (int cls = 0; cls < 2; ++cls)
             for (int m = -2; m <= 2; ++m) Th[cls * 5 + (m + 2)] = orc_lut16(A[cls] * m);
-        for (int nJ = -DJ; nJ <= DJ; ++nJ)
-            for (int nJp = -DJp; nJp <= DJp; ++nJp)
-                Tv[(nJ + DJ) * nP + (nJp + DJp)] = orc_lut16(B + A[0] * nJ + A[1] * nJp);
-        return 0;
+    } else {
+        for (int cls = 0; cls < 2; ++cls)
+            for (int m = -2; m <= 2; ++m) Th[cls * 5 + (m + 2)] = orc_threshold(2.0 * a[cls] * m);
     }
-    for (int cls = 0; cls < 2; ++cls)
-        for (int m = -2; m <= 2; ++m) Th[cls * 5 + (m + 2)] = orc_threshold(2.0 * a[cls] * m);
-    for (int nJ = -DJ; nJ <= DJ; ++nJ)
-        for (int nJp = -DJp; nJp <= DJp; ++nJp) {
-            double x = beta * hd + a[0] * nJ + a[1] * nJp;
-            Tv[(nJ + DJ) * nP + (nJp + DJp)] = orc_threshold(2.0 * x);
-        }
+    visible_table(DJ, DJp, a, beta, hd, precision, Tv);
+    if (Tv_odd) visible_table(DJ, DJp, a, beta, qho / 16.0, precision, Tv_odd);
     return 0;
 }
 
+int orc_tables_ex(int L, int periodic, const orc_bond* bonds, int nb, double J, double Jp,
+                  double h, double beta, int precision, uint32_t* Th, uint32_t* Tv) {
+    orc_geom g = {L, L, periodic, periodic};
+    return tables_g(&g, bonds, nb, J, Jp, h, h, beta, precision, Th, Tv, NULL);
+}
+
+int orc_tables_rect(int Lr, int Lc, int pr, int pc, const orc_bond* bonds, int nb, double J, double Jp,
+                    double h, double h_odd, double beta, int precision, uint32_t* Th, uint32_t* Tv,
+                    uint32_t* Tv_odd) {
+    orc_geom g = {Lr, Lc, pr, pc};
+    return tables_g(&g, bonds, nb, J, Jp, h, h_odd, beta, precision, Th, Tv, Tv_odd);
+}
+
 /* ------------------------------------------------------ configuration */
-void orc_init(int L, const uint32_t* chain_ids, int n_chains, uint64_t seed, int8_t* spins) {
-    int W = n_windows(L);
+void orc_init_rect(int Lr, int Lc, const uint32_t* chain_ids, int n_chains, uint64_t seed, int8_t* spins) {
+    int Wc = n_windows(Lc);
     for (int c = 0; c < n_chains; ++c)
-        for (int R = 0; R < L; ++R)
-            for (int C = 0; C < L; ++C) {
-                uint32_t cell = (uint32_t)((R >> 1) * W + (C >> 1));
+        for (int R = 0; R < Lr; ++R)
+            for (int C = 0; C < Lc; ++C) {
+                uint32_t cell = (uint32_t)((R >> 1) * Wc + (C >> 1));
                 uint32_t u = philox_word(cell, 0u, chain_ids[c], ORC_TAG_INIT, seed,
                                          2 * (R & 1) + (C & 1));
-                spins[(size_t)c * L * L + R * L + C] = (u < 0x80000000u) ? 1 : -1;
+                spins[(size_t)c * Lr * Lc + R * Lc + C] = (u < 0x80000000u) ? 1 : -1;
             }
 }
 
+void orc_init(int L, const uint32_t* chain_ids, int n_chains, uint64_t seed, int8_t* spins) {
+    orc_init_rect(L, L, chain_ids, n_chains, seed, spins);
+}
+
 /* Eq. (1) on the bond multiset generated by the stride-2 windows. */
-void orc_counts(int L, int periodic, const orc_bond* bonds, int nb, const int8_t* v,
-                int64_t* NJ, int64_t* NJp, int64_t* M) {
-    int W = n_windows(L);
+static void counts_g(const orc_geom* g, const orc_bond* bonds, int nb, const int8_t* v, int64_t* NJ,
+                     int64_t* NJp, int64_t* M) {
+    int Wr = n_windows(g->Lr), Wc = n_windows(g->Lc);
     int64_t n[2] = {0, 0}, m = 0;
-    for (int i = 0; i < W; ++i)
-        for (int j = 0; j < W; ++j)
+    for (int i = 0; i < Wr; ++i)
+        for (int j = 0; j < Wc; ++j)
             for (int k = 0; k < nb; ++k) {
-                int s1 = site_of(L, periodic, i, j, bonds[k].r1, bonds[k].c1);
-                int s2 = site_of(L, periodic, i, j, bonds[k].r2, bonds[k].c2);
+                int s1 = site_g(g, i, j, bonds[k].r1, bonds[k].c1);
+                int s2 = site_g(g, i, j, bonds[k].r2, bonds[k].c2);
                 if (s1 < 0 || s2 < 0) continue;
                 n[bonds[k].cls] += v[s1] * v[s2];
             }
-    for (int s = 0; s < L * L; ++s) m += v[s];
+    for (int s = 0; s < g->Lr * g->Lc; ++s) m += v[s];
     *NJ = n[0];
     *NJp = n[1];
     *M = m;
 }
 
+void orc_counts(int L, int periodic, const orc_bond* bonds, int nb, const int8_t* v,
+                int64_t* NJ, int64_t* NJp, int64_t* M) {
+    orc_geom g = {L, L, periodic, periodic};
+    counts_g(&g, bonds, nb, v, NJ, NJp, M);
+}
+
+void orc_counts_rect(int Lr, int Lc, int pr, int pc, const orc_bond* bonds, int nb, const int8_t* v,
+                     int64_t* NJ, int64_t* NJp, int64_t* M) {
+    orc_geom g = {Lr, Lc, pr, pc};
+    counts_g(&g, bonds, nb, v, NJ, NJp, M);
+}
+
 /* Sec. IV.B, Eq. (11): S(q) = sum_ij <s_i s_j> e^{i q.(R_i - R_j)}, reported
  * per spin: |sum_r s_r e^{i q.r}|^2 / N at q = 2 pi (nR, nC) / L. */
-static void add_structure_factor(int L, const int8_t* v, double* sq) {
+static void add_structure_factor(int Lr, int Lc, const int8_t* v, double* sq) {
     const double twopi = 6.283185307179586476925286766559;
-    int N = L * L;
-    for (int nR = 0; nR < L; ++nR)
-        for (int nC = 0; nC < L; ++nC) {
+    int N = Lr * Lc;
+    for (int nR = 0; nR < Lr; ++nR)
+        for (int nC = 0; nC < Lc; ++nC) {
             double re = 0.0, im = 0.0;
-            for (int R = 0; R < L; ++R)
-                for (int C = 0; C < L; ++C) {
-                    double ph = twopi * (double)(nR * R + nC * C) / (double)L;
-                    re += v[R * L + C] * cos(ph);
-                    im += v[R * L + C] * sin(ph);
+            for (int R = 0; R < Lr; ++R)
+                for (int C = 0; C < Lc; ++C) {
+                    double ph = twopi * ((double)(nR * R) / (double)Lr + (double)(nC * C) / (double)Lc);
+                    re += v[R * Lc + C] * cos(ph);
+                    im += v[R * Lc + C] * sin(ph);
                 }
-            sq[nR * L + nC] += (re * re + im * im) / (double)N;
+            sq[nR * Lc + nC] += (re * re + im * im) / (double)N;
         }
 }
 
@@ -272,6 +337,7 @@ static void add_structure_factor(int L, const int8_t* v, double* sq) {
 typedef struct {
     uint32_t Th[10];
     uint32_t* Tv;
+    uint32_t* Tv_odd;  /* visible table of the odd columns */
     int s[2];
     int paper;  /* ORC_PRECISION_PAPER: 16-bit uniforms and thresholds */
 } orc_point;
@@ -292,18 +358,18 @@ static int draw_below(const orc_point* pt, uint32_t cell, uint32_t sweep, uint32
  * hidden units.  The Philox counter (cell, sweep, chain, tag) fixes every draw:
  * hidden bond k of cell (i, j) uses word k&3 of tag k>>2; the spin at
  * window offset (r, c) uses word 2r+c of tag ORC_TAG_VIS. */
-static void one_sweep(int L, int periodic, const orc_bond* bonds, int nb, const orc_point* pt,
+static void one_sweep(const orc_geom* g, const orc_bond* bonds, int nb, const orc_point* pt,
                       int DJ, int DJp, uint32_t chain, uint32_t sweep, uint64_t seed, int8_t* v,
                       int8_t* hid, int* field) {
-    int W = n_windows(L);
+    int Wr = n_windows(g->Lr), Wc = n_windows(g->Lc), N = g->Lr * g->Lc;
     /* hidden | visible */
-    for (int i = 0; i < W; ++i)
-        for (int j = 0; j < W; ++j) {
-            uint32_t cell = (uint32_t)(i * W + j);
+    for (int i = 0; i < Wr; ++i)
+        for (int j = 0; j < Wc; ++j) {
+            uint32_t cell = (uint32_t)(i * Wc + j);
             for (int k = 0; k < nb; ++k) {
                 const orc_bond* b = &bonds[k];
-                int s1 = site_of(L, periodic, i, j, b->r1, b->c1);
-                int s2 = site_of(L, periodic, i, j, b->r2, b->c2);
+                int s1 = site_g(g, i, j, b->r1, b->c1);
+                int s2 = site_g(g, i, j, b->r2, b->c2);
                 int m = (s1 >= 0 ? v[s1] : 0) + pt->s[b->cls] * (s2 >= 0 ? v[s2] : 0);
                 uint32_t t = pt->Th[b->cls * 5 + (m + 2)];
                 int up;
@@ -318,26 +384,27 @@ static void one_sweep(int L, int periodic, const orc_bond* bonds, int nb, const 
         }
     /* visible | hidden: zero-padded reverse correlation = scatter of every
      * hidden unit onto its two endpoints with coefficients (+1, s). */
-    memset(field, 0, sizeof(int) * 2 * L * L);
-    for (int i = 0; i < W; ++i)
-        for (int j = 0; j < W; ++j) {
-            int cell = i * W + j;
+    memset(field, 0, sizeof(int) * 2 * N);
+    for (int i = 0; i < Wr; ++i)
+        for (int j = 0; j < Wc; ++j) {
+            int cell = i * Wc + j;
             for (int k = 0; k < nb; ++k) {
                 const orc_bond* b = &bonds[k];
-                int s1 = site_of(L, periodic, i, j, b->r1, b->c1);
-                int s2 = site_of(L, periodic, i, j, b->r2, b->c2);
+                int s1 = site_g(g, i, j, b->r1, b->c1);
+                int s2 = site_g(g, i, j, b->r2, b->c2);
                 int hv = hid[cell * nb + k];
-                if (s1 >= 0) field[b->cls * L * L + s1] += hv;
-                if (s2 >= 0) field[b->cls * L * L + s2] += pt->s[b->cls] * hv;
+                if (s1 >= 0) field[b->cls * N + s1] += hv;
+                if (s2 >= 0) field[b->cls * N + s2] += pt->s[b->cls] * hv;
             }
         }
     int nP = 2 * DJp + 1;
-    for (int R = 0; R < L; ++R)
-        for (int C = 0; C < L; ++C) {
-            int s = R * L + C;
-            uint32_t cell = (uint32_t)((R >> 1) * W + (C >> 1));
+    for (int R = 0; R < g->Lr; ++R)
+        for (int C = 0; C < g->Lc; ++C) {
+            int s = R * g->Lc + C;
+            uint32_t cell = (uint32_t)((R >> 1) * Wc + (C >> 1));
             int x = 2 * (R & 1) + (C & 1);
-            uint32_t t = pt->Tv[(field[s] + DJ) * nP + (field[L * L + s] + DJp)];
+            const uint32_t* Tv = (C & 1) ? pt->Tv_odd : pt->Tv;
+            uint32_t t = Tv[(field[s] + DJ) * nP + (field[N + s] + DJp)];
             int up = pt->paper ? draw_below(pt, cell, sweep, chain, 1u, 1 + (x >> 1), x & 1, seed, t)
                                : draw_below(pt, cell, sweep, chain, ORC_TAG_VIS, x, 0, seed, t);
             v[s] = up ? 1 : -1;
@@ -354,13 +421,13 @@ int orc_run(int L, int periodic, const orc_bond* bonds, int nb, const double* J,
                       series_cap, sq_every, sq, ORC_PRECISION_EXACT);
 }
 
-int orc_run_ex(int L, int periodic, const orc_bond* bonds, int nb, const double* J,
-               const double* Jp, const double* h, const double* beta, int n_params,
-               const int32_t* chain_param, const uint32_t* chain_ids, int n_chains, uint64_t seed,
-               int64_t sweep0, int64_t n_sweeps, int measure_every, int8_t* spins, int64_t* sums,
-               int32_t* series, int64_t series_cap, int sq_every, double* sq, int precision) {
+static int run_g(const orc_geom* g, const orc_bond* bonds, int nb, const double* J, const double* Jp,
+                 const double* h, const double* h_odd, const double* beta, int n_params,
+                 const int32_t* chain_param, const uint32_t* chain_ids, int n_chains, uint64_t seed,
+                 int64_t sweep0, int64_t n_sweeps, int measure_every, int8_t* spins, int64_t* sums,
+                 int32_t* series, int64_t series_cap, int sq_every, double* sq, int precision) {
     int DJ, DJp;
-    if (orc_degrees(L, periodic, bonds, nb, &DJ, &DJp)) return -1;
+    if (degrees_g(g, bonds, nb, &DJ, &DJp)) return -1;
     if (n_params < 1 || n_chains < 0 || n_sweeps < 0 || sweep0 < 0 ||
         sweep0 + n_sweeps > 4294967295LL || measure_every < 0 || sq_every < 0)
         return -1;
@@ -368,7 +435,7 @@ int orc_run_ex(int L, int periodic, const orc_bond* bonds, int nb, const double*
         if (chain_param[c] < 0 || chain_param[c] >= n_params) return -1;
     int nTv = (2 * DJ + 1) * (2 * DJp + 1);
     orc_point* pts = (orc_point*)calloc((size_t)n_params, sizeof(orc_point));
-    uint32_t* tv = (uint32_t*)calloc((size_t)n_params * nTv, sizeof(uint32_t));
+    uint32_t* tv = (uint32_t*)calloc((size_t)n_params * nTv * 2, sizeof(uint32_t));
     if (!pts || !tv) {
         free(pts);
         free(tv);
@@ -376,10 +443,11 @@ int orc_run_ex(int L, int periodic, const orc_bond* bonds, int nb, const double*
     }
     int err = 0;
     for (int p = 0; p < n_params; ++p) {
-        pts[p].Tv = tv + (size_t)p * nTv;
+        pts[p].Tv = tv + (size_t)p * 2 * nTv;
+        pts[p].Tv_odd = pts[p].Tv + nTv;
         pts[p].paper = precision == ORC_PRECISION_PAPER;
-        if (orc_tables_ex(L, periodic, bonds, nb, J[p], Jp[p], h[p], beta[p], precision, pts[p].Th,
-                          pts[p].Tv))
+        if (tables_g(g, bonds, nb, J[p], Jp[p], h[p], h_odd ? h_odd[p] : h[p], beta[p], precision, pts[p].Th,
+                     pts[p].Tv, pts[p].Tv_odd))
             err = -1;
         int32_t q;
         double a;
@@ -393,20 +461,19 @@ int orc_run_ex(int L, int periodic, const orc_bond* bonds, int nb, const double*
         free(tv);
         return -1;
     }
-    int W = n_windows(L);
-    int N = L * L;
+    int N = g->Lr * g->Lc;
+    int n_cells = n_windows(g->Lr) * n_windows(g->Lc);
 #pragma omp parallel for schedule(dynamic, 1)
     for (int c = 0; c < n_chains; ++c) {
         int8_t* v = spins + (size_t)c * N;
-        int8_t* hid = (int8_t*)malloc((size_t)W * W * nb);
+        int8_t* hid = (int8_t*)malloc((size_t)n_cells * nb);
         int* field = (int*)malloc(sizeof(int) * 2 * N);
         const orc_point* pt = &pts[chain_param[c]];
         for (int64_t t = sweep0; t < sweep0 + n_sweeps; ++t) {
-            one_sweep(L, periodic, bonds, nb, pt, DJ, DJp, chain_ids[c], (uint32_t)t, seed, v, hid,
-                      field);
+            one_sweep(g, bonds, nb, pt, DJ, DJp, chain_ids[c], (uint32_t)t, seed, v, hid, field);
             if (measure_every > 0 && (t + 1) % measure_every == 0 && sums) {
                 int64_t nJ, nJp, M;
-                orc_counts(L, periodic, bonds, nb, v, &nJ, &nJp, &M);
+                counts_g(g, bonds, nb, v, &nJ, &nJp, &M);
                 int64_t* s = sums + (size_t)c * ORC_NSUM;
                 if (series && s[0] < series_cap) {
                     int32_t* e = series + ((size_t)c * series_cap + s[0]) * 3;
@@ -427,7 +494,7 @@ int orc_run_ex(int L, int periodic, const orc_bond* bonds, int nb, const double*
                 s[10] += nJp * M;
             }
             if (sq_every > 0 && (t + 1) % sq_every == 0 && sq)
-                add_structure_factor(L, v, sq + (size_t)c * N);
+                add_structure_factor(g->Lr, g->Lc, v, sq + (size_t)c * N);
         }
         free(hid);
         free(field);
@@ -435,6 +502,26 @@ int orc_run_ex(int L, int periodic, const orc_bond* bonds, int nb, const double*
     free(pts);
     free(tv);
     return 0;
+}
+
+int orc_run_ex(int L, int periodic, const orc_bond* bonds, int nb, const double* J,
+               const double* Jp, const double* h, const double* beta, int n_params,
+               const int32_t* chain_param, const uint32_t* chain_ids, int n_chains, uint64_t seed,
+               int64_t sweep0, int64_t n_sweeps, int measure_every, int8_t* spins, int64_t* sums,
+               int32_t* series, int64_t series_cap, int sq_every, double* sq, int precision) {
+    orc_geom g = {L, L, periodic, periodic};
+    return run_g(&g, bonds, nb, J, Jp, h, NULL, beta, n_params, chain_param, chain_ids, n_chains, seed, sweep0,
+                 n_sweeps, measure_every, spins, sums, series, series_cap, sq_every, sq, precision);
+}
+
+int orc_run_rect(int Lr, int Lc, int pr, int pc, const orc_bond* bonds, int nb, const double* J,
+                 const double* Jp, const double* h, const double* h_odd, const double* beta, int n_params,
+                 const int32_t* chain_param, const uint32_t* chain_ids, int n_chains, uint64_t seed,
+                 int64_t sweep0, int64_t n_sweeps, int measure_every, int8_t* spins, int64_t* sums,
+                 int32_t* series, int64_t series_cap, int sq_every, double* sq, int precision) {
+    orc_geom g = {Lr, Lc, pr, pc};
+    return run_g(&g, bonds, nb, J, Jp, h, h_odd, beta, n_params, chain_param, chain_ids, n_chains, seed, sweep0,
+                 n_sweeps, measure_every, spins, sums, series, series_cap, sq_every, sq, precision);
 }
 
 /* ------------------------------------------------- parallel tempering */
@@ -458,14 +545,14 @@ int orc_run_pt(int L, int periodic, const orc_bond* bonds, int nb, const double*
                          series, series_cap, ORC_PRECISION_EXACT);
 }
 
-int orc_run_pt_ex(int L, int periodic, const orc_bond* bonds, int nb, const double* J,
-                  const double* Jp, const double* h, const double* beta, int n_params,
-                  const int32_t* chain_param, int n_chains, uint64_t seed, int64_t sweep0,
-                  int64_t n_sweeps, int measure_every, int swap_every, int8_t* spins,
-                  int32_t* slot_of_beta, int64_t* sums, int32_t* series, int64_t series_cap,
-                  int precision) {
+static int run_pt_g(const orc_geom* g, const orc_bond* bonds, int nb, const double* J,
+                    const double* Jp, const double* h, const double* beta, int n_params,
+                    const int32_t* chain_param, int n_chains, uint64_t seed, int64_t sweep0,
+                    int64_t n_sweeps, int measure_every, int swap_every, int8_t* spins,
+                    int32_t* slot_of_beta, int64_t* sums, int32_t* series, int64_t series_cap,
+                    int precision) {
     if (n_chains <= 0 || n_chains % 32 || swap_every <= 0 || measure_every < 0) return -1;
-    int n_lad = n_chains / 32, N = L * L;
+    int n_lad = n_chains / 32, N = g->Lr * g->Lc;
     for (int l = 0; l < n_lad; ++l) {
         const int32_t* cp = chain_param + 32 * l;
         for (int k = 0; k < 32; ++k) {
@@ -475,7 +562,7 @@ int orc_run_pt_ex(int L, int periodic, const orc_bond* bonds, int nb, const doub
         }
     }
     int DJ, DJp;
-    if (orc_degrees(L, periodic, bonds, nb, &DJ, &DJp)) return -1;
+    if (degrees_g(g, bonds, nb, &DJ, &DJp)) return -1;
     int nTv = (2 * DJ + 1) * (2 * DJp + 1);
     orc_point* pts = (orc_point*)calloc((size_t)n_params, sizeof(orc_point));
     uint32_t* tv = (uint32_t*)calloc((size_t)n_params * nTv, sizeof(uint32_t));
@@ -488,8 +575,8 @@ int orc_run_pt_ex(int L, int periodic, const orc_bond* bonds, int nb, const doub
     for (int p = 0; p < n_params; ++p) {
         pts[p].Tv = tv + (size_t)p * nTv;
         pts[p].paper = precision == ORC_PRECISION_PAPER;
-        if (orc_tables_ex(L, periodic, bonds, nb, J[p], Jp[p], h[p], beta[p], precision, pts[p].Th,
-                          pts[p].Tv))
+        pts[p].Tv_odd = pts[p].Tv;
+        if (tables_g(g, bonds, nb, J[p], Jp[p], h[p], h[p], beta[p], precision, pts[p].Th, pts[p].Tv, NULL))
             err = 1;
         int32_t qq;
         double a;
@@ -503,10 +590,10 @@ int orc_run_pt_ex(int L, int periodic, const orc_bond* bonds, int nb, const doub
         free(tv);
         return -1;
     }
-    int W = n_windows(L);
+    int n_cells = n_windows(g->Lr) * n_windows(g->Lc);
 #pragma omp parallel for schedule(dynamic, 1)
     for (int l = 0; l < n_lad; ++l) {
-        int8_t* hid = (int8_t*)malloc((size_t)W * W * nb);
+        int8_t* hid = (int8_t*)malloc((size_t)n_cells * nb);
         int* field = (int*)malloc(sizeof(int) * 2 * N);
         const int32_t* cp = chain_param + 32 * l;
         int32_t* sob = slot_of_beta + 32 * l;
@@ -518,12 +605,11 @@ int orc_run_pt_ex(int L, int periodic, const orc_bond* bonds, int nb, const doub
             int bos[32];
             for (int k = 0; k < 32; ++k) bos[sob[k]] = k;
             for (int r = 0; r < 32; ++r)
-                one_sweep(L, periodic, bonds, nb, &pts[cp[bos[r]]], DJ, DJp, (uint32_t)(32 * l + r),
+                one_sweep(g, bonds, nb, &pts[cp[bos[r]]], DJ, DJp, (uint32_t)(32 * l + r),
                           (uint32_t)t, seed, spins + (size_t)(32 * l + r) * N, hid, field);
             int64_t nJ[32], nP[32], M[32], E[32];
             for (int r = 0; r < 32; ++r) {
-                orc_counts(L, periodic, bonds, nb, spins + (size_t)(32 * l + r) * N, &nJ[r],
-                           &nP[r], &M[r]);
+                counts_g(g, bonds, nb, spins + (size_t)(32 * l + r) * N, &nJ[r], &nP[r], &M[r]);
                 E[r] = (int64_t)q[0] * nJ[r] + (int64_t)q[1] * nP[r] - (int64_t)q[2] * M[r];
             }
             if (measure_every > 0 && (t + 1) % measure_every == 0 && sums) {
@@ -576,6 +662,28 @@ int orc_run_pt_ex(int L, int periodic, const orc_bond* bonds, int nb, const doub
     free(pts);
     free(tv);
     return 0;
+}
+
+int orc_run_pt_ex(int L, int periodic, const orc_bond* bonds, int nb, const double* J,
+                  const double* Jp, const double* h, const double* beta, int n_params,
+                  const int32_t* chain_param, int n_chains, uint64_t seed, int64_t sweep0,
+                  int64_t n_sweeps, int measure_every, int swap_every, int8_t* spins,
+                  int32_t* slot_of_beta, int64_t* sums, int32_t* series, int64_t series_cap,
+                  int precision) {
+    orc_geom g = {L, L, periodic, periodic};
+    return run_pt_g(&g, bonds, nb, J, Jp, h, beta, n_params, chain_param, n_chains, seed, sweep0, n_sweeps,
+                    measure_every, swap_every, spins, slot_of_beta, sums, series, series_cap, precision);
+}
+
+int orc_run_pt_rect(int Lr, int Lc, int pr, int pc, const orc_bond* bonds, int nb, const double* J,
+                    const double* Jp, const double* h, const double* beta, int n_params,
+                    const int32_t* chain_param, int n_chains, uint64_t seed, int64_t sweep0,
+                    int64_t n_sweeps, int measure_every, int swap_every, int8_t* spins,
+                    int32_t* slot_of_beta, int64_t* sums, int32_t* series, int64_t series_cap,
+                    int precision) {
+    orc_geom g = {Lr, Lc, pr, pc};
+    return run_pt_g(&g, bonds, nb, J, Jp, h, beta, n_params, chain_param, n_chains, seed, sweep0, n_sweeps,
+                    measure_every, swap_every, spins, slot_of_beta, sums, series, series_cap, precision);
 }
 
 void orc_set_threads(int n) {

@@ -112,6 +112,35 @@ int orc_get_threads(void);
  * precision; the others are ORC_PRECISION_EXACT. */
 #define ORC_PRECISION_EXACT 0
 #define ORC_PRECISION_PAPER 1
+
+/* ---- rectangular lattices, a boundary per axis, odd-column field ----------
+ * Sec. III runs laterally confined strips (open boundaries along one axis)
+ * and the appendix lets odd and even columns take different visible biases.
+ * The _rect functions take Lr rows x Lc columns, pr / pc = 1 for a periodic
+ * row (vertical) / column (horizontal) axis, and (for the sampler) h_odd[p],
+ * the field of the odd columns (NULL: h on every column).  Windows (i, j),
+ * i < (Lr+1)/2, j < (Lc+1)/2; cell index i (Lc+1)/2 + j; spins [R][C] with
+ * R < Lr, C < Lc.  The square functions are the _rect ones with Lr = Lc = L,
+ * pr = pc = periodic and no odd-column field.  Replica exchange needs equal
+ * fields on both column parities (its energies use the total M). */
+int orc_degrees_rect(int Lr, int Lc, int pr, int pc, const orc_bond* bonds, int nb, int* DJ, int* DJp);
+int orc_tables_rect(int Lr, int Lc, int pr, int pc, const orc_bond* bonds, int nb, double J, double Jp,
+                    double h, double h_odd, double beta, int precision, uint32_t* Th, uint32_t* Tv,
+                    uint32_t* Tv_odd);
+void orc_init_rect(int Lr, int Lc, const uint32_t* chain_ids, int n_chains, uint64_t seed, int8_t* spins);
+void orc_counts_rect(int Lr, int Lc, int pr, int pc, const orc_bond* bonds, int nb, const int8_t* v,
+                     int64_t* NJ, int64_t* NJp, int64_t* M);
+int orc_run_rect(int Lr, int Lc, int pr, int pc, const orc_bond* bonds, int nb, const double* J,
+                 const double* Jp, const double* h, const double* h_odd, const double* beta, int n_params,
+                 const int32_t* chain_param, const uint32_t* chain_ids, int n_chains, uint64_t seed,
+                 int64_t sweep0, int64_t n_sweeps, int measure_every, int8_t* spins, int64_t* sums,
+                 int32_t* series, int64_t series_cap, int sq_every, double* sq, int precision);
+int orc_run_pt_rect(int Lr, int Lc, int pr, int pc, const orc_bond* bonds, int nb, const double* J,
+                    const double* Jp, const double* h, const double* beta, int n_params,
+                    const int32_t* chain_param, int n_chains, uint64_t seed, int64_t sweep0,
+                    int64_t n_sweeps, int measure_every, int swap_every, int8_t* spins,
+                    int32_t* slot_of_beta, int64_t* sums, int32_t* series, int64_t series_cap,
+                    int precision);
 int32_t orc_q54(double x);
 uint32_t orc_lut16(int32_t acc);
 int orc_tables_ex(int L, int periodic, const orc_bond* bonds, int nb,

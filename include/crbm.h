@@ -62,6 +62,10 @@ extern "C" {
 #define CRBM_SMEM_MAX_L 96
 
 /* Arithmetic of the conditionals (Eqs. 9-10). */
+#define CRBM_BC_AS_ROWS 0
+#define CRBM_BC_PERIODIC 1
+#define CRBM_BC_OPEN 2
+
 #define CRBM_PRECISION_EXACT 0 /* double-precision weights, 32-bit thresholds and uniforms */
 #define CRBM_PRECISION_PAPER 1 /* the paper's FPGA (Sec. III, "Dimension and Precision"):
                                 * weights and visible bias in 10-bit fixed point (4 fraction
@@ -120,6 +124,23 @@ typedef struct {
      * batches or with block proposals.  crbm_get_tables returns the 16-bit
      * thresholds in the upper halves of the 32-bit entries. */
     int32_t precision;
+    /* Rectangular lattices and a boundary per axis (Sec. III: open boundaries
+     * along the lateral direction for laterally confined strips).  L_cols = 0
+     * keeps the lattice L x L; otherwise it has L rows and L_cols columns
+     * (3..4096).  periodic_cols: CRBM_BC_AS_ROWS (0) takes `periodic` for the
+     * columns too, CRBM_BC_PERIODIC (1) or CRBM_BC_OPEN (2) sets the column
+     * axis on its own (`periodic` then covers the rows).  Windows (i, j),
+     * i < (L+1)/2, j < (L_cols+1)/2, cell index i (L_cols+1)/2 + j; spins
+     * [chain][row][column].  A lattice other than L x L periodic with L even
+     * runs on the generic SMEM sweep. */
+    int32_t L_cols;
+    int32_t periodic_cols;
+    /* Field of the odd columns (the appendix's separate odd- and even-column
+     * visible biases), host array of n_params, or NULL for h everywhere.  With
+     * it, crbm_get_tables returns a second visible table (odd columns) after
+     * the first, and crbm_observables' M is still the total magnetisation.
+     * Not with replica exchange (its energies use the total M). */
+    const double* h_odd;
 } crbm_params;
 
 /* Build the model (Eqs. 3-8), the threshold tables, allocate device state and

@@ -23,6 +23,7 @@ CRBM_OK, CRBM_EINVAL, CRBM_ENOMEM, CRBM_ECUDA, CRBM_ETIMEOUT, CRBM_EUNSUPPORTED 
 CRBM_NSUM = 11
 CRBM_LAYOUT_AUTO, CRBM_LAYOUT_SMEM, CRBM_LAYOUT_STREAM = 0, 1, 2
 CRBM_PRECISION_EXACT, CRBM_PRECISION_PAPER = 0, 1
+CRBM_BC_AS_ROWS, CRBM_BC_PERIODIC, CRBM_BC_OPEN = 0, 1, 2
 CRBM_SMEM_MAX_L = 96
 SUM_FIELDS = ("n", "NJ", "NJp", "M", "absM", "NJ2", "NJp2", "M2", "NJ_NJp", "NJ_M", "NJp_M")
 
@@ -61,7 +62,9 @@ class crbm_params(ctypes.Structure):
                 ("n_chains", ctypes.c_int32), ("seed", ctypes.c_uint64),
                 ("measure_every", ctypes.c_int32), ("series_len", ctypes.c_int32),
                 ("sq_every", ctypes.c_int32), ("layout", ctypes.c_int32),
-                ("swap_every", ctypes.c_int32), ("stream", ctypes.c_void_p), ("precision", ctypes.c_int32)]
+                ("swap_every", ctypes.c_int32), ("stream", ctypes.c_void_p), ("precision", ctypes.c_int32),
+                ("L_cols", ctypes.c_int32), ("periodic_cols", ctypes.c_int32),
+                ("h_odd", ctypes.POINTER(ctypes.c_double))]
 
 
 _lib = None
@@ -157,13 +160,17 @@ class Sampler:
 
     def __init__(self, L, params, n_chains, chain_param=None, seed=1, periodic=True,
                  bonds=None, measure_every=1, series_len=0, sq_every=0,
-                 layout=CRBM_LAYOUT_AUTO, swap_every=0, stream=None, precision=0):
+                 layout=CRBM_LAYOUT_AUTO, swap_every=0, stream=None, precision=0, L_cols=0,
+                 periodic_cols=CRBM_BC_AS_ROWS):
         lib = load_library()
         self.L, self.n_chains = int(L), int(n_chains)
+        self.L_cols = int(L_cols) if L_cols else self.L
         self._J = np.ascontiguousarray(params["J"], np.float64)
         self._Jp = np.ascontiguousarray(params["Jp"], np.float64)
         self._h = np.ascontiguousarray(params["h"], np.float64)
         self._beta = np.ascontiguousarray(params["beta"], np.float64)
+        self._h_odd = (None if params.get("h_odd") is None
+                       else np.ascontiguousarray(params["h_odd"], np.float64))
         self.n_params = len(self._J)
         self.series_len, self.sq_every = int(series_len), int(sq_every)
         self._cp = None if chain_param is None else np.ascontiguousarray(chain_param, np.int32)
@@ -189,6 +196,8 @@ class Sampler:
         p.swap_every = int(swap_every)
         p.stream = ctypes.c_void_p(int(stream)) if stream else None
         p.precision = int(precision)
+        p.L_cols, p.periodic_cols = int(L_cols), int(periodic_cols)
+        p.h_odd = _ptr(self._h_odd, ctypes.c_double) if self._h_odd is not None else None
         self.precision = int(precision)
         h = ctypes.c_void_p()
         _check(lib.crbm_create(ctypes.byref(h), ctypes.byref(p)))
@@ -249,7 +258,7 @@ class Sampler:
 
     def get_spins(self, out=None):
         if out is None:
-            out = np.zeros((self.n_chains, self.L, self.L), np.int8)
+            out = np.zeros((self.n_chains, self.L, self.L_cols), np.int8)
         _check(self._lib.crbm_get_spins(self._ctx, _ptr(out, ctypes.c_int8), out.size), self._ctx)
         return out
 
@@ -277,7 +286,7 @@ class Sampler:
         dims = np.zeros(2, np.int32)
         _check(self._lib.crbm_get_tables(self._ctx, None, 0, _ptr(dims, ctypes.c_int32)), self._ctx)
         dj, djp = int(dims[0]), int(dims[1])
-        ntab = 10 + (2 * dj + 1) * (2 * djp + 1)
+        ntab = 10 + (2 if self._h_odd is not None else 1) * (2 * dj + 1) * (2 * djp + 1)
         out = np.zeros((self.n_params, ntab), np.uint32)
         _check(self._lib.crbm_get_tables(self._ctx, _ptr(out, ctypes.c_uint32), out.size, None),
                self._ctx)

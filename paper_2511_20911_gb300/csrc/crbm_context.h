@@ -24,6 +24,7 @@ struct crbm_ctx {
     int device = 0;
     std::vector<int32_t> chain_param;
     std::vector<int32_t> q[3];     // quantised J, J', h per point
+    std::vector<int32_t> q_odd;    // quantised odd-column field per point (h when none is given)
     std::vector<double> beta;
     std::vector<uint32_t> tables;  // [n_params][nTab]
     crbm::DeviceState d;

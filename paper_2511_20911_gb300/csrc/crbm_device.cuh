@@ -196,21 +196,6 @@ __device__ __forceinline__ int warp_sum(int x) {
     return x;
 }
 
-// Site index of window offset (r, c) of cell (i, j), or -1 for a zero-padded
-// (open boundary) site.  r, c <= 2 and 2i, 2j <= L - 1, so one wrap suffices.
-__device__ __forceinline__ int site_of(const Geometry& g, int i, int j, int r, int c) {
-    int R = 2 * i + r, C = 2 * j + c;
-    if (R >= g.L) {
-        if (!g.periodic) return -1;
-        R -= g.L;
-    }
-    if (C >= g.L) {
-        if (!g.periodic) return -1;
-        C -= g.L;
-    }
-    return R * g.L + C;
-}
-
 // Post-sweep step of the SMEM kernels, run by warp 0 after every warp has
 // added its per-lane counts to s_cnt ([0..31] anti-aligned J filters, [32..63]
 // anti-aligned J' filters, [64..95] +1 spins; lane = replica slot).  Lane k

@@ -101,10 +101,10 @@ __device__ __forceinline__ void visible_cell_generic(char* sm, const uint4* __re
 }
 
 // Per-lane counts of one cell for the energy/magnetisation measurement:
-// anti[cls] = number of anti-aligned real bonds, pos = number of +1 spins.
+// anti[cls] = number of anti-aligned real bonds of the cell's filters.
 __device__ __forceinline__ void count_cell(const Geometry& g, const uint32_t* s_v,
-                                           const uint32_t* __restrict__ ep, int cell, int i, int j,
-                                           int lane, int& anti0, int& anti1, int& pos) {
+                                           const uint32_t* __restrict__ ep, int cell, int lane, int& anti0,
+                                           int& anti1) {
     const uint32_t* e = ep + static_cast<size_t>(cell) * g.nb;
 #pragma unroll
     for (int k = 0; k < kMaxBonds; ++k) {
@@ -115,11 +115,6 @@ __device__ __forceinline__ void count_cell(const Geometry& g, const uint32_t* s_
                 if (g.cls[k]) anti1 += x; else anti0 += x;
             }
         }
-    }
-#pragma unroll
-    for (int w = 0; w < 4; ++w) {
-        const int R = 2 * i + (w >> 1), C = 2 * j + (w & 1);
-        if (R < g.L && C < g.L) pos += static_cast<int>(bit_of(s_v[R * g.L + C], lane));
     }
 }
 
@@ -142,7 +137,7 @@ __device__ __forceinline__ void sweep_generic_body(const SweepArgs& a, int word)
     uint32_t* s_segmask = smem + gs.segmask;                       // [32]
     int* s_sob = reinterpret_cast<int*>(smem + gs.sob);            // [32] slot of each rung
     int* s_bos = s_sob + 32;                                        // [32] rung of each slot
-    const int nTg = kGenHid + g.nTv;
+    const int nTg = kGenHid + g.n_vis_tab * g.nTv;
     const uint4* rh = a.crec;                                           // [n_cells][nb] hidden records
     const uint4* rv = a.crec + static_cast<size_t>(g.n_cells) * g.nb;  // [n_cells][kGenVisRec]
     const uint32_t hw_byte = 4u * static_cast<uint32_t>(gs.hw);
@@ -179,8 +174,6 @@ __device__ __forceinline__ void sweep_generic_body(const SweepArgs& a, int word)
     // sweep and measurement counters: kernel arguments, or the batch's device clock
     const uint32_t t0 = a.clock ? static_cast<uint32_t>(a.clock[0]) : a.t0;
     int64_t meas = a.clock ? a.clock[1] : a.meas0;
-    const int i_first = warp / g.W, j_first = warp - (warp / g.W) * g.W;
-    const int di = nwarp / g.W, dj = nwarp - (nwarp / g.W) * g.W;
 
     const Round0Lane r0l = round0_lane(chain);
     for (int it = 0; it < a.n_sweeps; ++it) {
@@ -196,16 +189,8 @@ __device__ __forceinline__ void sweep_generic_body(const SweepArgs& a, int word)
         const bool do_swap = a.swap_every > 0 && (t + 1u) % static_cast<uint32_t>(a.swap_every) == 0u;
         if (do_meas || do_swap) {
             int anti0 = 0, anti1 = 0, pos = 0;
-            int i = i_first, j = j_first;
-            for (int cell = warp; cell < g.n_cells; cell += nwarp) {
-                count_cell(g, s_v, a.gep, cell, i, j, lane, anti0, anti1, pos);
-                i += di;
-                j += dj;
-                if (j >= g.W) {
-                    j -= g.W;
-                    ++i;
-                }
-            }
+            for (int cell = warp; cell < g.n_cells; cell += nwarp) count_cell(g, s_v, a.gep, cell, lane, anti0, anti1);
+            for (int x = warp; x < g.N; x += nwarp) pos += static_cast<int>(bit_of(s_v[x], lane));
             atomicAdd(&s_cnt[lane], anti0);
             atomicAdd(&s_cnt[32 + lane], anti1);
             atomicAdd(&s_cnt[64 + lane], pos);

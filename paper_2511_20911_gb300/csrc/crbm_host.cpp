@@ -98,12 +98,15 @@ uint32_t swap_threshold(double x) {
 
 int site_index(const Geometry& g, int i, int j, int r, int c) {
     int R = 2 * i + r, C = 2 * j + c;
-    if (R >= g.L || C >= g.L) {
+    if (R >= g.L) {
         if (!g.periodic) return -1;
         R %= g.L;
-        C %= g.L;
     }
-    return R * g.L + C;
+    if (C >= g.Lc) {
+        if (!g.pc) return -1;
+        C %= g.Lc;
+    }
+    return R * g.Lc + C;
 }
 
 // Geometry, visible field ranges and the generic endpoint words.
@@ -119,22 +122,30 @@ int build_geometry(crbm_ctx* ctx, const crbm_params* p, std::vector<uint32_t>& e
             return fail(nullptr, CRBM_EINVAL, "bond " + std::to_string(k) + " is not a bond of the 3x3 window");
         g.r1[k] = b.r1; g.c1[k] = b.c1; g.r2[k] = b.r2; g.c2[k] = b.c2; g.cls[k] = b.cls;
     }
+    if (p->L_cols != 0 && (p->L_cols < 3 || p->L_cols > 4096))
+        return fail(nullptr, CRBM_EINVAL, "L_cols must be 0 or in 3..4096");
+    if (p->periodic_cols < CRBM_BC_AS_ROWS || p->periodic_cols > CRBM_BC_OPEN)
+        return fail(nullptr, CRBM_EINVAL, "unknown periodic_cols");
     g.L = p->L;
     g.W = (p->L + 1) / 2;
-    g.N = p->L * p->L;
-    g.n_cells = g.W * g.W;
+    g.Lc = p->L_cols ? p->L_cols : p->L;
+    g.Wc = (g.Lc + 1) / 2;
+    g.N = g.L * g.Lc;
+    g.n_cells = g.W * g.Wc;
     g.nb = nb;
     g.n_calls = (nb + 3) / 4;
     g.periodic = p->periodic ? 1 : 0;
+    g.pc = p->periodic_cols == CRBM_BC_AS_ROWS ? g.periodic : (p->periodic_cols == CRBM_BC_PERIODIC ? 1 : 0);
+    g.n_vis_tab = p->h_odd ? 2 : 1;
     bool same = (nb == 10);
     for (int k = 0; same && k < 10; ++k)
         same = std::memcmp(&bonds[k], &kSSFilters[k], sizeof(crbm_bond)) == 0;
-    g.canonical = (same && g.periodic && (g.L % 2 == 0)) ? 1 : 0;
+    g.canonical = (same && g.periodic && g.pc && g.Lc == g.L && (g.L % 2 == 0) && g.n_vis_tab == 1) ? 1 : 0;
 
     std::vector<int> deg(2 * static_cast<size_t>(g.N), 0);  // filters per (class, site)
     g.n_real_bonds[0] = g.n_real_bonds[1] = 0;
     for (int i = 0; i < g.W; ++i)
-        for (int j = 0; j < g.W; ++j)
+        for (int j = 0; j < g.Wc; ++j)
             for (int k = 0; k < nb; ++k) {
                 const int s1 = site_index(g, i, j, g.r1[k], g.c1[k]);
                 const int s2 = site_index(g, i, j, g.r2[k], g.c2[k]);
@@ -149,7 +160,7 @@ int build_geometry(crbm_ctx* ctx, const crbm_params* p, std::vector<uint32_t>& e
         g.DJp = std::max(g.DJp, deg[g.N + s]);
     }
     g.nTv = (2 * g.DJ + 1) * (2 * g.DJp + 1);
-    g.nTab = 10 + g.nTv;
+    g.nTab = 10 + g.n_vis_tab * g.nTv;
     if (g.canonical && (g.DJ != 4 || g.DJp != 1))
         return fail(nullptr, CRBM_EINVAL, "internal: SS filters must give 4 J and 1 J' filter per spin");
     // endpoint words of the generic measurement, [n_cells][nb]: per endpoint
@@ -159,7 +170,7 @@ int build_geometry(crbm_ctx* ctx, const crbm_params* p, std::vector<uint32_t>& e
     ep.clear();
     if (!g.canonical && g.N <= 0x7FFF) {
         for (int i = 0; i < g.W; ++i)
-            for (int j = 0; j < g.W; ++j)
+            for (int j = 0; j < g.Wc; ++j)
                 for (int k = 0; k < nb; ++k)
                     ep.push_back(endpoint(site_index(g, i, j, g.r1[k], g.c1[k])) |
                                  (endpoint(site_index(g, i, j, g.r2[k], g.c2[k])) << 16));
@@ -167,31 +178,42 @@ int build_geometry(crbm_ctx* ctx, const crbm_params* p, std::vector<uint32_t>& e
     return CRBM_OK;
 }
 
-// Th[cls][m+2] = thr(2 a_cls m), Tv[nJ+DJ][nJ'+DJ'] = thr(2 (beta h + a_J nJ + a_J' nJ')).
-void point_tables(const Geometry& g, double beta, int32_t qJ, int32_t qJp, int32_t qh,
+// Visible rows of one field value: Tv[nJ+DJ][nJ'+DJ'] = thr(2 (beta h + a_J nJ + a_J' nJ')), or the
+// 16-bit table of paper precision.
+void visible_rows(const Geometry& g, double beta, const double a[2], int32_t qh, uint32_t* out) {
+    const int nP = 2 * g.DJp + 1;
+    if (g.paper) {
+        const int32_t A[2] = {fixed_q54(a[0]), fixed_q54(a[1])}, B = fixed_q54(beta * (qh / 16.0));
+        for (int nJ = -g.DJ; nJ <= g.DJ; ++nJ)
+            for (int nJp = -g.DJp; nJp <= g.DJp; ++nJp)
+                out[(nJ + g.DJ) * nP + (nJp + g.DJp)] = sigmoid_lut16(B + A[0] * nJ + A[1] * nJp);
+        return;
+    }
+    const double hd = qh / 16.0;
+    for (int nJ = -g.DJ; nJ <= g.DJ; ++nJ)
+        for (int nJp = -g.DJp; nJp <= g.DJp; ++nJp) {
+            const double x = beta * hd + a[0] * nJ + a[1] * nJp;
+            out[(nJ + g.DJ) * nP + (nJp + g.DJp)] = accept_threshold(2.0 * x);
+        }
+}
+
+// Th[cls][m+2] = thr(2 a_cls m), then the visible rows of field h and, with
+// an odd-column field, those of h_odd (qho).
+void point_tables(const Geometry& g, double beta, int32_t qJ, int32_t qJp, int32_t qh, int32_t qho,
                   uint32_t* out, int sgn[2]) {
     double a[2];
     bond_weight(beta, qJ / 16.0, a[0], sgn[0]);
     bond_weight(beta, qJp / 16.0, a[1], sgn[1]);
     if (g.paper) {
-        const int32_t A[2] = {fixed_q54(a[0]), fixed_q54(a[1])}, B = fixed_q54(beta * (qh / 16.0));
+        const int32_t A[2] = {fixed_q54(a[0]), fixed_q54(a[1])};
         for (int cls = 0; cls < 2; ++cls)
             for (int m = -2; m <= 2; ++m) out[cls * 5 + m + 2] = sigmoid_lut16(A[cls] * m);
-        const int nP = 2 * g.DJp + 1;
-        for (int nJ = -g.DJ; nJ <= g.DJ; ++nJ)
-            for (int nJp = -g.DJp; nJp <= g.DJp; ++nJp)
-                out[10 + (nJ + g.DJ) * nP + (nJp + g.DJp)] = sigmoid_lut16(B + A[0] * nJ + A[1] * nJp);
-        return;
+    } else {
+        for (int cls = 0; cls < 2; ++cls)
+            for (int m = -2; m <= 2; ++m) out[cls * 5 + m + 2] = accept_threshold(2.0 * a[cls] * m);
     }
-    for (int cls = 0; cls < 2; ++cls)
-        for (int m = -2; m <= 2; ++m) out[cls * 5 + m + 2] = accept_threshold(2.0 * a[cls] * m);
-    const double hd = qh / 16.0;
-    const int nP = 2 * g.DJp + 1;
-    for (int nJ = -g.DJ; nJ <= g.DJ; ++nJ)
-        for (int nJp = -g.DJp; nJp <= g.DJp; ++nJp) {
-            const double x = beta * hd + a[0] * nJ + a[1] * nJp;
-            out[10 + (nJ + g.DJ) * nP + (nJp + g.DJp)] = accept_threshold(2.0 * x);
-        }
+    visible_rows(g, beta, a, qh, out + 10);
+    if (g.n_vis_tab == 2) visible_rows(g, beta, a, qho, out + 10 + g.nTv);
 }
 
 template <typename T>
@@ -229,7 +251,7 @@ namespace crbm {
 bool host_to_q4(double x, int32_t& q) { return to_q4(x, q); }
 void host_point_tables(const Geometry& g, double beta, int32_t qJ, int32_t qJp, int32_t qh,
                        uint32_t* out, int sgn[2]) {
-    point_tables(g, beta, qJ, qJp, qh, out, sgn);
+    point_tables(g, beta, qJ, qJp, qh, qh, out, sgn);
 }
 }  // namespace crbm
 
@@ -307,11 +329,13 @@ int crbm_create(crbm_ctx** out, const crbm_params* p) {
     ctx->layout = p->layout;
     if (ctx->layout == CRBM_LAYOUT_AUTO) {
         const size_t need = g.canonical ? smem_bytes_canon(g) : smem_bytes_generic(g);
-        ctx->layout = (p->L <= CRBM_SMEM_MAX_L && need <= 227 * 1024) ? CRBM_LAYOUT_SMEM : CRBM_LAYOUT_STREAM;
+        ctx->layout = (p->L <= CRBM_SMEM_MAX_L && g.Lc <= CRBM_SMEM_MAX_L && need <= 227 * 1024)
+                          ? CRBM_LAYOUT_SMEM
+                          : CRBM_LAYOUT_STREAM;
     }
-    if (ctx->layout == CRBM_LAYOUT_SMEM && p->L > CRBM_SMEM_MAX_L) {
+    if (ctx->layout == CRBM_LAYOUT_SMEM && (p->L > CRBM_SMEM_MAX_L || g.Lc > CRBM_SMEM_MAX_L)) {
         delete ctx;
-        return fail(nullptr, CRBM_EINVAL, "SMEM layout needs L <= CRBM_SMEM_MAX_L");
+        return fail(nullptr, CRBM_EINVAL, "SMEM layout needs L, L_cols <= CRBM_SMEM_MAX_L");
     }
     if (g.paper && (!g.canonical || ctx->layout != CRBM_LAYOUT_SMEM)) {
         delete ctx;
@@ -334,9 +358,9 @@ int crbm_create(crbm_ctx** out, const crbm_params* p) {
         return fail(nullptr, CRBM_EUNSUPPORTED,
                     "lattice, hidden layer and threshold columns exceed 227 KB of shared memory");
     }
-    if (p->sq_every > 0 && !g.periodic) {
+    if (p->sq_every > 0 && (!g.periodic || !g.pc || g.Lc != g.L)) {
         delete ctx;
-        return fail(nullptr, CRBM_EINVAL, "spin correlations need a periodic lattice");
+        return fail(nullptr, CRBM_EINVAL, "spin correlations need a square lattice, periodic along both axes");
     }
     ctx->n_chains = p->n_chains;
     // the streamed layout stores 64-chain words: an even number of 32-chain halves
@@ -349,13 +373,14 @@ int crbm_create(crbm_ctx** out, const crbm_params* p) {
     ctx->stream = static_cast<cudaStream_t>(p->stream);
     ctx->warps = default_warps(g);
     for (int k = 0; k < 3; ++k) ctx->q[k].resize(p->n_params);
+    ctx->q_odd.resize(p->n_params);
     ctx->beta.assign(p->beta, p->beta + p->n_params);
     for (int i = 0; i < p->n_params; ++i) {
         if (!to_q4(p->J[i], ctx->q[0][i]) || !to_q4(p->Jp[i], ctx->q[1][i]) ||
-            !to_q4(p->h[i], ctx->q[2][i])) {
+            !to_q4(p->h[i], ctx->q[2][i]) || !to_q4(p->h_odd ? p->h_odd[i] : p->h[i], ctx->q_odd[i])) {
             delete ctx;
             return fail(nullptr, CRBM_EINVAL, "parameter point " + std::to_string(i) +
-                                                  ": J, J', h must be finite with |16 x| <= 2047");
+                                                  ": J, J', h, h_odd must be finite with |16 x| <= 2047");
         }
         if (!(p->beta[i] >= 0.0) || !(p->beta[i] <= 1.0e6)) {
             delete ctx;
@@ -385,6 +410,10 @@ int crbm_create(crbm_ctx** out, const crbm_params* p) {
         return fail(nullptr, CRBM_EINVAL, "swap_every must be >= 0");
     }
     if (p->swap_every > 0) {
+        if (g.n_vis_tab == 2) {
+            delete ctx;
+            return fail(nullptr, CRBM_EUNSUPPORTED, "replica exchange needs one field on every column (no h_odd)");
+        }
         if (p->n_chains % 32 != 0 || ctx->layout != CRBM_LAYOUT_SMEM) {
             delete ctx;
             return fail(nullptr, p->n_chains % 32 ? CRBM_EINVAL : CRBM_EUNSUPPORTED,
@@ -438,11 +467,11 @@ int crbm_create(crbm_ctx** out, const crbm_params* p) {
     ctx->tables.resize(static_cast<size_t>(p->n_params) * g.nTab);
     std::vector<int> sgn(2 * static_cast<size_t>(p->n_params));
     for (int i = 0; i < p->n_params; ++i)
-        point_tables(g, ctx->beta[i], ctx->q[0][i], ctx->q[1][i], ctx->q[2][i],
+        point_tables(g, ctx->beta[i], ctx->q[0][i], ctx->q[1][i], ctx->q[2][i], ctx->q_odd[i],
                      &ctx->tables[static_cast<size_t>(i) * g.nTab], &sgn[2 * i]);
     const int nw = ctx->n_words, npad = nw * 32;
     // generic lane-expanded tables (layout in crbm_internal.h); canonical contexts use ctab
-    const int nTg = g.canonical ? 0 : kGenHid + g.nTv;
+    const int nTg = g.canonical ? 0 : kGenHid + g.n_vis_tab * g.nTv;
     std::vector<uint32_t> tab(static_cast<size_t>(nw) * nTg * 32);
     std::vector<uint32_t> sneg(2 * static_cast<size_t>(nw), 0u);
     std::vector<int32_t> seg(33 * static_cast<size_t>(nw), 0);
@@ -463,7 +492,7 @@ int crbm_create(crbm_ctx** out, const crbm_params* p) {
                             const int m = ((pad & 1) ? 0 : 2 * e1 - 1) + ((pad & 2) ? 0 : sgn[2 * pp + cls] * (2 * e2 - 1));
                             out[((cls * 4 + pad) * 4 + idx) * 32] = T[cls * 5 + m + 2];
                         }
-                for (int e = 0; e < g.nTv; ++e) out[(kGenHid + e) * 32] = T[10 + e];
+                for (int e = 0; e < g.n_vis_tab * g.nTv; ++e) out[(kGenHid + e) * 32] = T[10 + e];
             }
             if (sgn[2 * pp] < 0) sneg[2 * w] |= 1u << l;
             if (sgn[2 * pp + 1] < 0) sneg[2 * w + 1] |= 1u << l;
@@ -553,13 +582,13 @@ int crbm_create(crbm_ctx** out, const crbm_params* p) {
     // Per-cell records of the generic SMEM sweep (layout in crbm_internal.h).
     if (!g.canonical && ctx->layout == CRBM_LAYOUT_SMEM) {
         const GenericSmem gs = generic_smem(g);
-        const int W = g.W, nb = g.nb, nP = 2 * g.DJp + 1;
+        const int Wr = g.W, Wc = g.Wc, nb = g.nb, nP = 2 * g.DJp + 1;
         const size_t nh = static_cast<size_t>(g.n_cells) * nb;
         crec.assign((nh + static_cast<size_t>(g.n_cells) * kGenVisRec) * 4, 0u);
         auto site_off = [&](int s) { return 4u * static_cast<uint32_t>(s >= 0 ? gs.v + s : gs.zero); };
         for (int c = 0; c < g.n_cells; ++c)
             for (int k = 0; k < nb; ++k) {
-                const int i = c / W, j = c % W;
+                const int i = c / Wc, j = c % Wc;
                 const int s1 = site_index(g, i, j, g.r1[k], g.c1[k]), s2 = site_index(g, i, j, g.r2[k], g.c2[k]);
                 const int pad = (s1 < 0 ? 1 : 0) | (s2 < 0 ? 2 : 0);
                 uint32_t* o = &crec[(static_cast<size_t>(c) * nb + k) * 4];
@@ -571,17 +600,17 @@ int crbm_create(crbm_ctx** out, const crbm_params* p) {
         std::vector<std::vector<int>> incid(g.N);
         for (int c = 0; c < g.n_cells; ++c)
             for (int k = 0; k < nb; ++k) {
-                const int i = c / W, j = c % W;
+                const int i = c / Wc, j = c % Wc;
                 const int s1 = site_index(g, i, j, g.r1[k], g.c1[k]), s2 = site_index(g, i, j, g.r2[k], g.c2[k]);
                 if (s1 >= 0) incid[s1].push_back((c * kMaxBonds + k) * 2);
                 if (s2 >= 0) incid[s2].push_back((c * kMaxBonds + k) * 2 + 1);
             }
         for (int c = 0; c < g.n_cells; ++c) {
-            const int i = c / W, j = c % W;
-            const int iu = i > 0 ? i - 1 : (g.periodic ? W - 1 : -1);
-            const int jl = j > 0 ? j - 1 : (g.periodic ? W - 1 : -1);
-            const int src[4] = {c, iu >= 0 ? iu * W + j : -1, jl >= 0 ? i * W + jl : -1,
-                                iu >= 0 && jl >= 0 ? iu * W + jl : -1};
+            const int i = c / Wc, j = c % Wc;
+            const int iu = i > 0 ? i - 1 : (g.periodic ? Wr - 1 : -1);
+            const int jl = j > 0 ? j - 1 : (g.pc ? Wc - 1 : -1);
+            const int src[4] = {c, iu >= 0 ? iu * Wc + j : -1, jl >= 0 ? i * Wc + jl : -1,
+                                iu >= 0 && jl >= 0 ? iu * Wc + jl : -1};
             uint32_t* o = &crec[(nh + static_cast<size_t>(c) * kGenVisRec) * 4];
             for (int q = 0; q < 4; ++q)
                 o[q] = 4u * static_cast<uint32_t>(src[q] >= 0 ? gs.hw + static_cast<size_t>(src[q]) * 16 : gs.zrow);
@@ -590,8 +619,8 @@ int crbm_create(crbm_ctx** out, const crbm_params* p) {
                 uint32_t* mj = o + 4 * (1 + 2 * x);
                 uint32_t* mp = o + 4 * (2 + 2 * x);
                 int deg[2] = {0, 0};
-                if (R < g.L && C < g.L) {
-                    const int s = R * g.L + C;
+                if (R < g.L && C < g.Lc) {
+                    const int s = R * g.Lc + C;
                     for (const int e : incid[s]) {
                         const int cc = e / (2 * kMaxBonds), k = (e / 2) % kMaxBonds, second = e & 1;
                         int q = 0;
@@ -608,8 +637,9 @@ int crbm_create(crbm_ctx** out, const crbm_params* p) {
                 } else {
                     o[4 * 10 + x] = 4u * static_cast<uint32_t>(gs.zero + 1);
                 }
+                const int odd_table = (g.n_vis_tab == 2 && (C & 1)) ? g.nTv : 0;  // odd column: second table
                 o[4 * 9 + x] = 4u * static_cast<uint32_t>(
-                    gs.tab + static_cast<size_t>(kGenHid + (g.DJ - deg[0]) * nP + (g.DJp - deg[1])) * 32);
+                    gs.tab + static_cast<size_t>(kGenHid + odd_table + (g.DJ - deg[0]) * nP + (g.DJp - deg[1])) * 32);
             }
         }
     }
@@ -874,7 +904,8 @@ int crbm_save(crbm_ctx* ctx, void* buf, size_t* n) {
     int64_t hdr[16] = {0x4d425243 /* "CRBM" */, 1, ctx->g.L, ctx->n_chains, ctx->n_params,
                        static_cast<int64_t>(ctx->seed), ctx->sweeps, ctx->meas, ctx->sq_meas,
                        ctx->series_len, ctx->sq_every, ctx->measure_every, ctx->g.nb,
-                       ctx->g.periodic, ctx->swap_every, ctx->g.paper};
+                       ctx->g.periodic | (ctx->g.pc << 1) | (static_cast<int64_t>(ctx->g.Lc) << 2), ctx->swap_every,
+                       ctx->g.paper};
     char* p = static_cast<char*>(buf);
     std::memcpy(p, hdr, sizeof(hdr));
     cudaError_t e = cudaMemcpyAsync(p + 128, ctx->d.v, b_v, cudaMemcpyDeviceToHost, ctx->stream);
@@ -901,7 +932,9 @@ int crbm_load(crbm_ctx* ctx, const void* buf, size_t n) {
     if (hdr[0] != 0x4d425243 || hdr[1] != 1 || hdr[2] != ctx->g.L || hdr[3] != ctx->n_chains ||
         hdr[4] != ctx->n_params || hdr[5] != static_cast<int64_t>(ctx->seed) ||
         hdr[9] != ctx->series_len || hdr[10] != ctx->sq_every || hdr[11] != ctx->measure_every ||
-        hdr[12] != ctx->g.nb || hdr[13] != ctx->g.periodic || hdr[14] != ctx->swap_every ||
+        hdr[12] != ctx->g.nb ||
+        hdr[13] != (ctx->g.periodic | (ctx->g.pc << 1) | (static_cast<int64_t>(ctx->g.Lc) << 2)) ||
+        hdr[14] != ctx->swap_every ||
         hdr[15] != ctx->g.paper)
         return fail(ctx, CRBM_EINVAL, "checkpoint does not match this context");
     const size_t npad = static_cast<size_t>(ctx->n_words) * 32, N = ctx->g.N;

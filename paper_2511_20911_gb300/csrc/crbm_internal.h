@@ -64,17 +64,21 @@ constexpr int kCanonSlot[4][5][2] = {{{0, 0}, {0, 0}, {1, 0}, {0, 1}, {0, 1}},
 // Lattice and filter geometry, passed by value to kernels (lives in the
 // kernel-parameter constant bank, read uniformly by every warp).
 struct Geometry {
-    int L;         // spins per side
-    int W;         // windows (cells) per side = (L + 1) / 2
-    int N;         // L * L
-    int n_cells;   // W * W
+    int L;         // rows of spins (the side of a square lattice)
+    int W;         // window rows = (L + 1) / 2
+    int Lc;        // columns of spins (L for a square lattice)
+    int Wc;        // window columns = (Lc + 1) / 2
+    int N;         // L * Lc
+    int n_cells;   // W * Wc
     int nb;        // filters per window
     int n_calls;   // hidden Philox calls per cell = ceil(nb / 4)
-    int periodic;  // 1 periodic, 0 open (zero padded)
+    int periodic;  // rows axis: 1 periodic, 0 open (zero padded)
+    int pc;        // columns axis: 1 periodic, 0 open
     int canonical; // 1: the ten SS filters on an even, periodic lattice
     int DJ, DJp;   // visible field ranges n_J in [-DJ, DJ], n_J' in [-DJp, DJp]
     int nTv;       // (2 DJ + 1) (2 DJp + 1)
-    int nTab;      // 10 hidden entries + nTv visible entries
+    int nTab;      // 10 hidden entries + n_vis_tab * nTv visible entries
+    int n_vis_tab; // 1, or 2 with an odd-column field (even-column table, then odd)
     int n_real_bonds[2];  // bonds with both endpoints real, per class
     int vil;       // spin storage: 0 = [word][site], 1 = 64-chain words [group][site][2]
     int paper;     // CRBM_PRECISION_PAPER: 16-bit thresholds and uniforms, two per Philox word
@@ -117,7 +121,7 @@ constexpr int kGenHid = 2 * 4 * 4;
 constexpr int kGenVisRec = 11;
 // Word offsets of the generic sweep's dynamic shared memory.
 struct GenericSmem {
-    size_t tab;      // [kGenHid + nTv][32] thresholds
+    size_t tab;      // [kGenHid + n_vis_tab nTv][32] thresholds
     size_t v;        // [N] spins
     size_t zero;     // one zero word (padded endpoints), then one scratch word
     size_t hw;       // [n_cells][32] 16-bit per-lane hidden words (bit k: filter k)
@@ -131,7 +135,7 @@ struct GenericSmem {
 __host__ __device__ inline GenericSmem generic_smem(const Geometry& g) {
     GenericSmem s;
     s.tab = static_cast<size_t>(kAccWords);
-    s.v = s.tab + static_cast<size_t>(kGenHid + g.nTv) * 32;
+    s.v = s.tab + static_cast<size_t>(kGenHid + g.n_vis_tab * g.nTv) * 32;
     s.zero = s.v + g.N;
     s.hw = (s.zero + 2 + 3) & ~static_cast<size_t>(3);
     s.zrow = s.hw + static_cast<size_t>(g.n_cells) * 16;

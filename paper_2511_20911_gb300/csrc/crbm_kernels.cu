@@ -28,8 +28,8 @@ __global__ void k_init(const Geometry g, uint32_t* v, int n_words, uint32_t k0, 
     for (long long x = blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
          x < static_cast<long long>(n_words) * g.N; x += nw) {
         const int word = static_cast<int>(x / g.N), s = static_cast<int>(x - static_cast<long long>(word) * g.N);
-        const int R = s / g.L, C = s - (s / g.L) * g.L;
-        const uint32_t cell = static_cast<uint32_t>((R >> 1) * g.W + (C >> 1));
+        const int R = s / g.Lc, C = s - (s / g.Lc) * g.Lc;
+        const uint32_t cell = static_cast<uint32_t>((R >> 1) * g.Wc + (C >> 1));
         const U4 q = philox(cell, 0u, static_cast<uint32_t>(word) * 32u + lane, kTagInit, k0, k1);
         const uint32_t b = __ballot_sync(0xffffffffu, pick(q, 2 * (R & 1) + (C & 1)) < 0x80000000u);
         if (lane == 0) v[word_index(g.vil, word, g.N, s)] = b;

@@ -79,6 +79,10 @@ extern "C" int crbm_sweep_stream_noalloc(const crbm_params* p, uint32_t* v, int6
     Geometry g{};
     g.L = L;
     g.W = W;
+    g.Lc = L;
+    g.Wc = W;
+    g.pc = 1;
+    g.n_vis_tab = 1;
     g.N = N;
     g.n_cells = n_cells;
     g.nb = 10;

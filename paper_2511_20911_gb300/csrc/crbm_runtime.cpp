@@ -39,7 +39,7 @@ std::string shape_key(const crbm_ctx* ctx) {
     std::ostringstream k;
     k << prop.name << "|sm" << prop.multiProcessorCount << "|L" << ctx->g.L << "|p" << ctx->g.periodic << "|c"
       << ctx->g.canonical << "|nb" << ctx->g.nb << "|w" << ctx->n_words << "|x" << (ctx->swap_every > 0)
-      << "|q" << ctx->g.paper;
+      << "|q" << ctx->g.paper << "|Lc" << ctx->g.Lc << "|pc" << ctx->g.pc << "|v" << ctx->g.n_vis_tab;
     std::string s = k.str();
     std::replace(s.begin(), s.end(), ' ', '_');
     return s;

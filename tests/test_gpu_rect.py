@@ -1,0 +1,104 @@
+"""Rectangular lattices, a boundary per axis and an odd-column field on the
+GPU (generic sweep) against the oracle, bit for bit: tables, spins, sums and
+series; the laterally confined 18 x 12 strip of Sec. III among them."""
+import numpy as np
+import pytest
+
+import paper_2511_20911_gb300 as crbm
+from paper_2511_20911_gb300 import workloads
+
+pytestmark = pytest.mark.gpu
+OPEN, PERIODIC = crbm.CRBM_BC_OPEN, crbm.CRBM_BC_PERIODIC
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _gpu():
+    torch = pytest.importorskip("torch")
+    if not torch.cuda.is_available():
+        pytest.skip("no GPU")
+    crbm.load_library()
+
+
+def run_pair(orc, L, Lc, pr, pc, params, n, seed, splits, measure_every=2, series_len=8, swap_every=0):
+    cp = (np.arange(n) % len(params["J"])).astype(np.int32)
+    s = crbm.Sampler(L, params, n, chain_param=cp, seed=seed, periodic=pr, L_cols=Lc,
+                     periodic_cols=PERIODIC if pc else OPEN, measure_every=measure_every,
+                     series_len=series_len)
+    assert s.get_spins().shape == (n, L, Lc)
+    ids = np.arange(n, dtype=np.uint32)
+    spins = orc.init_spins((L, Lc), ids, seed)
+    assert np.array_equal(s.get_spins(), spins), "initial spins"
+    sums, oser, t = None, None, 0
+    for k in splits:
+        s.sweep(k)
+        sums, ser, _ = orc.run((L, Lc), params, cp, spins, seed, t, k, measure_every, chain_ids=ids,
+                               periodic=(pr, pc), sums=sums, series_cap=series_len)
+        if ser is not None:
+            oser = ser if oser is None else np.where(ser != 0, ser, oser)
+        t += k
+        assert np.array_equal(s.get_spins(), spins), f"spins after {t} sweeps"
+    assert np.array_equal(s.observables(), sums)
+    if series_len:
+        assert np.array_equal(s.series().transpose(1, 0, 2), oser)
+    return s
+
+
+@pytest.mark.parametrize("L,Lc,pr,pc", [(6, 10, True, True), (18, 12, True, False), (12, 18, False, True),
+                                        (7, 10, True, True), (9, 5, False, False), (10, 3, True, True)])
+def test_rectangles_bitexact(orc, L, Lc, pr, pc):
+    rng = np.random.default_rng(L * 100 + Lc)
+    params = workloads.random_params(rng, 3)
+    s = run_pair(orc, L, Lc, pr, pc, params, 45, 3 + L + Lc, splits=[3, 14])
+    assert s.layout == crbm.CRBM_LAYOUT_SMEM
+
+
+@pytest.mark.parametrize("L,Lc,pr,pc", [(8, 6, True, False), (7, 9, False, False), (6, 6, True, True)])
+def test_odd_column_field_bitexact(orc, L, Lc, pr, pc):
+    rng = np.random.default_rng(L * 7 + Lc)
+    params = workloads.random_params(rng, 2)
+    params["h_odd"] = list(np.round(rng.uniform(-3, 3, 2) * 16) / 16)
+    s = run_pair(orc, L, Lc, pr, pc, params, 40, 11, splits=[5, 9])
+    tabs, (dj, djp) = s.tables()
+    for p in range(2):
+        th, tv, tvo = orc.tables((L, Lc), params["J"][p], params["Jp"][p], params["h"][p], params["beta"][p],
+                                 periodic=(pr, pc), h_odd=params["h_odd"][p])
+        assert np.array_equal(tabs[p], np.concatenate([th.reshape(-1), tv.reshape(-1), tvo.reshape(-1)]))
+
+
+def test_strip_in_a_batch_matches_its_twin(orc):
+    """The laterally confined strip (18 rows periodic, 12 columns open) and a
+    square member in one batched launch stay bit-identical to twins advanced
+    alone."""
+    rng = np.random.default_rng(5)
+    specs = [dict(L=18, L_cols=12, periodic=True, periodic_cols=OPEN, params=workloads.random_params(rng, 2),
+                  n_chains=64, seed=9, measure_every=4),
+             dict(L=12, params=workloads.random_params(rng, 2), n_chains=32, seed=10, measure_every=4)]
+    for sp in specs:
+        sp["chain_param"] = (np.arange(sp["n_chains"]) % 2).astype(np.int32)
+    batched = [crbm.Sampler(**sp) for sp in specs]
+    twins = [crbm.Sampler(**sp) for sp in specs]
+    batch = crbm.Batch(batched)
+    for n in (6, 11):
+        batch.sweep(n)
+        for t in twins:
+            t.sweep(n)
+    for a, b in zip(batched, twins):
+        assert np.array_equal(a.get_spins(), b.get_spins())
+        assert np.array_equal(a.observables(), b.observables())
+    batch.close()
+
+
+def test_rectangle_validation():
+    ok = dict(J=[1.0], Jp=[1.0], h=[0.5], beta=[2.0])
+    for kw, code in ((dict(L_cols=2), crbm.CRBM_EINVAL), (dict(periodic_cols=5), crbm.CRBM_EINVAL),
+                     (dict(L_cols=8, sq_every=2), crbm.CRBM_EINVAL),
+                     (dict(periodic_cols=OPEN, sq_every=2), crbm.CRBM_EINVAL),
+                     (dict(L_cols=8, layout=crbm.CRBM_LAYOUT_STREAM), crbm.CRBM_EUNSUPPORTED)):
+        with pytest.raises(crbm.CrbmError) as e:
+            crbm.Sampler(6, ok, 32, **kw)
+        assert e.value.code == code, kw
+    ladder = dict(J=[1.0] * 32, Jp=[1.0] * 32, h=[0.5] * 32, h_odd=[1.0] * 32,
+                  beta=list(0.5 + 0.1 * np.arange(32)))
+    with pytest.raises(crbm.CrbmError) as e:
+        crbm.Sampler(6, ladder, 32, chain_param=np.arange(32), swap_every=2)
+    assert e.value.code == crbm.CRBM_EUNSUPPORTED

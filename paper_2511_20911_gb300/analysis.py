@@ -44,3 +44,14 @@ def effective_samples(x, burn_frac=0.1, c=5.0):
     tau = integrated_autocorr_time(x, c)
     ess = x.shape[1] / (2.0 * tau)
     return np.where(np.isfinite(ess), ess, 0.0)
+
+
+def structure_factor(spins):
+    """Static structure factor per spin of configurations [n][rows][cols] of
+    +-1, S(q) = |sum_r s_r e^{i q.r}|^2 / N averaged over the n configurations,
+    at q = 2 pi (nR / rows, nC / cols) (Sec. IV.B, Eq. 11; defined for open
+    edges too, unlike the periodic correlation sums the sampler accumulates).
+    Returns [rows][cols] doubles."""
+    s = np.asarray(spins, dtype=np.float64)
+    f = np.fft.fft2(s, axes=(-2, -1))
+    return (np.abs(f) ** 2).mean(0) / (s.shape[-1] * s.shape[-2])

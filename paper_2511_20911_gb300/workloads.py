@@ -93,3 +93,16 @@ def proposal_eval_workload(L, n_chains=4096, betas=(1.5, 2.0, 3.0), h=3.0):
     return dict(L=L, params=params, n_chains=n_chains,
                 chain_param=(np.arange(n_chains) * len(betas) // n_chains).astype(np.int32),
                 seed=77)
+
+
+def strip_workload(hs=(3.0, 4.5), betas=(1.0, 2.0, 4.0), chains_per_point=256, rows=18, width=12):
+    """Laterally confined SS strip (Sec. III): `rows` periodic rows of `width`
+    spins with open edges across the width, J = 1, J'/J = 1.5 (the spin-liquid
+    cut of the paper: an ordered up-up-down state below h = 3.5, a classical
+    spin liquid above), h and beta on a small grid."""
+    pts = [(b, h) for h in hs for b in betas]
+    params = dict(J=[1.0] * len(pts), Jp=[1.5] * len(pts), h=[q4(h) for _, h in pts],
+                  beta=[b for b, _ in pts])
+    n = chains_per_point * len(pts)
+    return dict(L=rows, L_cols=width, periodic=True, periodic_cols=2, params=params, n_chains=n,
+                chain_param=(np.arange(n) // chains_per_point).astype(np.int32), seed=12, measure_every=10)

@@ -102,3 +102,26 @@ def test_rectangle_validation():
     with pytest.raises(crbm.CrbmError) as e:
         crbm.Sampler(6, ladder, 32, chain_param=np.arange(32), swap_every=2)
     assert e.value.code == crbm.CRBM_EUNSUPPORTED
+
+
+@pytest.mark.slow
+def test_strip_workload_sampled_chains(orc):
+    """The laterally confined strip workload at full size (18 periodic rows of
+    12 open columns, 2304 chains over 6 (beta, h) points): 32 chains spread
+    over every word against the oracle, and its S(q) from the sampled spins."""
+    from paper_2511_20911_gb300 import analysis
+    w = workloads.strip_workload()
+    s = crbm.Sampler(w["L"], w["params"], w["n_chains"], chain_param=w["chain_param"], seed=w["seed"],
+                     periodic=w["periodic"], L_cols=w["L_cols"], periodic_cols=w["periodic_cols"],
+                     measure_every=w["measure_every"])
+    n = 30
+    s.sweep(n)
+    ids = np.linspace(0, w["n_chains"] - 1, 32).astype(np.uint32)
+    spins = orc.init_spins((w["L"], w["L_cols"]), ids, w["seed"])
+    sums, _, _ = orc.run((w["L"], w["L_cols"]), w["params"], w["chain_param"][ids], spins, w["seed"], 0, n,
+                         w["measure_every"], chain_ids=ids, periodic=(True, False))
+    got = s.get_spins()
+    assert np.array_equal(got[ids], spins)
+    assert np.array_equal(s.observables()[ids], sums)
+    sq = analysis.structure_factor(got)
+    assert sq.shape == (w["L"], w["L_cols"]) and abs(sq.mean() - 1.0) < 1e-9   # sum rule: mean_q S = 1

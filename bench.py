@@ -57,7 +57,7 @@ def parse():
     ap.add_argument("--steps", type=int, default=10)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
-    ap.add_argument("--workload", default="grid", choices=["grid", "stream", "batch", "proposal"])
+    ap.add_argument("--workload", default="grid", choices=["grid", "stream", "batch", "proposal", "tts"])
     ap.add_argument("--sweeps-per-step", type=int, default=None)
     ap.add_argument("--measure-every", type=int, default=10)
     ap.add_argument("--cpu-seconds", type=float, default=8.0)
@@ -155,7 +155,7 @@ def workload_config(name, rank):
     return w
 
 
-DEFAULT_SWEEPS = {"grid": 2000, "stream": 20, "batch": 500, "proposal": 1000}
+DEFAULT_SWEEPS = {"grid": 2000, "stream": 20, "batch": 500, "proposal": 1000, "tts": 4000}
 
 
 def cpu_baseline(w, seconds, precision=0):
@@ -227,6 +227,70 @@ def config_dict(w, args):
             "layout": "smem (persistent, dynamically scheduled)" if args.workload == "grid" else "stream",
             "l2": "flushed between steps (256 MiB write outside the step events)",
             "parallelism": f"replicas x{args.gpus}"}
+
+
+# The paper's time-to-solution phases (Sec. III, "Hardware Acceleration") and
+# the times it prints for its FPGA (lattice sizes not stated in the text).
+TTS_PHASES = (("FM", 1.0, 1.0, 7.0, 33e-9), ("dimer", 1.0, 2.5, 0.0, 5e-6), ("Neel", 1.0, 1.0, 0.0, 200e-6),
+              ("1/3 plateau", 1.0, 0.5, 4.0, 120e-3))
+
+
+def run_tts(args, rank, ws):
+    """Time to solution: per lattice size one context with 1024 chains at each
+    of the paper's four phase points (beta = 4), every chain's first sweep at
+    its brute-force supercell ground-state energy recorded on the device
+    (measured every sweep), TTS_99 = T log(0.01) / log(1 - p_gnd) in sweeps
+    and in seconds of this GPU's sweep time for the whole context."""
+    import torch
+    import paper_2511_20911_gb300 as crbm
+    from paper_2511_20911_gb300 import analysis
+    S = args.sweeps_per_step or 4000
+    per, beta = 1024, 4.0
+    rows, total_updates, total_s = [], 0, 0.0
+    with ClockSampler(torch.cuda.current_device()) as clk:
+        for L in (6, 12, 18):
+            params = dict(J=[p[1] for p in TTS_PHASES], Jp=[p[2] for p in TTS_PHASES],
+                          h=[p[3] for p in TTS_PHASES], beta=[beta] * len(TTS_PHASES))
+            n = per * len(TTS_PHASES)
+            cp = (np.arange(n) // per).astype(np.int32)
+            s = crbm.Sampler(L, params, n, chain_param=cp, seed=replica_seed(21 + L, rank), measure_every=1,
+                             layout=crbm.CRBM_LAYOUT_SMEM)
+            e_gs = [analysis.ground_state_energy(L, J, Jp, h)[0] for _, J, Jp, h, _ in TTS_PHASES]
+            s.set_targets(e_gs)
+            a = torch.cuda.Event(enable_timing=True)
+            b = torch.cuda.Event(enable_timing=True)
+            torch.cuda.synchronize()
+            a.record()
+            s.sweep(S)
+            b.record()
+            torch.cuda.synchronize()
+            sec = a.elapsed_time(b) / 1e3
+            total_s += sec
+            total_updates += n * L * L * S
+            hits = s.first_hits()
+            for k, (name, J, Jp, h, paper) in enumerate(TTS_PHASES):
+                pg, T, tts = analysis.time_to_solution(hits[cp == k], S)
+                rows.append({"phase": name, "L": L, "J": J, "Jp": Jp, "h": h, "beta": beta, "p_gnd": pg,
+                             "T_sweeps": T, "tts99_sweeps": tts,
+                             "tts99_s": None if tts is None else tts * sec / S, "paper_fpga_s": paper,
+                             "e_gs_per_spin": e_gs[k] / 16.0 / (L * L)})
+    t_total = max_over_ranks(total_s, ws)
+    out = {"metric": METRIC, "value": replica_value(total_updates, ws, t_total), "unit": UNIT, "n_gpus": ws,
+           "steps": 1, "warmup": 0, "ms_per_step": t_total * 1e3, "higher_is_better": True, "scaling": "weak",
+           "vs_baseline": None, "dtype": "u32", "data": "synthetic",
+           "config": {"workload": "time to solution at the paper's FM, dimer, Neel and 1/3-plateau points, "
+                                  f"L in {{6,12,18}}, {per} chains per point, beta={beta}, {S} sweeps, "
+                                  "ground states by brute force over even supercells of <= 16 sites",
+                      "parallelism": f"replicas x{ws}"},
+           "clocks": clk.summary(),
+           "tts": rows,
+           "note": "tts99_s = TTS_99 in sweeps x this GPU's time per sweep of the whole context (all "
+                   f"{per * len(TTS_PHASES)} chains advance together); paper_fpga_s is the FPGA time the paper "
+                   "prints for the phase"}
+    if rank == 0:
+        print(json.dumps(out))
+    if ws > 1:
+        torch.distributed.destroy_process_group()
 
 
 def run_batch(args, rank, ws):
@@ -384,6 +448,9 @@ def main():
         return
     if args.workload == "proposal":
         run_proposal(args, rank, ws)
+        return
+    if args.workload == "tts":
+        run_tts(args, rank, ws)
         return
     import torch
     import paper_2511_20911_gb300 as crbm

@@ -168,6 +168,18 @@ int64_t crbm_sweep_count(const crbm_ctx* ctx);
  * Synchronises the stream. */
 int crbm_observables(crbm_ctx* ctx, int64_t* out, size_t n_out);
 
+/* Time to solution (Sec. III, "Hardware Acceleration").  Give every
+ * parameter point a target energy in 1/16 units, E = qJ NJ + qJ' NJ' - qh M
+ * (Q.4 couplings; e.g. its ground-state energy): from then on every
+ * measurement (measure_every) records, per chain, the first global sweep
+ * count t + 1 after which the chain's energy was at or below its target.
+ * crbm_set_targets (host array of n_params, synchronises) also clears the
+ * records; crbm_first_hits writes host out[n_chains] int64, -1 for a chain
+ * that has not reached its target.  With replica exchange the records belong
+ * to rungs.  Not part of checkpoints. */
+int crbm_set_targets(crbm_ctx* ctx, const int64_t* e_target, int32_t n_params);
+int crbm_first_hits(crbm_ctx* ctx, int64_t* out, size_t n_out);
+
 /* Time series, host array out[series_len][n_chains][3] int32 = (NJ, NJ', M)
  * per measurement (entries past the number of measurements are zero). */
 int crbm_series(crbm_ctx* ctx, int32_t* out, size_t n_out);

@@ -32,7 +32,7 @@ ABI_FUNCTIONS = (
     "crbm_create", "crbm_destroy", "crbm_sweep", "crbm_sweep_count", "crbm_observables",
     "crbm_series", "crbm_correlations", "crbm_structure_factor", "crbm_reset_observables",
     "crbm_get_spins", "crbm_set_spins", "crbm_get_tables", "crbm_get_permutation", "crbm_layout",
-    "crbm_launch_count", "crbm_autotune", "crbm_warps", "crbm_batch_create", "crbm_batch_sweep",
+    "crbm_launch_count", "crbm_autotune", "crbm_warps", "crbm_set_targets", "crbm_first_hits", "crbm_batch_create", "crbm_batch_sweep",
     "crbm_batch_threads", "crbm_batch_cluster", "crbm_batch_last_error", "crbm_batch_destroy",
     "crbm_proposal_create", "crbm_proposal_destroy", "crbm_proposal_set_weights",
     "crbm_proposal_get_weights", "crbm_proposal_train", "crbm_proposal_loss_grad",
@@ -102,6 +102,8 @@ def load_library(path: str | None = None):
         "crbm_batch_sweep": (c.c_int, [vp, c.c_int64]),
         "crbm_batch_threads": (c.c_int, [vp]),
         "crbm_batch_cluster": (c.c_int, [vp]),
+        "crbm_set_targets": (c.c_int, [vp, c.POINTER(c.c_int64), c.c_int32]),
+        "crbm_first_hits": (c.c_int, [vp, c.POINTER(c.c_int64), c.c_size_t]),
         "crbm_batch_last_error": (c.c_char_p, [vp]),
         "crbm_batch_destroy": (None, [vp]),
         "crbm_proposal_create": (c.c_int, [c.POINTER(vp), c.c_int32, c.c_uint64]),
@@ -251,6 +253,17 @@ class Sampler:
         out = np.zeros((self.n_params, self.L, self.L), np.float64)
         _check(self._lib.crbm_structure_factor(self._ctx, _ptr(out, ctypes.c_double), out.size),
                self._ctx)
+        return out
+
+    def set_targets(self, e_target):
+        """Target energy per parameter point (1/16 units); clears the first-hit records."""
+        t = np.ascontiguousarray(e_target, np.int64)
+        _check(self._lib.crbm_set_targets(self._ctx, _ptr(t, ctypes.c_int64), len(t)), self._ctx)
+
+    def first_hits(self):
+        """Per chain, the first sweep count after which its energy reached the target (-1: not yet)."""
+        out = np.zeros(self.n_chains, np.int64)
+        _check(self._lib.crbm_first_hits(self._ctx, _ptr(out, ctypes.c_int64), out.size), self._ctx)
         return out
 
     def reset_observables(self):

@@ -55,3 +55,55 @@ def structure_factor(spins):
     s = np.asarray(spins, dtype=np.float64)
     f = np.fft.fft2(s, axes=(-2, -1))
     return (np.abs(f) ** 2).mean(0) / (s.shape[-1] * s.shape[-2])
+
+
+def ss_counts(spins):
+    """Exact (N_J, N_J', M) of periodic SS configurations [n][rows][cols] of
+    +-1 (even sides): J bonds between lattice neighbours, J' dimers on the
+    plaquettes (2i, 2j) ('\\') and (2i+1, 2j+1) ('/'), as the ten filters place
+    them.  Returns three int64 arrays of length n."""
+    s = np.asarray(spins, dtype=np.int64)
+    nJ = (s * np.roll(s, -1, axis=2)).sum((1, 2)) + (s * np.roll(s, -1, axis=1)).sum((1, 2))
+    a = s[:, 0::2, 0::2] * np.roll(np.roll(s, -1, 1), -1, 2)[:, 0::2, 0::2]           # (2i,2j)-(2i+1,2j+1)
+    b = np.roll(s, -2, 2)[:, 1::2, 0::2] * np.roll(np.roll(s, -2, 1), -1, 2)[:, 0::2, 0::2]
+    return nJ, a.sum((1, 2)) + b.sum((1, 2)), s.sum((1, 2))
+
+
+def ground_state_energy(L, J, Jp, h, max_sites=16):
+    """Lowest energy per lattice (1/16 units, E = qJ N_J + qJ' N_J' - qh M with
+    Q.4 couplings) over all configurations of an L x L periodic lattice that
+    repeat with an even a x b supercell (a, b dividing L, a b <= max_sites):
+    the exact ground state whenever it has such a period, as the FM, Neel,
+    dimer and 1/3-plateau states do.  Also returns the supercell and pattern."""
+    qJ, qJp, qh = (int(round(16 * x)) for x in (J, Jp, h))
+    best = None
+    for a in range(2, L + 1, 2):
+        for b in range(2, L + 1, 2):
+            if L % a or L % b or a * b > max_sites:
+                continue
+            n = a * b
+            x = np.arange(1 << n, dtype=np.int64)
+            cells = (((x[:, None] >> np.arange(n)) & 1) * 2 - 1).reshape(-1, a, b)
+            nJ, nP, M = ss_counts(cells)
+            E = (qJ * nJ + qJp * nP - qh * M) * (L * L // n)
+            i = int(np.argmin(E))
+            if best is None or E[i] < best[0]:
+                best = (int(E[i]), (a, b), cells[i].copy())
+    return best
+
+
+def time_to_solution(first_hits, n_sweeps, level=99.0):
+    """TTS_l = T log(1 - l/100) / log(1 - p_gnd) (Sec. III, "Hardware
+    Acceleration"), in sweeps, from the first hitting sweeps of independent
+    runs of n_sweeps sweeps (-1: no hit): p_gnd = fraction of runs that reached
+    the ground state, T = their mean hitting sweep.  p_gnd = 1 gives TTS_100 =
+    T; p_gnd = 0 gives None.  Returns (p_gnd, T, TTS_l)."""
+    h = np.asarray(first_hits)
+    ok = (h >= 0) & (h <= n_sweeps)
+    p = float(ok.mean())
+    if p == 0.0:
+        return p, None, None
+    T = float(h[ok].mean())
+    if p == 1.0:
+        return p, T, T
+    return p, T, T * np.log(1.0 - level / 100.0) / np.log(1.0 - p)

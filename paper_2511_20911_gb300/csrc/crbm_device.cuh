@@ -243,6 +243,13 @@ __device__ __forceinline__ void post_sweep_warp0(const SweepArgs& a, int* s_cnt,
         acc[8 * 32] += nJ * nP;
         acc[9 * 32] += nJ * M;
         acc[10 * 32] += nP * M;
+        if (a.hit) {  // time to solution: first measured sweep at or below the target energy
+            int64_t* ht = a.hit + 2 * static_cast<size_t>(row);
+            const int32_t* q = a.hit_q + 4 * static_cast<size_t>(row);
+            const int64_t E = static_cast<int64_t>(q[0]) * nJ + static_cast<int64_t>(q[1]) * nP -
+                              static_cast<int64_t>(q[2]) * M;
+            if (ht[1] < 0 && E <= ht[0]) ht[1] = static_cast<int64_t>(t) + 1;
+        }
     }
     if (do_swap) {
         const int32_t* q = a.wq + 3 * word;

@@ -230,7 +230,7 @@ int dalloc(crbm_ctx* ctx, T*& ptr, size_t count) {
 void free_device(DeviceState& d) {
     void* ptrs[] = {d.v, d.tab, d.ctab, d.crec, d.sneg, d.gep, d.sums, d.series, d.corr,
                     d.seg, d.segmask, d.spins8, d.h, d.cnt, d.sob, d.swap_tab, d.swap_off,
-                    d.swap_len, d.wq, d.chain_bh, d.chain_q, d.sched};
+                    d.swap_len, d.wq, d.chain_bh, d.chain_q, d.sched, d.hit, d.hit_q};
     for (void* p : ptrs)
         if (p) cudaFree(p);
     d = DeviceState{};
@@ -265,6 +265,8 @@ SweepArgs fill_sweep_args(const crbm_ctx* ctx, int chunk) {
     a.crec = ctx->d.crec;
     a.sneg = ctx->d.sneg;
     a.gep = ctx->d.gep;
+    a.hit = ctx->d.hit;
+    a.hit_q = ctx->d.hit_q;
     a.sums = ctx->d.sums;
     a.series = ctx->d.series;
     a.h = ctx->d.h;
@@ -871,6 +873,42 @@ int crbm_get_permutation(crbm_ctx* ctx, int32_t* out, size_t n_out) {
                                     cudaMemcpyDeviceToHost, ctx->stream);
     if (e == cudaSuccess) e = cudaStreamSynchronize(ctx->stream);
     return e == cudaSuccess ? CRBM_OK : cuda_fail(ctx, e, "crbm_get_permutation");
+}
+
+int crbm_set_targets(crbm_ctx* ctx, const int64_t* e_target, int32_t n) {
+    if (!ctx || !e_target || n != ctx->n_params) return fail(ctx, CRBM_EINVAL, "need one target per parameter point");
+    const size_t np = static_cast<size_t>(ctx->n_words) * 32;
+    DeviceState& d = ctx->d;
+    int rc = CRBM_OK;
+    if (!d.hit && ((rc = dalloc(ctx, d.hit, 2 * np)) || (rc = dalloc(ctx, d.hit_q, 4 * np)))) return rc;
+    std::vector<int64_t> ht(2 * np);
+    std::vector<int32_t> hq(4 * np, 0);
+    for (size_t c = 0; c < np; ++c) {
+        const bool real = c < static_cast<size_t>(ctx->n_chains);
+        const int pp = real ? ctx->chain_param[c] : 0;
+        ht[2 * c] = real ? e_target[pp] : INT64_MIN;  // padding chains never count
+        ht[2 * c + 1] = -1;
+        hq[4 * c] = ctx->q[0][pp];
+        hq[4 * c + 1] = ctx->q[1][pp];
+        hq[4 * c + 2] = ctx->q[2][pp];
+    }
+    cudaError_t e = cudaMemcpyAsync(d.hit, ht.data(), ht.size() * 8, cudaMemcpyHostToDevice, ctx->stream);
+    if (e == cudaSuccess)
+        e = cudaMemcpyAsync(d.hit_q, hq.data(), hq.size() * 4, cudaMemcpyHostToDevice, ctx->stream);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(ctx->stream);
+    return e == cudaSuccess ? CRBM_OK : cuda_fail(ctx, e, "crbm_set_targets");
+}
+
+int crbm_first_hits(crbm_ctx* ctx, int64_t* out, size_t n_out) {
+    if (!ctx || !out) return CRBM_EINVAL;
+    if (!ctx->d.hit) return fail(ctx, CRBM_EINVAL, "no targets set (crbm_set_targets)");
+    if (n_out < static_cast<size_t>(ctx->n_chains)) return fail(ctx, CRBM_EINVAL, "output buffer too small");
+    std::vector<int64_t> ht(2 * static_cast<size_t>(ctx->n_chains));
+    cudaError_t e = cudaMemcpyAsync(ht.data(), ctx->d.hit, ht.size() * 8, cudaMemcpyDeviceToHost, ctx->stream);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(ctx->stream);
+    if (e != cudaSuccess) return cuda_fail(ctx, e, "crbm_first_hits");
+    for (int c = 0; c < ctx->n_chains; ++c) out[c] = ht[2 * static_cast<size_t>(c) + 1];
+    return CRBM_OK;
 }
 
 int crbm_get_tables(crbm_ctx* ctx, uint32_t* out, size_t n_out, int32_t* dims) {

@@ -171,6 +171,8 @@ struct DeviceState {
     float* chain_bh = nullptr;    // block proposals: [n_words * 32][2] beta, h (bf16-rounded)
     int32_t* chain_q = nullptr;   // block proposals: [n_words * 32][3] Q.4 J, J', h
     int* sched = nullptr;         // persistent scheduler: [n_words + 4] word states (chunks done, held)
+    int64_t* hit = nullptr;       // time to solution: [n_words * 32][2] target energy, first hitting sweep
+    int32_t* hit_q = nullptr;     // [n_words * 32][4] Q.4 J, J', h of each chain's point
 };
 
 struct SweepArgs {
@@ -193,6 +195,8 @@ struct SweepArgs {
     int swap_every;       // 0 = no replica exchange
     int n_bands;          // batched cluster launch: CTAs (bands of cell rows) per word, else 1
     const int64_t* clock; // batch launches: device {sweep, measurements} (else t0 / meas0)
+    int64_t* hit;         // time to solution (nullptr = off): per chain {target energy, first hitting sweep}
+    const int32_t* hit_q; // per chain {Q.4 J, J', h, 0}
     int64_t* corr;
     const int32_t* seg;
     const uint32_t* segmask;

@@ -113,6 +113,7 @@ int crbm_autotune(crbm_ctx* ctx, int64_t probe_sweeps, int32_t* best_warps) {
         a.series_len = 0;
         a.sq_every = 0;
         a.clock = nullptr;
+        a.hit = nullptr;  // the probes record no time to solution
         a.n_sweeps = static_cast<int>(std::max<int64_t>(1, probe_sweeps / 4));
         e = launch_one(a, ctx, w);  // warm-up
         a.n_sweeps = static_cast<int>(probe_sweeps);

@@ -242,7 +242,7 @@ __global__ void __launch_bounds__(kStreamThreads, CRBM_STREAM_MIN_BLOCKS) k_stre
 
 // Turn the per-chain counts into (NJ, NJ', M), append the series entry,
 // accumulate the sums and clear the counts.
-__global__ void k_stream_finalize(const SweepArgs a, int64_t meas) {
+__global__ void k_stream_finalize(const SweepArgs a, int64_t meas, int64_t sweeps_done) {
     const int c = blockIdx.x * blockDim.x + threadIdx.x;
     if (c >= a.n_chains_padded) return;
     const Geometry& g = a.g;
@@ -269,6 +269,13 @@ __global__ void k_stream_finalize(const SweepArgs a, int64_t meas) {
     s[8] += nJ * nP;
     s[9] += nJ * M;
     s[10] += nP * M;
+    if (a.hit) {  // time to solution: first measured sweep at or below the target energy
+        int64_t* ht = a.hit + 2 * static_cast<size_t>(c);
+        const int32_t* q = a.hit_q + 4 * static_cast<size_t>(c);
+        const int64_t E = static_cast<int64_t>(q[0]) * nJ + static_cast<int64_t>(q[1]) * nP -
+                          static_cast<int64_t>(q[2]) * M;
+        if (ht[1] < 0 && E <= ht[0]) ht[1] = sweeps_done;
+    }
 }
 
 }  // namespace
@@ -284,7 +291,7 @@ cudaError_t launch_sweep_stream(const SweepArgs& a, cudaStream_t st, int64_t* la
         *launches += 2;
         if (a.measure_every > 0 && (t + 1u) % static_cast<uint32_t>(a.measure_every) == 0u) {
             k_stream_count<<<grid, kStreamThreads, 0, st>>>(a);
-            k_stream_finalize<<<(a.n_chains_padded + 255) / 256, 256, 0, st>>>(a, meas);
+            k_stream_finalize<<<(a.n_chains_padded + 255) / 256, 256, 0, st>>>(a, meas, static_cast<int64_t>(t) + 1);
             *launches += 2;
             ++meas;
         }

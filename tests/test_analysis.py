@@ -22,3 +22,30 @@ def test_structure_factor_closed_forms():
     rng = np.random.default_rng(3)
     rnd = rng.choice([-1.0, 1.0], size=(4000, R, C))
     assert abs(analysis.structure_factor(rnd).mean() - 1.0) < 0.02
+
+
+def test_ss_counts_match_the_oracle(orc):
+    from paper_2511_20911_gb300 import analysis
+    rng = np.random.default_rng(9)
+    for L, Lc in ((6, 6), (4, 8), (18, 18), (2, 4)):
+        v = rng.choice(np.array([-1, 1], np.int8), size=(5, L, Lc))
+        nJ, nP, M = analysis.ss_counts(v)
+        for k in range(5):
+            if L >= 3 and Lc >= 3:
+                assert (nJ[k], nP[k], M[k]) == orc.counts(v[k], (L, Lc)), (L, Lc, k)
+
+
+def test_ground_states_of_the_known_phases():
+    """Per spin: FM 2J + J'/2 - h; Neel -2J + J'/2; dimer -J'/2 (J' > 2J);
+    the 1/3 plateau (J' = J/2, h = 4): rows up-up-down, neighbouring rows
+    shifted by one, so each row and each column pair contributes -1/3 of a
+    bond per site (N_J = -2N/3), the dimers average -1/3 (N_J' = -N/6) and
+    M = N/3: E/N = -2J/3 - J'/6 - h/3."""
+    from paper_2511_20911_gb300 import analysis
+    for L in (6, 12):
+        N = L * L
+        assert analysis.ground_state_energy(L, 1.0, 1.0, 7.0)[0] == 16 * N * (2 + 0.5 - 7)
+        assert analysis.ground_state_energy(L, 1.0, 1.0, 0.0)[0] == 16 * N * (-2 + 0.5)
+        assert analysis.ground_state_energy(L, 1.0, 2.5, 0.0)[0] == 16 * N * (-1.25)
+        e, cell, pat = analysis.ground_state_energy(L, 1.0, 0.5, 4.0)
+        assert e == round(16 * N * (-2 / 3 - 0.5 / 6 - 4 / 3)) and pat.sum() * 3 == pat.size

@@ -1,0 +1,95 @@
+"""Time-to-solution records on the GPU: per chain, the first measured sweep
+whose exact energy is at or below its point's target, against the same
+quantity read from the oracle's time series; and low-temperature runs that
+reach the brute-force ground states of the paper's phases."""
+import numpy as np
+import pytest
+
+import paper_2511_20911_gb300 as crbm
+from paper_2511_20911_gb300 import analysis, workloads
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _gpu():
+    torch = pytest.importorskip("torch")
+    if not torch.cuda.is_available():
+        pytest.skip("no GPU")
+    crbm.load_library()
+
+
+def oracle_first_hits(series, q, target, every):
+    """series [chain][T][3] (NJ, NJ', M), q [chain][3] Q.4 couplings."""
+    E = q[:, None, 0] * series[..., 0] + q[:, None, 1] * series[..., 1] - q[:, None, 2] * series[..., 2]
+    hit = E <= target[:, None]
+    first = np.where(hit.any(1), hit.argmax(1), -1)
+    return np.where(first >= 0, (first + 1) * every, -1)
+
+
+@pytest.mark.parametrize("L,periodic,every,layout,precision", [
+    (6, True, 1, crbm.CRBM_LAYOUT_SMEM, 0), (18, True, 2, crbm.CRBM_LAYOUT_SMEM, 0),
+    (7, False, 1, crbm.CRBM_LAYOUT_SMEM, 0), (20, True, 1, crbm.CRBM_LAYOUT_STREAM, 0),
+    (6, True, 3, crbm.CRBM_LAYOUT_SMEM, 1)])
+def test_first_hits_match_the_oracle_series(orc, L, periodic, every, layout, precision):
+    rng = np.random.default_rng(L * 10 + every)
+    params = workloads.random_params(rng, 3)
+    n, T = 70, 40
+    cp = (np.arange(n) % 3).astype(np.int32)
+    ids = np.arange(n, dtype=np.uint32)
+    spins = orc.init_spins(L, ids, 5)
+    _, ser, _ = orc.run(L, params, cp, spins, 5, 0, T, every, chain_ids=ids, periodic=periodic,
+                        series_cap=T // every, precision=precision)
+    q = np.array([[round(16 * params[k][p]) for k in ("J", "Jp", "h")] for p in cp], np.int64)
+    E = q[:, None, 0] * ser[..., 0] + q[:, None, 1] * ser[..., 1] - q[:, None, 2] * ser[..., 2]
+    targets = np.array([int(np.percentile(E[cp == p], 20)) for p in range(3)], np.int64)
+    want = oracle_first_hits(ser, q, targets[cp], every)
+    assert (want >= 0).any() and (want < 0).any()
+    s = crbm.Sampler(L, params, n, chain_param=cp, seed=5, periodic=periodic, measure_every=every,
+                     layout=layout, precision=precision)
+    s.set_targets(targets)
+    for k in (T // 2, T - T // 2):
+        s.sweep(k)
+    assert np.array_equal(s.first_hits(), want)
+    s.set_targets(targets)                      # clears the records
+    assert (s.first_hits() == -1).all()
+
+
+def test_first_hits_follow_rungs_under_tempering(orc):
+    L, n_lad, every = 6, 2, 1
+    betas = 0.2 * (50.0 ** (np.arange(32) / 31.0))
+    params = dict(J=[1.0] * 32, Jp=[1.5] * 32, h=[1.0] * 32, beta=list(betas))
+    cp = np.tile(np.arange(32, dtype=np.int32), n_lad)
+    spins = orc.init_spins(L, np.arange(32 * n_lad, dtype=np.uint32), 8)
+    sob = np.tile(np.arange(32, dtype=np.int32), (n_lad, 1))
+    T = 30
+    _, ser = orc.run_pt(L, params, cp, spins, sob, 8, 0, T, every, 2, series_cap=T)
+    q = np.array([[16, 24, 16]] * (32 * n_lad), np.int64)
+    target = np.full(32, int(np.percentile(q[0, 0] * ser[..., 0] + q[0, 1] * ser[..., 1] - q[0, 2] * ser[..., 2], 15)))
+    want = oracle_first_hits(ser, q, target[cp], every)
+    s = crbm.Sampler(L, params, 32 * n_lad, chain_param=cp, seed=8, measure_every=every, swap_every=2)
+    s.set_targets(target)
+    s.sweep(T)
+    assert np.array_equal(s.first_hits(), want)
+
+
+@pytest.mark.parametrize("J,Jp,h", [(1.0, 1.0, 7.0), (1.0, 1.0, 0.0), (1.0, 2.5, 0.0), (1.0, 0.5, 4.0)])
+def test_low_temperature_runs_reach_the_ground_state(J, Jp, h):
+    """FM, Neel, dimer and 1/3-plateau points of the paper at L=6, beta=4:
+    chains reach the brute-force supercell ground state within 2000 sweeps
+    (every chain in the field-driven FM phase; the long-range ordered Neel
+    state is the slowest for block Gibbs), and no chain ever records an
+    energy below it."""
+    L = 6
+    e_gs = analysis.ground_state_energy(L, J, Jp, h)[0]
+    s = crbm.Sampler(L, dict(J=[J], Jp=[Jp], h=[h], beta=[4.0]), 256, seed=3, measure_every=1, series_len=2000)
+    s.set_targets([e_gs])
+    s.sweep(2000)
+    p, T, tts = analysis.time_to_solution(s.first_hits(), 2000)
+    assert p > 0.0, (J, Jp, h, p)
+    if h == 7.0:
+        assert p == 1.0
+    ser = s.series().astype(np.int64)
+    q = [round(16 * x) for x in (J, Jp, h)]
+    E = q[0] * ser[..., 0] + q[1] * ser[..., 1] - q[2] * ser[..., 2]
+    assert E.min() == e_gs

@@ -193,6 +193,10 @@ def run_reference(args, rank, ws):
     """Reference arm: the CPU oracle timed on the host cores."""
     if rank != 0:
         return
+    if args.workload not in ("grid", "stream"):
+        print(json.dumps({"impl": "reference", "unavailable": f"the oracle's timed leg covers the grid and "
+                                                               f"stream workloads, not {args.workload}"}))
+        return
     w = workload_config(args.workload, 0)
     per_step = max(1.0, 60.0 / max(1, args.steps + args.warmup))
     for _ in range(args.warmup):

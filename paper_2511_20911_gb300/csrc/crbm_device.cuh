@@ -38,43 +38,9 @@ __device__ __forceinline__ U4 philox(uint32_t c0, uint32_t c1, uint32_t c2, uint
     return {c0, c1, c2, c3};
 }
 
-// Rounds 1..9 from the state after round 0, with precomputed round keys
+// Rounds 3..9 from the state after round 2, with precomputed round keys
 // rk[2r] = k0 + r W0, rk[2r+1] = k1 + r W1 (kernel parameters, so each key is
 // a constant-bank operand of its XOR).
-__device__ __forceinline__ U4 philox_rounds1to9(uint32_t c0, uint32_t c1, uint32_t c2, uint32_t c3,
-                                                const uint32_t (&rk)[20]) {
-#pragma unroll
-    for (int r = 1; r < 10; ++r) {
-        const uint64_t p0 = static_cast<uint64_t>(kPhiloxM0) * c0;
-        const uint64_t p1 = static_cast<uint64_t>(kPhiloxM1) * c2;
-        const uint32_t n0 = static_cast<uint32_t>(p1 >> 32) ^ c1 ^ rk[2 * r];
-        const uint32_t n2 = static_cast<uint32_t>(p0 >> 32) ^ c3 ^ rk[2 * r + 1];
-        c1 = static_cast<uint32_t>(p1);
-        c3 = static_cast<uint32_t>(p0);
-        c0 = n0;
-        c2 = n2;
-    }
-    return {c0, c1, c2, c3};
-}
-
-// Rounds 2..9 from the state after round 1 (c0, c1, c2, c3).
-__device__ __forceinline__ U4 philox_rounds2to9(uint32_t c0, uint32_t c1, uint32_t c2, uint32_t c3,
-                                                const uint32_t (&rk)[20]) {
-#pragma unroll
-    for (int r = 2; r < 10; ++r) {
-        const uint64_t p0 = static_cast<uint64_t>(kPhiloxM0) * c0;
-        const uint64_t p1 = static_cast<uint64_t>(kPhiloxM1) * c2;
-        const uint32_t n0 = static_cast<uint32_t>(p1 >> 32) ^ c1 ^ rk[2 * r];
-        const uint32_t n2 = static_cast<uint32_t>(p0 >> 32) ^ c3 ^ rk[2 * r + 1];
-        c1 = static_cast<uint32_t>(p1);
-        c3 = static_cast<uint32_t>(p0);
-        c0 = n0;
-        c2 = n2;
-    }
-    return {c0, c1, c2, c3};
-}
-
-// Rounds 3..9 from the state after round 2.
 __device__ __forceinline__ U4 philox_rounds3to9(uint32_t c0, uint32_t c1, uint32_t c2, uint32_t c3,
                                                 const uint32_t (&rk)[20]) {
 #pragma unroll
@@ -104,15 +70,6 @@ __device__ __forceinline__ Round1Sweep round1_sweep(uint32_t X, const uint32_t (
     const uint64_t p = static_cast<uint64_t>(kPhiloxM0) * X;
     return {static_cast<uint32_t>(p), static_cast<uint32_t>(p >> 32) ^ rk[3]};
 }
-// The full Philox-4x32-10 output for round-0 state (X, Y, c2, c3), given
-// r1 = round1_sweep(X) and n2 = r1.hik ^ c3 of the cell.
-__device__ __forceinline__ U4 philox_from_round1(uint32_t Y, const Round1Sweep& r1, uint32_t n2, uint32_t c2,
-                                                 const uint32_t (&rk)[20]) {
-    const uint64_t p1 = static_cast<uint64_t>(kPhiloxM1) * c2;
-    return philox_rounds2to9(static_cast<uint32_t>(p1 >> 32) ^ Y ^ rk[2], static_cast<uint32_t>(p1), n2, r1.lo,
-                             rk);
-}
-
 // Round 2 multiplies word 2 after round 1, which is the cell's n2 for every
 // call of the cell: its product is formed once per cell.
 struct Round2Cell {
@@ -180,12 +137,7 @@ __device__ __forceinline__ uint32_t bit_of(uint32_t word, int lane) { return (wo
 
 __device__ __forceinline__ uint32_t rotr(uint32_t x, uint32_t s) { return __funnelshift_r(x, x, s); }
 
-// Acquire load / release store of a progress counter in global memory.
-__device__ __forceinline__ int ld_acquire(const int* p) {
-    int v;
-    asm volatile("ld.acquire.gpu.global.s32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
-    return v;
-}
+// Release store of a progress counter in global memory.
 __device__ __forceinline__ void st_release(int* p, int v) {
     asm volatile("st.release.gpu.global.s32 [%0], %1;" ::"l"(p), "r"(v) : "memory");
 }

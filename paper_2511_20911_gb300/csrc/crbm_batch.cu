@@ -26,15 +26,20 @@ __global__ void __launch_bounds__(CRBM_SWEEP_MAX_THREADS, CRBM_SWEEP_MAX_THREADS
     if (task.x < 0) return;
     const SweepArgs& a = b.d[task.x];
     const uint32_t t0 = static_cast<uint32_t>(a.clock[0]);
-    if (!a.g.canonical)
+    if (!a.g.canonical) {
         generic::sweep_generic_body(a, task.y);
-    else if (kCluster && task.w > 1) {
+    } else if (kCluster && task.w > 1) {
         const int rank = static_cast<int>(cg::this_cluster().block_rank());
         const int rank0 = task.z < task.w ? rank - task.z : 0;
-        canon::sweep_canon_body<false, true>(a, task.y, t0, a.n_sweeps, a.clock[1], task.z, rank0);
-    }
-    else
+        if (b.smem_rec)
+            canon::sweep_canon_body<true, true>(a, task.y, t0, a.n_sweeps, a.clock[1], task.z, rank0);
+        else
+            canon::sweep_canon_body<false, true>(a, task.y, t0, a.n_sweeps, a.clock[1], task.z, rank0);
+    } else if (b.smem_rec) {
+        canon::sweep_canon_body<true, false>(a, task.y, t0, a.n_sweeps, a.clock[1]);
+    } else {
         canon::sweep_canon_body<false, false>(a, task.y, t0, a.n_sweeps, a.clock[1]);
+    }
 }
 
 // clocks[c] = {sweep, measurements}; every[c] = measure_every of context c.

@@ -225,6 +225,7 @@ constexpr int kMaxBatch = 16;
 struct BatchArgs {
     const int4* items;    // per CTA: (descriptor or -1, word, band, bands)
     int n_desc;
+    int smem_rec;         // 1: canonical members stage their per-cell records in shared memory
     SweepArgs d[kMaxBatch];
 };
 

@@ -167,6 +167,7 @@ struct crbm_batch {
     std::vector<int64_t> staged;       // pinned-free staging for clock uploads
     int threads = 0;
     size_t smem = 0;
+    int smem_rec = 0;                  // canonical members stage their records in shared memory
     int cluster = 1;                   // CTAs per item (thread-block cluster)
     std::vector<int> bands;            // per member: CTAs its words are split over
     cudaGraphExec_t exec = nullptr;
@@ -210,6 +211,16 @@ int crbm_batch_create(crbm_batch** out, crbm_ctx* const* ctxs, int32_t n_ctx) {
         b->ctx.push_back(x);
         warps = std::max(warps, x->warps);
         b->smem = std::max(b->smem, x->g.canonical ? smem_bytes_canon(x->g) : smem_bytes_generic(x->g));
+    }
+    // stage the canonical members' per-cell records in shared memory when all of them fit
+    size_t with_rec = b->smem;
+    for (auto* x : b->ctx)
+        if (x->g.canonical)
+            with_rec = std::max(with_rec, sizeof(uint32_t) * canon_smem_rec_offset(x->g) +
+                                              sizeof(uint4) * static_cast<size_t>(x->g.n_cells) * kCellRec);
+    if (with_rec <= 227 * 1024) {
+        b->smem = with_rec;
+        b->smem_rec = 1;
     }
     b->threads = 32 * warps;
     // Thread-block clusters of `cluster` CTAs (CRBM_BATCH_CLUSTER, default 8,
@@ -319,6 +330,7 @@ int crbm_batch_sweep(crbm_batch* b, int64_t n_sweeps) {
         BatchArgs args{};
         args.items = b->items;
         args.n_desc = n;
+        args.smem_rec = b->smem_rec;
         for (int c = 0; c < n; ++c) {
             args.d[c] = fill_sweep_args(b->ctx[c], static_cast<int>(n_sweeps));
             args.d[c].clock = b->clock + 2 * c;

@@ -16,6 +16,18 @@ template <bool kSmem>
 __device__ __forceinline__ uint4 ld_rec(const uint4* p) {
     return kSmem ? *p : __ldg(p);
 }
+// The first word of a cell's record 5 (Q2.lo).
+template <bool kSmem>
+__device__ __forceinline__ uint32_t ld_rec5(const uint4* r) {
+    return kSmem ? reinterpret_cast<const uint32_t*>(r + 5)[0] : __ldg(reinterpret_cast<const uint32_t*>(r + 5));
+}
+
+// The two halves of a cluster barrier, so that work no other CTA waits for
+// can run between them: arrive (release: this thread's earlier shared-memory
+// stores, local and remote) and wait (acquire).  Every thread of the CTA
+// executes both, the same number of times on every rank.
+__device__ __forceinline__ void cluster_arrive() { asm volatile("barrier.cluster.arrive.release.aligned;" ::: "memory"); }
+__device__ __forceinline__ void cluster_wait() { asm volatile("barrier.cluster.wait.acquire.aligned;" ::: "memory"); }
 
 // CTA barrier, or cluster barrier (release / acquire over the cluster's
 // shared memory) when a word is split over the CTAs of a cluster.
@@ -49,6 +61,12 @@ __device__ __forceinline__ void body_sync() {
 // (band >= n_bands) only keep the barrier count, which is the same for every
 // rank because a cluster never mixes contexts.  Correlations need the whole
 // lattice, so a word with sq_every > 0 is never split (n_bands == 1).
+// A band does the cells other bands wait for first (its last cell row in
+// the hidden half-step, its first in the visible one), arrives at the cluster
+// barrier, does the rest and only then waits.  Those boundary cells are the
+// only ones that read rows a neighbour writes, and they run after the
+// previous barrier completed, so no band overwrites a row its neighbour has
+// yet to read.
 // kPaper: CRBM_PRECISION_PAPER draws (two Philox calls per cell, the visible
 // uniforms passed from the hidden half-step through shared memory).
 template <bool kSmemRec, bool kCluster, bool kPaper = false>
@@ -147,26 +165,62 @@ __device__ __forceinline__ void sweep_canon_body(const SweepArgs& a, int word, u
             for (int cell = c_begin + warp; cell < c_end; cell += nwarp, rec += rstep)
                 visible_cell_rec_paper(sm, ld_rec<kSmemRec>(rec + 3), ld_rec<kSmemRec>(rec + 4), lane4, s_tv, lc);
             __syncthreads();
-        } else {
-        for (int cell = c_begin + warp; cell < c_end; cell += nwarp, rec += rstep) {
-            const uint4 h0 = ld_rec<kSmemRec>(rec), h1 = ld_rec<kSmemRec>(rec + 1), h2 = ld_rec<kSmemRec>(rec + 2);
-            const uint32_t h5 = kSmemRec ? reinterpret_cast<const uint32_t*>(rec + 5)[0]
-                                         : __ldg(reinterpret_cast<const uint32_t*>(rec + 5));
-            const uint32_t w = hidden_cell_rec(sm, h0, h1, h2, h5, s_th, rs, r0l.lo, a.rk, lc);
-            sts_off(sm, h1.y + lane4, w);
-            if (kCluster && nb > 1 && cell >= last_row) sts_off(sm_next, h1.y + lane4, w);
-        }
-        body_sync<kCluster>();
-        rec = rec0;
-        for (int cell = c_begin + warp; cell < c_end; cell += nwarp, rec += rstep) {
-            const uint4 v0 = ld_rec<kSmemRec>(rec + 3), v1 = ld_rec<kSmemRec>(rec + 4);
-            const U4 o = visible_cell_rec(sm, v0, v1, lane4, s_tv, rs, r0l.lo, a.rk, lc);
-            if (kCluster && nb > 1 && cell < first_row_end) {
-                sts_off(sm_prev, v0.x, o.x);
-                sts_off(sm_prev, v0.x + 4u, o.y);
+        } else if (kCluster && nb > 1) {  // a band of a split word, or a padding rank of one
+            // the last cell row first (the next band waits for its hidden words), arrive, the rest,
+            // then wait: the cluster barrier's latency overlaps the interior rows
+            if (active) {
+                for (int cell = last_row + warp; cell < c_end; cell += nwarp) {
+                    const uint4* r = recs + static_cast<size_t>(cell) * kCellRec;
+                    const uint4 h0 = ld_rec<kSmemRec>(r), h1 = ld_rec<kSmemRec>(r + 1), h2 = ld_rec<kSmemRec>(r + 2);
+                    const uint32_t w = hidden_cell_rec(sm, h0, h1, h2, ld_rec5<kSmemRec>(r), s_th, rs, r0l.lo, a.rk, lc);
+                    sts_off(sm, h1.y + lane4, w);
+                    sts_off(sm_next, h1.y + lane4, w);
+                }
             }
-        }
-        body_sync<kCluster>();
+            cluster_arrive();
+            if (active) {
+                for (int cell = c_begin + warp; cell < last_row; cell += nwarp) {
+                    const uint4* r = recs + static_cast<size_t>(cell) * kCellRec;
+                    const uint4 h0 = ld_rec<kSmemRec>(r), h1 = ld_rec<kSmemRec>(r + 1), h2 = ld_rec<kSmemRec>(r + 2);
+                    sts_off(sm, h1.y + lane4,
+                            hidden_cell_rec(sm, h0, h1, h2, ld_rec5<kSmemRec>(r), s_th, rs, r0l.lo, a.rk, lc));
+                }
+            }
+            __syncthreads();
+            cluster_wait();
+            // the first cell row first (the previous band waits for its spins)
+            if (active) {
+                for (int cell = c_begin + warp; cell < first_row_end; cell += nwarp) {
+                    const uint4* r = recs + static_cast<size_t>(cell) * kCellRec;
+                    const uint4 v0 = ld_rec<kSmemRec>(r + 3);
+                    const U4 o = visible_cell_rec(sm, v0, ld_rec<kSmemRec>(r + 4), lane4, s_tv, rs, r0l.lo, a.rk, lc);
+                    sts_off(sm_prev, v0.x, o.x);
+                    sts_off(sm_prev, v0.x + 4u, o.y);
+                }
+            }
+            cluster_arrive();
+            if (active) {
+                for (int cell = first_row_end + warp; cell < c_end; cell += nwarp) {
+                    const uint4* r = recs + static_cast<size_t>(cell) * kCellRec;
+                    visible_cell_rec(sm, ld_rec<kSmemRec>(r + 3), ld_rec<kSmemRec>(r + 4), lane4, s_tv, rs, r0l.lo,
+                                     a.rk, lc);
+                }
+            }
+            __syncthreads();
+            cluster_wait();
+        } else {  // the whole word in one CTA
+            for (int cell = c_begin + warp; cell < c_end; cell += nwarp, rec += rstep) {
+                const uint4 h0 = ld_rec<kSmemRec>(rec), h1 = ld_rec<kSmemRec>(rec + 1),
+                            h2 = ld_rec<kSmemRec>(rec + 2);
+                sts_off(sm, h1.y + lane4,
+                        hidden_cell_rec(sm, h0, h1, h2, ld_rec5<kSmemRec>(rec), s_th, rs, r0l.lo, a.rk, lc));
+            }
+            body_sync<kCluster>();
+            rec = rec0;
+            for (int cell = c_begin + warp; cell < c_end; cell += nwarp, rec += rstep)
+                visible_cell_rec(sm, ld_rec<kSmemRec>(rec + 3), ld_rec<kSmemRec>(rec + 4), lane4, s_tv, rs, r0l.lo,
+                                 a.rk, lc);
+            body_sync<kCluster>();
         }
         const bool do_meas = measuring && (t + 1u) % static_cast<uint32_t>(a.measure_every) == 0u;
         const bool do_swap = a.swap_every > 0 && (t + 1u) % static_cast<uint32_t>(a.swap_every) == 0u;

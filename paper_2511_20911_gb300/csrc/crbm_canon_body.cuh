@@ -209,18 +209,25 @@ __device__ __forceinline__ void sweep_canon_body(const SweepArgs& a, int word, u
             __syncthreads();
             cluster_wait();
         } else {  // the whole word in one CTA
-            for (int cell = c_begin + warp; cell < c_end; cell += nwarp, rec += rstep) {
-                const uint4 h0 = ld_rec<kSmemRec>(rec), h1 = ld_rec<kSmemRec>(rec + 1),
-                            h2 = ld_rec<kSmemRec>(rec + 2);
-                sts_off(sm, h1.y + lane4,
-                        hidden_cell_rec(sm, h0, h1, h2, ld_rec5<kSmemRec>(rec), s_th, rs, r0l.lo, a.rk, lc));
+        for (int cell = c_begin + warp; cell < c_end; cell += nwarp, rec += rstep) {
+            const uint4 h0 = ld_rec<kSmemRec>(rec), h1 = ld_rec<kSmemRec>(rec + 1), h2 = ld_rec<kSmemRec>(rec + 2);
+            const uint32_t h5 = kSmemRec ? reinterpret_cast<const uint32_t*>(rec + 5)[0]
+                                         : __ldg(reinterpret_cast<const uint32_t*>(rec + 5));
+            const uint32_t w = hidden_cell_rec(sm, h0, h1, h2, h5, s_th, rs, r0l.lo, a.rk, lc);
+            sts_off(sm, h1.y + lane4, w);
+            if (kCluster && nb > 1 && cell >= last_row) sts_off(sm_next, h1.y + lane4, w);
+        }
+        body_sync<kCluster>();
+        rec = rec0;
+        for (int cell = c_begin + warp; cell < c_end; cell += nwarp, rec += rstep) {
+            const uint4 v0 = ld_rec<kSmemRec>(rec + 3), v1 = ld_rec<kSmemRec>(rec + 4);
+            const U4 o = visible_cell_rec(sm, v0, v1, lane4, s_tv, rs, r0l.lo, a.rk, lc);
+            if (kCluster && nb > 1 && cell < first_row_end) {
+                sts_off(sm_prev, v0.x, o.x);
+                sts_off(sm_prev, v0.x + 4u, o.y);
             }
-            body_sync<kCluster>();
-            rec = rec0;
-            for (int cell = c_begin + warp; cell < c_end; cell += nwarp, rec += rstep)
-                visible_cell_rec(sm, ld_rec<kSmemRec>(rec + 3), ld_rec<kSmemRec>(rec + 4), lane4, s_tv, rs, r0l.lo,
-                                 a.rk, lc);
-            body_sync<kCluster>();
+        }
+        body_sync<kCluster>();
         }
         const bool do_meas = measuring && (t + 1u) % static_cast<uint32_t>(a.measure_every) == 0u;
         const bool do_swap = a.swap_every > 0 && (t + 1u) % static_cast<uint32_t>(a.swap_every) == 0u;

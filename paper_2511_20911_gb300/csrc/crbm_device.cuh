@@ -148,6 +148,17 @@ __device__ __forceinline__ int warp_sum(int x) {
     return x;
 }
 
+// Time to solution: the first measured sweep at or below the chain's target
+// energy (kept out of line: it runs only at measurements and only when
+// targets are set, and should not add to the sweep loop's registers).
+static __device__ __noinline__ void record_first_hit(int64_t* hit, const int32_t* hit_q, uint32_t row, int64_t nJ,
+                                              int64_t nP, int64_t M, uint32_t t) {
+    int64_t* ht = hit + 2 * static_cast<size_t>(row);
+    const int32_t* q = hit_q + 4 * static_cast<size_t>(row);
+    const int64_t E = static_cast<int64_t>(q[0]) * nJ + static_cast<int64_t>(q[1]) * nP - static_cast<int64_t>(q[2]) * M;
+    if (ht[1] < 0 && E <= ht[0]) ht[1] = static_cast<int64_t>(t) + 1;
+}
+
 // Post-sweep step of the SMEM kernels, run by warp 0 after every warp has
 // added its per-lane counts to s_cnt ([0..31] anti-aligned J filters, [32..63]
 // anti-aligned J' filters, [64..95] +1 spins; lane = replica slot).  Lane k
@@ -195,13 +206,7 @@ __device__ __forceinline__ void post_sweep_warp0(const SweepArgs& a, int* s_cnt,
         acc[8 * 32] += nJ * nP;
         acc[9 * 32] += nJ * M;
         acc[10 * 32] += nP * M;
-        if (a.hit) {  // time to solution: first measured sweep at or below the target energy
-            int64_t* ht = a.hit + 2 * static_cast<size_t>(row);
-            const int32_t* q = a.hit_q + 4 * static_cast<size_t>(row);
-            const int64_t E = static_cast<int64_t>(q[0]) * nJ + static_cast<int64_t>(q[1]) * nP -
-                              static_cast<int64_t>(q[2]) * M;
-            if (ht[1] < 0 && E <= ht[0]) ht[1] = static_cast<int64_t>(t) + 1;
-        }
+        if (a.hit) record_first_hit(a.hit, a.hit_q, row, nJ, nP, M, t);
     }
     if (do_swap) {
         const int32_t* q = a.wq + 3 * word;

@@ -45,9 +45,9 @@ CALLS_PER_CELL_PAPER = 2    # paper precision: 16-bit uniforms, two per Philox w
 # launch of k_sweep_canon_persistent (2000 sweeps of the L=18 grid), and one
 # streamed sweep of the L=384 lattice (k_stream_hidden + k_stream_visible).
 MEASURED_TRAFFIC = {
-    "grid": (8.31e6 + 0.61e6, "per launch; profiles/k_sweep_canon_persistent_L18_grid.md"),
-    "stream": (56.87e6 + 392.34e6 + 454.60e6 + 48.92e6, "per sweep (two launches); profiles/k_stream_L384.md"),
-    "grid_paper": (8.53e6 + 0.63e6, "per launch; profiles/k_sweep_canon_persistent_L18_grid_paper.md"),
+    "grid": (8.44e6 + 0.59e6, "per launch; profiles/k_sweep_canon_persistent_L18_grid.md"),
+    "stream": (56.74e6 + 392.31e6 + 454.82e6 + 48.83e6, "per sweep (two launches); profiles/k_stream_L384.md"),
+    "grid_paper": (8.77e6 + 0.64e6, "per launch; profiles/k_sweep_canon_persistent_L18_grid_paper.md"),
 }
 
 

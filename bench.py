@@ -40,6 +40,7 @@ IMUL_LANES_PER_SM_CLK = 64
 MUL_OPS_PER_CALL = 40
 CALLS_PER_CELL = 4          # 3 hidden calls (10 filters) + 1 visible call (4 spins) per cell
 CALLS_PER_CELL_PAPER = 2    # paper precision: 16-bit uniforms, two per Philox word (14 of 16 used)
+CALLS_PER_CELL_PAPER_STREAM = 3  # streamed paper precision: the visible half-step draws the tag-1 call again
 # DRAM bytes (read + write) of the timed unit, from one ncu capture of the
 # kernels as they stand (commands in the named profiles/ summaries): one bench
 # launch of k_sweep_canon_persistent (2000 sweeps of the L=18 grid), and one
@@ -48,6 +49,7 @@ MEASURED_TRAFFIC = {
     "grid": (8.44e6 + 0.59e6, "per launch; profiles/k_sweep_canon_persistent_L18_grid.md"),
     "stream": (56.74e6 + 392.31e6 + 454.82e6 + 48.83e6, "per sweep (two launches); profiles/k_stream_L384.md"),
     "grid_paper": (8.77e6 + 0.64e6, "per launch; profiles/k_sweep_canon_persistent_L18_grid_paper.md"),
+    "stream_paper": (56.76e6 + 390.29e6 + 454.76e6 + 45.71e6, "per sweep (two launches); profiles/k_stream_L384.md"),
 }
 
 
@@ -64,10 +66,10 @@ def parse():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--precision", default="exact", choices=["exact", "paper"],
                     help="paper: the FPGA's 10-bit weights, 16-bit sigmoid table and 16-bit uniforms "
-                         "(L=18 grid only)")
+                         "(grid and stream workloads)")
     args = ap.parse_args()
-    if args.precision == "paper" and args.workload != "grid":
-        ap.error("--precision paper runs the grid workload (SMEM layout) only")
+    if args.precision == "paper" and args.workload not in ("grid", "stream"):
+        ap.error("--precision paper runs the grid and stream workloads only")
     return args
 
 
@@ -523,14 +525,17 @@ def main():
     e2e_steps = max(1, K // 2)
     e2e_val = w["n_chains"] * w["L"] ** 2 * S * e2e_steps * ws / e2e_t
 
-    calls = (CALLS_PER_CELL_PAPER if paper else CALLS_PER_CELL) * (w["L"] // 2) ** 2 * w["n_chains"] * S
+    cpc = CALLS_PER_CELL
+    if paper:
+        cpc = CALLS_PER_CELL_PAPER if args.workload == "grid" else CALLS_PER_CELL_PAPER_STREAM
+    calls = cpc * (w["L"] // 2) ** 2 * w["n_chains"] * S
     if args.workload == "grid":   # one launch per step: spins in and out once
         hbm_bytes = w["n_chains"] * w["L"] ** 2 / 8 * 2
     else:                         # per sweep: spins read + written, hidden written + read
         hbm_bytes = w["n_chains"] * w["L"] ** 2 * 7 / 8 * S
     achieved = MUL_OPS_PER_CALL * calls / (t_total / K) / 1e12
     peak = SM_COUNT * IMUL_LANES_PER_SM_CLK * SM_MAX_MHZ * 1e6 / 1e12
-    traffic = MEASURED_TRAFFIC["grid_paper" if paper else args.workload]
+    traffic = MEASURED_TRAFFIC[args.workload + ("_paper" if paper else "")]
     cfg = config_dict(w, args)
     if tuned_warps:
         cfg["warps_per_cta_autotuned"] = tuned_warps
@@ -555,7 +560,7 @@ def main():
                      "traffic_unit": "bytes " + traffic[1],
                      "note": "integer-multiply ceiling: 152 SM x 64 lanes/clk x 2070 MHz; 40 "
                              "multiply ops per Philox-4x32-10 call, "
-                             f"{CALLS_PER_CELL_PAPER if paper else CALLS_PER_CELL} calls per chain-cell-sweep",
+                             f"{cpc} calls per chain-cell-sweep",
                      "philox_calls_per_s": calls / (t_total / K)},
     }
     if rank == 0 and not args.no_cpu_baseline:

@@ -119,9 +119,10 @@ typedef struct {
      * uniform is a half of a Philox word (low half first): hidden filter
      * k < 8 half k&1 of word k>>1 of tag 0, filters 8 and 9 word 0 of tag 1,
      * the spin at window offset (r, c) half (2r+c)&1 of word 1 + ((2r+c)>>1)
-     * of tag 1 -- two Philox calls per cell instead of four.  Needs the ten
-     * SS filters, an even periodic lattice and the SMEM layout; not in
-     * batches or with block proposals.  crbm_get_tables returns the 16-bit
+     * of tag 1 -- two Philox calls per cell instead of four (three in the
+     * streamed layout, whose visible half-step draws the tag-1 call again).
+     * Needs the ten SS filters and an even periodic lattice; not in batches
+     * or with block proposals.  crbm_get_tables returns the 16-bit
      * thresholds in the upper halves of the 32-bit entries. */
     int32_t precision;
     /* Rectangular lattices and a boundary per axis (Sec. III: open boundaries
@@ -332,8 +333,10 @@ const char* crbm_proposal_last_error(void);
  * CRBM_LAYOUT_STREAM contexts, stateless and without a context.
  *
  * p: the model and chains (L even, periodic = 1, bonds = NULL, J, Jp, h,
- *    beta, n_params, chain_param, n_chains, seed, stream); measure_every,
- *    series_len, sq_every and layout are ignored: no observables are kept.
+ *    beta, n_params, chain_param, n_chains, seed, stream, precision);
+ *    L_cols 0 or L, periodic_cols CRBM_BC_AS_ROWS or CRBM_BC_PERIODIC,
+ *    h_odd NULL; measure_every, series_len, sq_every and layout are ignored:
+ *    no observables are kept.
  * v: device spins owned by the caller, in/out, the streamed layout:
  *    u32 v[ceil(n_chains/64)][L*L][2], bit l of v[g][s][k] = spin +1 of chain
  *    64 g + 32 k + l at site s (pad chains of the last group are sampled too).

@@ -74,12 +74,12 @@ __device__ __forceinline__ void sweep_canon_body(const SweepArgs& a, int word, u
                                                  int64_t meas0, int band = 0, int rank0 = 0) {
     extern __shared__ __align__(16) uint32_t smem[];
     const Geometry& g = a.g;
-    const int W = g.W;
+    const int W = g.W, Wc = g.Wc;  // rows and columns of cells
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nwarp = blockDim.x >> 5;
     const int nb = kCluster ? a.n_bands : 1;
     const bool active = band < nb;
     const int row0 = active ? band * W / nb : 0, row1 = active ? (band + 1) * W / nb : 0;
-    const int c_begin = row0 * W, c_end = row1 * W;
+    const int c_begin = kCluster ? row0 * Wc : 0, c_end = kCluster ? row1 * Wc : g.n_cells;
     int64_t* s_acc = reinterpret_cast<int64_t*>(smem);  // [kNSum][32] running sums
     uint32_t* s_th = smem + kAccWords;          // [2][4][32]
     uint32_t* s_tv = s_th + kCanonTh;           // [4][32][32]
@@ -147,7 +147,7 @@ __device__ __forceinline__ void sweep_canon_body(const SweepArgs& a, int word, u
     const uint32_t lane4 = 4u * static_cast<uint32_t>(lane);
     const uint4* rec0 = recs + static_cast<size_t>(c_begin + warp) * kCellRec;
     const int rstep = nwarp * kCellRec;
-    const int last_row = c_end - W, first_row_end = c_begin + W;
+    const int last_row = c_end - Wc, first_row_end = c_begin + Wc;
 
     for (int it = 0; it < n_sweeps; ++it) {
         const uint32_t t = t0 + static_cast<uint32_t>(it);
@@ -256,7 +256,7 @@ __device__ __forceinline__ void sweep_canon_body(const SweepArgs& a, int word, u
     if (kCluster) body_sync<true>();  // no rank reads another's shared memory after this
     if (!active) return;
     uint32_t* gv = a.v + static_cast<size_t>(word) * g.N;
-    const int s_begin = 2 * row0 * g.L, s_end = min(2 * row1, g.L) * g.L;  // own spin rows
+    const int s_begin = 2 * row0 * g.Lc, s_end = min(2 * row1, g.L) * g.Lc;  // own spin rows
     for (int x = s_begin + static_cast<int>(threadIdx.x); x < s_end; x += blockDim.x) gv[x] = s_v[x];
     if (band == 0 && warp == 0 && a.swap_every > 0) a.sob[word * 32 + lane] = s_sob[lane];
     if (band == 0 && warp == 0 && measuring) {

@@ -273,6 +273,56 @@ __device__ __forceinline__ uint32_t hidden_cell_rec_paper(char* sm, const uint4&
     return w;
 }
 
+// Paper-precision hidden half-step of one cell from its window rows (the
+// streamed layout), with q0, q1 as for hidden_cell (the tag-2 product is not
+// used); the visible half-step draws the tag-1 call again.
+__device__ __forceinline__ uint32_t hidden_cell_paper(const uint32_t* s_v, int vs, const uint32_t* s_th,
+                                                      const Round1Sweep& rs, uint32_t Y, const uint4& q0,
+                                                      const uint4& q1, const uint32_t (&rk)[20],
+                                                      const LaneConst& lc) {
+    uint2 vis;
+    return hidden_core_paper(s_v[0], s_v[1], s_v[2], s_v[vs], s_v[vs + 1], s_v[vs + 2], s_v[2 * vs],
+                             s_v[2 * vs + 1], s_th, rs, Y, q0.x, {q0.y, q0.z}, {q0.w, q1.x}, rk, lc, vis);
+}
+
+// (rc.lo, Q1.h, Q1.l, 0): the cell's round-0 word and the round-1 product of
+// its tag-1 call, whose words 1 and 2 carry the visible uniforms in paper
+// precision.
+__device__ __forceinline__ uint4 visible_call_words_paper(uint32_t cell, const uint32_t (&rk)[20]) {
+    const Round0Cell rc = round0_cell(cell, rk[1]);
+    const Round1Call c1 = round1_call(rc.a ^ 1u, rk);
+    return make_uint4(rc.b, c1.h, c1.l, 0u);
+}
+
+// The four paper-precision decisions of a cell with site-class fields c
+// (own, down and right bits merged) from its visible uniform words vis.
+__device__ __forceinline__ U4 visible_decide_paper(uint32_t c, uint2 vis, const uint32_t* s_tv,
+                                                   const LaneConst& lc) {
+    const uint32_t f = 31u << 7;
+    const uint32_t t00 = lds_at(s_tv, (c & f) | lc.lb);
+    const uint32_t t01 = lds_at(s_tv + 1024, ((c >> 5) & f) | lc.lb);
+    const uint32_t t10 = lds_at(s_tv + 2048, ((c >> 10) & f) | lc.lb);
+    const uint32_t t11 = lds_at(s_tv + 3072, ((c >> 15) & f) | lc.lb);
+    return {__ballot_sync(0xffffffffu, (vis.x << 16) < t00), __ballot_sync(0xffffffffu, vis.x < t01),
+            __ballot_sync(0xffffffffu, (vis.y << 16) < t10), __ballot_sync(0xffffffffu, vis.y < t11)};
+}
+
+// Paper-precision visible half-step of one cell in the streamed layout, with
+// qv = visible_call_words_paper(cell): the tag-1 call is drawn again for its
+// words 1 and 2.  Stores as visible_cell.
+__device__ __forceinline__ void visible_cell_paper(uint32_t* out, int row, uint32_t wo, uint32_t wu,
+                                                   uint32_t wl, const uint32_t* s_tv, const Round1Sweep& rs,
+                                                   uint32_t Y, const uint4& qv, const uint32_t (&rk)[20],
+                                                   const LaneConst& lc) {
+    const uint32_t c = (wo & kOwnBits) | (wu & kDownBits) | (wl & kRightBits);
+    const U4 q = philox_from_call(Y, rs, round2_cell(rs.hik ^ qv.x), {qv.y, qv.z}, rk);
+    const U4 o = visible_decide_paper(c, make_uint2(q.y, q.z), s_tv, lc);
+    out[0] = o.x;
+    out[1] = o.y;
+    out[row] = o.z;
+    out[row + 1] = o.w;
+}
+
 // Paper-precision visible half-step of one cell: the four uniforms are the
 // halves of the two words its hidden half-step left at byte offset v1.z.
 __device__ __forceinline__ U4 visible_cell_rec_paper(char* sm, const uint4& v0, const uint4& v1, uint32_t lane4,
@@ -280,13 +330,7 @@ __device__ __forceinline__ U4 visible_cell_rec_paper(char* sm, const uint4& v0, 
     const uint32_t c = (lds_off(sm, v0.z + lane4) & kOwnBits) | (lds_off(sm, v0.w + lane4) & kDownBits) |
                        (lds_off(sm, v1.x + lane4) & kRightBits);
     const uint2 vis = *reinterpret_cast<const uint2*>(sm + v1.z + 2u * lane4);
-    const uint32_t f = 31u << 7;
-    const uint32_t t00 = lds_at(s_tv, (c & f) | lc.lb);
-    const uint32_t t01 = lds_at(s_tv + 1024, ((c >> 5) & f) | lc.lb);
-    const uint32_t t10 = lds_at(s_tv + 2048, ((c >> 10) & f) | lc.lb);
-    const uint32_t t11 = lds_at(s_tv + 3072, ((c >> 15) & f) | lc.lb);
-    const U4 o = {__ballot_sync(0xffffffffu, (vis.x << 16) < t00), __ballot_sync(0xffffffffu, vis.x < t01),
-                  __ballot_sync(0xffffffffu, (vis.y << 16) < t10), __ballot_sync(0xffffffffu, vis.y < t11)};
+    const U4 o = visible_decide_paper(c, vis, s_tv, lc);
     sts_off(sm, v0.x, o.x);
     sts_off(sm, v0.x + 4u, o.y);
     sts_off(sm, v0.y, o.z);

@@ -140,7 +140,7 @@ int build_geometry(crbm_ctx* ctx, const crbm_params* p, std::vector<uint32_t>& e
     bool same = (nb == 10);
     for (int k = 0; same && k < 10; ++k)
         same = std::memcmp(&bonds[k], &kSSFilters[k], sizeof(crbm_bond)) == 0;
-    g.canonical = (same && g.periodic && g.pc && g.Lc == g.L && (g.L % 2 == 0) && g.n_vis_tab == 1) ? 1 : 0;
+    g.canonical = (same && g.periodic && g.pc && g.L % 2 == 0 && g.Lc % 2 == 0 && g.n_vis_tab == 1) ? 1 : 0;
 
     std::vector<int> deg(2 * static_cast<size_t>(g.N), 0);  // filters per (class, site)
     g.n_real_bonds[0] = g.n_real_bonds[1] = 0;
@@ -339,15 +339,18 @@ int crbm_create(crbm_ctx** out, const crbm_params* p) {
         delete ctx;
         return fail(nullptr, CRBM_EINVAL, "SMEM layout needs L, L_cols <= CRBM_SMEM_MAX_L");
     }
-    if (g.paper && (!g.canonical || ctx->layout != CRBM_LAYOUT_SMEM)) {
+    if (g.paper && !g.canonical) {
         delete ctx;
-        return fail(nullptr, CRBM_EUNSUPPORTED,
-                    "paper precision serves the ten SS filters on an even periodic lattice in the SMEM layout");
+        return fail(nullptr, CRBM_EUNSUPPORTED, "paper precision serves the ten SS filters on an even periodic lattice");
     }
     if (ctx->layout == CRBM_LAYOUT_STREAM && !g.canonical) {
         delete ctx;
         return fail(nullptr, CRBM_EUNSUPPORTED,
                     "the streamed layout serves the ten SS filters on an even, periodic lattice");
+    }
+    if (ctx->layout == CRBM_LAYOUT_STREAM && g.Lc != g.L) {
+        delete ctx;
+        return fail(nullptr, CRBM_EUNSUPPORTED, "the streamed layout serves square lattices");
     }
     if (ctx->layout == CRBM_LAYOUT_STREAM && p->sq_every > 0) {
         delete ctx;
@@ -545,17 +548,17 @@ int crbm_create(crbm_ctx** out, const crbm_params* p) {
     // Per-cell records of the canonical SMEM sweep (layout in crbm_internal.h).
     std::vector<uint32_t> crec;
     if (g.canonical && ctx->layout == CRBM_LAYOUT_SMEM) {
-        const int L = g.L, W = g.W;
+        const int L = g.L, W = g.W, Lc = g.Lc, Wc = g.Wc;
         const uint32_t key0 = static_cast<uint32_t>(ctx->seed), key1 = static_cast<uint32_t>(ctx->seed >> 32);
         const uint32_t rk2 = key0 + 0x9E3779B9u, rk4 = key0 + 2u * 0x9E3779B9u;  // round keys 1, 2 (word 0)
         const uint32_t vb = 4u * kCanonSmemV, wb = 4u * static_cast<uint32_t>(kCanonSmemV + g.N);
-        auto site = [&](int R, int C) { return vb + 4u * static_cast<uint32_t>((R % L) * L + C % L); };
-        auto hrow = [&](int i, int j) { return wb + 128u * static_cast<uint32_t>(i * W + j); };
+        auto site = [&](int R, int C) { return vb + 4u * static_cast<uint32_t>((R % L) * Lc + C % Lc); };
+        auto hrow = [&](int i, int j) { return wb + 128u * static_cast<uint32_t>(i * Wc + j); };
         crec.assign(static_cast<size_t>(g.n_cells) * kCellRec * 4, 0u);
         for (int i = 0; i < W; ++i)
-            for (int j = 0; j < W; ++j) {
-                uint32_t* o = &crec[static_cast<size_t>(i * W + j) * kCellRec * 4];
-                const uint64_t m = 0xD2511F53ull * static_cast<uint32_t>(i * W + j);
+            for (int j = 0; j < Wc; ++j) {
+                uint32_t* o = &crec[static_cast<size_t>(i * Wc + j) * kCellRec * 4];
+                const uint64_t m = 0xD2511F53ull * static_cast<uint32_t>(i * Wc + j);
                 const uint32_t lo = static_cast<uint32_t>(m), hi = static_cast<uint32_t>(m >> 32) ^ key1;
                 uint32_t qh[4], ql[4];  // round-1 products of the calls with tags 0, 1, 2, visible
                 const uint32_t tags[4] = {0u, 1u, 2u, kTagVis};
@@ -570,12 +573,12 @@ int crbm_create(crbm_ctx** out, const crbm_params* p) {
                     site(R + 1, C + 2), hrow(i, j), lo,                    qh[2],
                     qh[0],          ql[0],          qh[1],                 ql[1],
                     site(R, C),     site(R + 1, C), hrow(i, j),            hrow((i + W - 1) % W, j),
-                    hrow(i, (j + W - 1) % W), lo,   qh[3],                 ql[3],
+                    hrow(i, (j + Wc - 1) % Wc), lo, qh[3],                 ql[3],
                     ql[2],          0u,             0u,                    0u};
                 std::copy(rec, rec + kCellRec * 4, o);
                 if (g.paper) {  // the cell's row of visible draws replaces Q2.hi and Qv.hi
                     const uint32_t pw = 4u * static_cast<uint32_t>(canon_smem_pw_offset(g)) +
-                                        256u * static_cast<uint32_t>(i * W + j);
+                                        256u * static_cast<uint32_t>(i * Wc + j);
                     o[7] = pw;
                     o[18] = pw;
                 }

@@ -15,7 +15,9 @@
 // The MH pass runs the three convolutions as implicit GEMMs on the tensor
 // cores (mma.sync m16n8k16, bf16 operands, fp32 accumulation): rows are
 // (chain, output position) of the 32 chains of a packed word, columns the 16
-// output channels, K = (tap, input channel).  Training runs one example per
+// output channels, K = (tap, input channel).  Layer 1's five constant planes
+// are folded into per-position and per-chain constants, so its convolution
+// runs on the spin plane alone (one k-tile).  Training runs one example per
 // thread in fp32 (bf16-rounded weights and activations), back-propagates the
 // binary cross-entropy and updates with Adam.
 #include <cstring>
@@ -44,9 +46,25 @@ constexpr int kPassThreads = 256;  // 8 warps
 constexpr int oW1 = 0, oB1 = 864, oW2 = 880, oB2 = 3184, oW3 = 3200, oB3 = 3344;
 
 // B-operand fragments of the three layers for mma m16n8k16 (per lane 2 x u32):
-// layer 1: 5 k-tiles x 2 n-tiles, layer 2: 9 x 2, layer 3: 9 x 1.
-constexpr int kFrag1 = 5 * 2, kFrag2 = 9 * 2, kFrag3 = 9;
+// layer 1: 1 k-tile (the nine taps of the spin plane) x 2 n-tiles, layer 2:
+// 9 x 2, layer 3: 9 x 1.
+constexpr int kFrag1 = 2, kFrag2 = 9 * 2, kFrag3 = 9;
 constexpr int kFrags = kFrag1 + kFrag2 + kFrag3;
+
+// Layer 1 on the five constant planes (block mask, row and column parity,
+// beta, h) is linear in them and the same for every chain of a pass, so it is
+// folded out of the convolution: per output position and channel a constant
+// for each parity of the patch's first row and column ([4][64][16]), and the
+// tap sums of the beta and h kernels ([2][16]).  Only the spin plane remains
+// a convolution (K = 9 taps).
+constexpr int kC1Pos = 4 * kS1 * kS1 * 16, kC1 = kC1Pos + 2 * 16;
+
+// Shared memory of the pass, 32-bit words.  A1 and A2 hold bf16 activations,
+// one 32-byte row per (chain, position) of 16 channels; the two 16-byte halves
+// of row R are swapped when bit 2 of R is set, so the eight rows an ldmatrix
+// phase reads (mostly consecutive) fall in distinct banks.
+constexpr int kSmA1 = 0, kSmA2 = 32 * kS1 * kS1 * 8, kSmFr = kSmA2 + 32 * kS2 * kS2 * 8;
+constexpr int kSmPw = kSmFr + kFrags * 32 * 2, kSmWords = kSmPw + kP * kP;
 
 // Per (word, block, lane) record of a pass run in inspection mode: the
 // logits, the proposed and current block bits, the exact dE and log alpha.
@@ -64,6 +82,7 @@ struct PassArgs {
     uint32_t* v;
     const uint2* frag;        // [kFrags][32] B fragments (bf16 pairs)
     const float* bias;        // b1[16], b2[16], b3
+    const float* c1;          // folded layer-1 constants [kC1]
     const float* chain_bh;    // [chains][2] beta, h (bf16-rounded)
     const int32_t* chain_q;   // [chains][3] Q.4 J, J', h
     unsigned long long* stats;  // {proposed, accepted}
@@ -80,33 +99,46 @@ __device__ __forceinline__ void mma_bf16(float (&d)[4], const uint32_t (&a)[4], 
         : "r"(a[0]), "r"(a[1]), "r"(a[2]), "r"(a[3]), "r"(b.x), "r"(b.y));
 }
 
+// The A fragment of one m16k16 tile from four 8x8 bf16 matrices in shared
+// memory; each lane passes the address of one 16-byte matrix row.
+__device__ __forceinline__ void ldmatrix_x4(uint32_t (&r)[4], uint32_t addr) {
+    asm volatile("ldmatrix.sync.aligned.m8n8.x4.shared.b16 {%0,%1,%2,%3}, [%4];\n"
+                 : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3])
+                 : "r"(addr));
+}
+
 __device__ __forceinline__ uint32_t pack_bf16(float lo, float hi) {
     const __nv_bfloat162 p = __floats2bfloat162_rn(lo, hi);
     return *reinterpret_cast<const uint32_t*>(&p);
 }
 
+// Word offset of 16-byte half h of activation row R (see the layout above).
+__device__ __forceinline__ int act_half(int R, int h) { return R * 8 + ((h ^ (R >> 2)) & 1) * 4; }
+
 // One pass of MH block moves: CTA = (block of the pass, packed word).
-__global__ void __launch_bounds__(kPassThreads, 1) k_prop_pass(const __grid_constant__ PassArgs a) {
+__global__ void __launch_bounds__(kPassThreads, 2) k_prop_pass(const __grid_constant__ PassArgs a) {
     extern __shared__ __align__(16) uint32_t sm[];
     const int L = a.g.L, N = a.g.N;
     const int word = blockIdx.y, b = blockIdx.x;
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     const int gq = lane >> 2, tq = lane & 3;
-    // shared memory: X (input, later A2) | A1 | logits | patch words | frags
-    uint32_t* X = sm;                          // [32][100][8] bf16 = 12800 words
-    uint32_t* A2 = sm;                         // [32][36][16] bf16 = 9216 words (after layer 1)
-    uint32_t* A1 = sm + 12800;                 // [32][64][16] bf16 = 16384 words
-    float* logit = reinterpret_cast<float*>(sm + 12800 + 16384);   // [32][16]
-    uint32_t* pw = sm + 12800 + 16384 + 512;   // [100] patch words
-    uint2* fr = reinterpret_cast<uint2*>(pw + 100 + 4);           // [kFrags][32]
-    uint32_t* s_par = reinterpret_cast<uint32_t*>(fr + kFrags * 32);  // [100] row/column parity planes (bf16 pair)
-    uint32_t* s_in = s_par + 100;                                  // [100] 1 inside the block
-    uint32_t* s_bh = s_in + 100;                                   // [32] beta, h of each lane (bf16 pair)
-    // Metropolis-Hastings per (chain, site), over A1 once layer 2 has read it
-    float* lqc = reinterpret_cast<float*>(A1);  // [32][16] log q of the current spin
-    float* lqn = lqc + 512;                     // [32][16] log q of the proposed spin
-    int* s_xx = reinterpret_cast<int*>(lqn + 512);  // [32][16] bit 0: current +1, bit 1: proposed +1
-    long long* s_de = reinterpret_cast<long long*>(s_xx + 512);  // [32][16] energy-change terms
+    uint32_t* A1 = sm + kSmA1;                 // [32][64] rows, layer-1 output
+    uint32_t* A2 = sm + kSmA2;                 // [32][36] rows, layer-2 output
+    // layer-1 inputs, in A2's space until layer 2 writes it
+    uint16_t* sp = reinterpret_cast<uint16_t*>(A2);        // [32][100] spin plane, bf16
+    float* c1s = reinterpret_cast<float*>(A2 + 1600);       // [64][16] position constants
+    float* cbs = c1s + kS1 * kS1 * 16;                      // [32][16] b1 + beta w_beta + h w_h
+    uint2* fr = reinterpret_cast<uint2*>(sm + kSmFr);       // [kFrags][32]
+    uint32_t* pw = sm + kSmPw;                              // [100] patch words
+    // after layer 2 (A1 is free): logits and the Metropolis-Hastings terms
+    // ([site][lane], so a warp's 32 chains fall in distinct banks)
+    float* logit = reinterpret_cast<float*>(A1);   // [16][32]
+    float* lqc = logit + 512;                      // [16][32] log q of the current spin
+    float* lqn = lqc + 512;                        // [16][32] log q of the proposed spin
+    int* s_xx = reinterpret_cast<int*>(lqn + 512);  // [16][32] bit 0: current +1, bit 1: proposed +1
+    long long* s_de = reinterpret_cast<long long*>(s_xx + 512);  // [16][32] energy-change terms
+    const uint32_t a1_base = static_cast<uint32_t>(__cvta_generic_to_shared(A1));
+    const uint32_t a2_base = static_cast<uint32_t>(__cvta_generic_to_shared(A2));
 
     // block origin of this pass
     const U4 off = philox(a.pass, 0u, 0u, kTagOffset, a.key0, a.key1);
@@ -115,101 +147,100 @@ __global__ void __launch_bounds__(kPassThreads, 1) k_prop_pass(const __grid_cons
     for (int x = threadIdx.x; x < kP * kP; x += blockDim.x) {  // per patch position
         const int R = (bR - 3 + x / kP + 2 * L) % L, C = (bC - 3 + x % kP + 2 * L) % L;
         pw[x] = a.v[static_cast<size_t>(word) * N + R * L + C];
-        s_in[x] = ((R - bR + L) % L) < kK && ((C - bC + L) % L) < kK;
-        s_par[x] = pack_bf16(static_cast<float>(R & 1), static_cast<float>(C & 1));
     }
-    if (threadIdx.x < 32) {
-        const int chain = word * 32 + threadIdx.x;
-        s_bh[threadIdx.x] = pack_bf16(a.chain_bh[2 * chain], a.chain_bh[2 * chain + 1]);
+    {
+        const int var = ((bR + 1) & 1) * 2 + ((bC + 1) & 1);  // parity of the patch's first row, column
+        const float* c1v = a.c1 + var * (kS1 * kS1 * 16);
+        for (int i = threadIdx.x; i < kS1 * kS1 * 16; i += blockDim.x) c1s[i] = c1v[i];
+        for (int i = threadIdx.x; i < 32 * 16; i += blockDim.x) {
+            const int c = i >> 4, n = i & 15, chain = word * 32 + c;
+            cbs[i] = a.bias[n] + a.chain_bh[2 * chain] * a.c1[kC1Pos + n] +
+                     a.chain_bh[2 * chain + 1] * a.c1[kC1Pos + 16 + n];
+        }
     }
     for (int x = threadIdx.x; x < kFrags * 32; x += blockDim.x) fr[x] = a.frag[x];
     __syncthreads();
-    // input planes, 8 channels per (chain, position): spin | mask | R&1 | C&1 | beta | h | 0 | 0
-    {
-        const uint32_t in_word = pack_bf16(0.f, 1.f), up = pack_bf16(1.f, 0.f), down = pack_bf16(-1.f, 0.f);
-        for (int x = threadIdx.x; x < 32 * kP * kP; x += blockDim.x) {
-            const int c = x / (kP * kP), pos = x - c * (kP * kP);
-            uint32_t* dst = X + (c * kP * kP + pos) * 4;
-            dst[0] = s_in[pos] ? in_word : (((pw[pos] >> c) & 1u) ? up : down);
-            dst[1] = s_par[pos];
-            dst[2] = s_bh[c];
-            dst[3] = 0u;
-        }
+    // spin plane: +-1 outside the block, 0 inside
+    for (int x = threadIdx.x; x < 32 * kP * kP; x += blockDim.x) {
+        const int c = x / (kP * kP), pos = x - c * (kP * kP);
+        const int y = pos / kP, xx = pos - y * kP;
+        const bool in = y >= 3 && y < 3 + kK && xx >= 3 && xx < 3 + kK;
+        sp[x] = in ? 0 : (((pw[pos] >> c) & 1u) ? 0x3F80 : 0xBF80);
     }
     __syncthreads();
-    // ---- layer 1: rows (chain, y*8+x) = 2048 (128 m-tiles), K = 10 taps x 8 ch
+    // ---- layer 1: rows (chain, y*8+x) = 2048 (128 m-tiles), K = 9 taps
     for (int mt = warp; mt < 128; mt += kPassThreads / 32) {
         const int chain = mt >> 2, p0 = (mt & 3) * 16;
-        float d[2][4] = {};
         const int pA = p0 + gq, pB = p0 + gq + 8;  // the two rows of this lane
-        const int yA = pA >> 3, xA = pA & 7, yB = pB >> 3, xB = pB & 7;
-#pragma unroll
-        for (int kt = 0; kt < 5; ++kt) {
-            uint32_t af[4];
-#pragma unroll
-            for (int half = 0; half < 2; ++half) {
-                const int tap = 2 * kt + half;
-                uint32_t lo = 0u, hi = 0u;
-                if (tap < 9) {
-                    const int ky = tap / 3, kx = tap % 3;
-                    lo = X[(chain * kP * kP + (yA + ky) * kP + xA + kx) * 4 + tq];
-                    hi = X[(chain * kP * kP + (yB + ky) * kP + xB + kx) * 4 + tq];
-                }
-                af[2 * half] = lo;
-                af[2 * half + 1] = hi;
-            }
-            mma_bf16(d[0], af, fr[(kt * 2 + 0) * 32 + lane]);
-            mma_bf16(d[1], af, fr[(kt * 2 + 1) * 32 + lane]);
-        }
+        const uint16_t* sc = sp + chain * kP * kP;
+        const int oA = (pA >> 3) * kP + (pA & 7), oB = (pB >> 3) * kP + (pB & 7);
+        const int t0 = 2 * tq, t1 = 2 * tq + 1;
+        const int d0 = (t0 / 3) * kP + t0 % 3, d1 = (t1 / 3) * kP + t1 % 3;
+        uint32_t af[4];
+        af[0] = sc[oA + d0] | (static_cast<uint32_t>(sc[oA + d1]) << 16);
+        af[1] = sc[oB + d0] | (static_cast<uint32_t>(sc[oB + d1]) << 16);
+        af[2] = tq == 0 ? sc[oA + 2 * kP + 2] : 0u;  // tap 8; taps 9-15 are padding
+        af[3] = tq == 0 ? sc[oB + 2 * kP + 2] : 0u;
+        float d[2][4] = {};
+        mma_bf16(d[0], af, fr[0 * 32 + lane]);
+        mma_bf16(d[1], af, fr[1 * 32 + lane]);
 #pragma unroll
         for (int nt = 0; nt < 2; ++nt) {
             const int n = 8 * nt + 2 * tq;
-            const float b0 = a.bias[n], b1 = a.bias[n + 1];
-            A1[(chain * 64 + pA) * 8 + (n >> 1)] = pack_bf16(fmaxf(d[nt][0] + b0, 0.f), fmaxf(d[nt][1] + b1, 0.f));
-            A1[(chain * 64 + pB) * 8 + (n >> 1)] = pack_bf16(fmaxf(d[nt][2] + b0, 0.f), fmaxf(d[nt][3] + b1, 0.f));
+            const float2 cb = *reinterpret_cast<const float2*>(cbs + chain * 16 + n);
+            const float2 cA = *reinterpret_cast<const float2*>(c1s + pA * 16 + n);
+            const float2 cB = *reinterpret_cast<const float2*>(c1s + pB * 16 + n);
+            const int RA = chain * 64 + pA, RB = chain * 64 + pB;
+            A1[act_half(RA, nt) + tq] = pack_bf16(fmaxf(d[nt][0] + (cA.x + cb.x), 0.f), fmaxf(d[nt][1] + (cA.y + cb.y), 0.f));
+            A1[act_half(RB, nt) + tq] = pack_bf16(fmaxf(d[nt][2] + (cB.x + cb.x), 0.f), fmaxf(d[nt][3] + (cB.y + cb.y), 0.f));
         }
     }
     __syncthreads();
-    // ---- layer 2: rows (chain, y*6+x) = 1152 (72 m-tiles), K = 9 taps x 16 ch
+    // ---- layer 2: rows (chain, y*6+x) = 1152 (72 m-tiles), K = 9 taps x 16 ch.
+    // ldmatrix: lane l gives the row (l & 7) + 8 ((l >> 3) & 1), half l >> 4.
+    const int lrow = (lane & 7) + 8 * ((lane >> 3) & 1), lhalf = lane >> 4;
+    uint2 b2[kFrag2];  // this lane's B fragments of layer 2, kept for all its m-tiles
+#pragma unroll
+    for (int f = 0; f < kFrag2; ++f) b2[f] = fr[(kFrag1 + f) * 32 + lane];
     for (int mt = warp; mt < 72; mt += kPassThreads / 32) {
-        const int rA = mt * 16 + gq, rB = rA + 8;
-        const int cA = rA / 36, qA = rA - cA * 36, cB = rB / 36, qB = rB - cB * 36;
-        const int yA = qA / 6, xA = qA - yA * 6, yB = qB / 6, xB = qB - yB * 6;
+        const int r = mt * 16 + lrow;
+        const int c = r / 36, q = r - c * 36;
+        const int R0 = c * 64 + (q / 6) * 8 + q % 6;
         float d[2][4] = {};
 #pragma unroll
         for (int tap = 0; tap < 9; ++tap) {
-            const int ky = tap / 3, kx = tap % 3;
-            const uint32_t* rowA = A1 + (cA * 64 + (yA + ky) * 8 + xA + kx) * 8;
-            const uint32_t* rowB = A1 + (cB * 64 + (yB + ky) * 8 + xB + kx) * 8;
-            const uint32_t af[4] = {rowA[tq], rowB[tq], rowA[tq + 4], rowB[tq + 4]};
-            mma_bf16(d[0], af, fr[(kFrag1 + tap * 2 + 0) * 32 + lane]);
-            mma_bf16(d[1], af, fr[(kFrag1 + tap * 2 + 1) * 32 + lane]);
+            const int R = R0 + (tap / 3) * 8 + tap % 3;
+            uint32_t af[4];
+            ldmatrix_x4(af, a1_base + 4u * static_cast<uint32_t>(act_half(R, lhalf)));
+            mma_bf16(d[0], af, b2[tap * 2 + 0]);
+            mma_bf16(d[1], af, b2[tap * 2 + 1]);
         }
+        const int rA = mt * 16 + gq, rB = rA + 8;
+        const int cA = rA / 36, qA = rA - cA * 36, cB = rB / 36, qB = rB - cB * 36;
 #pragma unroll
         for (int nt = 0; nt < 2; ++nt) {
             const int n = 8 * nt + 2 * tq;
             const float b0 = a.bias[16 + n], b1 = a.bias[16 + n + 1];
-            A2[(cA * 36 + qA) * 8 + (n >> 1)] = pack_bf16(fmaxf(d[nt][0] + b0, 0.f), fmaxf(d[nt][1] + b1, 0.f));
-            A2[(cB * 36 + qB) * 8 + (n >> 1)] = pack_bf16(fmaxf(d[nt][2] + b0, 0.f), fmaxf(d[nt][3] + b1, 0.f));
+            A2[act_half(cA * 36 + qA, nt) + tq] = pack_bf16(fmaxf(d[nt][0] + b0, 0.f), fmaxf(d[nt][1] + b1, 0.f));
+            A2[act_half(cB * 36 + qB, nt) + tq] = pack_bf16(fmaxf(d[nt][2] + b0, 0.f), fmaxf(d[nt][3] + b1, 0.f));
         }
     }
     __syncthreads();
     // ---- layer 3: rows (chain, y*4+x) = 512 (32 m-tiles), one output channel
     for (int mt = warp; mt < 32; mt += kPassThreads / 32) {
         const int ch = mt;  // one m-tile = the 16 block sites of chain mt
-        const int yA = gq >> 2, xA = gq & 3, yB = (gq + 8) >> 2, xB = (gq + 8) & 3;
+        const int R0 = ch * 36 + (lrow >> 2) * 6 + (lrow & 3);
         float d[4] = {};
 #pragma unroll
         for (int tap = 0; tap < 9; ++tap) {
-            const int ky = tap / 3, kx = tap % 3;
-            const uint32_t* rowA = A2 + (ch * 36 + (yA + ky) * 6 + xA + kx) * 8;
-            const uint32_t* rowB = A2 + (ch * 36 + (yB + ky) * 6 + xB + kx) * 8;
-            const uint32_t af[4] = {rowA[tq], rowB[tq], rowA[tq + 4], rowB[tq + 4]};
+            const int R = R0 + (tap / 3) * 6 + tap % 3;
+            uint32_t af[4];
+            ldmatrix_x4(af, a2_base + 4u * static_cast<uint32_t>(act_half(R, lhalf)));
             mma_bf16(d, af, fr[(kFrag1 + kFrag2 + tap) * 32 + lane]);
         }
         if (tq == 0) {
-            logit[ch * 16 + gq] = d[0] + a.bias[32];
-            logit[ch * 16 + gq + 8] = d[2] + a.bias[32];
+            logit[gq * 32 + ch] = d[0] + a.bias[32];
+            logit[(gq + 8) * 32 + ch] = d[2] + a.bias[32];
         }
     }
     __syncthreads();
@@ -228,16 +259,16 @@ __global__ void __launch_bounds__(kPassThreads, 1) k_prop_pass(const __grid_cons
             const int s = 4 * call + 2 * (warp & 1) + j;
             const int pos = (3 + s / kK) * kP + 3 + s % kK;
             const int xc = ((pw[pos] >> lane) & 1u) ? 1 : -1;
-            const float q = 1.f / (1.f + __expf(-logit[lane * 16 + s]));
+            const float q = 1.f / (1.f + __expf(-logit[s * 32 + lane]));
             float tf = q * 4294967296.f;
             tf = fminf(fmaxf(tf, 1.f), 4294967040.f);
             const uint32_t thr = static_cast<uint32_t>(tf);
             const float p1 = static_cast<float>(thr) * 2.3283064365386963e-10f;
             const float lp = __logf(p1), lm = log1pf(-p1);
             const int xp = pick(u, s & 3) < thr ? 1 : -1;
-            lqc[lane * 16 + s] = xc > 0 ? lp : lm;
-            lqn[lane * 16 + s] = xp > 0 ? lp : lm;
-            s_xx[lane * 16 + s] = (xc > 0 ? 1 : 0) | (xp > 0 ? 2 : 0);
+            lqc[s * 32 + lane] = xc > 0 ? lp : lm;
+            lqn[s * 32 + lane] = xp > 0 ? lp : lm;
+            s_xx[s * 32 + lane] = (xc > 0 ? 1 : 0) | (xp > 0 ? 2 : 0);
         }
     }
     __syncthreads();
@@ -247,8 +278,8 @@ __global__ void __launch_bounds__(kPassThreads, 1) k_prop_pass(const __grid_cons
     // of higher index)
     {
         auto spin_at = [&](int pr, int pc) -> int { return ((pw[pr * kP + pc] >> lane) & 1u) ? 1 : -1; };
-        auto xs = [&](int t) { return (s_xx[lane * 16 + t] & 1) ? 1 : -1; };
-        auto ns = [&](int t) { return (s_xx[lane * 16 + t] & 2) ? 1 : -1; };
+        auto xs = [&](int t) { return (s_xx[t * 32 + lane] & 1) ? 1 : -1; };
+        auto ns = [&](int t) { return (s_xx[t * 32 + lane] & 2) ? 1 : -1; };
 #pragma unroll
         for (int j = 0; j < 2; ++j) {
             const int s = 4 * (warp >> 1) + 2 * (warp & 1) + j;
@@ -272,7 +303,7 @@ __global__ void __launch_bounds__(kPassThreads, 1) k_prop_pass(const __grid_cons
             } else {
                 dE += static_cast<long long>(qJp) * d * spin_at(3 + pr, 3 + pc);
             }
-            s_de[lane * 16 + s] = dE;
+            s_de[s * 32 + lane] = dE;
         }
     }
     __syncthreads();
@@ -284,10 +315,10 @@ __global__ void __launch_bounds__(kPassThreads, 1) k_prop_pass(const __grid_cons
     uint32_t cb = 0, nb = 0;
 #pragma unroll
     for (int s = 0; s < kK * kK; ++s) {
-        logq_cur += lqc[lane * 16 + s];
-        logq_new += lqn[lane * 16 + s];
-        dE += s_de[lane * 16 + s];
-        const int xx = s_xx[lane * 16 + s];
+        logq_cur += lqc[s * 32 + lane];
+        logq_new += lqn[s * 32 + lane];
+        dE += s_de[s * 32 + lane];
+        const int xx = s_xx[s * 32 + lane];
         cb |= static_cast<uint32_t>(xx & 1) << s;
         nb |= static_cast<uint32_t>((xx >> 1) & 1) << s;
     }
@@ -299,7 +330,7 @@ __global__ void __launch_bounds__(kPassThreads, 1) k_prop_pass(const __grid_cons
     if (a.rec) {  // inspection: record, do not move
         PassRecord* r = a.rec + (static_cast<size_t>(word) * gridDim.x + b) * 32 + lane;
 #pragma unroll
-        for (int s = 0; s < kK * kK; ++s) r->logit[s] = logit[lane * 16 + s];
+        for (int s = 0; s < kK * kK; ++s) r->logit[s] = logit[s * 32 + lane];
         r->dE = static_cast<int32_t>(dE);
         r->cur_bits = cb;
         r->new_bits = nb;
@@ -494,10 +525,7 @@ __global__ void k_prop_fragments(const float* wb, uint2* frag, float* bias) {
     if (i >= kFrags * 32) return;
     const int f = i / 32, lane = i % 32, gq = lane >> 2, tq = lane & 3;
     auto Bv = [&](int k, int n) -> float {
-        if (f < kFrag1) {  // layer 1: k = tap * 8 + channel
-            const int tap = k >> 3, ch = k & 7;
-            return (tap < 9 && ch < 6) ? wb[oW1 + (n * 6 + ch) * 9 + tap] : 0.f;
-        }
+        if (f < kFrag1) return k < 9 ? wb[oW1 + n * 6 * 9 + k] : 0.f;  // layer 1: k = tap of the spin plane
         if (f < kFrag1 + kFrag2) {  // layer 2: k = tap * 16 + channel
             return wb[oW2 + (n * 16 + (k & 15)) * 9 + (k >> 4)];
         }
@@ -518,6 +546,34 @@ __global__ void k_prop_fragments(const float* wb, uint2* frag, float* bias) {
     frag[i] = make_uint2(pack_bf16(Bv(k0, n), Bv(k0 + 1, n)), pack_bf16(Bv(k0 + 8, n), Bv(k0 + 9, n)));
 }
 
+// The folded layer-1 constants (see kC1Pos) from the bf16-rounded weights:
+// per parity variant (row parity pr, column parity pc of the patch's first
+// site), output position and channel, the sum over the nine taps of the mask
+// and parity kernels times their planes; then the tap sums of the beta and h
+// kernels.
+__global__ void k_prop_layer1_consts(const float* wb, float* c1) {
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= kC1) return;
+    if (i >= kC1Pos) {
+        const int ch = 4 + (i - kC1Pos) / 16, n = (i - kC1Pos) % 16;
+        float s = 0.f;
+        for (int tap = 0; tap < 9; ++tap) s += wb[oW1 + (n * 6 + ch) * 9 + tap];
+        c1[i] = s;
+        return;
+    }
+    const int var = i / (kS1 * kS1 * 16), p = (i / 16) % (kS1 * kS1), n = i % 16;
+    const int pr = var >> 1, pc = var & 1, y = p / kS1, x = p % kS1;
+    float s = 0.f;
+    for (int tap = 0; tap < 9; ++tap) {
+        const int Y = y + tap / 3, X = x + tap % 3;
+        const bool in = Y >= 3 && Y < 3 + kK && X >= 3 && X < 3 + kK;
+        if (in) s += wb[oW1 + (n * 6 + 1) * 9 + tap];
+        if ((pr + Y) & 1) s += wb[oW1 + (n * 6 + 2) * 9 + tap];
+        if ((pc + X) & 1) s += wb[oW1 + (n * 6 + 3) * 9 + tap];
+    }
+    c1[i] = s;
+}
+
 }  // namespace
 }  // namespace crbm
 
@@ -532,6 +588,7 @@ struct crbm_proposal {
     float* loss = nullptr;
     uint2* frag = nullptr;   // mma B fragments
     float* bias = nullptr;
+    float* c1 = nullptr;     // folded layer-1 constants
     unsigned long long* stats = nullptr;
     crbm::Example* ex = nullptr;
     int ex_cap = 0;
@@ -567,6 +624,7 @@ double unit_normal(uint64_t& s) {  // Box-Muller
 
 cudaError_t refresh_fragments(crbm_proposal* p, cudaStream_t st) {
     crbm::k_prop_fragments<<<(crbm::kFrags * 32 + 127) / 128, 128, 0, st>>>(p->wb, p->frag, p->bias);
+    crbm::k_prop_layer1_consts<<<(crbm::kC1 + 127) / 128, 128, 0, st>>>(p->wb, p->c1);
     return cudaGetLastError();
 }
 
@@ -602,10 +660,11 @@ int ensure_chain_params(crbm_ctx* ctx) {
 
 int check_ctx(const crbm_ctx* ctx) {
     if (!ctx) return prop_fail(CRBM_EINVAL, "null context");
-    if (!ctx->g.canonical || ctx->layout != CRBM_LAYOUT_SMEM || ctx->swap_every > 0 || ctx->g.paper)
+    if (!ctx->g.canonical || ctx->g.Lc != ctx->g.L || ctx->layout != CRBM_LAYOUT_SMEM || ctx->swap_every > 0 ||
+        ctx->g.paper)
         return prop_fail(CRBM_EUNSUPPORTED,
-                         "block proposals need the ten SS filters on an even periodic lattice, the SMEM "
-                         "layout, exact precision and no replica exchange");
+                         "block proposals need the ten SS filters on an even periodic square lattice, the "
+                         "SMEM layout, exact precision and no replica exchange");
     return CRBM_OK;
 }
 
@@ -629,6 +688,7 @@ cudaError_t launch_pass(crbm_ctx* ctx, crbm_proposal* p, crbm::PassRecord* rec) 
     a.v = ctx->d.v;
     a.frag = p->frag;
     a.bias = p->bias;
+    a.c1 = p->c1;
     a.chain_bh = ctx->d.chain_bh;
     a.chain_q = ctx->d.chain_q;
     a.stats = p->stats;
@@ -637,7 +697,7 @@ cudaError_t launch_pass(crbm_ctx* ctx, crbm_proposal* p, crbm::PassRecord* rec) 
     a.pass = static_cast<uint32_t>(ctx->passes);
     a.nb1 = nb1;
     a.spacing = L / nb1;
-    const size_t smem = (12800 + 16384 + 512 + 104) * 4 + crbm::kFrags * 32 * 8 + 232 * 4;
+    const size_t smem = crbm::kSmWords * 4;
     cudaError_t e = cudaFuncSetAttribute(crbm::k_prop_pass, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                          static_cast<int>(smem));
     if (e != cudaSuccess) return e;
@@ -664,6 +724,7 @@ int crbm_proposal_create(crbm_proposal** out, int32_t block, uint64_t seed) {
     if (e == cudaSuccess) e = cudaMalloc(reinterpret_cast<void**>(&p->loss), sizeof(float));
     if (e == cudaSuccess) e = cudaMalloc(reinterpret_cast<void**>(&p->frag), crbm::kFrags * 32 * sizeof(uint2));
     if (e == cudaSuccess) e = cudaMalloc(reinterpret_cast<void**>(&p->bias), 33 * sizeof(float));
+    if (e == cudaSuccess) e = cudaMalloc(reinterpret_cast<void**>(&p->c1), crbm::kC1 * sizeof(float));
     if (e == cudaSuccess) e = cudaMalloc(reinterpret_cast<void**>(&p->stats), 2 * sizeof(unsigned long long));
     // He-style initial weights; the output layer starts small (q near 1/2)
     std::vector<float> w(kNP, 0.f);
@@ -691,7 +752,7 @@ int crbm_proposal_create(crbm_proposal** out, int32_t block, uint64_t seed) {
 
 void crbm_proposal_destroy(crbm_proposal* p) {
     if (!p) return;
-    void* b[] = {p->w, p->wb, p->m, p->v2, p->grad, p->loss, p->frag, p->bias, p->stats, p->ex};
+    void* b[] = {p->w, p->wb, p->m, p->v2, p->grad, p->loss, p->frag, p->bias, p->c1, p->stats, p->ex};
     for (void* x : b)
         if (x) cudaFree(x);
     delete p;

@@ -4,7 +4,10 @@
 // (Eq. 10).  Spins are stored as 64-chain words, two 32-bit halves per site
 // ([group][site][2]); a CTA works on one 32-chain half and one tile of cells,
 // staging its tile (plus a one-site / one-cell halo) in shared memory with
-// plain coalesced loads, and reuses the per-cell cores of the SMEM path.
+// plain coalesced loads, and reuses the per-cell cores of the SMEM path.  In
+// paper precision (kPaper) the hidden half-step makes the tag-0 and tag-1
+// calls and the visible half-step draws the tag-1 call again for its four
+// 16-bit uniforms: three calls per cell instead of four.
 #include "crbm_canon_core.cuh"
 
 namespace crbm {
@@ -118,6 +121,7 @@ __device__ __forceinline__ void stage_hidden_halo(const SweepArgs& a, int w, int
 // Hidden half-step of one tile: v tile rows 2 i0 .. 2 i0 + 2 TI and columns
 // 2 j0 .. 2 j0 + 2 TJ (wrapped), the lanes' hidden words out to
 // h[word][cell][32].
+template <bool kPaper>
 __global__ void __launch_bounds__(kStreamThreads, CRBM_STREAM_MIN_BLOCKS) k_stream_hidden(const SweepArgs a, uint32_t t) {
     __shared__ __align__(16) uint32_t s_th[kCanonTh];
     __shared__ uint32_t s_v[(2 * kTI + 1) * (2 * kTJ + 1)];
@@ -151,7 +155,8 @@ __global__ void __launch_bounds__(kStreamThreads, CRBM_STREAM_MIN_BLOCKS) k_stre
         uint32_t* hp = s_h + lj * 32 + lane;
         const uint4* q = s_q[lj];
         for (int li = 0; li < ni; ++li, v += 2 * VS, hp += kTJ * 32, q += 2 * kTJ)
-            *hp = hidden_cell(v, VS, s_th, rs, r0l.lo, q[0], q[1], a.rk, lc);
+            *hp = kPaper ? hidden_cell_paper(v, VS, s_th, rs, r0l.lo, q[0], q[1], a.rk, lc)
+                         : hidden_cell(v, VS, s_th, rs, r0l.lo, q[0], q[1], a.rk, lc);
     }
     __syncthreads();
     // tile rows of hidden words are contiguous runs of nj * 32 words in h
@@ -165,6 +170,7 @@ __global__ void __launch_bounds__(kStreamThreads, CRBM_STREAM_MIN_BLOCKS) k_stre
 
 // Visible half-step of one tile: hidden words of the tile cells plus the row
 // of cells above and the column to the left (wrapped), new spins out.
+template <bool kPaper>
 __global__ void __launch_bounds__(kStreamVisThreads, CRBM_STREAM_VIS_MIN_BLOCKS) k_stream_visible(const SweepArgs a, uint32_t t) {
     __shared__ __align__(16) uint32_t s_tv[4 * 32 * 32];
     __shared__ __align__(16) uint32_t s_h[(kTI + 1) * (kTJ + 1) * 32];
@@ -191,15 +197,22 @@ __global__ void __launch_bounds__(kStreamVisThreads, CRBM_STREAM_VIS_MIN_BLOCKS)
     const int ni = min(kTI, W - i0), nj = min(kTJ, W - j0);
     for (int x = threadIdx.x; x < kTI * kTJ; x += blockDim.x) {
         const int li = x / kTJ, lj = x - li * kTJ;
-        if (li < ni && lj < nj) s_q[x] = visible_call_words(static_cast<uint32_t>((i0 + li) * W + j0 + lj), a.rk);
+        if (li < ni && lj < nj) {
+            const uint32_t cell = static_cast<uint32_t>((i0 + li) * W + j0 + lj);
+            s_q[x] = kPaper ? visible_call_words_paper(cell, a.rk) : visible_call_words(cell, a.rk);
+        }
     }
     __syncthreads();
     for (int lj = warp; lj < nj; lj += nwarp) {
         const uint32_t* ho = s_h + (HS + lj + 1) * 32 + lane;
         uint32_t* o = s_o + 2 * lj;
         const uint4* q = s_q + lj;
-        for (int li = 0; li < ni; ++li, ho += HS * 32, o += 2 * VO, q += kTJ)
-            visible_cell(o, VO, ho[0], ho[-HS * 32], ho[-32], s_tv, rs, r0l.lo, *q, a.rk, lc);
+        for (int li = 0; li < ni; ++li, ho += HS * 32, o += 2 * VO, q += kTJ) {
+            if (kPaper)
+                visible_cell_paper(o, VO, ho[0], ho[-HS * 32], ho[-32], s_tv, rs, r0l.lo, *q, a.rk, lc);
+            else
+                visible_cell(o, VO, ho[0], ho[-HS * 32], ho[-32], s_tv, rs, r0l.lo, *q, a.rk, lc);
+        }
     }
     __syncthreads();
     for (int x = threadIdx.x; x < 2 * kTI * VO; x += blockDim.x) {
@@ -286,8 +299,13 @@ cudaError_t launch_sweep_stream(const SweepArgs& a, cudaStream_t st, int64_t* la
     int64_t meas = a.meas0;
     for (int it = 0; it < a.n_sweeps; ++it) {
         const uint32_t t = a.t0 + static_cast<uint32_t>(it);
-        k_stream_hidden<<<grid, kStreamThreads, 0, st>>>(a, t);
-        k_stream_visible<<<grid, kStreamVisThreads, 0, st>>>(a, t);
+        if (a.g.paper) {
+            k_stream_hidden<true><<<grid, kStreamThreads, 0, st>>>(a, t);
+            k_stream_visible<true><<<grid, kStreamVisThreads, 0, st>>>(a, t);
+        } else {
+            k_stream_hidden<false><<<grid, kStreamThreads, 0, st>>>(a, t);
+            k_stream_visible<false><<<grid, kStreamVisThreads, 0, st>>>(a, t);
+        }
         *launches += 2;
         if (a.measure_every > 0 && (t + 1u) % static_cast<uint32_t>(a.measure_every) == 0u) {
             k_stream_count<<<grid, kStreamThreads, 0, st>>>(a);

@@ -1,6 +1,7 @@
 """The paper-precision mode (CRBM_PRECISION_PAPER) on the GPU against the
 oracle's, bit for bit: host tables, spins, sums and series, replica exchange,
-and the full L=18 grid in the launch the benchmark times."""
+the streamed layout (which draws the tag-1 call twice), and the full L=18
+grid and L=384 lattice in the launches the benchmark times."""
 import numpy as np
 import pytest
 
@@ -20,9 +21,9 @@ def _gpu():
 
 
 def run_pair(orc, L, params, n_chains, chain_param, seed, splits, measure_every=1, series_len=0,
-             check_ids=None, sq_every=0):
+             check_ids=None, sq_every=0, layout=crbm.CRBM_LAYOUT_AUTO):
     s = crbm.Sampler(L, params, n_chains, chain_param=chain_param, seed=seed, measure_every=measure_every,
-                     series_len=series_len, sq_every=sq_every, precision=PAPER)
+                     series_len=series_len, sq_every=sq_every, precision=PAPER, layout=layout)
     ids = np.arange(n_chains, dtype=np.uint32) if check_ids is None else np.asarray(check_ids, np.uint32)
     cp = np.asarray(chain_param, np.int32)[ids]
     spins = orc.init_spins(L, ids, seed)
@@ -63,6 +64,35 @@ def test_paper_precision_bitexact(orc, L, n):
              measure_every=2, series_len=12)
 
 
+@pytest.mark.parametrize("L,n", [(8, 70), (40, 64), (34, 130)])
+def test_paper_precision_stream_bitexact(orc, L, n):
+    """Streamed layout in paper precision: ragged 16x16-cell tiles (W = 20,
+    17) and a ragged last 64-chain group, against the oracle and against the
+    shared-memory layout, which keeps the tag-1 words instead of drawing them
+    again."""
+    rng = np.random.default_rng(L * 13 + n)
+    params = workloads.random_params(rng, 3)
+    cp = rng.integers(0, 3, n).astype(np.int32)
+    s = run_pair(orc, L, params, n, cp, 5 + L, splits=[2, 5], measure_every=2, series_len=4,
+                 layout=crbm.CRBM_LAYOUT_STREAM)
+    assert s.layout == crbm.CRBM_LAYOUT_STREAM
+    m = crbm.Sampler(L, params, n, chain_param=cp, seed=5 + L, measure_every=2, precision=PAPER,
+                     layout=crbm.CRBM_LAYOUT_SMEM)
+    m.sweep(7)
+    assert np.array_equal(m.get_spins(), s.get_spins())
+    assert np.array_equal(m.observables(), s.observables())
+
+
+@pytest.mark.slow
+def test_paper_precision_stream_L384_sampled_chains(orc):
+    """The L=384 workload at full size (3072 chains) in paper precision, as
+    the benchmark's streamed paper line runs it: 16 chains over all words."""
+    w = workloads.stream_workload()
+    ids = np.linspace(0, w["n_chains"] - 1, 16).astype(np.uint32)
+    run_pair(orc, 384, w["params"], w["n_chains"], w["chain_param"], w["seed"], splits=[1, 2],
+             measure_every=1, check_ids=ids)
+
+
 def test_paper_precision_tempering_bitexact(orc):
     L, n_lad = 8, 2
     betas = 0.2 * (50.0 ** (np.arange(32) / 31.0))
@@ -92,7 +122,7 @@ def test_paper_precision_full_grid_sampled_chains(orc):
 
 def test_paper_precision_where_unsupported():
     ok = dict(J=[1.0], Jp=[1.0], h=[0.5], beta=[2.0])
-    for kw in (dict(L=9), dict(L=10, periodic=False), dict(L=20, layout=crbm.CRBM_LAYOUT_STREAM)):
+    for kw in (dict(L=9), dict(L=10, periodic=False), dict(L=9, layout=crbm.CRBM_LAYOUT_STREAM)):
         with pytest.raises(crbm.CrbmError) as e:
             crbm.Sampler(params=ok, n_chains=32, precision=PAPER, **kw)
         assert e.value.code == crbm.CRBM_EUNSUPPORTED, kw

@@ -1,6 +1,9 @@
 """Rectangular lattices, a boundary per axis and an odd-column field on the
-GPU (generic sweep) against the oracle, bit for bit: tables, spins, sums and
-series; the laterally confined 18 x 12 strip of Sec. III among them."""
+GPU against the oracle, bit for bit: tables, spins, sums and series; the
+laterally confined 18 x 12 strip of Sec. III among them.  Rectangles with even
+sides, periodic along both axes, run on the canonical shared-memory sweep
+(also split into bands over a cluster in a batch); the rest on the generic
+sweep."""
 import numpy as np
 import pytest
 
@@ -19,11 +22,12 @@ def _gpu():
     crbm.load_library()
 
 
-def run_pair(orc, L, Lc, pr, pc, params, n, seed, splits, measure_every=2, series_len=8, swap_every=0):
+def run_pair(orc, L, Lc, pr, pc, params, n, seed, splits, measure_every=2, series_len=8, swap_every=0,
+             precision=0):
     cp = (np.arange(n) % len(params["J"])).astype(np.int32)
     s = crbm.Sampler(L, params, n, chain_param=cp, seed=seed, periodic=pr, L_cols=Lc,
                      periodic_cols=PERIODIC if pc else OPEN, measure_every=measure_every,
-                     series_len=series_len)
+                     series_len=series_len, precision=precision)
     assert s.get_spins().shape == (n, L, Lc)
     ids = np.arange(n, dtype=np.uint32)
     spins = orc.init_spins((L, Lc), ids, seed)
@@ -32,7 +36,7 @@ def run_pair(orc, L, Lc, pr, pc, params, n, seed, splits, measure_every=2, serie
     for k in splits:
         s.sweep(k)
         sums, ser, _ = orc.run((L, Lc), params, cp, spins, seed, t, k, measure_every, chain_ids=ids,
-                               periodic=(pr, pc), sums=sums, series_cap=series_len)
+                               periodic=(pr, pc), sums=sums, series_cap=series_len, precision=precision)
         if ser is not None:
             oser = ser if oser is None else np.where(ser != 0, ser, oser)
         t += k
@@ -50,6 +54,49 @@ def test_rectangles_bitexact(orc, L, Lc, pr, pc):
     params = workloads.random_params(rng, 3)
     s = run_pair(orc, L, Lc, pr, pc, params, 45, 3 + L + Lc, splits=[3, 14])
     assert s.layout == crbm.CRBM_LAYOUT_SMEM
+
+
+@pytest.mark.parametrize("L,Lc", [(18, 12), (12, 30), (40, 8), (4, 16)])
+@pytest.mark.parametrize("precision", [crbm.CRBM_PRECISION_EXACT, crbm.CRBM_PRECISION_PAPER])
+def test_periodic_rectangles_on_the_canonical_sweep(orc, L, Lc, precision):
+    """Even sides, periodic along both axes: the ten SS filters' fast path
+    (per-cell records over W x Wc cells), in both precisions."""
+    rng = np.random.default_rng(L * 31 + Lc + precision)
+    params = workloads.random_params(rng, 3)
+    s = run_pair(orc, L, Lc, True, True, params, 70, 7 + L + Lc, splits=[4, 9], precision=precision)
+    assert s.layout == crbm.CRBM_LAYOUT_SMEM
+
+
+@pytest.mark.parametrize("cluster", [2, 8])
+def test_periodic_rectangle_split_over_a_cluster(orc, cluster, monkeypatch):
+    """A 24 x 16 periodic rectangle split into bands of cell rows over a
+    thread-block cluster, beside a square member, against its twin and the
+    oracle."""
+    monkeypatch.setenv("CRBM_BATCH_CLUSTER", str(cluster))
+    rng = np.random.default_rng(70 + cluster)
+    specs = [dict(L=24, L_cols=16, params=workloads.random_params(rng, 2), n_chains=64, seed=21,
+                  measure_every=3),
+             dict(L=20, params=workloads.random_params(rng, 2), n_chains=32, seed=22, measure_every=3)]
+    for sp in specs:
+        sp["chain_param"] = (np.arange(sp["n_chains"]) % 2).astype(np.int32)
+    batched = [crbm.Sampler(**sp) for sp in specs]
+    twins = [crbm.Sampler(**sp) for sp in specs]
+    batch = crbm.Batch(batched)
+    assert batch.cluster == cluster
+    for n in (5, 7):
+        batch.sweep(n)
+        for t in twins:
+            t.sweep(n)
+    for a, b in zip(batched, twins):
+        assert np.array_equal(a.get_spins(), b.get_spins())
+        assert np.array_equal(a.observables(), b.observables())
+    batch.close()
+    sp = specs[0]
+    ids = np.arange(sp["n_chains"], dtype=np.uint32)
+    spins = orc.init_spins((24, 16), ids, sp["seed"])
+    sums, _, _ = orc.run((24, 16), sp["params"], sp["chain_param"], spins, sp["seed"], 0, 12, 3, chain_ids=ids)
+    assert np.array_equal(batched[0].get_spins(), spins)
+    assert np.array_equal(batched[0].observables(), sums)
 
 
 @pytest.mark.parametrize("L,Lc,pr,pc", [(8, 6, True, False), (7, 9, False, False), (6, 6, True, True)])
@@ -93,7 +140,9 @@ def test_rectangle_validation():
     for kw, code in ((dict(L_cols=2), crbm.CRBM_EINVAL), (dict(periodic_cols=5), crbm.CRBM_EINVAL),
                      (dict(L_cols=8, sq_every=2), crbm.CRBM_EINVAL),
                      (dict(periodic_cols=OPEN, sq_every=2), crbm.CRBM_EINVAL),
-                     (dict(L_cols=8, layout=crbm.CRBM_LAYOUT_STREAM), crbm.CRBM_EUNSUPPORTED)):
+                     (dict(L_cols=8, layout=crbm.CRBM_LAYOUT_STREAM), crbm.CRBM_EUNSUPPORTED),
+                     (dict(L_cols=8, periodic_cols=OPEN, precision=crbm.CRBM_PRECISION_PAPER),
+                      crbm.CRBM_EUNSUPPORTED)):
         with pytest.raises(crbm.CrbmError) as e:
             crbm.Sampler(6, ok, 32, **kw)
         assert e.value.code == code, kw
@@ -101,6 +150,10 @@ def test_rectangle_validation():
                   beta=list(0.5 + 0.1 * np.arange(32)))
     with pytest.raises(crbm.CrbmError) as e:
         crbm.Sampler(6, ladder, 32, chain_param=np.arange(32), swap_every=2)
+    assert e.value.code == crbm.CRBM_EUNSUPPORTED
+    prop = crbm.Proposal(seed=1)                  # block proposals: square lattices only
+    with pytest.raises(crbm.CrbmError) as e:
+        prop.passes(crbm.Sampler(8, ok, 32, L_cols=12), 1)
     assert e.value.code == crbm.CRBM_EUNSUPPORTED
 
 

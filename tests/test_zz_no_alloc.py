@@ -43,7 +43,7 @@ def unpack_stream(words, n, L):
     return np.where(bits.reshape(G * 64, L, L)[:n] == 1, 1, -1).astype(np.int8)
 
 
-def make_params(L, params, n, cp, seed, stream):
+def make_params(L, params, n, cp, seed, stream, precision=0):
     keep = {k: np.ascontiguousarray(params[k], np.float64) for k in ("J", "Jp", "h", "beta")}
     keep["cp"] = np.ascontiguousarray(cp, np.int32)
     p = crbm.crbm_params()
@@ -53,11 +53,13 @@ def make_params(L, params, n, cp, seed, stream):
     p.n_params = len(keep["J"])
     p.chain_param = keep["cp"].ctypes.data_as(ctypes.POINTER(ctypes.c_int32))
     p.n_chains, p.seed = n, seed
+    p.precision = precision
     p.stream = ctypes.c_void_p(int(stream)) if stream else None
     return p, keep
 
 
-def test_noalloc_stream_sweep_matches_context(torch_cuda):
+@pytest.mark.parametrize("precision", [crbm.CRBM_PRECISION_EXACT, crbm.CRBM_PRECISION_PAPER])
+def test_noalloc_stream_sweep_matches_context(torch_cuda, precision):
     torch = torch_cuda
     lib = crbm.load_library()
     L, n, seed = 20, 70, 31
@@ -65,10 +67,10 @@ def test_noalloc_stream_sweep_matches_context(torch_cuda):
     params = workloads.random_params(rng, 3)
     cp = rng.integers(0, 3, n).astype(np.int32)
     ctx = crbm.Sampler(L, params, n, chain_param=cp, seed=seed, measure_every=0,
-                       layout=crbm.CRBM_LAYOUT_STREAM)
+                       layout=crbm.CRBM_LAYOUT_STREAM, precision=precision)
     dev = torch.from_numpy(pack_stream(ctx.get_spins()).view(np.int32)).cuda()
     stream = torch.cuda.current_stream().cuda_stream
-    p, _keep = make_params(L, params, n, cp, seed, stream)
+    p, _keep = make_params(L, params, n, cp, seed, stream, precision)
     t = 0
     for n_sweeps in (3, 4):                      # two calls in a row, continuing the counter
         rc = lib.crbm_sweep_stream_noalloc(ctypes.byref(p), ctypes.c_void_p(dev.data_ptr()), t, n_sweeps)
@@ -96,3 +98,9 @@ def test_noalloc_rejects_oversize_and_bad_arguments(torch_cuda):
     p.L = 20
     assert lib.crbm_sweep_stream_noalloc(ctypes.byref(p), ptr, -1, 1) == crbm.CRBM_EINVAL
     assert lib.crbm_sweep_stream_noalloc(ctypes.byref(p), None, 0, 1) == crbm.CRBM_EINVAL
+    for field, bad in (("precision", 7), ("L_cols", 12), ("periodic_cols", crbm.CRBM_BC_OPEN),
+                       ("periodic_cols", 5)):
+        old = getattr(p, field)
+        setattr(p, field, bad)
+        assert lib.crbm_sweep_stream_noalloc(ctypes.byref(p), ptr, 0, 1) == crbm.CRBM_EINVAL, field
+        setattr(p, field, old)

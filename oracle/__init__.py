@@ -25,6 +25,8 @@ _LIB = os.path.join(_LIB_DIR, "liboracle.so")
 NSUM = 11
 TAG_VIS, TAG_INIT, TAG_SWAP = 4, 5, 6
 PRECISION_EXACT, PRECISION_PAPER = 0, 1
+RNG_LANE, RNG_BITPLANE = 0, 1      # RNG_BITPLANE: ORC_RNG_BITPLANE in crbm_oracle.h
+TAG_BITPLANE = 256
 
 
 def build(force: bool = False) -> str:
@@ -182,10 +184,12 @@ def counts(spins, L, periodic=True, bonds=None):
 
 def run(L, params, chain_param, spins, seed, sweep0, n_sweeps, measure_every=1,
         chain_ids=None, periodic=True, bonds=None, sums=None, series_cap=0, sq_every=0,
-        sq=None, precision=PRECISION_EXACT):
+        sq=None, precision=PRECISION_EXACT, rng=RNG_LANE):
     """Advance ``spins`` [n_chains][L][L] (int8 +-1, modified in place).
 
     params: dict of equal-length sequences J, Jp, h, beta.
+    rng: RNG_LANE (one Philox stream per chain) or RNG_BITPLANE (uniforms from
+    bit-plane words shared by each group of 32 chains).
     Returns (sums [n_chains][11] int64, series or None, sq or None).
     """
     arr, nb = bonds_array(bonds)
@@ -211,7 +215,8 @@ def run(L, params, chain_param, spins, seed, sweep0, n_sweeps, measure_every=1,
                        ctypes.c_int64(sweep0), ctypes.c_int64(n_sweeps), int(measure_every),
                        _p(spins, ctypes.c_int8), _p(sums, ctypes.c_int64),
                        _p(series, ctypes.c_int32), ctypes.c_int64(series_cap), int(sq_every),
-                       _p(sq, ctypes.c_double) if sq_every > 0 else None, int(precision))
+                       _p(sq, ctypes.c_double) if sq_every > 0 else None,
+                       int(precision) | (0x10 if rng == RNG_BITPLANE else 0))
     if rc:
         raise ValueError(f"orc_run failed ({rc})")
     return sums, series, sq

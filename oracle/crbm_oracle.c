@@ -340,7 +340,26 @@ typedef struct {
     uint32_t* Tv_odd;  /* visible table of the odd columns */
     int s[2];
     int paper;  /* ORC_PRECISION_PAPER: 16-bit uniforms and thresholds */
+    int bitplane; /* ORC_RNG_BITPLANE: uniforms from shared bit-plane words */
 } orc_point;
+
+/* The bit-plane uniform of chain `chain` at node `node` of cell `cell` (see
+ * ORC_RNG_BITPLANE in crbm_oracle.h): all 32 planes of its 32-chain group,
+ * bit chain % 32 of each, most significant first. */
+static uint32_t bitplane_uniform(uint32_t cell, uint32_t sweep, uint32_t chain, int node, uint64_t seed) {
+    uint32_t key[2] = {(uint32_t)(seed & 0xffffffffu), (uint32_t)(seed >> 32)};
+    uint32_t u = 0;
+    for (int j = 0; j < 8; ++j) {
+        uint32_t ctr[4] = {cell, sweep, chain / 32u, ORC_TAG_BITPLANE + 8u * (uint32_t)node + (uint32_t)j};
+        uint32_t out[4];
+        orc_philox4x32_10(ctr, key, out);
+        for (int i = 0; i < 4; ++i) {
+            const int b = 4 * j + i;
+            u |= ((out[i] >> (chain % 32u)) & 1u) << (31 - b);
+        }
+    }
+    return u;
+}
 
 /* One unit's decision.  Exact precision: word w of Philox((cell, sweep,
  * chain, tag)) against the 32-bit threshold.  Paper precision: the 16-bit
@@ -373,7 +392,9 @@ static void one_sweep(const orc_geom* g, const orc_bond* bonds, int nb, const or
                 int m = (s1 >= 0 ? v[s1] : 0) + pt->s[b->cls] * (s2 >= 0 ? v[s2] : 0);
                 uint32_t t = pt->Th[b->cls * 5 + (m + 2)];
                 int up;
-                if (!pt->paper)
+                if (pt->bitplane)
+                    up = bitplane_uniform(cell, sweep, chain, k, seed) < t;
+                else if (!pt->paper)
                     up = draw_below(pt, cell, sweep, chain, (uint32_t)(k >> 2), k & 3, 0, seed, t);
                 else if (k < 8)
                     up = draw_below(pt, cell, sweep, chain, 0u, k >> 1, k & 1, seed, t);
@@ -405,8 +426,9 @@ static void one_sweep(const orc_geom* g, const orc_bond* bonds, int nb, const or
             int x = 2 * (R & 1) + (C & 1);
             const uint32_t* Tv = (C & 1) ? pt->Tv_odd : pt->Tv;
             uint32_t t = Tv[(field[s] + DJ) * nP + (field[N + s] + DJp)];
-            int up = pt->paper ? draw_below(pt, cell, sweep, chain, 1u, 1 + (x >> 1), x & 1, seed, t)
-                               : draw_below(pt, cell, sweep, chain, ORC_TAG_VIS, x, 0, seed, t);
+            int up = pt->bitplane ? bitplane_uniform(cell, sweep, chain, 10 + x, seed) < t
+                     : pt->paper  ? draw_below(pt, cell, sweep, chain, 1u, 1 + (x >> 1), x & 1, seed, t)
+                                  : draw_below(pt, cell, sweep, chain, ORC_TAG_VIS, x, 0, seed, t);
             v[s] = up ? 1 : -1;
         }
 }
@@ -426,6 +448,9 @@ static int run_g(const orc_geom* g, const orc_bond* bonds, int nb, const double*
                  const int32_t* chain_param, const uint32_t* chain_ids, int n_chains, uint64_t seed,
                  int64_t sweep0, int64_t n_sweeps, int measure_every, int8_t* spins, int64_t* sums,
                  int32_t* series, int64_t series_cap, int sq_every, double* sq, int precision) {
+    const int bitplane = (precision & ORC_RNG_BITPLANE) != 0;
+    precision &= ~ORC_RNG_BITPLANE;
+    if (bitplane && (precision != ORC_PRECISION_EXACT || nb > 10)) return -1;
     int DJ, DJp;
     if (degrees_g(g, bonds, nb, &DJ, &DJp)) return -1;
     if (n_params < 1 || n_chains < 0 || n_sweeps < 0 || sweep0 < 0 ||
@@ -446,6 +471,7 @@ static int run_g(const orc_geom* g, const orc_bond* bonds, int nb, const double*
         pts[p].Tv = tv + (size_t)p * 2 * nTv;
         pts[p].Tv_odd = pts[p].Tv + nTv;
         pts[p].paper = precision == ORC_PRECISION_PAPER;
+        pts[p].bitplane = bitplane;
         if (tables_g(g, bonds, nb, J[p], Jp[p], h[p], h_odd ? h_odd[p] : h[p], beta[p], precision, pts[p].Th,
                      pts[p].Tv, pts[p].Tv_odd))
             err = -1;
@@ -552,6 +578,7 @@ static int run_pt_g(const orc_geom* g, const orc_bond* bonds, int nb, const doub
                     int32_t* slot_of_beta, int64_t* sums, int32_t* series, int64_t series_cap,
                     int precision) {
     if (n_chains <= 0 || n_chains % 32 || swap_every <= 0 || measure_every < 0) return -1;
+    if (precision & ORC_RNG_BITPLANE) return -1;
     int n_lad = n_chains / 32, N = g->Lr * g->Lc;
     for (int l = 0; l < n_lad; ++l) {
         const int32_t* cp = chain_param + 32 * l;

@@ -153,6 +153,24 @@ int orc_run_ex(int L, int periodic, const orc_bond* bonds, int nb,
                int measure_every, int8_t* spins, int64_t* sums,
                int32_t* series, int64_t series_cap, int sq_every, double* sq, int precision);
 
+/* ---- bit-plane uniforms -----------------------------------------------------
+ * A second source of the uniforms, for groups of 32 chains (chain c is bit
+ * c % 32 of group c / 32): the uniform of every chain of a group at one node
+ * is built from shared bit-plane words, most significant bit first, so that a
+ * word-parallel comparison can stop as soon as all 32 decisions are known.
+ * The uniform of chain c at node n of cell `cell` in sweep t is
+ *   u = sum_b bit (c % 32) of P_b  <<  (31 - b),   b = 0 .. 31,
+ * where plane P_(4j+i) is output word i of
+ *   Philox((cell, t, c / 32, ORC_TAG_BITPLANE + 8 n + j)),  j = 0 .. 7,
+ * and the node of hidden filter k is n = k, the node of the spin at window
+ * offset (r, c) is n = 10 + 2r + c.  The unit is +1 iff u < t with the exact
+ * thresholds, as in every other mode.  Selected by OR-ing ORC_RNG_BITPLANE
+ * into the precision argument of the _ex and _rect samplers; it needs
+ * ORC_PRECISION_EXACT, at most 10 filters, and is not offered with replica
+ * exchange. */
+#define ORC_RNG_BITPLANE 0x10
+#define ORC_TAG_BITPLANE 256u
+
 #define ORC_TAG_VIS 4u
 #define ORC_TAG_INIT 5u
 #define ORC_TAG_SWAP 6u

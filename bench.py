@@ -50,7 +50,22 @@ MEASURED_TRAFFIC = {
     "stream": (56.74e6 + 392.31e6 + 454.82e6 + 48.83e6, "per sweep (two launches); profiles/k_stream_L384.md"),
     "grid_paper": (8.77e6 + 0.64e6, "per launch; profiles/k_sweep_canon_persistent_L18_grid_paper.md"),
     "stream_paper": (56.76e6 + 390.29e6 + 454.76e6 + 45.71e6, "per sweep (two launches); profiles/k_stream_L384.md"),
+    "grid_bitplane": (None, "not captured for this kernel"),
 }
+
+
+def bitplane_expected_calls(n_nodes):
+    """Expected Philox calls of one bit-plane half-step over n_nodes nodes of
+    one 32-chain word.  A warp takes 32 consecutive nodes and draws calls of
+    four planes while any of its (nodes x 32 chains) comparisons is undecided;
+    each plane decides an undecided comparison with probability 1/2, so it is
+    still open after 4 m planes with probability 2^-4m, independently."""
+    total = 0.0
+    for base in range(0, n_nodes, 32):
+        lanes = min(32, n_nodes - base)
+        calls = sum(1.0 - (1.0 - 2.0 ** (-4 * m)) ** (32 * lanes) for m in range(8))
+        total += calls * lanes
+    return total
 
 
 def parse():
@@ -67,7 +82,12 @@ def parse():
     ap.add_argument("--precision", default="exact", choices=["exact", "paper"],
                     help="paper: the FPGA's 10-bit weights, 16-bit sigmoid table and 16-bit uniforms "
                          "(grid and stream workloads)")
+    ap.add_argument("--rng", default="lane", choices=["lane", "bitplane"],
+                    help="bitplane: uniforms from bit-plane words shared by the 32 chains of a word, compared "
+                         "most significant bit first (grid workload)")
     args = ap.parse_args()
+    if args.rng == "bitplane" and (args.workload != "grid" or args.precision != "exact"):
+        ap.error("--rng bitplane runs the grid workload in exact precision")
     if args.precision == "paper" and args.workload not in ("grid", "stream"):
         ap.error("--precision paper runs the grid and stream workloads only")
     return args
@@ -160,7 +180,7 @@ def workload_config(name, rank):
 DEFAULT_SWEEPS = {"grid": 2000, "stream": 20, "batch": 500, "proposal": 1000, "tts": 4000}
 
 
-def cpu_baseline(w, seconds, precision=0):
+def cpu_baseline(w, seconds, precision=0, rng=0):
     """The oracle as it stands, OpenMP over chains on every host core, on a
     bounded sample of the same workload (a spread subset of its chains)."""
     import oracle
@@ -175,7 +195,7 @@ def cpu_baseline(w, seconds, precision=0):
         cp = np.asarray(w["chain_param"], np.int32)[ids]
         sp = oracle.init_spins(L, ids, w["seed"])
         t = time.perf_counter()
-        oracle.run(L, w["params"], cp, sp, w["seed"], 0, n_sw, 10, chain_ids=ids, precision=precision)
+        oracle.run(L, w["params"], cp, sp, w["seed"], 0, n_sw, 10, chain_ids=ids, precision=precision, rng=rng)
         return time.perf_counter() - t
 
     small = L <= 64
@@ -201,9 +221,10 @@ def run_reference(args, rank, ws):
         return
     w = workload_config(args.workload, 0)
     per_step = max(1.0, 60.0 / max(1, args.steps + args.warmup))
+    prec, rng = (1 if args.precision == "paper" else 0), (1 if args.rng == "bitplane" else 0)
     for _ in range(args.warmup):
-        cpu_baseline(w, min(per_step, 2.0), 1 if args.precision == "paper" else 0)
-    vals = [cpu_baseline(w, per_step, 1 if args.precision == "paper" else 0) for _ in range(args.steps)]
+        cpu_baseline(w, min(per_step, 2.0), prec, rng)
+    vals = [cpu_baseline(w, per_step, prec, rng) for _ in range(args.steps)]
     v = float(np.mean([x["value"] for x in vals]))
     cb = dict(vals[-1])
     cb["value"] = v
@@ -227,6 +248,9 @@ def config_dict(w, args):
     if getattr(args, "precision", "exact") == "paper":
         desc += ("; paper precision: Q5.4 weights and bias, 12-bit accumulator, 16-bit sigmoid table "
                  "and 16-bit uniforms (two per Philox word)")
+    if getattr(args, "rng", "lane") == "bitplane":
+        desc += ("; bit-plane uniforms: shared plane words per 32-chain word, compared most significant "
+                 "bit first with early exit (word-parallel kernel, one thread per node)")
     return {"workload": desc, "L": w["L"], "n_chains": w["n_chains"],
             "n_params": len(w["params"]["J"]), "sweeps_per_step": args.sweeps_per_step,
             "measure_every": args.measure_every,
@@ -468,9 +492,11 @@ def main():
     n_meas = S * K // args.measure_every
     layout = crbm.CRBM_LAYOUT_SMEM if args.workload == "grid" else crbm.CRBM_LAYOUT_STREAM
     paper = args.precision == "paper"
+    bitplane = args.rng == "bitplane"
     s = crbm.Sampler(w["L"], w["params"], w["n_chains"], chain_param=w["chain_param"], seed=w["seed"],
                      measure_every=args.measure_every, series_len=n_meas, layout=layout,
-                     precision=crbm.CRBM_PRECISION_PAPER if paper else crbm.CRBM_PRECISION_EXACT)
+                     precision=crbm.CRBM_PRECISION_PAPER if paper else crbm.CRBM_PRECISION_EXACT,
+                     rng=crbm.CRBM_RNG_BITPLANE if bitplane else crbm.CRBM_RNG_LANE)
     tuned_warps = s.autotune(200) if args.workload == "grid" else None  # CTA shape, on scratch copies
     stream = torch.cuda.current_stream()
     flush = torch.empty(256 * 1024 * 1024, dtype=torch.uint8, device="cuda")
@@ -529,13 +555,17 @@ def main():
     if paper:
         cpc = CALLS_PER_CELL_PAPER if args.workload == "grid" else CALLS_PER_CELL_PAPER_STREAM
     calls = cpc * (w["L"] // 2) ** 2 * w["n_chains"] * S
+    if bitplane:   # expected calls of the early-exit comparison (hidden nodes, then spins)
+        n_words = (w["n_chains"] + 31) // 32
+        calls = (bitplane_expected_calls(10 * (w["L"] // 2) ** 2) + bitplane_expected_calls(w["L"] ** 2)) * n_words * S
+        cpc = calls / ((w["L"] // 2) ** 2 * w["n_chains"] * S)
     if args.workload == "grid":   # one launch per step: spins in and out once
         hbm_bytes = w["n_chains"] * w["L"] ** 2 / 8 * 2
     else:                         # per sweep: spins read + written, hidden written + read
         hbm_bytes = w["n_chains"] * w["L"] ** 2 * 7 / 8 * S
     achieved = MUL_OPS_PER_CALL * calls / (t_total / K) / 1e12
     peak = SM_COUNT * IMUL_LANES_PER_SM_CLK * SM_MAX_MHZ * 1e6 / 1e12
-    traffic = MEASURED_TRAFFIC[args.workload + ("_paper" if paper else "")]
+    traffic = MEASURED_TRAFFIC[args.workload + ("_paper" if paper else "") + ("_bitplane" if bitplane else "")]
     cfg = config_dict(w, args)
     if tuned_warps:
         cfg["warps_per_cta_autotuned"] = tuned_warps
@@ -560,11 +590,12 @@ def main():
                      "traffic_unit": "bytes " + traffic[1],
                      "note": "integer-multiply ceiling: 152 SM x 64 lanes/clk x 2070 MHz; 40 "
                              "multiply ops per Philox-4x32-10 call, "
-                             f"{cpc} calls per chain-cell-sweep",
+                             f"{cpc:.3g} calls per chain-cell-sweep" + (" (expected count of the bit-plane "
+                             "early exit)" if bitplane else ""),
                      "philox_calls_per_s": calls / (t_total / K)},
     }
     if rank == 0 and not args.no_cpu_baseline:
-        out["cpu_baseline"] = cpu_baseline(w, args.cpu_seconds, 1 if paper else 0)
+        out["cpu_baseline"] = cpu_baseline(w, args.cpu_seconds, 1 if paper else 0, 1 if bitplane else 0)
     if rank == 0:
         print(json.dumps(out))
     if ws > 1:

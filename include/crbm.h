@@ -66,6 +66,10 @@ extern "C" {
 #define CRBM_BC_PERIODIC 1
 #define CRBM_BC_OPEN 2
 
+/* Source of the uniforms. */
+#define CRBM_RNG_LANE 0     /* one Philox stream per chain: counter (cell, sweep, chain, tag) */
+#define CRBM_RNG_BITPLANE 1 /* bit-plane words shared by the 32 chains of a word (see crbm_params) */
+
 #define CRBM_PRECISION_EXACT 0 /* double-precision weights, 32-bit thresholds and uniforms */
 #define CRBM_PRECISION_PAPER 1 /* the paper's FPGA (Sec. III, "Dimension and Precision"):
                                 * weights and visible bias in 10-bit fixed point (4 fraction
@@ -142,6 +146,20 @@ typedef struct {
      * the first, and crbm_observables' M is still the total magnetisation.
      * Not with replica exchange (its energies use the total M). */
     const double* h_odd;
+    /* CRBM_RNG_LANE (0) or CRBM_RNG_BITPLANE.  Bit-plane uniforms: for the
+     * 32 chains c = 32 w + l of word w, node n of cell `cell` in sweep t draws
+     * plane words P_b, b = 0..31, P_(4j+i) = word i of Philox((cell, t, w,
+     * 256 + 8 n + j)), and chain l's uniform is sum_b bit l of P_b << (31 -
+     * b): most significant bit first, so a comparison of all 32 uniforms
+     * with their thresholds can stop at the first plane on which every chain
+     * is decided (about 10 planes, 3 calls, per node and word instead of 8
+     * calls for 32 separate uniforms).  Node n = k for hidden filter k, 10 +
+     * 2r + c for the spin at window offset (r, c).  Needs the ten SS filters
+     * on an even periodic lattice in the SMEM layout, exact precision, no
+     * replica exchange or correlations; not in batches or with block
+     * proposals.  A different random stream: the chains differ from
+     * CRBM_RNG_LANE's, with the same law. */
+    int32_t rng;
 } crbm_params;
 
 /* Build the model (Eqs. 3-8), the threshold tables, allocate device state and
@@ -335,7 +353,7 @@ const char* crbm_proposal_last_error(void);
  * p: the model and chains (L even, periodic = 1, bonds = NULL, J, Jp, h,
  *    beta, n_params, chain_param, n_chains, seed, stream, precision);
  *    L_cols 0 or L, periodic_cols CRBM_BC_AS_ROWS or CRBM_BC_PERIODIC,
- *    h_odd NULL; measure_every, series_len, sq_every and layout are ignored:
+ *    h_odd NULL, rng CRBM_RNG_LANE; measure_every, series_len, sq_every and layout are ignored:
  *    no observables are kept.
  * v: device spins owned by the caller, in/out, the streamed layout:
  *    u32 v[ceil(n_chains/64)][L*L][2], bit l of v[g][s][k] = spin +1 of chain

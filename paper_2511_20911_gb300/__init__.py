@@ -24,6 +24,7 @@ CRBM_NSUM = 11
 CRBM_LAYOUT_AUTO, CRBM_LAYOUT_SMEM, CRBM_LAYOUT_STREAM = 0, 1, 2
 CRBM_PRECISION_EXACT, CRBM_PRECISION_PAPER = 0, 1
 CRBM_BC_AS_ROWS, CRBM_BC_PERIODIC, CRBM_BC_OPEN = 0, 1, 2
+CRBM_RNG_LANE, CRBM_RNG_BITPLANE = 0, 1
 CRBM_SMEM_MAX_L = 96
 SUM_FIELDS = ("n", "NJ", "NJp", "M", "absM", "NJ2", "NJp2", "M2", "NJ_NJp", "NJ_M", "NJp_M")
 
@@ -64,7 +65,7 @@ class crbm_params(ctypes.Structure):
                 ("sq_every", ctypes.c_int32), ("layout", ctypes.c_int32),
                 ("swap_every", ctypes.c_int32), ("stream", ctypes.c_void_p), ("precision", ctypes.c_int32),
                 ("L_cols", ctypes.c_int32), ("periodic_cols", ctypes.c_int32),
-                ("h_odd", ctypes.POINTER(ctypes.c_double))]
+                ("h_odd", ctypes.POINTER(ctypes.c_double)), ("rng", ctypes.c_int32)]
 
 
 _lib = None
@@ -163,7 +164,7 @@ class Sampler:
     def __init__(self, L, params, n_chains, chain_param=None, seed=1, periodic=True,
                  bonds=None, measure_every=1, series_len=0, sq_every=0,
                  layout=CRBM_LAYOUT_AUTO, swap_every=0, stream=None, precision=0, L_cols=0,
-                 periodic_cols=CRBM_BC_AS_ROWS):
+                 periodic_cols=CRBM_BC_AS_ROWS, rng=CRBM_RNG_LANE):
         lib = load_library()
         self.L, self.n_chains = int(L), int(n_chains)
         self.L_cols = int(L_cols) if L_cols else self.L
@@ -200,7 +201,8 @@ class Sampler:
         p.precision = int(precision)
         p.L_cols, p.periodic_cols = int(L_cols), int(periodic_cols)
         p.h_odd = _ptr(self._h_odd, ctypes.c_double) if self._h_odd is not None else None
-        self.precision = int(precision)
+        p.rng = int(rng)
+        self.precision, self.rng = int(precision), int(rng)
         h = ctypes.c_void_p()
         _check(lib.crbm_create(ctypes.byref(h), ctypes.byref(p)))
         self._ctx = h

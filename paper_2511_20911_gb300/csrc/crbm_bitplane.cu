@@ -1,0 +1,205 @@
+// Bit-plane sweep (CRBM_RNG_BITPLANE), ten SS filters on an even periodic
+// lattice, SMEM layout.  A CTA holds one packed word (32 chains) and works
+// word-parallel: a thread takes one node (hidden unit or spin) for all 32
+// chains at once, with the chains in the bits of every 32-bit value.
+//
+// A node's 32 uniforms are the bit-transpose of plane words drawn from
+// Philox((cell, sweep, word, kTagBitplane + 8 node + j)), four planes per
+// call, most significant plane first.  The thresholds are held the same way
+// (per word, one bit-plane word per configuration and plane), so the 32
+// comparisons u_l < t_l run as one word-parallel comparison, most significant
+// bit first: a chain is decided at the first plane where its uniform and
+// threshold bits differ (below when the threshold bit is the 1), and a warp
+// stops drawing planes once all its nodes' chains are decided.  The result
+// equals the full 32-bit comparison, bit for bit.
+//
+// Hidden unit k of a cell: its endpoints e1, e2 (spin words; e2 flipped on
+// the chains whose class coupling is negative) select the threshold of m = e1
+// + s e2 in {-2, 0, 2} per chain.  Spin x: its four J incidences (flipped
+// where the spin is a second endpoint of a negative coupling) are counted in
+// bit-sliced form (three count bits), its J' incidence gives one bit, and
+// these select one of the 5 x 2 visible thresholds per chain.
+#include <algorithm>
+
+#include "crbm_device.cuh"
+
+namespace crbm {
+namespace {
+
+using namespace dev;
+
+constexpr int kBpNodes = 10;   // hidden filters per cell
+constexpr int kBpMaxThreads = 512;
+
+// Records of the sweep: [n_cells * 10] hidden endpoint pairs, [N][3] spin
+// incidences (layout in crbm_host.cpp), rounded up to whole uint4.
+__host__ __device__ inline size_t bp_rec_words(const Geometry& g) {
+    return (static_cast<size_t>(g.n_cells) * kBpNodes + 3 * static_cast<size_t>(g.N) + 3) & ~static_cast<size_t>(3);
+}
+
+// Shared memory, 32-bit words: running sums, planes and sign masks, counts,
+// replica identity, spins, hidden words (rounded up to whole uint4), then the
+// records when staged.
+constexpr int kBpSmemV = kAccWords + kBpTab + 96 + 32;
+static_assert(kBpSmemV % 4 == 0, "spins start on a 16-byte boundary");
+__host__ __device__ inline size_t bp_hid_words(const Geometry& g) {
+    return (static_cast<size_t>(g.n_cells) * kBpNodes + 3) & ~static_cast<size_t>(3);
+}
+
+// One plane of the word-parallel comparison: lt collects the chains whose
+// uniform is below the threshold, eq the chains still undecided.
+__device__ __forceinline__ void plane_step(uint32_t U, uint32_t T, uint32_t& lt, uint32_t& eq) {
+    lt |= eq & T & ~U;
+    eq &= ~(T ^ U);
+}
+
+template <bool kSmemRec>
+__global__ void __launch_bounds__(kBpMaxThreads) k_sweep_bitplane(const SweepArgs a) {
+    extern __shared__ __align__(16) uint32_t smem[];
+    const Geometry& g = a.g;
+    const int word = blockIdx.x;
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nwarp = blockDim.x >> 5;
+    const int N = g.N, nh = g.n_cells * kBpNodes;
+    int64_t* s_acc = reinterpret_cast<int64_t*>(smem);          // [kNSum][32] running sums
+    uint32_t* s_tab = smem + kAccWords;                          // [kBpTab] planes, sign masks
+    int* s_cnt = reinterpret_cast<int*>(s_tab + kBpTab);         // [3][32] measurement counts
+    int* s_sob = s_cnt + 96;                                     // [32] identity permutation
+    uint32_t* s_v = smem + kBpSmemV;                             // [N] spin words
+    uint32_t* s_h = s_v + N;                                     // [n_cells * 10] hidden words
+    const uint32_t* rec = reinterpret_cast<const uint32_t*>(a.crec);
+    if (kSmemRec) {
+        uint32_t* s_rec = s_h + bp_hid_words(g);  // N is a multiple of 4 (even sides)
+        const uint4* src = a.crec;
+        for (int x = threadIdx.x; x < static_cast<int>(bp_rec_words(g) / 4); x += blockDim.x)
+            reinterpret_cast<uint4*>(s_rec)[x] = __ldg(src + x);
+        rec = s_rec;
+    }
+    const uint32_t* hrec = rec;       // [n_cells * 10]
+    const uint32_t* vrec = rec + nh;  // [N][3]
+    const uint32_t* gt = a.ctab + static_cast<size_t>(word) * kCanonTab;
+    for (int x = threadIdx.x; x < kBpTab; x += blockDim.x) s_tab[x] = gt[x];
+    const uint32_t* gv = a.v + static_cast<size_t>(word) * N;
+    for (int x = threadIdx.x; x < N; x += blockDim.x) s_v[x] = __ldcg(gv + x);
+    for (int x = threadIdx.x; x < 96; x += blockDim.x) s_cnt[x] = 0;
+    if (warp == 0) s_sob[lane] = lane;
+    const bool measuring = a.measure_every > 0;
+    const uint32_t chain = static_cast<uint32_t>(word) * 32u + lane;
+    if (measuring && warp == 0)
+        for (int x = 0; x < kNSum; ++x) s_acc[x * 32 + lane] = __ldcg(a.sums + static_cast<size_t>(chain) * kNSum + x);
+    __syncthreads();
+    const uint32_t fl0 = s_tab[kBpFlip], fl1 = s_tab[kBpFlip + 1];
+    const uint32_t w32 = static_cast<uint32_t>(word);
+    int64_t meas = a.meas0;
+
+    for (int it = 0; it < a.n_sweeps; ++it) {
+        const uint32_t t = a.t0 + static_cast<uint32_t>(it);
+        // hidden half-step (Eq. 9): thread = hidden node (cell, k)
+        for (int base = warp * 32; base < nh; base += nwarp * 32) {
+            const int node = base + lane;
+            const bool valid = node < nh;
+            const int nd = valid ? node : 0;
+            const uint32_t r = hrec[nd];
+            const uint32_t cell = static_cast<uint32_t>(nd / kBpNodes);
+            const uint32_t k = static_cast<uint32_t>(nd) - cell * kBpNodes;
+            const uint32_t cls = k >= 8u ? 1u : 0u;
+            const uint32_t e1 = s_v[r & 0xFFFFu];
+            const uint32_t e2 = s_v[r >> 16] ^ (cls ? fl1 : fl0);
+            const uint32_t P = e1 & e2, M = ~(e1 | e2), Z = e1 ^ e2;  // m = 2, -2, 0
+            const uint32_t* tp = s_tab + kBpHidPlanes + cls * 96u;     // [m = -2, 0, 2][32]
+            uint32_t lt = 0u, eq = valid ? 0xffffffffu : 0u;
+#pragma unroll 1
+            for (uint32_t j = 0; j < 8u; ++j) {
+                if (!__any_sync(0xffffffffu, eq != 0u)) break;
+                const U4 q = philox(cell, t, w32, kTagBitplane + 8u * k + j, a.key0, a.key1);
+                const uint32_t* tb = tp + 4u * j;
+                plane_step(q.x, (P & tb[64]) | (M & tb[0]) | (Z & tb[32]), lt, eq);
+                plane_step(q.y, (P & tb[65]) | (M & tb[1]) | (Z & tb[33]), lt, eq);
+                plane_step(q.z, (P & tb[66]) | (M & tb[2]) | (Z & tb[34]), lt, eq);
+                plane_step(q.w, (P & tb[67]) | (M & tb[3]) | (Z & tb[35]), lt, eq);
+            }
+            if (valid) s_h[node] = lt;
+        }
+        __syncthreads();
+        // visible half-step (Eq. 10): thread = spin site
+        for (int base = warp * 32; base < N; base += nwarp * 32) {
+            const int s = base + lane;
+            const bool valid = s < N;
+            const int sd = valid ? s : 0;
+            const uint32_t r0 = vrec[3 * sd], r1 = vrec[3 * sd + 1], r2 = vrec[3 * sd + 2];
+            auto hin = [&](uint32_t x, uint32_t fl) { return s_h[x & 0x7FFFu] ^ ((x & 0x8000u) ? fl : 0u); };
+            const uint32_t h0 = hin(r0, fl0), h1 = hin(r0 >> 16, fl0), h2 = hin(r1, fl0), h3 = hin(r1 >> 16, fl0);
+            const uint32_t hp = hin(r2, fl1);
+            const uint32_t cell = (r2 >> 16) & 0xFFFu, x = r2 >> 28;
+            // count of +1 among h0..h3 = c0 + 2 c1 + 4 c2, bit-sliced
+            const uint32_t s01 = h0 ^ h1, a01 = h0 & h1, s23 = h2 ^ h3, a23 = h2 & h3;
+            const uint32_t c0 = s01 ^ s23, cy = s01 & s23;
+            const uint32_t c1 = a01 ^ a23 ^ cy, c2 = (a01 & a23) | (cy & (a01 | a23));
+            const uint32_t D0 = ~(c0 | c1 | c2), D1 = c0 & ~(c1 | c2), D2 = c1 & ~c0, D3 = c1 & c0, D4 = c2;
+            const uint32_t* tv = s_tab + kBpVisPlanes;  // [count][J' bit][32]
+            uint32_t lt = 0u, eq = valid ? 0xffffffffu : 0u;
+            const uint32_t tag = kTagBitplane + 8u * (10u + x);
+#pragma unroll 1
+            for (uint32_t j = 0; j < 8u; ++j) {
+                if (!__any_sync(0xffffffffu, eq != 0u)) break;
+                const U4 q = philox(cell, t, w32, tag + j, a.key0, a.key1);
+                const uint32_t u[4] = {q.x, q.y, q.z, q.w};
+#pragma unroll
+                for (int i = 0; i < 4; ++i) {
+                    const uint32_t* tb = tv + 4u * j + i;
+                    auto sel = [&](int c) { return (hp & tb[(2 * c + 1) * 32]) | (~hp & tb[2 * c * 32]); };
+                    const uint32_t T = (D0 & sel(0)) | (D1 & sel(1)) | (D2 & sel(2)) | (D3 & sel(3)) | (D4 & sel(4));
+                    plane_step(u[i], T, lt, eq);
+                }
+            }
+            if (valid) s_v[s] = lt;
+        }
+        __syncthreads();
+        if (measuring && (t + 1u) % static_cast<uint32_t>(a.measure_every) == 0u) {
+            // lane = chain: anti-aligned J and J' filters, +1 spins
+            int anti0 = 0, anti1 = 0, pos = 0;
+            for (int node = warp; node < nh; node += nwarp) {
+                const uint32_t r = hrec[node];
+                const int d = static_cast<int>(((s_v[r & 0xFFFFu] ^ s_v[r >> 16]) >> lane) & 1u);
+                if (node % kBpNodes < 8) anti0 += d;
+                else anti1 += d;
+            }
+            for (int s = warp; s < N; s += nwarp) pos += static_cast<int>((s_v[s] >> lane) & 1u);
+            atomicAdd(&s_cnt[lane], anti0);
+            atomicAdd(&s_cnt[32 + lane], anti1);
+            atomicAdd(&s_cnt[64 + lane], pos);
+            __syncthreads();
+            if (warp == 0) post_sweep_warp0(a, s_cnt, s_sob, s_sob, lane, word, t, true, false, meas, s_acc);
+            ++meas;
+            __syncthreads();
+        }
+    }
+    uint32_t* gvo = a.v + static_cast<size_t>(word) * N;
+    for (int x = threadIdx.x; x < N; x += blockDim.x) gvo[x] = s_v[x];
+    if (measuring && warp == 0)
+        for (int x = 0; x < kNSum; ++x) a.sums[static_cast<size_t>(chain) * kNSum + x] = s_acc[x * 32 + lane];
+}
+
+}  // namespace
+
+size_t smem_bytes_bitplane(const Geometry& g, bool with_records) {
+    return sizeof(uint32_t) * (kBpSmemV + static_cast<size_t>(g.N) + bp_hid_words(g) +
+                               (with_records ? bp_rec_words(g) : 0));
+}
+
+cudaError_t launch_sweep_bitplane(const SweepArgs& a, int warps_per_cta, cudaStream_t st) {
+    const int warps = std::max(1, std::min(kBpMaxThreads / 32, warps_per_cta));
+    const bool staged = smem_bytes_bitplane(a.g, true) <= 227 * 1024;
+    const size_t smem = smem_bytes_bitplane(a.g, staged);
+    cudaError_t e = staged ? cudaFuncSetAttribute(k_sweep_bitplane<true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                                  static_cast<int>(smem))
+                           : cudaFuncSetAttribute(k_sweep_bitplane<false>,
+                                                  cudaFuncAttributeMaxDynamicSharedMemorySize, static_cast<int>(smem));
+    if (e != cudaSuccess) return e;
+    if (staged)
+        k_sweep_bitplane<true><<<a.n_words, 32 * warps, smem, st>>>(a);
+    else
+        k_sweep_bitplane<false><<<a.n_words, 32 * warps, smem, st>>>(a);
+    return cudaGetLastError();
+}
+
+}  // namespace crbm

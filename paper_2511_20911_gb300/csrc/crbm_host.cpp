@@ -326,11 +326,25 @@ int crbm_create(crbm_ctx** out, const crbm_params* p) {
         return fail(nullptr, CRBM_EINVAL, "unknown precision");
     }
     g.paper = p->precision == CRBM_PRECISION_PAPER ? 1 : 0;
+    if (p->rng != CRBM_RNG_LANE && p->rng != CRBM_RNG_BITPLANE) {
+        delete ctx;
+        return fail(nullptr, CRBM_EINVAL, "unknown rng");
+    }
+    g.bitplane = p->rng == CRBM_RNG_BITPLANE ? 1 : 0;
+    if (g.bitplane && (!g.canonical || g.paper || p->layout == CRBM_LAYOUT_STREAM || p->swap_every > 0 ||
+                       p->sq_every > 0)) {
+        delete ctx;
+        return fail(nullptr, CRBM_EUNSUPPORTED,
+                    "bit-plane uniforms need the ten SS filters on an even periodic lattice in the SMEM layout, "
+                    "exact precision, no replica exchange and no correlations");
+    }
     // AUTO: shared memory when the lattice, its hidden words and the tables fit
     // in one CTA's 227 KB, else the streamed layout (SS filters, even periodic L)
     ctx->layout = p->layout;
     if (ctx->layout == CRBM_LAYOUT_AUTO) {
-        const size_t need = g.canonical ? smem_bytes_canon(g) : smem_bytes_generic(g);
+        const size_t need = g.bitplane    ? smem_bytes_bitplane(g, false)
+                            : g.canonical ? smem_bytes_canon(g)
+                                          : smem_bytes_generic(g);
         ctx->layout = (p->L <= CRBM_SMEM_MAX_L && g.Lc <= CRBM_SMEM_MAX_L && need <= 227 * 1024)
                           ? CRBM_LAYOUT_SMEM
                           : CRBM_LAYOUT_STREAM;
@@ -357,8 +371,13 @@ int crbm_create(crbm_ctx** out, const crbm_params* p) {
         return fail(nullptr, CRBM_EUNSUPPORTED, "spin correlations are accumulated in the SMEM layout only");
     }
     g.vil = ctx->layout == CRBM_LAYOUT_STREAM ? 1 : 0;
+    if (g.bitplane && ctx->layout != CRBM_LAYOUT_SMEM) {
+        delete ctx;
+        return fail(nullptr, CRBM_EUNSUPPORTED, "bit-plane uniforms run in the SMEM layout");
+    }
     if (ctx->layout == CRBM_LAYOUT_SMEM &&
-        (g.canonical ? smem_bytes_canon(g) : smem_bytes_generic(g)) > 227 * 1024) {
+        (g.bitplane ? smem_bytes_bitplane(g, false) : g.canonical ? smem_bytes_canon(g) : smem_bytes_generic(g)) >
+            227 * 1024) {
         delete ctx;
         return fail(nullptr, CRBM_EUNSUPPORTED,
                     "lattice, hidden layer and threshold columns exceed 227 KB of shared memory");
@@ -518,7 +537,26 @@ int crbm_create(crbm_ctx** out, const crbm_params* p) {
     // visible tables indexed by the five raw filter bits of each spin
     // position; the coefficient signs and the field sums are folded in.
     std::vector<uint32_t> ctab;
-    if (g.canonical) {
+    if (g.bitplane) {  // threshold planes of each word (layout at kBpTab)
+        ctab.assign(static_cast<size_t>(nw) * kCanonTab, 0u);
+        for (int w = 0; w < nw; ++w)
+            for (int l = 0; l < 32; ++l) {
+                const int c = w * 32 + l;
+                const int pp = c < p->n_chains ? ctx->chain_param[c] : ctx->chain_param[0];
+                const uint32_t* T = &ctx->tables[static_cast<size_t>(pp) * g.nTab];
+                uint32_t* out = &ctab[static_cast<size_t>(w) * kCanonTab];
+                auto put = [&](int row, uint32_t t) {
+                    for (int b = 0; b < 32; ++b) out[row * 32 + b] |= ((t >> (31 - b)) & 1u) << l;
+                };
+                for (int cls = 0; cls < 2; ++cls)
+                    for (int mi = 0; mi < 3; ++mi) put(kBpHidPlanes / 32 + cls * 3 + mi, T[cls * 5 + 2 * mi]);
+                for (int cnt = 0; cnt <= 4; ++cnt)
+                    for (int j = 0; j < 2; ++j)
+                        put(kBpVisPlanes / 32 + cnt * 2 + j, T[10 + (2 * cnt) * (2 * g.DJp + 1) + 2 * j]);
+                for (int cls = 0; cls < 2; ++cls)
+                    if (sgn[2 * pp + cls] < 0) out[kBpFlip + cls] |= 1u << l;
+            }
+    } else if (g.canonical) {
         ctab.assign(static_cast<size_t>(nw) * kCanonTab, 0u);
         for (int w = 0; w < nw; ++w)
             for (int l = 0; l < 32; ++l) {
@@ -547,7 +585,38 @@ int crbm_create(crbm_ctx** out, const crbm_params* p) {
     }
     // Per-cell records of the canonical SMEM sweep (layout in crbm_internal.h).
     std::vector<uint32_t> crec;
-    if (g.canonical && ctx->layout == CRBM_LAYOUT_SMEM) {
+    if (g.bitplane) {
+        // hidden node cell*10 + k: its endpoint sites (s1 | s2 << 16); then per
+        // spin: its four J incidences and its J' incidence (hidden node | 0x8000
+        // when the spin is the second endpoint), its cell and window offset
+        // ([0] = J0 | J1 << 16, [1] = J2 | J3 << 16, [2] = J' | cell << 16 | x << 28)
+        const size_t nh = static_cast<size_t>(g.n_cells) * 10;
+        crec.assign((nh + 3 * static_cast<size_t>(g.N) + 3) & ~static_cast<size_t>(3), 0u);
+        std::vector<std::vector<uint32_t>> inc(2 * static_cast<size_t>(g.N));
+        for (int c = 0; c < g.n_cells; ++c)
+            for (int k = 0; k < 10; ++k) {
+                const int i = c / g.Wc, j = c % g.Wc;
+                const int s1 = site_index(g, i, j, g.r1[k], g.c1[k]), s2 = site_index(g, i, j, g.r2[k], g.c2[k]);
+                crec[static_cast<size_t>(c) * 10 + k] = static_cast<uint32_t>(s1) | (static_cast<uint32_t>(s2) << 16);
+                inc[static_cast<size_t>(g.cls[k]) * g.N + s1].push_back(static_cast<uint32_t>(c * 10 + k));
+                inc[static_cast<size_t>(g.cls[k]) * g.N + s2].push_back(static_cast<uint32_t>(c * 10 + k) | 0x8000u);
+            }
+        for (int s = 0; s < g.N; ++s) {
+            const std::vector<uint32_t>& a = inc[s];
+            const std::vector<uint32_t>& b = inc[static_cast<size_t>(g.N) + s];
+            if (a.size() != 4 || b.size() != 1) {
+                delete ctx;
+                return fail(nullptr, CRBM_EINVAL, "internal: bit-plane records need 4 J and 1 J' incidence per spin");
+            }
+            const int R = s / g.Lc, C = s % g.Lc;
+            const uint32_t cell = static_cast<uint32_t>((R >> 1) * g.Wc + (C >> 1));
+            const uint32_t x = static_cast<uint32_t>(2 * (R & 1) + (C & 1));
+            uint32_t* o = &crec[nh + 3 * static_cast<size_t>(s)];
+            o[0] = a[0] | (a[1] << 16);
+            o[1] = a[2] | (a[3] << 16);
+            o[2] = b[0] | (cell << 16) | (x << 28);
+        }
+    } else if (g.canonical && ctx->layout == CRBM_LAYOUT_SMEM) {
         const int L = g.L, W = g.W, Lc = g.Lc, Wc = g.Wc;
         const uint32_t key0 = static_cast<uint32_t>(ctx->seed), key1 = static_cast<uint32_t>(ctx->seed >> 32);
         const uint32_t rk2 = key0 + 0x9E3779B9u, rk4 = key0 + 2u * 0x9E3779B9u;  // round keys 1, 2 (word 0)
@@ -745,9 +814,9 @@ int crbm_sweep(crbm_ctx* ctx, int64_t n_sweeps) {
             // enough that the last round leaves few SMs idle, long enough that
             // reloading a word's tables and state stays cheap
             const int chunk = std::max(8, (a.n_sweeps + CRBM_CHUNKS_PER_WORD - 1) / CRBM_CHUNKS_PER_WORD);
-            e = ctx->g.canonical
-                    ? launch_sweep_canon_persistent(a, ctx->warps, chunk, ctx->d.sched, ctx->stream)
-                    : launch_sweep_generic(a, ctx->warps, ctx->stream);
+            e = ctx->g.bitplane    ? launch_sweep_bitplane(a, ctx->warps, ctx->stream)
+                : ctx->g.canonical ? launch_sweep_canon_persistent(a, ctx->warps, chunk, ctx->d.sched, ctx->stream)
+                                   : launch_sweep_generic(a, ctx->warps, ctx->stream);
             ++ctx->launches;
         }
         if (e != cudaSuccess) return cuda_fail(ctx, e, "sweep launch");
@@ -946,7 +1015,7 @@ int crbm_save(crbm_ctx* ctx, void* buf, size_t* n) {
                        static_cast<int64_t>(ctx->seed), ctx->sweeps, ctx->meas, ctx->sq_meas,
                        ctx->series_len, ctx->sq_every, ctx->measure_every, ctx->g.nb,
                        ctx->g.periodic | (ctx->g.pc << 1) | (static_cast<int64_t>(ctx->g.Lc) << 2), ctx->swap_every,
-                       ctx->g.paper};
+                       ctx->g.paper | (ctx->g.bitplane << 1)};
     char* p = static_cast<char*>(buf);
     std::memcpy(p, hdr, sizeof(hdr));
     cudaError_t e = cudaMemcpyAsync(p + 128, ctx->d.v, b_v, cudaMemcpyDeviceToHost, ctx->stream);
@@ -976,7 +1045,7 @@ int crbm_load(crbm_ctx* ctx, const void* buf, size_t n) {
         hdr[12] != ctx->g.nb ||
         hdr[13] != (ctx->g.periodic | (ctx->g.pc << 1) | (static_cast<int64_t>(ctx->g.Lc) << 2)) ||
         hdr[14] != ctx->swap_every ||
-        hdr[15] != ctx->g.paper)
+        hdr[15] != (ctx->g.paper | (ctx->g.bitplane << 1)))
         return fail(ctx, CRBM_EINVAL, "checkpoint does not match this context");
     const size_t npad = static_cast<size_t>(ctx->n_words) * 32, N = ctx->g.N;
     const size_t b_v = ctx->n_words * N * 4, b_s = npad * kNSum * 8,

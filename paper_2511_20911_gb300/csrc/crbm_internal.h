@@ -27,6 +27,13 @@ constexpr int kWordBits = 32;  // chains per packed word (one bit per chain)
 constexpr uint32_t kTagVis = 4u;   // Philox tag of the visible half-step
 constexpr uint32_t kTagInit = 5u;  // Philox tag of the initial spins
 constexpr uint32_t kTagSwap = 6u;  // Philox tag of replica-exchange decisions
+// Bit-plane uniforms (CRBM_RNG_BITPLANE): call j of node n of a cell has tag
+// kTagBitplane + 8 n + j and counter word 2 = the 32-chain word (not a chain).
+constexpr uint32_t kTagBitplane = 256u;
+// Per word, the bit-plane sweep's threshold planes and sign masks:
+// [2 classes][3 m = -2, 0, 2][32 planes] hidden, [5 counts][2 J' bits][32
+// planes] visible, [2] chains whose class coupling has a negative sign.
+constexpr int kBpHidPlanes = 0, kBpVisPlanes = 192, kBpFlip = 512, kBpTab = 516;
 
 // Canonical fast-path tables per packed word: hidden [2 cls][4 idx][32 lanes]
 // then visible [4 spin positions][32 idx][32 lanes] (see crbm_canon.cu).
@@ -82,6 +89,7 @@ struct Geometry {
     int n_real_bonds[2];  // bonds with both endpoints real, per class
     int vil;       // spin storage: 0 = [word][site], 1 = 64-chain words [group][site][2]
     int paper;     // CRBM_PRECISION_PAPER: 16-bit thresholds and uniforms, two per Philox word
+    int bitplane;  // CRBM_RNG_BITPLANE: uniforms from bit-plane words shared by the 32 chains of a word
     int8_t r1[kMaxBonds], c1[kMaxBonds], r2[kMaxBonds], c2[kMaxBonds];
     uint8_t cls[kMaxBonds];
 };
@@ -243,6 +251,11 @@ cudaError_t launch_sweep_generic(const SweepArgs& a, int warps_per_cta, cudaStre
 cudaError_t launch_sweep_canon_persistent(const SweepArgs& a, int warps_per_cta, int chunk, int* sched,
                                           cudaStream_t st);
 cudaError_t launch_sweep_stream(const SweepArgs& a, cudaStream_t st, int64_t* launches);
+// Bit-plane sweep (crbm_bitplane.cu): one CTA per word, its lattice, hidden
+// words and threshold planes in shared memory, the node records there too
+// when they fit.  Per-CTA dynamic shared memory with and without the records.
+size_t smem_bytes_bitplane(const Geometry& g, bool with_records);
+cudaError_t launch_sweep_bitplane(const SweepArgs& a, int warps_per_cta, cudaStream_t st);
 cudaError_t launch_sweep_batch(const BatchArgs& b, int n_tasks, int cluster, int threads, size_t smem,
                                cudaStream_t st);
 // Clusters of `cluster` batch CTAs that can be resident at once (0: none).

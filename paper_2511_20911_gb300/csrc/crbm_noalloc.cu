@@ -41,8 +41,9 @@ extern "C" int crbm_sweep_stream_noalloc(const crbm_params* p, uint32_t* v, int6
                             "needs an even L in 4..4096, periodic, and the ten SS filters (bonds = NULL)");
     if ((p->L_cols != 0 && p->L_cols != p->L) ||
         (p->periodic_cols != CRBM_BC_AS_ROWS && p->periodic_cols != CRBM_BC_PERIODIC) || p->h_odd ||
-        (p->precision != CRBM_PRECISION_EXACT && p->precision != CRBM_PRECISION_PAPER))
-        return noalloc_fail(CRBM_EINVAL, "needs a square periodic lattice, one field and a known precision");
+        (p->precision != CRBM_PRECISION_EXACT && p->precision != CRBM_PRECISION_PAPER) || p->rng != CRBM_RNG_LANE)
+        return noalloc_fail(CRBM_EINVAL,
+                            "needs a square periodic lattice, one field, a known precision and lane uniforms");
     if (p->n_params < 1 || !p->J || !p->Jp || !p->h || !p->beta || p->n_chains < 1)
         return noalloc_fail(CRBM_EINVAL, "need n_params >= 1, the four parameter arrays and n_chains >= 1");
     if (sweep0 < 0 || n_sweeps < 0 || n_sweeps > 2147483647LL || sweep0 + n_sweeps > 4294967295LL)

@@ -661,10 +661,10 @@ int ensure_chain_params(crbm_ctx* ctx) {
 int check_ctx(const crbm_ctx* ctx) {
     if (!ctx) return prop_fail(CRBM_EINVAL, "null context");
     if (!ctx->g.canonical || ctx->g.Lc != ctx->g.L || ctx->layout != CRBM_LAYOUT_SMEM || ctx->swap_every > 0 ||
-        ctx->g.paper)
+        ctx->g.paper || ctx->g.bitplane)
         return prop_fail(CRBM_EUNSUPPORTED,
                          "block proposals need the ten SS filters on an even periodic square lattice, the "
-                         "SMEM layout, exact precision and no replica exchange");
+                         "SMEM layout, exact precision, lane uniforms and no replica exchange");
     return CRBM_OK;
 }
 

@@ -39,7 +39,7 @@ std::string shape_key(const crbm_ctx* ctx) {
     std::ostringstream k;
     k << prop.name << "|sm" << prop.multiProcessorCount << "|L" << ctx->g.L << "|p" << ctx->g.periodic << "|c"
       << ctx->g.canonical << "|nb" << ctx->g.nb << "|w" << ctx->n_words << "|x" << (ctx->swap_every > 0)
-      << "|q" << ctx->g.paper << "|Lc" << ctx->g.Lc << "|pc" << ctx->g.pc << "|v" << ctx->g.n_vis_tab;
+      << "|q" << ctx->g.paper << "|bp" << ctx->g.bitplane << "|Lc" << ctx->g.Lc << "|pc" << ctx->g.pc << "|v" << ctx->g.n_vis_tab;
     std::string s = k.str();
     std::replace(s.begin(), s.end(), ' ', '_');
     return s;
@@ -50,6 +50,7 @@ int smem_ok(const crbm_ctx* ctx) {
 }
 
 cudaError_t launch_one(const SweepArgs& a, const crbm_ctx* ctx, int warps) {
+    if (ctx->g.bitplane) return launch_sweep_bitplane(a, warps, ctx->stream);
     if (!ctx->g.canonical) return launch_sweep_generic(a, warps, ctx->stream);
     const int chunk = std::max(8, (a.n_sweeps + CRBM_CHUNKS_PER_WORD - 1) / CRBM_CHUNKS_PER_WORD);  // as crbm_sweep does
     return launch_sweep_canon_persistent(a, warps, chunk, ctx->d.sched, ctx->stream);
@@ -99,7 +100,8 @@ int crbm_autotune(crbm_ctx* ctx, int64_t probe_sweeps, int32_t* best_warps) {
     for (int w : cand) {
         if (e != cudaSuccess) break;
         // the generic kernel is built for CTAs of at most 512 threads
-        if (w > std::max(1, ctx->g.n_cells) || w > (ctx->g.canonical ? kMaxSweepWarps : 16)) continue;
+        if (w > std::max(1, ctx->g.n_cells) || w > (ctx->g.canonical && !ctx->g.bitplane ? kMaxSweepWarps : 16))
+            continue;
         // scratch copies: the tuning sweeps never touch the context's chains
         e = cudaMemcpyAsync(v2, ctx->d.v, ctx->n_words * N * 4, cudaMemcpyDeviceToDevice, ctx->stream);
         if (e == cudaSuccess) e = cudaMemsetAsync(s2, 0, npad * kNSum * 8, ctx->stream);
@@ -201,7 +203,8 @@ int crbm_batch_create(crbm_batch** out, crbm_ctx* const* ctxs, int32_t n_ctx) {
     int warps = 1;
     for (int c = 0; c < n_ctx; ++c) {
         crbm_ctx* x = ctxs[c];
-        if (!x || x->layout != CRBM_LAYOUT_SMEM || !smem_ok(x) || x->g.paper || x->stream != ctxs[0]->stream ||
+        if (!x || x->layout != CRBM_LAYOUT_SMEM || !smem_ok(x) || x->g.paper || x->g.bitplane ||
+            x->stream != ctxs[0]->stream ||
             x->device != ctxs[0]->device || std::count(ctxs, ctxs + c, x)) {
             g_batch_create_error =
                 "batch members must be distinct SMEM-layout, exact-precision contexts on one device and stream";

@@ -1,0 +1,125 @@
+"""Bit-plane uniforms (CRBM_RNG_BITPLANE) on the GPU against the oracle's
+ORC_RNG_BITPLANE mode, bit for bit: spins, sums and series on square lattices
+and rectangles (ragged 32-chain words, signs of J and J' both ways, staged and
+global node records, several CTA shapes), the full L=18 grid on sampled chains
+in the launch the benchmark times, and the contexts that refuse the mode."""
+import numpy as np
+import pytest
+
+import paper_2511_20911_gb300 as crbm
+from paper_2511_20911_gb300 import workloads
+
+pytestmark = pytest.mark.gpu
+BP = crbm.CRBM_RNG_BITPLANE
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _gpu():
+    torch = pytest.importorskip("torch")
+    if not torch.cuda.is_available():
+        pytest.skip("no GPU")
+    crbm.load_library()
+
+
+def run_pair(orc, shape, params, n, cp, seed, splits, measure_every=2, series_len=0, check_ids=None):
+    L, Lc = shape if isinstance(shape, tuple) else (shape, shape)
+    s = crbm.Sampler(L, params, n, chain_param=cp, seed=seed, measure_every=measure_every,
+                     series_len=series_len, L_cols=Lc if Lc != L else 0, rng=BP)
+    assert s.layout == crbm.CRBM_LAYOUT_SMEM
+    ids = np.arange(n, dtype=np.uint32) if check_ids is None else np.asarray(check_ids, np.uint32)
+    cpi = np.asarray(cp, np.int32)[ids]
+    spins = orc.init_spins((L, Lc), ids, seed)
+    sums, oser, t = None, None, 0
+    for k in splits:
+        s.sweep(k)
+        sums, ser, _ = orc.run((L, Lc), params, cpi, spins, seed, t, k, measure_every, chain_ids=ids, sums=sums,
+                               series_cap=series_len, rng=orc.RNG_BITPLANE)
+        if ser is not None:
+            oser = ser if oser is None else np.where(ser != 0, ser, oser)
+        t += k
+        assert np.array_equal(s.get_spins()[ids], spins), f"spins after {t} sweeps"
+    if measure_every:
+        assert np.array_equal(s.observables()[ids], sums)
+    if series_len:
+        assert np.array_equal(s.series()[:, ids, :].transpose(1, 0, 2), oser)
+    return s
+
+
+@pytest.mark.parametrize("L,n", [(4, 40), (6, 64), (10, 33), (18, 70), (20, 96)])
+def test_bitplane_bitexact(orc, L, n):
+    rng = np.random.default_rng(L * 17 + n)
+    params = workloads.random_params(rng, 4)
+    run_pair(orc, L, params, n, rng.integers(0, 4, n).astype(np.int32), 3 + L, splits=[3, 14],
+             series_len=10)
+
+
+@pytest.mark.parametrize("shape", [(18, 12), (8, 30)])
+def test_bitplane_rectangles_bitexact(orc, shape):
+    rng = np.random.default_rng(shape[0] * 41 + shape[1])
+    params = workloads.random_params(rng, 3)
+    n = 50
+    run_pair(orc, shape, params, n, rng.integers(0, 3, n).astype(np.int32), 8, splits=[4, 9])
+
+
+@pytest.mark.parametrize("warps", ["1", "5", "16"])
+def test_bitplane_cta_shapes(orc, warps, monkeypatch):
+    """One warp (every node loop runs many rounds), five (ragged last round),
+    sixteen (most warps idle in the visible half-step at L=12)."""
+    monkeypatch.setenv("CRBM_WARPS", warps)
+    rng = np.random.default_rng(int(warps))
+    params = workloads.random_params(rng, 2)
+    run_pair(orc, 12, params, 64, (np.arange(64) % 2).astype(np.int32), 21, splits=[5, 6])
+
+
+def test_bitplane_records_from_global_memory(orc):
+    """L=96: the node records (about 200 KB) do not fit beside the lattice in
+    shared memory and are read through L1."""
+    rng = np.random.default_rng(96)
+    params = workloads.random_params(rng, 2)
+    run_pair(orc, 96, params, 40, (np.arange(40) % 2).astype(np.int32), 4, splits=[2, 2], measure_every=1)
+
+
+@pytest.mark.slow
+def test_bitplane_full_grid_sampled_chains(orc):
+    """The L=18 grid at full size (12288 chains over 768 points) as the
+    benchmark's bit-plane line runs it: 64 chains spread over every word."""
+    w = workloads.grid_workload()
+    ids = np.linspace(0, w["n_chains"] - 1, 64).astype(np.uint32)
+    run_pair(orc, 18, w["params"], w["n_chains"], w["chain_param"], w["seed"], splits=[10, 20],
+             measure_every=10, check_ids=ids)
+
+
+def test_bitplane_differs_from_lane_uniforms():
+    params = dict(J=[1.0], Jp=[1.5], h=[0.5], beta=[0.8])
+    a = crbm.Sampler(12, params, 64, seed=3)
+    b = crbm.Sampler(12, params, 64, seed=3, rng=BP)
+    assert np.array_equal(a.get_spins(), b.get_spins())   # same initial spins
+    a.sweep(3)
+    b.sweep(3)
+    assert not np.array_equal(a.get_spins(), b.get_spins())
+    with pytest.raises(crbm.CrbmError) as e:                # a checkpoint keeps its uniform source
+        a.load(b.save())
+    assert e.value.code == crbm.CRBM_EINVAL
+
+
+def test_bitplane_where_unsupported():
+    ok = dict(J=[1.0], Jp=[1.0], h=[0.5], beta=[2.0])
+    for kw in (dict(L=9), dict(L=10, periodic=False), dict(L=20, layout=crbm.CRBM_LAYOUT_STREAM),
+               dict(L=10, precision=crbm.CRBM_PRECISION_PAPER), dict(L=10, sq_every=2)):
+        with pytest.raises(crbm.CrbmError) as e:
+            crbm.Sampler(params=ok, n_chains=32, rng=BP, **kw)
+        assert e.value.code == crbm.CRBM_EUNSUPPORTED, kw
+    ladder = dict(J=[1.0] * 32, Jp=[1.0] * 32, h=[0.5] * 32, beta=list(0.5 + 0.1 * np.arange(32)))
+    with pytest.raises(crbm.CrbmError) as e:
+        crbm.Sampler(8, ladder, 32, chain_param=np.arange(32), swap_every=2, rng=BP)
+    assert e.value.code == crbm.CRBM_EUNSUPPORTED
+    with pytest.raises(crbm.CrbmError) as e:
+        crbm.Sampler(8, ok, 32, rng=7)
+    assert e.value.code == crbm.CRBM_EINVAL
+    a = crbm.Sampler(8, ok, 32, rng=BP)
+    with pytest.raises(crbm.CrbmError) as e:
+        crbm.Batch([a, crbm.Sampler(8, ok, 32)])
+    assert e.value.code == crbm.CRBM_EINVAL
+    with pytest.raises(crbm.CrbmError) as e:
+        crbm.Proposal(seed=1).passes(a, 1)
+    assert e.value.code == crbm.CRBM_EUNSUPPORTED

@@ -99,7 +99,7 @@ def test_noalloc_rejects_oversize_and_bad_arguments(torch_cuda):
     assert lib.crbm_sweep_stream_noalloc(ctypes.byref(p), ptr, -1, 1) == crbm.CRBM_EINVAL
     assert lib.crbm_sweep_stream_noalloc(ctypes.byref(p), None, 0, 1) == crbm.CRBM_EINVAL
     for field, bad in (("precision", 7), ("L_cols", 12), ("periodic_cols", crbm.CRBM_BC_OPEN),
-                       ("periodic_cols", 5)):
+                       ("periodic_cols", 5), ("rng", crbm.CRBM_RNG_BITPLANE)):
         old = getattr(p, field)
         setattr(p, field, bad)
         assert lib.crbm_sweep_stream_noalloc(ctypes.byref(p), ptr, 0, 1) == crbm.CRBM_EINVAL, field

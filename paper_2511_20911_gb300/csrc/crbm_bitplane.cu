@@ -1,6 +1,6 @@
 // Bit-plane sweep (CRBM_RNG_BITPLANE), ten SS filters on an even periodic
-// lattice, SMEM layout.  A CTA holds one packed word (32 chains) and works
-// word-parallel: a thread takes one node (hidden unit or spin) for all 32
+// lattice, SMEM layout.  A persistent CTA claims one packed word (32 chains)
+// at a time, for a chunk of sweeps, and works on it word-parallel: a thread takes one node (hidden unit or spin) for all 32
 // chains at once, with the chains in the bits of every 32-bit value.
 //
 // A node's 32 uniforms are the bit-transpose of plane words drawn from
@@ -29,7 +29,7 @@ namespace {
 using namespace dev;
 
 constexpr int kBpNodes = 10;   // hidden filters per cell
-constexpr int kBpMaxThreads = 512;
+constexpr int kBpMaxThreads = CRBM_SWEEP_MAX_THREADS;  // 64 registers a thread
 
 // Records of the sweep: [n_cells * 10] hidden endpoint pairs, [N][3] spin
 // incidences (layout in crbm_host.cpp), rounded up to whole uint4.
@@ -53,11 +53,13 @@ __device__ __forceinline__ void plane_step(uint32_t U, uint32_t T, uint32_t& lt,
     eq &= ~(T ^ U);
 }
 
+// The sweeps of one claimed word: its planes, spins and sums in, n sweeps
+// from global sweep t0 (measurement index meas0), spins and sums out.
 template <bool kSmemRec>
-__global__ void __launch_bounds__(kBpMaxThreads) k_sweep_bitplane(const SweepArgs a) {
+__device__ __forceinline__ void sweep_bitplane_body(const SweepArgs& a, const uint32_t* hrec, const uint32_t* vrec,
+                                                    int word, uint32_t t0, int n_sweeps, int64_t meas) {
     extern __shared__ __align__(16) uint32_t smem[];
     const Geometry& g = a.g;
-    const int word = blockIdx.x;
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nwarp = blockDim.x >> 5;
     const int N = g.N, nh = g.n_cells * kBpNodes;
     int64_t* s_acc = reinterpret_cast<int64_t*>(smem);          // [kNSum][32] running sums
@@ -66,16 +68,6 @@ __global__ void __launch_bounds__(kBpMaxThreads) k_sweep_bitplane(const SweepArg
     int* s_sob = s_cnt + 96;                                     // [32] identity permutation
     uint32_t* s_v = smem + kBpSmemV;                             // [N] spin words
     uint32_t* s_h = s_v + N;                                     // [n_cells * 10] hidden words
-    const uint32_t* rec = reinterpret_cast<const uint32_t*>(a.crec);
-    if (kSmemRec) {
-        uint32_t* s_rec = s_h + bp_hid_words(g);  // N is a multiple of 4 (even sides)
-        const uint4* src = a.crec;
-        for (int x = threadIdx.x; x < static_cast<int>(bp_rec_words(g) / 4); x += blockDim.x)
-            reinterpret_cast<uint4*>(s_rec)[x] = __ldg(src + x);
-        rec = s_rec;
-    }
-    const uint32_t* hrec = rec;       // [n_cells * 10]
-    const uint32_t* vrec = rec + nh;  // [N][3]
     const uint32_t* gt = a.ctab + static_cast<size_t>(word) * kCanonTab;
     for (int x = threadIdx.x; x < kBpTab; x += blockDim.x) s_tab[x] = gt[x];
     const uint32_t* gv = a.v + static_cast<size_t>(word) * N;
@@ -88,11 +80,13 @@ __global__ void __launch_bounds__(kBpMaxThreads) k_sweep_bitplane(const SweepArg
         for (int x = 0; x < kNSum; ++x) s_acc[x * 32 + lane] = __ldcg(a.sums + static_cast<size_t>(chain) * kNSum + x);
     __syncthreads();
     const uint32_t fl0 = s_tab[kBpFlip], fl1 = s_tab[kBpFlip + 1];
-    const uint32_t w32 = static_cast<uint32_t>(word);
-    int64_t meas = a.meas0;
+    // Philox round 0 of the word (counter word 2): shared by every call of the CTA
+    const uint64_t pw = static_cast<uint64_t>(kPhiloxM1) * static_cast<uint32_t>(word);
+    const uint32_t Yw = static_cast<uint32_t>(pw), hiW = static_cast<uint32_t>(pw >> 32) ^ a.rk[0];
 
-    for (int it = 0; it < a.n_sweeps; ++it) {
-        const uint32_t t = a.t0 + static_cast<uint32_t>(it);
+    for (int it = 0; it < n_sweeps; ++it) {
+        const uint32_t t = t0 + static_cast<uint32_t>(it);
+        const Round1Sweep rs = round1_sweep(hiW ^ t, a.rk);  // round 1's sweep-wide product
         // hidden half-step (Eq. 9): thread = hidden node (cell, k)
         for (int base = warp * 32; base < nh; base += nwarp * 32) {
             const int node = base + lane;
@@ -105,17 +99,21 @@ __global__ void __launch_bounds__(kBpMaxThreads) k_sweep_bitplane(const SweepArg
             const uint32_t e1 = s_v[r & 0xFFFFu];
             const uint32_t e2 = s_v[r >> 16] ^ (cls ? fl1 : fl0);
             const uint32_t P = e1 & e2, M = ~(e1 | e2), Z = e1 ^ e2;  // m = 2, -2, 0
-            const uint32_t* tp = s_tab + kBpHidPlanes + cls * 96u;     // [m = -2, 0, 2][32]
+            // m = 0 has the threshold 2^31 on every chain: plane 0 all ones, the rest zero
+            const uint32_t* tp = s_tab + kBpHidPlanes + cls * 96u;  // [m = -2, 0, 2][32]
+            const uint64_t pc = static_cast<uint64_t>(kPhiloxM0) * cell;
+            const Round2Cell r2 = round2_cell(rs.hik ^ static_cast<uint32_t>(pc));
+            const uint32_t c2 = static_cast<uint32_t>(pc >> 32) ^ a.rk[1] ^ (kTagBitplane + 8u * k);
             uint32_t lt = 0u, eq = valid ? 0xffffffffu : 0u;
 #pragma unroll 1
             for (uint32_t j = 0; j < 8u; ++j) {
                 if (!__any_sync(0xffffffffu, eq != 0u)) break;
-                const U4 q = philox(cell, t, w32, kTagBitplane + 8u * k + j, a.key0, a.key1);
+                const U4 q = philox_from_round2(Yw, rs, r2, c2 ^ j, a.rk);
                 const uint32_t* tb = tp + 4u * j;
-                plane_step(q.x, (P & tb[64]) | (M & tb[0]) | (Z & tb[32]), lt, eq);
-                plane_step(q.y, (P & tb[65]) | (M & tb[1]) | (Z & tb[33]), lt, eq);
-                plane_step(q.z, (P & tb[66]) | (M & tb[2]) | (Z & tb[34]), lt, eq);
-                plane_step(q.w, (P & tb[67]) | (M & tb[3]) | (Z & tb[35]), lt, eq);
+                plane_step(q.x, (P & tb[64]) | (M & tb[0]) | (j == 0u ? Z : 0u), lt, eq);
+                plane_step(q.y, (P & tb[65]) | (M & tb[1]), lt, eq);
+                plane_step(q.z, (P & tb[66]) | (M & tb[2]), lt, eq);
+                plane_step(q.w, (P & tb[67]) | (M & tb[3]), lt, eq);
             }
             if (valid) s_h[node] = lt;
         }
@@ -125,23 +123,25 @@ __global__ void __launch_bounds__(kBpMaxThreads) k_sweep_bitplane(const SweepArg
             const int s = base + lane;
             const bool valid = s < N;
             const int sd = valid ? s : 0;
-            const uint32_t r0 = vrec[3 * sd], r1 = vrec[3 * sd + 1], r2 = vrec[3 * sd + 2];
+            const uint32_t r0 = vrec[3 * sd], r1 = vrec[3 * sd + 1], r2w = vrec[3 * sd + 2];
             auto hin = [&](uint32_t x, uint32_t fl) { return s_h[x & 0x7FFFu] ^ ((x & 0x8000u) ? fl : 0u); };
             const uint32_t h0 = hin(r0, fl0), h1 = hin(r0 >> 16, fl0), h2 = hin(r1, fl0), h3 = hin(r1 >> 16, fl0);
-            const uint32_t hp = hin(r2, fl1);
-            const uint32_t cell = (r2 >> 16) & 0xFFFu, x = r2 >> 28;
+            const uint32_t hp = hin(r2w, fl1);
+            const uint32_t cell = (r2w >> 16) & 0xFFFu, x = r2w >> 28;
             // count of +1 among h0..h3 = c0 + 2 c1 + 4 c2, bit-sliced
             const uint32_t s01 = h0 ^ h1, a01 = h0 & h1, s23 = h2 ^ h3, a23 = h2 & h3;
             const uint32_t c0 = s01 ^ s23, cy = s01 & s23;
-            const uint32_t c1 = a01 ^ a23 ^ cy, c2 = (a01 & a23) | (cy & (a01 | a23));
-            const uint32_t D0 = ~(c0 | c1 | c2), D1 = c0 & ~(c1 | c2), D2 = c1 & ~c0, D3 = c1 & c0, D4 = c2;
+            const uint32_t c1 = a01 ^ a23 ^ cy, cc2 = (a01 & a23) | (cy & (a01 | a23));
+            const uint32_t D0 = ~(c0 | c1 | cc2), D1 = c0 & ~(c1 | cc2), D2 = c1 & ~c0, D3 = c1 & c0, D4 = cc2;
             const uint32_t* tv = s_tab + kBpVisPlanes;  // [count][J' bit][32]
+            const uint64_t pc = static_cast<uint64_t>(kPhiloxM0) * cell;
+            const Round2Cell r2 = round2_cell(rs.hik ^ static_cast<uint32_t>(pc));
+            const uint32_t c2 = static_cast<uint32_t>(pc >> 32) ^ a.rk[1] ^ (kTagBitplane + 8u * (10u + x));
             uint32_t lt = 0u, eq = valid ? 0xffffffffu : 0u;
-            const uint32_t tag = kTagBitplane + 8u * (10u + x);
 #pragma unroll 1
             for (uint32_t j = 0; j < 8u; ++j) {
                 if (!__any_sync(0xffffffffu, eq != 0u)) break;
-                const U4 q = philox(cell, t, w32, tag + j, a.key0, a.key1);
+                const U4 q = philox_from_round2(Yw, rs, r2, c2 ^ j, a.rk);
                 const uint32_t u[4] = {q.x, q.y, q.z, q.w};
 #pragma unroll
                 for (int i = 0; i < 4; ++i) {
@@ -179,6 +179,51 @@ __global__ void __launch_bounds__(kBpMaxThreads) k_sweep_bitplane(const SweepArg
         for (int x = 0; x < kNSum; ++x) a.sums[static_cast<size_t>(chain) * kNSum + x] = s_acc[x * 32 + lane];
 }
 
+// Persistent grid over (word, chunk of sweeps) items (claim_word): the node
+// records are staged once per CTA, then each claimed chunk runs the body.
+template <bool kSmemRec>
+__global__ void __launch_bounds__(kBpMaxThreads) k_sweep_bitplane(const SweepArgs a, int chunk, int* state) {
+    extern __shared__ __align__(16) uint32_t smem[];
+    __shared__ int s_word, s_chunk;
+    const Geometry& g = a.g;
+    const int lane = threadIdx.x & 31;
+    const int nh = g.n_cells * kBpNodes;
+    const uint32_t* rec = reinterpret_cast<const uint32_t*>(a.crec);
+    if (kSmemRec) {
+        uint32_t* s_rec = smem + kBpSmemV + g.N + bp_hid_words(g);  // N is a multiple of 4 (even sides)
+        for (int x = threadIdx.x; x < static_cast<int>(bp_rec_words(g) / 4); x += blockDim.x)
+            reinterpret_cast<uint4*>(s_rec)[x] = __ldg(a.crec + x);
+        rec = s_rec;
+    }
+    const int n_chunks = (a.n_sweeps + chunk - 1) / chunk;
+    const int nw = a.n_words;
+    const int K = a.measure_every;
+    const unsigned int start = (blockIdx.x * 97u) % static_cast<unsigned int>(nw);
+    for (;;) {
+        if (threadIdx.x < 32) {
+            int word, c;
+            claim_word(state, nw, n_chunks, start, lane, word, c);
+            if (lane == 0) {
+                s_word = word;
+                s_chunk = c;
+            }
+        }
+        __syncthreads();
+        const int word = s_word, c = s_chunk;
+        if (word < 0) break;
+        const uint32_t t0 = a.t0 + static_cast<uint32_t>(c * chunk);
+        const int n = min(chunk, a.n_sweeps - c * chunk);
+        const int64_t meas0 =
+            K > 0 ? a.meas0 + static_cast<int64_t>(t0 / K) - static_cast<int64_t>(a.t0 / K) : a.meas0;
+        sweep_bitplane_body<kSmemRec>(a, rec, rec + nh, word, t0, n, meas0);
+        __syncthreads();  // every thread's state stores are issued
+        if (threadIdx.x == 0) {
+            __threadfence();
+            st_release(state + word, 2 * (c + 1));
+        }
+    }
+}
+
 }  // namespace
 
 size_t smem_bytes_bitplane(const Geometry& g, bool with_records) {
@@ -186,19 +231,23 @@ size_t smem_bytes_bitplane(const Geometry& g, bool with_records) {
                                (with_records ? bp_rec_words(g) : 0));
 }
 
-cudaError_t launch_sweep_bitplane(const SweepArgs& a, int warps_per_cta, cudaStream_t st) {
+cudaError_t launch_sweep_bitplane(const SweepArgs& a, int warps_per_cta, int chunk, int* sched, cudaStream_t st) {
     const int warps = std::max(1, std::min(kBpMaxThreads / 32, warps_per_cta));
     const bool staged = smem_bytes_bitplane(a.g, true) <= 227 * 1024;
     const size_t smem = smem_bytes_bitplane(a.g, staged);
-    cudaError_t e = staged ? cudaFuncSetAttribute(k_sweep_bitplane<true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                                  static_cast<int>(smem))
-                           : cudaFuncSetAttribute(k_sweep_bitplane<false>,
-                                                  cudaFuncAttributeMaxDynamicSharedMemorySize, static_cast<int>(smem));
+    auto kernel = staged ? k_sweep_bitplane<true> : k_sweep_bitplane<false>;
+    cudaError_t e = cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, static_cast<int>(smem));
+    int per_sm = 0, dev = 0, sms = 0;
+    if (e == cudaSuccess) e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kernel, 32 * warps, smem);
+    if (e == cudaSuccess) e = cudaGetDevice(&dev);
+    if (e == cudaSuccess) e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
     if (e != cudaSuccess) return e;
-    if (staged)
-        k_sweep_bitplane<true><<<a.n_words, 32 * warps, smem, st>>>(a);
-    else
-        k_sweep_bitplane<false><<<a.n_words, 32 * warps, smem, st>>>(a);
+    if (per_sm < 1) return cudaErrorInvalidConfiguration;
+    const int n_items = ((a.n_sweeps + chunk - 1) / chunk) * a.n_words;
+    const int grid = std::min(std::min(n_items, a.n_words), per_sm * sms);
+    e = cudaMemsetAsync(sched, 0, sizeof(int) * (4 + static_cast<size_t>(a.n_words)), st);
+    if (e != cudaSuccess) return e;
+    kernel<<<grid, 32 * warps, smem, st>>>(a, chunk, sched);
     return cudaGetLastError();
 }
 

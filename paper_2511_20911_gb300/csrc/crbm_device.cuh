@@ -142,6 +142,58 @@ __device__ __forceinline__ void st_release(int* p, int v) {
     asm volatile("st.release.gpu.global.s32 [%0], %1;" ::"l"(p), "r"(v) : "memory");
 }
 
+// Persistent scheduling of (word, chunk of sweeps) items: state[w] = 2 (chunks
+// of w done) + (1 while a CTA holds w).  Called by one whole warp: claims,
+// with a compare-and-swap on state, the free word with the fewest chunks done
+// (all states scanned with 16-byte loads; ties go to the first word in the
+// scan order that starts at `start`).  Every lane returns the word (-1 when
+// every unfinished word is held by a running CTA, which claims again after
+// its chunk, so no work is left behind and nothing waits) and its chunk.
+__device__ __forceinline__ void claim_word(int* state, int nw, int n_chunks, unsigned int start, int lane,
+                                           int& word, int& chunk) {
+    const int nq = (nw + 3) / 4;
+    word = -1;
+    chunk = 0;
+    for (int tries = 0; tries < (1 << 20) && word < 0; ++tries) {
+        int best = 0x7fffffff, bk = 0x7fffffff, bw = -1;  // (chunks done, scan rank, word)
+        for (int q = lane; q < nq; q += 32) {
+            const int4 v = __ldcg(reinterpret_cast<const int4*>(state) + q);
+            const int sv[4] = {v.x, v.y, v.z, v.w};
+#pragma unroll
+            for (int j = 0; j < 4; ++j) {
+                const int w = 4 * q + j;
+                const int dw = sv[j] >> 1;
+                const int rank =
+                    static_cast<int>((static_cast<unsigned int>(w) + nw - start) % static_cast<unsigned int>(nw));
+                if (w < nw && (sv[j] & 1) == 0 && dw < n_chunks && (dw < best || (dw == best && rank < bk))) {
+                    best = dw;
+                    bk = rank;
+                    bw = w;
+                }
+            }
+        }
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) {
+            const int ob = __shfl_xor_sync(0xffffffffu, best, o);
+            const int ok = __shfl_xor_sync(0xffffffffu, bk, o);
+            const int ow = __shfl_xor_sync(0xffffffffu, bw, o);
+            if (ob < best || (ob == best && ok < bk)) {
+                best = ob;
+                bk = ok;
+                bw = ow;
+            }
+        }
+        if (bw < 0) break;
+        if (lane == 0 && atomicCAS(state + bw, 2 * best, 2 * best + 1) == 2 * best) {
+            __threadfence();  // acquire: the previous chunk's stores precede its release
+            word = bw;
+            chunk = best;
+        }
+        word = __shfl_sync(0xffffffffu, word, 0);
+        chunk = __shfl_sync(0xffffffffu, chunk, 0);
+    }
+}
+
 __device__ __forceinline__ int warp_sum(int x) {
 #pragma unroll
     for (int o = 16; o > 0; o >>= 1) x += __shfl_xor_sync(0xffffffffu, x, o);

@@ -550,6 +550,10 @@ int crbm_create(crbm_ctx** out, const crbm_params* p) {
                 };
                 for (int cls = 0; cls < 2; ++cls)
                     for (int mi = 0; mi < 3; ++mi) put(kBpHidPlanes / 32 + cls * 3 + mi, T[cls * 5 + 2 * mi]);
+                if (T[2] != 0x80000000u || T[7] != 0x80000000u) {  // the sweep takes m = 0 as exactly 1/2
+                    delete ctx;
+                    return fail(nullptr, CRBM_EINVAL, "internal: bit-plane sweep needs thr(0) = 2^31");
+                }
                 for (int cnt = 0; cnt <= 4; ++cnt)
                     for (int j = 0; j < 2; ++j)
                         put(kBpVisPlanes / 32 + cnt * 2 + j, T[10 + (2 * cnt) * (2 * g.DJp + 1) + 2 * j]);
@@ -814,7 +818,7 @@ int crbm_sweep(crbm_ctx* ctx, int64_t n_sweeps) {
             // enough that the last round leaves few SMs idle, long enough that
             // reloading a word's tables and state stays cheap
             const int chunk = std::max(8, (a.n_sweeps + CRBM_CHUNKS_PER_WORD - 1) / CRBM_CHUNKS_PER_WORD);
-            e = ctx->g.bitplane    ? launch_sweep_bitplane(a, ctx->warps, ctx->stream)
+            e = ctx->g.bitplane    ? launch_sweep_bitplane(a, ctx->warps, chunk, ctx->d.sched, ctx->stream)
                 : ctx->g.canonical ? launch_sweep_canon_persistent(a, ctx->warps, chunk, ctx->d.sched, ctx->stream)
                                    : launch_sweep_generic(a, ctx->warps, ctx->stream);
             ++ctx->launches;

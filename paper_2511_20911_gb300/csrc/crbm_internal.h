@@ -251,11 +251,13 @@ cudaError_t launch_sweep_generic(const SweepArgs& a, int warps_per_cta, cudaStre
 cudaError_t launch_sweep_canon_persistent(const SweepArgs& a, int warps_per_cta, int chunk, int* sched,
                                           cudaStream_t st);
 cudaError_t launch_sweep_stream(const SweepArgs& a, cudaStream_t st, int64_t* launches);
-// Bit-plane sweep (crbm_bitplane.cu): one CTA per word, its lattice, hidden
-// words and threshold planes in shared memory, the node records there too
-// when they fit.  Per-CTA dynamic shared memory with and without the records.
+// Bit-plane sweep (crbm_bitplane.cu): a persistent grid that claims (word,
+// chunk) items as the canonical sweep does (sched: 4 + n_words ints), each
+// word's lattice, hidden words and threshold planes in shared memory, the
+// node records there too when they fit.  Per-CTA dynamic shared memory with
+// and without the records.
 size_t smem_bytes_bitplane(const Geometry& g, bool with_records);
-cudaError_t launch_sweep_bitplane(const SweepArgs& a, int warps_per_cta, cudaStream_t st);
+cudaError_t launch_sweep_bitplane(const SweepArgs& a, int warps_per_cta, int chunk, int* sched, cudaStream_t st);
 cudaError_t launch_sweep_batch(const BatchArgs& b, int n_tasks, int cluster, int threads, size_t smem,
                                cudaStream_t st);
 // Clusters of `cluster` batch CTAs that can be resident at once (0: none).

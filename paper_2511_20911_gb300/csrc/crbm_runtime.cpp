@@ -50,9 +50,9 @@ int smem_ok(const crbm_ctx* ctx) {
 }
 
 cudaError_t launch_one(const SweepArgs& a, const crbm_ctx* ctx, int warps) {
-    if (ctx->g.bitplane) return launch_sweep_bitplane(a, warps, ctx->stream);
     if (!ctx->g.canonical) return launch_sweep_generic(a, warps, ctx->stream);
     const int chunk = std::max(8, (a.n_sweeps + CRBM_CHUNKS_PER_WORD - 1) / CRBM_CHUNKS_PER_WORD);  // as crbm_sweep does
+    if (ctx->g.bitplane) return launch_sweep_bitplane(a, warps, chunk, ctx->d.sched, ctx->stream);
     return launch_sweep_canon_persistent(a, warps, chunk, ctx->d.sched, ctx->stream);
 }
 
@@ -100,8 +100,7 @@ int crbm_autotune(crbm_ctx* ctx, int64_t probe_sweeps, int32_t* best_warps) {
     for (int w : cand) {
         if (e != cudaSuccess) break;
         // the generic kernel is built for CTAs of at most 512 threads
-        if (w > std::max(1, ctx->g.n_cells) || w > (ctx->g.canonical && !ctx->g.bitplane ? kMaxSweepWarps : 16))
-            continue;
+        if (w > std::max(1, ctx->g.n_cells) || w > (ctx->g.canonical ? kMaxSweepWarps : 16)) continue;
         // scratch copies: the tuning sweeps never touch the context's chains
         e = cudaMemcpyAsync(v2, ctx->d.v, ctx->n_words * N * 4, cudaMemcpyDeviceToDevice, ctx->stream);
         if (e == cudaSuccess) e = cudaMemsetAsync(s2, 0, npad * kNSum * 8, ctx->stream);

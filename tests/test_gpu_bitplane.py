@@ -61,10 +61,11 @@ def test_bitplane_rectangles_bitexact(orc, shape):
     run_pair(orc, shape, params, n, rng.integers(0, 3, n).astype(np.int32), 8, splits=[4, 9])
 
 
-@pytest.mark.parametrize("warps", ["1", "5", "16"])
+@pytest.mark.parametrize("warps", ["1", "5", "16", "32"])
 def test_bitplane_cta_shapes(orc, warps, monkeypatch):
     """One warp (every node loop runs many rounds), five (ragged last round),
-    sixteen (most warps idle in the visible half-step at L=12)."""
+    sixteen and thirty-two (most warps idle in the visible half-step at L=12,
+    one CTA per SM)."""
     monkeypatch.setenv("CRBM_WARPS", warps)
     rng = np.random.default_rng(int(warps))
     params = workloads.random_params(rng, 2)

@@ -74,7 +74,7 @@ def parse():
     ap.add_argument("--steps", type=int, default=10)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
-    ap.add_argument("--workload", default="grid", choices=["grid", "stream", "batch", "proposal", "tts"])
+    ap.add_argument("--workload", default="grid", choices=["grid", "stream", "batch", "proposal", "tts", "phase"])
     ap.add_argument("--sweeps-per-step", type=int, default=None)
     ap.add_argument("--measure-every", type=int, default=10)
     ap.add_argument("--cpu-seconds", type=float, default=8.0)
@@ -177,7 +177,7 @@ def workload_config(name, rank):
     return w
 
 
-DEFAULT_SWEEPS = {"grid": 2000, "stream": 20, "batch": 500, "proposal": 1000, "tts": 4000}
+DEFAULT_SWEEPS = {"grid": 2000, "stream": 20, "batch": 500, "proposal": 1000, "tts": 4000, "phase": 4000}
 
 
 def cpu_baseline(w, seconds, precision=0, rng=0):
@@ -317,6 +317,75 @@ def run_tts(args, rank, ws):
            "note": "tts99_s = TTS_99 in sweeps x this GPU's time per sweep of the whole context (all "
                    f"{per * len(TTS_PHASES)} chains advance together); paper_fpga_s is the FPGA time the paper "
                    "prints for the phase"}
+    if rank == 0:
+        print(json.dumps(out))
+    if ws > 1:
+        torch.distributed.destroy_process_group()
+
+
+def run_phase(args, rank, ws):
+    """Ground-state phase diagram scan at L=18: 429 points (J'/J in [0, 3],
+    h in [-8, 8]) x one 32-rung replica-exchange ladder each (beta in
+    [0.25, 8]), every rung's first sweep at the point's brute-force supercell
+    ground-state energy recorded on the device.  A point is solved when any
+    of its rungs reaches that energy; the point's phase is the supercell
+    ground state's (FM, Neel, dimer, 1/3 or 1/2 plateau)."""
+    import torch
+    import paper_2511_20911_gb300 as crbm
+    from paper_2511_20911_gb300 import analysis, workloads
+    S = args.sweeps_per_step
+    w = workloads.phase_scan_workload()
+    L, R, N = w["L"], w["rungs"], w["L"] ** 2
+    s = crbm.Sampler(L, w["params"], w["n_chains"], chain_param=w["chain_param"], seed=replica_seed(w["seed"], rank),
+                     measure_every=w["measure_every"], swap_every=w["swap_every"], layout=crbm.CRBM_LAYOUT_SMEM)
+    e_gs, labels = [], []
+    for J, Jp, h in w["points"]:
+        E, (a, b), pattern = analysis.ground_state_energy(L, J, Jp, h)
+        nJ, nP, M = (int(x[0]) * (N // (a * b)) for x in analysis.ss_counts(pattern[None]))
+        e_gs.append(E)
+        labels.append(analysis.phase_label(nJ, nP, M, N))
+    s.set_targets(np.repeat(np.asarray(e_gs, np.int64), R))
+    with ClockSampler(torch.cuda.current_device()) as clk:
+        a_ev, b_ev = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        torch.cuda.synchronize()
+        a_ev.record()
+        s.sweep(S)
+        b_ev.record()
+        torch.cuda.synchronize()
+    sec = max_over_ranks(a_ev.elapsed_time(b_ev) / 1e3, ws)
+    hits = s.first_hits().reshape(len(w["points"]), R)
+    first = np.where((hits >= 0).any(1), np.where(hits >= 0, hits, np.iinfo(np.int64).max).min(1), -1)
+    by_phase = {}
+    for lab, f in zip(labels, first):
+        d = by_phase.setdefault(lab, {"points": 0, "solved": 0, "first_hit_sweeps": []})
+        d["points"] += 1
+        if f >= 0:
+            d["solved"] += 1
+            d["first_hit_sweeps"].append(int(f))
+    for d in by_phase.values():
+        f = d.pop("first_hit_sweeps")
+        d["median_first_hit_sweep"] = float(np.median(f)) if f else None
+    short = {"FM": "F", "Neel": "N", "dimer": "D", "1/3 plateau": "3", "1/2 plateau": "2"}
+    rows = []
+    for i in range(w["n_jp"]):
+        row = ""
+        for j in range(w["n_h"]):
+            k = i * w["n_h"] + j
+            c = short.get(labels[k], "?")
+            row += c if first[k] >= 0 else c.lower() if c.isalpha() else "."
+        rows.append(f"J'={w['points'][i * w['n_h']][1]:.2f} " + row)
+    out = {"metric": METRIC, "value": replica_value(w["n_chains"] * N * S, ws, sec), "unit": UNIT, "n_gpus": ws,
+           "steps": 1, "warmup": 0, "ms_per_step": sec * 1e3, "higher_is_better": True, "scaling": "weak",
+           "vs_baseline": None, "dtype": "u32", "data": "synthetic",
+           "config": {"workload": "ground-state phase scan: L=18, J=1, J'/J in [0,3] step 1/4, h in [-8,8] step 1/2 "
+                                  f"(429 points) x 32-rung replica-exchange ladders (beta 0.25..8, swaps every "
+                                  f"{w['swap_every']} sweeps), {S} sweeps, ground states by brute force over even "
+                                  "supercells of <= 16 sites", "parallelism": f"replicas x{ws}"},
+           "clocks": clk.summary(),
+           "phase_scan": {"points": len(first), "solved": int((first >= 0).sum()), "by_phase": by_phase,
+                          "map": rows,
+                          "map_key": "rows J'/J, columns h = -8..8; F FM, N Neel, D dimer, 3 1/3 plateau, "
+                                     "2 1/2 plateau (supercell ground state); lower case or '.': not reached"}}
     if rank == 0:
         print(json.dumps(out))
     if ws > 1:
@@ -481,6 +550,9 @@ def main():
         return
     if args.workload == "tts":
         run_tts(args, rank, ws)
+        return
+    if args.workload == "phase":
+        run_phase(args, rank, ws)
         return
     import torch
     import paper_2511_20911_gb300 as crbm

@@ -92,6 +92,28 @@ def ground_state_energy(L, J, Jp, h, max_sites=16):
     return best
 
 
+def phase_label(nJ, nJp, M, N):
+    """A name for a ground state of N spins from its counts: FM (|M| = N),
+    Neel (M = 0, every J bond antiparallel: N_J = -2N), dimer (M = 0, every
+    J' dimer antiparallel: N_J' = -N/2, N_J = 0), the 1/3 and 1/2
+    magnetisation plateaus, else its magnetisation per spin."""
+    from fractions import Fraction
+    m = abs(Fraction(int(M), int(N)))
+    if m == 1:
+        return "FM"
+    if m == 0:
+        if nJ == -2 * N:
+            return "Neel"
+        if nJp == -(N // 2) and nJ == 0:
+            return "dimer"
+        return "m=0"
+    if m == Fraction(1, 3):
+        return "1/3 plateau"
+    if m == Fraction(1, 2):
+        return "1/2 plateau"
+    return f"m={m}"
+
+
 def time_to_solution(first_hits, n_sweeps, level=99.0):
     """TTS_l = T log(1 - l/100) / log(1 - p_gnd) (Sec. III, "Hardware
     Acceleration"), in sweeps, from the first hitting sweeps of independent

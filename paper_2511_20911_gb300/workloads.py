@@ -106,3 +106,25 @@ def strip_workload(hs=(3.0, 4.5), betas=(1.0, 2.0, 4.0), chains_per_point=256, r
     n = chains_per_point * len(pts)
     return dict(L=rows, L_cols=width, periodic=True, periodic_cols=2, params=params, n_chains=n,
                 chain_param=(np.arange(n) // chains_per_point).astype(np.int32), seed=12, measure_every=10)
+
+
+def phase_scan_workload(jp_values=None, h_values=None, L=18, rungs=32, beta_min=0.25, beta_max=8.0, seed=909):
+    """The ground-state phase diagram scan (Sec. III, next to the paper's
+    time-to-solution points): J = 1, J'/J over [0, 3] in steps of 1/4 and h
+    over [-8, 8] in steps of 1/2 (all on the Q.4 grid), one replica-exchange
+    ladder of `rungs` chains per point, beta geometric in [beta_min,
+    beta_max].  Chain 32 p + k is rung k of point p; each chain has its own
+    parameter point (its rung's beta)."""
+    jp = np.arange(0.0, 3.0001, 0.25) if jp_values is None else np.asarray(jp_values, np.float64)
+    hs = np.arange(-8.0, 8.0001, 0.5) if h_values is None else np.asarray(h_values, np.float64)
+    betas = beta_min * (beta_max / beta_min) ** (np.arange(rungs) / (rungs - 1))
+    points = [(1.0, q4(a), q4(x)) for a in jp for x in hs]
+    params = dict(J=[], Jp=[], h=[], beta=[])
+    for J, a, x in points:
+        params["J"] += [J] * rungs
+        params["Jp"] += [a] * rungs
+        params["h"] += [x] * rungs
+        params["beta"] += [float(b) for b in betas]
+    n = len(points) * rungs
+    return dict(L=L, params=params, n_chains=n, chain_param=np.arange(n, dtype=np.int32), swap_every=10,
+                measure_every=2, seed=seed, points=points, rungs=rungs, n_jp=len(jp), n_h=len(hs))

@@ -49,3 +49,23 @@ def test_ground_states_of_the_known_phases():
         assert analysis.ground_state_energy(L, 1.0, 2.5, 0.0)[0] == 16 * N * (-1.25)
         e, cell, pat = analysis.ground_state_energy(L, 1.0, 0.5, 4.0)
         assert e == round(16 * N * (-2 / 3 - 0.5 / 6 - 4 / 3)) and pat.sum() * 3 == pat.size
+
+
+def test_phase_labels_of_the_known_ground_states():
+    """Counts of the ideal states (N = 36): FM N_J = 2N, N_J' = N/2, M = N;
+    Neel N_J = -2N, N_J' = N/2, M = 0; dimer N_J = 0, N_J' = -N/2, M = 0; the
+    1/3 plateau of the closed form above (N_J = -2N/3, N_J' = -N/6, M = N/3)."""
+    from paper_2511_20911_gb300 import analysis
+    N = 36
+    assert analysis.phase_label(2 * N, N // 2, -N, N) == "FM"
+    assert analysis.phase_label(-2 * N, N // 2, 0, N) == "Neel"
+    assert analysis.phase_label(0, -N // 2, 0, N) == "dimer"
+    assert analysis.phase_label(-2 * N // 3, -N // 6, N // 3, N) == "1/3 plateau"
+    assert analysis.phase_label(0, 0, N // 2, N) == "1/2 plateau"
+    assert analysis.phase_label(0, 0, N // 9, N) == "m=1/9"
+    for J, Jp, h, name in ((1.0, 1.0, 7.0, "FM"), (1.0, 1.0, 0.0, "Neel"), (1.0, 2.5, 0.0, "dimer"),
+                           (1.0, 0.5, 4.0, "1/3 plateau")):
+        L = 12
+        e, (a, b), pat = analysis.ground_state_energy(L, J, Jp, h)
+        nJ, nP, M = (int(x[0]) * (L * L // (a * b)) for x in analysis.ss_counts(pat[None]))
+        assert analysis.phase_label(nJ, nP, M, L * L) == name

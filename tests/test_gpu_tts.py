@@ -93,3 +93,26 @@ def test_low_temperature_runs_reach_the_ground_state(J, Jp, h):
     q = [round(16 * x) for x in (J, Jp, h)]
     E = q[0] * ser[..., 0] + q[1] * ser[..., 1] - q[2] * ser[..., 2]
     assert E.min() == e_gs
+
+
+def test_phase_scan_reaches_the_easy_ground_states():
+    """A small phase scan (L=6, J'/J in {1, 2.5}, h in {0, 7}): one 32-rung
+    replica-exchange ladder per point with its brute-force ground-state energy
+    as the target; the FM (h = 7), Neel (J' = 1, h = 0) and dimer (J' = 2.5,
+    h = 0) points are reached within 2000 sweeps, and no rung goes below the
+    supercell bound of the FM point, which is the true ground state there."""
+    from paper_2511_20911_gb300 import analysis
+    w = workloads.phase_scan_workload(jp_values=[1.0, 2.5], h_values=[0.0, 7.0], L=6)
+    s = crbm.Sampler(w["L"], w["params"], w["n_chains"], chain_param=w["chain_param"], seed=5,
+                     measure_every=w["measure_every"], swap_every=w["swap_every"])
+    e_gs = [analysis.ground_state_energy(6, J, Jp, h)[0] for J, Jp, h in w["points"]]
+    s.set_targets(np.repeat(np.asarray(e_gs, np.int64), w["rungs"]))
+    s.sweep(2000)
+    hits = s.first_hits().reshape(len(w["points"]), w["rungs"])
+    assert (hits >= 0).any(1).all(), hits
+    sums = s.observables().reshape(len(w["points"]), w["rungs"], -1)
+    fm = [k for k, (J, Jp, h) in enumerate(w["points"]) if h == 7.0]
+    for k in fm:
+        J, Jp, h = w["points"][k]
+        mean_e = (16 * J * sums[k, :, 1] + 16 * Jp * sums[k, :, 2] - 16 * h * sums[k, :, 3]) / sums[k, :, 0]
+        assert (mean_e >= e_gs[k] - 1e-9).all()

@@ -464,8 +464,9 @@ def run_proposal(args, rank, ws):
     """Learned block proposal: train it on the GPU on configurations the
     sampler generates (L=18, J'/J=1, beta in [1.5,3], h in [2.5,3.5]), then
     compare effective samples per second of E and m, plain Gibbs against
-    Gibbs + one block-move pass per sweep, from the same equilibrated state,
-    at L=18 and L=48 (J'/J=1, h=3, beta in {1.5,2,3}, 4096 chains)."""
+    Gibbs + one block-move pass per sweep and per 4 sweeps, from the same
+    equilibrated state, at L=18 and L=48 (J'/J=1, h=3, beta in {1.5,2,3},
+    4096 chains)."""
     import torch
     import paper_2511_20911_gb300 as crbm
     from paper_2511_20911_gb300 import analysis, workloads
@@ -487,7 +488,7 @@ def run_proposal(args, rank, ws):
         ck = base.save()
         cp = np.asarray(ew["chain_param"])
         out = {}
-        for mode in ("plain", "mixed"):
+        for mode in ("plain", "mixed", "mixed4"):
             s = crbm.Sampler(**dict(ew, measure_every=1, series_len=T))
             s.load(ck)
             s.reset_observables()
@@ -498,7 +499,7 @@ def run_proposal(args, rank, ws):
             if mode == "plain":
                 s.sweep(T)
             else:
-                prop.sweep_mixed(s, T)
+                prop.sweep_mixed(s, T, every=1 if mode == "mixed" else 4)
             b.record(stream)
             torch.cuda.synchronize()
             sec = a.elapsed_time(b) / 1e3
@@ -514,11 +515,15 @@ def run_proposal(args, rank, ws):
                          "ess_per_s_E": [float(essE[cp == g].sum() / sec) for g in range(3)],
                          "ess_per_s_m": [float(essM[cp == g].sum() / sec) for g in range(3)],
                          "e_per_spin": [float(E[cp == g].mean() / (16 * L * L) * 16) for g in range(3)],
-                         "accept": (p1[1] - p0[1]) / max(1, p1[0] - p0[0]) if mode == "mixed" else None}
-        gain_E = [m / p if p > 0 else None for m, p in zip(out["mixed"]["ess_per_s_E"], out["plain"]["ess_per_s_E"])]
-        gain_m = [m / p if p > 0 else None for m, p in zip(out["mixed"]["ess_per_s_m"], out["plain"]["ess_per_s_m"])]
+                         "accept": (p1[1] - p0[1]) / max(1, p1[0] - p0[0]) if mode != "plain" else None}
+        def gain(mode, key):
+            return [m / p if p > 0 else None for m, p in zip(out[mode][key], out["plain"][key])]
         results.append({"L": L, "beta": ew["params"]["beta"], "h": 3.0, "plain": out["plain"],
-                        "mixed": out["mixed"], "ess_per_s_gain_E": gain_E, "ess_per_s_gain_m": gain_m})
+                        "mixed": out["mixed"], "mixed_every4": out["mixed4"],
+                        "ess_per_s_gain_E": gain("mixed", "ess_per_s_E"),
+                        "ess_per_s_gain_m": gain("mixed", "ess_per_s_m"),
+                        "ess_per_s_gain_E_every4": gain("mixed4", "ess_per_s_E"),
+                        "ess_per_s_gain_m_every4": gain("mixed4", "ess_per_s_m")})
     mixed_rate = sum(sum(r["mixed"]["ess_per_s_E"]) for r in results)
     line = {"metric": METRIC, "value": mixed_rate, "unit": "effective samples/s (E, mixed sampler)",
             "n_gpus": ws, "steps": 1, "warmup": 0, "higher_is_better": True, "scaling": "weak",

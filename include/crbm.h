@@ -335,6 +335,11 @@ int crbm_proposal_loss_grad(crbm_proposal* p, const int8_t* spins, int32_t L, co
 int crbm_proposal_pass(crbm_ctx* ctx, crbm_proposal* p, int64_t n_passes);
 /* n_sweeps times: one Gibbs sweep, then one pass of block moves. */
 int crbm_sweep_mixed(crbm_ctx* ctx, crbm_proposal* p, int64_t n_sweeps);
+/* n_sweeps Gibbs sweeps with one pass of block moves after every `every`
+ * sweeps (the sweeps between passes run in one launch); every >= 1, every =
+ * 1 is crbm_sweep_mixed.  A final group shorter than `every` ends with a pass
+ * too. */
+int crbm_sweep_mixed_every(crbm_ctx* ctx, crbm_proposal* p, int64_t n_sweeps, int32_t every);
 /* The next pass, evaluated without moving: records out[n_words][n_blocks][32]. */
 int crbm_proposal_inspect(crbm_ctx* ctx, crbm_proposal* p, crbm_pass_record* out, size_t n_out);
 /* Cumulative proposed / accepted block moves of p. */

@@ -37,7 +37,8 @@ ABI_FUNCTIONS = (
     "crbm_batch_threads", "crbm_batch_cluster", "crbm_batch_last_error", "crbm_batch_destroy",
     "crbm_proposal_create", "crbm_proposal_destroy", "crbm_proposal_set_weights",
     "crbm_proposal_get_weights", "crbm_proposal_train", "crbm_proposal_loss_grad",
-    "crbm_proposal_pass", "crbm_sweep_mixed", "crbm_proposal_inspect", "crbm_proposal_stats",
+    "crbm_proposal_pass", "crbm_sweep_mixed", "crbm_sweep_mixed_every", "crbm_proposal_inspect",
+    "crbm_proposal_stats",
     "crbm_proposal_last_error",
     "crbm_save", "crbm_load", "crbm_philox", "crbm_sweep_stream_noalloc", "crbm_last_error",
 )
@@ -118,6 +119,7 @@ def load_library(path: str | None = None):
                                               c.POINTER(c.c_float)]),
         "crbm_proposal_pass": (c.c_int, [vp, vp, c.c_int64]),
         "crbm_sweep_mixed": (c.c_int, [vp, vp, c.c_int64]),
+        "crbm_sweep_mixed_every": (c.c_int, [vp, vp, c.c_int64, c.c_int32]),
         "crbm_proposal_inspect": (c.c_int, [vp, vp, vp, c.c_size_t]),
         "crbm_proposal_stats": (c.c_int, [vp, c.POINTER(c.c_int64), c.POINTER(c.c_int64)]),
         "crbm_proposal_last_error": (c.c_char_p, []),
@@ -423,8 +425,12 @@ class Proposal:
     def passes(self, sampler, n):
         self._chk(self._lib.crbm_proposal_pass(sampler._ctx, self._p, int(n)))
 
-    def sweep_mixed(self, sampler, n):
-        self._chk(self._lib.crbm_sweep_mixed(sampler._ctx, self._p, int(n)))
+    def sweep_mixed(self, sampler, n, every=1):
+        """n Gibbs sweeps with one pass of block moves after every `every` sweeps."""
+        if every == 1:
+            self._chk(self._lib.crbm_sweep_mixed(sampler._ctx, self._p, int(n)))
+        else:
+            self._chk(self._lib.crbm_sweep_mixed_every(sampler._ctx, self._p, int(n), int(every)))
 
     def inspect(self, sampler):
         nb1 = max(1, sampler.L // 8)

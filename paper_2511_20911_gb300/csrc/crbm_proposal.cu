@@ -20,6 +20,7 @@
 // runs on the spin plane alone (one k-tile).  Training runs one example per
 // thread in fp32 (bf16-rounded weights and activations), back-propagates the
 // binary cross-entropy and updates with Adam.
+#include <algorithm>
 #include <cstring>
 #include <string>
 #include <vector>
@@ -869,15 +870,19 @@ int crbm_proposal_pass(crbm_ctx* ctx, crbm_proposal* p, int64_t n_passes) {
     return CRBM_OK;
 }
 
-int crbm_sweep_mixed(crbm_ctx* ctx, crbm_proposal* p, int64_t n_sweeps) {
-    if (!p || n_sweeps < 0) return prop_fail(CRBM_EINVAL, "bad arguments");
+int crbm_sweep_mixed_every(crbm_ctx* ctx, crbm_proposal* p, int64_t n_sweeps, int32_t every) {
+    if (!p || n_sweeps < 0 || every < 1) return prop_fail(CRBM_EINVAL, "bad arguments");
     int rc = check_ctx(ctx);
     if (rc) return rc;
-    for (int64_t i = 0; i < n_sweeps; ++i) {
-        if ((rc = crbm_sweep(ctx, 1))) return prop_fail(rc, crbm_last_error(ctx));
+    for (int64_t i = 0; i < n_sweeps; i += every) {
+        if ((rc = crbm_sweep(ctx, std::min<int64_t>(every, n_sweeps - i)))) return prop_fail(rc, crbm_last_error(ctx));
         if ((rc = crbm_proposal_pass(ctx, p, 1))) return rc;
     }
     return CRBM_OK;
+}
+
+int crbm_sweep_mixed(crbm_ctx* ctx, crbm_proposal* p, int64_t n_sweeps) {
+    return crbm_sweep_mixed_every(ctx, p, n_sweeps, 1);
 }
 
 int crbm_proposal_inspect(crbm_ctx* ctx, crbm_proposal* p, crbm_pass_record* out, size_t n_out) {

@@ -124,6 +124,24 @@ def test_mixed_sampler_matches_plain_gibbs():
         assert abs(m0 - m1) < 4 * np.hypot(s0, s1), (m0, m1, s0, s1)
 
 
+def test_mixed_every_is_sweeps_then_a_pass():
+    """sweep_mixed(n, every) = groups of `every` sweeps (the last one
+    shorter), each followed by one pass: bit-identical to the same calls made
+    one by one (the passes are keyed on the pass count)."""
+    params = dict(J=[1.0], Jp=[1.5], h=[0.5], beta=[1.2])
+    a = crbm.Sampler(12, params, 96, seed=4, measure_every=1)
+    b = crbm.Sampler(12, params, 96, seed=4, measure_every=1)
+    p = crbm.Proposal(seed=2)
+    p.sweep_mixed(a, 11, every=4)
+    for n in (4, 4, 3):
+        b.sweep(n)
+        p.passes(b, 1)
+    assert np.array_equal(a.get_spins(), b.get_spins())
+    assert np.array_equal(a.observables(), b.observables())
+    with pytest.raises(crbm.CrbmError):
+        p.sweep_mixed(a, 4, every=0)
+
+
 def test_trained_network_gains_effective_samples_per_sweep():
     """What the trained network adds over the method without it: from one
     equilibrated L=18 state (J'/J = 1, h = 3, beta = 2, near the 1/3 plateau),

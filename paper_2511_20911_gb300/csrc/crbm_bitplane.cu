@@ -105,15 +105,24 @@ __device__ __forceinline__ void sweep_bitplane_body(const SweepArgs& a, const ui
             const Round2Cell r2 = round2_cell(rs.hik ^ static_cast<uint32_t>(pc));
             const uint32_t c2 = static_cast<uint32_t>(pc >> 32) ^ a.rk[1] ^ (kTagBitplane + 8u * k);
             uint32_t lt = 0u, eq = valid ? 0xffffffffu : 0u;
-#pragma unroll 1
-            for (uint32_t j = 0; j < 8u; ++j) {
-                if (!__any_sync(0xffffffffu, eq != 0u)) break;
-                const U4 q = philox_from_round2(Yw, rs, r2, c2 ^ j, a.rk);
+            auto planes = [&](const U4& q, uint32_t j) {
                 const uint32_t* tb = tp + 4u * j;
                 plane_step(q.x, (P & tb[64]) | (M & tb[0]) | (j == 0u ? Z : 0u), lt, eq);
                 plane_step(q.y, (P & tb[65]) | (M & tb[1]), lt, eq);
                 plane_step(q.z, (P & tb[66]) | (M & tb[2]), lt, eq);
                 plane_step(q.w, (P & tb[67]) | (M & tb[3]), lt, eq);
+            };
+            // calls 0 and 1 together (a group of 32 nodes nearly always needs both:
+            // all 1024 comparisons close within 4 planes with probability
+            // (15/16)^1024), then one call at a time while any is open
+            const U4 q0 = philox_from_round2(Yw, rs, r2, c2, a.rk);
+            const U4 q1 = philox_from_round2(Yw, rs, r2, c2 ^ 1u, a.rk);
+            planes(q0, 0u);
+            planes(q1, 1u);
+#pragma unroll 1
+            for (uint32_t j = 2; j < 8u; ++j) {
+                if (!__any_sync(0xffffffffu, eq != 0u)) break;
+                planes(philox_from_round2(Yw, rs, r2, c2 ^ j, a.rk), j);
             }
             if (valid) s_h[node] = lt;
         }
@@ -138,10 +147,7 @@ __device__ __forceinline__ void sweep_bitplane_body(const SweepArgs& a, const ui
             const Round2Cell r2 = round2_cell(rs.hik ^ static_cast<uint32_t>(pc));
             const uint32_t c2 = static_cast<uint32_t>(pc >> 32) ^ a.rk[1] ^ (kTagBitplane + 8u * (10u + x));
             uint32_t lt = 0u, eq = valid ? 0xffffffffu : 0u;
-#pragma unroll 1
-            for (uint32_t j = 0; j < 8u; ++j) {
-                if (!__any_sync(0xffffffffu, eq != 0u)) break;
-                const U4 q = philox_from_round2(Yw, rs, r2, c2 ^ j, a.rk);
+            auto planes = [&](const U4& q, uint32_t j) {
                 const uint32_t u[4] = {q.x, q.y, q.z, q.w};
 #pragma unroll
                 for (int i = 0; i < 4; ++i) {
@@ -150,6 +156,11 @@ __device__ __forceinline__ void sweep_bitplane_body(const SweepArgs& a, const ui
                     const uint32_t T = (D0 & sel(0)) | (D1 & sel(1)) | (D2 & sel(2)) | (D3 & sel(3)) | (D4 & sel(4));
                     plane_step(u[i], T, lt, eq);
                 }
+            };
+#pragma unroll 1
+            for (uint32_t j = 0; j < 8u; ++j) {
+                if (!__any_sync(0xffffffffu, eq != 0u)) break;
+                planes(philox_from_round2(Yw, rs, r2, c2 ^ j, a.rk), j);
             }
             if (valid) s_v[s] = lt;
         }

@@ -141,7 +141,6 @@ __device__ __forceinline__ void sweep_bitplane_body(const SweepArgs& a, const ui
             const uint32_t s01 = h0 ^ h1, a01 = h0 & h1, s23 = h2 ^ h3, a23 = h2 & h3;
             const uint32_t c0 = s01 ^ s23, cy = s01 & s23;
             const uint32_t c1 = a01 ^ a23 ^ cy, cc2 = (a01 & a23) | (cy & (a01 | a23));
-            const uint32_t D0 = ~(c0 | c1 | cc2), D1 = c0 & ~(c1 | cc2), D2 = c1 & ~c0, D3 = c1 & c0, D4 = cc2;
             const uint32_t* tv = s_tab + kBpVisPlanes;  // [count][J' bit][32]
             const uint64_t pc = static_cast<uint64_t>(kPhiloxM0) * cell;
             const Round2Cell r2 = round2_cell(rs.hik ^ static_cast<uint32_t>(pc));
@@ -152,8 +151,10 @@ __device__ __forceinline__ void sweep_bitplane_body(const SweepArgs& a, const ui
 #pragma unroll
                 for (int i = 0; i < 4; ++i) {
                     const uint32_t* tb = tv + 4u * j + i;
+                    // the count's threshold plane by a mux tree: J' bit, then count bits 0, 1, 2
                     auto sel = [&](int c) { return (hp & tb[(2 * c + 1) * 32]) | (~hp & tb[2 * c * 32]); };
-                    const uint32_t T = (D0 & sel(0)) | (D1 & sel(1)) | (D2 & sel(2)) | (D3 & sel(3)) | (D4 & sel(4));
+                    const uint32_t m01 = (c0 & sel(1)) | (~c0 & sel(0)), m23 = (c0 & sel(3)) | (~c0 & sel(2));
+                    const uint32_t T = (cc2 & sel(4)) | (~cc2 & ((c1 & m23) | (~c1 & m01)));
                     plane_step(u[i], T, lt, eq);
                 }
             };

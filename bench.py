@@ -51,6 +51,7 @@ MEASURED_TRAFFIC = {
     "grid_paper": (8.77e6 + 0.64e6, "per launch; profiles/k_sweep_canon_persistent_L18_grid_paper.md"),
     "stream_paper": (56.76e6 + 390.29e6 + 454.76e6 + 45.71e6, "per sweep (two launches); profiles/k_stream_L384.md"),
     "grid_bitplane": (2.81e6 + 0.65e6, "per launch; profiles/k_sweep_bitplane_L18_grid.md"),
+    "stream_bitplane": (None, "not captured for this kernel"),
 }
 
 
@@ -86,8 +87,8 @@ def parse():
                     help="bitplane: uniforms from bit-plane words shared by the 32 chains of a word, compared "
                          "most significant bit first (grid workload)")
     args = ap.parse_args()
-    if args.rng == "bitplane" and (args.workload != "grid" or args.precision != "exact"):
-        ap.error("--rng bitplane runs the grid workload in exact precision")
+    if args.rng == "bitplane" and (args.workload not in ("grid", "stream") or args.precision != "exact"):
+        ap.error("--rng bitplane runs the grid and stream workloads in exact precision")
     if args.precision == "paper" and args.workload not in ("grid", "stream"):
         ap.error("--precision paper runs the grid and stream workloads only")
     return args
@@ -633,8 +634,18 @@ def main():
         cpc = CALLS_PER_CELL_PAPER if args.workload == "grid" else CALLS_PER_CELL_PAPER_STREAM
     calls = cpc * (w["L"] // 2) ** 2 * w["n_chains"] * S
     if bitplane:   # expected calls of the early-exit comparison (hidden nodes, then spins)
-        n_words = (w["n_chains"] + 31) // 32
-        calls = (bitplane_expected_calls(10 * (w["L"] // 2) ** 2) + bitplane_expected_calls(w["L"] ** 2)) * n_words * S
+        W = w["L"] // 2
+        if args.workload == "grid":   # one CTA per word: its nodes in groups of 32
+            n_words = (w["n_chains"] + 31) // 32
+            per_word = bitplane_expected_calls(10 * W * W) + bitplane_expected_calls(w["L"] ** 2)
+        else:                         # 64-chain groups of two words; 16 x 16-cell tiles
+            n_words = 2 * ((w["n_chains"] + 63) // 64)
+            per_word = 0.0
+            for ti in range(0, W, 16):
+                for tj in range(0, W, 16):
+                    cells = min(16, W - ti) * min(16, W - tj)
+                    per_word += bitplane_expected_calls(10 * cells) + bitplane_expected_calls(4 * cells)
+        calls = per_word * n_words * S
         cpc = calls / ((w["L"] // 2) ** 2 * w["n_chains"] * S)
     if args.workload == "grid":   # one launch per step: spins in and out once
         hbm_bytes = w["n_chains"] * w["L"] ** 2 / 8 * 2

@@ -331,12 +331,11 @@ int crbm_create(crbm_ctx** out, const crbm_params* p) {
         return fail(nullptr, CRBM_EINVAL, "unknown rng");
     }
     g.bitplane = p->rng == CRBM_RNG_BITPLANE ? 1 : 0;
-    if (g.bitplane && (!g.canonical || g.paper || p->layout == CRBM_LAYOUT_STREAM || p->swap_every > 0 ||
-                       p->sq_every > 0)) {
+    if (g.bitplane && (!g.canonical || g.paper || p->swap_every > 0 || p->sq_every > 0)) {
         delete ctx;
         return fail(nullptr, CRBM_EUNSUPPORTED,
-                    "bit-plane uniforms need the ten SS filters on an even periodic lattice in the SMEM layout, "
-                    "exact precision, no replica exchange and no correlations");
+                    "bit-plane uniforms need the ten SS filters on an even periodic lattice, exact precision, "
+                    "no replica exchange and no correlations");
     }
     // AUTO: shared memory when the lattice, its hidden words and the tables fit
     // in one CTA's 227 KB, else the streamed layout (SS filters, even periodic L)
@@ -371,10 +370,6 @@ int crbm_create(crbm_ctx** out, const crbm_params* p) {
         return fail(nullptr, CRBM_EUNSUPPORTED, "spin correlations are accumulated in the SMEM layout only");
     }
     g.vil = ctx->layout == CRBM_LAYOUT_STREAM ? 1 : 0;
-    if (g.bitplane && ctx->layout != CRBM_LAYOUT_SMEM) {
-        delete ctx;
-        return fail(nullptr, CRBM_EUNSUPPORTED, "bit-plane uniforms run in the SMEM layout");
-    }
     if (ctx->layout == CRBM_LAYOUT_SMEM &&
         (g.bitplane ? smem_bytes_bitplane(g, false) : g.canonical ? smem_bytes_canon(g) : smem_bytes_generic(g)) >
             227 * 1024) {
@@ -589,7 +584,7 @@ int crbm_create(crbm_ctx** out, const crbm_params* p) {
     }
     // Per-cell records of the canonical SMEM sweep (layout in crbm_internal.h).
     std::vector<uint32_t> crec;
-    if (g.bitplane) {
+    if (g.bitplane && ctx->layout == CRBM_LAYOUT_SMEM) {
         // hidden node cell*10 + k: its endpoint sites (s1 | s2 << 16); then per
         // spin: its four J incidences and its J' incidence (hidden node | 0x8000
         // when the spin is the second endpoint), its cell and window offset

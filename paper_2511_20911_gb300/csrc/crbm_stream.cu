@@ -223,6 +223,190 @@ __global__ void __launch_bounds__(kStreamVisThreads, CRBM_STREAM_VIS_MIN_BLOCKS)
     }
 }
 
+// ---- bit-plane uniforms (CRBM_RNG_BITPLANE) in the streamed layout ----
+// The same word-parallel comparison as the SMEM bit-plane sweep
+// (crbm_bitplane.cu): a thread takes one node of a tile for the 32 chains of
+// the half-word, and the hidden units travel through HBM bit-sliced, one
+// word per (cell, filter): h[word][cell][10].
+
+__device__ __forceinline__ void bp_plane_step(uint32_t U, uint32_t T, uint32_t& lt, uint32_t& eq) {
+    lt |= eq & T & ~U;
+    eq &= ~(T ^ U);
+}
+
+// Hidden half-step of one tile: the spin tile (halo included) in, the tile's
+// hidden words out.
+__global__ void __launch_bounds__(kStreamThreads) k_stream_bp_hidden(const SweepArgs a, uint32_t t) {
+    __shared__ uint32_t s_tab[kBpTab];
+    __shared__ uint32_t s_v[(2 * kTI + 1) * (2 * kTJ + 1)];
+    __shared__ uint32_t s_h[kTI * kTJ * 10];
+    __shared__ int s_off[2][10];  // the filters' endpoint offsets in the staged tile
+    const Geometry& g = a.g;
+    const int W = g.W;
+    const int w = blockIdx.y;
+    const int tiles_j = (W + kTJ - 1) / kTJ;
+    const int i0 = (blockIdx.x / tiles_j) * kTI, j0 = (blockIdx.x % tiles_j) * kTJ;
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nwarp = blockDim.x >> 5;
+    constexpr int VS = 2 * kTJ + 1;
+    const uint32_t* gt = a.ctab + static_cast<size_t>(w) * kCanonTab;
+    for (int x = threadIdx.x; x < kBpTab; x += blockDim.x) s_tab[x] = gt[x];
+    if (threadIdx.x < 10) {
+        const int k = threadIdx.x;
+        s_off[0][k] = g.r1[k] * VS + g.c1[k];
+        s_off[1][k] = g.r2[k] * VS + g.c2[k];
+    }
+    stage_spin_tile(a, w, i0, j0, s_v);
+    __syncthreads();
+    const uint32_t fl0 = s_tab[kBpFlip], fl1 = s_tab[kBpFlip + 1];
+    const int ni = min(kTI, W - i0), nj = min(kTJ, W - j0), nn = ni * nj * 10;
+    const uint64_t pw = static_cast<uint64_t>(kPhiloxM1) * static_cast<uint32_t>(w);
+    const uint32_t Yw = static_cast<uint32_t>(pw);
+    const Round1Sweep rs = round1_sweep(static_cast<uint32_t>(pw >> 32) ^ a.rk[0] ^ t, a.rk);
+    for (int base = warp * 32; base < nn; base += nwarp * 32) {
+        const int node = base + lane;
+        const bool valid = node < nn;
+        const int nd = valid ? node : 0;
+        const int lc = nd / 10, k = nd - lc * 10;
+        const int li = lc / nj, lj = lc - li * nj;
+        const uint32_t cls = k >= 8 ? 1u : 0u;
+        const uint32_t* v = s_v + 2 * li * VS + 2 * lj;
+        const uint32_t e1 = v[s_off[0][k]];
+        const uint32_t e2 = v[s_off[1][k]] ^ (cls ? fl1 : fl0);
+        const uint32_t P = e1 & e2, M = ~(e1 | e2), Z = e1 ^ e2;
+        const uint32_t* tp = s_tab + kBpHidPlanes + cls * 96u;
+        const uint32_t cell = static_cast<uint32_t>((i0 + li) * W + j0 + lj);
+        const uint64_t pc = static_cast<uint64_t>(kPhiloxM0) * cell;
+        const Round2Cell r2 = round2_cell(rs.hik ^ static_cast<uint32_t>(pc));
+        const uint32_t c2 = static_cast<uint32_t>(pc >> 32) ^ a.rk[1] ^ (kTagBitplane + 8u * static_cast<uint32_t>(k));
+        uint32_t lt = 0u, eq = valid ? 0xffffffffu : 0u;
+        auto planes = [&](const U4& q, uint32_t j) {
+            const uint32_t* tb = tp + 4u * j;
+            bp_plane_step(q.x, (P & tb[64]) | (M & tb[0]) | (j == 0u ? Z : 0u), lt, eq);
+            bp_plane_step(q.y, (P & tb[65]) | (M & tb[1]), lt, eq);
+            bp_plane_step(q.z, (P & tb[66]) | (M & tb[2]), lt, eq);
+            bp_plane_step(q.w, (P & tb[67]) | (M & tb[3]), lt, eq);
+        };
+        const U4 q0 = philox_from_round2(Yw, rs, r2, c2, a.rk);
+        const U4 q1 = philox_from_round2(Yw, rs, r2, c2 ^ 1u, a.rk);
+        planes(q0, 0u);
+        planes(q1, 1u);
+#pragma unroll 1
+        for (uint32_t j = 2; j < 8u; ++j) {
+            if (!__any_sync(0xffffffffu, eq != 0u)) break;
+            planes(philox_from_round2(Yw, rs, r2, c2 ^ j, a.rk), j);
+        }
+        if (valid) s_h[(li * kTJ + lj) * 10 + k] = lt;
+    }
+    __syncthreads();
+    // tile rows of hidden words are runs of 10 nj words in h
+    for (int x = threadIdx.x; x < kTI * kTJ * 10; x += blockDim.x) {
+        const int li = x / (kTJ * 10), rest = x - li * (kTJ * 10);
+        if (li >= ni || rest >= nj * 10) continue;
+        a.h[(static_cast<size_t>(w) * g.n_cells + (i0 + li) * W + j0) * 10 + rest] = s_h[x];
+    }
+}
+
+// Visible half-step of one tile: the hidden words of the tile's cells and of
+// the row above and the column to the left (wrapped) in, new spins out.
+__global__ void __launch_bounds__(kStreamVisThreads) k_stream_bp_visible(const SweepArgs a, uint32_t t) {
+    constexpr int HS = kTJ + 1;
+    __shared__ uint32_t s_tab[kBpTab];
+    __shared__ uint32_t s_h[(kTI + 1) * HS * 10];
+    __shared__ uint32_t s_o[2 * kTI * 2 * kTJ];
+    __shared__ int s_inc[4][5];  // per spin class x: hidden word offset (cell row, column, filter) | flags
+    const Geometry& g = a.g;
+    const int L = g.L, W = g.W, N = g.N;
+    const int w = blockIdx.y;
+    const int tiles_j = (W + kTJ - 1) / kTJ;
+    const int i0 = (blockIdx.x / tiles_j) * kTI, j0 = (blockIdx.x % tiles_j) * kTJ;
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nwarp = blockDim.x >> 5;
+    const uint32_t* gt = a.ctab + static_cast<size_t>(w) * kCanonTab;
+    for (int x = threadIdx.x; x < kBpTab; x += blockDim.x) s_tab[x] = gt[x];
+    if (threadIdx.x < 4) {
+        // the five filters touching the spin at window offset (r, c): endpoints
+        // at (r, c) of the own cell, (r + 2, c) of the cell above, (r, c + 2) of
+        // the cell to the left; J filters first, the J' filter last
+        const int x = threadIdx.x, r = x >> 1, c = x & 1;
+        int nJ = 0;
+        for (int k = 0; k < 10; ++k)
+            for (int e = 0; e < 2; ++e) {
+                const int er = e ? g.r2[k] : g.r1[k], ec = e ? g.c2[k] : g.c1[k];
+                int dr = -1, dc = -1;
+                if (er == r && ec == c) dr = 1, dc = 1;
+                else if (er == r + 2 && ec == c) dr = 0, dc = 1;
+                else if (er == r && ec == c + 2) dr = 1, dc = 0;
+                if (dr < 0) continue;
+                const int off = (dr * HS + dc) * 10 + k;  // relative to the spin's cell at (li, lj) -> (li + 1, lj + 1)
+                const int v = off | (e << 16);
+                if (g.cls[k] == 0) s_inc[x][nJ++] = v;
+                else s_inc[x][4] = v;
+            }
+    }
+    // hidden halo: cells (i0 - 1 .. i0 + ni - 1) x (j0 - 1 .. j0 + nj - 1), wrapped
+    const int ni = min(kTI, W - i0), nj = min(kTJ, W - j0);
+    const uint32_t* hw = a.h + static_cast<size_t>(w) * g.n_cells * 10;
+    for (int x = threadIdx.x; x < (kTI + 1) * HS * 10; x += blockDim.x) {
+        const int lc = x / 10, k = x - lc * 10;
+        const int li = lc / HS, lj = lc - li * HS;
+        if (li > ni || lj > nj) continue;
+        const int gi = (i0 - 1 + li + W) % W, gj = (j0 - 1 + lj + W) % W;
+        s_h[x] = hw[(gi * W + gj) * 10 + k];
+    }
+    __syncthreads();
+    const uint32_t fl0 = s_tab[kBpFlip], fl1 = s_tab[kBpFlip + 1];
+    const int nr = 2 * ni, nc = 2 * nj, nn = nr * nc;
+    constexpr int VO = 2 * kTJ;
+    const uint64_t pw = static_cast<uint64_t>(kPhiloxM1) * static_cast<uint32_t>(w);
+    const uint32_t Yw = static_cast<uint32_t>(pw);
+    const Round1Sweep rs = round1_sweep(static_cast<uint32_t>(pw >> 32) ^ a.rk[0] ^ t, a.rk);
+    const uint32_t* tv = s_tab + kBpVisPlanes;
+    for (int base = warp * 32; base < nn; base += nwarp * 32) {
+        const int sx = base + lane;
+        const bool valid = sx < nn;
+        const int sd = valid ? sx : 0;
+        const int R = sd / nc, C = sd - R * nc;  // tile-local spin row and column
+        const int x = 2 * (R & 1) + (C & 1);
+        const uint32_t* hc = s_h + (((R >> 1) + 1) * HS + (C >> 1) + 1) * 10;  // own cell's words
+        auto hin = [&](int v, uint32_t fl) {
+            return hc[(v & 0xFFFF) - (HS + 1) * 10] ^ ((v >> 16) ? fl : 0u);
+        };
+        const uint32_t h0 = hin(s_inc[x][0], fl0), h1 = hin(s_inc[x][1], fl0), h2 = hin(s_inc[x][2], fl0),
+                       h3 = hin(s_inc[x][3], fl0), hp = hin(s_inc[x][4], fl1);
+        const uint32_t s01 = h0 ^ h1, a01 = h0 & h1, s23 = h2 ^ h3, a23 = h2 & h3;
+        const uint32_t c0 = s01 ^ s23, cy = s01 & s23;
+        const uint32_t c1 = a01 ^ a23 ^ cy, cc2 = (a01 & a23) | (cy & (a01 | a23));
+        const uint32_t cell = static_cast<uint32_t>((i0 + (R >> 1)) * W + j0 + (C >> 1));
+        const uint64_t pc = static_cast<uint64_t>(kPhiloxM0) * cell;
+        const Round2Cell r2 = round2_cell(rs.hik ^ static_cast<uint32_t>(pc));
+        const uint32_t c2 =
+            static_cast<uint32_t>(pc >> 32) ^ a.rk[1] ^ (kTagBitplane + 8u * (10u + static_cast<uint32_t>(x)));
+        uint32_t lt = 0u, eq = valid ? 0xffffffffu : 0u;
+        auto planes = [&](const U4& q, uint32_t j) {
+            const uint32_t u[4] = {q.x, q.y, q.z, q.w};
+#pragma unroll
+            for (int i = 0; i < 4; ++i) {
+                const uint32_t* tb = tv + 4u * j + i;
+                auto sel = [&](int c) { return (hp & tb[(2 * c + 1) * 32]) | (~hp & tb[2 * c * 32]); };
+                const uint32_t m01 = (c0 & sel(1)) | (~c0 & sel(0)), m23 = (c0 & sel(3)) | (~c0 & sel(2));
+                bp_plane_step(u[i], (cc2 & sel(4)) | (~cc2 & ((c1 & m23) | (~c1 & m01))), lt, eq);
+            }
+        };
+#pragma unroll 1
+        for (uint32_t j = 0; j < 8u; ++j) {
+            if (!__any_sync(0xffffffffu, eq != 0u)) break;
+            planes(philox_from_round2(Yw, rs, r2, c2 ^ j, a.rk), j);
+        }
+        if (valid) s_o[R * VO + C] = lt;
+    }
+    __syncthreads();
+    for (int x = threadIdx.x; x < 2 * kTI * VO; x += blockDim.x) {
+        const int r = x / VO, c = x - (x / VO) * VO;
+        const int R = 2 * i0 + r, C = 2 * j0 + c;
+        if (r >= nr || c >= nc || R >= L || C >= L) continue;
+        a.v[vidx(w, N, R * L + C)] = s_o[x];
+    }
+}
+
 // Measurement counts of one tile (anti-aligned J / J' filters and +1 spins
 // per chain), summed over the CTA in shared memory, then into cnt[chain][3].
 __global__ void __launch_bounds__(kStreamThreads, CRBM_STREAM_MIN_BLOCKS) k_stream_count(const SweepArgs a) {
@@ -299,7 +483,10 @@ cudaError_t launch_sweep_stream(const SweepArgs& a, cudaStream_t st, int64_t* la
     int64_t meas = a.meas0;
     for (int it = 0; it < a.n_sweeps; ++it) {
         const uint32_t t = a.t0 + static_cast<uint32_t>(it);
-        if (a.g.paper) {
+        if (a.g.bitplane) {
+            k_stream_bp_hidden<<<grid, kStreamThreads, 0, st>>>(a, t);
+            k_stream_bp_visible<<<grid, kStreamVisThreads, 0, st>>>(a, t);
+        } else if (a.g.paper) {
             k_stream_hidden<true><<<grid, kStreamThreads, 0, st>>>(a, t);
             k_stream_visible<true><<<grid, kStreamVisThreads, 0, st>>>(a, t);
         } else {

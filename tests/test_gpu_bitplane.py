@@ -1,8 +1,10 @@
 """Bit-plane uniforms (CRBM_RNG_BITPLANE) on the GPU against the oracle's
 ORC_RNG_BITPLANE mode, bit for bit: spins, sums and series on square lattices
 and rectangles (ragged 32-chain words, signs of J and J' both ways, staged and
-global node records, several CTA shapes), the full L=18 grid on sampled chains
-in the launch the benchmark times, and the contexts that refuse the mode."""
+global node records, several CTA shapes), the streamed layout (ragged tiles,
+against the oracle and the SMEM layout), the full L=18 grid and L=384 lattice
+on sampled chains in the launches the benchmark times, and the contexts that
+refuse the mode."""
 import numpy as np
 import pytest
 
@@ -21,11 +23,12 @@ def _gpu():
     crbm.load_library()
 
 
-def run_pair(orc, shape, params, n, cp, seed, splits, measure_every=2, series_len=0, check_ids=None):
+def run_pair(orc, shape, params, n, cp, seed, splits, measure_every=2, series_len=0, check_ids=None,
+             layout=crbm.CRBM_LAYOUT_SMEM):
     L, Lc = shape if isinstance(shape, tuple) else (shape, shape)
     s = crbm.Sampler(L, params, n, chain_param=cp, seed=seed, measure_every=measure_every,
-                     series_len=series_len, L_cols=Lc if Lc != L else 0, rng=BP)
-    assert s.layout == crbm.CRBM_LAYOUT_SMEM
+                     series_len=series_len, L_cols=Lc if Lc != L else 0, rng=BP, layout=layout)
+    assert s.layout == layout
     ids = np.arange(n, dtype=np.uint32) if check_ids is None else np.asarray(check_ids, np.uint32)
     cpi = np.asarray(cp, np.int32)[ids]
     spins = orc.init_spins((L, Lc), ids, seed)
@@ -80,6 +83,33 @@ def test_bitplane_records_from_global_memory(orc):
     run_pair(orc, 96, params, 40, (np.arange(40) % 2).astype(np.int32), 4, splits=[2, 2], measure_every=1)
 
 
+@pytest.mark.parametrize("L,n", [(8, 70), (40, 64), (34, 130)])
+def test_bitplane_stream_bitexact(orc, L, n):
+    """Streamed layout: 16 x 16-cell tiles (ragged at W = 20 and 17), hidden
+    words bit-sliced in HBM, a ragged last 64-chain group; against the oracle
+    and against the SMEM layout."""
+    rng = np.random.default_rng(L * 29 + n)
+    params = workloads.random_params(rng, 3)
+    cp = rng.integers(0, 3, n).astype(np.int32)
+    s = run_pair(orc, L, params, n, cp, 13 + L, splits=[2, 5], series_len=4, layout=crbm.CRBM_LAYOUT_STREAM)
+    m = crbm.Sampler(L, params, n, chain_param=cp, seed=13 + L, measure_every=2, rng=BP,
+                     layout=crbm.CRBM_LAYOUT_SMEM)
+    m.sweep(7)
+    assert np.array_equal(m.get_spins(), s.get_spins())
+    assert np.array_equal(m.observables(), s.observables())
+
+
+@pytest.mark.slow
+def test_bitplane_stream_L384_sampled_chains(orc):
+    """The L=384 workload at full size (3072 chains) with bit-plane uniforms,
+    as the benchmark's streamed bit-plane line runs it: 16 chains over all
+    words."""
+    w = workloads.stream_workload()
+    ids = np.linspace(0, w["n_chains"] - 1, 16).astype(np.uint32)
+    run_pair(orc, 384, w["params"], w["n_chains"], w["chain_param"], w["seed"], splits=[1, 2],
+             measure_every=1, check_ids=ids, layout=crbm.CRBM_LAYOUT_STREAM)
+
+
 @pytest.mark.slow
 def test_bitplane_full_grid_sampled_chains(orc):
     """The L=18 grid at full size (12288 chains over 768 points) as the
@@ -105,7 +135,7 @@ def test_bitplane_differs_from_lane_uniforms():
 
 def test_bitplane_where_unsupported():
     ok = dict(J=[1.0], Jp=[1.0], h=[0.5], beta=[2.0])
-    for kw in (dict(L=9), dict(L=10, periodic=False), dict(L=20, layout=crbm.CRBM_LAYOUT_STREAM),
+    for kw in (dict(L=9), dict(L=10, periodic=False), dict(L=20, L_cols=12, layout=crbm.CRBM_LAYOUT_STREAM),
                dict(L=10, precision=crbm.CRBM_PRECISION_PAPER), dict(L=10, sq_every=2)):
         with pytest.raises(crbm.CrbmError) as e:
             crbm.Sampler(params=ok, n_chains=32, rng=BP, **kw)

@@ -51,7 +51,7 @@ MEASURED_TRAFFIC = {
     "grid_paper": (8.77e6 + 0.64e6, "per launch; profiles/k_sweep_canon_persistent_L18_grid_paper.md"),
     "stream_paper": (56.76e6 + 390.29e6 + 454.76e6 + 45.71e6, "per sweep (two launches); profiles/k_stream_L384.md"),
     "grid_bitplane": (2.81e6 + 0.65e6, "per launch; profiles/k_sweep_bitplane_L18_grid.md"),
-    "stream_bitplane": (None, "not captured for this kernel"),
+    "stream_bitplane": (56.90e6 + 82.46e6 + 141.79e6 + 29.12e6, "per sweep (two launches); profiles/k_stream_bp_L384.md"),
 }
 
 

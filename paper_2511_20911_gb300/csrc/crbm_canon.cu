@@ -32,14 +32,52 @@ __global__ void __launch_bounds__(CRBM_SWEEP_MAX_THREADS, CRBM_SWEEP_MIN_BLOCKS)
     k_sweep_canon_persistent(const SweepArgs a, int chunk, int* state) {
     __shared__ int s_word, s_chunk;
     const int n_chunks = (a.n_sweeps + chunk - 1) / chunk;
-    const int nw = a.n_words;
+    const int nw = a.n_words, nq = (nw + 3) / 4;
     const int K = a.measure_every;
     const int lane = threadIdx.x & 31;
     const unsigned int start = (blockIdx.x * 97u) % static_cast<unsigned int>(nw);
     for (;;) {
         if (threadIdx.x < 32) {
-            int word, c;
-            claim_word(state, nw, n_chunks, start, lane, word, c);
+            int word = -1, c = 0;
+            for (int tries = 0; tries < (1 << 20) && word < 0; ++tries) {
+                int best = 0x7fffffff, bk = 0x7fffffff, bw = -1;  // (chunks done, scan rank, word)
+                for (int q = lane; q < nq; q += 32) {
+                    const int4 v = __ldcg(reinterpret_cast<const int4*>(state) + q);
+                    const int sv[4] = {v.x, v.y, v.z, v.w};
+#pragma unroll
+                    for (int j = 0; j < 4; ++j) {
+                        const int w = 4 * q + j;
+                        const int dw = sv[j] >> 1;
+                        const int rank = static_cast<int>((static_cast<unsigned int>(w) + nw - start) %
+                                                          static_cast<unsigned int>(nw));
+                        if (w < nw && (sv[j] & 1) == 0 && dw < n_chunks &&
+                            (dw < best || (dw == best && rank < bk))) {
+                            best = dw;
+                            bk = rank;
+                            bw = w;
+                        }
+                    }
+                }
+#pragma unroll
+                for (int o = 16; o > 0; o >>= 1) {
+                    const int ob = __shfl_xor_sync(0xffffffffu, best, o);
+                    const int ok = __shfl_xor_sync(0xffffffffu, bk, o);
+                    const int ow = __shfl_xor_sync(0xffffffffu, bw, o);
+                    if (ob < best || (ob == best && ok < bk)) {
+                        best = ob;
+                        bk = ok;
+                        bw = ow;
+                    }
+                }
+                if (bw < 0) break;  // every unfinished word is held by a running CTA
+                if (lane == 0 && atomicCAS(state + bw, 2 * best, 2 * best + 1) == 2 * best) {
+                    __threadfence();  // acquire: the previous chunk's stores precede its release
+                    word = bw;
+                    c = best;
+                }
+                word = __shfl_sync(0xffffffffu, word, 0);
+                c = __shfl_sync(0xffffffffu, c, 0);
+            }
             if (lane == 0) {
                 s_word = word;
                 s_chunk = c;

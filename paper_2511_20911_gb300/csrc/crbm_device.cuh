@@ -143,7 +143,9 @@ __device__ __forceinline__ void st_release(int* p, int v) {
 }
 
 // Persistent scheduling of (word, chunk of sweeps) items: state[w] = 2 (chunks
-// of w done) + (1 while a CTA holds w).  Called by one whole warp: claims,
+// of w done) + (1 while a CTA holds w), as k_sweep_canon_persistent keeps it
+// (which has the same loop inline: its sweep compiles faster that way).
+// Called by one whole warp: claims,
 // with a compare-and-swap on state, the free word with the fewest chunks done
 // (all states scanned with 16-byte loads; ties go to the first word in the
 // scan order that starts at `start`).  Every lane returns the word (-1 when

@@ -232,7 +232,7 @@ def get_threads():
 
 def run_pt(L, params, chain_param, spins, slot_of_beta, seed, sweep0, n_sweeps, measure_every=1,
            swap_every=10, periodic=True, bonds=None, sums=None, series_cap=0,
-           precision=PRECISION_EXACT):
+           precision=PRECISION_EXACT, rng=RNG_LANE):
     """Parallel tempering on ladders of 32 chains (see orc_run_pt).  Advances
     ``spins`` (per slot) and ``slot_of_beta`` [n_ladders][32] in place; sums
     and series rows are per rung (chain index 32 l + k)."""
@@ -255,7 +255,8 @@ def run_pt(L, params, chain_param, spins, slot_of_beta, seed, sweep0, n_sweeps, 
                           ctypes.c_uint64(seed), ctypes.c_int64(sweep0), ctypes.c_int64(n_sweeps),
                           int(measure_every), int(swap_every), _p(spins, ctypes.c_int8),
                           _p(slot_of_beta, ctypes.c_int32), _p(sums, ctypes.c_int64),
-                          _p(series, ctypes.c_int32), ctypes.c_int64(series_cap), int(precision))
+                          _p(series, ctypes.c_int32), ctypes.c_int64(series_cap),
+                          int(precision) | (0x10 if rng == RNG_BITPLANE else 0))
     if rc:
         raise ValueError(f"orc_run_pt failed ({rc})")
     return sums, series

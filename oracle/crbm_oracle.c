@@ -578,7 +578,9 @@ static int run_pt_g(const orc_geom* g, const orc_bond* bonds, int nb, const doub
                     int32_t* slot_of_beta, int64_t* sums, int32_t* series, int64_t series_cap,
                     int precision) {
     if (n_chains <= 0 || n_chains % 32 || swap_every <= 0 || measure_every < 0) return -1;
-    if (precision & ORC_RNG_BITPLANE) return -1;
+    const int bitplane = (precision & ORC_RNG_BITPLANE) != 0;  /* replica r draws as chain 32 l + r */
+    precision &= ~ORC_RNG_BITPLANE;
+    if (bitplane && (precision != ORC_PRECISION_EXACT || nb > 10)) return -1;
     int n_lad = n_chains / 32, N = g->Lr * g->Lc;
     for (int l = 0; l < n_lad; ++l) {
         const int32_t* cp = chain_param + 32 * l;
@@ -602,6 +604,7 @@ static int run_pt_g(const orc_geom* g, const orc_bond* bonds, int nb, const doub
     for (int p = 0; p < n_params; ++p) {
         pts[p].Tv = tv + (size_t)p * nTv;
         pts[p].paper = precision == ORC_PRECISION_PAPER;
+        pts[p].bitplane = bitplane;
         pts[p].Tv_odd = pts[p].Tv;
         if (tables_g(g, bonds, nb, J[p], Jp[p], h[p], h[p], beta[p], precision, pts[p].Th, pts[p].Tv, NULL))
             err = 1;

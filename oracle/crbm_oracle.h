@@ -165,9 +165,9 @@ int orc_run_ex(int L, int periodic, const orc_bond* bonds, int nb,
  * and the node of hidden filter k is n = k, the node of the spin at window
  * offset (r, c) is n = 10 + 2r + c.  The unit is +1 iff u < t with the exact
  * thresholds, as in every other mode.  Selected by OR-ing ORC_RNG_BITPLANE
- * into the precision argument of the _ex and _rect samplers; it needs
- * ORC_PRECISION_EXACT, at most 10 filters, and is not offered with replica
- * exchange. */
+ * into the precision argument of the _ex and _rect samplers (replica exchange
+ * included: replica r of ladder l draws as chain 32 l + r, whichever rung it
+ * holds); it needs ORC_PRECISION_EXACT and at most 10 filters. */
 #define ORC_RNG_BITPLANE 0x10
 #define ORC_TAG_BITPLANE 256u
 

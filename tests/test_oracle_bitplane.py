@@ -81,3 +81,23 @@ def test_bitplane_chain_samples_boltzmann_L4(orc, J, Jp, h, beta):
     idx = {tuple(k): i for i, k in enumerate(keys)}
     obs = np.bincount([idx[tuple(g)] for g in got], minlength=len(keys)).astype(float)
     assert _chi2_p(obs, p) > 1e-3
+
+
+def test_bitplane_tempering_without_swaps_is_the_plain_chain(orc):
+    """Replica exchange whose first swap round lies beyond the run leaves every
+    replica on its rung, so each replica is the plain bit-plane chain of its
+    index: the ladder plumbing of the bit-plane mode against the pinned sampler."""
+    L, n = 6, 64
+    betas = list(0.3 * (10.0 ** (np.arange(32) / 31.0)))
+    params = dict(J=[1.0] * 32, Jp=[1.5] * 32, h=[0.5] * 32, beta=betas)
+    cp = np.tile(np.arange(32, dtype=np.int32), 2)
+    ids = np.arange(n, dtype=np.uint32)
+    a, b = orc.init_spins(L, ids, 8), orc.init_spins(L, ids, 8)
+    sob = np.tile(np.arange(32, dtype=np.int32), (2, 1))
+    orc.run_pt(L, params, cp, a, sob, 8, 0, 12, 0, swap_every=100, rng=orc.RNG_BITPLANE)
+    orc.run(L, params, cp, b, 8, 0, 12, 0, chain_ids=ids, rng=orc.RNG_BITPLANE)
+    assert np.array_equal(a, b)
+    c = orc.init_spins(L, ids, 8)                # and the swaps change the trajectory once they start
+    orc.run_pt(L, params, cp, c, np.tile(np.arange(32, dtype=np.int32), (2, 1)), 8, 0, 12, 0, swap_every=3,
+               rng=orc.RNG_BITPLANE)
+    assert not np.array_equal(a, c)

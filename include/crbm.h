@@ -155,9 +155,10 @@ typedef struct {
      * is decided (about 10 planes, 3 calls, per node and word instead of 8
      * calls for 32 separate uniforms).  Node n = k for hidden filter k, 10 +
      * 2r + c for the spin at window offset (r, c).  Needs the ten SS filters
-     * on an even periodic lattice (SMEM or streamed layout), exact precision,
-     * no replica exchange or correlations; not in batches or with block
-     * proposals.  A different random stream: the chains differ from
+     * on an even periodic lattice (SMEM or streamed layout; replica exchange
+     * in the SMEM layout, where slot l draws as chain 32 w + l whichever rung
+     * it holds), exact precision, no correlations; not in batches or with
+     * block proposals.  A different random stream: the chains differ from
      * CRBM_RNG_LANE's, with the same law. */
     int32_t rng;
 } crbm_params;

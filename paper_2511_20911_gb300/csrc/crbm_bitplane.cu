@@ -37,10 +37,12 @@ __host__ __device__ inline size_t bp_rec_words(const Geometry& g) {
     return (static_cast<size_t>(g.n_cells) * kBpNodes + 3 * static_cast<size_t>(g.N) + 3) & ~static_cast<size_t>(3);
 }
 
-// Shared memory, 32-bit words: running sums, planes and sign masks, counts,
-// replica identity, spins, hidden words (rounded up to whole uint4), then the
-// records when staged.
-constexpr int kBpSmemV = kAccWords + kBpTab + 96 + 32;
+// Shared memory, 32-bit words: running sums, the word's planes and sign masks
+// as built (bit l = rung l) and as used (bit l = the rung that slot l holds,
+// the identity without replica exchange), counts, the replica permutation
+// (rung -> slot, slot -> rung), spins, hidden words (rounded up to whole
+// uint4), then the records when staged.
+constexpr int kBpSmemV = kAccWords + 2 * kBpTab + 96 + 64;
 static_assert(kBpSmemV % 4 == 0, "spins start on a 16-byte boundary");
 __host__ __device__ inline size_t bp_hid_words(const Geometry& g) {
     return (static_cast<size_t>(g.n_cells) * kBpNodes + 3) & ~static_cast<size_t>(3);
@@ -55,7 +57,7 @@ __device__ __forceinline__ void plane_step(uint32_t U, uint32_t T, uint32_t& lt,
 
 // The sweeps of one claimed word: its planes, spins and sums in, n sweeps
 // from global sweep t0 (measurement index meas0), spins and sums out.
-template <bool kSmemRec>
+template <bool kSmemRec, bool kSwap>
 __device__ __forceinline__ void sweep_bitplane_body(const SweepArgs& a, const uint32_t* hrec, const uint32_t* vrec,
                                                     int word, uint32_t t0, int n_sweeps, int64_t meas) {
     extern __shared__ __align__(16) uint32_t smem[];
@@ -63,23 +65,38 @@ __device__ __forceinline__ void sweep_bitplane_body(const SweepArgs& a, const ui
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nwarp = blockDim.x >> 5;
     const int N = g.N, nh = g.n_cells * kBpNodes;
     int64_t* s_acc = reinterpret_cast<int64_t*>(smem);          // [kNSum][32] running sums
-    uint32_t* s_tab = smem + kAccWords;                          // [kBpTab] planes, sign masks
+    uint32_t* s_tab0 = smem + kAccWords;                         // [kBpTab] planes, sign masks by rung
+    uint32_t* s_tab = s_tab0 + kBpTab;                           // [kBpTab] the same by slot
     int* s_cnt = reinterpret_cast<int*>(s_tab + kBpTab);         // [3][32] measurement counts
-    int* s_sob = s_cnt + 96;                                     // [32] identity permutation
+    int* s_sob = s_cnt + 96;                                     // [32] slot of each rung
+    int* s_bos = s_sob + 32;                                     // [32] rung of each slot
     uint32_t* s_v = smem + kBpSmemV;                             // [N] spin words
     uint32_t* s_h = s_v + N;                                     // [n_cells * 10] hidden words
     const uint32_t* gt = a.ctab + static_cast<size_t>(word) * kCanonTab;
-    for (int x = threadIdx.x; x < kBpTab; x += blockDim.x) s_tab[x] = gt[x];
+    for (int x = threadIdx.x; x < kBpTab; x += blockDim.x) (kSwap ? s_tab0 : s_tab)[x] = gt[x];
     const uint32_t* gv = a.v + static_cast<size_t>(word) * N;
     for (int x = threadIdx.x; x < N; x += blockDim.x) s_v[x] = __ldcg(gv + x);
     for (int x = threadIdx.x; x < 96; x += blockDim.x) s_cnt[x] = 0;
-    if (warp == 0) s_sob[lane] = lane;
+    if (warp == 0) {  // replica permutation (identity without replica exchange)
+        const int sob = kSwap ? __ldcg(a.sob + word * 32 + lane) : lane;
+        s_sob[lane] = sob;
+        s_bos[sob] = lane;
+    }
+    // bit l of a plane as used = bit s_bos[l] of the plane as built
+    auto permute_planes = [&]() {
+        const uint32_t src = static_cast<uint32_t>(s_bos[lane]);
+        for (int x = warp; x < kBpTab; x += nwarp) s_tab[x] = __ballot_sync(0xffffffffu, (s_tab0[x] >> src) & 1u);
+    };
+    if (kSwap) {
+        __syncthreads();
+        permute_planes();
+    }
     const bool measuring = a.measure_every > 0;
     const uint32_t chain = static_cast<uint32_t>(word) * 32u + lane;
     if (measuring && warp == 0)
         for (int x = 0; x < kNSum; ++x) s_acc[x * 32 + lane] = __ldcg(a.sums + static_cast<size_t>(chain) * kNSum + x);
     __syncthreads();
-    const uint32_t fl0 = s_tab[kBpFlip], fl1 = s_tab[kBpFlip + 1];
+    uint32_t fl0 = s_tab[kBpFlip], fl1 = s_tab[kBpFlip + 1];
     // Philox round 0 of the word (counter word 2): shared by every call of the CTA
     const uint64_t pw = static_cast<uint64_t>(kPhiloxM1) * static_cast<uint32_t>(word);
     const uint32_t Yw = static_cast<uint32_t>(pw), hiW = static_cast<uint32_t>(pw >> 32) ^ a.rk[0];
@@ -87,6 +104,10 @@ __device__ __forceinline__ void sweep_bitplane_body(const SweepArgs& a, const ui
     for (int it = 0; it < n_sweeps; ++it) {
         const uint32_t t = t0 + static_cast<uint32_t>(it);
         const Round1Sweep rs = round1_sweep(hiW ^ t, a.rk);  // round 1's sweep-wide product
+        if (kSwap) {  // the sign masks follow the rungs
+            fl0 = s_tab[kBpFlip];
+            fl1 = s_tab[kBpFlip + 1];
+        }
         // hidden half-step (Eq. 9): thread = hidden node (cell, k)
         for (int base = warp * 32; base < nh; base += nwarp * 32) {
             const int node = base + lane;
@@ -166,7 +187,9 @@ __device__ __forceinline__ void sweep_bitplane_body(const SweepArgs& a, const ui
             if (valid) s_v[s] = lt;
         }
         __syncthreads();
-        if (measuring && (t + 1u) % static_cast<uint32_t>(a.measure_every) == 0u) {
+        const bool do_meas = measuring && (t + 1u) % static_cast<uint32_t>(a.measure_every) == 0u;
+        const bool do_swap = kSwap && (t + 1u) % static_cast<uint32_t>(a.swap_every) == 0u;
+        if (do_meas || do_swap) {
             // lane = chain: anti-aligned J and J' filters, +1 spins
             int anti0 = 0, anti1 = 0, pos = 0;
             for (int node = warp; node < nh; node += nwarp) {
@@ -180,11 +203,16 @@ __device__ __forceinline__ void sweep_bitplane_body(const SweepArgs& a, const ui
             atomicAdd(&s_cnt[32 + lane], anti1);
             atomicAdd(&s_cnt[64 + lane], pos);
             __syncthreads();
-            if (warp == 0) post_sweep_warp0(a, s_cnt, s_sob, s_sob, lane, word, t, true, false, meas, s_acc);
-            ++meas;
+            if (warp == 0) post_sweep_warp0(a, s_cnt, s_sob, s_bos, lane, word, t, do_meas, do_swap, meas, s_acc);
+            if (do_meas) ++meas;
             __syncthreads();
+            if (do_swap) {
+                permute_planes();
+                __syncthreads();
+            }
         }
     }
+    if (kSwap && warp == 0) a.sob[word * 32 + lane] = s_sob[lane];
     uint32_t* gvo = a.v + static_cast<size_t>(word) * N;
     for (int x = threadIdx.x; x < N; x += blockDim.x) gvo[x] = s_v[x];
     if (measuring && warp == 0)
@@ -193,7 +221,7 @@ __device__ __forceinline__ void sweep_bitplane_body(const SweepArgs& a, const ui
 
 // Persistent grid over (word, chunk of sweeps) items (claim_word): the node
 // records are staged once per CTA, then each claimed chunk runs the body.
-template <bool kSmemRec>
+template <bool kSmemRec, bool kSwap>
 __global__ void __launch_bounds__(kBpMaxThreads) k_sweep_bitplane(const SweepArgs a, int chunk, int* state) {
     extern __shared__ __align__(16) uint32_t smem[];
     __shared__ int s_word, s_chunk;
@@ -227,7 +255,7 @@ __global__ void __launch_bounds__(kBpMaxThreads) k_sweep_bitplane(const SweepArg
         const int n = min(chunk, a.n_sweeps - c * chunk);
         const int64_t meas0 =
             K > 0 ? a.meas0 + static_cast<int64_t>(t0 / K) - static_cast<int64_t>(a.t0 / K) : a.meas0;
-        sweep_bitplane_body<kSmemRec>(a, rec, rec + nh, word, t0, n, meas0);
+        sweep_bitplane_body<kSmemRec, kSwap>(a, rec, rec + nh, word, t0, n, meas0);
         __syncthreads();  // every thread's state stores are issued
         if (threadIdx.x == 0) {
             __threadfence();
@@ -247,7 +275,9 @@ cudaError_t launch_sweep_bitplane(const SweepArgs& a, int warps_per_cta, int chu
     const int warps = std::max(1, std::min(kBpMaxThreads / 32, warps_per_cta));
     const bool staged = smem_bytes_bitplane(a.g, true) <= 227 * 1024;
     const size_t smem = smem_bytes_bitplane(a.g, staged);
-    auto kernel = staged ? k_sweep_bitplane<true> : k_sweep_bitplane<false>;
+    const bool swap = a.swap_every > 0;  // replica exchange compiled in only where used
+    auto kernel = staged ? (swap ? k_sweep_bitplane<true, true> : k_sweep_bitplane<true, false>)
+                         : (swap ? k_sweep_bitplane<false, true> : k_sweep_bitplane<false, false>);
     cudaError_t e = cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, static_cast<int>(smem));
     int per_sm = 0, dev = 0, sms = 0;
     if (e == cudaSuccess) e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kernel, 32 * warps, smem);

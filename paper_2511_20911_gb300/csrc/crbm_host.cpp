@@ -331,11 +331,12 @@ int crbm_create(crbm_ctx** out, const crbm_params* p) {
         return fail(nullptr, CRBM_EINVAL, "unknown rng");
     }
     g.bitplane = p->rng == CRBM_RNG_BITPLANE ? 1 : 0;
-    if (g.bitplane && (!g.canonical || g.paper || p->swap_every > 0 || p->sq_every > 0)) {
+    if (g.bitplane && (!g.canonical || g.paper || p->sq_every > 0 ||
+                       (p->swap_every > 0 && p->layout == CRBM_LAYOUT_STREAM))) {
         delete ctx;
         return fail(nullptr, CRBM_EUNSUPPORTED,
                     "bit-plane uniforms need the ten SS filters on an even periodic lattice, exact precision, "
-                    "no replica exchange and no correlations");
+                    "no correlations, and the SMEM layout for replica exchange");
     }
     // AUTO: shared memory when the lattice, its hidden words and the tables fit
     // in one CTA's 227 KB, else the streamed layout (SS filters, even periodic L)

@@ -120,6 +120,31 @@ def test_bitplane_full_grid_sampled_chains(orc):
              measure_every=10, check_ids=ids)
 
 
+@pytest.mark.parametrize("L,n_lad,signs", [(8, 2, (1.0, 1.5)), (12, 3, (-1.0, 0.5))])
+def test_bitplane_tempering_bitexact(orc, L, n_lad, signs):
+    """Replica exchange with bit-plane uniforms: slot l of a ladder draws as
+    chain 32 w + l and reads the threshold planes of the rung it holds (the
+    planes are re-permuted after every swap round); spins, permutation and
+    sums against the oracle, with both coupling signs."""
+    J, Jp = signs
+    betas = 0.2 * (50.0 ** (np.arange(32) / 31.0))
+    params = dict(J=[J] * 32, Jp=[Jp] * 32, h=[0.75] * 32, beta=list(betas))
+    cp = np.tile(np.arange(32, dtype=np.int32), n_lad)
+    s = crbm.Sampler(L, params, 32 * n_lad, chain_param=cp, seed=6, measure_every=2, swap_every=3, rng=BP)
+    spins = orc.init_spins(L, np.arange(32 * n_lad, dtype=np.uint32), 6)
+    sob = np.tile(np.arange(32, dtype=np.int32), (n_lad, 1))
+    sums = None
+    t = 0
+    for k in (10, 17):
+        s.sweep(k)
+        sums, _ = orc.run_pt(L, params, cp, spins, sob, 6, t, k, 2, 3, sums=sums, rng=orc.RNG_BITPLANE)
+        t += k
+        assert np.array_equal(s.get_spins(), spins), f"spins after {t} sweeps"
+        assert np.array_equal(s.permutation().reshape(n_lad, 32), sob)
+    assert np.array_equal(s.observables(), sums)
+    assert (sob != np.arange(32)).any()
+
+
 def test_bitplane_differs_from_lane_uniforms():
     params = dict(J=[1.0], Jp=[1.5], h=[0.5], beta=[0.8])
     a = crbm.Sampler(12, params, 64, seed=3)
@@ -142,7 +167,8 @@ def test_bitplane_where_unsupported():
         assert e.value.code == crbm.CRBM_EUNSUPPORTED, kw
     ladder = dict(J=[1.0] * 32, Jp=[1.0] * 32, h=[0.5] * 32, beta=list(0.5 + 0.1 * np.arange(32)))
     with pytest.raises(crbm.CrbmError) as e:
-        crbm.Sampler(8, ladder, 32, chain_param=np.arange(32), swap_every=2, rng=BP)
+        crbm.Sampler(8, ladder, 32, chain_param=np.arange(32), swap_every=2, rng=BP,
+                     layout=crbm.CRBM_LAYOUT_STREAM)
     assert e.value.code == crbm.CRBM_EUNSUPPORTED
     with pytest.raises(crbm.CrbmError) as e:
         crbm.Sampler(8, ok, 32, rng=7)

@@ -87,8 +87,8 @@ def parse():
                     help="bitplane: uniforms from bit-plane words shared by the 32 chains of a word, compared "
                          "most significant bit first (grid workload)")
     args = ap.parse_args()
-    if args.rng == "bitplane" and (args.workload not in ("grid", "stream") or args.precision != "exact"):
-        ap.error("--rng bitplane runs the grid and stream workloads in exact precision")
+    if args.rng == "bitplane" and (args.workload not in ("grid", "stream", "phase") or args.precision != "exact"):
+        ap.error("--rng bitplane runs the grid, stream and phase workloads in exact precision")
     if args.precision == "paper" and args.workload not in ("grid", "stream"):
         ap.error("--precision paper runs the grid and stream workloads only")
     return args
@@ -338,7 +338,8 @@ def run_phase(args, rank, ws):
     w = workloads.phase_scan_workload()
     L, R, N = w["L"], w["rungs"], w["L"] ** 2
     s = crbm.Sampler(L, w["params"], w["n_chains"], chain_param=w["chain_param"], seed=replica_seed(w["seed"], rank),
-                     measure_every=w["measure_every"], swap_every=w["swap_every"], layout=crbm.CRBM_LAYOUT_SMEM)
+                     measure_every=w["measure_every"], swap_every=w["swap_every"], layout=crbm.CRBM_LAYOUT_SMEM,
+                     rng=crbm.CRBM_RNG_BITPLANE if args.rng == "bitplane" else crbm.CRBM_RNG_LANE)
     e_gs, labels = [], []
     for J, Jp, h in w["points"]:
         E, (a, b), pattern = analysis.ground_state_energy(L, J, Jp, h)
@@ -381,7 +382,8 @@ def run_phase(args, rank, ws):
            "config": {"workload": "ground-state phase scan: L=18, J=1, J'/J in [0,3] step 1/4, h in [-8,8] step 1/2 "
                                   f"(429 points) x 32-rung replica-exchange ladders (beta 0.25..8, swaps every "
                                   f"{w['swap_every']} sweeps), {S} sweeps, ground states by brute force over even "
-                                  "supercells of <= 16 sites", "parallelism": f"replicas x{ws}"},
+                                  "supercells of <= 16 sites" + ("; bit-plane uniforms" if args.rng == "bitplane"
+                                                                  else ""), "parallelism": f"replicas x{ws}"},
            "clocks": clk.summary(),
            "phase_scan": {"points": len(first), "solved": int((first >= 0).sum()), "by_phase": by_phase,
                           "map": rows,

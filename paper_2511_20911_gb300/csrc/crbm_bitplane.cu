@@ -21,7 +21,7 @@
 // these select one of the 5 x 2 visible thresholds per chain.
 #include <algorithm>
 
-#include "crbm_device.cuh"
+#include "crbm_bitplane_core.cuh"
 
 namespace crbm {
 namespace {
@@ -46,13 +46,6 @@ constexpr int kBpSmemV = kAccWords + 2 * kBpTab + 96 + 64;
 static_assert(kBpSmemV % 4 == 0, "spins start on a 16-byte boundary");
 __host__ __device__ inline size_t bp_hid_words(const Geometry& g) {
     return (static_cast<size_t>(g.n_cells) * kBpNodes + 3) & ~static_cast<size_t>(3);
-}
-
-// One plane of the word-parallel comparison: lt collects the chains whose
-// uniform is below the threshold, eq the chains still undecided.
-__device__ __forceinline__ void plane_step(uint32_t U, uint32_t T, uint32_t& lt, uint32_t& eq) {
-    lt |= eq & T & ~U;
-    eq &= ~(T ^ U);
 }
 
 // The sweeps of one claimed word: its planes, spins and sums in, n sweeps
@@ -127,11 +120,7 @@ __device__ __forceinline__ void sweep_bitplane_body(const SweepArgs& a, const ui
             const uint32_t c2 = static_cast<uint32_t>(pc >> 32) ^ a.rk[1] ^ (kTagBitplane + 8u * k);
             uint32_t lt = 0u, eq = valid ? 0xffffffffu : 0u;
             auto planes = [&](const U4& q, uint32_t j) {
-                const uint32_t* tb = tp + 4u * j;
-                plane_step(q.x, (P & tb[64]) | (M & tb[0]) | (j == 0u ? Z : 0u), lt, eq);
-                plane_step(q.y, (P & tb[65]) | (M & tb[1]), lt, eq);
-                plane_step(q.z, (P & tb[66]) | (M & tb[2]), lt, eq);
-                plane_step(q.w, (P & tb[67]) | (M & tb[3]), lt, eq);
+                bp::hidden_planes(q, tp + 4u * j, P, M, j == 0u ? Z : 0u, lt, eq);
             };
             // calls 0 and 1 together (a group of 32 nodes nearly always needs both:
             // all 1024 comparisons close within 4 planes with probability
@@ -159,9 +148,7 @@ __device__ __forceinline__ void sweep_bitplane_body(const SweepArgs& a, const ui
             const uint32_t hp = hin(r2w, fl1);
             const uint32_t cell = (r2w >> 16) & 0xFFFu, x = r2w >> 28;
             // count of +1 among h0..h3 = c0 + 2 c1 + 4 c2, bit-sliced
-            const uint32_t s01 = h0 ^ h1, a01 = h0 & h1, s23 = h2 ^ h3, a23 = h2 & h3;
-            const uint32_t c0 = s01 ^ s23, cy = s01 & s23;
-            const uint32_t c1 = a01 ^ a23 ^ cy, cc2 = (a01 & a23) | (cy & (a01 | a23));
+            const bp::Count4 n4 = bp::count4(h0, h1, h2, h3);
             const uint32_t* tv = s_tab + kBpVisPlanes;  // [count][J' bit][32]
             const uint64_t pc = static_cast<uint64_t>(kPhiloxM0) * cell;
             const Round2Cell r2 = round2_cell(rs.hik ^ static_cast<uint32_t>(pc));
@@ -170,14 +157,7 @@ __device__ __forceinline__ void sweep_bitplane_body(const SweepArgs& a, const ui
             auto planes = [&](const U4& q, uint32_t j) {
                 const uint32_t u[4] = {q.x, q.y, q.z, q.w};
 #pragma unroll
-                for (int i = 0; i < 4; ++i) {
-                    const uint32_t* tb = tv + 4u * j + i;
-                    // the count's threshold plane by a mux tree: J' bit, then count bits 0, 1, 2
-                    auto sel = [&](int c) { return (hp & tb[(2 * c + 1) * 32]) | (~hp & tb[2 * c * 32]); };
-                    const uint32_t m01 = (c0 & sel(1)) | (~c0 & sel(0)), m23 = (c0 & sel(3)) | (~c0 & sel(2));
-                    const uint32_t T = (cc2 & sel(4)) | (~cc2 & ((c1 & m23) | (~c1 & m01)));
-                    plane_step(u[i], T, lt, eq);
-                }
+                for (int i = 0; i < 4; ++i) bp::plane_step(u[i], bp::visible_plane(tv + 4u * j + i, hp, n4), lt, eq);
             };
 #pragma unroll 1
             for (uint32_t j = 0; j < 8u; ++j) {

@@ -8,6 +8,7 @@
 // paper precision (kPaper) the hidden half-step makes the tag-0 and tag-1
 // calls and the visible half-step draws the tag-1 call again for its four
 // 16-bit uniforms: three calls per cell instead of four.
+#include "crbm_bitplane_core.cuh"
 #include "crbm_canon_core.cuh"
 
 namespace crbm {
@@ -229,11 +230,6 @@ __global__ void __launch_bounds__(kStreamVisThreads, CRBM_STREAM_VIS_MIN_BLOCKS)
 // the half-word, and the hidden units travel through HBM bit-sliced, one
 // word per (cell, filter): h[word][cell][10].
 
-__device__ __forceinline__ void bp_plane_step(uint32_t U, uint32_t T, uint32_t& lt, uint32_t& eq) {
-    lt |= eq & T & ~U;
-    eq &= ~(T ^ U);
-}
-
 // Hidden half-step of one tile: the spin tile (halo included) in, the tile's
 // hidden words out.
 __global__ void __launch_bounds__(kStreamThreads) k_stream_bp_hidden(const SweepArgs a, uint32_t t) {
@@ -279,13 +275,7 @@ __global__ void __launch_bounds__(kStreamThreads) k_stream_bp_hidden(const Sweep
         const Round2Cell r2 = round2_cell(rs.hik ^ static_cast<uint32_t>(pc));
         const uint32_t c2 = static_cast<uint32_t>(pc >> 32) ^ a.rk[1] ^ (kTagBitplane + 8u * static_cast<uint32_t>(k));
         uint32_t lt = 0u, eq = valid ? 0xffffffffu : 0u;
-        auto planes = [&](const U4& q, uint32_t j) {
-            const uint32_t* tb = tp + 4u * j;
-            bp_plane_step(q.x, (P & tb[64]) | (M & tb[0]) | (j == 0u ? Z : 0u), lt, eq);
-            bp_plane_step(q.y, (P & tb[65]) | (M & tb[1]), lt, eq);
-            bp_plane_step(q.z, (P & tb[66]) | (M & tb[2]), lt, eq);
-            bp_plane_step(q.w, (P & tb[67]) | (M & tb[3]), lt, eq);
-        };
+        auto planes = [&](const U4& q, uint32_t j) { bp::hidden_planes(q, tp + 4u * j, P, M, j == 0u ? Z : 0u, lt, eq); };
         const U4 q0 = philox_from_round2(Yw, rs, r2, c2, a.rk);
         const U4 q1 = philox_from_round2(Yw, rs, r2, c2 ^ 1u, a.rk);
         planes(q0, 0u);
@@ -372,9 +362,7 @@ __global__ void __launch_bounds__(kStreamVisThreads) k_stream_bp_visible(const S
         };
         const uint32_t h0 = hin(s_inc[x][0], fl0), h1 = hin(s_inc[x][1], fl0), h2 = hin(s_inc[x][2], fl0),
                        h3 = hin(s_inc[x][3], fl0), hp = hin(s_inc[x][4], fl1);
-        const uint32_t s01 = h0 ^ h1, a01 = h0 & h1, s23 = h2 ^ h3, a23 = h2 & h3;
-        const uint32_t c0 = s01 ^ s23, cy = s01 & s23;
-        const uint32_t c1 = a01 ^ a23 ^ cy, cc2 = (a01 & a23) | (cy & (a01 | a23));
+        const bp::Count4 n4 = bp::count4(h0, h1, h2, h3);
         const uint32_t cell = static_cast<uint32_t>((i0 + (R >> 1)) * W + j0 + (C >> 1));
         const uint64_t pc = static_cast<uint64_t>(kPhiloxM0) * cell;
         const Round2Cell r2 = round2_cell(rs.hik ^ static_cast<uint32_t>(pc));
@@ -384,12 +372,7 @@ __global__ void __launch_bounds__(kStreamVisThreads) k_stream_bp_visible(const S
         auto planes = [&](const U4& q, uint32_t j) {
             const uint32_t u[4] = {q.x, q.y, q.z, q.w};
 #pragma unroll
-            for (int i = 0; i < 4; ++i) {
-                const uint32_t* tb = tv + 4u * j + i;
-                auto sel = [&](int c) { return (hp & tb[(2 * c + 1) * 32]) | (~hp & tb[2 * c * 32]); };
-                const uint32_t m01 = (c0 & sel(1)) | (~c0 & sel(0)), m23 = (c0 & sel(3)) | (~c0 & sel(2));
-                bp_plane_step(u[i], (cc2 & sel(4)) | (~cc2 & ((c1 & m23) | (~c1 & m01))), lt, eq);
-            }
+            for (int i = 0; i < 4; ++i) bp::plane_step(u[i], bp::visible_plane(tv + 4u * j + i, hp, n4), lt, eq);
         };
 #pragma unroll 1
         for (uint32_t j = 0; j < 8u; ++j) {

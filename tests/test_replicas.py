@@ -56,3 +56,25 @@ def test_single_rank_is_identity():
     import bench
     assert bench.max_over_ranks(2.5, 1) == 2.5
     assert bench.replica_seed(7, 0) == 7
+
+
+def test_bitplane_expected_calls_matches_a_simulation():
+    """The bit-plane roofline counts the expected Philox calls of the early
+    exit: per warp of up to 32 nodes x 32 chains, calls of four planes while
+    any comparison is open.  A direct simulation of that comparison (random
+    uniforms and thresholds, bits drawn plane by plane) must give the same
+    mean call count."""
+    import numpy as np
+    import bench
+    rng = np.random.default_rng(3)
+    for lanes in (32, 10):
+        trials, calls = 4000, 0
+        for _ in range(trials):
+            u = rng.integers(0, 2**32, size=(lanes, 32), dtype=np.uint64)
+            t = rng.integers(0, 2**32, size=(lanes, 32), dtype=np.uint64)
+            diff = u ^ t                                   # first differing bit decides
+            first = np.where(diff == 0, 32, 31 - np.floor(np.log2(np.maximum(diff, 1))).astype(int))
+            planes = int(first.max()) + 1                  # planes until every comparison is decided
+            calls += min(8, (planes + 3) // 4)
+        expect = bench.bitplane_expected_calls(lanes) / lanes
+        assert abs(calls / trials - expect) < 0.03, (lanes, calls / trials, expect)

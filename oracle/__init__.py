@@ -343,3 +343,47 @@ def random_net(seed, scale=0.3):
     w[864:880] *= 0.1
     w[3184:3200] *= 0.1
     return w
+
+
+PASS_REC = np.dtype([("logit", np.float64, 16), ("thr", np.uint32, 16), ("bR", np.int32),
+                     ("bC", np.int32), ("cur_bits", np.uint32), ("new_bits", np.uint32),
+                     ("dE", np.int64), ("log_alpha", np.float64), ("u_accept", np.float64),
+                     ("accept", np.int32), ("pad", np.int32)])
+
+
+def prop_pass(spins, params, chain_param, w, seed, pass_index, apply=False, logits=None):
+    """One pass of learned block moves (see orc_prop_pass): records
+    [n_blocks][n_chains] of PASS_REC; with apply, accepted blocks are written
+    into ``spins`` [n_chains][L][L] in place.  logits: optional
+    [n_blocks][n_chains][16] used instead of the net."""
+    assert spins.dtype == np.int8 and spins.flags.c_contiguous
+    n, L = spins.shape[0], spins.shape[-1]
+    J = np.ascontiguousarray(params["J"], np.float64)
+    Jp = np.ascontiguousarray(params["Jp"], np.float64)
+    h = np.ascontiguousarray(params["h"], np.float64)
+    beta = np.ascontiguousarray(params["beta"], np.float64)
+    cp = np.ascontiguousarray(chain_param, np.int32)
+    w = np.ascontiguousarray(w, np.float64)
+    nb1 = max(1, L // 8)
+    rec = np.zeros((nb1 * nb1, n), PASS_REC)
+    lg = None if logits is None else np.ascontiguousarray(logits, np.float64)
+    if lg is not None:
+        assert lg.shape == (nb1 * nb1, n, 16)
+    f = lib().orc_prop_pass
+    f.restype = ctypes.c_int
+    rc = f(L, _p(spins, ctypes.c_int8), n, _p(J, ctypes.c_double), _p(Jp, ctypes.c_double),
+           _p(h, ctypes.c_double), _p(beta, ctypes.c_double), _p(cp, ctypes.c_int32),
+           _p(w, ctypes.c_double), _p(lg, ctypes.c_double), ctypes.c_uint64(seed),
+           ctypes.c_uint32(pass_index), int(bool(apply)), rec.ctypes.data_as(ctypes.c_void_p))
+    if rc < 0:
+        raise ValueError(f"orc_prop_pass failed ({rc})")
+    return rec
+
+
+def structure_factor(spins):
+    """S(q) [Lr][Lc] of one configuration (orc_structure_factor)."""
+    v = np.ascontiguousarray(spins, np.int8)
+    Lr, Lc = v.shape
+    out = np.zeros((Lr, Lc), np.float64)
+    lib().orc_structure_factor(Lr, Lc, _p(v, ctypes.c_int8), _p(out, ctypes.c_double))
+    return out

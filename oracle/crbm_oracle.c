@@ -333,6 +333,13 @@ static void add_structure_factor(int Lr, int Lc, const int8_t* v, double* sq) {
         }
 }
 
+/* S(q) of one configuration alone (sq overwritten), the function the sampler
+ * accumulates every sq_every sweeps. */
+void orc_structure_factor(int Lr, int Lc, const int8_t* v, double* sq) {
+    for (int i = 0; i < Lr * Lc; ++i) sq[i] = 0.0;
+    add_structure_factor(Lr, Lc, v, sq);
+}
+
 /* ------------------------------------------------------------ sampling */
 typedef struct {
     uint32_t Th[10];
@@ -733,7 +740,9 @@ int orc_get_threads(void) {
 }
 
 /* ------------------------------------------------ learned block proposal */
-/* Round a double to the nearest bfloat16 (8-bit mantissa), ties to even. */
+/* bfloat16 rounding as the GPU applies it to fp32 values: x is first rounded
+ * to float (exact for every float-valued x), then to the nearest bfloat16
+ * (8 significant bits), ties to even; infinities and NaN pass through. */
 double orc_bf16(double x) {
     float f = (float)x;
     uint32_t u;
@@ -1021,4 +1030,104 @@ int orc_mh_rows(int L, const int8_t* v, int n, int bR, int bC, int k, const doub
                        probs + ((size_t)i << (k * k))))
             err = 1;
     return err ? -1 : 0;
+}
+
+/* One pass of learned block moves (no counterpart in the paper: the learned
+ * proposal mixed with the block Gibbs sweeps of Sec. II.B).  The steps, in
+ * order, for every block b of the pass and every chain c:
+ *   1. origin: nb1 = max(1, L / 8) blocks per side at spacing L / nb1, shifted
+ *      by words 0 and 1 of Philox((pass, 0, 0, ORC_TAG_PROP_OFFSET));
+ *   2. logits of the net on the patch (orc_patch_input, bf16 on, beta and h
+ *      rounded to bf16 as net inputs), or the given ones;
+ *   3. t_s = clamp(nearbyint(2^32 sigmoid(logit_s)), 1, 2^32 - 1); site s
+ *      proposes +1 iff word s % 4 of Philox((b, pass, c, ORC_TAG_PROP_BITS +
+ *      s / 4)) < t_s;
+ *   4. dE of the proposed block (orc_block_delta_e), log alpha = -beta dE / 16
+ *      + sum_s log q(x_s) - sum_s log q(x'_s) with q(+1) = t_s / 2^32 and
+ *      q(-1) = 1 - t_s / 2^32 (the exact beta, not its bf16 rounding);
+ *   5. u = (word 0 of Philox((b, pass, c, ORC_TAG_PROP_ACCEPT)) >> 8) / 2^24;
+ *      accept iff log alpha >= 0 or u < exp(log alpha);
+ *   6. with apply != 0, accepted blocks are written into v.
+ * Blocks of one pass are at least 8 sites apart, so with L >= 10 no block
+ * lies in another's patch or energy halo and the order of the moves does not
+ * matter.  rec[b * n_chains + c] receives the record; logits_in (NULL: run
+ * the net) is [n_blocks][n_chains][16].  Returns the number of blocks, or a
+ * negative error. */
+int orc_prop_pass(int L, int8_t* v, int n_chains, const double* J, const double* Jp,
+                  const double* h, const double* beta, const int32_t* chain_param,
+                  const double* w, const double* logits_in, uint64_t seed, uint32_t pass,
+                  int apply, orc_pass_rec* rec) {
+    const int k = 4, K2 = 16, P = k + 6;
+    if (L < 10 || (L & 1) || n_chains < 1) return -1;
+    int nb1 = L / 8 > 1 ? L / 8 : 1;
+    int spacing = L / nb1, n_blocks = nb1 * nb1;
+    uint32_t key[2] = {(uint32_t)(seed & 0xffffffffu), (uint32_t)(seed >> 32)};
+    uint32_t ctr[4] = {pass, 0u, 0u, ORC_TAG_PROP_OFFSET}, off[4];
+    orc_philox4x32_10(ctr, key, off);
+    int err = 0;
+#pragma omp parallel for schedule(dynamic, 1)
+    for (int c = 0; c < n_chains; ++c) {
+        int p = chain_param[c];
+        int32_t qJ, qJp, qh;
+        if (orc_quantize(J[p], &qJ) || orc_quantize(Jp[p], &qJp) || orc_quantize(h[p], &qh)) {
+            err = 1;
+            continue;
+        }
+        int8_t* vc = v + (size_t)c * L * L;
+        double input[6 * 10 * 10];
+        for (int b = 0; b < n_blocks; ++b) {
+            orc_pass_rec* r = rec + (size_t)b * n_chains + c;
+            int bR = (int)((off[0] % (uint32_t)L + (uint32_t)(spacing * (b / nb1))) % (uint32_t)L);
+            int bC = (int)((off[1] % (uint32_t)L + (uint32_t)(spacing * (b % nb1))) % (uint32_t)L);
+            r->bR = bR;
+            r->bC = bC;
+            if (logits_in) {
+                for (int s = 0; s < K2; ++s) r->logit[s] = logits_in[((size_t)b * n_chains + c) * K2 + s];
+            } else {
+                orc_patch_input(L, vc, bR, bC, k, orc_bf16(beta[p]), orc_bf16(h[p]), input);
+                orc_net_forward(k, w, input, 1, r->logit);
+            }
+            (void)P;
+            uint32_t draws[16];
+            for (int call = 0; call < 4; ++call) {
+                uint32_t cc[4] = {(uint32_t)b, pass, (uint32_t)c, ORC_TAG_PROP_BITS + (uint32_t)call}, o[4];
+                orc_philox4x32_10(cc, key, o);
+                for (int j = 0; j < 4; ++j) draws[4 * call + j] = o[j];
+            }
+            uint32_t cur = 0, nw = 0;
+            double logq_cur = 0.0, logq_new = 0.0;
+            int8_t nb[16];
+            for (int s = 0; s < K2; ++s) {
+                double q = 1.0 / (1.0 + exp(-r->logit[s]));
+                double t = nearbyint(ldexp(q, 32));
+                if (t < 1.0) t = 1.0;
+                if (t > 4294967295.0) t = 4294967295.0;
+                r->thr[s] = (uint32_t)t;
+                double pq = ldexp(t, -32);
+                int xc = vc[((bR + s / k) % L) * L + (bC + s % k) % L] > 0;
+                int xn = draws[s] < (uint32_t)t;
+                cur |= (uint32_t)xc << s;
+                nw |= (uint32_t)xn << s;
+                nb[s] = xn ? 1 : -1;
+                logq_cur += xc ? log(pq) : log1p(-pq);
+                logq_new += xn ? log(pq) : log1p(-pq);
+            }
+            r->cur_bits = cur;
+            r->new_bits = nw;
+            r->dE = orc_block_delta_e(L, vc, bR, bC, k, nb, qJ, qJp, qh);
+            r->log_alpha = -beta[p] * (double)r->dE / 16.0 + logq_cur - logq_new;
+            uint32_t ca[4] = {(uint32_t)b, pass, (uint32_t)c, ORC_TAG_PROP_ACCEPT}, oa[4];
+            orc_philox4x32_10(ca, key, oa);
+            r->u_accept = ldexp((double)(oa[0] >> 8), -24);
+            r->accept = r->log_alpha >= 0.0 || r->u_accept < exp(r->log_alpha);
+        }
+        if (apply)
+            for (int b = 0; b < n_blocks; ++b) {
+                const orc_pass_rec* r = rec + (size_t)b * n_chains + c;
+                if (!r->accept) continue;
+                for (int s = 0; s < K2; ++s)
+                    vc[((r->bR + s / k) % L) * L + (r->bC + s % k) % L] = ((r->new_bits >> s) & 1u) ? 1 : -1;
+            }
+    }
+    return err ? -1 : n_blocks;
 }

@@ -242,6 +242,30 @@ int64_t orc_block_delta_e(int L, const int8_t* v, int bR, int bC, int k, const i
                           int32_t qJ, int32_t qJp, int32_t qh);
 int orc_mh_row(int L, const int8_t* v, int bR, int bC, int k, const double* w, double J,
                double Jp, double h, double beta, int bf16, double* probs);
+
+/* One pass of block moves over n_chains chains, keyed as the library keys
+ * it (see orc_prop_pass in crbm_oracle.c for the steps); needs L >= 10. */
+#define ORC_TAG_PROP_OFFSET 8u
+#define ORC_TAG_PROP_BITS 9u
+#define ORC_TAG_PROP_ACCEPT 13u
+typedef struct {
+    double logit[16];
+    uint32_t thr[16];     /* t_s: site s proposes +1 iff its draw < t_s */
+    int32_t bR, bC;       /* block origin */
+    uint32_t cur_bits, new_bits;  /* bit s = site (s / 4, s % 4) is +1 */
+    int64_t dE;           /* exact energy change of the proposal, 1/16 units */
+    double log_alpha, u_accept;
+    int32_t accept;
+    int32_t pad;
+} orc_pass_rec;
+int orc_prop_pass(int L, int8_t* v, int n_chains, const double* J, const double* Jp,
+                  const double* h, const double* beta, const int32_t* chain_param,
+                  const double* w, const double* logits_in, uint64_t seed, uint32_t pass,
+                  int apply, orc_pass_rec* rec);
+
+/* S(q) = |sum_r s_r e^{i q.r}|^2 / N of one configuration [Lr][Lc] at
+ * q = 2 pi (nR / Lr, nC / Lc), into sq[nR][nC]. */
+void orc_structure_factor(int Lr, int Lc, const int8_t* v, double* sq);
 #ifdef __cplusplus
 }
 #endif

@@ -102,3 +102,41 @@ def supercell_ground_energy(L, J, Jp, h, max_sites=18):
             if best is None or E[i] < best[0]:
                 best = (float(E[i]), states[i].reshape(L, L).copy())
     return best
+
+
+def transfer_matrix_sample(L, J, Jp, h, beta, n, rng):
+    """n independent exact samples [n][L][L] (+-1, int8) of the even-L
+    periodic SS Ising model at (J, J', h, beta), drawn row by row from the
+    same row transfer matrices as transfer_matrix_moments:
+    P(r_0 .. r_{L-1}) is proportional to prod_R A_R(r_R, r_{R+1}) with
+    r_L = r_0; r_0 is drawn from diag(A_0 ... A_{L-1}), then each r_R given
+    r_{R-1} and r_0 from A_{R-1}(r_{R-1}, .) (A_R ... A_{L-1})(., r_0)."""
+    assert L % 2 == 0 and L <= 8
+    nr = 1 << L
+    rows = np.array([[1 if (x >> C) & 1 else -1 for C in range(L)] for x in range(nr)],
+                    dtype=np.float64)
+    e_row = J * (rows * np.roll(rows, -1, axis=1)).sum(1) - h * rows.sum(1)
+    vert = J * rows @ rows.T
+    even = np.zeros((nr, nr))
+    odd = np.zeros((nr, nr))
+    for C in range(0, L, 2):
+        even += Jp * np.outer(rows[:, C], rows[:, (C + 1) % L])
+        odd += Jp * np.outer(rows[:, C], rows[:, (C - 1) % L])
+    es = [e_row[:, None] + vert + (even if R % 2 == 0 else odd) for R in range(L)]
+    emin = min(e.min() for e in es)
+    A = [np.exp(-beta * (e - emin)) for e in es]
+    suffix = [None] * (L + 1)             # suffix[R] = A_R ... A_{L-1}, normalised
+    suffix[L] = np.eye(nr)
+    for R in range(L - 1, -1, -1):
+        m = A[R] @ suffix[R + 1]
+        suffix[R] = m / m.max()
+    out = np.zeros((n, L, L), np.int8)
+    for i in range(n):
+        p0 = np.clip(np.diag(suffix[0]), 0, None)
+        r0 = rng.choice(nr, p=p0 / p0.sum())
+        seq = [r0]
+        for R in range(1, L):
+            w = A[R - 1][seq[-1], :] * suffix[R][:, r0]
+            seq.append(rng.choice(nr, p=w / w.sum()))
+        out[i] = rows[seq].astype(np.int8)
+    return out

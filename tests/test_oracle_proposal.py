@@ -102,3 +102,117 @@ def test_mh_block_move_is_exactly_stationary(orc, origin, use_bf16):
     assert np.abs(flow - pi).max() < 1e-14, np.abs(flow - pi).max()
     # a real move happens: the net does not propose the current block surely
     assert (1 - rows[np.arange(len(rows)), ((V[:, sites] > 0) << np.arange(4)).sum(1)]).mean() > 0.05
+
+
+def _pass_setup(orc, L=12, n=24, seed=31):
+    rng = np.random.default_rng(seed)
+    params = dict(J=[1.0, 1.0], Jp=[1.0, 1.5], h=[3.0, 0.5], beta=[0.6, 1.3])
+    cp = rng.integers(0, 2, n).astype(np.int32)
+    spins = rng.choice(np.array([-1, 1], np.int8), size=(n, L, L))
+    return params, cp, spins
+
+
+def test_pass_matches_the_pinned_transition_kernel(orc):
+    """Each record of a pass is one draw of the block move whose exact kernel
+    orc_mh_row enumerates (and which the L=4 test above pins by exact
+    stationarity): for the proposed block y != x, q(y) min(1, exp(log alpha))
+    equals the kernel entry K(x -> y); the origin, current block and dE agree
+    with the lattice."""
+    L = 12
+    params, cp, spins = _pass_setup(orc, L)
+    w = orc.random_net(17, scale=0.15)
+    rec = orc.prop_pass(spins.copy(), params, cp, w, seed=5, pass_index=3)
+    assert rec.shape == (1, len(cp))
+    for c in range(8):
+        r = rec[0, c]
+        p = cp[c]
+        bR, bC = int(r["bR"]), int(r["bC"])
+        cur = sum(1 << s for s in range(16) if spins[c, (bR + s // 4) % L, (bC + s % 4) % L] > 0)
+        assert int(r["cur_bits"]) == cur
+        nb = np.array([1 if (int(r["new_bits"]) >> s) & 1 else -1 for s in range(16)], np.int8)
+        assert int(r["dE"]) == orc.block_delta_e(spins[c], bR, bC, nb, params["J"][p],
+                                                 params["Jp"][p], params["h"][p])
+        if int(r["new_bits"]) == cur:
+            continue
+        pr = r["thr"].astype(np.float64) / 2.0 ** 32
+        bits = (int(r["new_bits"]) >> np.arange(16)) & 1
+        q_new = np.prod(np.where(bits == 1, pr, 1 - pr))
+        k = orc.mh_rows(spins[c][None], bR, bC, 4, w, params["J"][p], params["Jp"][p],
+                        params["h"][p], params["beta"][p], use_bf16=True)[0]
+        ours = q_new * min(1.0, np.exp(r["log_alpha"]))
+        assert abs(ours - k[int(r["new_bits"])]) <= 1e-12 * k[int(r["new_bits"])] + 1e-300, (c, ours)
+
+
+def test_pass_draws_and_accepts_follow_their_laws(orc):
+    """With the logits fixed, each site of a proposal is +1 with probability
+    t_s / 2^32 independently of the other sites, and a move is accepted with
+    probability min(1, exp(log alpha)): binomial checks of every site and
+    every pair of sites over 2000 chains x 16 passes (a Philox word shared by
+    two sites fails the pair check)."""
+    from scipy.stats import chi2
+    L, n, passes = 12, 2000, 16
+    params, cp, spins = _pass_setup(orc, L, n, seed=4)
+    rng = np.random.default_rng(8)
+    logits = rng.normal(0.0, 1.5, (1, n, 16))
+    ones = np.zeros(16)
+    pair = np.zeros((16, 16))              # sites s and s' both +1
+    acc, exp_acc, var_acc = 0, 0.0, 0.0
+    p_exp = None
+    for ps in range(passes):
+        rec = orc.prop_pass(spins.copy(), params, cp, None, seed=9, pass_index=ps, logits=logits)[0]
+        bits = ((rec["new_bits"][:, None] >> np.arange(16)) & 1).astype(np.float64)
+        ones += bits.sum(0)
+        pair += bits.T @ bits
+        pr = rec["thr"].astype(np.float64) / 2.0 ** 32
+        if p_exp is None:
+            p_exp = pr
+        assert np.array_equal(pr, p_exp)   # same logits -> same thresholds
+        a = np.minimum(1.0, np.exp(rec["log_alpha"]))
+        acc += int(rec["accept"].sum())
+        exp_acc += a.sum()
+        var_acc += (a * (1 - a)).sum()
+    e1 = p_exp.sum(0) * passes
+    v1 = (p_exp * (1 - p_exp)).sum(0) * passes
+    stat = ((ones - e1) ** 2 / v1).sum()
+    assert chi2.sf(stat, 16) > 1e-3, stat
+    iu = np.triu_indices(16, 1)
+    pp = p_exp[:, :, None] * p_exp[:, None, :]
+    e2 = pp.sum(0)[iu] * passes
+    v2 = (pp * (1 - pp)).sum(0)[iu] * passes
+    stat2 = ((pair[iu] - e2) ** 2 / v2).sum()
+    assert chi2.sf(stat2, len(e2)) > 1e-3, stat2
+    assert abs(acc - exp_acc) < 4 * np.sqrt(var_acc), (acc, exp_acc, var_acc)
+
+
+def test_pass_applies_exactly_the_accepted_moves(orc):
+    """apply = 1 writes the proposed block of every accepted record and
+    nothing else; each chain's energy changes by the sum of its accepted dE
+    (full SS energies of the test's own geometry, two blocks per side at
+    L = 18 so the moves of a pass must not interfere)."""
+    L = 18
+    params, cp, spins = _pass_setup(orc, L, n=40, seed=6)
+    w = orc.random_net(2, scale=0.1)
+    before = spins.copy()
+    rec = orc.prop_pass(spins, params, cp, w, seed=3, pass_index=11, apply=True)
+    assert rec.shape == (4, 40)
+    assert rec["accept"].any() and not rec["accept"].all()
+    expect = before.copy()
+    for b in range(4):
+        for c in range(40):
+            r = rec[b, c]
+            if r["accept"]:
+                for s in range(16):
+                    expect[c, (r["bR"] + s // 4) % L, (r["bC"] + s % 4) % L] = \
+                        1 if (int(r["new_bits"]) >> s) & 1 else -1
+    assert np.array_equal(spins, expect)
+    q = lambda x: round(16 * x)
+    for c in range(40):
+        p = cp[c]
+        (a0, b0, m0), (a1, b1, m1) = [tuple(x[0] for x in ss_counts_batch(st.reshape(1, -1), L))
+                                      for st in (before[c], spins[c])]
+        e0 = q(params["J"][p]) * a0 + q(params["Jp"][p]) * b0 - q(params["h"][p]) * m0
+        e1 = q(params["J"][p]) * a1 + q(params["Jp"][p]) * b1 - q(params["h"][p]) * m1
+        assert e1 - e0 == int(rec["dE"][:, c][rec["accept"][:, c] == 1].sum())
+    # origins: two per side, spaced L / 2 apart
+    assert len(set(rec["bR"][:, 0])) == 2 and len(set(rec["bC"][:, 0])) == 2
+    assert (rec["bR"][2, 0] - rec["bR"][0, 0]) % L == 9 and (rec["bC"][1, 0] - rec["bC"][0, 0]) % L == 9

@@ -80,6 +80,11 @@ def parse():
     ap.add_argument("--measure-every", type=int, default=10)
     ap.add_argument("--cpu-seconds", type=float, default=8.0)
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-extra-lines", action="store_true",
+                    help="grid workload: skip the L=384 streamed line printed inside the same JSON line")
+    ap.add_argument("--sq-every", type=int, default=None,
+                    help="structure-factor accumulation every K sweeps (grid default 100, the grid "
+                         "workload's estimator; 0 = off)")
     ap.add_argument("--precision", default="exact", choices=["exact", "paper"],
                     help="paper: the FPGA's 10-bit weights, 16-bit sigmoid table and 16-bit uniforms "
                          "(grid and stream workloads)")
@@ -181,15 +186,34 @@ def workload_config(name, rank):
 DEFAULT_SWEEPS = {"grid": 2000, "stream": 20, "batch": 500, "proposal": 1000, "tts": 4000, "phase": 4000}
 
 
-def cpu_baseline(w, seconds, precision=0, rng=0):
+def cpu_model():
+    """The host CPU's model name (lscpu, else /proc/cpuinfo)."""
+    try:
+        out = subprocess.run(["lscpu"], capture_output=True, text=True, timeout=10).stdout
+        for line in out.splitlines():
+            if line.strip().startswith("Model name:"):
+                return line.split(":", 1)[1].strip()
+    except (OSError, subprocess.SubprocessError):
+        pass
+    try:
+        with open("/proc/cpuinfo") as f:
+            for line in f:
+                if line.lower().startswith(("model name", "cpu part")):
+                    return line.split(":", 1)[1].strip()
+    except OSError:
+        pass
+    return None
+
+
+def cpu_baseline(w, seconds, precision=0, rng=0, one_core=True):
     """The oracle as it stands, OpenMP over chains on every host core, on a
-    bounded sample of the same workload (a spread subset of its chains)."""
+    bounded sample of the same workload (a spread subset of its chains); then
+    the same on one core for a third of the time."""
     import oracle
     oracle.build()
     n_all = w["n_chains"]
     L = w["L"]
     cores = os.cpu_count() or 1
-    oracle.set_threads(cores)
 
     def run(n_ch, n_sw):
         ids = np.linspace(0, n_all - 1, n_ch).astype(np.uint32)
@@ -199,17 +223,29 @@ def cpu_baseline(w, seconds, precision=0, rng=0):
         oracle.run(L, w["params"], cp, sp, w["seed"], 0, n_sw, 10, chain_ids=ids, precision=precision, rng=rng)
         return time.perf_counter() - t
 
+    def timed(threads, n_ch, budget):
+        oracle.set_threads(threads)
+        sw0 = 20 if L <= 64 else 1
+        dt = run(n_ch, sw0)
+        while dt < 0.2 and sw0 < (1 << 20):   # calibrate on at least 0.2 s of work
+            sw0 *= 4
+            dt = run(n_ch, sw0)
+        n_sw = max(sw0, int(sw0 * budget / max(dt, 1e-3)))
+        dt = run(n_ch, n_sw)
+        return n_ch * n_sw * L * L / dt, n_ch, n_sw, dt
+
     small = L <= 64
-    n_ch = 16 * cores if small else cores
-    sw0 = 20 if small else 1
-    dt = run(n_ch, sw0)
-    n_sw = max(sw0, int(sw0 * seconds / max(dt, 1e-3)))
-    dt = run(n_ch, n_sw)
-    value = n_ch * n_sw * L * L / dt
-    return {"value": value, "unit": UNIT, "cores": oracle.get_threads(), "kind": "oracle",
-            "seconds": dt,
-            "sample": f"{n_ch} of the {n_all} chains (spread over all parameter points), "
-                      f"{n_sw} sweeps, measure every 10, {dt:.1f} s wall"}
+    value, n_ch, n_sw, dt = timed(cores, 16 * cores if small else cores, seconds)
+    out = {"value": value, "unit": UNIT, "cores": oracle.get_threads(), "kind": "oracle",
+           "cpu_model": cpu_model(), "seconds": dt,
+           "sample": f"{n_ch} of the {n_all} chains (spread over all parameter points), "
+                     f"{n_sw} sweeps, measure every 10, {dt:.1f} s wall"}
+    if one_core:
+        v1, n1, s1, d1 = timed(1, 16 if small else 1, seconds / 3)
+        out["one_core"] = {"value": v1, "unit": UNIT,
+                           "sample": f"{n1} chains, {s1} sweeps, one thread, {d1:.1f} s wall"}
+    oracle.set_threads(cores)
+    return out
 
 
 def run_reference(args, rank, ws):
@@ -224,8 +260,8 @@ def run_reference(args, rank, ws):
     per_step = max(1.0, 60.0 / max(1, args.steps + args.warmup))
     prec, rng = (1 if args.precision == "paper" else 0), (1 if args.rng == "bitplane" else 0)
     for _ in range(args.warmup):
-        cpu_baseline(w, min(per_step, 2.0), prec, rng)
-    vals = [cpu_baseline(w, per_step, prec, rng) for _ in range(args.steps)]
+        cpu_baseline(w, min(per_step, 2.0), prec, rng, one_core=False)
+    vals = [cpu_baseline(w, per_step, prec, rng, one_core=False) for _ in range(args.steps)]
     v = float(np.mean([x["value"] for x in vals]))
     cb = dict(vals[-1])
     cb["value"] = v
@@ -239,8 +275,9 @@ def run_reference(args, rank, ws):
         "e2e": {"value": v, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}))
 
 
-def config_dict(w, args):
-    if args.workload == "grid":
+def config_dict(w, args, workload=None):
+    workload = workload or args.workload
+    if workload == "grid":
         desc = ("L=18 periodic SS grid: J'/J in {0.5,1,2} x 16 beta in [0.1,5] x 16 h in [0,4] "
                 "x 16 chains, SMEM-resident")
     else:
@@ -255,7 +292,7 @@ def config_dict(w, args):
     return {"workload": desc, "L": w["L"], "n_chains": w["n_chains"],
             "n_params": len(w["params"]["J"]), "sweeps_per_step": args.sweeps_per_step,
             "measure_every": args.measure_every,
-            "layout": "smem (persistent, dynamically scheduled)" if args.workload == "grid" else "stream",
+            "layout": "smem (persistent, dynamically scheduled)" if workload == "grid" else "stream",
             "l2": "flushed between steps (256 MiB write outside the step events)",
             "parallelism": f"replicas x{args.gpus}"}
 
@@ -542,42 +579,54 @@ def run_proposal(args, rank, ws):
         print(json.dumps(line))
 
 
-def main():
-    args = parse()
-    if args.sweeps_per_step is None:
-        args.sweeps_per_step = DEFAULT_SWEEPS[args.workload]
-    rank, ws = dist_setup(args)
-    if args.impl == "reference":
-        run_reference(args, rank, ws)
-        return
-    if args.workload == "batch":
-        run_batch(args, rank, ws)
-        return
-    if args.workload == "proposal":
-        run_proposal(args, rank, ws)
-        return
-    if args.workload == "tts":
-        run_tts(args, rank, ws)
-        return
-    if args.workload == "phase":
-        run_phase(args, rank, ws)
-        return
+def philox_peak(dev, sm_max_mhz):
+    """Measured integer-multiply ceiling: the library's Philox throughput probe
+    (crbm_philox_stream, 20 wide products per call, none shareable) on 8 CTAs
+    of 256 threads per SM, best of 5 timed launches after 2 warm-ups."""
+    import torch
+    import paper_2511_20911_gb300 as crbm
+    sms = torch.cuda.get_device_properties(dev).multi_processor_count
+    nb, th, calls = sms * 8, 256, 4096
+    sink = torch.zeros(nb * th, dtype=torch.int32, device="cuda")
+    st = torch.cuda.current_stream()
+    best = None
+    for k in range(7):
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        a.record(st)
+        crbm.crbm_philox_stream(sink, nb, th, calls, seed=k)
+        b.record(st)
+        torch.cuda.synchronize()
+        if k >= 2:
+            t = a.elapsed_time(b) / 1e3
+            best = t if best is None else min(best, t)
+    rate = nb * th * calls / best
+    derived = sms * IMUL_LANES_PER_SM_CLK * sm_max_mhz * 1e6
+    return {"philox_calls_per_s": rate, "mul_ops_per_s": rate * MUL_OPS_PER_CALL, "sms": sms,
+            "derived_mul_ops_per_s": derived, "probe": f"crbm_philox_stream {nb}x{th} threads x {calls} calls, "
+                                                      "best of 5 launches"}
+
+
+def measure_sampler(args, workload, rank, ws, with_e2e=True, sq_every=0):
+    """One timed line of the grid (L=18, SMEM) or stream (L=384, HBM) workload:
+    W warm-up steps, K timed steps of S sweeps with CUDA events on the
+    library's stream, L2 flushed between steps, clocks sampled meanwhile."""
     import torch
     import paper_2511_20911_gb300 as crbm
     from paper_2511_20911_gb300 import analysis
 
     dev = torch.cuda.current_device()
-    w = workload_config(args.workload, rank)
-    S, K, W = args.sweeps_per_step, args.steps, args.warmup
+    w = workload_config(workload, rank)
+    S = args.sweeps_per_step if workload == args.workload else DEFAULT_SWEEPS[workload]
+    K, W = args.steps, args.warmup
     n_meas = S * K // args.measure_every
-    layout = crbm.CRBM_LAYOUT_SMEM if args.workload == "grid" else crbm.CRBM_LAYOUT_STREAM
+    layout = crbm.CRBM_LAYOUT_SMEM if workload == "grid" else crbm.CRBM_LAYOUT_STREAM
     paper = args.precision == "paper"
     bitplane = args.rng == "bitplane"
     s = crbm.Sampler(w["L"], w["params"], w["n_chains"], chain_param=w["chain_param"], seed=w["seed"],
-                     measure_every=args.measure_every, series_len=n_meas, layout=layout,
+                     measure_every=args.measure_every, series_len=n_meas, layout=layout, sq_every=sq_every,
                      precision=crbm.CRBM_PRECISION_PAPER if paper else crbm.CRBM_PRECISION_EXACT,
                      rng=crbm.CRBM_RNG_BITPLANE if bitplane else crbm.CRBM_RNG_LANE)
-    tuned_warps = s.autotune(200) if args.workload == "grid" else None  # CTA shape, on scratch copies
+    tuned_warps = s.autotune(200) if workload == "grid" else None  # CTA shape, on scratch copies
     stream = torch.cuda.current_stream()
     flush = torch.empty(256 * 1024 * 1024, dtype=torch.uint8, device="cuda")
     for _ in range(W):
@@ -616,47 +665,65 @@ def main():
         ess_m = float(analysis.effective_samples(Mx).sum())
     else:                      # too few measurements in the timed steps for a windowed estimate
         ess_E = ess_m = float("nan")
+    sq_info = None
+    if sq_every:
+        sq = s.structure_factor()                      # [n_params][L][L]
+        _, ns = s.correlations()
+        sq_info = {"every_sweeps": sq_every, "samples_per_point": int(np.min(ns)),
+                   "note": "per-point S(q) = (1/N)<|sum_r s_r e^{iq.r}|^2> accumulated on the device "
+                           "inside the timed steps",
+                   "max_S_over_N": float(sq[:, :, :].max() / w["L"] ** 2)}
 
-    # end to end through the C ABI with host buffers: set spins (H2D), sweep,
-    # read observables (D2H), every step
-    spins_h = s.get_spins()
-    obs_h = np.zeros((w["n_chains"], crbm.CRBM_NSUM), np.int64)
-    torch.cuda.synchronize()
-    t0 = time.perf_counter()
-    for k in range(max(1, K // 2)):
-        s.set_spins(spins_h)
-        s.sweep(S)
-        obs_h[:] = s.observables()
-    e2e_t = time.perf_counter() - t0
-    e2e_steps = max(1, K // 2)
-    e2e_val = w["n_chains"] * w["L"] ** 2 * S * e2e_steps * ws / e2e_t
+    e2e = None
+    if with_e2e:
+        # end to end through the C ABI with host buffers: set spins (H2D),
+        # sweep, read observables (D2H), every step
+        spins_h = s.get_spins()
+        obs_h = np.zeros((w["n_chains"], crbm.CRBM_NSUM), np.int64)
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        e2e_steps = max(1, K // 2)
+        for k in range(e2e_steps):
+            s.set_spins(spins_h)
+            s.sweep(S)
+            obs_h[:] = s.observables()
+        e2e_t = time.perf_counter() - t0
+        e2e = {"value": w["n_chains"] * w["L"] ** 2 * S * e2e_steps * ws / e2e_t, "unit": UNIT,
+               "h2d_bytes_per_step": int(spins_h.nbytes), "d2h_bytes_per_step": int(obs_h.nbytes)}
 
     cpc = CALLS_PER_CELL
     if paper:
-        cpc = CALLS_PER_CELL_PAPER if args.workload == "grid" else CALLS_PER_CELL_PAPER_STREAM
+        cpc = CALLS_PER_CELL_PAPER if workload == "grid" else CALLS_PER_CELL_PAPER_STREAM
     calls = cpc * (w["L"] // 2) ** 2 * w["n_chains"] * S
     if bitplane:   # expected calls of the early-exit comparison (hidden nodes, then spins)
-        W = w["L"] // 2
-        if args.workload == "grid":   # one CTA per word: its nodes in groups of 32
+        Wc = w["L"] // 2
+        if workload == "grid":   # one CTA per word: its nodes in groups of 32
             n_words = (w["n_chains"] + 31) // 32
-            per_word = bitplane_expected_calls(10 * W * W) + bitplane_expected_calls(w["L"] ** 2)
-        else:                         # 64-chain groups of two words; 16 x 16-cell tiles
+            per_word = bitplane_expected_calls(10 * Wc * Wc) + bitplane_expected_calls(w["L"] ** 2)
+        else:                    # 64-chain groups of two words; 16 x 16-cell tiles
             n_words = 2 * ((w["n_chains"] + 63) // 64)
             per_word = 0.0
-            for ti in range(0, W, 16):
-                for tj in range(0, W, 16):
-                    cells = min(16, W - ti) * min(16, W - tj)
+            for ti in range(0, Wc, 16):
+                for tj in range(0, Wc, 16):
+                    cells = min(16, Wc - ti) * min(16, Wc - tj)
                     per_word += bitplane_expected_calls(10 * cells) + bitplane_expected_calls(4 * cells)
         calls = per_word * n_words * S
         cpc = calls / ((w["L"] // 2) ** 2 * w["n_chains"] * S)
-    if args.workload == "grid":   # one launch per step: spins in and out once
+    if workload == "grid":   # one launch per step: spins in and out once
         hbm_bytes = w["n_chains"] * w["L"] ** 2 / 8 * 2
-    else:                         # per sweep: spins read + written, hidden written + read
+    else:                    # per sweep: spins read + written, hidden written + read
         hbm_bytes = w["n_chains"] * w["L"] ** 2 * 7 / 8 * S
+    ck = clk.summary()
+    sm_max = ck["sm_max_mhz"] or SM_MAX_MHZ
+    pk = philox_peak(dev, sm_max)
     achieved = MUL_OPS_PER_CALL * calls / (t_total / K) / 1e12
-    peak = SM_COUNT * IMUL_LANES_PER_SM_CLK * SM_MAX_MHZ * 1e6 / 1e12
-    traffic = MEASURED_TRAFFIC[args.workload + ("_paper" if paper else "") + ("_bitplane" if bitplane else "")]
-    cfg = config_dict(w, args)
+    peak = pk["derived_mul_ops_per_s"] / 1e12
+    traffic = MEASURED_TRAFFIC.get(workload + ("_paper" if paper else "") + ("_bitplane" if bitplane else "") +
+                                   ("_sq" if sq_every else ""))
+    cfg = config_dict(w, args, workload)
+    cfg["sweeps_per_step"] = S
+    if sq_every:
+        cfg["sq_every"] = sq_every
     if tuned_warps:
         cfg["warps_per_cta_autotuned"] = tuned_warps
     out = {
@@ -668,24 +735,69 @@ def main():
                       "method": "Sokal windowing c=5 on per-chain series (every "
                                 f"{args.measure_every} sweeps), first 10% discarded, summed over chains"},
         "node_updates_per_s": value * 3.5,
-        "clocks": clk.summary(),
-        "e2e": {"value": e2e_val, "unit": UNIT, "h2d_bytes_per_step": int(spins_h.nbytes),
-                "d2h_bytes_per_step": int(obs_h.nbytes)},
+        "clocks": ck,
         "gpu_launches": int(launches),
-        "hbm": {"algorithmic_gbs": hbm_bytes / (t_total / K) / 1e9, "peak_gbs": 6797.9,
+        "hbm": {"algorithmic_gbs": hbm_bytes / (t_total / K) / 1e9, "peak_gbs": 6790.0,
                 "note": "0.25 B (SMEM layout: spins in and out once per launch) or 0.875 B "
                         "(streamed: spins 2 bits + hidden 5 bits per spin-update) of algorithmic traffic"},
         "roofline": {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "Tops/s",
-                     "frac": achieved / peak, "traffic": traffic[0],
-                     "traffic_unit": "bytes " + traffic[1],
-                     "note": "integer-multiply ceiling: 152 SM x 64 lanes/clk x 2070 MHz; 40 "
+                     "frac": achieved / peak,
+                     "peak_measured": pk["mul_ops_per_s"] / 1e12,
+                     "frac_of_measured": achieved / (pk["mul_ops_per_s"] / 1e12),
+                     "peak_probe": pk["probe"],
+                     "traffic": traffic[0] if traffic else None,
+                     "traffic_unit": "bytes " + traffic[1] if traffic else None,
+                     "note": f"integer-multiply ceiling: {pk['sms']} SM x 64 lanes/clk x {sm_max:.0f} MHz "
+                             "(peak) and the library's Philox throughput probe (peak_measured); 40 "
                              "multiply ops per Philox-4x32-10 call, "
                              f"{cpc:.3g} calls per chain-cell-sweep" + (" (expected count of the bit-plane "
                              "early exit)" if bitplane else ""),
                      "philox_calls_per_s": calls / (t_total / K)},
     }
+    if e2e:
+        out["e2e"] = e2e
+    if sq_info:
+        out["structure_factor"] = sq_info
+    s.close()
+    del flush
+    torch.cuda.empty_cache()
+    return out
+
+
+def main():
+    args = parse()
+    if args.sweeps_per_step is None:
+        args.sweeps_per_step = DEFAULT_SWEEPS[args.workload]
+    rank, ws = dist_setup(args)
+    if args.impl == "reference":
+        run_reference(args, rank, ws)
+        return
+    if args.workload == "batch":
+        run_batch(args, rank, ws)
+        return
+    if args.workload == "proposal":
+        run_proposal(args, rank, ws)
+        return
+    if args.workload == "tts":
+        run_tts(args, rank, ws)
+        return
+    if args.workload == "phase":
+        run_phase(args, rank, ws)
+        return
+    import torch
+    sq_every = 100 if args.workload == "grid" and args.sq_every is None else (args.sq_every or 0)
+    if args.rng == "bitplane" or args.workload != "grid":
+        sq_every = 0            # correlations: lane uniforms, SMEM layout
+    out = measure_sampler(args, args.workload, rank, ws, with_e2e=True, sq_every=sq_every)
+    if args.workload == "grid" and not args.no_extra_lines:
+        sub = measure_sampler(args, "stream", rank, ws, with_e2e=False)
+        out["lines"] = {"stream_L384": {k: sub[k] for k in ("value", "unit", "ms_per_step", "steps", "warmup",
+                                                             "config", "clocks", "gpu_launches", "hbm",
+                                                             "roofline")}}
     if rank == 0 and not args.no_cpu_baseline:
-        out["cpu_baseline"] = cpu_baseline(w, args.cpu_seconds, 1 if paper else 0, 1 if bitplane else 0)
+        w = workload_config(args.workload, 0)
+        out["cpu_baseline"] = cpu_baseline(w, args.cpu_seconds, 1 if args.precision == "paper" else 0,
+                                           1 if args.rng == "bitplane" else 0)
     if rank == 0:
         print(json.dumps(out))
     if ws > 1:

@@ -99,7 +99,7 @@ typedef struct {
     /* chain -> parameter point (host array of n_chains), NULL -> contiguous
      * equal blocks: p(c) = c * n_params / n_chains */
     const int32_t* chain_param;
-    int32_t n_chains;       /* >= 1 */
+    int32_t n_chains;       /* 1 .. 2^30 */
     uint64_t seed;          /* Philox key */
     int32_t measure_every;  /* accumulate observables after every K-th sweep, 0 = never */
     int32_t series_len;     /* per-chain time-series capacity in measurements, 0 = none */
@@ -262,6 +262,17 @@ int crbm_load(crbm_ctx* ctx, const void* buf, size_t n);
  * keys every draw; synchronous.  Errors: CRBM_EINVAL, CRBM_ENOMEM, CRBM_ECUDA. */
 int crbm_philox(const uint32_t* in, uint32_t* out, size_t n);
 
+/* Philox throughput probe (integer-multiply ceiling of this path): device
+ * sink[n_blocks * threads] (caller-owned), thread t of the launch runs `calls`
+ * Philox-4x32-10 calls with key = (seed lo, seed hi) on the counters
+ * (i, t, i ^ t, 0x9E3779B9), i = 0 .. calls - 1, and stores the XOR of all
+ * their output words in sink[t].  Each call is 20 32x32->64 products, none
+ * shareable between calls.  Asynchronous on `stream` (a cudaStream_t, NULL =
+ * legacy); time it with events there.  threads a multiple of 32 in 32..1024.
+ * Errors: CRBM_EINVAL, CRBM_ECUDA. */
+int crbm_philox_stream(uint32_t* sink, int32_t n_blocks, int32_t threads, int32_t calls, uint64_t seed,
+                       void* stream);
+
 /* Batched sweeps: several SMEM-layout contexts -- mixed lattice sizes,
  * filter lists and tempering ladders -- advanced together by ONE kernel
  * launch plus a one-thread clock update, captured once in a CUDA graph and
@@ -307,15 +318,24 @@ void crbm_batch_destroy(crbm_batch* batch);
  * Parameter order (3345 floats): W1[16][6][3][3], b1[16], W2[16][16][3][3],
  * b2[16], W3[16][3][3], b3.
  * Contexts used with proposals need the ten SS filters, an even periodic
- * lattice, the SMEM layout and no replica exchange (else CRBM_EUNSUPPORTED).
+ * lattice of side L >= 10 (so that a patch does not wrap onto its own
+ * block), the SMEM layout and no replica exchange (else CRBM_EUNSUPPORTED).
+ * Keying of a pass (Philox key = the context's seed): block b of pass P has
+ * origin (o0 % L + S (b / n), o1 % L + S (b % n)) mod L, n = max(1, L / 8)
+ * blocks per side, S = L / n, (o0, o1) = words 0, 1 of Philox((P, 0, 0, 8));
+ * site s of chain c proposes +1 iff word s % 4 of Philox((b, P, c, 9 + s / 4))
+ * is below thr[s] = clamp(2^32 q_s, 1, 2^32 - 256); the move is accepted iff
+ * log alpha >= 0 or (word 0 of Philox((b, P, c, 13)) >> 8) / 2^24 <
+ * exp(log alpha).
  * Errors of these functions: see crbm_proposal_last_error(). */
 typedef struct crbm_proposal crbm_proposal;
 typedef struct {
     float logit[16];
     int32_t dE;               /* exact energy change of the proposed block, 1/16 units */
     uint32_t cur_bits, new_bits; /* bit s = site (s / 4, s % 4) of the block is +1 */
-    float log_alpha;
+    float log_alpha;          /* -beta dE / 16 + sum log q(current) - sum log q(proposed) */
     int32_t bR, bC;           /* block origin */
+    uint32_t thr[16];         /* site s proposes +1 iff its Philox draw < thr[s] */
 } crbm_pass_record;
 /* New net with seeded He-style weights; block must be 4. */
 int crbm_proposal_create(crbm_proposal** out, int32_t block, uint64_t seed);
@@ -376,11 +396,14 @@ const char* crbm_proposal_last_error(void);
  * behind (each call rewrites all of it that it reads), so calls that overlap
  * on the GPU -- on different streams, or from several threads -- race.
  * The first call on a device fetches the array's device address
- * (cudaGetSymbolAddress, with that device current); make that first call
- * before any stream capture.  Asynchronous on p->stream apart from the table
- * upload from host memory.  No cudaMalloc, cudaFree or other allocation.
+ * (cudaGetSymbolAddress, with that device current; a failed lookup is tried
+ * again by the next call); make that first call before any stream capture.
+ * Asynchronous on p->stream apart from the table upload: every call copies
+ * the lane tables from pageable host memory, one cudaMemcpyAsync per 32-chain
+ * word, and each of those copies may wait on p->stream.  No cudaMalloc,
+ * cudaFree or other allocation.
  * Errors (code only, crbm_last_error is not updated): CRBM_EINVAL (bad
- * arguments or parameters), CRBM_EUNSUPPORTED (needs more scratch than
+ * arguments or parameters, n_chains outside 1..2^30), CRBM_EUNSUPPORTED (needs more scratch than
  * CRBM_NOALLOC_SCRATCH_BYTES), CRBM_ECUDA. */
 int crbm_sweep_stream_noalloc(const crbm_params* p, uint32_t* v, int64_t sweep0, int64_t n_sweeps);
 

@@ -345,17 +345,19 @@ def random_net(seed, scale=0.3):
     return w
 
 
-PASS_REC = np.dtype([("logit", np.float64, 16), ("thr", np.uint32, 16), ("bR", np.int32),
+PASS_REC = np.dtype([("logit", np.float64, 16), ("thr", np.uint32, 16), ("draw", np.uint32, 16),
+                     ("bR", np.int32),
                      ("bC", np.int32), ("cur_bits", np.uint32), ("new_bits", np.uint32),
                      ("dE", np.int64), ("log_alpha", np.float64), ("u_accept", np.float64),
                      ("accept", np.int32), ("pad", np.int32)])
 
 
-def prop_pass(spins, params, chain_param, w, seed, pass_index, apply=False, logits=None):
+def prop_pass(spins, params, chain_param, w, seed, pass_index, apply=False, logits=None, thr=None):
     """One pass of learned block moves (see orc_prop_pass): records
     [n_blocks][n_chains] of PASS_REC; with apply, accepted blocks are written
     into ``spins`` [n_chains][L][L] in place.  logits: optional
-    [n_blocks][n_chains][16] used instead of the net."""
+    [n_blocks][n_chains][16] used instead of the net; thr: optional
+    [n_blocks][n_chains][16] thresholds used instead of the logits' ones."""
     assert spins.dtype == np.int8 and spins.flags.c_contiguous
     n, L = spins.shape[0], spins.shape[-1]
     J = np.ascontiguousarray(params["J"], np.float64)
@@ -369,11 +371,15 @@ def prop_pass(spins, params, chain_param, w, seed, pass_index, apply=False, logi
     lg = None if logits is None else np.ascontiguousarray(logits, np.float64)
     if lg is not None:
         assert lg.shape == (nb1 * nb1, n, 16)
+    th = None if thr is None else np.ascontiguousarray(thr, np.uint32)
+    if th is not None:
+        assert th.shape == (nb1 * nb1, n, 16)
     f = lib().orc_prop_pass
     f.restype = ctypes.c_int
     rc = f(L, _p(spins, ctypes.c_int8), n, _p(J, ctypes.c_double), _p(Jp, ctypes.c_double),
            _p(h, ctypes.c_double), _p(beta, ctypes.c_double), _p(cp, ctypes.c_int32),
-           _p(w, ctypes.c_double), _p(lg, ctypes.c_double), ctypes.c_uint64(seed),
+           _p(w, ctypes.c_double), _p(lg, ctypes.c_double), _p(th, ctypes.c_uint32),
+           ctypes.c_uint64(seed),
            ctypes.c_uint32(pass_index), int(bool(apply)), rec.ctypes.data_as(ctypes.c_void_p))
     if rc < 0:
         raise ValueError(f"orc_prop_pass failed ({rc})")

@@ -1051,13 +1051,15 @@ int orc_mh_rows(int L, const int8_t* v, int n, int bR, int bC, int k, const doub
  * Blocks of one pass are at least 8 sites apart, so with L >= 10 no block
  * lies in another's patch or energy halo and the order of the moves does not
  * matter.  rec[b * n_chains + c] receives the record; logits_in (NULL: run
- * the net) is [n_blocks][n_chains][16].  Returns the number of blocks, or a
- * negative error. */
+ * the net) is [n_blocks][n_chains][16]; thr_in (NULL: step 3's thresholds)
+ * [n_blocks][n_chains][16] replaces the thresholds, so that a test can feed
+ * another implementation's thresholds and compare the remaining steps.
+ * Returns the number of blocks, or a negative error. */
 int orc_prop_pass(int L, int8_t* v, int n_chains, const double* J, const double* Jp,
                   const double* h, const double* beta, const int32_t* chain_param,
-                  const double* w, const double* logits_in, uint64_t seed, uint32_t pass,
-                  int apply, orc_pass_rec* rec) {
-    const int k = 4, K2 = 16, P = k + 6;
+                  const double* w, const double* logits_in, const uint32_t* thr_in,
+                  uint64_t seed, uint32_t pass, int apply, orc_pass_rec* rec) {
+    const int k = 4, K2 = 16;
     if (L < 10 || (L & 1) || n_chains < 1) return -1;
     int nb1 = L / 8 > 1 ? L / 8 : 1;
     int spacing = L / nb1, n_blocks = nb1 * nb1;
@@ -1087,7 +1089,6 @@ int orc_prop_pass(int L, int8_t* v, int n_chains, const double* J, const double*
                 orc_patch_input(L, vc, bR, bC, k, orc_bf16(beta[p]), orc_bf16(h[p]), input);
                 orc_net_forward(k, w, input, 1, r->logit);
             }
-            (void)P;
             uint32_t draws[16];
             for (int call = 0; call < 4; ++call) {
                 uint32_t cc[4] = {(uint32_t)b, pass, (uint32_t)c, ORC_TAG_PROP_BITS + (uint32_t)call}, o[4];
@@ -1102,7 +1103,9 @@ int orc_prop_pass(int L, int8_t* v, int n_chains, const double* J, const double*
                 double t = nearbyint(ldexp(q, 32));
                 if (t < 1.0) t = 1.0;
                 if (t > 4294967295.0) t = 4294967295.0;
+                if (thr_in) t = (double)thr_in[((size_t)b * n_chains + c) * K2 + s];
                 r->thr[s] = (uint32_t)t;
+                r->draw[s] = draws[s];
                 double pq = ldexp(t, -32);
                 int xc = vc[((bR + s / k) % L) * L + (bC + s % k) % L] > 0;
                 int xn = draws[s] < (uint32_t)t;

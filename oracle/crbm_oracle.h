@@ -251,6 +251,7 @@ int orc_mh_row(int L, const int8_t* v, int bR, int bC, int k, const double* w, d
 typedef struct {
     double logit[16];
     uint32_t thr[16];     /* t_s: site s proposes +1 iff its draw < t_s */
+    uint32_t draw[16];    /* the Philox draw of site s */
     int32_t bR, bC;       /* block origin */
     uint32_t cur_bits, new_bits;  /* bit s = site (s / 4, s % 4) is +1 */
     int64_t dE;           /* exact energy change of the proposal, 1/16 units */
@@ -260,8 +261,8 @@ typedef struct {
 } orc_pass_rec;
 int orc_prop_pass(int L, int8_t* v, int n_chains, const double* J, const double* Jp,
                   const double* h, const double* beta, const int32_t* chain_param,
-                  const double* w, const double* logits_in, uint64_t seed, uint32_t pass,
-                  int apply, orc_pass_rec* rec);
+                  const double* w, const double* logits_in, const uint32_t* thr_in,
+                  uint64_t seed, uint32_t pass, int apply, orc_pass_rec* rec);
 
 /* S(q) = |sum_r s_r e^{i q.r}|^2 / N of one configuration [Lr][Lc] at
  * q = 2 pi (nR / Lr, nC / Lc), into sq[nR][nC]. */

@@ -40,7 +40,8 @@ ABI_FUNCTIONS = (
     "crbm_proposal_pass", "crbm_sweep_mixed", "crbm_sweep_mixed_every", "crbm_proposal_inspect",
     "crbm_proposal_stats",
     "crbm_proposal_last_error",
-    "crbm_save", "crbm_load", "crbm_philox", "crbm_sweep_stream_noalloc", "crbm_last_error",
+    "crbm_save", "crbm_load", "crbm_philox", "crbm_philox_stream", "crbm_sweep_stream_noalloc",
+    "crbm_last_error",
 )
 
 
@@ -127,6 +128,7 @@ def load_library(path: str | None = None):
         "crbm_save": (c.c_int, [vp, vp, c.POINTER(c.c_size_t)]),
         "crbm_load": (c.c_int, [vp, vp, c.c_size_t]),
         "crbm_philox": (c.c_int, [c.POINTER(c.c_uint32), c.POINTER(c.c_uint32), c.c_size_t]),
+        "crbm_philox_stream": (c.c_int, [vp, c.c_int32, c.c_int32, c.c_int32, c.c_uint64, vp]),
         "crbm_sweep_stream_noalloc": (c.c_int, [c.POINTER(crbm_params), vp, c.c_int64, c.c_int64]),
         "crbm_last_error": (c.c_char_p, [vp]),
     }
@@ -365,7 +367,7 @@ class Batch:
 NET_PARAMS = 3345
 PASS_RECORD = np.dtype([("logit", np.float32, 16), ("dE", np.int32), ("cur_bits", np.uint32),
                         ("new_bits", np.uint32), ("log_alpha", np.float32), ("bR", np.int32),
-                        ("bC", np.int32)])
+                        ("bC", np.int32), ("thr", np.uint32, 16)])
 
 
 class Proposal:
@@ -452,6 +454,18 @@ def crbm_philox(inputs):
     out = np.zeros((len(a), 4), np.uint32)
     _check(load_library().crbm_philox(_ptr(a, ctypes.c_uint32), _ptr(out, ctypes.c_uint32), len(a)))
     return out
+
+
+def crbm_philox_stream(sink, n_blocks, threads, calls, seed=0, stream=None):
+    """Philox throughput probe on a device uint32 tensor sink[n_blocks *
+    threads] (see include/crbm.h); asynchronous on `stream` (torch stream,
+    default: the current one)."""
+    import torch
+    assert sink.dtype == torch.int32 or sink.dtype == torch.uint32
+    assert sink.is_cuda and sink.numel() >= n_blocks * threads
+    st = stream if stream is not None else torch.cuda.current_stream()
+    _check(load_library().crbm_philox_stream(ctypes.c_void_p(sink.data_ptr()), int(n_blocks), int(threads),
+                                             int(calls), ctypes.c_uint64(seed), ctypes.c_void_p(st.cuda_stream)))
 
 
 # C-ABI names, for callers that prefer the flat interface.

@@ -297,28 +297,99 @@ __device__ __forceinline__ void post_sweep_warp0(const SweepArgs& a, int* s_cnt,
 
 // Spin correlations of Sec. IV.B for the chains of each parameter-point
 // segment of this word:  C_p(d) += n_p N - 2 sum_r popc((v_r ^ v_{r+d}) & mask_p).
-__device__ __forceinline__ void accumulate_correlations(const SweepArgs& a, const uint32_t* s_v,
+// C_p(d) = C_p(-d), so only row offsets dR <= L/2 are counted and each count
+// with 0 < dR < L - dR is added at -d as well.  Work items are (dR, slice of
+// rows R); in an item, lane j holds the column offsets dC = j + 32 k and
+// walks the row pairs (R, R + dR): the word at (R, C) is a broadcast, the one
+// at (R + dR, C + dC) a conflict-free gather, and each XOR word is counted
+// for two segments at once.
+static __device__ __noinline__ void accumulate_correlations(const SweepArgs& a, const uint32_t* s_v,
                                                         const int* s_seg, const uint32_t* s_segmask,
                                                         int warp, int nwarp, int lane) {
     const int L = a.g.L, N = a.g.N, nseg = s_seg[0];
-    for (int d = warp; d < N; d += nwarp) {
-        const int dR = d / L, dC = d - (d / L) * L;
-        for (int sgi = 0; sgi < nseg; ++sgi) {
-            const uint32_t mask = s_segmask[sgi];
-            int cnt = 0;
-            for (int r = lane; r < N; r += 32) {
-                const int R = r / L, C = r - (r / L) * L;
-                int R2 = R + dR, C2 = C + dC;
-                if (R2 >= L) R2 -= L;
-                if (C2 >= L) C2 -= L;
-                cnt += __popc((s_v[r] ^ s_v[R2 * L + C2]) & mask);
+    const int n_dr = L / 2 + 1;
+    const int slices = max(1, min(L, (3 * nwarp + n_dr - 1) / n_dr));  // about three items per warp
+    const int n_items = n_dr * slices;
+    constexpr int kMaxK = 3;  // column offsets per lane: L <= 96 in the SMEM layout
+    if (L <= 32) {  // one column offset per lane; lanes >= L count a valid column and drop it
+        for (int item = warp; item < n_items; item += nwarp) {
+            const int dR = item / slices, sl = item - (item / slices) * slices;
+            const int R_begin = sl * L / slices, R_end = (sl + 1) * L / slices;
+            const bool mirror = dR > 0 && 2 * dR != L;
+            for (int s0 = 0; s0 < nseg; s0 += 2) {
+                const uint32_t m0 = s_segmask[s0], m1 = s0 + 1 < nseg ? s_segmask[s0 + 1] : 0u;
+                int c0 = 0, c1 = 0;
+                for (int R = R_begin; R < R_end; ++R) {
+                    const int R2 = R + dR >= L ? R + dR - L : R + dR;
+                    const uint32_t* row = s_v + R * L;
+                    const uint32_t* row2 = s_v + R2 * L;
+                    int C2 = lane < L ? lane : 0;
+#pragma unroll 3
+                    for (int C = 0; C < L; ++C) {
+                        const uint32_t x = row[C] ^ row2[C2];
+                        c0 += __popc(x & m0);
+                        c1 += __popc(x & m1);
+                        C2 = C2 + 1 == L ? 0 : C2 + 1;
+                    }
+                }
+                if (lane < L) {
+                    const long long sites = static_cast<long long>(R_end - R_begin) * L;
+                    for (int j = 0; j < 2 && s0 + j < nseg; ++j) {
+                        const uint32_t mask = j ? m1 : m0;
+                        const int p = s_seg[1 + s0 + j] >> 8;
+                        const unsigned long long val =
+                            static_cast<unsigned long long>(__popc(mask) * sites - 2LL * (j ? c1 : c0));
+                        unsigned long long* cp =
+                            reinterpret_cast<unsigned long long*>(a.corr + static_cast<size_t>(p) * N);
+                        atomicAdd(cp + dR * L + lane, val);
+                        if (mirror) atomicAdd(cp + (L - dR) * L + (lane == 0 ? 0 : L - lane), val);
+                    }
+                }
             }
-            cnt = warp_sum(cnt);
-            if (lane == 0) {
-                const int p = s_seg[1 + sgi] >> 8;
-                const long long val = static_cast<long long>(__popc(mask)) * N - 2LL * cnt;
-                atomicAdd(reinterpret_cast<unsigned long long*>(a.corr + static_cast<size_t>(p) * N + d),
-                          static_cast<unsigned long long>(val));
+        }
+        return;
+    }
+    for (int item = warp; item < n_items; item += nwarp) {
+        const int dR = item / slices, sl = item - (item / slices) * slices;
+        const int R_begin = sl * L / slices, R_end = (sl + 1) * L / slices;
+        const bool mirror = dR > 0 && 2 * dR != L;
+        for (int s0 = 0; s0 < nseg; s0 += 2) {
+            const uint32_t m0 = s_segmask[s0], m1 = s0 + 1 < nseg ? s_segmask[s0 + 1] : 0u;
+            int c0[kMaxK], c1[kMaxK];
+#pragma unroll
+            for (int k = 0; k < kMaxK; ++k) c0[k] = c1[k] = 0;
+            for (int R = R_begin; R < R_end; ++R) {
+                const int R2 = R + dR >= L ? R + dR - L : R + dR;
+                const uint32_t* row = s_v + R * L;
+                const uint32_t* row2 = s_v + R2 * L;
+                for (int C = 0; C < L; ++C) {
+                    const uint32_t x0 = row[C];
+#pragma unroll
+                    for (int k = 0; k < kMaxK; ++k) {
+                        const int dC = lane + 32 * k;
+                        if (k * 32 < L && dC < L) {
+                            const int C2 = C + dC >= L ? C + dC - L : C + dC;
+                            const uint32_t x = x0 ^ row2[C2];
+                            c0[k] += __popc(x & m0);
+                            c1[k] += __popc(x & m1);
+                        }
+                    }
+                }
+            }
+            const long long sites = static_cast<long long>(R_end - R_begin) * L;
+#pragma unroll
+            for (int k = 0; k < kMaxK; ++k) {
+                const int dC = lane + 32 * k;
+                if (k * 32 >= L || dC >= L) continue;
+                for (int j = 0; j < 2 && s0 + j < nseg; ++j) {
+                    const uint32_t mask = j ? m1 : m0;
+                    const int p = s_seg[1 + s0 + j] >> 8;
+                    const unsigned long long val = static_cast<unsigned long long>(
+                        __popc(mask) * sites - 2LL * (j ? c1[k] : c0[k]));
+                    unsigned long long* cp = reinterpret_cast<unsigned long long*>(a.corr + static_cast<size_t>(p) * N);
+                    atomicAdd(cp + dR * L + dC, val);
+                    if (mirror) atomicAdd(cp + (L - dR) * L + (dC == 0 ? 0 : L - dC), val);
+                }
             }
         }
     }

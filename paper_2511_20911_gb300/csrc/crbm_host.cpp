@@ -222,6 +222,7 @@ int dalloc(crbm_ctx* ctx, T*& ptr, size_t count) {
     const cudaError_t e = cudaMalloc(reinterpret_cast<void**>(&ptr), count * sizeof(T));
     if (e != cudaSuccess) {
         ptr = nullptr;
+        cudaGetLastError();  // clear the (non-sticky) allocation error so later launch checks do not see it
         return fail(ctx, CRBM_ENOMEM, std::string("cudaMalloc: ") + cudaGetErrorString(e));
     }
     return CRBM_OK;
@@ -307,7 +308,7 @@ int crbm_create(crbm_ctx** out, const crbm_params* p) {
     if (p->L < 3 || p->L > 4096) return fail(nullptr, CRBM_EINVAL, "L must be in 3..4096");
     if (p->n_params < 1 || !p->J || !p->Jp || !p->h || !p->beta)
         return fail(nullptr, CRBM_EINVAL, "need n_params >= 1 and J, Jp, h, beta arrays");
-    if (p->n_chains < 1) return fail(nullptr, CRBM_EINVAL, "n_chains must be >= 1");
+    if (p->n_chains < 1 || p->n_chains > (1 << 30)) return fail(nullptr, CRBM_EINVAL, "n_chains must be in 1..2^30");
     if (p->measure_every < 0 || p->series_len < 0 || p->sq_every < 0)
         return fail(nullptr, CRBM_EINVAL, "measure_every, series_len and sq_every must be >= 0");
     if (p->layout < CRBM_LAYOUT_AUTO || p->layout > CRBM_LAYOUT_STREAM)
@@ -1085,6 +1086,16 @@ int crbm_philox(const uint32_t* in, uint32_t* out, size_t n) {
     cudaFree(din);
     cudaFree(dout);
     return e == cudaSuccess ? CRBM_OK : cuda_fail(nullptr, e, "crbm_philox");
+}
+
+int crbm_philox_stream(uint32_t* sink, int32_t n_blocks, int32_t threads, int32_t calls, uint64_t seed,
+                       void* stream) {
+    if (!sink || n_blocks < 1 || n_blocks > (1 << 20) || threads < 32 || threads > 1024 || threads % 32 ||
+        calls < 0 || static_cast<int64_t>(n_blocks) * threads > (1LL << 31))
+        return fail(nullptr, CRBM_EINVAL, "crbm_philox_stream: bad arguments");
+    const cudaError_t e = launch_philox_stream(sink, n_blocks, threads, calls, static_cast<uint32_t>(seed),
+                                               static_cast<uint32_t>(seed >> 32), static_cast<cudaStream_t>(stream));
+    return e == cudaSuccess ? CRBM_OK : cuda_fail(nullptr, e, "crbm_philox_stream");
 }
 
 const char* crbm_last_error(const crbm_ctx* ctx) {

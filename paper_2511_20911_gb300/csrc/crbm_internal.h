@@ -264,6 +264,8 @@ cudaError_t launch_sweep_batch(const BatchArgs& b, int n_tasks, int cluster, int
 int batch_max_active_clusters(int cluster, int threads, size_t smem);
 cudaError_t launch_batch_advance(int64_t* clocks, const int* every, int n_ctx, int64_t n_sweeps, cudaStream_t st);
 cudaError_t launch_philox(const uint32_t* in, uint32_t* out, int n, cudaStream_t st);
+cudaError_t launch_philox_stream(uint32_t* sink, int n_blocks, int threads, int calls, uint32_t k0,
+                                 uint32_t k1, cudaStream_t st);
 cudaError_t launch_unpack(const Geometry& g, const uint32_t* v, int8_t* out, int n_words,
                           cudaStream_t st);
 cudaError_t launch_pack(const Geometry& g, const int8_t* in, uint32_t* v, int n_words,

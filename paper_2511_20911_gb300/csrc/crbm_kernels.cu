@@ -72,7 +72,29 @@ __global__ void k_philox(const uint32_t* in, uint32_t* out, int n) {
     o[3] = q.w;
 }
 
+// Philox throughput probe: thread t runs `calls` Philox-4x32-10 calls on the
+// counters (i, t, i ^ t, 0x9E3779B9), i = 0 .. calls - 1, and stores the XOR
+// of all their output words.  Every round's two wide products depend on i,
+// so none can leave the loop: 20 32x32->64 products per call.
+__global__ void k_philox_stream(uint32_t* sink, int calls, uint32_t k0, uint32_t k1) {
+    const uint32_t t = blockIdx.x * blockDim.x + threadIdx.x;
+    uint32_t acc = 0u;
+#pragma unroll 2
+    for (int i = 0; i < calls; ++i) {
+        const uint32_t c = static_cast<uint32_t>(i);
+        const U4 q = philox(c, t, c ^ t, 0x9E3779B9u, k0, k1);
+        acc ^= q.x ^ q.y ^ q.z ^ q.w;
+    }
+    sink[t] = acc;
+}
+
 }  // namespace
+
+cudaError_t launch_philox_stream(uint32_t* sink, int n_blocks, int threads, int calls, uint32_t k0,
+                                 uint32_t k1, cudaStream_t st) {
+    k_philox_stream<<<n_blocks, threads, 0, st>>>(sink, calls, k0, k1);
+    return cudaGetLastError();
+}
 
 cudaError_t launch_philox(const uint32_t* in, uint32_t* out, int n, cudaStream_t st) {
     if (n <= 0) return cudaSuccess;

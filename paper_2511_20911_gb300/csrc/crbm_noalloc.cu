@@ -25,9 +25,10 @@ constexpr size_t kScratchWords = CRBM_NOALLOC_SCRATCH_BYTES / sizeof(uint32_t);
 __device__ __align__(256) uint32_t g_noalloc_scratch[kScratchWords];
 
 constexpr int kMaxDevices = 64;
-std::once_flag g_setup_once[kMaxDevices];
+// Device address of g_noalloc_scratch per device, stored only once the
+// lookup has succeeded (a failed lookup is retried by the next call).
+std::mutex g_setup_mutex;
 uint32_t* g_scratch_addr[kMaxDevices];
-cudaError_t g_setup_status[kMaxDevices];
 // Failures report only their code (no message string: that would allocate).
 int noalloc_fail(int code, const char*) { return code; }
 
@@ -44,8 +45,8 @@ extern "C" int crbm_sweep_stream_noalloc(const crbm_params* p, uint32_t* v, int6
         (p->precision != CRBM_PRECISION_EXACT && p->precision != CRBM_PRECISION_PAPER) || p->rng != CRBM_RNG_LANE)
         return noalloc_fail(CRBM_EINVAL,
                             "needs a square periodic lattice, one field, a known precision and lane uniforms");
-    if (p->n_params < 1 || !p->J || !p->Jp || !p->h || !p->beta || p->n_chains < 1)
-        return noalloc_fail(CRBM_EINVAL, "need n_params >= 1, the four parameter arrays and n_chains >= 1");
+    if (p->n_params < 1 || !p->J || !p->Jp || !p->h || !p->beta || p->n_chains < 1 || p->n_chains > (1 << 30))
+        return noalloc_fail(CRBM_EINVAL, "need n_params >= 1, the four parameter arrays and 1 <= n_chains <= 2^30");
     if (sweep0 < 0 || n_sweeps < 0 || n_sweeps > 2147483647LL || sweep0 + n_sweeps > 4294967295LL)
         return noalloc_fail(CRBM_EINVAL, "sweep range outside the 32-bit Philox sweep counter");
     const int L = p->L, W = L / 2, N = L * L, n_cells = W * W;
@@ -71,14 +72,17 @@ extern "C" int crbm_sweep_stream_noalloc(const crbm_params* p, uint32_t* v, int6
     cudaError_t e = cudaGetDevice(&dev);
     if (e != cudaSuccess || dev < 0 || dev >= kMaxDevices)
         return noalloc_fail(CRBM_ECUDA, "cudaGetDevice failed or device index too large");
-    std::call_once(g_setup_once[dev], [dev] {
-        void* ptr = nullptr;
-        g_setup_status[dev] = cudaGetSymbolAddress(&ptr, g_noalloc_scratch);
-        g_scratch_addr[dev] = static_cast<uint32_t*>(ptr);
-    });
-    if (g_setup_status[dev] != cudaSuccess || !g_scratch_addr[dev])
-        return noalloc_fail(CRBM_ECUDA, "cudaGetSymbolAddress of the scratch array failed");
-    uint32_t* scratch = g_scratch_addr[dev];
+    uint32_t* scratch = nullptr;
+    {
+        std::lock_guard<std::mutex> lock(g_setup_mutex);
+        if (!g_scratch_addr[dev]) {
+            void* ptr = nullptr;
+            if (cudaGetSymbolAddress(&ptr, g_noalloc_scratch) == cudaSuccess)
+                g_scratch_addr[dev] = static_cast<uint32_t*>(ptr);
+        }
+        scratch = g_scratch_addr[dev];
+    }
+    if (!scratch) return noalloc_fail(CRBM_ECUDA, "cudaGetSymbolAddress of the scratch array failed");
     cudaStream_t st = static_cast<cudaStream_t>(p->stream);
 
     Geometry g{};

@@ -75,6 +75,7 @@ struct PassRecord {
     uint32_t cur_bits, new_bits;
     float log_alpha;
     int32_t bR, bC;
+    uint32_t thr[16];
 };
 
 struct PassArgs {
@@ -84,7 +85,7 @@ struct PassArgs {
     const uint2* frag;        // [kFrags][32] B fragments (bf16 pairs)
     const float* bias;        // b1[16], b2[16], b3
     const float* c1;          // folded layer-1 constants [kC1]
-    const float* chain_bh;    // [chains][2] beta, h (bf16-rounded)
+    const float* chain_bh;    // [chains][4] beta, h (bf16-rounded net inputs), beta (fp32), 0
     const int32_t* chain_q;   // [chains][3] Q.4 J, J', h
     unsigned long long* stats;  // {proposed, accepted}
     uint32_t key0, key1;
@@ -138,6 +139,7 @@ __global__ void __launch_bounds__(kPassThreads, 2) k_prop_pass(const __grid_cons
     float* lqn = lqc + 512;                        // [16][32] log q of the proposed spin
     int* s_xx = reinterpret_cast<int*>(lqn + 512);  // [16][32] bit 0: current +1, bit 1: proposed +1
     long long* s_de = reinterpret_cast<long long*>(s_xx + 512);  // [16][32] energy-change terms
+    uint32_t* s_thr = reinterpret_cast<uint32_t*>(s_de + 512);    // [16][32] proposal thresholds
     const uint32_t a1_base = static_cast<uint32_t>(__cvta_generic_to_shared(A1));
     const uint32_t a2_base = static_cast<uint32_t>(__cvta_generic_to_shared(A2));
 
@@ -155,8 +157,8 @@ __global__ void __launch_bounds__(kPassThreads, 2) k_prop_pass(const __grid_cons
         for (int i = threadIdx.x; i < kS1 * kS1 * 16; i += blockDim.x) c1s[i] = c1v[i];
         for (int i = threadIdx.x; i < 32 * 16; i += blockDim.x) {
             const int c = i >> 4, n = i & 15, chain = word * 32 + c;
-            cbs[i] = a.bias[n] + a.chain_bh[2 * chain] * a.c1[kC1Pos + n] +
-                     a.chain_bh[2 * chain + 1] * a.c1[kC1Pos + 16 + n];
+            cbs[i] = a.bias[n] + a.chain_bh[4 * chain] * a.c1[kC1Pos + n] +
+                     a.chain_bh[4 * chain + 1] * a.c1[kC1Pos + 16 + n];
         }
     }
     for (int x = threadIdx.x; x < kFrags * 32; x += blockDim.x) fr[x] = a.frag[x];
@@ -270,6 +272,7 @@ __global__ void __launch_bounds__(kPassThreads, 2) k_prop_pass(const __grid_cons
             lqc[s * 32 + lane] = xc > 0 ? lp : lm;
             lqn[s * 32 + lane] = xp > 0 ? lp : lm;
             s_xx[s * 32 + lane] = (xc > 0 ? 1 : 0) | (xp > 0 ? 2 : 0);
+            s_thr[s * 32 + lane] = thr;
         }
     }
     __syncthreads();
@@ -323,7 +326,7 @@ __global__ void __launch_bounds__(kPassThreads, 2) k_prop_pass(const __grid_cons
         cb |= static_cast<uint32_t>(xx & 1) << s;
         nb |= static_cast<uint32_t>((xx >> 1) & 1) << s;
     }
-    const float beta = a.chain_bh[2 * chain];
+    const float beta = a.chain_bh[4 * chain + 2];  // the exact beta: the MH test targets exp(-beta H)
     const float log_alpha = -beta * static_cast<float>(dE) * 0.0625f + logq_cur - logq_new;
     const U4 ua = philox(cell_id, a.pass, static_cast<uint32_t>(chain), kTagAccept, a.key0, a.key1);
     const bool accept = log_alpha >= 0.f ||
@@ -331,7 +334,10 @@ __global__ void __launch_bounds__(kPassThreads, 2) k_prop_pass(const __grid_cons
     if (a.rec) {  // inspection: record, do not move
         PassRecord* r = a.rec + (static_cast<size_t>(word) * gridDim.x + b) * 32 + lane;
 #pragma unroll
-        for (int s = 0; s < kK * kK; ++s) r->logit[s] = logit[s * 32 + lane];
+        for (int s = 0; s < kK * kK; ++s) {
+            r->logit[s] = logit[s * 32 + lane];
+            r->thr[s] = s_thr[s * 32 + lane];
+        }
         r->dE = static_cast<int32_t>(dE);
         r->cur_bits = cb;
         r->new_bits = nb;
@@ -390,8 +396,8 @@ __global__ void k_prop_extract(Geometry g, const uint32_t* v, const float* chain
     }
     x.pr = static_cast<uint8_t>((bR + 1) & 1);  // parity of row bR - 3 (L even)
     x.pc = static_cast<uint8_t>((bC + 1) & 1);
-    x.beta = chain_bh[2 * c];
-    x.h = chain_bh[2 * c + 1];
+    x.beta = chain_bh[4 * c];
+    x.h = chain_bh[4 * c + 1];
 }
 
 __device__ __forceinline__ float bf16r(float x) { return __bfloat162float(__float2bfloat16_rn(x)); }
@@ -629,27 +635,31 @@ cudaError_t refresh_fragments(crbm_proposal* p, cudaStream_t st) {
     return cudaGetLastError();
 }
 
-// Per-chain (beta, h) and Q.4 couplings of a context, on the device.
+// Per-chain (beta, h) and Q.4 couplings of a context, on the device:
+// chain_bh[c] = {bf16(beta), bf16(h), beta, 0} (the net reads the bf16
+// inputs, the Metropolis-Hastings test the fp32 beta).
 int ensure_chain_params(crbm_ctx* ctx) {
     if (ctx->d.chain_bh) return CRBM_OK;
     const int npad = ctx->n_words * 32;
-    std::vector<float> bh(2 * static_cast<size_t>(npad));
+    std::vector<float> bh(4 * static_cast<size_t>(npad));
     std::vector<int32_t> cq(3 * static_cast<size_t>(npad));
-    for (int c = 0; c < npad; ++c) {
-        const int p = ctx->chain_param[c < ctx->n_chains ? c : 0];
-        bh[2 * c] = static_cast<float>(ctx->beta[p]);
-        bh[2 * c + 1] = static_cast<float>(ctx->q[2][p]) * 0.0625f;
-        cq[3 * c] = ctx->q[0][p];
-        cq[3 * c + 1] = ctx->q[1][p];
-        cq[3 * c + 2] = ctx->q[2][p];
-    }
-    // bf16 rounding of beta and h (the net's input precision), on the host
-    for (float& x : bh) {
+    auto bf16 = [](float x) {  // round to nearest even, 8 significant bits
         uint32_t u;
         std::memcpy(&u, &x, 4);
         u += 0x7fffu + ((u >> 16) & 1u);
         u &= 0xffff0000u;
         std::memcpy(&x, &u, 4);
+        return x;
+    };
+    for (int c = 0; c < npad; ++c) {
+        const int p = ctx->chain_param[c < ctx->n_chains ? c : 0];
+        bh[4 * c] = bf16(static_cast<float>(ctx->beta[p]));
+        bh[4 * c + 1] = bf16(static_cast<float>(ctx->q[2][p]) * 0.0625f);
+        bh[4 * c + 2] = static_cast<float>(ctx->beta[p]);
+        bh[4 * c + 3] = 0.f;
+        cq[3 * c] = ctx->q[0][p];
+        cq[3 * c + 1] = ctx->q[1][p];
+        cq[3 * c + 2] = ctx->q[2][p];
     }
     cudaError_t e = cudaMalloc(reinterpret_cast<void**>(&ctx->d.chain_bh), bh.size() * 4);
     if (e == cudaSuccess) e = cudaMalloc(reinterpret_cast<void**>(&ctx->d.chain_q), cq.size() * 4);
@@ -661,11 +671,12 @@ int ensure_chain_params(crbm_ctx* ctx) {
 
 int check_ctx(const crbm_ctx* ctx) {
     if (!ctx) return prop_fail(CRBM_EINVAL, "null context");
-    if (!ctx->g.canonical || ctx->g.Lc != ctx->g.L || ctx->layout != CRBM_LAYOUT_SMEM || ctx->swap_every > 0 ||
-        ctx->g.paper || ctx->g.bitplane)
+    if (!ctx->g.canonical || ctx->g.Lc != ctx->g.L || ctx->g.L < crbm::kP || ctx->layout != CRBM_LAYOUT_SMEM ||
+        ctx->swap_every > 0 || ctx->g.paper || ctx->g.bitplane)
         return prop_fail(CRBM_EUNSUPPORTED,
-                         "block proposals need the ten SS filters on an even periodic square lattice, the "
-                         "SMEM layout, exact precision, lane uniforms and no replica exchange");
+                         "block proposals need the ten SS filters on an even periodic square lattice of side "
+                         ">= 10 (a patch must not wrap onto its own block), the SMEM layout, exact precision, "
+                         "lane uniforms and no replica exchange");
     return CRBM_OK;
 }
 

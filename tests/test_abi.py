@@ -74,3 +74,25 @@ def test_binding_struct_layout_matches_the_header(tmp_path):
         assert got[(name, "sizeof")] == ctypes.sizeof(cls), name
         for field, _ in cls._fields_:
             assert got[(name, field)] == getattr(cls, field).offset, (name, field)
+
+
+def test_pass_record_layout_matches_the_header(tmp_path):
+    """The numpy record of crbm_proposal_inspect has the C layout of
+    crbm_pass_record (size and every field offset)."""
+    import subprocess
+    import paper_2511_20911_gb300 as crbm
+    dt = crbm.PASS_RECORD
+    lines = ['#include <stdio.h>', '#include <stddef.h>', '#include "crbm.h"', "int main(void) {",
+             'printf("sizeof %zu\\n", sizeof(crbm_pass_record));']
+    for field in dt.names:
+        lines.append(f'printf("{field} %zu\\n", offsetof(crbm_pass_record, {field}));')
+    lines.append("return 0; }")
+    src = tmp_path / "rec.c"
+    src.write_text("\n".join(lines))
+    exe = tmp_path / "rec"
+    subprocess.check_call(["gcc", "-std=c11", "-I", os.path.join(ROOT, "include"), str(src), "-o", str(exe)])
+    out = subprocess.run([str(exe)], capture_output=True, text=True, check=True).stdout.split("\n")
+    got = {l.split()[0]: int(l.split()[1]) for l in out if l.strip()}
+    assert got["sizeof"] == dt.itemsize
+    for field in dt.names:
+        assert got[field] == dt.fields[field][1], field

@@ -64,6 +64,24 @@ def test_philox_device_matches_oracle(orc):
         assert list(out[i]) == orc.philox(x[i, :4], x[i, 4:]), i
 
 
+def test_philox_stream_probe_matches_oracle(orc):
+    """The throughput probe computes what it claims: thread t's XOR over
+    calls i of the oracle's Philox((i, t, i ^ t, 0x9E3779B9), seed)."""
+    import torch
+    nb, th, calls, seed = 2, 64, 5, 0x1234567890ABCDEF
+    sink = torch.zeros(nb * th, dtype=torch.int32, device="cuda")
+    crbm.crbm_philox_stream(sink, nb, th, calls, seed)
+    torch.cuda.synchronize()
+    got = sink.cpu().numpy().view(np.uint32)
+    key = (seed & 0xFFFFFFFF, seed >> 32)
+    for t in range(nb * th):
+        acc = 0
+        for i in range(calls):
+            for x in orc.philox((i, t, i ^ t, 0x9E3779B9), key):
+                acc ^= x
+        assert got[t] == acc, t
+
+
 @pytest.mark.parametrize("L,periodic", [(6, True), (18, True), (3, True), (3, False), (9, True),
                                         (10, False)])
 def test_tables_match_oracle(orc, L, periodic):
@@ -118,9 +136,10 @@ def test_custom_filters_bitexact(orc, bonds):
                  periodic=periodic, bonds=bonds)
 
 
-def test_structure_factor_matches_oracle(orc):
-    L, n = 8, 70
-    rng = np.random.default_rng(8)
+@pytest.mark.parametrize("L", [8, 6, 9, 36])
+def test_structure_factor_matches_oracle(orc, L):
+    n = 70
+    rng = np.random.default_rng(8 + L)
     params = workloads.random_params(rng, 3)
     cp = np.sort(rng.integers(0, 3, n)).astype(np.int32)
     s, _, _, osq = run_pair(orc, L, params, n, cp, 4, splits=[9, 12], measure_every=0,
@@ -183,6 +202,25 @@ def test_host_side_errors():
         s.sweep(-1)
     with pytest.raises(crbm.CrbmError):
         s.set_spins(np.zeros((4, 6, 6), np.int8))
+
+
+def test_device_memory_exhaustion_returns_enomem(orc):
+    """A context whose device state exceeds the GPU's memory (L=4096 streamed,
+    32768 chains: 69 GB of packed spins, then 550 GB of int8 staging) fails
+    with CRBM_ENOMEM from the failed cudaMalloc, before any kernel is
+    launched; its earlier allocations are released and the device stays
+    usable (a small run afterwards is bit-exact against the oracle)."""
+    import torch
+    torch.cuda.synchronize()
+    free0, _ = torch.cuda.mem_get_info()
+    ok = dict(J=[1.0], Jp=[1.0], h=[0.5], beta=[1.0])
+    with pytest.raises(crbm.CrbmError) as e:
+        crbm.Sampler(4096, ok, 32768, layout=crbm.CRBM_LAYOUT_STREAM)
+    assert e.value.code == crbm.CRBM_ENOMEM, e.value
+    assert "cudaMalloc" in str(e.value)
+    free1, _ = torch.cuda.mem_get_info()
+    assert abs(free1 - free0) < (64 << 20), (free0, free1)
+    run_pair(orc, 6, ok, 64, np.zeros(64, np.int32), seed=5, splits=[3, 2])
 
 
 @pytest.mark.slow

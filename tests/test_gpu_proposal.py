@@ -59,6 +59,72 @@ def test_pass_logits_and_exact_energy_change(orc, L):
     assert worst <= 1.0, worst
 
 
+@pytest.mark.parametrize("L,n", [(12, 600), (18, 300)])
+def test_pass_matches_the_oracle_element_wise(orc, L, n):
+    """Every record of a pass, every chain of every word (the last one
+    ragged), against the oracle's pass (orc_prop_pass) on the same spins:
+    block origins and current blocks exactly; the GPU's thresholds within
+    fp32 rounding of those the oracle derives from the GPU's logits; with the
+    GPU's thresholds fed to the oracle, the proposed blocks (the Philox draws
+    and their comparisons) and the exact dE bit for bit and log alpha to fp32
+    accuracy; then, after the pass itself runs, every block whose accept test
+    is not within 1e-3 of its boundary equals the oracle's result (beta = 0.6
+    is not a bfloat16 value: the test must use the exact beta)."""
+    rng = np.random.default_rng(L + 1)
+    params = dict(J=[1.0, 1.0, -0.5], Jp=[1.0, 1.5, 2.0], h=[3.0, 0.5, -1.0], beta=[2.0, 0.6, 0.25])
+    cp = rng.integers(0, 3, n).astype(np.int32)
+    s = crbm.Sampler(L, params, n, chain_param=cp, seed=3, measure_every=0)
+    s.sweep(7)
+    p = crbm.Proposal(seed=1)
+    w = orc.random_net(21, scale=0.15)
+    p.weights = w
+    g = p.inspect(s)                                       # [word][block][lane]
+    g = g.transpose(1, 0, 2).reshape(g.shape[1], -1)[:, :n]  # [block][chain]
+    spins = s.get_spins()
+    seed, pass_index = 3, 0
+    o_net = orc.prop_pass(spins.copy(), params, cp, w, seed, pass_index)
+    o_lg = orc.prop_pass(spins.copy(), params, cp, None, seed, pass_index,
+                         logits=g["logit"].astype(np.float64))
+    o_thr = orc.prop_pass(spins.copy(), params, cp, None, seed, pass_index,
+                          logits=g["logit"].astype(np.float64), thr=g["thr"])
+    assert g.shape == o_net.shape == (max(1, L // 8) ** 2, n)
+    for f in ("bR", "bC", "cur_bits"):
+        assert np.array_equal(g[f].astype(np.int64), o_net[f].astype(np.int64)), f
+    err = np.abs(g["logit"] - o_net["logit"]) / (0.05 + 0.02 * np.abs(o_net["logit"]))
+    assert err.max() <= 1.0, err.max()
+    tg, to = g["thr"].astype(np.float64), o_lg["thr"].astype(np.float64)
+    assert (np.abs(tg - to) <= 4096 + tg * 2.0 ** -20).all(), np.abs(tg - to).max()
+    assert np.array_equal(g["new_bits"], o_thr["new_bits"])
+    assert np.array_equal(g["dE"].astype(np.int64), o_thr["dE"])
+    la_err = np.abs(g["log_alpha"] - o_thr["log_alpha"])
+    assert (la_err <= 2e-4 + 1e-5 * np.abs(o_thr["log_alpha"])).all(), la_err.max()
+    # the pass itself: accept decisions away from the boundary
+    after = spins.copy()
+    orc.prop_pass(after, params, cp, None, seed, pass_index, apply=True,
+                  logits=g["logit"].astype(np.float64), thr=g["thr"])
+    p.passes(s, 1)
+    got = s.get_spins()
+    la, lu = o_thr["log_alpha"], np.log(o_thr["u_accept"])
+    clear = (la > 1e-3) | (np.abs(la - lu) > 1e-3)
+    assert clear.mean() > 0.99 and 0 < o_thr["accept"].mean() < 1
+    for b in range(g.shape[0]):
+        for c in range(n):
+            r = o_thr[b, c]
+            sites = [((r["bR"] + t // 4) % L, (r["bC"] + t % 4) % L) for t in range(16)]
+            blk = np.array([got[c][x] for x in sites])
+            if clear[b, c]:
+                assert np.array_equal(blk, np.array([after[c][x] for x in sites])), (b, c)
+            else:
+                assert np.array_equal(blk, np.array([after[c][x] for x in sites])) or \
+                    np.array_equal(blk, np.array([spins[c][x] for x in sites]))
+    outside = np.ones((n, L, L), bool)
+    for b in range(g.shape[0]):
+        r = o_thr[b, 0]
+        for t in range(16):
+            outside[:, (r["bR"] + t // 4) % L, (r["bC"] + t % 4) % L] = False
+    assert np.array_equal(got[outside], spins[outside])
+
+
 def test_training_gradient_matches_oracle(orc):
     rng = np.random.default_rng(4)
     L, n = 12, 24
@@ -98,8 +164,9 @@ def test_training_lowers_the_loss_and_moves_are_accepted():
 
 def test_mixed_sampler_matches_plain_gibbs():
     """Exact MH keeps the Boltzmann law: energy and magnetisation per spin of
-    Gibbs + block moves agree with plain Gibbs within 4 standard errors."""
-    L, n = 12, 512
+    Gibbs + block moves agree with plain Gibbs within 3 standard errors
+    (standard errors from the spread of independent chain means)."""
+    L, n = 12, 2048
     params = dict(J=[1.0], Jp=[1.0], h=[1.0], beta=[0.6])
     res = []
     for mixed in (False, True):
@@ -121,7 +188,7 @@ def test_mixed_sampler_matches_plain_gibbs():
         M = ser[..., 2] / (L * L)
         res.append([(x.mean(0).mean(), x.mean(0).std(ddof=1) / np.sqrt(n)) for x in (E, M)])
     for (m0, s0), (m1, s1) in zip(res[0], res[1]):
-        assert abs(m0 - m1) < 4 * np.hypot(s0, s1), (m0, m1, s0, s1)
+        assert abs(m0 - m1) < 3 * np.hypot(s0, s1), (m0, m1, s0, s1)
 
 
 def test_mixed_every_is_sweeps_then_a_pass():

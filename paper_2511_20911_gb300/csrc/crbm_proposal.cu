@@ -1,5 +1,5 @@
 // Learned block proposal (Metropolis-Hastings block moves mixed with the
-// Gibbs sweeps), canonical SS lattice (even L, periodic).
+// Gibbs sweeps), canonical SS lattice (even L >= 10, periodic).
 //
 // A k x k block (k = 4) is proposed from a small convolutional net over the
 // (k+6) x (k+6) patch around it: input channels 0 spin (0 inside the block),
@@ -12,14 +12,34 @@
 // least 8 sites apart, so no block lies in another's receptive field or
 // energy halo and the moves of a pass commute.
 //
-// The MH pass runs the three convolutions as implicit GEMMs on the tensor
-// cores (mma.sync m16n8k16, bf16 operands, fp32 accumulation): rows are
-// (chain, output position) of the 32 chains of a packed word, columns the 16
-// output channels, K = (tap, input channel).  Layer 1's five constant planes
-// are folded into per-position and per-chain constants, so its convolution
-// runs on the spin plane alone (one k-tile).  Training runs one example per
-// thread in fp32 (bf16-rounded weights and activations), back-propagates the
-// binary cross-entropy and updates with Adam.
+// The pass runs the three convolutions on the tcgen05 tensor cores (bf16
+// operands from shared memory, fp32 accumulators in tensor memory), one CTA
+// of four warps per work item = (block of the pass, 16 chains of a packed
+// word), persistent over the items.  Activations live in an 8 x 8 frame per
+// chain, stored as "column planes": plane (x, h) holds channels 8h .. 8h + 7
+// of frame column x for the 128 rows (chain, frame row y), 16 bytes a row.
+//  * layer 1 acts on the spin plane alone (its five constant planes are folded
+//    into per-position constants added in its epilogue, and b1 + beta w_beta
+//    + h w_h enter through constant K columns): one K = 16 MMA per frame
+//    column x on a gathered 9-tap operand (M = 128 rows (chain, y), N = 16);
+//  * layer 2 is banded: D[(chain, y)][(x, n)] over the six frame columns it
+//    needs accumulates, for each tap row dy and input column o, the operand
+//    plane o shifted by dy rows (a 3 x 3 convolution's row offset is a
+//    shared-memory row offset) against the taps o - x of W2 for the output
+//    columns x = o - 2 .. o it feeds (N = 16 .. 48): 24 MMAs into an
+//    accumulator zeroed beforehand;
+//  * layer 3 (one output channel) is banded the same way with N = the four
+//    block columns: its accumulator is the block's logits (18 MMAs);
+//  * epilogues read the accumulators with tcgen05.ld, add the bias, apply
+//    ReLU and round to bf16 in one conversion, and write the next operand.
+// The Metropolis-Hastings step then runs on the CUDA cores: Philox draws of
+// the proposed bits against thresholds of q, exact integer dE, log alpha
+// with the exact beta, and accepted blocks flipped in place with atomic XOR
+// (the two halves of a word are separate items).
+//
+// Training runs one example per thread in fp32 (bf16-rounded weights and
+// activations), back-propagates the binary cross-entropy and updates with
+// Adam.
 #include <algorithm>
 #include <cstring>
 #include <string>
@@ -29,6 +49,7 @@
 
 #include "crbm_context.h"
 #include "crbm_device.cuh"
+#include "crbm_umma.cuh"
 
 namespace crbm {
 namespace {
@@ -41,16 +62,9 @@ constexpr int kS1 = kK + 4;        // layer-1 output side (8)
 constexpr int kS2 = kK + 2;        // layer-2 output side (6)
 constexpr int kNP = 3345;          // parameters
 constexpr uint32_t kTagOffset = 8u, kTagBits = 9u, kTagAccept = 13u, kTagExample = 14u;
-constexpr int kPassThreads = 256;  // 8 warps
 
 // Parameter offsets (W1[16][6][3][3], b1, W2[16][16][3][3], b2, W3[16][3][3], b3).
 constexpr int oW1 = 0, oB1 = 864, oW2 = 880, oB2 = 3184, oW3 = 3200, oB3 = 3344;
-
-// B-operand fragments of the three layers for mma m16n8k16 (per lane 2 x u32):
-// layer 1: 1 k-tile (the nine taps of the spin plane) x 2 n-tiles, layer 2:
-// 9 x 2, layer 3: 9 x 1.
-constexpr int kFrag1 = 2, kFrag2 = 9 * 2, kFrag3 = 9;
-constexpr int kFrags = kFrag1 + kFrag2 + kFrag3;
 
 // Layer 1 on the five constant planes (block mask, row and column parity,
 // beta, h) is linear in them and the same for every chain of a pass, so it is
@@ -60,15 +74,45 @@ constexpr int kFrags = kFrag1 + kFrag2 + kFrag3;
 // a convolution (K = 9 taps).
 constexpr int kC1Pos = 4 * kS1 * kS1 * 16, kC1 = kC1Pos + 2 * 16;
 
-// Shared memory of the pass, 32-bit words.  A1 and A2 hold bf16 activations,
-// one 32-byte row per (chain, position) of 16 channels; the two 16-byte halves
-// of row R are swapped when bit 2 of R is set, so the eight rows an ldmatrix
-// phase reads (mostly consecutive) fall in distinct banks.
-constexpr int kSmA1 = 0, kSmA2 = 32 * kS1 * kS1 * 8, kSmFr = kSmA2 + 32 * kS2 * kS2 * 8;
-constexpr int kSmPw = kSmFr + kFrags * 32 * 2, kSmWords = kSmPw + kP * kP;
+// ---- tensor-core pass geometry
+constexpr int kPassThreads = 128;              // one warpgroup: warp w reads TMEM lanes 32 w ..
+constexpr int kItemChains = 16;                // chains of one work item (half a packed word)
+constexpr int kFrame = 8;                      // every layer in an 8 x 8 frame per chain
+constexpr int kTmemCols = 128;
+constexpr int kPlaneRows = 136;                // 128 rows (chain, y) + rows read by the dy = 1, 2 shifts
+constexpr int kPlane = kPlaneRows * 16;        // bytes of one column plane (x, h)
+// Layer-1 operand (gathered): rows (x, chain, y), K = 9 spin taps, then 1,
+// beta, beta, h, h, 0, 0: two planes of 1024 rows.
+constexpr int kA0Plane = 1024 * 16;
+// B operands (bf16, K-major, element offsets): B1 [n 16][k 16]; layer-2 taps
+// per dy: [h 2][row 3 * 16][8] with row = block j * 16 + n, block j = tap
+// column 2 - j; layer-3 bands per dy: [h 2][row 24][8], row 7 - dx = tap
+// column dx, zero rows elsewhere.
+constexpr int kZ2Rows = 3 * 16, kZ3Rows = 24;
+constexpr int kB1 = 0, kZ2 = 256, kZ3 = kZ2 + 3 * 2 * kZ2Rows * 8, kBElems = kZ3 + 3 * 2 * kZ3Rows * 8;
+constexpr uint32_t kIdesc1 = umma::idesc_bf16_f32(128, 16);
+constexpr uint32_t kIdesc3 = umma::idesc_bf16_f32(128, 16);
+// Shared memory of the pass (bytes).  X holds, in turn, layer 1's gathered
+// operand, layer 1's output planes (layer 2's operand), layer 2's output
+// planes (layer 3's operand) and the Metropolis-Hastings arrays.  Item data
+// are double-buffered (the next item's are fetched during this one); the
+// folded layer-1 constants of the item are fetched at its start.
+constexpr int kSmX = 0, kSmXBytes = 8 * 2 * kPlane;        // 34816 >= 2 * kA0Plane
+constexpr int kSmB = kSmX + kSmXBytes;
+constexpr int kItemBytes = 104 * 4 + kItemChains * 8 * 4;  // patch [100](+4), chain_bh [16][4], Q.4 [16][4]
+constexpr int kC1Stride = 20;                              // floats per (x, y) row of staged constants
+constexpr int kC1Bytes = 64 * kC1Stride * 4;
+constexpr int kSmItem = kSmB + kBElems * 2;
+constexpr int kSmC1 = kSmItem + 2 * kItemBytes;
+constexpr int kSmBar = kSmC1 + kC1Bytes, kSmBytes = kSmBar + 16;
+constexpr int kMHBytes = 256 * 4 * 3 + 128 * 4 * 2 + 16 * 4 + 128 * 8;
+static_assert(kSmXBytes >= 2 * kA0Plane && kSmXBytes >= kMHBytes, "layer-1 operand and MH arrays fit in X");
+static_assert(kSmB % 16 == 0 && kSmItem % 16 == 0 && kSmC1 % 16 == 0 && kSmBar % 8 == 0, "alignment");
+constexpr int kWaitTries = 1 << 22;            // mbarrier polls before the pass gives up
 
 // Per (word, block, lane) record of a pass run in inspection mode: the
-// logits, the proposed and current block bits, the exact dE and log alpha.
+// logits, the proposed and current block bits, the exact dE, log alpha and
+// the proposal thresholds.
 struct PassRecord {
     float logit[16];
     int32_t dE;
@@ -82,282 +126,403 @@ struct PassArgs {
     Geometry g;
     PassRecord* rec;          // inspection mode when non-null: records, no move
     uint32_t* v;
-    const uint2* frag;        // [kFrags][32] B fragments (bf16 pairs)
-    const float* bias;        // b1[16], b2[16], b3
+    const uint4* bmat;        // [kBElems / 8] B operands (bf16, canonical layout)
+    const float* bias;        // b2[16], b3
     const float* c1;          // folded layer-1 constants [kC1]
     const float* chain_bh;    // [chains][4] beta, h (bf16-rounded net inputs), beta (fp32), 0
     const int32_t* chain_q;   // [chains][3] Q.4 J, J', h
-    unsigned long long* stats;  // {proposed, accepted}
+    unsigned long long* stats;  // {proposed, accepted, timeouts}
     uint32_t key0, key1;
     uint32_t pass;
     int nb1, spacing;         // blocks per side, block spacing
+    int n_items;              // blocks x half-words
 };
 
-__device__ __forceinline__ void mma_bf16(float (&d)[4], const uint32_t (&a)[4], uint2 b) {
-    asm volatile(
-        "mma.sync.aligned.m16n8k16.row.col.f32.bf16.bf16.f32 {%0,%1,%2,%3}, {%4,%5,%6,%7}, {%8,%9}, "
-        "{%0,%1,%2,%3};\n"
-        : "+f"(d[0]), "+f"(d[1]), "+f"(d[2]), "+f"(d[3])
-        : "r"(a[0]), "r"(a[1]), "r"(a[2]), "r"(a[3]), "r"(b.x), "r"(b.y));
+// Start fetching item `item`'s patch words and chain data into buffer `buf`
+// (cp.async: complete at the next cp.async.wait).
+__device__ __forceinline__ void prefetch_item(const PassArgs& a, uint8_t* sm, int buf, int item, int bR0, int bC0,
+                                              int tid) {
+    const int L = a.g.L, n_blocks = a.nb1 * a.nb1;
+    const int b = item % n_blocks, hw = item / n_blocks, word = hw >> 1, half = hw & 1;
+    const int bR = (bR0 + a.spacing * (b / a.nb1)) % L, bC = (bC0 + a.spacing * (b % a.nb1)) % L;
+    uint8_t* ib = sm + kSmItem + buf * kItemBytes;
+    if (tid < kP * kP) {
+        const int R = (bR - 3 + tid / kP + 2 * L) % L, C = (bC - 3 + tid % kP + 2 * L) % L;
+        const uint32_t* src = a.v + static_cast<size_t>(word) * a.g.N + R * L + C;
+        asm volatile("cp.async.ca.shared.global [%0], [%1], 4;" ::"r"(umma::smem_addr(ib + 4 * tid)), "l"(src)
+                     : "memory");
+    } else if (tid < kP * kP + kItemChains) {
+        const int c = tid - kP * kP, chain = word * 32 + half * 16 + c;
+        asm volatile("cp.async.ca.shared.global [%0], [%1], 16;" ::"r"(umma::smem_addr(ib + 416 + 16 * c)),
+                     "l"(a.chain_bh + 4 * static_cast<size_t>(chain))
+                     : "memory");
+        for (int j = 0; j < 3; ++j)
+            asm volatile("cp.async.ca.shared.global [%0], [%1], 4;" ::"r"(umma::smem_addr(ib + 672 + 16 * c + 4 * j)),
+                         "l"(a.chain_q + 3 * static_cast<size_t>(chain) + j)
+                         : "memory");
+    }
+    asm volatile("cp.async.commit_group;" ::: "memory");
 }
 
-// The A fragment of one m16k16 tile from four 8x8 bf16 matrices in shared
-// memory; each lane passes the address of one 16-byte matrix row.
-__device__ __forceinline__ void ldmatrix_x4(uint32_t (&r)[4], uint32_t addr) {
-    asm volatile("ldmatrix.sync.aligned.m8n8.x4.shared.b16 {%0,%1,%2,%3}, [%4];\n"
-                 : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3])
-                 : "r"(addr));
+// Start fetching the folded layer-1 constants of parity variant `var`: row
+// (x, y) of 16 floats at stride kC1Stride (c1 is stored [var][y * 8 + x][16]).
+__device__ __forceinline__ void fetch_c1(const PassArgs& a, uint8_t* sm, int var, int tid) {
+    uint8_t* cb = sm + kSmC1;
+    for (int q = tid; q < 64 * 4; q += kPassThreads) {
+        const int row = q >> 2, x = row >> 3, y = row & 7;
+        asm volatile("cp.async.ca.shared.global [%0], [%1], 16;" ::"r"(
+                         umma::smem_addr(cb + (row * kC1Stride + 4 * (q & 3)) * 4)),
+                     "l"(a.c1 + (var * 64 + y * 8 + x) * 16 + 4 * (q & 3))
+                     : "memory");
+    }
+    asm volatile("cp.async.commit_group;" ::: "memory");
 }
 
-__device__ __forceinline__ uint32_t pack_bf16(float lo, float hi) {
-    const __nv_bfloat162 p = __floats2bfloat162_rn(lo, hi);
-    return *reinterpret_cast<const uint32_t*>(&p);
-}
-
-// Word offset of 16-byte half h of activation row R (see the layout above).
-__device__ __forceinline__ int act_half(int R, int h) { return R * 8 + ((h ^ (R >> 2)) & 1) * 4; }
-
-// One pass of MH block moves: CTA = (block of the pass, packed word).
-__global__ void __launch_bounds__(kPassThreads, 2) k_prop_pass(const __grid_constant__ PassArgs a) {
-    extern __shared__ __align__(16) uint32_t sm[];
+// One pass of MH block moves; persistent CTAs of four warps take items
+// (block b, half-word hw) in turn.
+__global__ void __launch_bounds__(kPassThreads, 4) k_prop_pass(const __grid_constant__ PassArgs a) {
+    extern __shared__ __align__(1024) uint8_t sm[];
     const int L = a.g.L, N = a.g.N;
-    const int word = blockIdx.y, b = blockIdx.x;
-    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-    const int gq = lane >> 2, tq = lane & 3;
-    uint32_t* A1 = sm + kSmA1;                 // [32][64] rows, layer-1 output
-    uint32_t* A2 = sm + kSmA2;                 // [32][36] rows, layer-2 output
-    // layer-1 inputs, in A2's space until layer 2 writes it
-    uint16_t* sp = reinterpret_cast<uint16_t*>(A2);        // [32][100] spin plane, bf16
-    float* c1s = reinterpret_cast<float*>(A2 + 1600);       // [64][16] position constants
-    float* cbs = c1s + kS1 * kS1 * 16;                      // [32][16] b1 + beta w_beta + h w_h
-    uint2* fr = reinterpret_cast<uint2*>(sm + kSmFr);       // [kFrags][32]
-    uint32_t* pw = sm + kSmPw;                              // [100] patch words
-    // after layer 2 (A1 is free): logits and the Metropolis-Hastings terms
-    // ([site][lane], so a warp's 32 chains fall in distinct banks)
-    float* logit = reinterpret_cast<float*>(A1);   // [16][32]
-    float* lqc = logit + 512;                      // [16][32] log q of the current spin
-    float* lqn = lqc + 512;                        // [16][32] log q of the proposed spin
-    int* s_xx = reinterpret_cast<int*>(lqn + 512);  // [16][32] bit 0: current +1, bit 1: proposed +1
-    long long* s_de = reinterpret_cast<long long*>(s_xx + 512);  // [16][32] energy-change terms
-    uint32_t* s_thr = reinterpret_cast<uint32_t*>(s_de + 512);    // [16][32] proposal thresholds
-    const uint32_t a1_base = static_cast<uint32_t>(__cvta_generic_to_shared(A1));
-    const uint32_t a2_base = static_cast<uint32_t>(__cvta_generic_to_shared(A2));
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+    const int n_blocks = a.nb1 * a.nb1;
+    uint8_t* X = sm + kSmX;
+    uint16_t* Bs = reinterpret_cast<uint16_t*>(sm + kSmB);
+    const uint32_t bar = umma::smem_addr(sm + kSmBar);
+    uint32_t* tslot = reinterpret_cast<uint32_t*>(sm + kSmBar + 8);
+    __shared__ int s_fail;
+    // Metropolis-Hastings arrays in X after layer 3 ([site][chain] or [part][chain], 16 chains)
+    float* logit = reinterpret_cast<float*>(X);                   // [16 sites][16]
+    uint32_t* s_thr = reinterpret_cast<uint32_t*>(logit + 256);   // [16 sites][16]
+    int* s_xx = reinterpret_cast<int*>(s_thr + 256);  // [16 sites][16] bit 0: current +1, bit 1: proposed +1
+    float* p_lq = reinterpret_cast<float*>(s_xx + 256);  // [8 parts][16] sum log q(cur) - log q(new)
+    uint32_t* p_bits = reinterpret_cast<uint32_t*>(p_lq + 128);  // [8 parts][16] cur | new << 16
+    uint32_t* s_uacc = p_bits + 128;                  // [16] accept draw
+    long long* p_de = reinterpret_cast<long long*>(s_uacc + 16);  // [8 parts][16] dE shares
 
-    // block origin of this pass
+    // set-up: B operands, zero X (the shift rows past 128 must hold finite values), mbarrier, TMEM
+    for (int x = tid; x < kBElems / 8; x += kPassThreads) reinterpret_cast<uint4*>(Bs)[x] = a.bmat[x];
+    for (int x = tid; x < kSmXBytes / 16; x += kPassThreads) reinterpret_cast<uint4*>(X)[x] = make_uint4(0, 0, 0, 0);
+    if (tid == 0) {
+        umma::mbar_init(bar, 1);
+        s_fail = 0;
+    }
+    if (warp == 0) umma::tmem_alloc(umma::smem_addr(tslot), kTmemCols);
     const U4 off = philox(a.pass, 0u, 0u, kTagOffset, a.key0, a.key1);
-    const int bR = static_cast<int>((off.x % static_cast<uint32_t>(L) + a.spacing * (b / a.nb1)) % L);
-    const int bC = static_cast<int>((off.y % static_cast<uint32_t>(L) + a.spacing * (b % a.nb1)) % L);
-    for (int x = threadIdx.x; x < kP * kP; x += blockDim.x) {  // per patch position
-        const int R = (bR - 3 + x / kP + 2 * L) % L, C = (bC - 3 + x % kP + 2 * L) % L;
-        pw[x] = a.v[static_cast<size_t>(word) * N + R * L + C];
-    }
-    {
-        const int var = ((bR + 1) & 1) * 2 + ((bC + 1) & 1);  // parity of the patch's first row, column
-        const float* c1v = a.c1 + var * (kS1 * kS1 * 16);
-        for (int i = threadIdx.x; i < kS1 * kS1 * 16; i += blockDim.x) c1s[i] = c1v[i];
-        for (int i = threadIdx.x; i < 32 * 16; i += blockDim.x) {
-            const int c = i >> 4, n = i & 15, chain = word * 32 + c;
-            cbs[i] = a.bias[n] + a.chain_bh[4 * chain] * a.c1[kC1Pos + n] +
-                     a.chain_bh[4 * chain + 1] * a.c1[kC1Pos + 16 + n];
-        }
-    }
-    for (int x = threadIdx.x; x < kFrags * 32; x += blockDim.x) fr[x] = a.frag[x];
+    const int bR0 = static_cast<int>(off.x % static_cast<uint32_t>(L));
+    const int bC0 = static_cast<int>(off.y % static_cast<uint32_t>(L));
+    if (blockIdx.x < a.n_items) prefetch_item(a, sm, 0, blockIdx.x, bR0, bC0, tid);
+    umma::fence_before_sync();
     __syncthreads();
-    // spin plane: +-1 outside the block, 0 inside
-    for (int x = threadIdx.x; x < 32 * kP * kP; x += blockDim.x) {
-        const int c = x / (kP * kP), pos = x - c * (kP * kP);
-        const int y = pos / kP, xx = pos - y * kP;
-        const bool in = y >= 3 && y < 3 + kK && xx >= 3 && xx < 3 + kK;
-        sp[x] = in ? 0 : (((pw[pos] >> c) & 1u) ? 0x3F80 : 0xBF80);
-    }
-    __syncthreads();
-    // ---- layer 1: rows (chain, y*8+x) = 2048 (128 m-tiles), K = 9 taps
-    for (int mt = warp; mt < 128; mt += kPassThreads / 32) {
-        const int chain = mt >> 2, p0 = (mt & 3) * 16;
-        const int pA = p0 + gq, pB = p0 + gq + 8;  // the two rows of this lane
-        const uint16_t* sc = sp + chain * kP * kP;
-        const int oA = (pA >> 3) * kP + (pA & 7), oB = (pB >> 3) * kP + (pB & 7);
-        const int t0 = 2 * tq, t1 = 2 * tq + 1;
-        const int d0 = (t0 / 3) * kP + t0 % 3, d1 = (t1 / 3) * kP + t1 % 3;
-        uint32_t af[4];
-        af[0] = sc[oA + d0] | (static_cast<uint32_t>(sc[oA + d1]) << 16);
-        af[1] = sc[oB + d0] | (static_cast<uint32_t>(sc[oB + d1]) << 16);
-        af[2] = tq == 0 ? sc[oA + 2 * kP + 2] : 0u;  // tap 8; taps 9-15 are padding
-        af[3] = tq == 0 ? sc[oB + 2 * kP + 2] : 0u;
-        float d[2][4] = {};
-        mma_bf16(d[0], af, fr[0 * 32 + lane]);
-        mma_bf16(d[1], af, fr[1 * 32 + lane]);
+    umma::fence_after_sync();
+    const uint32_t tmem = *tslot;
+    const uint32_t xs = umma::smem_addr(X), bs = umma::smem_addr(Bs);
+    uint32_t phase = 0;
+    // this thread's accumulator lane 32 warp + lane = row (chain cl, frame row y)
+    const int my_row = 32 * warp + lane, my_c = my_row >> 3, my_y = my_row & 7;
+    const uint32_t tl = tmem + (static_cast<uint32_t>(32 * warp) << 16);
+    float b2[16];
 #pragma unroll
-        for (int nt = 0; nt < 2; ++nt) {
-            const int n = 8 * nt + 2 * tq;
-            const float2 cb = *reinterpret_cast<const float2*>(cbs + chain * 16 + n);
-            const float2 cA = *reinterpret_cast<const float2*>(c1s + pA * 16 + n);
-            const float2 cB = *reinterpret_cast<const float2*>(c1s + pB * 16 + n);
-            const int RA = chain * 64 + pA, RB = chain * 64 + pB;
-            A1[act_half(RA, nt) + tq] = pack_bf16(fmaxf(d[nt][0] + (cA.x + cb.x), 0.f), fmaxf(d[nt][1] + (cA.y + cb.y), 0.f));
-            A1[act_half(RB, nt) + tq] = pack_bf16(fmaxf(d[nt][2] + (cB.x + cb.x), 0.f), fmaxf(d[nt][3] + (cB.y + cb.y), 0.f));
-        }
-    }
-    __syncthreads();
-    // ---- layer 2: rows (chain, y*6+x) = 1152 (72 m-tiles), K = 9 taps x 16 ch.
-    // ldmatrix: lane l gives the row (l & 7) + 8 ((l >> 3) & 1), half l >> 4.
-    const int lrow = (lane & 7) + 8 * ((lane >> 3) & 1), lhalf = lane >> 4;
-    uint2 b2[kFrag2];  // this lane's B fragments of layer 2, kept for all its m-tiles
+    for (int n = 0; n < 16; ++n) b2[n] = a.bias[n];
+    const float b3 = a.bias[16];
+    bool ok = true;
+    int buf = 0;
+
+    for (int item = blockIdx.x; item < a.n_items && ok; item += gridDim.x, buf ^= 1) {
+        const int b = item % n_blocks, hw = item / n_blocks;
+        const int word = hw >> 1, half = hw & 1;
+        const int bR = (bR0 + a.spacing * (b / a.nb1)) % L, bC = (bC0 + a.spacing * (b % a.nb1)) % L;
+        const uint8_t* ib = sm + kSmItem + buf * kItemBytes;
+        const uint32_t* pw = reinterpret_cast<const uint32_t*>(ib);               // [100] patch words
+        const float* cbh = reinterpret_cast<const float*>(ib + 416);            // [16][4] chain_bh
+        const int32_t* cq = reinterpret_cast<const int32_t*>(ib + 672);         // [16][4] Q.4 J, J', h
+        const float* c1s = reinterpret_cast<const float*>(sm + kSmC1);
+        asm volatile("cp.async.wait_all;" ::: "memory");
+        __syncthreads();
+        fetch_c1(a, sm, ((bR + 1) & 1) * 2 + ((bC + 1) & 1), tid);
+        if (item + static_cast<int>(gridDim.x) < a.n_items)   // the next item's data, during this one
+            prefetch_item(a, sm, buf ^ 1, item + gridDim.x, bR0, bC0, tid);
+        else
+            asm volatile("cp.async.commit_group;" ::: "memory");
+        // ---- layer-1 operand: rows x * 128 + (chain c, y) = tid, K = 9 spin taps (0 inside
+        // the block), then 1, beta, beta, h, h (the constant columns), 0, 0
+        {
+            const int c = my_c, y = my_y, bit = half * 16 + c;
+            uint32_t sp[3][kP];  // bf16 spin values of patch rows y .. y + 2
 #pragma unroll
-    for (int f = 0; f < kFrag2; ++f) b2[f] = fr[(kFrag1 + f) * 32 + lane];
-    for (int mt = warp; mt < 72; mt += kPassThreads / 32) {
-        const int r = mt * 16 + lrow;
-        const int c = r / 36, q = r - c * 36;
-        const int R0 = c * 64 + (q / 6) * 8 + q % 6;
-        float d[2][4] = {};
+            for (int dy = 0; dy < 3; ++dy)
 #pragma unroll
-        for (int tap = 0; tap < 9; ++tap) {
-            const int R = R0 + (tap / 3) * 8 + tap % 3;
-            uint32_t af[4];
-            ldmatrix_x4(af, a1_base + 4u * static_cast<uint32_t>(act_half(R, lhalf)));
-            mma_bf16(d[0], af, b2[tap * 2 + 0]);
-            mma_bf16(d[1], af, b2[tap * 2 + 1]);
-        }
-        const int rA = mt * 16 + gq, rB = rA + 8;
-        const int cA = rA / 36, qA = rA - cA * 36, cB = rB / 36, qB = rB - cB * 36;
+                for (int Xc = 0; Xc < kP; ++Xc) {
+                    const int Y = y + dy;
+                    const uint32_t keep = (Y >= 3 && Y < 3 + kK && Xc >= 3 && Xc < 3 + kK) ? 0u : 0xFFFFu;
+                    sp[dy][Xc] = (0xBF80u ^ (((pw[Y * kP + Xc] >> bit) & 1u) << 15)) & keep;
+                }
+            const uint32_t beta_b = __float_as_uint(cbh[4 * c]) >> 16, h_b = __float_as_uint(cbh[4 * c + 1]) >> 16;
+            const uint4 k1 = make_uint4(0u, beta_b | (beta_b << 16), h_b | (h_b << 16), 0u);
 #pragma unroll
-        for (int nt = 0; nt < 2; ++nt) {
-            const int n = 8 * nt + 2 * tq;
-            const float b0 = a.bias[16 + n], b1 = a.bias[16 + n + 1];
-            A2[act_half(cA * 36 + qA, nt) + tq] = pack_bf16(fmaxf(d[nt][0] + b0, 0.f), fmaxf(d[nt][1] + b1, 0.f));
-            A2[act_half(cB * 36 + qB, nt) + tq] = pack_bf16(fmaxf(d[nt][2] + b0, 0.f), fmaxf(d[nt][3] + b1, 0.f));
-        }
-    }
-    __syncthreads();
-    // ---- layer 3: rows (chain, y*4+x) = 512 (32 m-tiles), one output channel
-    for (int mt = warp; mt < 32; mt += kPassThreads / 32) {
-        const int ch = mt;  // one m-tile = the 16 block sites of chain mt
-        const int R0 = ch * 36 + (lrow >> 2) * 6 + (lrow & 3);
-        float d[4] = {};
-#pragma unroll
-        for (int tap = 0; tap < 9; ++tap) {
-            const int R = R0 + (tap / 3) * 6 + tap % 3;
-            uint32_t af[4];
-            ldmatrix_x4(af, a2_base + 4u * static_cast<uint32_t>(act_half(R, lhalf)));
-            mma_bf16(d, af, fr[(kFrag1 + kFrag2 + tap) * 32 + lane]);
-        }
-        if (tq == 0) {
-            logit[gq * 32 + ch] = d[0] + a.bias[32];
-            logit[(gq + 8) * 32 + ch] = d[2] + a.bias[32];
-        }
-    }
-    __syncthreads();
-    // ---- Metropolis-Hastings, phase A on every warp: lane = chain, warp w
-    // draws Philox call w / 2 of its chain (4 sites) and takes sites
-    // 4 (w / 2) + 2 (w % 2) + {0, 1}: threshold, log q of the current and the
-    // proposed spin, the proposed spin.
-    const int chain = word * 32 + lane;
-    const uint32_t cell_id = static_cast<uint32_t>(b);
-    const int qJ = a.chain_q[3 * chain], qJp = a.chain_q[3 * chain + 1], qh = a.chain_q[3 * chain + 2];
-    {
-        const int call = warp >> 1;
-        const U4 u = philox(cell_id, a.pass, static_cast<uint32_t>(chain), kTagBits + call, a.key0, a.key1);
-#pragma unroll
-        for (int j = 0; j < 2; ++j) {
-            const int s = 4 * call + 2 * (warp & 1) + j;
-            const int pos = (3 + s / kK) * kP + 3 + s % kK;
-            const int xc = ((pw[pos] >> lane) & 1u) ? 1 : -1;
-            const float q = 1.f / (1.f + __expf(-logit[s * 32 + lane]));
-            float tf = q * 4294967296.f;
-            tf = fminf(fmaxf(tf, 1.f), 4294967040.f);
-            const uint32_t thr = static_cast<uint32_t>(tf);
-            const float p1 = static_cast<float>(thr) * 2.3283064365386963e-10f;
-            const float lp = __logf(p1), lm = log1pf(-p1);
-            const int xp = pick(u, s & 3) < thr ? 1 : -1;
-            lqc[s * 32 + lane] = xc > 0 ? lp : lm;
-            lqn[s * 32 + lane] = xp > 0 ? lp : lm;
-            s_xx[s * 32 + lane] = (xc > 0 ? 1 : 0) | (xp > 0 ? 2 : 0);
-            s_thr[s * 32 + lane] = thr;
-        }
-    }
-    __syncthreads();
-    // phase A': each site's share of the exact energy change (1/16 units) over
-    // the bonds touching the block; a bond inside the block is counted by its
-    // left / upper endpoint (right and down neighbours, and the dimer partner
-    // of higher index)
-    {
-        auto spin_at = [&](int pr, int pc) -> int { return ((pw[pr * kP + pc] >> lane) & 1u) ? 1 : -1; };
-        auto xs = [&](int t) { return (s_xx[t * 32 + lane] & 1) ? 1 : -1; };
-        auto ns = [&](int t) { return (s_xx[t * 32 + lane] & 2) ? 1 : -1; };
-#pragma unroll
-        for (int j = 0; j < 2; ++j) {
-            const int s = 4 * (warp >> 1) + 2 * (warp & 1) + j;
-            const int ar = s / kK, ac = s % kK;
-            const int x0 = xs(s), n0 = ns(s), d = n0 - x0;
-            long long dE = -static_cast<long long>(qh) * d;
-            if (ac + 1 < kK) dE += static_cast<long long>(qJ) * (n0 * ns(s + 1) - x0 * xs(s + 1));
-            else dE += static_cast<long long>(qJ) * d * spin_at(3 + ar, 3 + ac + 1);
-            if (ar + 1 < kK) dE += static_cast<long long>(qJ) * (n0 * ns(s + kK) - x0 * xs(s + kK));
-            else dE += static_cast<long long>(qJ) * d * spin_at(3 + ar + 1, 3 + ac);
-            if (ac == 0) dE += static_cast<long long>(qJ) * d * spin_at(3 + ar, 2);
-            if (ar == 0) dE += static_cast<long long>(qJ) * d * spin_at(2, 3 + ac);
-            // the orthogonal dimer of this site
-            const int R = bR + ar, C = bC + ac;
-            const int dR = (R & 1) ? ((C & 1) ? -1 : 1) : ((C & 1) ? -1 : 1);
-            const int dC = (R & 1) ? -1 : 1;
-            const int pr = ar + dR, pc = ac + dC;
-            if (pr >= 0 && pr < kK && pc >= 0 && pc < kK) {
-                const int t = pr * kK + pc;
-                if (t > s) dE += static_cast<long long>(qJp) * (n0 * ns(t) - x0 * xs(t));
-            } else {
-                dE += static_cast<long long>(qJp) * d * spin_at(3 + pr, 3 + pc);
+            for (int x = 0; x < kFrame; ++x) {
+                const int r = x * 128 + my_row;
+                reinterpret_cast<uint4*>(X + r * 16)[0] =
+                    make_uint4(sp[0][x] | (sp[0][x + 1] << 16), sp[0][x + 2] | (sp[1][x] << 16),
+                               sp[1][x + 1] | (sp[1][x + 2] << 16), sp[2][x] | (sp[2][x + 1] << 16));
+                uint4 q = k1;
+                q.x = sp[2][x + 2] | (0x3F80u << 16);
+                reinterpret_cast<uint4*>(X + kA0Plane + r * 16)[0] = q;
             }
-            s_de[s * 32 + lane] = dE;
         }
+        asm volatile("cp.async.wait_group 1;" ::: "memory");  // this item's constants (not the next item's data)
+        umma::fence_async_smem();
+        umma::fence_before_sync();
+        __syncthreads();
+        if (tid == 0) {  // layer 1: one K = 16 MMA per frame column x (accumulator columns 16 x)
+            umma::fence_after_sync();
+            for (int x = 0; x < kFrame; ++x)
+                umma::mma(tmem + 16 * x, umma::desc(xs + 2048 * x, kA0Plane, 128), umma::desc(bs + 2 * kB1, 256, 128),
+                          kIdesc1, 0u);
+            umma::commit(bar);
+        }
+        if (!umma::mbar_wait(bar, phase, kWaitTries)) s_fail = 1;
+        phase ^= 1u;
+        umma::fence_after_sync();
+        // ---- epilogue 1: + folded constants, ReLU, bf16 -> column planes (x, h), row my_row
+        for (int x = 0; x < kFrame; x += 2) {
+            uint32_t r0[16], r1[16];
+            umma::tmem_ld16(tl + 16 * x, r0);
+            umma::tmem_ld16(tl + 16 * (x + 1), r1);
+            umma::tmem_ld_wait();
+#pragma unroll
+            for (int t = 0; t < 2; ++t) {
+                const uint32_t* r = t ? r1 : r0;
+                const float4* cr = reinterpret_cast<const float4*>(c1s + ((x + t) * 8 + my_y) * kC1Stride);
+                uint32_t o[8];
+#pragma unroll
+                for (int q = 0; q < 4; ++q) {
+                    const float4 f = cr[q];
+                    o[2 * q] = umma::relu_bf16x2(__uint_as_float(r[4 * q]) + f.x, __uint_as_float(r[4 * q + 1]) + f.y);
+                    o[2 * q + 1] =
+                        umma::relu_bf16x2(__uint_as_float(r[4 * q + 2]) + f.z, __uint_as_float(r[4 * q + 3]) + f.w);
+                }
+                uint8_t* pl = X + 2 * (x + t) * kPlane + my_row * 16;
+                reinterpret_cast<uint4*>(pl)[0] = make_uint4(o[0], o[1], o[2], o[3]);
+                reinterpret_cast<uint4*>(pl + kPlane)[0] = make_uint4(o[4], o[5], o[6], o[7]);
+            }
+        }
+#pragma unroll
+        for (int x = 0; x < 6; ++x) umma::tmem_zero16(tl + 16 * x);  // layer 2 accumulates from zero
+        umma::tmem_st_wait();
+        umma::fence_async_smem();
+        umma::fence_before_sync();
+        __syncthreads();
+        if (s_fail) {
+            ok = false;
+            break;
+        }
+        if (tid == 0) {  // layer 2: 3 tap rows x 8 input columns o, output columns o - 2 .. o
+            umma::fence_after_sync();
+            for (int dy = 0; dy < 3; ++dy)
+                for (int o = 0; o < kFrame; ++o) {
+                    const int lo = o < 2 ? 0 : o - 2, hi = o < 5 ? o : 5;
+                    umma::mma(tmem + 16 * lo, umma::desc(xs + 2 * o * kPlane + 16 * dy, kPlane, 128),
+                              umma::desc(bs + 2 * (kZ2 + dy * 2 * kZ2Rows * 8) + (2 - o + lo) * 256, kZ2Rows * 16, 128),
+                              umma::idesc_bf16_f32(128, 16 * (hi - lo + 1)), 1u);
+                }
+            umma::commit(bar);
+        }
+        if (!umma::mbar_wait(bar, phase, kWaitTries)) s_fail = 1;
+        phase ^= 1u;
+        umma::fence_after_sync();
+        // ---- epilogue 2: + b2, ReLU, bf16 -> column planes 0..5 (layer 3's operand)
+        for (int x = 0; x < 6; x += 2) {
+            uint32_t r0[16], r1[16];
+            umma::tmem_ld16(tl + 16 * x, r0);
+            umma::tmem_ld16(tl + 16 * (x + 1), r1);
+            umma::tmem_ld_wait();
+#pragma unroll
+            for (int t = 0; t < 2; ++t) {
+                const uint32_t* r = t ? r1 : r0;
+                uint32_t o[8];
+#pragma unroll
+                for (int n = 0; n < 8; ++n)
+                    o[n] = umma::relu_bf16x2(__uint_as_float(r[2 * n]) + b2[2 * n],
+                                             __uint_as_float(r[2 * n + 1]) + b2[2 * n + 1]);
+                uint8_t* pl = X + 2 * (x + t) * kPlane + my_row * 16;
+                reinterpret_cast<uint4*>(pl)[0] = make_uint4(o[0], o[1], o[2], o[3]);
+                reinterpret_cast<uint4*>(pl + kPlane)[0] = make_uint4(o[4], o[5], o[6], o[7]);
+            }
+        }
+        umma::fence_async_smem();
+        umma::fence_before_sync();
+        __syncthreads();
+        if (s_fail) {
+            ok = false;
+            break;
+        }
+        if (tid == 0) {  // layer 3: banded, 3 tap rows x 6 input columns, N = the block's 4 columns (+ 12)
+            umma::fence_after_sync();
+            for (int dy = 0; dy < 3; ++dy)
+                for (int o = 0; o < 6; ++o)
+                    umma::mma(tmem, umma::desc(xs + 2 * o * kPlane + 16 * dy, kPlane, 128),
+                              umma::desc(bs + 2 * (kZ3 + dy * 2 * kZ3Rows * 8) + (7 - o) * 16, kZ3Rows * 16, 128),
+                              kIdesc3, (dy | o) ? 1u : 0u);
+            umma::commit(bar);
+        }
+        if (!umma::mbar_wait(bar, phase, kWaitTries)) s_fail = 1;
+        phase ^= 1u;
+        umma::fence_after_sync();
+        // ---- epilogue 3: rows y < 4 hold the logits of block sites (y, 0..3)
+        {
+            uint32_t r[4];
+            umma::tmem_ld4(tl, r);
+            umma::tmem_ld_wait();
+            if (my_y < kK) {
+#pragma unroll
+                for (int x = 0; x < kK; ++x) logit[(my_y * kK + x) * 16 + my_c] = __uint_as_float(r[x]) + b3;
+            }
+        }
+        umma::fence_before_sync();
+        __syncthreads();
+        if (s_fail) {
+            ok = false;
+            break;
+        }
+        // ---- Metropolis-Hastings, phase A: thread = (chain c, Philox call k, pair jj): sites
+        // 4 k + 2 jj + {0, 1}: threshold, the proposed spin, this pair's share of
+        // log q(current) - log q(proposed); threads k = jj = 0 also draw the accept word
+        const int c = tid & 15, k = (tid >> 4) & 3, jj = tid >> 6;
+        const int part = 2 * k + jj;
+        const int chain = word * 32 + half * 16 + c;
+        const int cbit = half * 16 + c;
+        const uint32_t cell_id = static_cast<uint32_t>(b);
+        {
+            const U4 u = philox(cell_id, a.pass, static_cast<uint32_t>(chain), kTagBits + k, a.key0, a.key1);
+            float lq = 0.f;
+            uint32_t bits = 0u;
+#pragma unroll
+            for (int j = 0; j < 2; ++j) {
+                const int s = 4 * k + 2 * jj + j;
+                const int pos = (3 + s / kK) * kP + 3 + s % kK;
+                const bool xc = (pw[pos] >> cbit) & 1u;
+                const float q = 1.f / (1.f + __expf(-logit[s * 16 + c]));
+                float tf = q * 4294967296.f;
+                tf = fminf(fmaxf(tf, 1.f), 4294967040.f);
+                const uint32_t thr = static_cast<uint32_t>(tf);
+                const float p1 = static_cast<float>(thr) * 2.3283064365386963e-10f;
+                const float lp = __logf(p1), lm = log1pf(-p1);
+                const bool xp = pick(u, s & 3) < thr;
+                lq += (xc ? lp : lm) - (xp ? lp : lm);
+                s_xx[s * 16 + c] = (xc ? 1 : 0) | (xp ? 2 : 0);
+                s_thr[s * 16 + c] = thr;
+                bits |= (xc ? 1u : 0u) << s | (xp ? 1u : 0u) << (16 + s);
+            }
+            p_lq[part * 16 + c] = lq;
+            p_bits[part * 16 + c] = bits;
+            if (part == 0) s_uacc[c] = philox(cell_id, a.pass, static_cast<uint32_t>(chain), kTagAccept, a.key0, a.key1).x;
+        }
+        __syncthreads();
+        // phase A': this pair's share of the exact energy change (1/16 units)
+        // over the bonds touching the block; a bond inside the block is counted
+        // by its left / upper endpoint (right and down neighbours, and the dimer
+        // partner of higher index)
+        {
+            const int qJ = cq[4 * c], qJp = cq[4 * c + 1], qh = cq[4 * c + 2];
+            auto spin_at = [&](int pr, int pc) -> int { return ((pw[pr * kP + pc] >> cbit) & 1u) ? 1 : -1; };
+            auto xs_ = [&](int t) { return (s_xx[t * 16 + c] & 1) ? 1 : -1; };
+            auto ns = [&](int t) { return (s_xx[t * 16 + c] & 2) ? 1 : -1; };
+            long long de2 = 0;
+#pragma unroll
+            for (int j = 0; j < 2; ++j) {
+                const int s = 4 * k + 2 * jj + j;
+                const int ar = s / kK, ac = s % kK;
+                const int x0 = xs_(s), n0 = ns(s), d = n0 - x0;
+                long long dE = -static_cast<long long>(qh) * d;
+                if (ac + 1 < kK) dE += static_cast<long long>(qJ) * (n0 * ns(s + 1) - x0 * xs_(s + 1));
+                else dE += static_cast<long long>(qJ) * d * spin_at(3 + ar, 3 + ac + 1);
+                if (ar + 1 < kK) dE += static_cast<long long>(qJ) * (n0 * ns(s + kK) - x0 * xs_(s + kK));
+                else dE += static_cast<long long>(qJ) * d * spin_at(3 + ar + 1, 3 + ac);
+                if (ac == 0) dE += static_cast<long long>(qJ) * d * spin_at(3 + ar, 2);
+                if (ar == 0) dE += static_cast<long long>(qJ) * d * spin_at(2, 3 + ac);
+                // the orthogonal dimer of this site
+                const int R = bR + ar, C = bC + ac;
+                const int dR = (R & 1) ? ((C & 1) ? -1 : 1) : ((C & 1) ? -1 : 1);
+                const int dC = (R & 1) ? -1 : 1;
+                const int pr = ar + dR, pc = ac + dC;
+                if (pr >= 0 && pr < kK && pc >= 0 && pc < kK) {
+                    const int t = pr * kK + pc;
+                    if (t > s) dE += static_cast<long long>(qJp) * (n0 * ns(t) - x0 * xs_(t));
+                } else {
+                    dE += static_cast<long long>(qJp) * d * spin_at(3 + pr, 3 + pc);
+                }
+                de2 += dE;
+            }
+            p_de[part * 16 + c] = de2;
+        }
+        __syncthreads();
+        // ---- phase B, warp 0, lane = chain (lanes >= 16 follow lane - 16 and drop out):
+        // the eight shares in order, the exact MH test and the move
+        if (warp == 0) {
+            const int cc = lane & 15;
+            float lq = 0.f;
+            long long dE = 0;
+            uint32_t bits = 0u;
+#pragma unroll
+            for (int q = 0; q < 8; ++q) {
+                lq += p_lq[q * 16 + cc];
+                dE += p_de[q * 16 + cc];
+                bits |= p_bits[q * 16 + cc];
+            }
+            const uint32_t cb = bits & 0xFFFFu, nb = bits >> 16;
+            const float beta = cbh[4 * cc + 2];  // the exact beta: the MH test targets exp(-beta H)
+            const float log_alpha = -beta * static_cast<float>(dE) * 0.0625f + lq;
+            const bool accept = lane < 16 && (log_alpha >= 0.f ||
+                                              static_cast<float>(s_uacc[cc] >> 8) * 5.9604644775390625e-08f <
+                                                  __expf(log_alpha));
+            if (a.rec) {  // inspection: record, do not move
+                if (lane < 16) {
+                    PassRecord* r = a.rec + (static_cast<size_t>(word) * n_blocks + b) * 32 + half * 16 + cc;
+#pragma unroll
+                    for (int s = 0; s < kK * kK; ++s) {
+                        r->logit[s] = logit[s * 16 + cc];
+                        r->thr[s] = s_thr[s * 16 + cc];
+                    }
+                    r->dE = static_cast<int32_t>(dE);
+                    r->cur_bits = cb;
+                    r->new_bits = nb;
+                    r->log_alpha = log_alpha;
+                    r->bR = bR;
+                    r->bC = bC;
+                }
+            } else {
+                const uint32_t am = __ballot_sync(0xffffffffu, accept);
+                const uint32_t flip = accept ? (cb ^ nb) : 0u;
+                uint32_t my_fm = 0u;  // lane s < 16: the chains whose site s flips
+#pragma unroll
+                for (int s = 0; s < kK * kK; ++s) {
+                    const uint32_t fm = __ballot_sync(0xffffffffu, (flip >> s) & 1u) & 0xFFFFu;
+                    my_fm = lane == s ? fm : my_fm;
+                }
+                if (lane < 16 && my_fm) {
+                    const int R = (bR + lane / kK) % L, C = (bC + lane % kK) % L;
+                    atomicXor(a.v + static_cast<size_t>(word) * N + R * L + C, my_fm << (16 * half));
+                }
+                if (lane == 0) {
+                    atomicAdd(&a.stats[0], static_cast<unsigned long long>(kItemChains));
+                    atomicAdd(&a.stats[1], static_cast<unsigned long long>(__popc(am)));
+                }
+            }
+        }
+        __syncthreads();
     }
+    asm volatile("cp.async.wait_all;" ::: "memory");
+    // a timed-out wait: record it, give the tensor cores one more bounded wait
+    // for the MMAs in flight, then free the tensor memory
+    if (!ok) {
+        if (tid == 0) atomicAdd(&a.stats[2], 1ull);
+        umma::mbar_wait(bar, phase ^ 1u, kWaitTries);
+    }
+    umma::fence_before_sync();
     __syncthreads();
-    // ---- phase B, warp 0, lane = chain: sums over the sites in site order,
-    // the exact MH test and the move
-    if (warp != 0) return;
-    float logq_cur = 0.f, logq_new = 0.f;
-    long long dE = 0;
-    uint32_t cb = 0, nb = 0;
-#pragma unroll
-    for (int s = 0; s < kK * kK; ++s) {
-        logq_cur += lqc[s * 32 + lane];
-        logq_new += lqn[s * 32 + lane];
-        dE += s_de[s * 32 + lane];
-        const int xx = s_xx[s * 32 + lane];
-        cb |= static_cast<uint32_t>(xx & 1) << s;
-        nb |= static_cast<uint32_t>((xx >> 1) & 1) << s;
-    }
-    const float beta = a.chain_bh[4 * chain + 2];  // the exact beta: the MH test targets exp(-beta H)
-    const float log_alpha = -beta * static_cast<float>(dE) * 0.0625f + logq_cur - logq_new;
-    const U4 ua = philox(cell_id, a.pass, static_cast<uint32_t>(chain), kTagAccept, a.key0, a.key1);
-    const bool accept = log_alpha >= 0.f ||
-                        static_cast<float>(ua.x >> 8) * 5.9604644775390625e-08f < __expf(log_alpha);
-    if (a.rec) {  // inspection: record, do not move
-        PassRecord* r = a.rec + (static_cast<size_t>(word) * gridDim.x + b) * 32 + lane;
-#pragma unroll
-        for (int s = 0; s < kK * kK; ++s) {
-            r->logit[s] = logit[s * 32 + lane];
-            r->thr[s] = s_thr[s * 32 + lane];
-        }
-        r->dE = static_cast<int32_t>(dE);
-        r->cur_bits = cb;
-        r->new_bits = nb;
-        r->log_alpha = log_alpha;
-        r->bR = bR;
-        r->bC = bC;
-        return;
-    }
-    const uint32_t am = __ballot_sync(0xffffffffu, accept);
-#pragma unroll
-    for (int s = 0; s < kK * kK; ++s) {
-        const uint32_t wv = __ballot_sync(0xffffffffu, ((accept ? nb : cb) >> s) & 1u);
-        if (lane == s) {
-            const int R = (bR + s / kK) % L, C = (bC + s % kK) % L;
-            a.v[static_cast<size_t>(word) * N + R * L + C] = wv;
-        }
-    }
-    if (lane == 0) {
-        atomicAdd(&a.stats[0], 32ull);
-        atomicAdd(&a.stats[1], static_cast<unsigned long long>(__popc(am)));
+    if (warp == 0) {
+        umma::fence_after_sync();
+        umma::tmem_dealloc(tmem, kTmemCols);
     }
 }
 
@@ -524,33 +689,42 @@ __global__ void k_prop_round(const float* w, float* wb, int n) {
     if (i < n) wb[i] = bf16r(w[i]);
 }
 
-// mma B fragments and biases from the bf16-rounded weights (device side, so
-// the fragments follow the trained weights without a host round trip).
-__global__ void k_prop_fragments(const float* wb, uint2* frag, float* bias) {
+// The tensor-core B operands and biases from the bf16-rounded weights (on the
+// device, so they follow the trained weights without a host round trip), in
+// the layout described at kB1 / kZ2 / kZ3.  B1 (element (n, k) at (k / 8) *
+// 128 + n * 8 + k % 8): layer 1 on the spin plane (k < 9: tap k), then the
+// constant columns b1 (k = 9) and the tap sums of the beta and h kernels as
+// bf16 hi + lo pairs (k = 10, 11 and 12, 13).
+__global__ void k_prop_operands(const float* wb, uint16_t* bmat, float* bias) {
     const int i = blockIdx.x * blockDim.x + threadIdx.x;
-    if (i < 33) bias[i] = i < 16 ? wb[oB1 + i] : (i < 32 ? wb[oB2 + i - 16] : wb[oB3]);
-    if (i >= kFrags * 32) return;
-    const int f = i / 32, lane = i % 32, gq = lane >> 2, tq = lane & 3;
-    auto Bv = [&](int k, int n) -> float {
-        if (f < kFrag1) return k < 9 ? wb[oW1 + n * 6 * 9 + k] : 0.f;  // layer 1: k = tap of the spin plane
-        if (f < kFrag1 + kFrag2) {  // layer 2: k = tap * 16 + channel
-            return wb[oW2 + (n * 16 + (k & 15)) * 9 + (k >> 4)];
+    if (i < 17) bias[i] = i < 16 ? wb[oB2 + i] : wb[oB3];
+    if (i >= kBElems) return;
+    float v = 0.f;
+    if (i < kZ2) {
+        const int n = (i % 128) / 8, k = (i / 128) * 8 + i % 8;
+        if (k < 9) {
+            v = wb[oW1 + n * 6 * 9 + k];
+        } else if (k == 9) {
+            v = wb[oB1 + n];
+        } else if (k <= 13) {
+            const int ch = k < 12 ? 4 : 5;
+            float sum = 0.f;
+            for (int tap = 0; tap < 9; ++tap) sum += wb[oW1 + (n * 6 + ch) * 9 + tap];
+            const float hi = bf16r(sum);
+            v = ((k - 10) & 1) ? bf16r(sum - hi) : hi;
         }
-        return n == 0 ? wb[oW3 + (k & 15) * 9 + (k >> 4)] : 0.f;  // layer 3
-    };
-    int kt, nt;
-    if (f < kFrag1) {
-        kt = f / 2;
-        nt = f % 2;
-    } else if (f < kFrag1 + kFrag2) {
-        kt = (f - kFrag1) / 2;
-        nt = (f - kFrag1) % 2;
-    } else {
-        kt = f - kFrag1 - kFrag2;
-        nt = 0;
+    } else if (i < kZ3) {  // layer-2 taps: [dy][h][row j * 16 + n][8], tap column 2 - j
+        const int e = i - kZ2, dy = e / (2 * kZ2Rows * 8), r = e % (2 * kZ2Rows * 8);
+        const int h = r / (kZ2Rows * 8), row = (r % (kZ2Rows * 8)) / 8, ch = h * 8 + r % 8;
+        const int j = row / 16, n = row % 16, dx = 2 - j;
+        v = wb[oW2 + (n * 16 + ch) * 9 + dy * 3 + dx];
+    } else {  // layer-3 bands: [dy][h][row][8], row 7 - dx
+        const int e = i - kZ3, dy = e / (2 * kZ3Rows * 8), r = e % (2 * kZ3Rows * 8);
+        const int h = r / (kZ3Rows * 8), row = (r % (kZ3Rows * 8)) / 8, ch = h * 8 + r % 8;
+        const int dx = 7 - row;
+        if (dx >= 0 && dx <= 2) v = wb[oW3 + ch * 9 + dy * 3 + dx];
     }
-    const int n = 8 * nt + gq, k0 = 16 * kt + 2 * tq;
-    frag[i] = make_uint2(pack_bf16(Bv(k0, n), Bv(k0 + 1, n)), pack_bf16(Bv(k0 + 8, n), Bv(k0 + 9, n)));
+    bmat[i] = __bfloat16_as_ushort(__float2bfloat16_rn(v));
 }
 
 // The folded layer-1 constants (see kC1Pos) from the bf16-rounded weights:
@@ -593,8 +767,8 @@ struct crbm_proposal {
     float* v2 = nullptr;
     float* grad = nullptr;
     float* loss = nullptr;
-    uint2* frag = nullptr;   // mma B fragments
-    float* bias = nullptr;
+    uint16_t* bmat = nullptr;  // tensor-core B operands (bf16)
+    float* bias = nullptr;     // b2, b3
     float* c1 = nullptr;     // folded layer-1 constants
     unsigned long long* stats = nullptr;
     crbm::Example* ex = nullptr;
@@ -630,7 +804,7 @@ double unit_normal(uint64_t& s) {  // Box-Muller
 }
 
 cudaError_t refresh_fragments(crbm_proposal* p, cudaStream_t st) {
-    crbm::k_prop_fragments<<<(crbm::kFrags * 32 + 127) / 128, 128, 0, st>>>(p->wb, p->frag, p->bias);
+    crbm::k_prop_operands<<<(crbm::kBElems + 127) / 128, 128, 0, st>>>(p->wb, p->bmat, p->bias);
     crbm::k_prop_layer1_consts<<<(crbm::kC1 + 127) / 128, 128, 0, st>>>(p->wb, p->c1);
     return cudaGetLastError();
 }
@@ -698,7 +872,7 @@ cudaError_t launch_pass(crbm_ctx* ctx, crbm_proposal* p, crbm::PassRecord* rec) 
     a.g = ctx->g;
     a.rec = rec;
     a.v = ctx->d.v;
-    a.frag = p->frag;
+    a.bmat = reinterpret_cast<const uint4*>(p->bmat);
     a.bias = p->bias;
     a.c1 = p->c1;
     a.chain_bh = ctx->d.chain_bh;
@@ -709,11 +883,23 @@ cudaError_t launch_pass(crbm_ctx* ctx, crbm_proposal* p, crbm::PassRecord* rec) 
     a.pass = static_cast<uint32_t>(ctx->passes);
     a.nb1 = nb1;
     a.spacing = L / nb1;
-    const size_t smem = crbm::kSmWords * 4;
+    a.n_items = nb1 * nb1 * 2 * ctx->n_words;  // (block, 16-chain half of a word)
+    const size_t smem = crbm::kSmBytes;
     cudaError_t e = cudaFuncSetAttribute(crbm::k_prop_pass, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                          static_cast<int>(smem));
+    if (e == cudaSuccess)  // all of the unified L1 / shared memory as shared memory
+        e = cudaFuncSetAttribute(crbm::k_prop_pass, cudaFuncAttributePreferredSharedMemoryCarveout, 100);
+    int sms = 0, smem_sm = 0;
+    if (e == cudaSuccess) e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, ctx->device);
+    if (e == cudaSuccess) e = cudaDeviceGetAttribute(&smem_sm, cudaDevAttrMaxSharedMemoryPerMultiprocessor, ctx->device);
     if (e != cudaSuccess) return e;
-    crbm::k_prop_pass<<<dim3(nb1 * nb1, ctx->n_words), crbm::kPassThreads, smem, ctx->stream>>>(a);
+    // persistent: as many CTAs per SM as shared memory holds (each also takes
+    // 1 KB of static and 1 KB of reserved shared memory), at most four, whose
+    // tensor-memory columns, 4 x 128, fill the SM's 512.  (The occupancy
+    // query reports one CTA per SM for this kernel; four run side by side.)
+    const int per_sm = std::max(1, std::min(4, smem_sm / static_cast<int>(smem + 2048)));
+    const int grid = std::min(a.n_items, per_sm * sms);
+    crbm::k_prop_pass<<<grid, crbm::kPassThreads, smem, ctx->stream>>>(a);
     return cudaGetLastError();
 }
 
@@ -734,10 +920,10 @@ int crbm_proposal_create(crbm_proposal** out, int32_t block, uint64_t seed) {
     for (float** b : bufs)
         if (e == cudaSuccess) e = cudaMalloc(reinterpret_cast<void**>(b), kNP * sizeof(float));
     if (e == cudaSuccess) e = cudaMalloc(reinterpret_cast<void**>(&p->loss), sizeof(float));
-    if (e == cudaSuccess) e = cudaMalloc(reinterpret_cast<void**>(&p->frag), crbm::kFrags * 32 * sizeof(uint2));
+    if (e == cudaSuccess) e = cudaMalloc(reinterpret_cast<void**>(&p->bmat), crbm::kBElems * sizeof(uint16_t));
     if (e == cudaSuccess) e = cudaMalloc(reinterpret_cast<void**>(&p->bias), 33 * sizeof(float));
     if (e == cudaSuccess) e = cudaMalloc(reinterpret_cast<void**>(&p->c1), crbm::kC1 * sizeof(float));
-    if (e == cudaSuccess) e = cudaMalloc(reinterpret_cast<void**>(&p->stats), 2 * sizeof(unsigned long long));
+    if (e == cudaSuccess) e = cudaMalloc(reinterpret_cast<void**>(&p->stats), 4 * sizeof(unsigned long long));
     // He-style initial weights; the output layer starts small (q near 1/2)
     std::vector<float> w(kNP, 0.f);
     uint64_t s = seed ^ 0x243F6A8885A308D3ull;
@@ -747,7 +933,7 @@ int crbm_proposal_create(crbm_proposal** out, int32_t block, uint64_t seed) {
     if (e == cudaSuccess) e = cudaMemcpy(p->w, w.data(), kNP * 4, cudaMemcpyHostToDevice);
     if (e == cudaSuccess) e = cudaMemset(p->m, 0, kNP * 4);
     if (e == cudaSuccess) e = cudaMemset(p->v2, 0, kNP * 4);
-    if (e == cudaSuccess) e = cudaMemset(p->stats, 0, 16);
+    if (e == cudaSuccess) e = cudaMemset(p->stats, 0, 32);
     if (e == cudaSuccess) {
         crbm::k_prop_round<<<(kNP + 255) / 256, 256>>>(p->w, p->wb, kNP);
         e = cudaGetLastError();
@@ -764,7 +950,7 @@ int crbm_proposal_create(crbm_proposal** out, int32_t block, uint64_t seed) {
 
 void crbm_proposal_destroy(crbm_proposal* p) {
     if (!p) return;
-    void* b[] = {p->w, p->wb, p->m, p->v2, p->grad, p->loss, p->frag, p->bias, p->c1, p->stats, p->ex};
+    void* b[] = {p->w, p->wb, p->m, p->v2, p->grad, p->loss, p->bmat, p->bias, p->c1, p->stats, p->ex};
     for (void* x : b)
         if (x) cudaFree(x);
     delete p;
@@ -916,11 +1102,14 @@ int crbm_proposal_inspect(crbm_ctx* ctx, crbm_proposal* p, crbm_pass_record* out
 
 int crbm_proposal_stats(crbm_proposal* p, int64_t* proposed, int64_t* accepted) {
     if (!p || !proposed || !accepted) return prop_fail(CRBM_EINVAL, "bad arguments");
-    unsigned long long s[2];
-    const cudaError_t e = cudaMemcpy(s, p->stats, 16, cudaMemcpyDeviceToHost);
+    unsigned long long s[3];
+    const cudaError_t e = cudaMemcpy(s, p->stats, 24, cudaMemcpyDeviceToHost);
     if (e != cudaSuccess) return prop_fail(CRBM_ECUDA, cudaGetErrorString(e));
     *proposed = static_cast<int64_t>(s[0]);
     *accepted = static_cast<int64_t>(s[1]);
+    if (s[2] != 0)
+        return prop_fail(CRBM_ETIMEOUT, "a block-move pass gave up waiting for its tensor-core MMAs (" +
+                                            std::to_string(s[2]) + " CTAs); its moves are incomplete");
     return CRBM_OK;
 }
 

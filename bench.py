@@ -183,7 +183,7 @@ def workload_config(name, rank):
     return w
 
 
-DEFAULT_SWEEPS = {"grid": 2000, "stream": 20, "batch": 500, "proposal": 1000, "tts": 4000, "phase": 4000}
+DEFAULT_SWEEPS = {"grid": 2000, "stream": 20, "batch": 500, "proposal": 250, "tts": 4000, "phase": 4000}
 
 
 def cpu_model():
@@ -500,17 +500,87 @@ def run_batch(args, rank, ws):
         print(json.dumps(out))
 
 
-def run_proposal(args, rank, ws):
+PASS_FLOP_PER_BLOCK = 2 * (64 * 16 * 54 + 36 * 16 * 144 + 16 * 144)  # the net's MACs x 2 per 4x4 block
+
+
+def proposal_arm(s, prop, every, chunk, target_se, max_chunks, cp, L, stream, min_chunks=4):
+    """Advance sampler ``s`` in chunks of ``chunk`` sweeps (plain Gibbs when
+    ``every`` is None, else Gibbs with a block-move pass after every ``every``
+    sweeps) until the standard error of the mean energy per spin is at most
+    ``target_se`` at every beta point (and at least ``min_chunks`` chunks, so
+    the autocorrelation estimates rest on enough samples), or ``max_chunks``.  Per chunk and
+    chain: the mean, and the effective samples of E and m by Sokal windowing
+    (c = 5) on the chunk's series (chunks are much longer than the
+    autocorrelation times); SE of a point = pooled sigma / sqrt(sum of ESS).
+    Returns the GPU seconds of the sweeps and passes, sweeps run, and per point
+    the SE of e and m, the ESS of E and m and the mean e."""
+    import torch
+    from paper_2511_20911_gb300 import analysis
+    N = L * L
+    G = int(cp.max()) + 1
+    sums = {k: np.zeros(G) for k in ("essE", "essM", "sE", "sE2", "sM", "sM2", "n")}
+    sec, chunks = 0.0, 0
+    p0 = prop.stats() if prop is not None else None
+    se_e = np.full(G, np.inf)
+    while chunks < max_chunks:  # at least min_chunks, then until the target error
+        s.reset_observables()
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        torch.cuda.synchronize()
+        a.record(stream)
+        if every is None:
+            s.sweep(chunk)
+        else:
+            prop.sweep_mixed(s, chunk, every=every)
+        b.record(stream)
+        torch.cuda.synchronize()
+        sec += a.elapsed_time(b) / 1e3
+        chunks += 1
+        ser = s.series().transpose(1, 0, 2).astype(np.float64)     # [chain][T][3]
+        E = (ser[..., 0] + ser[..., 1] - 3.0 * ser[..., 2]) / N     # e per spin (J = J' = 1, h = 3)
+        M = ser[..., 2] / N
+        essE = analysis.effective_samples(E, burn_frac=0.0)
+        essM = analysis.effective_samples(M, burn_frac=0.0)
+        for g in range(G):
+            m = cp == g
+            sums["essE"][g] += essE[m].sum()
+            sums["essM"][g] += essM[m].sum()
+            sums["sE"][g] += E[m].sum()
+            sums["sE2"][g] += (E[m] ** 2).sum()
+            sums["sM"][g] += M[m].sum()
+            sums["sM2"][g] += (M[m] ** 2).sum()
+            sums["n"][g] += E[m].size
+        varE = sums["sE2"] / sums["n"] - (sums["sE"] / sums["n"]) ** 2
+        varM = sums["sM2"] / sums["n"] - (sums["sM"] / sums["n"]) ** 2
+        se_e = np.sqrt(np.maximum(varE, 0) / np.maximum(sums["essE"], 1e-300))
+        se_m = np.sqrt(np.maximum(varM, 0) / np.maximum(sums["essM"], 1e-300))
+        if chunks >= min_chunks and (se_e <= target_se).all():
+            break
+    out = {"seconds": sec, "sweeps": chunks * chunk, "reached": bool((se_e <= target_se).all()),
+           "se_e": se_e.tolist(), "se_m": se_m.tolist(), "ess_E": sums["essE"].tolist(),
+           "ess_m": sums["essM"].tolist(), "e_per_spin": (sums["sE"] / sums["n"]).tolist(),
+           "m_per_spin": (sums["sM"] / sums["n"]).tolist(),
+           "ess_per_s_E": (sums["essE"] / sec).tolist(), "ess_per_s_m": (sums["essM"] / sec).tolist()}
+    if prop is not None:
+        p1 = prop.stats()
+        out["accept"] = (p1[1] - p0[1]) / max(1, p1[0] - p0[0])
+    return out
+
+
+def run_proposal(args, rank, ws, sizes=((18, 20000), (48, 60000)), everys=(1, 4, 8), quiet=False):
     """Learned block proposal: train it on the GPU on configurations the
-    sampler generates (L=18, J'/J=1, beta in [1.5,3], h in [2.5,3.5]), then
-    compare effective samples per second of E and m, plain Gibbs against
-    Gibbs + one block-move pass per sweep and per 4 sweeps, from the same
-    equilibrated state, at L=18 and L=48 (J'/J=1, h=3, beta in {1.5,2,3},
-    4096 chains)."""
+    sampler generates (L=18, J'/J=1, beta in [1.5,3], h in [2.5,3.5]); then, at
+    L=18 and L=48 (J'/J=1, h=3, beta in {1.5,2,3}, 4096 chains, from one
+    equilibrated state), run plain Gibbs and Gibbs + block moves (a pass after
+    every 1, 4 or 8 sweeps) each until the standard error of the energy per
+    spin is <= 1e-4 at every beta, and compare effective samples per second
+    (and the time to that error).  Also times the pass kernel alone against
+    the measured bf16 tensor peak."""
     import torch
     import paper_2511_20911_gb300 as crbm
-    from paper_2511_20911_gb300 import analysis, workloads
-    T = args.sweeps_per_step
+    from paper_2511_20911_gb300 import workloads
+    chunk = args.sweeps_per_step
+    target = 1e-4
+    stream = torch.cuda.current_stream()
     tw = workloads.proposal_training_workload()
     src = crbm.Sampler(**tw)
     src.sweep(500)
@@ -519,64 +589,86 @@ def run_proposal(args, rank, ws):
     losses = prop.train(src, steps=400, batch=4096, lr=1e-2, sweeps_between=2)
     torch.cuda.synchronize()
     train_s = time.perf_counter() - t0
-    stream = torch.cuda.current_stream()
-    results = []
-    for L, burn in ((18, 20000), (48, 6000)):
-        ew = workloads.proposal_eval_workload(L)
-        base = crbm.Sampler(**dict(ew, measure_every=1, series_len=T))
-        base.sweep(burn)
-        ck = base.save()
-        cp = np.asarray(ew["chain_param"])
-        out = {}
-        for mode in ("plain", "mixed", "mixed4"):
-            s = crbm.Sampler(**dict(ew, measure_every=1, series_len=T))
-            s.load(ck)
-            s.reset_observables()
-            p0 = prop.stats()
+    results, kernel = [], {}
+    peak = measured_peaks().get("bf16_tflops") or 1900.8
+    with ClockSampler(torch.cuda.current_device()) as clk:
+        for L, burn in sizes:
+            ew = workloads.proposal_eval_workload(L)
+            cp = np.asarray(ew["chain_param"])
+            base = crbm.Sampler(**dict(ew, measure_every=1, series_len=chunk))
+            base.sweep(burn)
+            ck = base.save()
+            # the pass alone: CUDA events around 200 passes
+            pk = crbm.Sampler(**dict(ew, measure_every=1, series_len=chunk))
+            pk.load(ck)
+            prop.passes(pk, 5)
             a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
             torch.cuda.synchronize()
             a.record(stream)
-            if mode == "plain":
-                s.sweep(T)
-            else:
-                prop.sweep_mixed(s, T, every=1 if mode == "mixed" else 4)
+            prop.passes(pk, 200)
             b.record(stream)
             torch.cuda.synchronize()
-            sec = a.elapsed_time(b) / 1e3
-            p1 = prop.stats()
-            ser = s.series().transpose(1, 0, 2)                    # [chain][T][3]
-            E = ser[..., 0] + ser[..., 1] - 3.0 * ser[..., 2]       # J = J' = 1, h = 3
-            M = ser[..., 2].astype(np.float64)
-            essE, essM = analysis.effective_samples(E), analysis.effective_samples(M)
-            half = E.shape[1] // 2
-            drift = [float((E[cp == g][:, half:].mean() - E[cp == g][:, :half].mean()) / (16 * L * L) * 16)
-                     for g in range(3)]
-            out[mode] = {"seconds": sec, "sweeps": T, "e_drift_second_minus_first_half": drift,
-                         "ess_per_s_E": [float(essE[cp == g].sum() / sec) for g in range(3)],
-                         "ess_per_s_m": [float(essM[cp == g].sum() / sec) for g in range(3)],
-                         "e_per_spin": [float(E[cp == g].mean() / (16 * L * L) * 16) for g in range(3)],
-                         "accept": (p1[1] - p0[1]) / max(1, p1[0] - p0[0]) if mode != "plain" else None}
-        def gain(mode, key):
-            return [m / p if p > 0 else None for m, p in zip(out[mode][key], out["plain"][key])]
-        results.append({"L": L, "beta": ew["params"]["beta"], "h": 3.0, "plain": out["plain"],
-                        "mixed": out["mixed"], "mixed_every4": out["mixed4"],
-                        "ess_per_s_gain_E": gain("mixed", "ess_per_s_E"),
-                        "ess_per_s_gain_m": gain("mixed", "ess_per_s_m"),
-                        "ess_per_s_gain_E_every4": gain("mixed4", "ess_per_s_E"),
-                        "ess_per_s_gain_m_every4": gain("mixed4", "ess_per_s_m")})
-    mixed_rate = sum(sum(r["mixed"]["ess_per_s_E"]) for r in results)
-    line = {"metric": METRIC, "value": mixed_rate, "unit": "effective samples/s (E, mixed sampler)",
+            pass_s = a.elapsed_time(b) / 1e3 / 200
+            a.record(stream)
+            pk.sweep(200)
+            b.record(stream)
+            torch.cuda.synchronize()
+            sweep_s = a.elapsed_time(b) / 1e3 / 200
+            flop = PASS_FLOP_PER_BLOCK * max(1, L // 8) ** 2 * ew["n_chains"]
+            kernel[f"L{L}"] = {"pass_us": pass_s * 1e6, "sweep_us": sweep_s * 1e6,
+                               "pass_in_sweeps": pass_s / sweep_s, "flop_per_pass": flop,
+                               "tflops": flop / pass_s / 1e12, "frac_of_bf16_peak": flop / pass_s / 1e12 / peak}
+            pk.close()
+            arms = {}
+            for name, every in [("plain", None)] + [(f"every{k}", k) for k in everys]:
+                s = crbm.Sampler(**dict(ew, measure_every=1, series_len=chunk))
+                s.load(ck)
+                arms[name] = proposal_arm(s, None if every is None else prop, every, chunk, target, 80, cp, L,
+                                          stream)
+                s.close()
+            row = {"L": L, "beta": ew["params"]["beta"], "h": 3.0, "burn_in_sweeps": burn, "arms": arms}
+            for name in arms:
+                if name == "plain":
+                    continue
+                row[f"ess_per_s_gain_E_{name}"] = [m / p for m, p in zip(arms[name]["ess_per_s_E"],
+                                                                           arms["plain"]["ess_per_s_E"])]
+                row[f"ess_per_s_gain_m_{name}"] = [m / p for m, p in zip(arms[name]["ess_per_s_m"],
+                                                                           arms["plain"]["ess_per_s_m"])]
+                row[f"time_to_se_ratio_{name}"] = (arms["plain"]["seconds"] / arms[name]["seconds"]
+                                                   if arms[name]["reached"] and arms["plain"]["reached"] else None)
+            results.append(row)
+            base.close()
+    best = max((g for r in results for k, v in r.items() if k.startswith("ess_per_s_gain_E_") for g in v),
+               default=None)
+    k18 = kernel.get("L18", next(iter(kernel.values())))
+    line = {"metric": METRIC, "value": best, "unit": "ESS/s of E, mixed / plain Gibbs (best arm and beta)",
             "n_gpus": ws, "steps": 1, "warmup": 0, "higher_is_better": True, "scaling": "weak",
             "vs_baseline": None, "dtype": "bf16+u32", "data": "synthetic",
-            "config": {"workload": "learned 4x4 block proposal (3x3 conv net 6-16-16-1, bf16/fp32, "
-                                   "mma.sync) + Gibbs vs plain Gibbs, J'/J=1, h=3, beta in {1.5,2,3}, "
-                                   "L in {18,48}, 4096 chains, from one equilibrated state",
-                       "sweeps": T, "train_steps": 400, "train_batch": 4096},
-           "train": {"seconds": train_s, "loss_first": float(losses[:5].mean()),
-                     "loss_last": float(losses[-20:].mean())},
-           "results": results}
-    if rank == 0:
+            "config": {"workload": "learned 4x4 block proposal (3x3 conv net 6-16-16-1, bf16/fp32, tcgen05) + "
+                                   "Gibbs vs plain Gibbs, J'/J=1, h=3, beta in {1.5,2,3}, L in {18,48}, 4096 "
+                                   "chains, from one equilibrated state, each arm run until SE(E)/N <= 1e-4",
+                       "chunk_sweeps": chunk, "train_steps": 400, "train_batch": 4096},
+            "train": {"seconds": train_s, "loss_first": float(losses[:5].mean()),
+                      "loss_last": float(losses[-20:].mean())},
+            "pass_kernel": kernel,
+            "roofline": {"bound": "tensor", "achieved": k18["tflops"], "peak": peak, "unit": "TFLOP/s",
+                         "frac": k18["tflops"] / peak, "traffic": None,
+                         "note": "k_prop_pass at L=18, 4096 chains: the net's algorithmic FLOPs (0.28 MFLOP per "
+                                 "4x4 block) per pass over the CUDA-event time of one pass; peak = measured bf16 "
+                                 "burst (MEASURED_PEAKS.json)"},
+            "clocks": clk.summary(),
+            "results": results}
+    if rank == 0 and not quiet:
         print(json.dumps(line))
+    return line
+
+
+def measured_peaks():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            return json.load(f)
+    except (OSError, ValueError):
+        return {}
 
 
 def philox_peak(dev, sm_max_mhz):

@@ -183,7 +183,7 @@ def workload_config(name, rank):
     return w
 
 
-DEFAULT_SWEEPS = {"grid": 2000, "stream": 20, "batch": 500, "proposal": 250, "tts": 4000, "phase": 4000}
+DEFAULT_SWEEPS = {"grid": 2000, "stream": 20, "batch": 500, "proposal": 250, "tts": 50000, "phase": 4000}
 
 
 def cpu_model():
@@ -304,57 +304,90 @@ TTS_PHASES = (("FM", 1.0, 1.0, 7.0, 33e-9), ("dimer", 1.0, 2.5, 0.0, 5e-6), ("Ne
 
 
 def run_tts(args, rank, ws):
-    """Time to solution: per lattice size one context with 1024 chains at each
-    of the paper's four phase points (beta = 4), every chain's first sweep at
-    its brute-force supercell ground-state energy recorded on the device
-    (measured every sweep), TTS_99 = T log(0.01) / log(1 - p_gnd) in sweeps
-    and in seconds of this GPU's sweep time for the whole context."""
+    """Time to solution at the paper's four phase points, L in {6, 12, 18}.
+    Per point, 32 independent replica-exchange ladders of 32 rungs (beta
+    geometric in [0.25, 8], swaps every 2 sweeps) and, for comparison, 1024
+    independent chains at fixed beta = 4; every chain's first sweep at its
+    point's brute-force supercell ground-state energy is recorded on the
+    device (measured every sweep).  A run is a ladder (first hit of any rung)
+    or a fixed-beta chain; TTS_99 = T log(0.01) / log(1 - p_gnd) in sweeps,
+    and in seconds of this GPU's sweep time for the whole context (every run
+    of the context advances together)."""
     import torch
     import paper_2511_20911_gb300 as crbm
     from paper_2511_20911_gb300 import analysis
-    S = args.sweeps_per_step or 4000
-    per, beta = 1024, 4.0
+    S = args.sweeps_per_step
+    R, ladders, beta_fixed = 32, 32, 4.0
+    betas = 0.25 * (8.0 / 0.25) ** (np.arange(R) / (R - 1))
     rows, total_updates, total_s = [], 0, 0.0
     with ClockSampler(torch.cuda.current_device()) as clk:
         for L in (6, 12, 18):
-            params = dict(J=[p[1] for p in TTS_PHASES], Jp=[p[2] for p in TTS_PHASES],
-                          h=[p[3] for p in TTS_PHASES], beta=[beta] * len(TTS_PHASES))
-            n = per * len(TTS_PHASES)
-            cp = (np.arange(n) // per).astype(np.int32)
-            s = crbm.Sampler(L, params, n, chain_param=cp, seed=replica_seed(21 + L, rank), measure_every=1,
-                             layout=crbm.CRBM_LAYOUT_SMEM)
             e_gs = [analysis.ground_state_energy(L, J, Jp, h)[0] for _, J, Jp, h, _ in TTS_PHASES]
-            s.set_targets(e_gs)
-            a = torch.cuda.Event(enable_timing=True)
-            b = torch.cuda.Event(enable_timing=True)
-            torch.cuda.synchronize()
-            a.record()
-            s.sweep(S)
-            b.record()
-            torch.cuda.synchronize()
-            sec = a.elapsed_time(b) / 1e3
-            total_s += sec
-            total_updates += n * L * L * S
-            hits = s.first_hits()
-            for k, (name, J, Jp, h, paper) in enumerate(TTS_PHASES):
-                pg, T, tts = analysis.time_to_solution(hits[cp == k], S)
-                rows.append({"phase": name, "L": L, "J": J, "Jp": Jp, "h": h, "beta": beta, "p_gnd": pg,
-                             "T_sweeps": T, "tts99_sweeps": tts,
-                             "tts99_s": None if tts is None else tts * sec / S, "paper_fpga_s": paper,
-                             "e_gs_per_spin": e_gs[k] / 16.0 / (L * L)})
+            for mode in ("tempering", "fixed"):
+                if mode == "tempering":
+                    params = dict(J=[], Jp=[], h=[], beta=[])
+                    for _, J, Jp, h, _ in TTS_PHASES:
+                        for _ in range(ladders):
+                            params["J"] += [J] * R
+                            params["Jp"] += [Jp] * R
+                            params["h"] += [h] * R
+                            params["beta"] += [float(b) for b in betas]
+                    n = len(params["J"])
+                    cp = np.arange(n, dtype=np.int32)
+                    point_of_chain = np.arange(n) // (ladders * R)
+                    s = crbm.Sampler(L, params, n, chain_param=cp, seed=replica_seed(31 + L, rank), measure_every=1,
+                                     swap_every=2, layout=crbm.CRBM_LAYOUT_SMEM)
+                    s.set_targets(np.repeat(np.asarray(e_gs, np.int64), ladders * R))
+                else:
+                    params = dict(J=[p[1] for p in TTS_PHASES], Jp=[p[2] for p in TTS_PHASES],
+                                  h=[p[3] for p in TTS_PHASES], beta=[beta_fixed] * len(TTS_PHASES))
+                    n = ladders * R * len(TTS_PHASES)
+                    cp = (np.arange(n) // (ladders * R)).astype(np.int32)
+                    point_of_chain = cp
+                    s = crbm.Sampler(L, params, n, chain_param=cp, seed=replica_seed(21 + L, rank), measure_every=1,
+                                     layout=crbm.CRBM_LAYOUT_SMEM)
+                    s.set_targets(e_gs)
+                a = torch.cuda.Event(enable_timing=True)
+                b = torch.cuda.Event(enable_timing=True)
+                torch.cuda.synchronize()
+                a.record()
+                s.sweep(S)
+                b.record()
+                torch.cuda.synchronize()
+                sec = a.elapsed_time(b) / 1e3
+                total_s += sec
+                total_updates += n * L * L * S
+                hits = s.first_hits()
+                if mode == "tempering":   # a run is a ladder: its first rung to reach the ground state
+                    h = hits.reshape(-1, R)
+                    runs = np.where((h >= 0).any(1), np.where(h >= 0, h, np.iinfo(np.int64).max).min(1), -1)
+                    run_point = point_of_chain[::R]
+                else:
+                    runs, run_point = hits, point_of_chain
+                for k, (name, J, Jp, h_, paper) in enumerate(TTS_PHASES):
+                    pg, T, tts = analysis.time_to_solution(runs[run_point == k], S)
+                    rows.append({"phase": name, "L": L, "mode": mode, "J": J, "Jp": Jp, "h": h_,
+                                 "beta": [0.25, 8.0] if mode == "tempering" else beta_fixed,
+                                 "runs": int((run_point == k).sum()), "p_gnd": pg, "T_sweeps": T,
+                                 "tts99_sweeps": tts, "tts99_s": None if tts is None else tts * sec / S,
+                                 "context_s_per_sweep": sec / S, "paper_fpga_s": paper,
+                                 "e_gs_per_spin": e_gs[k] / 16.0 / (L * L)})
+                s.close()
     t_total = max_over_ranks(total_s, ws)
     out = {"metric": METRIC, "value": replica_value(total_updates, ws, t_total), "unit": UNIT, "n_gpus": ws,
            "steps": 1, "warmup": 0, "ms_per_step": t_total * 1e3, "higher_is_better": True, "scaling": "weak",
            "vs_baseline": None, "dtype": "u32", "data": "synthetic",
            "config": {"workload": "time to solution at the paper's FM, dimer, Neel and 1/3-plateau points, "
-                                  f"L in {{6,12,18}}, {per} chains per point, beta={beta}, {S} sweeps, "
-                                  "ground states by brute force over even supercells of <= 16 sites",
+                                  f"L in {{6,12,18}}: {ladders} replica-exchange ladders of {R} rungs (beta "
+                                  f"geometric in [0.25, 8], swaps every 2 sweeps) per point, and {ladders * R} "
+                                  f"chains at fixed beta = {beta_fixed} per point; {S} sweeps; ground states by "
+                                  "brute force over even supercells of <= 16 sites",
                       "parallelism": f"replicas x{ws}"},
            "clocks": clk.summary(),
            "tts": rows,
-           "note": "tts99_s = TTS_99 in sweeps x this GPU's time per sweep of the whole context (all "
-                   f"{per * len(TTS_PHASES)} chains advance together); paper_fpga_s is the FPGA time the paper "
-                   "prints for the phase"}
+           "note": "tts99_s = TTS_99 in sweeps x this GPU's time per sweep of the whole context (all runs of "
+                   "the context advance together); a tempering run is a 32-rung ladder; paper_fpga_s is the "
+                   "FPGA time the paper prints for the phase"}
     if rank == 0:
         print(json.dumps(out))
     if ws > 1:

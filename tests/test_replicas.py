@@ -78,3 +78,27 @@ def test_bitplane_expected_calls_matches_a_simulation():
             calls += min(8, (planes + 3) // 4)
         expect = bench.bitplane_expected_calls(lanes) / lanes
         assert abs(calls / trials - expect) < 0.03, (lanes, calls / trials, expect)
+
+
+def test_bitplane_expected_calls_with_half_thresholds():
+    """Hidden units with m = 0 have the threshold exactly 2^31.  Such a
+    comparison is decided on the first plane only when the uniform's top bit
+    is 0; otherwise it stays open until the uniform's first further 1 bit, so
+    it too closes with probability 1/2 per plane and the model needs no
+    correction for them: a direct simulation with half (or most) of the
+    thresholds at 2^31 gives the same mean call count."""
+    import numpy as np
+    import bench
+    rng = np.random.default_rng(5)
+    for f in (0.5, 0.9):
+        trials, calls = 4000, 0
+        for _ in range(trials):
+            u = rng.integers(0, 2**32, size=(32, 32), dtype=np.uint64)
+            t = rng.integers(0, 2**32, size=(32, 32), dtype=np.uint64)
+            t[rng.random((32, 32)) < f] = 2**31
+            diff = u ^ t
+            first = np.where(diff == 0, 32, 31 - np.floor(np.log2(np.maximum(diff, 1))).astype(int))
+            planes = int(first.max()) + 1
+            calls += min(8, max(2, (planes + 3) // 4))   # the hidden half-step draws two calls first
+        expect = bench.bitplane_expected_calls(32) / 32
+        assert abs(calls / trials - expect) < 0.03, (f, calls / trials, expect)

@@ -466,14 +466,15 @@ def run_phase(args, rank, ws):
         torch.distributed.destroy_process_group()
 
 
-def run_batch(args, rank, ws):
+def run_batch(args, rank, ws, quiet=False):
     """Mixed L in {6,9,12,18,24,48} x 8 tempering ladders of 32 betas, all
     members advanced by one graph-captured launch per step."""
     import torch
     import paper_2511_20911_gb300 as crbm
     from paper_2511_20911_gb300 import workloads
     specs = workloads.tempering_batch_workload()
-    S, K, W = args.sweeps_per_step, args.steps, args.warmup
+    S = args.sweeps_per_step if args.workload == "batch" else DEFAULT_SWEEPS["batch"]
+    K, W = args.steps, args.warmup
     members = []
     for sp in specs:
         sp = dict(sp, seed=replica_seed(sp["seed"], rank), measure_every=args.measure_every)
@@ -530,8 +531,11 @@ def run_batch(args, rank, ws):
            "gpu_launches": int(sum(m.launch_count for m in members) - l0),
            "roofline": {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "Tops/s",
                         "frac": achieved / peak, "traffic": None}}
-    if rank == 0:
+    for m in members:
+        m.close()
+    if rank == 0 and not quiet:
         print(json.dumps(out))
+    return out
 
 
 PASS_FLOP_PER_BLOCK = 2 * (64 * 16 * 54 + 36 * 16 * 144 + 16 * 144)  # the net's MACs x 2 per 4x4 block
@@ -916,10 +920,25 @@ def main():
         sq_every = 0            # correlations: lane uniforms, SMEM layout
     out = measure_sampler(args, args.workload, rank, ws, with_e2e=True, sq_every=sq_every)
     if args.workload == "grid" and not args.no_extra_lines:
+        keys = ("value", "unit", "ms_per_step", "steps", "warmup", "config", "clocks", "gpu_launches", "hbm",
+                "roofline")
+        out["lines"] = {}
         sub = measure_sampler(args, "stream", rank, ws, with_e2e=False)
-        out["lines"] = {"stream_L384": {k: sub[k] for k in ("value", "unit", "ms_per_step", "steps", "warmup",
-                                                             "config", "clocks", "gpu_launches", "hbm",
-                                                             "roofline")}}
+        out["lines"]["stream_L384"] = {k: sub[k] for k in keys}
+        if args.precision == "exact" and args.rng == "lane":
+            # the other modes of the grid workload, the tempering batch and the learned
+            # proposal (L=18), so that one bench run measures every line
+            for name, prec, rng in (("grid_paper_precision", "paper", "lane"), ("grid_bitplane", "exact", "bitplane")):
+                sub = measure_sampler(argparse.Namespace(**dict(vars(args), precision=prec, rng=rng)), "grid",
+                                      rank, ws, with_e2e=False)
+                out["lines"][name] = {k: sub[k] for k in keys}
+            sub = run_batch(args, rank, ws, quiet=True)
+            out["lines"]["tempering_batch"] = {k: sub[k] for k in ("value", "unit", "ms_per_step", "steps", "warmup",
+                                                                 "config", "clocks", "gpu_launches", "roofline")}
+            sub = run_proposal(argparse.Namespace(**dict(vars(args), sweeps_per_step=DEFAULT_SWEEPS["proposal"])),
+                               rank, ws, sizes=((18, 20000),), everys=(1, 8), quiet=True)
+            out["lines"]["learned_proposal_L18"] = {k: sub[k] for k in ("value", "unit", "config", "pass_kernel",
+                                                                        "roofline", "clocks", "results")}
     if rank == 0 and not args.no_cpu_baseline:
         w = workload_config(args.workload, 0)
         out["cpu_baseline"] = cpu_baseline(w, args.cpu_seconds, 1 if args.precision == "paper" else 0,

@@ -105,8 +105,7 @@ constexpr int kC1Bytes = 64 * kC1Stride * 4;
 constexpr int kSmItem = kSmB + kBElems * 2;
 constexpr int kSmC1 = kSmItem + 2 * kItemBytes;
 constexpr int kSmBar = kSmC1 + kC1Bytes, kSmBytes = kSmBar + 16;
-constexpr int kMHBytes = 256 * 4 * 3 + 128 * 4 * 2 + 16 * 4 + 128 * 8;
-static_assert(kSmXBytes >= 2 * kA0Plane && kSmXBytes >= kMHBytes, "layer-1 operand and MH arrays fit in X");
+static_assert(kSmXBytes >= 2 * kA0Plane, "layer-1 operand fits in X");
 static_assert(kSmB % 16 == 0 && kSmItem % 16 == 0 && kSmC1 % 16 == 0 && kSmBar % 8 == 0, "alignment");
 constexpr int kWaitTries = 1 << 22;            // mbarrier polls before the pass gives up
 
@@ -190,14 +189,8 @@ __global__ void __launch_bounds__(kPassThreads, 4) k_prop_pass(const __grid_cons
     const uint32_t bar = umma::smem_addr(sm + kSmBar);
     uint32_t* tslot = reinterpret_cast<uint32_t*>(sm + kSmBar + 8);
     __shared__ int s_fail;
-    // Metropolis-Hastings arrays in X after layer 3 ([site][chain] or [part][chain], 16 chains)
-    float* logit = reinterpret_cast<float*>(X);                   // [16 sites][16]
-    uint32_t* s_thr = reinterpret_cast<uint32_t*>(logit + 256);   // [16 sites][16]
-    int* s_xx = reinterpret_cast<int*>(s_thr + 256);  // [16 sites][16] bit 0: current +1, bit 1: proposed +1
-    float* p_lq = reinterpret_cast<float*>(s_xx + 256);  // [8 parts][16] sum log q(cur) - log q(new)
-    uint32_t* p_bits = reinterpret_cast<uint32_t*>(p_lq + 128);  // [8 parts][16] cur | new << 16
-    uint32_t* s_uacc = p_bits + 128;                  // [16] accept draw
-    long long* p_de = reinterpret_cast<long long*>(s_uacc + 16);  // [8 parts][16] dE shares
+    // the block's logits in X after layer 3 ([site][chain], 16 chains)
+    float* logit = reinterpret_cast<float*>(X);
 
     // set-up: B operands, zero X (the shift rows past 128 must hold finite values), mbarrier, TMEM
     for (int x = tid; x < kBElems / 8; x += kPassThreads) reinterpret_cast<uint4*>(Bs)[x] = a.bmat[x];
@@ -384,24 +377,31 @@ __global__ void __launch_bounds__(kPassThreads, 4) k_prop_pass(const __grid_cons
             ok = false;
             break;
         }
-        // ---- Metropolis-Hastings, phase A: thread = (chain c, Philox call k, pair jj): sites
-        // 4 k + 2 jj + {0, 1}: threshold, the proposed spin, this pair's share of
-        // log q(current) - log q(proposed); threads k = jj = 0 also draw the accept word
-        const int c = tid & 15, k = (tid >> 4) & 3, jj = tid >> 6;
-        const int part = 2 * k + jj;
-        const int chain = word * 32 + half * 16 + c;
-        const int cbit = half * 16 + c;
-        const uint32_t cell_id = static_cast<uint32_t>(b);
+        // ---- Metropolis-Hastings: warp w takes chains 4 w .. 4 w + 3, eight lanes per chain,
+        // lane part p the sites 2 p and 2 p + 1 (words (2 p) % 4 and (2 p + 1) % 4 of Philox
+        // call p / 2).  A lane forms its sites' thresholds, proposals and shares of
+        // log q(current) - log q(proposed), and of the exact dE the terms linear in the block's
+        // spins (bonds to spins outside the block, and the field); the chain's eight lanes sum
+        // them by shuffles, add the bonds inside the block from the current and proposed bit
+        // masks, and run the test; accepted sites flip with one atomic XOR per site and warp.
         {
-            const U4 u = philox(cell_id, a.pass, static_cast<uint32_t>(chain), kTagBits + k, a.key0, a.key1);
+            const int c = 4 * warp + (lane >> 3), part = lane & 7;
+            const int chain = word * 32 + half * 16 + c;
+            const int cbit = half * 16 + c;
+            const uint32_t cell_id = static_cast<uint32_t>(b);
+            const int qJ = cq[4 * c], qJp = cq[4 * c + 1], qh = cq[4 * c + 2];
+            const U4 u = philox(cell_id, a.pass, static_cast<uint32_t>(chain), kTagBits + (part >> 1), a.key0, a.key1);
             float lq = 0.f;
+            int de = 0;
             uint32_t bits = 0u;
+            auto spin_at = [&](int pr, int pc) -> int { return ((pw[pr * kP + pc] >> cbit) & 1u) ? 1 : -1; };
 #pragma unroll
             for (int j = 0; j < 2; ++j) {
-                const int s = 4 * k + 2 * jj + j;
-                const int pos = (3 + s / kK) * kP + 3 + s % kK;
-                const bool xc = (pw[pos] >> cbit) & 1u;
-                const float q = 1.f / (1.f + __expf(-logit[s * 16 + c]));
+                const int s = 2 * part + j;
+                const int ar = s / kK, ac = s % kK;
+                const bool xc = (pw[(3 + ar) * kP + 3 + ac] >> cbit) & 1u;
+                const float lg = logit[s * 16 + c];
+                const float q = 1.f / (1.f + __expf(-lg));
                 float tf = q * 4294967296.f;
                 tf = fminf(fmaxf(tf, 1.f), 4294967040.f);
                 const uint32_t thr = static_cast<uint32_t>(tf);
@@ -409,81 +409,59 @@ __global__ void __launch_bounds__(kPassThreads, 4) k_prop_pass(const __grid_cons
                 const float lp = __logf(p1), lm = log1pf(-p1);
                 const bool xp = pick(u, s & 3) < thr;
                 lq += (xc ? lp : lm) - (xp ? lp : lm);
-                s_xx[s * 16 + c] = (xc ? 1 : 0) | (xp ? 2 : 0);
-                s_thr[s * 16 + c] = thr;
                 bits |= (xc ? 1u : 0u) << s | (xp ? 1u : 0u) << (16 + s);
-            }
-            p_lq[part * 16 + c] = lq;
-            p_bits[part * 16 + c] = bits;
-            if (part == 0) s_uacc[c] = philox(cell_id, a.pass, static_cast<uint32_t>(chain), kTagAccept, a.key0, a.key1).x;
-        }
-        __syncthreads();
-        // phase A': this pair's share of the exact energy change (1/16 units)
-        // over the bonds touching the block; a bond inside the block is counted
-        // by its left / upper endpoint (right and down neighbours, and the dimer
-        // partner of higher index)
-        {
-            const int qJ = cq[4 * c], qJp = cq[4 * c + 1], qh = cq[4 * c + 2];
-            auto spin_at = [&](int pr, int pc) -> int { return ((pw[pr * kP + pc] >> cbit) & 1u) ? 1 : -1; };
-            auto xs_ = [&](int t) { return (s_xx[t * 16 + c] & 1) ? 1 : -1; };
-            auto ns = [&](int t) { return (s_xx[t * 16 + c] & 2) ? 1 : -1; };
-            long long de2 = 0;
-#pragma unroll
-            for (int j = 0; j < 2; ++j) {
-                const int s = 4 * k + 2 * jj + j;
-                const int ar = s / kK, ac = s % kK;
-                const int x0 = xs_(s), n0 = ns(s), d = n0 - x0;
-                long long dE = -static_cast<long long>(qh) * d;
-                if (ac + 1 < kK) dE += static_cast<long long>(qJ) * (n0 * ns(s + 1) - x0 * xs_(s + 1));
-                else dE += static_cast<long long>(qJ) * d * spin_at(3 + ar, 3 + ac + 1);
-                if (ar + 1 < kK) dE += static_cast<long long>(qJ) * (n0 * ns(s + kK) - x0 * xs_(s + kK));
-                else dE += static_cast<long long>(qJ) * d * spin_at(3 + ar + 1, 3 + ac);
-                if (ac == 0) dE += static_cast<long long>(qJ) * d * spin_at(3 + ar, 2);
-                if (ar == 0) dE += static_cast<long long>(qJ) * d * spin_at(2, 3 + ac);
-                // the orthogonal dimer of this site
+                // field on site s from outside the block (1/16 units): J to its outside neighbours,
+                // J' to an outside dimer partner, -h
+                int f = -qh;
+                if (ac == 0) f += qJ * spin_at(3 + ar, 2);
+                if (ac == kK - 1) f += qJ * spin_at(3 + ar, 3 + kK);
+                if (ar == 0) f += qJ * spin_at(2, 3 + ac);
+                if (ar == kK - 1) f += qJ * spin_at(3 + kK, 3 + ac);
                 const int R = bR + ar, C = bC + ac;
-                const int dR = (R & 1) ? ((C & 1) ? -1 : 1) : ((C & 1) ? -1 : 1);
-                const int dC = (R & 1) ? -1 : 1;
-                const int pr = ar + dR, pc = ac + dC;
-                if (pr >= 0 && pr < kK && pc >= 0 && pc < kK) {
-                    const int t = pr * kK + pc;
-                    if (t > s) dE += static_cast<long long>(qJp) * (n0 * ns(t) - x0 * xs_(t));
-                } else {
-                    dE += static_cast<long long>(qJp) * d * spin_at(3 + pr, 3 + pc);
+                const int pr = ar + ((C & 1) ? -1 : 1), pc = ac + ((R & 1) ? -1 : 1);  // the dimer partner
+                if (pr < 0 || pr >= kK || pc < 0 || pc >= kK) f += qJp * spin_at(3 + pr, 3 + pc);
+                de += ((xp ? 1 : -1) - (xc ? 1 : -1)) * f;
+                if (a.rec) {  // inspection: this lane's sites of the record
+                    PassRecord* r = a.rec + (static_cast<size_t>(word) * n_blocks + b) * 32 + cbit;
+                    r->logit[s] = lg;
+                    r->thr[s] = thr;
                 }
-                de2 += dE;
             }
-            p_de[part * 16 + c] = de2;
-        }
-        __syncthreads();
-        // ---- phase B, warp 0, lane = chain (lanes >= 16 follow lane - 16 and drop out):
-        // the eight shares in order, the exact MH test and the move
-        if (warp == 0) {
-            const int cc = lane & 15;
-            float lq = 0.f;
-            long long dE = 0;
-            uint32_t bits = 0u;
+            // the chain's eight lanes: sums in a fixed tree order
 #pragma unroll
-            for (int q = 0; q < 8; ++q) {
-                lq += p_lq[q * 16 + cc];
-                dE += p_de[q * 16 + cc];
-                bits |= p_bits[q * 16 + cc];
+            for (int o = 1; o < 8; o <<= 1) {
+                lq += __shfl_xor_sync(0xffffffffu, lq, o);
+                de += __shfl_xor_sync(0xffffffffu, de, o);
+                bits |= __shfl_xor_sync(0xffffffffu, bits, o);
             }
             const uint32_t cb = bits & 0xFFFFu, nb = bits >> 16;
-            const float beta = cbh[4 * cc + 2];  // the exact beta: the MH test targets exp(-beta H)
-            const float log_alpha = -beta * static_cast<float>(dE) * 0.0625f + lq;
-            const bool accept = lane < 16 && (log_alpha >= 0.f ||
-                                              static_cast<float>(s_uacc[cc] >> 8) * 5.9604644775390625e-08f <
-                                                  __expf(log_alpha));
-            if (a.rec) {  // inspection: record, do not move
-                if (lane < 16) {
-                    PassRecord* r = a.rec + (static_cast<size_t>(word) * n_blocks + b) * 32 + half * 16 + cc;
+            // bonds inside the block: s_i s_j = 1 - 2 [bits differ], counted once per pair
+            // (right neighbour, lower neighbour, the dimer partner of the upper site)
+            uint32_t d5 = 0u, d3 = 0u;  // sites whose partner is site + 5 / site + 3
 #pragma unroll
-                    for (int s = 0; s < kK * kK; ++s) {
-                        r->logit[s] = logit[s * 16 + cc];
-                        r->thr[s] = s_thr[s * 16 + cc];
-                    }
-                    r->dE = static_cast<int32_t>(dE);
+            for (int s = 0; s < 12; ++s) {
+                const int ar = s / kK, ac = s % kK, R = bR + ar, C = bC + ac;
+                if (!(C & 1)) {  // the partner lies one row down
+                    if (!(R & 1) && ac < kK - 1) d5 |= 1u << s;
+                    if ((R & 1) && ac > 0) d3 |= 1u << s;
+                }
+            }
+            auto diffs = [&](uint32_t x) {
+                return static_cast<int>(__popc((x ^ (x >> 1)) & 0x7777u) + __popc((x ^ (x >> 4)) & 0x0FFFu));
+            };
+            auto ddiffs = [&](uint32_t x) { return static_cast<int>(__popc(((x ^ (x >> 5)) & d5) | ((x ^ (x >> 3)) & d3))); };
+            de += 2 * qJ * (diffs(cb) - diffs(nb)) + 2 * qJp * (ddiffs(cb) - ddiffs(nb));
+            const float beta = cbh[4 * c + 2];  // the exact beta: the MH test targets exp(-beta H)
+            const float log_alpha = -beta * static_cast<float>(de) * 0.0625f + lq;
+            uint32_t ua = 0u;
+            if (part == 0) ua = philox(cell_id, a.pass, static_cast<uint32_t>(chain), kTagAccept, a.key0, a.key1).x;
+            ua = __shfl_sync(0xffffffffu, ua, lane & 24);
+            const bool accept =
+                log_alpha >= 0.f || static_cast<float>(ua >> 8) * 5.9604644775390625e-08f < __expf(log_alpha);
+            if (a.rec) {
+                if (part == 0) {
+                    PassRecord* r = a.rec + (static_cast<size_t>(word) * n_blocks + b) * 32 + cbit;
+                    r->dE = de;
                     r->cur_bits = cb;
                     r->new_bits = nb;
                     r->log_alpha = log_alpha;
@@ -491,20 +469,21 @@ __global__ void __launch_bounds__(kPassThreads, 4) k_prop_pass(const __grid_cons
                     r->bC = bC;
                 }
             } else {
-                const uint32_t am = __ballot_sync(0xffffffffu, accept);
                 const uint32_t flip = accept ? (cb ^ nb) : 0u;
-                uint32_t my_fm = 0u;  // lane s < 16: the chains whose site s flips
+                uint32_t my_fm = 0u;  // lane s < 16: the warp's chains whose site s flips
 #pragma unroll
                 for (int s = 0; s < kK * kK; ++s) {
-                    const uint32_t fm = __ballot_sync(0xffffffffu, (flip >> s) & 1u) & 0xFFFFu;
+                    const uint32_t bl = __ballot_sync(0xffffffffu, (flip >> s) & 1u);
+                    const uint32_t fm = (bl & 1u) | ((bl >> 7) & 2u) | ((bl >> 14) & 4u) | ((bl >> 21) & 8u);
                     my_fm = lane == s ? fm : my_fm;
                 }
                 if (lane < 16 && my_fm) {
                     const int R = (bR + lane / kK) % L, C = (bC + lane % kK) % L;
-                    atomicXor(a.v + static_cast<size_t>(word) * N + R * L + C, my_fm << (16 * half));
+                    atomicXor(a.v + static_cast<size_t>(word) * N + R * L + C, my_fm << (16 * half + 4 * warp));
                 }
+                const uint32_t am = __ballot_sync(0xffffffffu, accept && part == 0);
                 if (lane == 0) {
-                    atomicAdd(&a.stats[0], static_cast<unsigned long long>(kItemChains));
+                    atomicAdd(&a.stats[0], 4ull);
                     atomicAdd(&a.stats[1], static_cast<unsigned long long>(__popc(am)));
                 }
             }

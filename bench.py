@@ -15,7 +15,9 @@ N > 1 (torchrun): every rank runs an independent replica with its own chains
 from __future__ import annotations
 
 import argparse
+import functools
 import json
+import math
 import os
 import statistics
 import subprocess
@@ -56,17 +58,36 @@ MEASURED_TRAFFIC = {
 }
 
 
+@functools.lru_cache(maxsize=None)
 def bitplane_expected_calls(n_nodes):
-    """Expected Philox calls of one bit-plane half-step over n_nodes nodes of
-    one 32-chain word.  A warp takes 32 consecutive nodes and draws calls of
-    four planes while any of its (nodes x 32 chains) comparisons is undecided;
-    each plane decides an undecided comparison with probability 1/2, so it is
-    still open after 4 m planes with probability 2^-4m, independently."""
-    total = 0.0
-    for base in range(0, n_nodes, 32):
-        lanes = min(32, n_nodes - base)
-        calls = sum(1.0 - (1.0 - 2.0 ** (-4 * m)) ** (32 * lanes) for m in range(8))
-        total += calls * lanes
+    """Expected Philox calls (lane-calls) of one bit-plane half-step over
+    n_nodes nodes of one 32-chain word.  Every node draws two calls of four
+    planes; the nodes with a comparison still open after them go to a
+    straggler list, taken 32 at a time, and a group of stragglers draws calls
+    while any of its comparisons is open.  Each plane decides an undecided
+    comparison with probability 1/2, so it is still open after 4 m planes with
+    probability 2^-4m, independently; the number of stragglers is binomial.
+    (A node past the list's capacity, a quarter of the half-step, finishes in
+    place; its probability is negligible and not modelled.)"""
+    def node_open(m):                         # any of the node's 32 chains open after m calls
+        return -math.expm1(32.0 * math.log1p(-(2.0 ** (-4 * m))))
+    p2 = node_open(2)
+    cond = [node_open(2 + m) / p2 for m in range(6)]   # open after m more calls, given open after 2
+
+    def group_calls(g):                       # lane-calls of a group of g stragglers
+        return g * sum(1.0 if c >= 1.0 else -math.expm1(g * math.log1p(-c)) for c in cond)
+
+    n = int(n_nodes)
+    total = 2.0 * n
+    lq, lp = math.log1p(-p2), math.log(p2)
+    for k in range(1, n + 1):
+        lpmf = math.lgamma(n + 1) - math.lgamma(k + 1) - math.lgamma(n - k + 1) + k * lp + (n - k) * lq
+        if lpmf < -60.0 and k > n * p2:
+            break
+        pmf = math.exp(lpmf)
+        if pmf == 0.0:
+            continue
+        total += pmf * sum(group_calls(min(32, k - b)) for b in range(0, k, 32))
     return total
 
 

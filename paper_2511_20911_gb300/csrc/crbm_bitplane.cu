@@ -9,9 +9,12 @@
 // (per word, one bit-plane word per configuration and plane), so the 32
 // comparisons u_l < t_l run as one word-parallel comparison, most significant
 // bit first: a chain is decided at the first plane where its uniform and
-// threshold bits differ (below when the threshold bit is the 1), and a warp
-// stops drawing planes once all its nodes' chains are decided.  The result
-// equals the full 32-bit comparison, bit for bit.
+// threshold bits differ (below when the threshold bit is the 1).  Every node
+// draws two calls (eight planes); the nodes with chains still open after them
+// (about 12 %) go to a straggler list, which the CTA's warps then take 32 at a
+// time, drawing further calls while any of a warp's stragglers is open.  The
+// result equals the full 32-bit comparison, bit for bit, whichever call a
+// node stops at.
 //
 // Hidden unit k of a cell: its endpoints e1, e2 (spin words; e2 flipped on
 // the chains whose class coupling is negative) select the threshold of m = e1
@@ -41,12 +44,22 @@ __host__ __device__ inline size_t bp_rec_words(const Geometry& g) {
 // as built (bit l = rung l) and as used (bit l = the rung that slot l holds,
 // the identity without replica exchange), counts, the replica permutation
 // (rung -> slot, slot -> rung), spins, hidden words (rounded up to whole
-// uint4), then the records when staged.
+// uint4), the straggler counts and list, then the records when staged.
 constexpr int kBpSmemV = kAccWords + 2 * kBpTab + 96 + 64;
 static_assert(kBpSmemV % 4 == 0, "spins start on a 16-byte boundary");
 __host__ __device__ inline size_t bp_hid_words(const Geometry& g) {
     return (static_cast<size_t>(g.n_cells) * kBpNodes + 3) & ~static_cast<size_t>(3);
 }
+// Straggler list: (node, open chains) pairs, a quarter of the larger half-step
+// (at least 32 entries, a multiple of 4); nodes beyond it finish in place.
+__host__ __device__ inline int bp_strag_cap(const Geometry& g) {
+    const int n = g.n_cells * kBpNodes > g.N ? g.n_cells * kBpNodes : g.N;
+    const int q = ((n / 4) + 3) & ~3;
+    return q < 32 ? 32 : q;
+}
+// the list and its two counters (hidden, visible), padded to a whole uint4
+__host__ __device__ inline size_t bp_strag_words(const Geometry& g) { return 2 * static_cast<size_t>(bp_strag_cap(g)) + 4; }
+
 
 // The sweeps of one claimed word: its planes, spins and sums in, n sweeps
 // from global sweep t0 (measurement index meas0), spins and sums out.
@@ -65,11 +78,15 @@ __device__ __forceinline__ void sweep_bitplane_body(const SweepArgs& a, const ui
     int* s_bos = s_sob + 32;                                     // [32] rung of each slot
     uint32_t* s_v = smem + kBpSmemV;                             // [N] spin words
     uint32_t* s_h = s_v + N;                                     // [n_cells * 10] hidden words
+    int* s_nst = reinterpret_cast<int*>(s_h + bp_hid_words(g));   // [2] straggler counts (+2 pad)
+    uint2* s_list = reinterpret_cast<uint2*>(s_nst + 4);           // [cap] stragglers (node, open chains)
+    const int cap = bp_strag_cap(g);
     const uint32_t* gt = a.ctab + static_cast<size_t>(word) * kCanonTab;
     for (int x = threadIdx.x; x < kBpTab; x += blockDim.x) (kSwap ? s_tab0 : s_tab)[x] = gt[x];
     const uint32_t* gv = a.v + static_cast<size_t>(word) * N;
     for (int x = threadIdx.x; x < N; x += blockDim.x) s_v[x] = __ldcg(gv + x);
     for (int x = threadIdx.x; x < 96; x += blockDim.x) s_cnt[x] = 0;
+    if (threadIdx.x < 2) s_nst[threadIdx.x] = 0;
     if (warp == 0) {  // replica permutation (identity without replica exchange)
         const int sob = kSwap ? __ldcg(a.sob + word * 32 + lane) : lane;
         s_sob[lane] = sob;
@@ -101,72 +118,123 @@ __device__ __forceinline__ void sweep_bitplane_body(const SweepArgs& a, const ui
             fl0 = s_tab[kBpFlip];
             fl1 = s_tab[kBpFlip + 1];
         }
-        // hidden half-step (Eq. 9): thread = hidden node (cell, k)
-        for (int base = warp * 32; base < nh; base += nwarp * 32) {
-            const int node = base + lane;
-            const bool valid = node < nh;
-            const int nd = valid ? node : 0;
+        // hidden half-step (Eq. 9): thread = hidden node (cell, k).  Its endpoints select per chain
+        // the threshold planes of m = e1 + s e2 (P: m = 2, M: m = -2, Z: m = 0, whose threshold 2^31
+        // has only plane 0 set)
+        struct Hid {
+            uint32_t P, M, Z, c2;
+            const uint32_t* tp;
+            Round2Cell r2;
+        };
+        auto hidden_node = [&](int nd) {
             const uint32_t r = hrec[nd];
             const uint32_t cell = static_cast<uint32_t>(nd / kBpNodes);
             const uint32_t k = static_cast<uint32_t>(nd) - cell * kBpNodes;
             const uint32_t cls = k >= 8u ? 1u : 0u;
             const uint32_t e1 = s_v[r & 0xFFFFu];
             const uint32_t e2 = s_v[r >> 16] ^ (cls ? fl1 : fl0);
-            const uint32_t P = e1 & e2, M = ~(e1 | e2), Z = e1 ^ e2;  // m = 2, -2, 0
-            // m = 0 has the threshold 2^31 on every chain: plane 0 all ones, the rest zero
-            const uint32_t* tp = s_tab + kBpHidPlanes + cls * 96u;  // [m = -2, 0, 2][32]
             const uint64_t pc = static_cast<uint64_t>(kPhiloxM0) * cell;
-            const Round2Cell r2 = round2_cell(rs.hik ^ static_cast<uint32_t>(pc));
-            const uint32_t c2 = static_cast<uint32_t>(pc >> 32) ^ a.rk[1] ^ (kTagBitplane + 8u * k);
+            return Hid{e1 & e2, ~(e1 | e2), e1 ^ e2,
+                       static_cast<uint32_t>(pc >> 32) ^ a.rk[1] ^ (kTagBitplane + 8u * k),
+                       s_tab + kBpHidPlanes + cls * 96u, round2_cell(rs.hik ^ static_cast<uint32_t>(pc))};
+        };
+        for (int base = warp * 32; base < nh; base += nwarp * 32) {
+            const int node = base + lane;
+            const bool valid = node < nh;
+            const Hid hn = hidden_node(valid ? node : 0);
             uint32_t lt = 0u, eq = valid ? 0xffffffffu : 0u;
             auto planes = [&](const U4& q, uint32_t j) {
-                bp::hidden_planes(q, tp + 4u * j, P, M, j == 0u ? Z : 0u, lt, eq);
+                bp::hidden_planes(q, hn.tp + 4u * j, hn.P, hn.M, j == 0u ? hn.Z : 0u, lt, eq);
             };
-            // calls 0 and 1 together (a group of 32 nodes nearly always needs both:
-            // all 1024 comparisons close within 4 planes with probability
-            // (15/16)^1024), then one call at a time while any is open
-            const U4 q0 = philox_from_round2(Yw, rs, r2, c2, a.rk);
-            const U4 q1 = philox_from_round2(Yw, rs, r2, c2 ^ 1u, a.rk);
+            // calls 0 and 1 together, then the open nodes to the straggler list
+            const U4 q0 = philox_from_round2(Yw, rs, hn.r2, hn.c2, a.rk);
+            const U4 q1 = philox_from_round2(Yw, rs, hn.r2, hn.c2 ^ 1u, a.rk);
             planes(q0, 0u);
             planes(q1, 1u);
+            if (bp::push_straggler(static_cast<uint32_t>(node), eq, s_nst, s_list, cap, lane)) eq = 0u;
 #pragma unroll 1
-            for (uint32_t j = 2; j < 8u; ++j) {
+            for (uint32_t j = 2; j < 8u; ++j) {  // only where the list was full
                 if (!__any_sync(0xffffffffu, eq != 0u)) break;
-                planes(philox_from_round2(Yw, rs, r2, c2 ^ j, a.rk), j);
+                planes(philox_from_round2(Yw, rs, hn.r2, hn.c2 ^ j, a.rk), j);
             }
-            if (valid) s_h[node] = lt;
+            if (valid) s_h[node] = lt;  // final, or the decided part of a straggler
         }
         __syncthreads();
-        // visible half-step (Eq. 10): thread = spin site
-        for (int base = warp * 32; base < N; base += nwarp * 32) {
-            const int s = base + lane;
-            const bool valid = s < N;
-            const int sd = valid ? s : 0;
+        {
+            const int n_st = min(s_nst[0], cap);
+            for (int base = warp * 32; base < n_st; base += nwarp * 32) {
+                const bool valid = base + lane < n_st;
+                const uint2 e = valid ? s_list[base + lane] : make_uint2(0u, 0u);
+                const int node = static_cast<int>(e.x);
+                const Hid hn = hidden_node(node);
+                uint32_t lt = s_h[node], eq = e.y;
+#pragma unroll 1
+                for (uint32_t j = 2; j < 8u; ++j) {
+                    if (!__any_sync(0xffffffffu, eq != 0u)) break;
+                    bp::hidden_planes(philox_from_round2(Yw, rs, hn.r2, hn.c2 ^ j, a.rk), hn.tp + 4u * j, hn.P, hn.M,
+                                      0u, lt, eq);
+                }
+                if (valid) s_h[node] = lt;
+            }
+        }
+        __syncthreads();
+        if (threadIdx.x == 0) s_nst[0] = 0;  // every thread has read it (before the barrier above)
+        // visible half-step (Eq. 10): thread = spin site; its four J incidences, counted bit-sliced,
+        // and its J' incidence select one of the 5 x 2 visible threshold planes per chain
+        struct Vis {
+            uint32_t hp, c2;
+            bp::Count4 n4;
+            Round2Cell r2;
+        };
+        auto visible_node = [&](int sd) {
             const uint32_t r0 = vrec[3 * sd], r1 = vrec[3 * sd + 1], r2w = vrec[3 * sd + 2];
             auto hin = [&](uint32_t x, uint32_t fl) { return s_h[x & 0x7FFFu] ^ ((x & 0x8000u) ? fl : 0u); };
             const uint32_t h0 = hin(r0, fl0), h1 = hin(r0 >> 16, fl0), h2 = hin(r1, fl0), h3 = hin(r1 >> 16, fl0);
-            const uint32_t hp = hin(r2w, fl1);
             const uint32_t cell = (r2w >> 16) & 0xFFFu, x = r2w >> 28;
-            // count of +1 among h0..h3 = c0 + 2 c1 + 4 c2, bit-sliced
-            const bp::Count4 n4 = bp::count4(h0, h1, h2, h3);
-            const uint32_t* tv = s_tab + kBpVisPlanes;  // [count][J' bit][32]
             const uint64_t pc = static_cast<uint64_t>(kPhiloxM0) * cell;
-            const Round2Cell r2 = round2_cell(rs.hik ^ static_cast<uint32_t>(pc));
-            const uint32_t c2 = static_cast<uint32_t>(pc >> 32) ^ a.rk[1] ^ (kTagBitplane + 8u * (10u + x));
-            uint32_t lt = 0u, eq = valid ? 0xffffffffu : 0u;
-            auto planes = [&](const U4& q, uint32_t j) {
-                const uint32_t u[4] = {q.x, q.y, q.z, q.w};
+            return Vis{hin(r2w, fl1), static_cast<uint32_t>(pc >> 32) ^ a.rk[1] ^ (kTagBitplane + 8u * (10u + x)),
+                       bp::count4(h0, h1, h2, h3), round2_cell(rs.hik ^ static_cast<uint32_t>(pc))};
+        };
+        const uint32_t* tv = s_tab + kBpVisPlanes;  // [count][J' bit][32]
+        auto vis_planes = [&](const Vis& vn, const U4& q, uint32_t j, uint32_t& lt, uint32_t& eq) {
+            const uint32_t u[4] = {q.x, q.y, q.z, q.w};
 #pragma unroll
-                for (int i = 0; i < 4; ++i) bp::plane_step(u[i], bp::visible_plane(tv + 4u * j + i, hp, n4), lt, eq);
-            };
+            for (int i = 0; i < 4; ++i) bp::plane_step(u[i], bp::visible_plane(tv + 4u * j + i, vn.hp, vn.n4), lt, eq);
+        };
+        for (int base = warp * 32; base < N; base += nwarp * 32) {
+            const int sx = base + lane;
+            const bool valid = sx < N;
+            const Vis vn = visible_node(valid ? sx : 0);
+            uint32_t lt = 0u, eq = valid ? 0xffffffffu : 0u;
+            vis_planes(vn, philox_from_round2(Yw, rs, vn.r2, vn.c2, a.rk), 0u, lt, eq);
+            vis_planes(vn, philox_from_round2(Yw, rs, vn.r2, vn.c2 ^ 1u, a.rk), 1u, lt, eq);
+            if (bp::push_straggler(static_cast<uint32_t>(sx), eq, s_nst + 1, s_list, cap, lane)) eq = 0u;
 #pragma unroll 1
-            for (uint32_t j = 0; j < 8u; ++j) {
+            for (uint32_t j = 2; j < 8u; ++j) {  // only where the list was full
                 if (!__any_sync(0xffffffffu, eq != 0u)) break;
-                planes(philox_from_round2(Yw, rs, r2, c2 ^ j, a.rk), j);
+                vis_planes(vn, philox_from_round2(Yw, rs, vn.r2, vn.c2 ^ j, a.rk), j, lt, eq);
             }
-            if (valid) s_v[s] = lt;
+            if (valid) s_v[sx] = lt;  // no spin is read in this half-step
         }
         __syncthreads();
+        {
+            const int n_st = min(s_nst[1], cap);
+            for (int base = warp * 32; base < n_st; base += nwarp * 32) {
+                const bool valid = base + lane < n_st;
+                const uint2 e = valid ? s_list[base + lane] : make_uint2(0u, 0u);
+                const int sx = static_cast<int>(e.x);
+                const Vis vn = visible_node(sx);
+                uint32_t lt = s_v[sx], eq = e.y;
+#pragma unroll 1
+                for (uint32_t j = 2; j < 8u; ++j) {
+                    if (!__any_sync(0xffffffffu, eq != 0u)) break;
+                    vis_planes(vn, philox_from_round2(Yw, rs, vn.r2, vn.c2 ^ j, a.rk), j, lt, eq);
+                }
+                if (valid) s_v[sx] = lt;
+            }
+        }
+        __syncthreads();
+        if (threadIdx.x == 0) s_nst[1] = 0;
         const bool do_meas = measuring && (t + 1u) % static_cast<uint32_t>(a.measure_every) == 0u;
         const bool do_swap = kSwap && (t + 1u) % static_cast<uint32_t>(a.swap_every) == 0u;
         if (do_meas || do_swap) {
@@ -210,7 +278,7 @@ __global__ void __launch_bounds__(kBpMaxThreads) k_sweep_bitplane(const SweepArg
     const int nh = g.n_cells * kBpNodes;
     const uint32_t* rec = reinterpret_cast<const uint32_t*>(a.crec);
     if (kSmemRec) {
-        uint32_t* s_rec = smem + kBpSmemV + g.N + bp_hid_words(g);  // N is a multiple of 4 (even sides)
+        uint32_t* s_rec = smem + kBpSmemV + g.N + bp_hid_words(g) + bp_strag_words(g);  // N: a multiple of 4
         for (int x = threadIdx.x; x < static_cast<int>(bp_rec_words(g) / 4); x += blockDim.x)
             reinterpret_cast<uint4*>(s_rec)[x] = __ldg(a.crec + x);
         rec = s_rec;
@@ -247,7 +315,7 @@ __global__ void __launch_bounds__(kBpMaxThreads) k_sweep_bitplane(const SweepArg
 }  // namespace
 
 size_t smem_bytes_bitplane(const Geometry& g, bool with_records) {
-    return sizeof(uint32_t) * (kBpSmemV + static_cast<size_t>(g.N) + bp_hid_words(g) +
+    return sizeof(uint32_t) * (kBpSmemV + static_cast<size_t>(g.N) + bp_hid_words(g) + bp_strag_words(g) +
                                (with_records ? bp_rec_words(g) : 0));
 }
 

@@ -50,5 +50,22 @@ __device__ __forceinline__ uint32_t visible_plane(const uint32_t* tb, uint32_t h
     return (n.c2 & sel(4)) | (~n.c2 & ((n.c1 & m23) | (~n.c1 & m01)));
 }
 
+// Appends the lanes whose comparison is still open (open != 0: its
+// undecided chains) to a straggler list of (node, open chains) pairs, with
+// one atomic per warp; returns true on the lanes whose node went to the list
+// (false where the list is full: that lane finishes its node itself).
+__device__ __forceinline__ bool push_straggler(uint32_t node, uint32_t open, int* count, uint2* list, int cap,
+                                               int lane) {
+    const uint32_t bal = __ballot_sync(0xffffffffu, open != 0u);
+    if (bal == 0u) return false;
+    int first = 0;
+    if (lane == 0) first = atomicAdd(count, __popc(bal));
+    first = __shfl_sync(0xffffffffu, first, 0);
+    const int slot = first + __popc(bal & ((1u << lane) - 1u));
+    if (open == 0u || slot >= cap) return false;
+    list[slot] = make_uint2(node, open);
+    return true;
+}
+
 }  // namespace bp
 }  // namespace crbm

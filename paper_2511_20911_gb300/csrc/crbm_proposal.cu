@@ -13,9 +13,12 @@
 // energy halo and the moves of a pass commute.
 //
 // The pass runs the three convolutions on the tcgen05 tensor cores (bf16
-// operands from shared memory, fp32 accumulators in tensor memory), one CTA
-// of four warps per work item = (block of the pass, 16 chains of a packed
-// word), persistent over the items.  Activations live in an 8 x 8 frame per
+// operands from shared memory, fp32 accumulators in tensor memory): one
+// persistent CTA per SM holds four independent groups of four warps, each
+// group working through its own work items = (block of the pass, 16 chains
+// of a packed word) with its own shared-memory buffers, mbarrier, named
+// barrier and 128 of the SM's 512 tensor-memory columns (one CTA, so the
+// tensor memory is allocated once and the B operands staged once per SM).  Activations live in an 8 x 8 frame per
 // chain, stored as "column planes": plane (x, h) holds channels 8h .. 8h + 7
 // of frame column x for the 128 rows (chain, frame row y), 16 bytes a row.
 //  * layer 1 acts on the spin plane alone (its five constant planes are folded
@@ -75,10 +78,13 @@ constexpr int oW1 = 0, oB1 = 864, oW2 = 880, oB2 = 3184, oW3 = 3200, oB3 = 3344;
 constexpr int kC1Pos = 4 * kS1 * kS1 * 16, kC1 = kC1Pos + 2 * 16;
 
 // ---- tensor-core pass geometry
-constexpr int kPassThreads = 128;              // one warpgroup: warp w reads TMEM lanes 32 w ..
+constexpr int kPassThreads = 128;              // one group (warpgroup): warp w reads TMEM lanes 32 (w % 4) ..
+constexpr int kGroups = 1;                     // groups per CTA (2 or 4 measured slower)
+constexpr int kCtasPerSm = 4 / kGroups;        // four groups per SM: 4 x 128 tensor-memory columns
+constexpr int kCtaThreads = kGroups * kPassThreads;
 constexpr int kItemChains = 16;                // chains of one work item (half a packed word)
 constexpr int kFrame = 8;                      // every layer in an 8 x 8 frame per chain
-constexpr int kTmemCols = 128;
+constexpr int kTmemCols = 128;                 // per group; the CTA allocates kGroups x 128 = 512
 constexpr int kPlaneRows = 136;                // 128 rows (chain, y) + rows read by the dy = 1, 2 shifts
 constexpr int kPlane = kPlaneRows * 16;        // bytes of one column plane (x, h)
 // Layer-1 operand (gathered): rows (x, chain, y), K = 9 spin taps, then 1,
@@ -92,21 +98,26 @@ constexpr int kZ2Rows = 3 * 16, kZ3Rows = 24;
 constexpr int kB1 = 0, kZ2 = 256, kZ3 = kZ2 + 3 * 2 * kZ2Rows * 8, kBElems = kZ3 + 3 * 2 * kZ3Rows * 8;
 constexpr uint32_t kIdesc1 = umma::idesc_bf16_f32(128, 16);
 constexpr uint32_t kIdesc3 = umma::idesc_bf16_f32(128, 16);
-// Shared memory of the pass (bytes).  X holds, in turn, layer 1's gathered
+// Shared memory of the pass (bytes): the B operands (shared by the groups),
+// then one region per group.  A group's X holds, in turn, layer 1's gathered
 // operand, layer 1's output planes (layer 2's operand), layer 2's output
-// planes (layer 3's operand) and the Metropolis-Hastings arrays.  Item data
-// are double-buffered (the next item's are fetched during this one); the
-// folded layer-1 constants of the item are fetched at its start.
-constexpr int kSmX = 0, kSmXBytes = 8 * 2 * kPlane;        // 34816 >= 2 * kA0Plane
-constexpr int kSmB = kSmX + kSmXBytes;
+// planes (layer 3's operand) and the block's logits.  Item data are
+// double-buffered (the next item's are fetched during this one); the folded
+// layer-1 constants of the item are fetched at its start.
+constexpr int kSmB = 0;
+constexpr int kSmG0 = ((kBElems * 2 + 127) / 128) * 128;   // first group region
+constexpr int kSmX = 0, kSmXBytes = 8 * 2 * kPlane;        // 34816 >= 2 * kA0Plane (offsets in a group)
 constexpr int kItemBytes = 104 * 4 + kItemChains * 8 * 4;  // patch [100](+4), chain_bh [16][4], Q.4 [16][4]
 constexpr int kC1Stride = 20;                              // floats per (x, y) row of staged constants
 constexpr int kC1Bytes = 64 * kC1Stride * 4;
-constexpr int kSmItem = kSmB + kBElems * 2;
+constexpr int kSmItem = kSmX + kSmXBytes;
 constexpr int kSmC1 = kSmItem + 2 * kItemBytes;
-constexpr int kSmBar = kSmC1 + kC1Bytes, kSmBytes = kSmBar + 16;
+constexpr int kSmBar = kSmC1 + kC1Bytes, kSmGroup = kSmBar + 16;
+constexpr int kSmBytes = kSmG0 + kGroups * kSmGroup + 16;  // + the tensor-memory address slot
 static_assert(kSmXBytes >= 2 * kA0Plane, "layer-1 operand fits in X");
-static_assert(kSmB % 16 == 0 && kSmItem % 16 == 0 && kSmC1 % 16 == 0 && kSmBar % 8 == 0, "alignment");
+static_assert(kSmG0 % 128 == 0 && kSmGroup % 16 == 0 && kSmItem % 16 == 0 && kSmC1 % 16 == 0 && kSmBar % 8 == 0,
+              "alignment");
+static_assert(kSmBytes * kCtasPerSm <= 226 * 1024, "kCtasPerSm CTAs per SM");
 constexpr int kWaitTries = 1 << 22;            // mbarrier polls before the pass gives up
 
 // Per (word, block, lane) record of a pass run in inspection mode: the
@@ -177,37 +188,50 @@ __device__ __forceinline__ void fetch_c1(const PassArgs& a, uint8_t* sm, int var
     asm volatile("cp.async.commit_group;" ::: "memory");
 }
 
-// One pass of MH block moves; persistent CTAs of four warps take items
-// (block b, half-word hw) in turn.
-__global__ void __launch_bounds__(kPassThreads, 4) k_prop_pass(const __grid_constant__ PassArgs a) {
-    extern __shared__ __align__(1024) uint8_t sm[];
+// Group barrier: the 128 threads of group g (named barrier 1 + g).
+__device__ __forceinline__ void group_sync(int g) {
+    asm volatile("bar.sync %0, %1;" ::"r"(1 + g), "n"(kPassThreads) : "memory");
+}
+
+// One pass of MH block moves; one persistent CTA per SM, whose four groups
+// of four warps take items (block b, half-word hw) in turn.
+__global__ void __launch_bounds__(kCtaThreads, kCtasPerSm) k_prop_pass(const __grid_constant__ PassArgs a) {
+    extern __shared__ __align__(1024) uint8_t smem_all[];
     const int L = a.g.L, N = a.g.N;
-    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+    const int g = threadIdx.x / kPassThreads;  // group
+    const int tid = threadIdx.x % kPassThreads, lane = tid & 31, warp = tid >> 5;  // within the group
     const int n_blocks = a.nb1 * a.nb1;
+    uint8_t* sm = smem_all + kSmG0 + g * kSmGroup;  // the group's region
     uint8_t* X = sm + kSmX;
-    uint16_t* Bs = reinterpret_cast<uint16_t*>(sm + kSmB);
+    uint16_t* Bs = reinterpret_cast<uint16_t*>(smem_all + kSmB);
     const uint32_t bar = umma::smem_addr(sm + kSmBar);
-    uint32_t* tslot = reinterpret_cast<uint32_t*>(sm + kSmBar + 8);
-    __shared__ int s_fail;
+    uint32_t* tslot = reinterpret_cast<uint32_t*>(smem_all + kSmG0 + kGroups * kSmGroup);
+    __shared__ int s_fail[kGroups];
+    __shared__ unsigned long long s_stats[2];  // proposed, accepted by this CTA
     // the block's logits in X after layer 3 ([site][chain], 16 chains)
     float* logit = reinterpret_cast<float*>(X);
 
-    // set-up: B operands, zero X (the shift rows past 128 must hold finite values), mbarrier, TMEM
-    for (int x = tid; x < kBElems / 8; x += kPassThreads) reinterpret_cast<uint4*>(Bs)[x] = a.bmat[x];
-    for (int x = tid; x < kSmXBytes / 16; x += kPassThreads) reinterpret_cast<uint4*>(X)[x] = make_uint4(0, 0, 0, 0);
+    // set-up: the tensor memory first (a CTA of a kernel that allocates tensor memory starts only
+    // after the SM's previous one gave up its allocation permit), B operands, the never-written tail
+    // of each X (rows past 128 of the last plane, read by the dy = 1, 2 shifts), mbarriers
+    if (threadIdx.x < 32) umma::tmem_alloc(umma::smem_addr(tslot), kGroups * kTmemCols);
+    for (int x = threadIdx.x; x < kBElems / 8; x += kCtaThreads) reinterpret_cast<uint4*>(Bs)[x] = a.bmat[x];
+    for (int x = 2 * kA0Plane / 16 + tid; x < kSmXBytes / 16; x += kPassThreads)
+        reinterpret_cast<uint4*>(X)[x] = make_uint4(0, 0, 0, 0);
     if (tid == 0) {
         umma::mbar_init(bar, 1);
-        s_fail = 0;
+        s_fail[g] = 0;
     }
-    if (warp == 0) umma::tmem_alloc(umma::smem_addr(tslot), kTmemCols);
+    if (threadIdx.x < 2) s_stats[threadIdx.x] = 0ull;
     const U4 off = philox(a.pass, 0u, 0u, kTagOffset, a.key0, a.key1);
     const int bR0 = static_cast<int>(off.x % static_cast<uint32_t>(L));
     const int bC0 = static_cast<int>(off.y % static_cast<uint32_t>(L));
-    if (blockIdx.x < a.n_items) prefetch_item(a, sm, 0, blockIdx.x, bR0, bC0, tid);
+    const int item0 = blockIdx.x * kGroups + g, stride = gridDim.x * kGroups;
+    if (item0 < a.n_items) prefetch_item(a, sm, 0, item0, bR0, bC0, tid);
     umma::fence_before_sync();
     __syncthreads();
     umma::fence_after_sync();
-    const uint32_t tmem = *tslot;
+    const uint32_t tmem = *tslot + static_cast<uint32_t>(kTmemCols * g);
     const uint32_t xs = umma::smem_addr(X), bs = umma::smem_addr(Bs);
     uint32_t phase = 0;
     // this thread's accumulator lane 32 warp + lane = row (chain cl, frame row y)
@@ -220,7 +244,7 @@ __global__ void __launch_bounds__(kPassThreads, 4) k_prop_pass(const __grid_cons
     bool ok = true;
     int buf = 0;
 
-    for (int item = blockIdx.x; item < a.n_items && ok; item += gridDim.x, buf ^= 1) {
+    for (int item = item0; item < a.n_items && ok; item += stride, buf ^= 1) {
         const int b = item % n_blocks, hw = item / n_blocks;
         const int word = hw >> 1, half = hw & 1;
         const int bR = (bR0 + a.spacing * (b / a.nb1)) % L, bC = (bC0 + a.spacing * (b % a.nb1)) % L;
@@ -230,10 +254,10 @@ __global__ void __launch_bounds__(kPassThreads, 4) k_prop_pass(const __grid_cons
         const int32_t* cq = reinterpret_cast<const int32_t*>(ib + 672);         // [16][4] Q.4 J, J', h
         const float* c1s = reinterpret_cast<const float*>(sm + kSmC1);
         asm volatile("cp.async.wait_all;" ::: "memory");
-        __syncthreads();
+        group_sync(g);
         fetch_c1(a, sm, ((bR + 1) & 1) * 2 + ((bC + 1) & 1), tid);
-        if (item + static_cast<int>(gridDim.x) < a.n_items)   // the next item's data, during this one
-            prefetch_item(a, sm, buf ^ 1, item + gridDim.x, bR0, bC0, tid);
+        if (item + stride < a.n_items)   // the next item's data, during this one
+            prefetch_item(a, sm, buf ^ 1, item + stride, bR0, bC0, tid);
         else
             asm volatile("cp.async.commit_group;" ::: "memory");
         // ---- layer-1 operand: rows x * 128 + (chain c, y) = tid, K = 9 spin taps (0 inside
@@ -265,7 +289,7 @@ __global__ void __launch_bounds__(kPassThreads, 4) k_prop_pass(const __grid_cons
         asm volatile("cp.async.wait_group 1;" ::: "memory");  // this item's constants (not the next item's data)
         umma::fence_async_smem();
         umma::fence_before_sync();
-        __syncthreads();
+        group_sync(g);
         if (tid == 0) {  // layer 1: one K = 16 MMA per frame column x (accumulator columns 16 x)
             umma::fence_after_sync();
             for (int x = 0; x < kFrame; ++x)
@@ -273,7 +297,7 @@ __global__ void __launch_bounds__(kPassThreads, 4) k_prop_pass(const __grid_cons
                           kIdesc1, 0u);
             umma::commit(bar);
         }
-        if (!umma::mbar_wait(bar, phase, kWaitTries)) s_fail = 1;
+        if (!umma::mbar_wait(bar, phase, kWaitTries)) s_fail[g] = 1;
         phase ^= 1u;
         umma::fence_after_sync();
         // ---- epilogue 1: + folded constants, ReLU, bf16 -> column planes (x, h), row my_row
@@ -304,8 +328,8 @@ __global__ void __launch_bounds__(kPassThreads, 4) k_prop_pass(const __grid_cons
         umma::tmem_st_wait();
         umma::fence_async_smem();
         umma::fence_before_sync();
-        __syncthreads();
-        if (s_fail) {
+        group_sync(g);
+        if (s_fail[g]) {
             ok = false;
             break;
         }
@@ -320,7 +344,7 @@ __global__ void __launch_bounds__(kPassThreads, 4) k_prop_pass(const __grid_cons
                 }
             umma::commit(bar);
         }
-        if (!umma::mbar_wait(bar, phase, kWaitTries)) s_fail = 1;
+        if (!umma::mbar_wait(bar, phase, kWaitTries)) s_fail[g] = 1;
         phase ^= 1u;
         umma::fence_after_sync();
         // ---- epilogue 2: + b2, ReLU, bf16 -> column planes 0..5 (layer 3's operand)
@@ -344,8 +368,8 @@ __global__ void __launch_bounds__(kPassThreads, 4) k_prop_pass(const __grid_cons
         }
         umma::fence_async_smem();
         umma::fence_before_sync();
-        __syncthreads();
-        if (s_fail) {
+        group_sync(g);
+        if (s_fail[g]) {
             ok = false;
             break;
         }
@@ -358,7 +382,7 @@ __global__ void __launch_bounds__(kPassThreads, 4) k_prop_pass(const __grid_cons
                               kIdesc3, (dy | o) ? 1u : 0u);
             umma::commit(bar);
         }
-        if (!umma::mbar_wait(bar, phase, kWaitTries)) s_fail = 1;
+        if (!umma::mbar_wait(bar, phase, kWaitTries)) s_fail[g] = 1;
         phase ^= 1u;
         umma::fence_after_sync();
         // ---- epilogue 3: rows y < 4 hold the logits of block sites (y, 0..3)
@@ -372,8 +396,8 @@ __global__ void __launch_bounds__(kPassThreads, 4) k_prop_pass(const __grid_cons
             }
         }
         umma::fence_before_sync();
-        __syncthreads();
-        if (s_fail) {
+        group_sync(g);
+        if (s_fail[g]) {
             ok = false;
             break;
         }
@@ -401,12 +425,13 @@ __global__ void __launch_bounds__(kPassThreads, 4) k_prop_pass(const __grid_cons
                 const int ar = s / kK, ac = s % kK;
                 const bool xc = (pw[(3 + ar) * kP + 3 + ac] >> cbit) & 1u;
                 const float lg = logit[s * 16 + c];
-                const float q = 1.f / (1.f + __expf(-lg));
+                const float q = __fdividef(1.f, 1.f + __expf(-lg));
                 float tf = q * 4294967296.f;
                 tf = fminf(fmaxf(tf, 1.f), 4294967040.f);
                 const uint32_t thr = static_cast<uint32_t>(tf);
-                const float p1 = static_cast<float>(thr) * 2.3283064365386963e-10f;
-                const float lp = __logf(p1), lm = log1pf(-p1);
+                // log p and log (1 - p) of p = thr / 2^32, from the exact integers thr and 2^32 - thr
+                const float lp = __logf(static_cast<float>(thr)) - 22.18070977791825f;
+                const float lm = __logf(static_cast<float>(0u - thr)) - 22.18070977791825f;
                 const bool xp = pick(u, s & 3) < thr;
                 lq += (xc ? lp : lm) - (xp ? lp : lm);
                 bits |= (xc ? 1u : 0u) << s | (xp ? 1u : 0u) << (16 + s);
@@ -472,36 +497,37 @@ __global__ void __launch_bounds__(kPassThreads, 4) k_prop_pass(const __grid_cons
                 const uint32_t flip = accept ? (cb ^ nb) : 0u;
                 uint32_t my_fm = 0u;  // lane s < 16: the warp's chains whose site s flips
 #pragma unroll
-                for (int s = 0; s < kK * kK; ++s) {
-                    const uint32_t bl = __ballot_sync(0xffffffffu, (flip >> s) & 1u);
-                    const uint32_t fm = (bl & 1u) | ((bl >> 7) & 2u) | ((bl >> 14) & 4u) | ((bl >> 21) & 8u);
-                    my_fm = lane == s ? fm : my_fm;
-                }
+                for (int j = 0; j < 4; ++j)
+                    my_fm |= ((__shfl_sync(0xffffffffu, flip, 8 * j) >> (lane & 15)) & 1u) << j;
                 if (lane < 16 && my_fm) {
                     const int R = (bR + lane / kK) % L, C = (bC + lane % kK) % L;
                     atomicXor(a.v + static_cast<size_t>(word) * N + R * L + C, my_fm << (16 * half + 4 * warp));
                 }
                 const uint32_t am = __ballot_sync(0xffffffffu, accept && part == 0);
                 if (lane == 0) {
-                    atomicAdd(&a.stats[0], 4ull);
-                    atomicAdd(&a.stats[1], static_cast<unsigned long long>(__popc(am)));
+                    atomicAdd(&s_stats[0], 4ull);
+                    atomicAdd(&s_stats[1], static_cast<unsigned long long>(__popc(am)));
                 }
             }
         }
-        __syncthreads();
+        group_sync(g);
     }
     asm volatile("cp.async.wait_all;" ::: "memory");
     // a timed-out wait: record it, give the tensor cores one more bounded wait
-    // for the MMAs in flight, then free the tensor memory
+    // for the group's MMAs in flight, then (every group done) free the tensor memory
     if (!ok) {
         if (tid == 0) atomicAdd(&a.stats[2], 1ull);
         umma::mbar_wait(bar, phase ^ 1u, kWaitTries);
     }
     umma::fence_before_sync();
     __syncthreads();
-    if (warp == 0) {
+    if (threadIdx.x < 32) {
         umma::fence_after_sync();
-        umma::tmem_dealloc(tmem, kTmemCols);
+        umma::tmem_dealloc(*tslot, kGroups * kTmemCols);
+    }
+    if (threadIdx.x == 32 && s_stats[0]) {
+        atomicAdd(&a.stats[0], s_stats[0]);
+        atomicAdd(&a.stats[1], s_stats[1]);
     }
 }
 
@@ -754,6 +780,7 @@ struct crbm_proposal {
     int ex_cap = 0;
     int64_t adam_t = 0;
     uint64_t seed = 0;
+    int pass_sms = 0, pass_dev = -1;  // SM count of the device the pass kernel was set up on
 };
 
 namespace {
@@ -863,22 +890,21 @@ cudaError_t launch_pass(crbm_ctx* ctx, crbm_proposal* p, crbm::PassRecord* rec) 
     a.nb1 = nb1;
     a.spacing = L / nb1;
     a.n_items = nb1 * nb1 * 2 * ctx->n_words;  // (block, 16-chain half of a word)
-    const size_t smem = crbm::kSmBytes;
-    cudaError_t e = cudaFuncSetAttribute(crbm::k_prop_pass, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                         static_cast<int>(smem));
-    if (e == cudaSuccess)  // all of the unified L1 / shared memory as shared memory
-        e = cudaFuncSetAttribute(crbm::k_prop_pass, cudaFuncAttributePreferredSharedMemoryCarveout, 100);
-    int sms = 0, smem_sm = 0;
-    if (e == cudaSuccess) e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, ctx->device);
-    if (e == cudaSuccess) e = cudaDeviceGetAttribute(&smem_sm, cudaDevAttrMaxSharedMemoryPerMultiprocessor, ctx->device);
-    if (e != cudaSuccess) return e;
-    // persistent: as many CTAs per SM as shared memory holds (each also takes
-    // 1 KB of static and 1 KB of reserved shared memory), at most four, whose
-    // tensor-memory columns, 4 x 128, fill the SM's 512.  (The occupancy
-    // query reports one CTA per SM for this kernel; four run side by side.)
-    const int per_sm = std::max(1, std::min(4, smem_sm / static_cast<int>(smem + 2048)));
-    const int grid = std::min(a.n_items, per_sm * sms);
-    crbm::k_prop_pass<<<grid, crbm::kPassThreads, smem, ctx->stream>>>(a);
+    // one persistent CTA per SM (four groups of four warps); the attribute and the SM count are set
+    // and read once per proposal
+    if (p->pass_sms == 0 || p->pass_dev != ctx->device) {
+        cudaError_t e = cudaFuncSetAttribute(crbm::k_prop_pass, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                             static_cast<int>(crbm::kSmBytes));
+        if (e == cudaSuccess)  // all of the unified L1 / shared memory as shared memory
+            e = cudaFuncSetAttribute(crbm::k_prop_pass, cudaFuncAttributePreferredSharedMemoryCarveout, 100);
+        int sms = 0;
+        if (e == cudaSuccess) e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, ctx->device);
+        if (e != cudaSuccess) return e;
+        p->pass_sms = sms;
+        p->pass_dev = ctx->device;
+    }
+    const int grid = std::min((a.n_items + crbm::kGroups - 1) / crbm::kGroups, crbm::kCtasPerSm * p->pass_sms);
+    crbm::k_prop_pass<<<grid, crbm::kCtaThreads, crbm::kSmBytes, ctx->stream>>>(a);
     return cudaGetLastError();
 }
 

@@ -233,10 +233,13 @@ __global__ void __launch_bounds__(kStreamVisThreads, CRBM_STREAM_VIS_MIN_BLOCKS)
 // Hidden half-step of one tile: the spin tile (halo included) in, the tile's
 // hidden words out.
 __global__ void __launch_bounds__(kStreamThreads) k_stream_bp_hidden(const SweepArgs a, uint32_t t) {
+    constexpr int kCap = kTI * kTJ * 10 / 4;  // straggler list: a quarter of the tile's nodes
     __shared__ uint32_t s_tab[kBpTab];
     __shared__ uint32_t s_v[(2 * kTI + 1) * (2 * kTJ + 1)];
     __shared__ uint32_t s_h[kTI * kTJ * 10];
+    __shared__ uint2 s_list[kCap];
     __shared__ int s_off[2][10];  // the filters' endpoint offsets in the staged tile
+    __shared__ int s_nst;
     const Geometry& g = a.g;
     const int W = g.W;
     const int w = blockIdx.y;
@@ -251,6 +254,7 @@ __global__ void __launch_bounds__(kStreamThreads) k_stream_bp_hidden(const Sweep
         s_off[0][k] = g.r1[k] * VS + g.c1[k];
         s_off[1][k] = g.r2[k] * VS + g.c2[k];
     }
+    if (threadIdx.x == 0) s_nst = 0;
     stage_spin_tile(a, w, i0, j0, s_v);
     __syncthreads();
     const uint32_t fl0 = s_tab[kBpFlip], fl1 = s_tab[kBpFlip + 1];
@@ -258,34 +262,63 @@ __global__ void __launch_bounds__(kStreamThreads) k_stream_bp_hidden(const Sweep
     const uint64_t pw = static_cast<uint64_t>(kPhiloxM1) * static_cast<uint32_t>(w);
     const uint32_t Yw = static_cast<uint32_t>(pw);
     const Round1Sweep rs = round1_sweep(static_cast<uint32_t>(pw >> 32) ^ a.rk[0] ^ t, a.rk);
-    for (int base = warp * 32; base < nn; base += nwarp * 32) {
-        const int node = base + lane;
-        const bool valid = node < nn;
-        const int nd = valid ? node : 0;
+    // node nd of the tile: its threshold planes (P: m = 2, M: m = -2, Z: m = 0), Philox cell words
+    // and the index of its hidden word in s_h
+    struct Hid {
+        uint32_t P, M, Z, c2;
+        const uint32_t* tp;
+        Round2Cell r2;
+        int out;
+    };
+    auto hidden_node = [&](int nd) {
         const int lc = nd / 10, k = nd - lc * 10;
         const int li = lc / nj, lj = lc - li * nj;
         const uint32_t cls = k >= 8 ? 1u : 0u;
         const uint32_t* v = s_v + 2 * li * VS + 2 * lj;
         const uint32_t e1 = v[s_off[0][k]];
         const uint32_t e2 = v[s_off[1][k]] ^ (cls ? fl1 : fl0);
-        const uint32_t P = e1 & e2, M = ~(e1 | e2), Z = e1 ^ e2;
-        const uint32_t* tp = s_tab + kBpHidPlanes + cls * 96u;
         const uint32_t cell = static_cast<uint32_t>((i0 + li) * W + j0 + lj);
         const uint64_t pc = static_cast<uint64_t>(kPhiloxM0) * cell;
-        const Round2Cell r2 = round2_cell(rs.hik ^ static_cast<uint32_t>(pc));
-        const uint32_t c2 = static_cast<uint32_t>(pc >> 32) ^ a.rk[1] ^ (kTagBitplane + 8u * static_cast<uint32_t>(k));
+        return Hid{e1 & e2, ~(e1 | e2), e1 ^ e2,
+                   static_cast<uint32_t>(pc >> 32) ^ a.rk[1] ^ (kTagBitplane + 8u * static_cast<uint32_t>(k)),
+                   s_tab + kBpHidPlanes + cls * 96u, round2_cell(rs.hik ^ static_cast<uint32_t>(pc)),
+                   (li * kTJ + lj) * 10 + k};
+    };
+    for (int base = warp * 32; base < nn; base += nwarp * 32) {
+        const int node = base + lane;
+        const bool valid = node < nn;
+        const Hid hn = hidden_node(valid ? node : 0);
         uint32_t lt = 0u, eq = valid ? 0xffffffffu : 0u;
-        auto planes = [&](const U4& q, uint32_t j) { bp::hidden_planes(q, tp + 4u * j, P, M, j == 0u ? Z : 0u, lt, eq); };
-        const U4 q0 = philox_from_round2(Yw, rs, r2, c2, a.rk);
-        const U4 q1 = philox_from_round2(Yw, rs, r2, c2 ^ 1u, a.rk);
+        auto planes = [&](const U4& q, uint32_t j) {
+            bp::hidden_planes(q, hn.tp + 4u * j, hn.P, hn.M, j == 0u ? hn.Z : 0u, lt, eq);
+        };
+        // calls 0 and 1 together, then the open nodes to the straggler list
+        const U4 q0 = philox_from_round2(Yw, rs, hn.r2, hn.c2, a.rk);
+        const U4 q1 = philox_from_round2(Yw, rs, hn.r2, hn.c2 ^ 1u, a.rk);
         planes(q0, 0u);
         planes(q1, 1u);
+        if (bp::push_straggler(static_cast<uint32_t>(node), eq, &s_nst, s_list, kCap, lane)) eq = 0u;
+#pragma unroll 1
+        for (uint32_t j = 2; j < 8u; ++j) {  // only where the list was full
+            if (!__any_sync(0xffffffffu, eq != 0u)) break;
+            planes(philox_from_round2(Yw, rs, hn.r2, hn.c2 ^ j, a.rk), j);
+        }
+        if (valid) s_h[hn.out] = lt;  // final, or the decided part of a straggler
+    }
+    __syncthreads();
+    const int n_st = min(s_nst, kCap);
+    for (int base = warp * 32; base < n_st; base += nwarp * 32) {
+        const bool valid = base + lane < n_st;
+        const uint2 e = valid ? s_list[base + lane] : make_uint2(0u, 0u);
+        const Hid hn = hidden_node(static_cast<int>(e.x));
+        uint32_t lt = s_h[hn.out], eq = e.y;
 #pragma unroll 1
         for (uint32_t j = 2; j < 8u; ++j) {
             if (!__any_sync(0xffffffffu, eq != 0u)) break;
-            planes(philox_from_round2(Yw, rs, r2, c2 ^ j, a.rk), j);
+            bp::hidden_planes(philox_from_round2(Yw, rs, hn.r2, hn.c2 ^ j, a.rk), hn.tp + 4u * j, hn.P, hn.M, 0u, lt,
+                              eq);
         }
-        if (valid) s_h[(li * kTJ + lj) * 10 + k] = lt;
+        if (valid) s_h[hn.out] = lt;
     }
     __syncthreads();
     // tile rows of hidden words are runs of 10 nj words in h
@@ -298,12 +331,15 @@ __global__ void __launch_bounds__(kStreamThreads) k_stream_bp_hidden(const Sweep
 
 // Visible half-step of one tile: the hidden words of the tile's cells and of
 // the row above and the column to the left (wrapped) in, new spins out.
-__global__ void __launch_bounds__(kStreamVisThreads) k_stream_bp_visible(const SweepArgs a, uint32_t t) {
+__global__ void __launch_bounds__(kStreamVisThreads, CRBM_STREAM_MIN_BLOCKS) k_stream_bp_visible(const SweepArgs a, uint32_t t) {
     constexpr int HS = kTJ + 1;
     __shared__ uint32_t s_tab[kBpTab];
     __shared__ uint32_t s_h[(kTI + 1) * HS * 10];
     __shared__ uint32_t s_o[2 * kTI * 2 * kTJ];
+    constexpr int kCap = 2 * kTI * 2 * kTJ / 4;  // straggler list: a quarter of the tile's spins
+    __shared__ uint2 s_list[kCap];
     __shared__ int s_inc[4][5];  // per spin class x: hidden word offset (cell row, column, filter) | flags
+    __shared__ int s_nst;
     const Geometry& g = a.g;
     const int L = g.L, W = g.W, N = g.N;
     const int w = blockIdx.y;
@@ -312,6 +348,7 @@ __global__ void __launch_bounds__(kStreamVisThreads) k_stream_bp_visible(const S
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nwarp = blockDim.x >> 5;
     const uint32_t* gt = a.ctab + static_cast<size_t>(w) * kCanonTab;
     for (int x = threadIdx.x; x < kBpTab; x += blockDim.x) s_tab[x] = gt[x];
+    if (threadIdx.x == 0) s_nst = 0;
     if (threadIdx.x < 4) {
         // the five filters touching the spin at window offset (r, c): endpoints
         // at (r, c) of the own cell, (r + 2, c) of the cell above, (r, c + 2) of
@@ -350,10 +387,15 @@ __global__ void __launch_bounds__(kStreamVisThreads) k_stream_bp_visible(const S
     const uint32_t Yw = static_cast<uint32_t>(pw);
     const Round1Sweep rs = round1_sweep(static_cast<uint32_t>(pw >> 32) ^ a.rk[0] ^ t, a.rk);
     const uint32_t* tv = s_tab + kBpVisPlanes;
-    for (int base = warp * 32; base < nn; base += nwarp * 32) {
-        const int sx = base + lane;
-        const bool valid = sx < nn;
-        const int sd = valid ? sx : 0;
+    // spin sx of the tile: its J' bit hp, the bit-sliced count n4 of its four J incidences, Philox
+    // cell words and its index in s_o
+    struct Vis {
+        uint32_t hp, c2;
+        bp::Count4 n4;
+        Round2Cell r2;
+        int out;
+    };
+    auto visible_node = [&](int sd) {
         const int R = sd / nc, C = sd - R * nc;  // tile-local spin row and column
         const int x = 2 * (R & 1) + (C & 1);
         const uint32_t* hc = s_h + (((R >> 1) + 1) * HS + (C >> 1) + 1) * 10;  // own cell's words
@@ -361,25 +403,48 @@ __global__ void __launch_bounds__(kStreamVisThreads) k_stream_bp_visible(const S
             return hc[(v & 0xFFFF) - (HS + 1) * 10] ^ ((v >> 16) ? fl : 0u);
         };
         const uint32_t h0 = hin(s_inc[x][0], fl0), h1 = hin(s_inc[x][1], fl0), h2 = hin(s_inc[x][2], fl0),
-                       h3 = hin(s_inc[x][3], fl0), hp = hin(s_inc[x][4], fl1);
-        const bp::Count4 n4 = bp::count4(h0, h1, h2, h3);
+                       h3 = hin(s_inc[x][3], fl0);
         const uint32_t cell = static_cast<uint32_t>((i0 + (R >> 1)) * W + j0 + (C >> 1));
         const uint64_t pc = static_cast<uint64_t>(kPhiloxM0) * cell;
-        const Round2Cell r2 = round2_cell(rs.hik ^ static_cast<uint32_t>(pc));
-        const uint32_t c2 =
-            static_cast<uint32_t>(pc >> 32) ^ a.rk[1] ^ (kTagBitplane + 8u * (10u + static_cast<uint32_t>(x)));
-        uint32_t lt = 0u, eq = valid ? 0xffffffffu : 0u;
-        auto planes = [&](const U4& q, uint32_t j) {
-            const uint32_t u[4] = {q.x, q.y, q.z, q.w};
+        return Vis{hin(s_inc[x][4], fl1),
+                   static_cast<uint32_t>(pc >> 32) ^ a.rk[1] ^ (kTagBitplane + 8u * (10u + static_cast<uint32_t>(x))),
+                   bp::count4(h0, h1, h2, h3), round2_cell(rs.hik ^ static_cast<uint32_t>(pc)), R * VO + C};
+    };
+    auto planes = [&](const Vis& vn, const U4& q, uint32_t j, uint32_t& lt, uint32_t& eq) {
+        const uint32_t u[4] = {q.x, q.y, q.z, q.w};
 #pragma unroll
-            for (int i = 0; i < 4; ++i) bp::plane_step(u[i], bp::visible_plane(tv + 4u * j + i, hp, n4), lt, eq);
-        };
+        for (int i = 0; i < 4; ++i) bp::plane_step(u[i], bp::visible_plane(tv + 4u * j + i, vn.hp, vn.n4), lt, eq);
+    };
+    for (int base = warp * 32; base < nn; base += nwarp * 32) {
+        const int sx = base + lane;
+        const bool valid = sx < nn;
+        const Vis vn = visible_node(valid ? sx : 0);
+        uint32_t lt = 0u, eq = valid ? 0xffffffffu : 0u;
+        // calls 0 and 1 (a loop, so that the threshold planes are not held in registers across
+        // tiles), then the open spins to the straggler list
 #pragma unroll 1
-        for (uint32_t j = 0; j < 8u; ++j) {
+        for (uint32_t j = 0; j < 2u; ++j) planes(vn, philox_from_round2(Yw, rs, vn.r2, vn.c2 ^ j, a.rk), j, lt, eq);
+        if (bp::push_straggler(static_cast<uint32_t>(sx), eq, &s_nst, s_list, kCap, lane)) eq = 0u;
+#pragma unroll 1
+        for (uint32_t j = 2; j < 8u; ++j) {  // only where the list was full
             if (!__any_sync(0xffffffffu, eq != 0u)) break;
-            planes(philox_from_round2(Yw, rs, r2, c2 ^ j, a.rk), j);
+            planes(vn, philox_from_round2(Yw, rs, vn.r2, vn.c2 ^ j, a.rk), j, lt, eq);
         }
-        if (valid) s_o[R * VO + C] = lt;
+        if (valid) s_o[vn.out] = lt;  // final, or the decided part of a straggler
+    }
+    __syncthreads();
+    const int n_st = min(s_nst, kCap);
+    for (int base = warp * 32; base < n_st; base += nwarp * 32) {
+        const bool valid = base + lane < n_st;
+        const uint2 e = valid ? s_list[base + lane] : make_uint2(0u, 0u);
+        const Vis vn = visible_node(static_cast<int>(e.x));
+        uint32_t lt = s_o[vn.out], eq = e.y;
+#pragma unroll 1
+        for (uint32_t j = 2; j < 8u; ++j) {
+            if (!__any_sync(0xffffffffu, eq != 0u)) break;
+            planes(vn, philox_from_round2(Yw, rs, vn.r2, vn.c2 ^ j, a.rk), j, lt, eq);
+        }
+        if (valid) s_o[vn.out] = lt;
     }
     __syncthreads();
     for (int x = threadIdx.x; x < 2 * kTI * VO; x += blockDim.x) {

@@ -58,26 +58,45 @@ def test_single_rank_is_identity():
     assert bench.replica_seed(7, 0) == 7
 
 
+def _straggler_calls(first):
+    """Lane-calls of the straggler scheme for one half-step, given per node
+    and chain the first plane (0-based) at which the comparison is decided:
+    two calls per node, then the nodes needing more, 32 at a time, each group
+    drawing calls until its slowest node is decided."""
+    import numpy as np
+    need = np.minimum(8, (first.max(axis=1) + 1 + 3) // 4)   # calls each node needs
+    extra = need[need > 2] - 2
+    calls = 2 * len(need)
+    for b in range(0, len(extra), 32):
+        grp = extra[b:b + 32]
+        calls += len(grp) * int(grp.max())
+    return calls
+
+
+def _first_planes(u, t):
+    import numpy as np
+    diff = u ^ t                                   # the first differing bit decides
+    return np.where(diff == 0, 32, 31 - np.floor(np.log2(np.maximum(diff, 1))).astype(int))
+
+
 def test_bitplane_expected_calls_matches_a_simulation():
-    """The bit-plane roofline counts the expected Philox calls of the early
-    exit: per warp of up to 32 nodes x 32 chains, calls of four planes while
-    any comparison is open.  A direct simulation of that comparison (random
-    uniforms and thresholds, bits drawn plane by plane) must give the same
-    mean call count."""
+    """The bit-plane roofline counts the expected Philox calls of the
+    comparison as the kernels run it: two calls of four planes for every node,
+    then the nodes with an open comparison (any of their 32 chains) from a
+    straggler list, 32 at a time, each group drawing calls while any of its
+    comparisons is open.  A direct simulation (random uniforms and thresholds,
+    bits compared plane by plane) must give the same mean call count."""
     import numpy as np
     import bench
     rng = np.random.default_rng(3)
-    for lanes in (32, 10):
-        trials, calls = 4000, 0
+    for nodes, trials in ((32, 3000), (810, 300), (10, 3000)):
+        calls = 0
         for _ in range(trials):
-            u = rng.integers(0, 2**32, size=(lanes, 32), dtype=np.uint64)
-            t = rng.integers(0, 2**32, size=(lanes, 32), dtype=np.uint64)
-            diff = u ^ t                                   # first differing bit decides
-            first = np.where(diff == 0, 32, 31 - np.floor(np.log2(np.maximum(diff, 1))).astype(int))
-            planes = int(first.max()) + 1                  # planes until every comparison is decided
-            calls += min(8, (planes + 3) // 4)
-        expect = bench.bitplane_expected_calls(lanes) / lanes
-        assert abs(calls / trials - expect) < 0.03, (lanes, calls / trials, expect)
+            u = rng.integers(0, 2**32, size=(nodes, 32), dtype=np.uint64)
+            t = rng.integers(0, 2**32, size=(nodes, 32), dtype=np.uint64)
+            calls += _straggler_calls(_first_planes(u, t))
+        expect = bench.bitplane_expected_calls(nodes) / nodes
+        assert abs(calls / trials / nodes - expect) < 0.01, (nodes, calls / trials / nodes, expect)
 
 
 def test_bitplane_expected_calls_with_half_thresholds():
@@ -91,14 +110,11 @@ def test_bitplane_expected_calls_with_half_thresholds():
     import bench
     rng = np.random.default_rng(5)
     for f in (0.5, 0.9):
-        trials, calls = 4000, 0
+        trials, calls, nodes = 300, 0, 810
         for _ in range(trials):
-            u = rng.integers(0, 2**32, size=(32, 32), dtype=np.uint64)
-            t = rng.integers(0, 2**32, size=(32, 32), dtype=np.uint64)
-            t[rng.random((32, 32)) < f] = 2**31
-            diff = u ^ t
-            first = np.where(diff == 0, 32, 31 - np.floor(np.log2(np.maximum(diff, 1))).astype(int))
-            planes = int(first.max()) + 1
-            calls += min(8, max(2, (planes + 3) // 4))   # the hidden half-step draws two calls first
-        expect = bench.bitplane_expected_calls(32) / 32
-        assert abs(calls / trials - expect) < 0.03, (f, calls / trials, expect)
+            u = rng.integers(0, 2**32, size=(nodes, 32), dtype=np.uint64)
+            t = rng.integers(0, 2**32, size=(nodes, 32), dtype=np.uint64)
+            t[rng.random((nodes, 32)) < f] = 2**31
+            calls += _straggler_calls(_first_planes(u, t))
+        expect = bench.bitplane_expected_calls(nodes) / nodes
+        assert abs(calls / trials / nodes - expect) < 0.01, (f, calls / trials / nodes, expect)

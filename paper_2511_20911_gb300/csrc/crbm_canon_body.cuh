@@ -252,7 +252,7 @@ __device__ __forceinline__ void sweep_canon_body(const SweepArgs& a, int word, u
             if (do_swap && active) lc.lb = 4u * static_cast<uint32_t>(bos0[lane]);
         }
         if (!kCluster && a.sq_every > 0 && (t + 1u) % static_cast<uint32_t>(a.sq_every) == 0u) {
-            accumulate_correlations(a, s_v, s_seg, s_segmask, warp, nwarp, lane);
+            accumulate_correlations_any(a, s_v, s_w, s_seg, s_segmask, warp, nwarp, lane);  // s_w: dead here
             __syncthreads();
         }
     }

@@ -303,9 +303,9 @@ __device__ __forceinline__ void post_sweep_warp0(const SweepArgs& a, int* s_cnt,
 // walks the row pairs (R, R + dR): the word at (R, C) is a broadcast, the one
 // at (R + dR, C + dC) a conflict-free gather, and each XOR word is counted
 // for two segments at once.
-static __device__ __noinline__ void accumulate_correlations(const SweepArgs& a, const uint32_t* s_v,
-                                                        const int* s_seg, const uint32_t* s_segmask,
-                                                        int warp, int nwarp, int lane) {
+static __device__ __forceinline__ void accumulate_correlations_word(const SweepArgs& a, const uint32_t* s_v,
+                                                                    const int* s_seg, const uint32_t* s_segmask,
+                                                                    int warp, int nwarp, int lane) {
     const int L = a.g.L, N = a.g.N, nseg = s_seg[0];
     const int n_dr = L / 2 + 1;
     const int slices = max(1, min(L, (3 * nwarp + n_dr - 1) / n_dr));  // about three items per warp
@@ -392,6 +392,90 @@ static __device__ __noinline__ void accumulate_correlations(const SweepArgs& a, 
                 }
             }
         }
+    }
+}
+
+// The same correlations for a square lattice of even side kL <= 32, in
+// bit-transposed form: the lattice is first transposed so that lane l holds,
+// for every row R, the kL spins of chain l as a kL-bit mask (rows in
+// `scratch`, [kL][32] words of the caller's dead shared memory).  Work items
+// are (dR, slice of rows R); in an item lane l counts, for every column offset
+// dC, the sites at which row R of chain l and row R + dR rotated by dC differ
+// (the rotation is one funnel shift of the row written twice side by side),
+// and the counts of a parameter point's chains are summed by one warp
+// reduction over the point's lane mask.  Every thread of the CTA calls it.
+template <int kL>
+static __device__ __forceinline__ void accumulate_correlations_bits(const SweepArgs& a, const uint32_t* s_v,
+                                                             uint32_t* scratch, const int* s_seg,
+                                                             const uint32_t* s_segmask, int warp, int nwarp,
+                                                             int lane) {
+    static_assert(kL % 2 == 0 && kL >= 4 && kL <= 32, "even side up to 32");
+    constexpr int N = kL * kL, n_dr = kL / 2 + 1;
+    constexpr uint32_t kFull = kL == 32 ? 0xffffffffu : (1u << (kL % 32)) - 1u;
+    for (int R = warp; R < kL; R += nwarp) {
+        const uint32_t* row = s_v + R * kL;
+        uint32_t m = 0u;
+#pragma unroll
+        for (int C = 0; C < kL; ++C) m |= ((row[C] >> lane) & 1u) << C;
+        scratch[R * 32 + lane] = m;
+    }
+    // this lane's parameter point: its lane mask, index and whether it reports
+    const int nseg = s_seg[0];
+    uint32_t smask = 1u << lane;
+    int p = -1;
+    for (int s = 0; s < nseg; ++s)
+        if ((s_segmask[s] >> lane) & 1u) {
+            smask = s_segmask[s];
+            p = s_seg[1 + s] >> 8;
+        }
+    const bool leader = p >= 0 && (smask & ((1u << lane) - 1u)) == 0u;  // the point's lowest lane
+    const long long n_pt = __popc(smask);
+    unsigned long long* cp = reinterpret_cast<unsigned long long*>(a.corr) + static_cast<size_t>(p < 0 ? 0 : p) * N;
+    __syncthreads();
+    const int slices = max(1, min(kL, (nwarp + n_dr - 1) / n_dr));
+    const int n_items = n_dr * slices;
+    for (int item = warp; item < n_items; item += nwarp) {
+        const int dR = item / slices, sl = item - (item / slices) * slices;
+        const int R_begin = sl * kL / slices, R_end = (sl + 1) * kL / slices;
+        const bool mirror = dR > 0 && 2 * dR != kL;
+        uint32_t cnt[kL];
+#pragma unroll
+        for (int d = 0; d < kL; ++d) cnt[d] = 0u;
+        for (int R = R_begin; R < R_end; ++R) {
+            const int R2 = R + dR >= kL ? R + dR - kL : R + dR;
+            const uint32_t x = scratch[R * 32 + lane], y = scratch[R2 * 32 + lane];
+            const uint32_t lo = kL == 32 ? y : (y | (y << (kL % 32))), hi = kL == 32 ? y : (y >> ((32 - kL) % 32));
+#pragma unroll
+            for (int d = 0; d < kL; ++d) cnt[d] += __popc((x ^ __funnelshift_r(lo, hi, d)) & kFull);
+        }
+        const long long sites = static_cast<long long>(R_end - R_begin) * kL;
+#pragma unroll
+        for (int d = 0; d < kL; ++d) {
+            const uint32_t diff = __reduce_add_sync(smask, cnt[d]);
+            if (leader) {
+                const unsigned long long val = static_cast<unsigned long long>(n_pt * sites - 2LL * diff);
+                atomicAdd(cp + dR * kL + d, val);
+                if (mirror) atomicAdd(cp + (kL - dR) * kL + (d == 0 ? 0 : kL - d), val);
+            }
+        }
+    }
+}
+
+// Correlations of one word: the bit-transposed form for even square sides up
+// to 32 when the caller has scratch space, else the word-parallel one (one
+// call site in the sweep kernels, out of line: it runs every sq_every sweeps).
+static __device__ __noinline__ void accumulate_correlations_any(const SweepArgs& a, const uint32_t* s_v,
+                                                                   uint32_t* scratch, const int* s_seg,
+                                                                   const uint32_t* s_segmask, int warp, int nwarp,
+                                                                   int lane) {
+    switch (scratch ? a.g.L : 0) {
+#define CRBM_CORR_BITS(k) \
+    case k: accumulate_correlations_bits<k>(a, s_v, scratch, s_seg, s_segmask, warp, nwarp, lane); return;
+        CRBM_CORR_BITS(4) CRBM_CORR_BITS(6) CRBM_CORR_BITS(8) CRBM_CORR_BITS(10) CRBM_CORR_BITS(12)
+        CRBM_CORR_BITS(14) CRBM_CORR_BITS(16) CRBM_CORR_BITS(18) CRBM_CORR_BITS(20) CRBM_CORR_BITS(22)
+        CRBM_CORR_BITS(24) CRBM_CORR_BITS(26) CRBM_CORR_BITS(28) CRBM_CORR_BITS(30) CRBM_CORR_BITS(32)
+#undef CRBM_CORR_BITS
+        default: accumulate_correlations_word(a, s_v, s_seg, s_segmask, warp, nwarp, lane);
     }
 }
 

@@ -201,7 +201,7 @@ __device__ __forceinline__ void sweep_generic_body(const SweepArgs& a, int word)
             if (do_swap) lb = 4u * static_cast<uint32_t>(s_bos[lane]);
         }
         if (a.sq_every > 0 && (t + 1u) % static_cast<uint32_t>(a.sq_every) == 0u) {
-            accumulate_correlations(a, s_v, s_seg, s_segmask, warp, nwarp, lane);
+            accumulate_correlations_any(a, s_v, nullptr, s_seg, s_segmask, warp, nwarp, lane);
             __syncthreads();
         }
     }

@@ -136,12 +136,19 @@ def test_custom_filters_bitexact(orc, bonds):
                  periodic=periodic, bonds=bonds)
 
 
-@pytest.mark.parametrize("L", [8, 6, 9, 36])
-def test_structure_factor_matches_oracle(orc, L):
+@pytest.mark.parametrize("L,interleaved", [(8, False), (6, False), (9, False), (36, False), (4, False),
+                                           (18, False), (32, False), (18, True), (10, True)])
+def test_structure_factor_matches_oracle(orc, L, interleaved):
+    """S(q) against the oracle: even sides up to 32 take the bit-transposed
+    accumulation (lane = chain, one warp reduction per parameter point), odd
+    and larger sides the word-parallel one; interleaved parameter points give
+    lane masks that are not runs of lanes."""
     n = 70
-    rng = np.random.default_rng(8 + L)
+    rng = np.random.default_rng(8 + L + 100 * interleaved)
     params = workloads.random_params(rng, 3)
-    cp = np.sort(rng.integers(0, 3, n)).astype(np.int32)
+    cp = rng.integers(0, 3, n).astype(np.int32)
+    if not interleaved:
+        cp = np.sort(cp)
     s, _, _, osq = run_pair(orc, L, params, n, cp, 4, splits=[9, 12], measure_every=0,
                             sq_every=3)
     sq = s.structure_factor()

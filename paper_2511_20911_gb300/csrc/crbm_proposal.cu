@@ -572,108 +572,142 @@ __global__ void k_prop_extract(Geometry g, const uint32_t* v, const float* chain
 
 __device__ __forceinline__ float bf16r(float x) { return __bfloat162float(__float2bfloat16_rn(x)); }
 
-// Forward + backward of the mean binary cross-entropy, one example per
-// thread, fp32 arithmetic on bf16-rounded weights and activations (the
-// roundings pass gradients straight through).  grad and loss accumulate.
-__global__ void __launch_bounds__(128) k_prop_train(const float* __restrict__ w, const Example* ex, int n,
-                                                    float* grad, float* loss) {
-    const int e = blockIdx.x * blockDim.x + threadIdx.x;
-    if (e >= n) return;
-    const Example& x = ex[e];
-    float in[6][kP * kP];
-    for (int pos = 0; pos < kP * kP; ++pos) {
-        in[0][pos] = x.spin[pos];
-        in[1][pos] = x.inside[pos];
-        in[2][pos] = static_cast<float>((x.pr + pos / kP) & 1);
-        in[3][pos] = static_cast<float>((x.pc + pos % kP) & 1);
-        in[4][pos] = x.beta;
-        in[5][pos] = x.h;
+// Forward + backward of the mean binary cross-entropy in fp32 on
+// bf16-rounded weights and activations (the roundings pass gradients straight
+// through).  A CTA takes kTrainEx examples in turn, with the weights, its
+// gradient sums and one example's activations and deltas in shared memory;
+// within an example a thread takes output positions (forward, deltas) or
+// parameters (weight gradients), so every gradient sum has one owner thread
+// and the CTA adds its sums to grad with one atomic per parameter.  grad and
+// loss accumulate.
+constexpr int kTrainEx = 16, kTrainThreads = 128;
+__global__ void __launch_bounds__(kTrainThreads) k_prop_train(const float* __restrict__ w, const Example* ex, int n,
+                                                              float* grad, float* loss) {
+    __shared__ float sW[kNP], sG[kNP];
+    __shared__ float s_in[6][kP * kP], s_a1[16][kS1 * kS1], s_a2[16][kS2 * kS2];
+    __shared__ float s_d1[16][kS1 * kS1], s_d2[16][kS2 * kS2], s_dl[kK * kK];
+    __shared__ float s_loss;
+    const int tid = threadIdx.x;
+    for (int i = tid; i < kNP; i += kTrainThreads) {
+        sW[i] = w[i];
+        sG[i] = 0.f;
     }
-    float a1[16][kS1 * kS1], a2[16][kS2 * kS2];
-    for (int o = 0; o < 16; ++o)
-        for (int p = 0; p < kS1 * kS1; ++p) {
-            const int y = p / kS1, xx = p % kS1;
-            float acc = w[oB1 + o];
+    if (tid == 0) s_loss = 0.f;
+    const float inv = 1.f / (static_cast<float>(n) * kK * kK);
+    const int e_end = min(n, (blockIdx.x + 1) * kTrainEx);
+    for (int e = blockIdx.x * kTrainEx; e < e_end; ++e) {
+        const Example& x = ex[e];
+        __syncthreads();  // the previous example's buffers are free
+        for (int pos = tid; pos < kP * kP; pos += kTrainThreads) {
+            s_in[0][pos] = x.spin[pos];
+            s_in[1][pos] = x.inside[pos];
+            s_in[2][pos] = static_cast<float>((x.pr + pos / kP) & 1);
+            s_in[3][pos] = static_cast<float>((x.pc + pos % kP) & 1);
+            s_in[4][pos] = x.beta;
+            s_in[5][pos] = x.h;
+        }
+        __syncthreads();
+        for (int i = tid; i < 16 * kS1 * kS1; i += kTrainThreads) {  // layer 1
+            const int o = i / (kS1 * kS1), p = i % (kS1 * kS1), y = p / kS1, xx = p % kS1;
+            float acc = sW[oB1 + o];
             for (int c = 0; c < 6; ++c)
-                for (int t = 0; t < 9; ++t) acc += w[oW1 + (o * 6 + c) * 9 + t] * in[c][(y + t / 3) * kP + xx + t % 3];
-            a1[o][p] = bf16r(fmaxf(acc, 0.f));
+#pragma unroll
+                for (int t = 0; t < 9; ++t) acc += sW[oW1 + (o * 6 + c) * 9 + t] * s_in[c][(y + t / 3) * kP + xx + t % 3];
+            s_a1[o][p] = bf16r(fmaxf(acc, 0.f));
         }
-    for (int o = 0; o < 16; ++o)
-        for (int p = 0; p < kS2 * kS2; ++p) {
-            const int y = p / kS2, xx = p % kS2;
-            float acc = w[oB2 + o];
+        __syncthreads();
+        for (int i = tid; i < 16 * kS2 * kS2; i += kTrainThreads) {  // layer 2
+            const int o = i / (kS2 * kS2), p = i % (kS2 * kS2), y = p / kS2, xx = p % kS2;
+            float acc = sW[oB2 + o];
             for (int c = 0; c < 16; ++c)
-                for (int t = 0; t < 9; ++t) acc += w[oW2 + (o * 16 + c) * 9 + t] * a1[c][(y + t / 3) * kS1 + xx + t % 3];
-            a2[o][p] = bf16r(fmaxf(acc, 0.f));
+#pragma unroll
+                for (int t = 0; t < 9; ++t) acc += sW[oW2 + (o * 16 + c) * 9 + t] * s_a1[c][(y + t / 3) * kS1 + xx + t % 3];
+            s_a2[o][p] = bf16r(fmaxf(acc, 0.f));
         }
-    float lsum = 0.f, dl[kK * kK];
-    for (int p = 0; p < kK * kK; ++p) {
-        const int y = p / kK, xx = p % kK;
-        float acc = w[oB3];
-        for (int c = 0; c < 16; ++c)
-            for (int t = 0; t < 9; ++t) acc += w[oW3 + c * 9 + t] * a2[c][(y + t / 3) * kS2 + xx + t % 3];
-        const float yv = x.target[p] > 0 ? 1.f : 0.f;
-        lsum += (acc > 0.f ? acc + log1pf(__expf(-acc)) : log1pf(__expf(acc))) - yv * acc;
-        dl[p] = (1.f / (1.f + __expf(-acc)) - yv) / (static_cast<float>(n) * kK * kK);
-    }
-    atomicAdd(loss, lsum / (static_cast<float>(n) * kK * kK));
-    // layer 3
-    float d2[16][kS2 * kS2];
-    for (int c = 0; c < 16; ++c)
-        for (int p = 0; p < kS2 * kS2; ++p) d2[c][p] = 0.f;
-    float gb3 = 0.f;
-    for (int p = 0; p < kK * kK; ++p) gb3 += dl[p];
-    atomicAdd(&grad[oB3], gb3);
-    for (int c = 0; c < 16; ++c)
-        for (int t = 0; t < 9; ++t) {
-            float gsum = 0.f;
-            const float wv = w[oW3 + c * 9 + t];
-            for (int p = 0; p < kK * kK; ++p) {
-                const int q = (p / kK + t / 3) * kS2 + p % kK + t % 3;
-                gsum += dl[p] * a2[c][q];
-                d2[c][q] += dl[p] * wv;
+        __syncthreads();
+        if (tid < 32) {  // layer 3 and the loss: lanes 0 .. 15 take the block sites
+            float l = 0.f;
+            if (tid < kK * kK) {
+                const int y = tid / kK, xx = tid % kK;
+                float acc = sW[oB3];
+                for (int c = 0; c < 16; ++c)
+#pragma unroll
+                    for (int t = 0; t < 9; ++t) acc += sW[oW3 + c * 9 + t] * s_a2[c][(y + t / 3) * kS2 + xx + t % 3];
+                const float yv = x.target[tid] > 0 ? 1.f : 0.f;
+                l = (acc > 0.f ? acc + log1pf(__expf(-acc)) : log1pf(__expf(acc))) - yv * acc;
+                s_dl[tid] = (1.f / (1.f + __expf(-acc)) - yv) * inv;
             }
-            atomicAdd(&grad[oW3 + c * 9 + t], gsum);
+#pragma unroll
+            for (int o = 16; o > 0; o >>= 1) l += __shfl_xor_sync(0xffffffffu, l, o);
+            if (tid == 0) s_loss += l;
         }
-    for (int c = 0; c < 16; ++c)
-        for (int p = 0; p < kS2 * kS2; ++p)
-            if (!(a2[c][p] > 0.f)) d2[c][p] = 0.f;
-    // layer 2
-    float d1[16][kS1 * kS1];
-    for (int c = 0; c < 16; ++c)
-        for (int p = 0; p < kS1 * kS1; ++p) d1[c][p] = 0.f;
-    for (int o = 0; o < 16; ++o) {
-        float gb = 0.f;
-        for (int p = 0; p < kS2 * kS2; ++p) gb += d2[o][p];
-        atomicAdd(&grad[oB2 + o], gb);
-        for (int c = 0; c < 16; ++c)
+        __syncthreads();
+        // layer 3: weight gradients and the deltas of layer 2's outputs (zero where ReLU was off)
+        for (int i = tid; i < 16 * 9; i += kTrainThreads) {
+            const int c = i / 9, t = i % 9;
+            float g = 0.f;
+#pragma unroll
+            for (int p = 0; p < kK * kK; ++p) g += s_dl[p] * s_a2[c][(p / kK + t / 3) * kS2 + p % kK + t % 3];
+            sG[oW3 + i] += g;
+        }
+        if (tid == 0) {
+            float g = 0.f;
+            for (int p = 0; p < kK * kK; ++p) g += s_dl[p];
+            sG[oB3] += g;
+        }
+        for (int i = tid; i < 16 * kS2 * kS2; i += kTrainThreads) {
+            const int c = i / (kS2 * kS2), q = i % (kS2 * kS2), qy = q / kS2, qx = q % kS2;
+            float d = 0.f;
+#pragma unroll
             for (int t = 0; t < 9; ++t) {
-                float gsum = 0.f;
-                const float wv = w[oW2 + (o * 16 + c) * 9 + t];
-                for (int p = 0; p < kS2 * kS2; ++p) {
-                    const int q = (p / kS2 + t / 3) * kS1 + p % kS2 + t % 3;
-                    gsum += d2[o][p] * a1[c][q];
-                    d1[c][q] += d2[o][p] * wv;
-                }
-                atomicAdd(&grad[oW2 + (o * 16 + c) * 9 + t], gsum);
+                const int py = qy - t / 3, px = qx - t % 3;
+                if (py >= 0 && py < kK && px >= 0 && px < kK) d += s_dl[py * kK + px] * sW[oW3 + c * 9 + t];
             }
-    }
-    for (int c = 0; c < 16; ++c)
-        for (int p = 0; p < kS1 * kS1; ++p)
-            if (!(a1[c][p] > 0.f)) d1[c][p] = 0.f;
-    // layer 1
-    for (int o = 0; o < 16; ++o) {
-        float gb = 0.f;
-        for (int p = 0; p < kS1 * kS1; ++p) gb += d1[o][p];
-        atomicAdd(&grad[oB1 + o], gb);
-        for (int c = 0; c < 6; ++c)
+            s_d2[c][q] = s_a2[c][q] > 0.f ? d : 0.f;
+        }
+        __syncthreads();
+        // layer 2: weight and bias gradients, the deltas of layer 1's outputs
+        for (int i = tid; i < 16 * 16 * 9; i += kTrainThreads) {
+            const int o = i / 144, c = (i / 9) % 16, t = i % 9;
+            float g = 0.f;
+#pragma unroll 4
+            for (int p = 0; p < kS2 * kS2; ++p) g += s_d2[o][p] * s_a1[c][(p / kS2 + t / 3) * kS1 + p % kS2 + t % 3];
+            sG[oW2 + i] += g;
+        }
+        if (tid < 16) {
+            float g = 0.f;
+            for (int p = 0; p < kS2 * kS2; ++p) g += s_d2[tid][p];
+            sG[oB2 + tid] += g;
+        }
+        for (int i = tid; i < 16 * kS1 * kS1; i += kTrainThreads) {
+            const int c = i / (kS1 * kS1), q = i % (kS1 * kS1), qy = q / kS1, qx = q % kS1;
+            float d = 0.f;
+#pragma unroll
             for (int t = 0; t < 9; ++t) {
-                float gsum = 0.f;
-                for (int p = 0; p < kS1 * kS1; ++p)
-                    gsum += d1[o][p] * in[c][(p / kS1 + t / 3) * kP + p % kS1 + t % 3];
-                atomicAdd(&grad[oW1 + (o * 6 + c) * 9 + t], gsum);
+                const int py = qy - t / 3, px = qx - t % 3;
+                if (py >= 0 && py < kS2 && px >= 0 && px < kS2)
+                    for (int o = 0; o < 16; ++o) d += s_d2[o][py * kS2 + px] * sW[oW2 + (o * 16 + c) * 9 + t];
             }
+            s_d1[c][q] = s_a1[c][q] > 0.f ? d : 0.f;
+        }
+        __syncthreads();
+        // layer 1: weight and bias gradients
+        for (int i = tid; i < 16 * 6 * 9; i += kTrainThreads) {
+            const int o = i / 54, c = (i / 9) % 6, t = i % 9;
+            float g = 0.f;
+#pragma unroll 4
+            for (int p = 0; p < kS1 * kS1; ++p) g += s_d1[o][p] * s_in[c][(p / kS1 + t / 3) * kP + p % kS1 + t % 3];
+            sG[oW1 + i] += g;
+        }
+        if (tid < 16) {
+            float g = 0.f;
+            for (int p = 0; p < kS1 * kS1; ++p) g += s_d1[tid][p];
+            sG[oB1 + tid] += g;
+        }
     }
+    __syncthreads();
+    for (int i = tid; i < kNP; i += kTrainThreads) atomicAdd(&grad[i], sG[i]);
+    if (tid == 0) atomicAdd(loss, s_loss * inv);
 }
 
 // Adam (Kingma & Ba) on the fp32 master weights; also refreshes the
@@ -1008,7 +1042,8 @@ int crbm_proposal_loss_grad(crbm_proposal* p, const int8_t* spins, int32_t L, co
     if (e == cudaSuccess) e = cudaMemset(p->grad, 0, kNP * 4);
     if (e == cudaSuccess) e = cudaMemset(p->loss, 0, 4);
     if (e == cudaSuccess) {
-        crbm::k_prop_train<<<(n + 127) / 128, 128>>>(p->wb, p->ex, n, p->grad, p->loss);
+        crbm::k_prop_train<<<(n + crbm::kTrainEx - 1) / crbm::kTrainEx, crbm::kTrainThreads>>>(p->wb, p->ex, n,
+                                                                                              p->grad, p->loss);
         e = cudaGetLastError();
     }
     if (e == cudaSuccess) e = cudaMemcpy(grad, p->grad, kNP * 4, cudaMemcpyDeviceToHost);
@@ -1035,7 +1070,8 @@ int crbm_proposal_train(crbm_proposal* p, crbm_ctx* ctx, int32_t steps, int32_t 
         if (e == cudaSuccess) e = cudaMemsetAsync(p->grad, 0, kNP * 4, st);
         if (e == cudaSuccess) e = cudaMemsetAsync(p->loss, 0, 4, st);
         if (e == cudaSuccess) {
-            crbm::k_prop_train<<<(batch + 127) / 128, 128, 0, st>>>(p->wb, p->ex, batch, p->grad, p->loss);
+            crbm::k_prop_train<<<(batch + crbm::kTrainEx - 1) / crbm::kTrainEx, crbm::kTrainThreads, 0, st>>>(
+                p->wb, p->ex, batch, p->grad, p->loss);
             e = cudaGetLastError();
         }
         ++p->adam_t;

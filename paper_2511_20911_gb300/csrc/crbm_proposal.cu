@@ -208,7 +208,9 @@ __global__ void __launch_bounds__(kCtaThreads, kCtasPerSm) k_prop_pass(const __g
     uint32_t* tslot = reinterpret_cast<uint32_t*>(smem_all + kSmG0 + kGroups * kSmGroup);
     __shared__ int s_fail[kGroups];
     __shared__ unsigned long long s_stats[2];  // proposed, accepted by this CTA
-    // the block's logits in X after layer 3 ([site][chain], 16 chains)
+    // the block's logits in X after layer 3: site s of chain c at (s & 1) * 256 + 8 c + (s >> 1), so
+    // that the Metropolis-Hastings lanes (chain c, part p: sites 2 p, 2 p + 1) read them without
+    // bank conflicts
     float* logit = reinterpret_cast<float*>(X);
 
     // set-up: the tensor memory first (a CTA of a kernel that allocates tensor memory starts only
@@ -392,7 +394,8 @@ __global__ void __launch_bounds__(kCtaThreads, kCtasPerSm) k_prop_pass(const __g
             umma::tmem_ld_wait();
             if (my_y < kK) {
 #pragma unroll
-                for (int x = 0; x < kK; ++x) logit[(my_y * kK + x) * 16 + my_c] = __uint_as_float(r[x]) + b3;
+                for (int x = 0; x < kK; ++x)
+                    logit[(x & 1) * 256 + 8 * my_c + (my_y * kK + x) / 2] = __uint_as_float(r[x]) + b3;
             }
         }
         umma::fence_before_sync();
@@ -424,7 +427,7 @@ __global__ void __launch_bounds__(kCtaThreads, kCtasPerSm) k_prop_pass(const __g
                 const int s = 2 * part + j;
                 const int ar = s / kK, ac = s % kK;
                 const bool xc = (pw[(3 + ar) * kP + 3 + ac] >> cbit) & 1u;
-                const float lg = logit[s * 16 + c];
+                const float lg = logit[j * 256 + 8 * c + part];
                 const float q = __fdividef(1.f, 1.f + __expf(-lg));
                 float tf = q * 4294967296.f;
                 tf = fminf(fmaxf(tf, 1.f), 4294967040.f);

@@ -13,14 +13,15 @@
 // energy halo and the moves of a pass commute.
 //
 // The pass runs the three convolutions on the tcgen05 tensor cores (bf16
-// operands from shared memory, fp32 accumulators in tensor memory): one
-// persistent CTA per SM holds four independent groups of four warps, each
-// group working through its own work items = (block of the pass, 16 chains
-// of a packed word) with its own shared-memory buffers, mbarrier, named
-// barrier and 128 of the SM's 512 tensor-memory columns (one CTA, so the
-// tensor memory is allocated once and the B operands staged once per SM).  Activations live in an 8 x 8 frame per
-// chain, stored as "column planes": plane (x, h) holds channels 8h .. 8h + 7
-// of frame column x for the 128 rows (chain, frame row y), 16 bytes a row.
+// operands from shared memory, fp32 accumulators in tensor memory).  Four
+// independent groups of four warps run on each SM, each working through its
+// own work items = (block of the pass, 16 chains of a packed word) with its
+// own shared-memory buffers, mbarrier, named barrier and 128 of the SM's 512
+// tensor-memory columns; kGroups of them share a persistent CTA (one group
+// per CTA measured fastest: four CTAs per SM).  Activations live in an 8 x 8
+// frame per chain, stored as "column planes": plane (x, h) holds channels
+// 8h .. 8h + 7 of frame column x for the 128 rows (chain, frame row y), 16
+// bytes a row.
 //  * layer 1 acts on the spin plane alone (its five constant planes are folded
 //    into per-position constants added in its epilogue, and b1 + beta w_beta
 //    + h w_h enter through constant K columns): one K = 16 MMA per frame
@@ -193,8 +194,8 @@ __device__ __forceinline__ void group_sync(int g) {
     asm volatile("bar.sync %0, %1;" ::"r"(1 + g), "n"(kPassThreads) : "memory");
 }
 
-// One pass of MH block moves; one persistent CTA per SM, whose four groups
-// of four warps take items (block b, half-word hw) in turn.
+// One pass of MH block moves; persistent CTAs of kGroups groups of four
+// warps, each group taking items (block b, half-word hw) in turn.
 __global__ void __launch_bounds__(kCtaThreads, kCtasPerSm) k_prop_pass(const __grid_constant__ PassArgs a) {
     extern __shared__ __align__(1024) uint8_t smem_all[];
     const int L = a.g.L, N = a.g.N;

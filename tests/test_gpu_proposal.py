@@ -125,6 +125,58 @@ def test_pass_matches_the_oracle_element_wise(orc, L, n):
     assert np.array_equal(got[outside], spins[outside])
 
 
+@pytest.mark.parametrize("L,n_orc", [(18, 4096), (48, 4096)])
+def test_pass_full_size(orc, L, n_orc):
+    """The pass at the bench's full size and launch configuration (4096
+    chains at the evaluation points J'/J = 1, h = 3, beta in {1.5, 2, 3}; the
+    persistent grid of the bench) against the oracle's pass on the first
+    n_orc chains (all of them): block origins, current blocks, the proposed
+    blocks (with the GPU's thresholds) and dE exactly, logits and log alpha
+    within tolerance, and after the pass runs every block whose accept test is
+    clear of its boundary."""
+    ew = workloads.proposal_eval_workload(L)
+    s = crbm.Sampler(**dict(ew, measure_every=0))
+    s.sweep(20)
+    p = crbm.Proposal(seed=1)
+    w = orc.random_net(5, scale=0.15)
+    p.weights = w
+    g = p.inspect(s)                                                   # [word][block][lane]
+    g = g.transpose(1, 0, 2).reshape(g.shape[1], -1)[:, :n_orc]        # [block][chain]
+    spins = np.ascontiguousarray(s.get_spins()[:n_orc])
+    params, cp, seed = ew["params"], ew["chain_param"][:n_orc], ew["seed"]
+    assert len(set(cp.tolist())) >= 2
+    o_net = orc.prop_pass(spins.copy(), params, cp, w, seed, 0)
+    for f in ("bR", "bC", "cur_bits"):
+        assert np.array_equal(g[f].astype(np.int64), o_net[f].astype(np.int64)), f
+    err = np.abs(g["logit"] - o_net["logit"]) / (0.05 + 0.02 * np.abs(o_net["logit"]))
+    assert err.max() <= 1.0, err.max()
+    o_thr = orc.prop_pass(spins.copy(), params, cp, None, seed, 0,
+                          logits=g["logit"].astype(np.float64), thr=g["thr"])
+    assert np.array_equal(g["new_bits"], o_thr["new_bits"])
+    assert np.array_equal(g["dE"].astype(np.int64), o_thr["dE"])
+    la_err = np.abs(g["log_alpha"] - o_thr["log_alpha"])
+    assert (la_err <= 2e-4 + 1e-5 * np.abs(o_thr["log_alpha"])).all(), la_err.max()
+    after = spins.copy()
+    orc.prop_pass(after, params, cp, None, seed, 0, apply=True,
+                  logits=g["logit"].astype(np.float64), thr=g["thr"])
+    p.passes(s, 1)
+    got = s.get_spins()[:n_orc]
+    la, lu = o_thr["log_alpha"], np.log(o_thr["u_accept"])
+    clear = (la > 1e-3) | (np.abs(la - lu) > 1e-3)
+    assert clear.mean() > 0.99 and 0 < o_thr["accept"].mean() < 1
+    for b in range(g.shape[0]):
+        r = o_thr[b, 0]
+        rows = (int(r["bR"]) + np.arange(16) // 4) % L
+        cols = (int(r["bC"]) + np.arange(16) % 4) % L
+        blk_got, blk_after, blk_before = got[:, rows, cols], after[:, rows, cols], spins[:, rows, cols]
+        same_after = (blk_got == blk_after).all(1)
+        assert same_after[clear[b]].all(), b
+        assert (same_after | (blk_got == blk_before).all(1)).all(), b
+        got[:, rows, cols] = 0
+        after[:, rows, cols] = 0
+    assert np.array_equal(got, after)  # nothing outside the blocks moved
+
+
 def test_training_gradient_matches_oracle(orc):
     rng = np.random.default_rng(4)
     L, n = 12, 24

@@ -136,8 +136,9 @@ typedef struct {
      * columns too, CRBM_BC_PERIODIC (1) or CRBM_BC_OPEN (2) sets the column
      * axis on its own (`periodic` then covers the rows).  Windows (i, j),
      * i < (L+1)/2, j < (L_cols+1)/2, cell index i (L_cols+1)/2 + j; spins
-     * [chain][row][column].  A lattice other than L x L periodic with L even
-     * runs on the generic SMEM sweep. */
+     * [chain][row][column].  Even sides periodic along both axes run on the
+     * SS fast path (SMEM or streamed layout); any other lattice on the
+     * generic SMEM sweep. */
     int32_t L_cols;
     int32_t periodic_cols;
     /* Field of the odd columns (the appendix's separate odd- and even-column

@@ -363,10 +363,6 @@ int crbm_create(crbm_ctx** out, const crbm_params* p) {
         return fail(nullptr, CRBM_EUNSUPPORTED,
                     "the streamed layout serves the ten SS filters on an even, periodic lattice");
     }
-    if (ctx->layout == CRBM_LAYOUT_STREAM && g.Lc != g.L) {
-        delete ctx;
-        return fail(nullptr, CRBM_EUNSUPPORTED, "the streamed layout serves square lattices");
-    }
     if (ctx->layout == CRBM_LAYOUT_STREAM && p->sq_every > 0) {
         delete ctx;
         return fail(nullptr, CRBM_EUNSUPPORTED, "spin correlations are accumulated in the SMEM layout only");

@@ -1,5 +1,5 @@
 // Streamed sweep for lattices too large for shared memory (canonical SS
-// filters, even periodic L): spins and hidden units live in HBM and one sweep
+// filters, even periodic L x Lc): spins and hidden units live in HBM and one sweep
 // is two launches, the hidden half-step (Eq. 9) then the visible half-step
 // (Eq. 10).  Spins are stored as 64-chain words, two 32-bit halves per site
 // ([group][site][2]); a CTA works on one 32-chain half and one tile of cells,
@@ -40,13 +40,14 @@ __device__ __forceinline__ size_t vidx(int w, int N, int s) {
 
 // Stage spin rows 2 i0 .. 2 i0 + 2 TI and columns 2 j0 .. 2 j0 + 2 TJ
 // (wrapped) of half-word w into s_v[(2 TI + 1)][(2 TJ + 1)].  Every load of a
-// thread is issued before its first shared store.  kOneWrap: L >= 2 TJ, so
-// 2 i0 + r <= L + 30 needs at most one subtraction of L.
+// thread is issued before its first shared store.  kOneWrap: L >= 2 TI and
+// Lc >= 2 TJ, so 2 i0 + r <= L + 30 (2 j0 + c <= Lc + 30) needs at most one
+// subtraction of L (Lc).
 template <bool kOneWrap>
 __device__ __forceinline__ void stage_spin_tile(const SweepArgs& a, int w, int i0, int j0, uint32_t* s_v) {
     constexpr int VS = 2 * kTJ + 1, NV = (2 * kTI + 1) * VS;
     constexpr int IT = (NV + kStreamThreads - 1) / kStreamThreads;
-    const int L = a.g.L;
+    const int L = a.g.L, Lc = a.g.Lc;
     const uint32_t* vw = a.v + vidx(w, a.g.N, 0);  // site s of half-word w at vw[2 s]
     uint32_t val[IT];
 #pragma unroll
@@ -56,13 +57,13 @@ __device__ __forceinline__ void stage_spin_tile(const SweepArgs& a, int w, int i
         int R = 2 * i0 + r, C = 2 * j0 + c;
         if (kOneWrap) {
             R -= R >= L ? L : 0;
-            C -= C >= L ? L : 0;
+            C -= C >= Lc ? Lc : 0;
         } else {
             R %= L;
-            C %= L;
+            C %= Lc;
         }
         val[k] = 0u;
-        if (x < NV) val[k] = vw[2 * (R * L + C)];
+        if (x < NV) val[k] = vw[2 * (R * Lc + C)];
     }
 #pragma unroll
     for (int k = 0; k < IT; ++k) {
@@ -72,7 +73,7 @@ __device__ __forceinline__ void stage_spin_tile(const SweepArgs& a, int w, int i
 }
 
 __device__ __forceinline__ void stage_spin_tile(const SweepArgs& a, int w, int i0, int j0, uint32_t* s_v) {
-    if (a.g.L >= 2 * kTJ)
+    if (a.g.L >= 2 * kTI && a.g.Lc >= 2 * kTJ)
         stage_spin_tile<true>(a, w, i0, j0, s_v);
     else
         stage_spin_tile<false>(a, w, i0, j0, s_v);
@@ -81,14 +82,14 @@ __device__ __forceinline__ void stage_spin_tile(const SweepArgs& a, int w, int i
 // Stage the hidden words of cells i0 - 1 .. i0 + TI - 1 x j0 - 1 .. j0 + TJ - 1
 // (wrapped) of half-word w into s_h[(TI + 1)][(TJ + 1)][32], 16 bytes per
 // load, in batches whose loads are all issued before their stores.
-// kOneWrap: W > TI, so i0 - 1 + li in [-1, W + TI - 2] wraps with one add or
-// subtraction of W.
+// kOneWrap: W > TI and Wc > TJ, so i0 - 1 + li in [-1, W + TI - 2] (and the
+// same for columns) wraps with one add or subtraction of W (Wc).
 template <bool kOneWrap>
 __device__ __forceinline__ void stage_hidden_halo(const SweepArgs& a, int w, int i0, int j0, uint32_t* s_h) {
     constexpr int HS = kTJ + 1, NQ = (kTI + 1) * HS * 8;  // 8 uint4 per cell
     constexpr int IT = (NQ + kStreamVisThreads - 1) / kStreamVisThreads;
     constexpr int B = 5;  // loads in flight per thread
-    const int W = a.g.W;
+    const int W = a.g.W, Wc = a.g.Wc;
     const uint4* hw = reinterpret_cast<const uint4*>(a.h + static_cast<size_t>(w) * a.g.n_cells * 32);
 #pragma unroll
     for (int k0 = 0; k0 < IT; k0 += B) {
@@ -102,14 +103,14 @@ __device__ __forceinline__ void stage_hidden_halo(const SweepArgs& a, int w, int
             if (kOneWrap) {
                 gi += gi < 0 ? W : 0;
                 gi -= gi >= W ? W : 0;
-                gj += gj < 0 ? W : 0;
-                gj -= gj >= W ? W : 0;
+                gj += gj < 0 ? Wc : 0;
+                gj -= gj >= Wc ? Wc : 0;
             } else {
                 gi = (gi % W + W) % W;
-                gj = (gj % W + W) % W;
+                gj = (gj % Wc + Wc) % Wc;
             }
             val[k] = make_uint4(0u, 0u, 0u, 0u);
-            if (k0 + k < IT && x < NQ) val[k] = hw[(gi * W + gj) * 8 + q];
+            if (k0 + k < IT && x < NQ) val[k] = hw[(gi * Wc + gj) * 8 + q];
         }
 #pragma unroll
         for (int k = 0; k < B; ++k) {
@@ -129,9 +130,9 @@ __global__ void __launch_bounds__(kStreamThreads, CRBM_STREAM_MIN_BLOCKS) k_stre
     __shared__ __align__(16) uint32_t s_h[kTI * kTJ * 32];
     __shared__ uint4 s_q[kTI * kTJ][2];  // per tile cell: hidden_call_words
     const Geometry& g = a.g;
-    const int W = g.W;
+    const int W = g.W, Wc = g.Wc;
     const int w = blockIdx.y;
-    const int tiles_j = (W + kTJ - 1) / kTJ;
+    const int tiles_j = (Wc + kTJ - 1) / kTJ;
     const int i0 = (blockIdx.x / tiles_j) * kTI, j0 = (blockIdx.x % tiles_j) * kTJ;
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nwarp = blockDim.x >> 5;
     const uint32_t* gt = a.ctab + static_cast<size_t>(w) * kCanonTab;
@@ -142,12 +143,12 @@ __global__ void __launch_bounds__(kStreamThreads, CRBM_STREAM_MIN_BLOCKS) k_stre
     const LaneConst lc = lane_const(lane, lane);
     const Round0Lane r0l = round0_lane(chain);
     const Round1Sweep rs = round1_sweep(r0l.hi ^ t ^ a.rk[0], a.rk);
-    const int ni = min(kTI, W - i0), nj = min(kTJ, W - j0);
+    const int ni = min(kTI, W - i0), nj = min(kTJ, Wc - j0);
     // the warp-uniform Philox words of each cell, once per CTA instead of once per warp-cell
     for (int x = threadIdx.x; x < kTI * kTJ; x += blockDim.x) {
         const int li = x / kTJ, lj = x - li * kTJ;
         if (li < ni && lj < nj)
-            hidden_call_words(static_cast<uint32_t>((i0 + li) * W + j0 + lj), a.rk, s_q[x][0], s_q[x][1]);
+            hidden_call_words(static_cast<uint32_t>((i0 + li) * Wc + j0 + lj), a.rk, s_q[x][0], s_q[x][1]);
     }
     __syncthreads();
     // warp = columns lj of the tile, cells walked down the column
@@ -164,7 +165,7 @@ __global__ void __launch_bounds__(kStreamThreads, CRBM_STREAM_MIN_BLOCKS) k_stre
     for (int x = threadIdx.x; x < kTI * kTJ * 8; x += blockDim.x) {
         const int li = x / (kTJ * 8), rest = x - li * (kTJ * 8);
         if (li >= ni || rest >= nj * 8) continue;
-        reinterpret_cast<uint4*>(a.h + (static_cast<size_t>(w) * g.n_cells + (i0 + li) * W + j0) * 32)[rest] =
+        reinterpret_cast<uint4*>(a.h + (static_cast<size_t>(w) * g.n_cells + (i0 + li) * Wc + j0) * 32)[rest] =
             reinterpret_cast<const uint4*>(s_h)[x];
     }
 }
@@ -178,15 +179,15 @@ __global__ void __launch_bounds__(kStreamVisThreads, CRBM_STREAM_VIS_MIN_BLOCKS)
     __shared__ uint32_t s_o[2 * kTI * 2 * kTJ];
     __shared__ uint4 s_q[kTI * kTJ];  // per tile cell: visible_call_words
     const Geometry& g = a.g;
-    const int L = g.L, W = g.W, N = g.N;
+    const int L = g.L, Lc = g.Lc, W = g.W, Wc = g.Wc, N = g.N;
     const int w = blockIdx.y;
-    const int tiles_j = (W + kTJ - 1) / kTJ;
+    const int tiles_j = (Wc + kTJ - 1) / kTJ;
     const int i0 = (blockIdx.x / tiles_j) * kTI, j0 = (blockIdx.x % tiles_j) * kTJ;
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nwarp = blockDim.x >> 5;
     const uint4* gt = reinterpret_cast<const uint4*>(a.ctab + static_cast<size_t>(w) * kCanonTab + kCanonTh);
     for (int x = threadIdx.x; x < 4 * 32 * 32 / 4; x += blockDim.x) reinterpret_cast<uint4*>(s_tv)[x] = gt[x];
     constexpr int HS = kTJ + 1;
-    if (W > kTI)
+    if (W > kTI && Wc > kTJ)
         stage_hidden_halo<true>(a, w, i0, j0, s_h);
     else
         stage_hidden_halo<false>(a, w, i0, j0, s_h);
@@ -195,11 +196,11 @@ __global__ void __launch_bounds__(kStreamVisThreads, CRBM_STREAM_VIS_MIN_BLOCKS)
     const Round0Lane r0l = round0_lane(chain);
     const Round1Sweep rs = round1_sweep(r0l.hi ^ t ^ a.rk[0], a.rk);
     constexpr int VO = 2 * kTJ;
-    const int ni = min(kTI, W - i0), nj = min(kTJ, W - j0);
+    const int ni = min(kTI, W - i0), nj = min(kTJ, Wc - j0);
     for (int x = threadIdx.x; x < kTI * kTJ; x += blockDim.x) {
         const int li = x / kTJ, lj = x - li * kTJ;
         if (li < ni && lj < nj) {
-            const uint32_t cell = static_cast<uint32_t>((i0 + li) * W + j0 + lj);
+            const uint32_t cell = static_cast<uint32_t>((i0 + li) * Wc + j0 + lj);
             s_q[x] = kPaper ? visible_call_words_paper(cell, a.rk) : visible_call_words(cell, a.rk);
         }
     }
@@ -219,8 +220,8 @@ __global__ void __launch_bounds__(kStreamVisThreads, CRBM_STREAM_VIS_MIN_BLOCKS)
     for (int x = threadIdx.x; x < 2 * kTI * VO; x += blockDim.x) {
         const int r = x / VO, c = x - (x / VO) * VO;
         const int R = 2 * i0 + r, C = 2 * j0 + c;
-        if (R >= L || C >= L) continue;
-        a.v[vidx(w, N, R * L + C)] = s_o[x];
+        if (R >= L || C >= Lc) continue;
+        a.v[vidx(w, N, R * Lc + C)] = s_o[x];
     }
 }
 
@@ -241,9 +242,9 @@ __global__ void __launch_bounds__(kStreamThreads) k_stream_bp_hidden(const Sweep
     __shared__ int s_off[2][10];  // the filters' endpoint offsets in the staged tile
     __shared__ int s_nst;
     const Geometry& g = a.g;
-    const int W = g.W;
+    const int W = g.W, Wc = g.Wc;
     const int w = blockIdx.y;
-    const int tiles_j = (W + kTJ - 1) / kTJ;
+    const int tiles_j = (Wc + kTJ - 1) / kTJ;
     const int i0 = (blockIdx.x / tiles_j) * kTI, j0 = (blockIdx.x % tiles_j) * kTJ;
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nwarp = blockDim.x >> 5;
     constexpr int VS = 2 * kTJ + 1;
@@ -258,7 +259,7 @@ __global__ void __launch_bounds__(kStreamThreads) k_stream_bp_hidden(const Sweep
     stage_spin_tile(a, w, i0, j0, s_v);
     __syncthreads();
     const uint32_t fl0 = s_tab[kBpFlip], fl1 = s_tab[kBpFlip + 1];
-    const int ni = min(kTI, W - i0), nj = min(kTJ, W - j0), nn = ni * nj * 10;
+    const int ni = min(kTI, W - i0), nj = min(kTJ, Wc - j0), nn = ni * nj * 10;
     const uint64_t pw = static_cast<uint64_t>(kPhiloxM1) * static_cast<uint32_t>(w);
     const uint32_t Yw = static_cast<uint32_t>(pw);
     const Round1Sweep rs = round1_sweep(static_cast<uint32_t>(pw >> 32) ^ a.rk[0] ^ t, a.rk);
@@ -277,7 +278,7 @@ __global__ void __launch_bounds__(kStreamThreads) k_stream_bp_hidden(const Sweep
         const uint32_t* v = s_v + 2 * li * VS + 2 * lj;
         const uint32_t e1 = v[s_off[0][k]];
         const uint32_t e2 = v[s_off[1][k]] ^ (cls ? fl1 : fl0);
-        const uint32_t cell = static_cast<uint32_t>((i0 + li) * W + j0 + lj);
+        const uint32_t cell = static_cast<uint32_t>((i0 + li) * Wc + j0 + lj);
         const uint64_t pc = static_cast<uint64_t>(kPhiloxM0) * cell;
         return Hid{e1 & e2, ~(e1 | e2), e1 ^ e2,
                    static_cast<uint32_t>(pc >> 32) ^ a.rk[1] ^ (kTagBitplane + 8u * static_cast<uint32_t>(k)),
@@ -325,7 +326,7 @@ __global__ void __launch_bounds__(kStreamThreads) k_stream_bp_hidden(const Sweep
     for (int x = threadIdx.x; x < kTI * kTJ * 10; x += blockDim.x) {
         const int li = x / (kTJ * 10), rest = x - li * (kTJ * 10);
         if (li >= ni || rest >= nj * 10) continue;
-        a.h[(static_cast<size_t>(w) * g.n_cells + (i0 + li) * W + j0) * 10 + rest] = s_h[x];
+        a.h[(static_cast<size_t>(w) * g.n_cells + (i0 + li) * Wc + j0) * 10 + rest] = s_h[x];
     }
 }
 
@@ -341,9 +342,9 @@ __global__ void __launch_bounds__(kStreamVisThreads, CRBM_STREAM_MIN_BLOCKS) k_s
     __shared__ int s_inc[4][5];  // per spin class x: hidden word offset (cell row, column, filter) | flags
     __shared__ int s_nst;
     const Geometry& g = a.g;
-    const int L = g.L, W = g.W, N = g.N;
+    const int L = g.L, Lc = g.Lc, W = g.W, Wc = g.Wc, N = g.N;
     const int w = blockIdx.y;
-    const int tiles_j = (W + kTJ - 1) / kTJ;
+    const int tiles_j = (Wc + kTJ - 1) / kTJ;
     const int i0 = (blockIdx.x / tiles_j) * kTI, j0 = (blockIdx.x % tiles_j) * kTJ;
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nwarp = blockDim.x >> 5;
     const uint32_t* gt = a.ctab + static_cast<size_t>(w) * kCanonTab;
@@ -370,14 +371,14 @@ __global__ void __launch_bounds__(kStreamVisThreads, CRBM_STREAM_MIN_BLOCKS) k_s
             }
     }
     // hidden halo: cells (i0 - 1 .. i0 + ni - 1) x (j0 - 1 .. j0 + nj - 1), wrapped
-    const int ni = min(kTI, W - i0), nj = min(kTJ, W - j0);
+    const int ni = min(kTI, W - i0), nj = min(kTJ, Wc - j0);
     const uint32_t* hw = a.h + static_cast<size_t>(w) * g.n_cells * 10;
     for (int x = threadIdx.x; x < (kTI + 1) * HS * 10; x += blockDim.x) {
         const int lc = x / 10, k = x - lc * 10;
         const int li = lc / HS, lj = lc - li * HS;
         if (li > ni || lj > nj) continue;
-        const int gi = (i0 - 1 + li + W) % W, gj = (j0 - 1 + lj + W) % W;
-        s_h[x] = hw[(gi * W + gj) * 10 + k];
+        const int gi = (i0 - 1 + li + W) % W, gj = (j0 - 1 + lj + Wc) % Wc;
+        s_h[x] = hw[(gi * Wc + gj) * 10 + k];
     }
     __syncthreads();
     const uint32_t fl0 = s_tab[kBpFlip], fl1 = s_tab[kBpFlip + 1];
@@ -404,7 +405,7 @@ __global__ void __launch_bounds__(kStreamVisThreads, CRBM_STREAM_MIN_BLOCKS) k_s
         };
         const uint32_t h0 = hin(s_inc[x][0], fl0), h1 = hin(s_inc[x][1], fl0), h2 = hin(s_inc[x][2], fl0),
                        h3 = hin(s_inc[x][3], fl0);
-        const uint32_t cell = static_cast<uint32_t>((i0 + (R >> 1)) * W + j0 + (C >> 1));
+        const uint32_t cell = static_cast<uint32_t>((i0 + (R >> 1)) * Wc + j0 + (C >> 1));
         const uint64_t pc = static_cast<uint64_t>(kPhiloxM0) * cell;
         return Vis{hin(s_inc[x][4], fl1),
                    static_cast<uint32_t>(pc >> 32) ^ a.rk[1] ^ (kTagBitplane + 8u * (10u + static_cast<uint32_t>(x))),
@@ -450,8 +451,8 @@ __global__ void __launch_bounds__(kStreamVisThreads, CRBM_STREAM_MIN_BLOCKS) k_s
     for (int x = threadIdx.x; x < 2 * kTI * VO; x += blockDim.x) {
         const int r = x / VO, c = x - (x / VO) * VO;
         const int R = 2 * i0 + r, C = 2 * j0 + c;
-        if (r >= nr || c >= nc || R >= L || C >= L) continue;
-        a.v[vidx(w, N, R * L + C)] = s_o[x];
+        if (r >= nr || c >= nc || R >= L || C >= Lc) continue;
+        a.v[vidx(w, N, R * Lc + C)] = s_o[x];
     }
 }
 
@@ -461,9 +462,9 @@ __global__ void __launch_bounds__(kStreamThreads, CRBM_STREAM_MIN_BLOCKS) k_stre
     __shared__ uint32_t s_v[(2 * kTI + 1) * (2 * kTJ + 1)];
     __shared__ int s_cnt[96];
     const Geometry& g = a.g;
-    const int W = g.W;
+    const int W = g.W, Wc = g.Wc;
     const int w = blockIdx.y;
-    const int tiles_j = (W + kTJ - 1) / kTJ;
+    const int tiles_j = (Wc + kTJ - 1) / kTJ;
     const int i0 = (blockIdx.x / tiles_j) * kTI, j0 = (blockIdx.x % tiles_j) * kTJ;
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nwarp = blockDim.x >> 5;
     constexpr int VS = 2 * kTJ + 1;
@@ -471,7 +472,7 @@ __global__ void __launch_bounds__(kStreamThreads, CRBM_STREAM_MIN_BLOCKS) k_stre
     for (int x = threadIdx.x; x < 96; x += blockDim.x) s_cnt[x] = 0;
     __syncthreads();
     int anti0 = 0, anti1 = 0, pos = 0;
-    const int ni = min(kTI, W - i0), nj = min(kTJ, W - j0);
+    const int ni = min(kTI, W - i0), nj = min(kTJ, Wc - j0);
     for (int lj = warp; lj < nj; lj += nwarp)
         for (int li = 0; li < ni; ++li)
             count_cell(s_v + 2 * li * VS + 2 * lj, 0, VS, 2 * VS, 0, 1, 2, lane, anti0, anti1, pos);
@@ -526,7 +527,7 @@ __global__ void k_stream_finalize(const SweepArgs a, int64_t meas, int64_t sweep
 }  // namespace
 
 cudaError_t launch_sweep_stream(const SweepArgs& a, cudaStream_t st, int64_t* launches) {
-    const int tiles = ((a.g.W + kTI - 1) / kTI) * ((a.g.W + kTJ - 1) / kTJ);
+    const int tiles = ((a.g.W + kTI - 1) / kTI) * ((a.g.Wc + kTJ - 1) / kTJ);
     const dim3 grid(tiles, a.n_words);
     int64_t meas = a.meas0;
     for (int it = 0; it < a.n_sweeps; ++it) {

@@ -160,7 +160,8 @@ def test_bitplane_differs_from_lane_uniforms():
 
 def test_bitplane_where_unsupported():
     ok = dict(J=[1.0], Jp=[1.0], h=[0.5], beta=[2.0])
-    for kw in (dict(L=9), dict(L=10, periodic=False), dict(L=20, L_cols=12, layout=crbm.CRBM_LAYOUT_STREAM),
+    for kw in (dict(L=9), dict(L=10, periodic=False),
+               dict(L=20, L_cols=12, periodic_cols=crbm.CRBM_BC_OPEN, layout=crbm.CRBM_LAYOUT_STREAM),
                dict(L=10, precision=crbm.CRBM_PRECISION_PAPER), dict(L=10, sq_every=2)):
         with pytest.raises(crbm.CrbmError) as e:
             crbm.Sampler(params=ok, n_chains=32, rng=BP, **kw)

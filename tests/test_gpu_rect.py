@@ -2,8 +2,8 @@
 GPU against the oracle, bit for bit: tables, spins, sums and series; the
 laterally confined 18 x 12 strip of Sec. III among them.  Rectangles with even
 sides, periodic along both axes, run on the canonical shared-memory sweep
-(also split into bands over a cluster in a batch); the rest on the generic
-sweep."""
+(also split into bands over a cluster in a batch) and on the streamed sweep;
+the rest on the generic sweep."""
 import numpy as np
 import pytest
 
@@ -135,12 +135,52 @@ def test_strip_in_a_batch_matches_its_twin(orc):
     batch.close()
 
 
+@pytest.mark.parametrize("L,Lc", [(18, 12), (12, 40), (40, 12), (36, 34), (4, 16)])
+@pytest.mark.parametrize("mode", ["exact", "paper", "bitplane"])
+def test_periodic_rectangles_streamed(orc, L, Lc, mode):
+    """The streamed layout on even periodic rectangles: tiles of 16 x 16
+    cells over W x Wc cells (one tile or several, ragged along either axis;
+    the spin and hidden halos wrapping once or by the modulo), a ragged last
+    64-chain group, in exact precision, paper precision and with bit-plane
+    uniforms, against the oracle and against the SMEM layout."""
+    rng = np.random.default_rng(L * 53 + Lc + len(mode))
+    params = workloads.random_params(rng, 3)
+    n = 70
+    cp = rng.integers(0, 3, n).astype(np.int32)
+    precision = crbm.CRBM_PRECISION_PAPER if mode == "paper" else crbm.CRBM_PRECISION_EXACT
+    rng_mode = crbm.CRBM_RNG_BITPLANE if mode == "bitplane" else crbm.CRBM_RNG_LANE
+    seed = 11 + L + Lc
+    kw = dict(chain_param=cp, seed=seed, L_cols=Lc, measure_every=2, series_len=4, precision=precision,
+              rng=rng_mode)
+    s = crbm.Sampler(L, params, n, layout=crbm.CRBM_LAYOUT_STREAM, **kw)
+    assert s.layout == crbm.CRBM_LAYOUT_STREAM
+    ids = np.arange(n, dtype=np.uint32)
+    spins = orc.init_spins((L, Lc), ids, seed)
+    assert np.array_equal(s.get_spins(), spins), "initial spins"
+    sums, oser, t = None, None, 0
+    orng = orc.RNG_BITPLANE if mode == "bitplane" else orc.RNG_LANE
+    for k in (3, 4):
+        s.sweep(k)
+        sums, ser, _ = orc.run((L, Lc), params, cp, spins, seed, t, k, 2, chain_ids=ids, sums=sums,
+                               series_cap=4, precision=precision, rng=orng)
+        oser = ser if oser is None else np.where(ser != 0, ser, oser)
+        t += k
+        assert np.array_equal(s.get_spins(), spins), f"spins after {t} sweeps"
+    assert np.array_equal(s.observables(), sums)
+    assert np.array_equal(s.series().transpose(1, 0, 2), oser)
+    m = crbm.Sampler(L, params, n, layout=crbm.CRBM_LAYOUT_SMEM, **kw)
+    m.sweep(7)
+    assert np.array_equal(m.get_spins(), s.get_spins())
+    assert np.array_equal(m.observables(), s.observables())
+
+
 def test_rectangle_validation():
     ok = dict(J=[1.0], Jp=[1.0], h=[0.5], beta=[2.0])
     for kw, code in ((dict(L_cols=2), crbm.CRBM_EINVAL), (dict(periodic_cols=5), crbm.CRBM_EINVAL),
                      (dict(L_cols=8, sq_every=2), crbm.CRBM_EINVAL),
                      (dict(periodic_cols=OPEN, sq_every=2), crbm.CRBM_EINVAL),
-                     (dict(L_cols=8, layout=crbm.CRBM_LAYOUT_STREAM), crbm.CRBM_EUNSUPPORTED),
+                     (dict(L_cols=8, periodic_cols=OPEN, layout=crbm.CRBM_LAYOUT_STREAM),
+                      crbm.CRBM_EUNSUPPORTED),
                      (dict(L_cols=8, periodic_cols=OPEN, precision=crbm.CRBM_PRECISION_PAPER),
                       crbm.CRBM_EUNSUPPORTED)):
         with pytest.raises(crbm.CrbmError) as e:

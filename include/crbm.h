@@ -125,8 +125,8 @@ typedef struct {
      * the spin at window offset (r, c) half (2r+c)&1 of word 1 + ((2r+c)>>1)
      * of tag 1 -- two Philox calls per cell instead of four (three in the
      * streamed layout, whose visible half-step draws the tag-1 call again).
-     * Needs the ten SS filters and an even periodic lattice; not in batches
-     * or with block proposals.  crbm_get_tables returns the 16-bit
+     * Needs the ten SS filters and an even periodic lattice; not with block
+     * proposals (a batch runs such a member's words whole, unsplit).  crbm_get_tables returns the 16-bit
      * thresholds in the upper halves of the 32-bit entries. */
     int32_t precision;
     /* Rectangular lattices and a boundary per axis (Sec. III: open boundaries
@@ -153,13 +153,15 @@ typedef struct {
      * 256 + 8 n + j)), and chain l's uniform is sum_b bit l of P_b << (31 -
      * b): most significant bit first, so a comparison of all 32 uniforms
      * with their thresholds can stop at the first plane on which every chain
-     * is decided (about 10 planes, 3 calls, per node and word instead of 8
-     * calls for 32 separate uniforms).  Node n = k for hidden filter k, 10 +
+     * is decided (two calls per node, then the nodes still open, about 12 %,
+     * from a straggler list: 2.2 calls per node and word instead of 8 calls
+     * for 32 separate uniforms).  Node n = k for hidden filter k, 10 +
      * 2r + c for the spin at window offset (r, c).  Needs the ten SS filters
      * on an even periodic lattice (SMEM or streamed layout; replica exchange
      * in the SMEM layout, where slot l draws as chain 32 w + l whichever rung
-     * it holds), exact precision, no correlations; not in batches or with
-     * block proposals.  A different random stream: the chains differ from
+     * it holds), exact precision, no correlations; not with block proposals
+     * (a batch runs such a member's words whole, node records read from
+     * global memory).  A different random stream: the chains differ from
      * CRBM_RNG_LANE's, with the same law. */
     int32_t rng;
 } crbm_params;
@@ -275,15 +277,15 @@ int crbm_philox_stream(uint32_t* sink, int32_t n_blocks, int32_t threads, int32_
                        void* stream);
 
 /* Batched sweeps: several SMEM-layout contexts -- mixed lattice sizes,
- * filter lists and tempering ladders -- advanced together by ONE kernel
- * launch plus a one-thread clock update, captured once in a CUDA graph and
- * replayed on the members' common stream.  The launch has one CTA per packed
- * word of every member, heaviest lattices first, except that with
- * thread-block clusters of C CTAs (environment CRBM_BATCH_CLUSTER, default 8,
- * 1 = none) a canonical word without correlations that has at least C cell
- * rows and 16 cells per band is split into C bands of cell rows, one cluster
- * per word, the bands exchanging their boundary rows through distributed
- * shared memory.  Members keep their own state, counters and getters; each
+ * filter lists, precisions, uniform modes and tempering ladders -- advanced
+ * together by ONE kernel launch plus a one-thread clock update, captured once
+ * in a CUDA graph and replayed on the members' common stream.  The launch has
+ * one CTA per packed word of every member, heaviest lattices first, except
+ * that with thread-block clusters of C CTAs (environment CRBM_BATCH_CLUSTER,
+ * default 8, 1 = none) a canonical exact-precision, lane-uniform word without
+ * correlations that has at least C cell rows and 16 cells per band is split
+ * into C bands of cell rows, one cluster per word, the bands exchanging their
+ * boundary rows through distributed shared memory.  Members keep their own state, counters and getters; each
  * batched call advances every member by n_sweeps sweeps, bit-identical to
  * calling crbm_sweep on each.  The CTA shape is the largest warps count of
  * the members (see crbm_autotune). */

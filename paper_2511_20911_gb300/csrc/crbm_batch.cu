@@ -1,10 +1,12 @@
-// Batched sweep: several contexts (mixed lattice sizes, filter lists and
-// tempering ladders) in one kernel launch.  Each CTA (or cluster of CTAs)
-// takes one (context, word) item of the work list and runs the canonical or
-// the generic SMEM-resident body for it; the contexts' descriptors travel by
+// Batched sweep: several contexts (mixed lattice sizes, filter lists,
+// precisions, uniform modes and tempering ladders) in one kernel launch.
+// Each CTA (or cluster of CTAs) takes one (context, word) item of the work
+// list and runs the canonical (exact or paper precision), bit-plane or
+// generic SMEM-resident body for it; the contexts' descriptors travel by
 // value in the kernel parameters.  Sweep and measurement counters come from a device
 // clock per context, advanced by a one-thread epilogue, so the pair of
 // launches can be captured once in a CUDA graph and replayed.
+#include "crbm_bitplane_body.cuh"
 #include "crbm_canon_body.cuh"
 #include "crbm_generic_body.cuh"
 
@@ -19,8 +21,10 @@ namespace cg = cooperative_groups;
 // padding ranks of that context, band >= bands), all synchronising with
 // cluster barriers; every other cluster holds whole words, one per CTA,
 // which synchronise within their CTA only; tasks with descriptor -1 return
-// at once.
-template <bool kCluster>
+// at once.  kModes: the member kinds besides exact lane-uniform and generic
+// ones that the batch holds (kBatchPaper, kBatchBitplane), so that a batch
+// without them runs code that carries neither body.
+template <bool kCluster, int kModes>
 __global__ void __launch_bounds__(CRBM_SWEEP_MAX_THREADS, CRBM_SWEEP_MAX_THREADS <= 512 ? 2 : 1) k_sweep_batch(const __grid_constant__ BatchArgs b) {
     const int4 task = b.items[blockIdx.x];
     if (task.x < 0) return;
@@ -28,6 +32,18 @@ __global__ void __launch_bounds__(CRBM_SWEEP_MAX_THREADS, CRBM_SWEEP_MAX_THREADS
     const uint32_t t0 = static_cast<uint32_t>(a.clock[0]);
     if (!a.g.canonical) {
         generic::sweep_generic_body(a, task.y);
+    } else if ((kModes & kBatchBitplane) && a.g.bitplane) {  // whole words; node records from global memory
+        const uint32_t* hrec = reinterpret_cast<const uint32_t*>(a.crec);
+        const uint32_t* vrec = hrec + static_cast<size_t>(a.g.n_cells) * bp::kBpNodes;
+        if (a.swap_every > 0)
+            bp::sweep_bitplane_body<true>(a, hrec, vrec, task.y, t0, a.n_sweeps, a.clock[1]);
+        else
+            bp::sweep_bitplane_body<false>(a, hrec, vrec, task.y, t0, a.n_sweeps, a.clock[1]);
+    } else if ((kModes & kBatchPaper) && a.g.paper) {  // whole words
+        if (b.smem_rec)
+            canon::sweep_canon_body<true, false, true>(a, task.y, t0, a.n_sweeps, a.clock[1]);
+        else
+            canon::sweep_canon_body<false, false, true>(a, task.y, t0, a.n_sweeps, a.clock[1]);
     } else if (kCluster && task.w > 1) {
         const int rank = static_cast<int>(cg::this_cluster().block_rank());
         const int rank0 = task.z < task.w ? rank - task.z : 0;
@@ -39,6 +55,18 @@ __global__ void __launch_bounds__(CRBM_SWEEP_MAX_THREADS, CRBM_SWEEP_MAX_THREADS
         canon::sweep_canon_body<true, false>(a, task.y, t0, a.n_sweeps, a.clock[1]);
     } else {
         canon::sweep_canon_body<false, false>(a, task.y, t0, a.n_sweeps, a.clock[1]);
+    }
+}
+
+// The instantiation for a cluster flag and a set of member kinds.
+using BatchKernel = void (*)(const BatchArgs);
+template <bool kCluster>
+BatchKernel batch_kernel(int modes) {
+    switch (modes & (kBatchPaper | kBatchBitplane)) {
+        case kBatchPaper: return k_sweep_batch<kCluster, kBatchPaper>;
+        case kBatchBitplane: return k_sweep_batch<kCluster, kBatchBitplane>;
+        case kBatchPaper | kBatchBitplane: return k_sweep_batch<kCluster, kBatchPaper | kBatchBitplane>;
+        default: return k_sweep_batch<kCluster, 0>;
     }
 }
 
@@ -54,21 +82,17 @@ __global__ void k_batch_advance(int64_t* clocks, const int* every, int n_ctx, in
 
 }  // namespace
 
-cudaError_t launch_sweep_batch(const BatchArgs& b, int n_tasks, int cluster, int threads, size_t smem,
+cudaError_t launch_sweep_batch(const BatchArgs& b, int n_tasks, int cluster, int threads, size_t smem, int modes,
                                cudaStream_t st) {
-    if (cluster <= 1) {
-        if (smem > 48 * 1024) {
-            const cudaError_t e = cudaFuncSetAttribute(k_sweep_batch<false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                                       static_cast<int>(smem));
-            if (e != cudaSuccess) return e;
-        }
-        k_sweep_batch<false><<<n_tasks, threads, smem, st>>>(b);
-        return cudaGetLastError();
-    }
+    const BatchKernel kernel = cluster <= 1 ? batch_kernel<false>(modes) : batch_kernel<true>(modes);
     if (smem > 48 * 1024) {
-        const cudaError_t e = cudaFuncSetAttribute(k_sweep_batch<true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                                   static_cast<int>(smem));
+        const cudaError_t e =
+            cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, static_cast<int>(smem));
         if (e != cudaSuccess) return e;
+    }
+    if (cluster <= 1) {
+        kernel<<<n_tasks, threads, smem, st>>>(b);
+        return cudaGetLastError();
     }
     cudaLaunchConfig_t cfg = {};
     cfg.gridDim = dim3(static_cast<unsigned int>(n_tasks));
@@ -82,12 +106,14 @@ cudaError_t launch_sweep_batch(const BatchArgs& b, int n_tasks, int cluster, int
     attr[0].val.clusterDim.z = 1;
     cfg.attrs = attr;
     cfg.numAttrs = 1;
-    return cudaLaunchKernelEx(&cfg, k_sweep_batch<true>, b);
+    return cudaLaunchKernelEx(&cfg, kernel, b);
 }
 
-int batch_max_active_clusters(int cluster, int threads, size_t smem) {
-    if (smem > 48 * 1024 && cudaFuncSetAttribute(k_sweep_batch<true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                                 static_cast<int>(smem)) != cudaSuccess)
+int batch_max_active_clusters(int cluster, int threads, size_t smem, int modes) {
+    const BatchKernel kernel = batch_kernel<true>(modes);
+    if (smem > 48 * 1024 &&
+        cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, static_cast<int>(smem)) !=
+            cudaSuccess)
         return 0;
     cudaLaunchConfig_t cfg = {};
     cfg.gridDim = dim3(static_cast<unsigned int>(cluster));
@@ -101,7 +127,7 @@ int batch_max_active_clusters(int cluster, int threads, size_t smem) {
     cfg.attrs = attr;
     cfg.numAttrs = 1;
     int n = 0;
-    if (cudaOccupancyMaxActiveClusters(&n, k_sweep_batch<true>, &cfg) != cudaSuccess) {
+    if (cudaOccupancyMaxActiveClusters(&n, kernel, &cfg) != cudaSuccess) {
         cudaGetLastError();
         return 0;
     }

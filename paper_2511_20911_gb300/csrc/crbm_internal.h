@@ -258,10 +258,13 @@ cudaError_t launch_sweep_stream(const SweepArgs& a, cudaStream_t st, int64_t* la
 // and without the records.
 size_t smem_bytes_bitplane(const Geometry& g, bool with_records);
 cudaError_t launch_sweep_bitplane(const SweepArgs& a, int warps_per_cta, int chunk, int* sched, cudaStream_t st);
-cudaError_t launch_sweep_batch(const BatchArgs& b, int n_tasks, int cluster, int threads, size_t smem,
+// modes: the member kinds of the batch besides exact lane-uniform and generic
+// ones (kBatchPaper, kBatchBitplane), which pick the kernel instantiation.
+constexpr int kBatchPaper = 1, kBatchBitplane = 2;
+cudaError_t launch_sweep_batch(const BatchArgs& b, int n_tasks, int cluster, int threads, size_t smem, int modes,
                                cudaStream_t st);
 // Clusters of `cluster` batch CTAs that can be resident at once (0: none).
-int batch_max_active_clusters(int cluster, int threads, size_t smem);
+int batch_max_active_clusters(int cluster, int threads, size_t smem, int modes);
 cudaError_t launch_batch_advance(int64_t* clocks, const int* every, int n_ctx, int64_t n_sweeps, cudaStream_t st);
 cudaError_t launch_philox(const uint32_t* in, uint32_t* out, int n, cudaStream_t st);
 cudaError_t launch_philox_stream(uint32_t* sink, int n_blocks, int threads, int calls, uint32_t k0,

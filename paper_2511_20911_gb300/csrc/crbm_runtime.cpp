@@ -45,8 +45,17 @@ std::string shape_key(const crbm_ctx* ctx) {
     return s;
 }
 
+// Shared memory of a batch member's body (bit-plane records from global memory).
+size_t member_smem(const crbm_ctx* ctx) {
+    return ctx->g.bitplane ? smem_bytes_bitplane(ctx->g, false)
+           : ctx->g.canonical ? smem_bytes_canon(ctx->g)
+                              : smem_bytes_generic(ctx->g);
+}
+
 int smem_ok(const crbm_ctx* ctx) {
-    return (ctx->g.canonical ? smem_bytes_canon(ctx->g) : smem_bytes_generic(ctx->g)) <= 227 * 1024;
+    return (ctx->g.bitplane ? smem_bytes_bitplane(ctx->g, false)
+            : ctx->g.canonical ? smem_bytes_canon(ctx->g)
+                               : smem_bytes_generic(ctx->g)) <= 227 * 1024;
 }
 
 cudaError_t launch_one(const SweepArgs& a, const crbm_ctx* ctx, int warps) {
@@ -169,6 +178,7 @@ struct crbm_batch {
     int threads = 0;
     size_t smem = 0;
     int smem_rec = 0;                  // canonical members stage their records in shared memory
+    int modes = 0;                     // kBatchPaper | kBatchBitplane: member kinds present
     int cluster = 1;                   // CTAs per item (thread-block cluster)
     std::vector<int> bands;            // per member: CTAs its words are split over
     cudaGraphExec_t exec = nullptr;
@@ -202,22 +212,22 @@ int crbm_batch_create(crbm_batch** out, crbm_ctx* const* ctxs, int32_t n_ctx) {
     int warps = 1;
     for (int c = 0; c < n_ctx; ++c) {
         crbm_ctx* x = ctxs[c];
-        if (!x || x->layout != CRBM_LAYOUT_SMEM || !smem_ok(x) || x->g.paper || x->g.bitplane ||
-            x->stream != ctxs[0]->stream ||
+        if (!x || x->layout != CRBM_LAYOUT_SMEM || !smem_ok(x) || x->stream != ctxs[0]->stream ||
             x->device != ctxs[0]->device || std::count(ctxs, ctxs + c, x)) {
-            g_batch_create_error =
-                "batch members must be distinct SMEM-layout, exact-precision contexts on one device and stream";
+            g_batch_create_error = "batch members must be distinct SMEM-layout contexts on one device and stream";
             delete b;
             return CRBM_EINVAL;
         }
         b->ctx.push_back(x);
         warps = std::max(warps, x->warps);
-        b->smem = std::max(b->smem, x->g.canonical ? smem_bytes_canon(x->g) : smem_bytes_generic(x->g));
+        b->smem = std::max(b->smem, member_smem(x));
+        if (x->g.paper) b->modes |= kBatchPaper;
+        if (x->g.bitplane) b->modes |= kBatchBitplane;
     }
     // stage the canonical members' per-cell records in shared memory when all of them fit
     size_t with_rec = b->smem;
     for (auto* x : b->ctx)
-        if (x->g.canonical)
+        if (x->g.canonical && !x->g.bitplane)
             with_rec = std::max(with_rec, sizeof(uint32_t) * canon_smem_rec_offset(x->g) +
                                               sizeof(uint4) * static_cast<size_t>(x->g.n_cells) * kCellRec);
     if (with_rec <= 227 * 1024) {
@@ -226,7 +236,8 @@ int crbm_batch_create(crbm_batch** out, crbm_ctx* const* ctxs, int32_t n_ctx) {
     }
     b->threads = 32 * warps;
     // Thread-block clusters of `cluster` CTAs (CRBM_BATCH_CLUSTER, default 8,
-    // a power of two; 1 = none).  A canonical member without correlations is
+    // a power of two; 1 = none).  A canonical exact-precision, lane-uniform
+    // member without correlations is
     // split into B bands of cell rows per word, B the smallest power of two
     // (at most the cluster size and W) that brings its cells per CTA down to
     // the heaviest member's when split over a whole cluster (at least 16);
@@ -236,8 +247,10 @@ int crbm_batch_create(crbm_batch** out, crbm_ctx* const* ctxs, int32_t n_ctx) {
     int cluster = 8;
     if (const char* env = std::getenv("CRBM_BATCH_CLUSTER")) cluster = std::max(1, std::min(8, std::atoi(env)));
     while (cluster & (cluster - 1)) --cluster;  // a power of two
-    if (cluster > 1 && batch_max_active_clusters(cluster, b->threads, b->smem) < 1) cluster = 1;
-    auto splittable = [&](const crbm_ctx* x) { return cluster > 1 && x->g.canonical && x->sq_every == 0; };
+    if (cluster > 1 && batch_max_active_clusters(cluster, b->threads, b->smem, b->modes) < 1) cluster = 1;
+    auto splittable = [&](const crbm_ctx* x) {
+        return cluster > 1 && x->g.canonical && !x->g.paper && !x->g.bitplane && x->sq_every == 0;
+    };
     int target = 16;
     for (auto* x : b->ctx)
         if (splittable(x)) target = std::max(target, x->g.n_cells / std::min(cluster, x->g.W));
@@ -341,7 +354,8 @@ int crbm_batch_sweep(crbm_batch* b, int64_t n_sweeps) {
         cudaGraph_t graph = nullptr;
         e = cudaStreamBeginCapture(b->capture, cudaStreamCaptureModeThreadLocal);
         if (e == cudaSuccess) {
-            cudaError_t e1 = launch_sweep_batch(args, b->n_items, b->cluster, b->threads, b->smem, b->capture);
+            cudaError_t e1 =
+                launch_sweep_batch(args, b->n_items, b->cluster, b->threads, b->smem, b->modes, b->capture);
             cudaError_t e2 = launch_batch_advance(b->clock, b->every, n, n_sweeps, b->capture);
             e = cudaStreamEndCapture(b->capture, &graph);
             if (e == cudaSuccess) e = e1 != cudaSuccess ? e1 : e2;

@@ -99,6 +99,41 @@ def test_batch_cluster_split_matches_individual_sweeps(cluster, monkeypatch):
     batch.close()
 
 
+@pytest.mark.parametrize("cluster", [1, 8])
+def test_batch_with_paper_precision_and_bitplane_members(cluster, monkeypatch):
+    """Paper-precision and bit-plane members (whole words, one per CTA; the
+    bit-plane ladder with replica exchange) beside exact members split over a
+    cluster and a generic member, in one launch: every member bit-identical
+    to a twin advanced on its own (the twins' sweeps are pinned to the oracle
+    elsewhere); a batch holding only exact members keeps the kernel without
+    the other bodies."""
+    monkeypatch.setenv("CRBM_BATCH_CLUSTER", str(cluster))
+    rng = np.random.default_rng(60 + cluster)
+    ladder = workloads.tempering_batch_workload(sizes=(8,), ladders=2)[0]
+    specs = [dict(L=10, params=workloads.random_params(rng, 3), n_chains=64,
+                  chain_param=rng.integers(0, 3, 64).astype(np.int32), seed=21, measure_every=2, series_len=12,
+                  precision=crbm.CRBM_PRECISION_PAPER),
+             dict(L=12, params=workloads.random_params(rng, 2), n_chains=50,
+                  chain_param=rng.integers(0, 2, 50).astype(np.int32), seed=22, measure_every=3, series_len=12,
+                  rng=crbm.CRBM_RNG_BITPLANE),
+             dict(ladder, measure_every=5, series_len=10, rng=crbm.CRBM_RNG_BITPLANE),
+             dict(L=24, params=workloads.random_params(rng, 2), n_chains=40,
+                  chain_param=rng.integers(0, 2, 40).astype(np.int32), seed=23, measure_every=4, series_len=12),
+             dict(L=9, params=workloads.random_params(rng, 2), n_chains=32,
+                  chain_param=rng.integers(0, 2, 32).astype(np.int32), seed=24, measure_every=4)]
+    batched = [make(s) for s in specs]
+    twins = [make(s) for s in specs]
+    batch = crbm.Batch(batched)
+    assert batch.cluster == cluster
+    for n in (5, 11, 30):
+        batch.sweep(n)
+        for t in twins:
+            t.sweep(n)
+    for a, b in zip(batched, twins):
+        same(a, b)
+    batch.close()
+
+
 def test_batch_validation():
     spec = members()[0]
     a, b = make(spec), make(spec)

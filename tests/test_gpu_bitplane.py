@@ -175,8 +175,8 @@ def test_bitplane_where_unsupported():
         crbm.Sampler(8, ok, 32, rng=7)
     assert e.value.code == crbm.CRBM_EINVAL
     a = crbm.Sampler(8, ok, 32, rng=BP)
-    with pytest.raises(crbm.CrbmError) as e:
-        crbm.Batch([a, crbm.Sampler(8, ok, 32)])
+    with pytest.raises(crbm.CrbmError) as e:    # a batch member twice
+        crbm.Batch([a, a])
     assert e.value.code == crbm.CRBM_EINVAL
     with pytest.raises(crbm.CrbmError) as e:
         crbm.Proposal(seed=1).passes(a, 1)

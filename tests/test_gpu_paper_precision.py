@@ -131,8 +131,8 @@ def test_paper_precision_where_unsupported():
     assert e.value.code == crbm.CRBM_EINVAL
     a = crbm.Sampler(6, ok, 32, precision=PAPER)
     b = crbm.Sampler(6, ok, 32)
-    with pytest.raises(crbm.CrbmError) as e:
-        crbm.Batch([a, b])
+    with pytest.raises(crbm.CrbmError) as e:    # a batch member twice
+        crbm.Batch([a, a])
     assert e.value.code == crbm.CRBM_EINVAL
     prop = crbm.Proposal(seed=1)
     with pytest.raises(crbm.CrbmError) as e:

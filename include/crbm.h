@@ -125,8 +125,10 @@ typedef struct {
      * the spin at window offset (r, c) half (2r+c)&1 of word 1 + ((2r+c)>>1)
      * of tag 1 -- two Philox calls per cell instead of four (three in the
      * streamed layout, whose visible half-step draws the tag-1 call again).
-     * Needs the ten SS filters and an even periodic lattice; not with block
-     * proposals (a batch runs such a member's words whole, unsplit).  crbm_get_tables returns the 16-bit
+     * Needs at most ten filters (any lattice: the SS fast path, SMEM or
+     * streamed, or the generic SMEM sweep, whose visible half-step also draws
+     * the tag-1 call again); not with block proposals (a batch runs such a
+     * member's words whole, unsplit).  crbm_get_tables returns the 16-bit
      * thresholds in the upper halves of the 32-bit entries. */
     int32_t precision;
     /* Rectangular lattices and a boundary per axis (Sec. III: open boundaries

@@ -31,7 +31,10 @@ __global__ void __launch_bounds__(CRBM_SWEEP_MAX_THREADS, CRBM_SWEEP_MAX_THREADS
     const SweepArgs& a = b.d[task.x];
     const uint32_t t0 = static_cast<uint32_t>(a.clock[0]);
     if (!a.g.canonical) {
-        generic::sweep_generic_body(a, task.y);
+        if ((kModes & kBatchPaper) && a.g.paper)
+            generic::sweep_generic_body<true>(a, task.y);
+        else
+            generic::sweep_generic_body<false>(a, task.y);
     } else if ((kModes & kBatchBitplane) && a.g.bitplane) {  // whole words; node records from global memory
         const uint32_t* hrec = reinterpret_cast<const uint32_t*>(a.crec);
         const uint32_t* vrec = hrec + static_cast<size_t>(a.g.n_cells) * bp::kBpNodes;

@@ -37,7 +37,11 @@ __device__ __forceinline__ uint32_t or_if_less(uint32_t w, uint32_t q, uint32_t 
 // filter k, in row `cell` of the hidden words.
 // Draws: Philox-4x32-10 of counter (cell, sweep, chain, tag) from the split
 // rounds (crbm_device.cuh): rs = round1_sweep of the lane's sweep word, Y the
-// lane's chain word, rk the round keys.
+// lane's chain word, rk the round keys.  kPaper (CRBM_PRECISION_PAPER, at most
+// ten filters): filter k < 8 takes half k & 1 of word k >> 1 of tag 0, filters
+// 8 and 9 the halves of word 0 of tag 1, each compared as the upper half of a
+// 32-bit word against the 16-bit threshold in the table entry's upper half.
+template <bool kPaper>
 __device__ __forceinline__ void hidden_cell_generic(const Geometry& g, char* sm, const uint4* __restrict__ rh,
                                                     uint32_t hw_byte, int cell, const Round1Sweep& rs, uint32_t Y,
                                                     const uint32_t (&rk)[20], uint32_t lm, uint32_t rot0,
@@ -46,9 +50,22 @@ __device__ __forceinline__ void hidden_cell_generic(const Geometry& g, char* sm,
     const Round2Cell r2 = round2_cell(rs.hik ^ rc.b);
     const uint4* r = rh + static_cast<size_t>(cell) * g.nb;
     uint32_t h = 0u;
+    if (kPaper) {
+        const U4 q0 = philox_from_round2(Y, rs, r2, rc.a, rk);
+        const U4 q1 = g.nb > 8 ? philox_from_round2(Y, rs, r2, rc.a ^ 1u, rk) : U4{0u, 0u, 0u, 0u};
+#pragma unroll
+        for (int k = 0; k < 10; ++k) {
+            if (k < g.nb) {
+                const uint32_t word = k < 8 ? pick(q0, k >> 1) : q1.x;
+                const uint4 e = __ldg(r + k);
+                const uint32_t a = rotr(lds32(sm, e.x) & lm, rot0), b = rotr(lds32(sm, e.y) & lm, rot1);
+                h = or_if_less(h, (k & 1) ? word : word << 16, lds32(sm, e.z + (a | b | lb)), 1u << k);
+            }
+        }
+    }
 #pragma unroll
     for (int c = 0; c < 4; ++c) {  // call c draws for filters 4c .. 4c + 3
-        if (c < g.n_calls) {
+        if (!kPaper && c < g.n_calls) {
             const U4 q = philox_from_round2(Y, rs, r2, rc.a ^ static_cast<uint32_t>(c), rk);
 #pragma unroll
             for (int x = 0; x < 4; ++x) {
@@ -72,13 +89,15 @@ __device__ __forceinline__ void hidden_cell_generic(const Geometry& g, char* sm,
 // lane), so that bit k is the term of filter k at its first endpoint and bit
 // 16 + k at its second; a spin's n_J, n_J' are then 2 popc(masked) - degree,
 // and its table row is the record's row of n = -degree plus
-// 2 (2 DJp + 1) popc_J + 2 popc_J'.
+// 2 (2 DJp + 1) popc_J + 2 popc_J'.  kPaper: the spin at window offset x =
+// 2r + c takes half x & 1 of word 1 + (x >> 1) of tag 1.
+template <bool kPaper>
 __device__ __forceinline__ void visible_cell_generic(char* sm, const uint4* __restrict__ rv, int cell,
                                                      const Round1Sweep& rs, uint32_t Y, const uint32_t (&rk)[20],
                                                      uint32_t sflip, uint32_t stepJ, uint32_t lb, int lane) {
     const uint4* r = rv + static_cast<size_t>(cell) * kGenVisRec;
     const Round0Cell rc = round0_cell(static_cast<uint32_t>(cell), rk[1]);
-    const U4 q = philox_from_round2(Y, rs, round2_cell(rs.hik ^ rc.b), rc.a ^ kTagVis, rk);
+    const U4 q = philox_from_round2(Y, rs, round2_cell(rs.hik ^ rc.b), rc.a ^ (kPaper ? 1u : kTagVis), rk);
     const uint4 src = __ldg(r);
     const uint32_t l2 = 2u * static_cast<uint32_t>(lane);
     uint32_t w[4];
@@ -95,7 +114,8 @@ __device__ __forceinline__ void visible_cell_generic(char* sm, const uint4* __re
         const uint32_t cj = __popc(w[0] & mj.x) + __popc(w[1] & mj.y) + __popc(w[2] & mj.z) + __popc(w[3] & mj.w);
         const uint32_t cp = __popc(w[0] & mp.x) + __popc(w[1] & mp.y) + __popc(w[2] & mp.z) + __popc(w[3] & mp.w);
         const uint32_t row = (x == 0 ? tb.x : x == 1 ? tb.y : x == 2 ? tb.z : tb.w) + cj * stepJ + (cp << 8);
-        const uint32_t vw = __ballot_sync(0xffffffffu, pick(q, x) < lds32(sm, row + lb));
+        const uint32_t u = kPaper ? ((x & 1) ? pick(q, 1 + (x >> 1)) : pick(q, 1 + (x >> 1)) << 16) : pick(q, x);
+        const uint32_t vw = __ballot_sync(0xffffffffu, u < lds32(sm, row + lb));
         *reinterpret_cast<uint32_t*>(sm + (x == 0 ? so.x : x == 1 ? so.y : x == 2 ? so.z : so.w)) = vw;
     }
 }
@@ -122,7 +142,8 @@ __device__ __forceinline__ void count_cell(const Geometry& g, const uint32_t* s_
 // lattice, hidden layer and threshold columns in shared memory, all n_sweeps
 // sweeps on device.  Warps split the cells of each half-step; __syncthreads
 // separates the half-steps (hidden reads v / writes h; visible reads h /
-// writes v).
+// writes v).  kPaper: CRBM_PRECISION_PAPER draws (see the cores).
+template <bool kPaper>
 __device__ __forceinline__ void sweep_generic_body(const SweepArgs& a, int word) {
     extern __shared__ __align__(16) uint32_t smem[];
     const Geometry& g = a.g;
@@ -180,10 +201,10 @@ __device__ __forceinline__ void sweep_generic_body(const SweepArgs& a, int word)
         const uint32_t t = t0 + static_cast<uint32_t>(it);
         const Round1Sweep rs = round1_sweep(r0l.hi ^ t ^ a.rk[0], a.rk);
         for (int cell = warp; cell < g.n_cells; cell += nwarp)
-            hidden_cell_generic(g, sm, rh, hw_byte, cell, rs, r0l.lo, a.rk, lm, rot0, rot1, lb, lane);
+            hidden_cell_generic<kPaper>(g, sm, rh, hw_byte, cell, rs, r0l.lo, a.rk, lm, rot0, rot1, lb, lane);
         __syncthreads();
         for (int cell = warp; cell < g.n_cells; cell += nwarp)
-            visible_cell_generic(sm, rv, cell, rs, r0l.lo, a.rk, sflip, stepJ, lb, lane);
+            visible_cell_generic<kPaper>(sm, rv, cell, rs, r0l.lo, a.rk, sflip, stepJ, lb, lane);
         __syncthreads();
         const bool do_meas = measuring && (t + 1u) % static_cast<uint32_t>(a.measure_every) == 0u;
         const bool do_swap = a.swap_every > 0 && (t + 1u) % static_cast<uint32_t>(a.swap_every) == 0u;

@@ -354,9 +354,9 @@ int crbm_create(crbm_ctx** out, const crbm_params* p) {
         delete ctx;
         return fail(nullptr, CRBM_EINVAL, "SMEM layout needs L, L_cols <= CRBM_SMEM_MAX_L");
     }
-    if (g.paper && !g.canonical) {
+    if (g.paper && g.nb > 10) {
         delete ctx;
-        return fail(nullptr, CRBM_EUNSUPPORTED, "paper precision serves the ten SS filters on an even periodic lattice");
+        return fail(nullptr, CRBM_EUNSUPPORTED, "paper precision draws 16-bit uniforms for at most ten filters");
     }
     if (ctx->layout == CRBM_LAYOUT_STREAM && !g.canonical) {
         delete ctx;

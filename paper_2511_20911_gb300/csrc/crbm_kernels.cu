@@ -16,8 +16,9 @@ namespace {
 
 using namespace dev;
 
+template <bool kPaper>
 __global__ void __launch_bounds__(512, 1) k_sweep_generic(const SweepArgs a) {
-    generic::sweep_generic_body(a, blockIdx.x);
+    generic::sweep_generic_body<kPaper>(a, blockIdx.x);
 }
 
 // Initial spins: site (R, C) of chain c is +1 iff word 2(R&1)+(C&1) of
@@ -114,12 +115,13 @@ cudaError_t launch_init(const Geometry& g, uint32_t* v, int n_words, uint32_t ke
 
 cudaError_t launch_sweep_generic(const SweepArgs& a, int warps_per_cta, cudaStream_t st) {
     const size_t smem = smem_bytes_generic(a.g);
+    auto kernel = a.g.paper ? k_sweep_generic<true> : k_sweep_generic<false>;
     if (smem > 48 * 1024) {
-        const cudaError_t e = cudaFuncSetAttribute(k_sweep_generic, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                                   static_cast<int>(smem));
+        const cudaError_t e =
+            cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, static_cast<int>(smem));
         if (e != cudaSuccess) return e;
     }
-    k_sweep_generic<<<a.n_words, warps_per_cta * 32, smem, st>>>(a);
+    kernel<<<a.n_words, warps_per_cta * 32, smem, st>>>(a);
     return cudaGetLastError();
 }
 

@@ -101,9 +101,10 @@ def test_batch_cluster_split_matches_individual_sweeps(cluster, monkeypatch):
 
 @pytest.mark.parametrize("cluster", [1, 8])
 def test_batch_with_paper_precision_and_bitplane_members(cluster, monkeypatch):
-    """Paper-precision and bit-plane members (whole words, one per CTA; the
-    bit-plane ladder with replica exchange) beside exact members split over a
-    cluster and a generic member, in one launch: every member bit-identical
+    """Paper-precision members (canonical and generic) and bit-plane members
+    (whole words, one per CTA; the bit-plane ladder with replica exchange)
+    beside exact members split over a cluster and a generic member, in one
+    launch: every member bit-identical
     to a twin advanced on its own (the twins' sweeps are pinned to the oracle
     elsewhere); a batch holding only exact members keeps the kernel without
     the other bodies."""
@@ -120,7 +121,10 @@ def test_batch_with_paper_precision_and_bitplane_members(cluster, monkeypatch):
              dict(L=24, params=workloads.random_params(rng, 2), n_chains=40,
                   chain_param=rng.integers(0, 2, 40).astype(np.int32), seed=23, measure_every=4, series_len=12),
              dict(L=9, params=workloads.random_params(rng, 2), n_chains=32,
-                  chain_param=rng.integers(0, 2, 32).astype(np.int32), seed=24, measure_every=4)]
+                  chain_param=rng.integers(0, 2, 32).astype(np.int32), seed=24, measure_every=4),
+             dict(L=7, params=workloads.random_params(rng, 2), n_chains=45, periodic=False,
+                  chain_param=rng.integers(0, 2, 45).astype(np.int32), seed=25, measure_every=3, series_len=12,
+                  precision=crbm.CRBM_PRECISION_PAPER)]
     batched = [make(s) for s in specs]
     twins = [make(s) for s in specs]
     batch = crbm.Batch(batched)

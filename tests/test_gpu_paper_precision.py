@@ -120,9 +120,51 @@ def test_paper_precision_full_grid_sampled_chains(orc):
              measure_every=10, check_ids=ids)
 
 
+THIRTEEN = [(0, 0, 0, 1, 0), (0, 1, 0, 2, 0), (1, 0, 1, 1, 0), (1, 1, 1, 2, 0), (0, 0, 1, 0, 0),
+            (1, 0, 2, 0, 0), (0, 1, 1, 1, 0), (1, 1, 2, 1, 0), (0, 0, 1, 1, 1), (1, 2, 2, 1, 1),
+            (0, 1, 1, 0, 1), (0, 0, 2, 2, 0), (2, 0, 0, 2, 1)]
+
+
+@pytest.mark.parametrize("shape,periodic,bonds", [
+    (9, True, None), (7, False, None), ((18, 12), (True, False), None), ((9, 5), (False, False), None),
+    ((10, 3), (True, True), None),
+    (6, True, [(0, 0, 0, 1, 0), (1, 0, 1, 1, 0), (0, 0, 1, 0, 0), (0, 1, 1, 1, 0)]),
+    (7, False, [(0, 0, 1, 1, 1)])])
+def test_paper_precision_on_the_generic_sweep(orc, shape, periodic, bonds):
+    """Odd sides, open axes, laterally confined strips and custom filter lists
+    of at most ten filters in paper precision (the generic SMEM sweep: filter k
+    draws half k & 1 of word k >> 1 of tag 0, filters 8 and 9 of word 0 of tag
+    1, spin x half x & 1 of word 1 + (x >> 1) of tag 1): spins, sums and
+    series against the oracle, bit for bit."""
+    L, Lc = shape if isinstance(shape, tuple) else (shape, shape)
+    pr, pc = periodic if isinstance(periodic, tuple) else (periodic, periodic)
+    rng = np.random.default_rng(L * 7 + Lc + (0 if bonds is None else len(bonds)))
+    params = workloads.random_params(rng, 3)
+    n = 45
+    cp = rng.integers(0, 3, n).astype(np.int32)
+    seed = 31 + L + Lc
+    s = crbm.Sampler(L, params, n, chain_param=cp, seed=seed, periodic=pr, L_cols=Lc,
+                     periodic_cols=crbm.CRBM_BC_PERIODIC if pc else crbm.CRBM_BC_OPEN, measure_every=2,
+                     series_len=8, precision=PAPER, bonds=bonds)
+    assert s.layout == crbm.CRBM_LAYOUT_SMEM
+    ids = np.arange(n, dtype=np.uint32)
+    spins = orc.init_spins((L, Lc), ids, seed)
+    assert np.array_equal(s.get_spins(), spins)
+    sums, oser, t = None, None, 0
+    for k in (3, 9):
+        s.sweep(k)
+        sums, ser, _ = orc.run((L, Lc), params, cp, spins, seed, t, k, 2, chain_ids=ids, periodic=(pr, pc),
+                               bonds=bonds, sums=sums, series_cap=8, precision=PAPER)
+        oser = ser if oser is None else np.where(ser != 0, ser, oser)
+        t += k
+        assert np.array_equal(s.get_spins(), spins), f"spins after {t} sweeps"
+    assert np.array_equal(s.observables(), sums)
+    assert np.array_equal(s.series().transpose(1, 0, 2), oser)
+
+
 def test_paper_precision_where_unsupported():
     ok = dict(J=[1.0], Jp=[1.0], h=[0.5], beta=[2.0])
-    for kw in (dict(L=9), dict(L=10, periodic=False), dict(L=9, layout=crbm.CRBM_LAYOUT_STREAM)):
+    for kw in (dict(L=6, bonds=THIRTEEN), dict(L=9, layout=crbm.CRBM_LAYOUT_STREAM)):
         with pytest.raises(crbm.CrbmError) as e:
             crbm.Sampler(params=ok, n_chains=32, precision=PAPER, **kw)
         assert e.value.code == crbm.CRBM_EUNSUPPORTED, kw

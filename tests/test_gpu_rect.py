@@ -180,8 +180,6 @@ def test_rectangle_validation():
                      (dict(L_cols=8, sq_every=2), crbm.CRBM_EINVAL),
                      (dict(periodic_cols=OPEN, sq_every=2), crbm.CRBM_EINVAL),
                      (dict(L_cols=8, periodic_cols=OPEN, layout=crbm.CRBM_LAYOUT_STREAM),
-                      crbm.CRBM_EUNSUPPORTED),
-                     (dict(L_cols=8, periodic_cols=OPEN, precision=crbm.CRBM_PRECISION_PAPER),
                       crbm.CRBM_EUNSUPPORTED)):
         with pytest.raises(crbm.CrbmError) as e:
             crbm.Sampler(6, ok, 32, **kw)

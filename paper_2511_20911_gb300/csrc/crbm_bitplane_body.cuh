@@ -219,15 +219,24 @@ __device__ __forceinline__ void sweep_bitplane_body(const SweepArgs& a, const ui
         const bool do_meas = measuring && (t + 1u) % static_cast<uint32_t>(a.measure_every) == 0u;
         const bool do_swap = kSwap && (t + 1u) % static_cast<uint32_t>(a.swap_every) == 0u;
         if (do_meas || do_swap) {
-            // lane = chain: anti-aligned J and J' filters, +1 spins
+            // per chain: anti-aligned J and J' filters, +1 spins.  A warp takes 32 nodes (spins) at
+            // a time, lane = node, and a bit transpose turns their 32 chain words into one word per
+            // chain, lane = chain, whose popcount is that chain's count
             int anti0 = 0, anti1 = 0, pos = 0;
-            for (int node = warp; node < nh; node += nwarp) {
-                const uint32_t r = hrec[node];
-                const int d = static_cast<int>(((s_v[r & 0xFFFFu] ^ s_v[r >> 16]) >> lane) & 1u);
-                if (node % kBpNodes < 8) anti0 += d;
-                else anti1 += d;
+            for (int base = warp * 32; base < nh; base += nwarp * 32) {
+                const int node = base + lane;
+                uint32_t dJ = 0u, dP = 0u;
+                if (node < nh) {
+                    const uint32_t r = hrec[node];
+                    const uint32_t d = s_v[r & 0xFFFFu] ^ s_v[r >> 16];
+                    if (node % kBpNodes < 8) dJ = d;
+                    else dP = d;
+                }
+                anti0 += __popc(transpose32(dJ, lane));
+                anti1 += __popc(transpose32(dP, lane));
             }
-            for (int s = warp; s < N; s += nwarp) pos += static_cast<int>((s_v[s] >> lane) & 1u);
+            for (int base = warp * 32; base < N; base += nwarp * 32)
+                pos += __popc(transpose32(base + lane < N ? s_v[base + lane] : 0u, lane));
             atomicAdd(&s_cnt[lane], anti0);
             atomicAdd(&s_cnt[32 + lane], anti1);
             atomicAdd(&s_cnt[64 + lane], pos);

@@ -50,6 +50,20 @@ __device__ __forceinline__ uint32_t visible_plane(const uint32_t* tb, uint32_t h
     return (n.c2 & sel(4)) | (~n.c2 & ((n.c1 & m23) | (~n.c1 & m01)));
 }
 
+// 32 x 32 bit transpose across a warp: lane c returns the word whose bit l is
+// bit c of lane l's x (block swaps of 16, 8, 4, 2 and 1 rows and columns).
+__device__ __forceinline__ uint32_t transpose32(uint32_t x, int lane) {
+    constexpr uint32_t kLow[5] = {0x0000FFFFu, 0x00FF00FFu, 0x0F0F0F0Fu, 0x33333333u, 0x55555555u};
+#pragma unroll
+    for (int i = 0; i < 5; ++i) {
+        const int j = 16 >> i;
+        const uint32_t m = kLow[i];
+        const uint32_t y = __shfl_xor_sync(0xffffffffu, x, j);
+        x = (lane & j) ? ((x & ~m) | ((y >> j) & m)) : ((x & m) | ((y << j) & ~m));
+    }
+    return x;
+}
+
 // Appends the lanes whose comparison is still open (open != 0: its
 // undecided chains) to a straggler list of (node, open chains) pairs, with
 // one atomic per warp; returns true on the lanes whose node went to the list

@@ -53,7 +53,7 @@ MEASURED_TRAFFIC = {
     "stream": (56.74e6 + 392.31e6 + 454.82e6 + 48.83e6, "per sweep (two launches); profiles/k_stream_L384.md"),
     "grid_paper": (8.78e6 + 0.83e6, "per launch; profiles/k_sweep_canon_persistent_L18_grid_paper.md"),
     "stream_paper": (56.76e6 + 390.29e6 + 454.76e6 + 45.71e6, "per sweep (two launches); profiles/k_stream_L384.md"),
-    "grid_bitplane": (2.46e6 + 0.29e6, "per launch; profiles/k_sweep_bitplane_L18_grid.md"),
+    "grid_bitplane": (2.53e6 + 0.56e6, "per launch; profiles/k_sweep_bitplane_L18_grid.md"),
     "stream_bitplane": (56.86e6 + 82.62e6 + 141.80e6 + 29.18e6, "per sweep (two launches); profiles/k_stream_bp_L384.md"),
 }
 

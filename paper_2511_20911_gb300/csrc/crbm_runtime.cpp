@@ -52,11 +52,7 @@ size_t member_smem(const crbm_ctx* ctx) {
                               : smem_bytes_generic(ctx->g);
 }
 
-int smem_ok(const crbm_ctx* ctx) {
-    return (ctx->g.bitplane ? smem_bytes_bitplane(ctx->g, false)
-            : ctx->g.canonical ? smem_bytes_canon(ctx->g)
-                               : smem_bytes_generic(ctx->g)) <= 227 * 1024;
-}
+int smem_ok(const crbm_ctx* ctx) { return member_smem(ctx) <= 227 * 1024; }
 
 cudaError_t launch_one(const SweepArgs& a, const crbm_ctx* ctx, int warps) {
     if (!ctx->g.canonical) return launch_sweep_generic(a, warps, ctx->stream);

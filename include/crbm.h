@@ -111,7 +111,8 @@ typedef struct {
      * beta strictly increasing in k -- and after every swap_every-th sweep
      * adjacent rungs exchange configurations by the Metropolis rule
      * min(1, exp((beta_k - beta_{k+1}) (E_k - E_{k+1}))) on exact integer
-     * energies.  Needs n_chains % 32 == 0 and the SMEM layout.  Observables
+     * energies.  Needs n_chains % 32 == 0 (either layout; in the streamed
+     * one a 32-chain half of a 64-chain group is a ladder).  Observables
      * then belong to rungs (row 32 l + k), spins to replica slots (see
      * crbm_get_permutation). */
     int32_t swap_every;

@@ -284,6 +284,7 @@ SweepArgs fill_sweep_args(const crbm_ctx* ctx, int chunk) {
     a.segmask = ctx->d.segmask;
     a.n_words = ctx->n_words;
     a.n_chains_padded = ctx->n_words * 32;
+    a.n_chains = ctx->n_chains;
     a.key0 = static_cast<uint32_t>(ctx->seed);
     a.key1 = static_cast<uint32_t>(ctx->seed >> 32);
     for (int r = 0; r < 10; ++r) {  // Philox key schedule (Weyl increments)
@@ -332,12 +333,11 @@ int crbm_create(crbm_ctx** out, const crbm_params* p) {
         return fail(nullptr, CRBM_EINVAL, "unknown rng");
     }
     g.bitplane = p->rng == CRBM_RNG_BITPLANE ? 1 : 0;
-    if (g.bitplane && (!g.canonical || g.paper || p->sq_every > 0 ||
-                       (p->swap_every > 0 && p->layout == CRBM_LAYOUT_STREAM))) {
+    if (g.bitplane && (!g.canonical || g.paper || p->sq_every > 0)) {
         delete ctx;
         return fail(nullptr, CRBM_EUNSUPPORTED,
-                    "bit-plane uniforms need the ten SS filters on an even periodic lattice, exact precision, "
-                    "no correlations, and the SMEM layout for replica exchange");
+                    "bit-plane uniforms need the ten SS filters on an even periodic lattice, exact precision and "
+                    "no correlations");
     }
     // AUTO: shared memory when the lattice, its hidden words and the tables fit
     // in one CTA's 227 KB, else the streamed layout (SS filters, even periodic L)
@@ -362,6 +362,10 @@ int crbm_create(crbm_ctx** out, const crbm_params* p) {
         delete ctx;
         return fail(nullptr, CRBM_EUNSUPPORTED,
                     "the streamed layout serves the ten SS filters on an even, periodic lattice");
+    }
+    if (ctx->layout == CRBM_LAYOUT_STREAM && g.bitplane && p->swap_every > 0) {
+        delete ctx;
+        return fail(nullptr, CRBM_EUNSUPPORTED, "bit-plane uniforms take replica exchange in the SMEM layout only");
     }
     if (ctx->layout == CRBM_LAYOUT_STREAM && p->sq_every > 0) {
         delete ctx;
@@ -431,10 +435,9 @@ int crbm_create(crbm_ctx** out, const crbm_params* p) {
             delete ctx;
             return fail(nullptr, CRBM_EUNSUPPORTED, "replica exchange needs one field on every column (no h_odd)");
         }
-        if (p->n_chains % 32 != 0 || ctx->layout != CRBM_LAYOUT_SMEM) {
+        if (p->n_chains % 32 != 0) {
             delete ctx;
-            return fail(nullptr, p->n_chains % 32 ? CRBM_EINVAL : CRBM_EUNSUPPORTED,
-                        "replica exchange needs n_chains % 32 == 0 and the SMEM layout");
+            return fail(nullptr, CRBM_EINVAL, "replica exchange needs n_chains % 32 == 0");
         }
         const int nwl = p->n_chains / 32;
         const int64_t e_max = 2 * (2047LL * g.n_real_bonds[0] + 2047LL * g.n_real_bonds[1] + 2047LL * g.N);

@@ -210,6 +210,7 @@ struct SweepArgs {
     const uint32_t* segmask;
     int n_words;
     int n_chains_padded;
+    int n_chains;  // real chains (replica-exchange ladders: n_chains / 32)
     uint32_t key0, key1;
     uint32_t rk[20];      // Philox round keys: rk[2r] = key0 + r W0, rk[2r+1] = key1 + r W1
     uint32_t t0;          // first global sweep index of this launch

@@ -31,6 +31,16 @@ constexpr int kStreamVisThreads = CRBM_STREAM_VIS_THREADS;
 __device__ __forceinline__ size_t vidx(int w, int N, int s) {
     return (static_cast<size_t>(w >> 1) * N + s) * 2 + (w & 1);
 }
+
+// With replica exchange a lane (replica slot) reads the threshold column of
+// the rung it holds: s_bos[slot] = rung, from the word's slot-of-rung array.
+// Threads of warp 0 write it; the caller's next barrier publishes it.
+__device__ __forceinline__ void stage_rungs(const SweepArgs& a, int w, int* s_bos) {
+    if (threadIdx.x < 32) {
+        const int lane = static_cast<int>(threadIdx.x);
+        s_bos[a.swap_every > 0 ? __ldg(a.sob + static_cast<size_t>(w) * 32 + lane) : lane] = lane;
+    }
+}
 #ifndef CRBM_STREAM_MIN_BLOCKS
 #define CRBM_STREAM_MIN_BLOCKS 4
 #endif
@@ -129,6 +139,7 @@ __global__ void __launch_bounds__(kStreamThreads, CRBM_STREAM_MIN_BLOCKS) k_stre
     __shared__ uint32_t s_v[(2 * kTI + 1) * (2 * kTJ + 1)];
     __shared__ __align__(16) uint32_t s_h[kTI * kTJ * 32];
     __shared__ uint4 s_q[kTI * kTJ][2];  // per tile cell: hidden_call_words
+    __shared__ int s_bos[32];            // rung of each replica slot
     const Geometry& g = a.g;
     const int W = g.W, Wc = g.Wc;
     const int w = blockIdx.y;
@@ -139,8 +150,8 @@ __global__ void __launch_bounds__(kStreamThreads, CRBM_STREAM_MIN_BLOCKS) k_stre
     for (int x = threadIdx.x; x < kCanonTh; x += blockDim.x) s_th[x] = gt[x];
     constexpr int VS = 2 * kTJ + 1;
     stage_spin_tile(a, w, i0, j0, s_v);
+    stage_rungs(a, w, s_bos);
     const uint32_t chain = static_cast<uint32_t>(w) * 32u + lane;
-    const LaneConst lc = lane_const(lane, lane);
     const Round0Lane r0l = round0_lane(chain);
     const Round1Sweep rs = round1_sweep(r0l.hi ^ t ^ a.rk[0], a.rk);
     const int ni = min(kTI, W - i0), nj = min(kTJ, Wc - j0);
@@ -151,6 +162,7 @@ __global__ void __launch_bounds__(kStreamThreads, CRBM_STREAM_MIN_BLOCKS) k_stre
             hidden_call_words(static_cast<uint32_t>((i0 + li) * Wc + j0 + lj), a.rk, s_q[x][0], s_q[x][1]);
     }
     __syncthreads();
+    const LaneConst lc = lane_const(lane, s_bos[lane]);
     // warp = columns lj of the tile, cells walked down the column
     for (int lj = warp; lj < nj; lj += nwarp) {
         const uint32_t* v = s_v + 2 * lj;
@@ -178,6 +190,7 @@ __global__ void __launch_bounds__(kStreamVisThreads, CRBM_STREAM_VIS_MIN_BLOCKS)
     __shared__ __align__(16) uint32_t s_h[(kTI + 1) * (kTJ + 1) * 32];
     __shared__ uint32_t s_o[2 * kTI * 2 * kTJ];
     __shared__ uint4 s_q[kTI * kTJ];  // per tile cell: visible_call_words
+    __shared__ int s_bos[32];         // rung of each replica slot
     const Geometry& g = a.g;
     const int L = g.L, Lc = g.Lc, W = g.W, Wc = g.Wc, N = g.N;
     const int w = blockIdx.y;
@@ -191,8 +204,8 @@ __global__ void __launch_bounds__(kStreamVisThreads, CRBM_STREAM_VIS_MIN_BLOCKS)
         stage_hidden_halo<true>(a, w, i0, j0, s_h);
     else
         stage_hidden_halo<false>(a, w, i0, j0, s_h);
+    stage_rungs(a, w, s_bos);
     const uint32_t chain = static_cast<uint32_t>(w) * 32u + lane;
-    const LaneConst lc = lane_const(lane, lane);
     const Round0Lane r0l = round0_lane(chain);
     const Round1Sweep rs = round1_sweep(r0l.hi ^ t ^ a.rk[0], a.rk);
     constexpr int VO = 2 * kTJ;
@@ -205,6 +218,7 @@ __global__ void __launch_bounds__(kStreamVisThreads, CRBM_STREAM_VIS_MIN_BLOCKS)
         }
     }
     __syncthreads();
+    const LaneConst lc = lane_const(lane, s_bos[lane]);
     for (int lj = warp; lj < nj; lj += nwarp) {
         const uint32_t* ho = s_h + (HS + lj + 1) * 32 + lane;
         uint32_t* o = s_o + 2 * lj;
@@ -524,6 +538,38 @@ __global__ void k_stream_finalize(const SweepArgs a, int64_t meas, int64_t sweep
     }
 }
 
+// Post-sweep step with replica exchange: one warp per 32-chain half-word w
+// (a ladder), lane = slot for the counts and rung for the rest, exactly the
+// SMEM kernels' step (post_sweep_warp0): rung k's measurement from the slot
+// that holds it into row 32 w + k of the sums and series, then the
+// exchange round, and the new slot-of-rung array back to sob.  Half-words
+// past the last ladder (padding of the 64-chain groups) only clear their
+// counts.
+__global__ void __launch_bounds__(32) k_stream_post_pt(const SweepArgs a, int64_t meas, uint32_t t, int do_meas,
+                                                       int do_swap) {
+    __shared__ int s_cnt[96], s_sob[32], s_bos[32];
+    __shared__ int64_t s_acc[kNSum * 32];
+    const int w = blockIdx.x, lane = threadIdx.x;
+    int* cn = a.cnt + (static_cast<size_t>(w) * 32 + lane) * 3;
+    s_cnt[lane] = cn[0];
+    s_cnt[32 + lane] = cn[1];
+    s_cnt[64 + lane] = cn[2];
+    cn[0] = cn[1] = cn[2] = 0;
+    if (w >= a.n_chains / 32) return;
+    const size_t row = static_cast<size_t>(w) * 32 + lane;
+    const int sob = a.sob[row];
+    s_sob[lane] = sob;
+    s_bos[sob] = lane;
+    if (do_meas)
+        for (int x = 0; x < kNSum; ++x) s_acc[x * 32 + lane] = a.sums[row * kNSum + x];
+    __syncwarp();
+    post_sweep_warp0(a, s_cnt, s_sob, s_bos, lane, w, t, do_meas != 0, do_swap != 0, meas, s_acc);
+    __syncwarp();
+    if (do_meas)
+        for (int x = 0; x < kNSum; ++x) a.sums[row * kNSum + x] = s_acc[x * 32 + lane];
+    if (do_swap) a.sob[row] = s_sob[lane];
+}
+
 }  // namespace
 
 cudaError_t launch_sweep_stream(const SweepArgs& a, cudaStream_t st, int64_t* launches) {
@@ -543,11 +589,17 @@ cudaError_t launch_sweep_stream(const SweepArgs& a, cudaStream_t st, int64_t* la
             k_stream_visible<false><<<grid, kStreamVisThreads, 0, st>>>(a, t);
         }
         *launches += 2;
-        if (a.measure_every > 0 && (t + 1u) % static_cast<uint32_t>(a.measure_every) == 0u) {
+        const bool do_meas = a.measure_every > 0 && (t + 1u) % static_cast<uint32_t>(a.measure_every) == 0u;
+        const bool do_swap = a.swap_every > 0 && (t + 1u) % static_cast<uint32_t>(a.swap_every) == 0u;
+        if (do_meas || do_swap) {
             k_stream_count<<<grid, kStreamThreads, 0, st>>>(a);
-            k_stream_finalize<<<(a.n_chains_padded + 255) / 256, 256, 0, st>>>(a, meas, static_cast<int64_t>(t) + 1);
+            if (a.swap_every > 0)
+                k_stream_post_pt<<<a.n_words, 32, 0, st>>>(a, meas, t, do_meas ? 1 : 0, do_swap ? 1 : 0);
+            else
+                k_stream_finalize<<<(a.n_chains_padded + 255) / 256, 256, 0, st>>>(a, meas,
+                                                                                   static_cast<int64_t>(t) + 1);
             *launches += 2;
-            ++meas;
+            if (do_meas) ++meas;
         }
         const cudaError_t e = cudaGetLastError();
         if (e != cudaSuccess) return e;

@@ -30,11 +30,12 @@ def ladder(n_lad, lo=0.2, hi=10.0, J=1.0, Jp=1.5, h=1.0, jitter=None):
 
 
 def run_pt_pair(orc, L, n_lad, seed, splits, swap_every, measure_every, periodic=True,
-                jitter=None, series_len=0):
+                jitter=None, series_len=0, layout=crbm.CRBM_LAYOUT_AUTO, precision=crbm.CRBM_PRECISION_EXACT):
     params, cp = ladder(n_lad, jitter=jitter)
     n = 32 * n_lad
     s = crbm.Sampler(L, params, n, chain_param=cp, seed=seed, periodic=periodic,
-                     measure_every=measure_every, series_len=series_len, swap_every=swap_every)
+                     measure_every=measure_every, series_len=series_len, swap_every=swap_every,
+                     layout=layout, precision=precision)
     spins = orc.init_spins(L, np.arange(n, dtype=np.uint32), seed)
     sob = np.tile(np.arange(32, dtype=np.int32), (n_lad, 1))
     sums, oser = None, None
@@ -42,7 +43,7 @@ def run_pt_pair(orc, L, n_lad, seed, splits, swap_every, measure_every, periodic
     for k in splits:
         s.sweep(k)
         sums, ser = orc.run_pt(L, params, cp, spins, sob, seed, t, k, measure_every, swap_every,
-                               periodic=periodic, sums=sums, series_cap=series_len)
+                               periodic=periodic, sums=sums, series_cap=series_len, precision=precision)
         if ser is not None:
             oser = ser if oser is None else np.where(ser != 0, ser, oser)
         t += k
@@ -61,6 +62,20 @@ def test_tempering_bitexact(orc, L, periodic, n_lad):
     s, sob = run_pt_pair(orc, L, n_lad, 40 + L, splits=[7, 23], swap_every=3, measure_every=2,
                          periodic=periodic, series_len=15)
     assert (sob != np.arange(32)).any()
+
+
+@pytest.mark.parametrize("L,n_lad,precision", [(8, 2, 0), (12, 3, 0), (34, 1, 0), (12, 2, 1)])
+def test_tempering_streamed_bitexact(orc, L, n_lad, precision):
+    """Replica exchange in the streamed layout: a ladder is a 32-chain half of
+    a 64-chain group (an odd ladder count leaves a padding half-word), the
+    kernels read each slot's rung column, and the post-sweep step (counts,
+    per-rung measurement, exchange round) runs as one warp per ladder; spins
+    per slot, the permutation and per-rung sums and series against the
+    oracle, in exact and paper precision, over ragged 16 x 16-cell tiles."""
+    s, _ = run_pt_pair(orc, L, n_lad, 40 + L + n_lad, splits=[7, 13], swap_every=2, measure_every=3,
+                       series_len=8, layout=crbm.CRBM_LAYOUT_STREAM,
+                       precision=crbm.CRBM_PRECISION_PAPER if precision else crbm.CRBM_PRECISION_EXACT)
+    assert s.layout == crbm.CRBM_LAYOUT_STREAM
 
 
 def test_tempering_per_ladder_betas(orc):
@@ -89,7 +104,7 @@ def test_tempering_validation():
     for kw, code in ((dict(params=bad_beta, n_chains=32), crbm.CRBM_EINVAL),
                      (dict(params=bad_h, n_chains=32), crbm.CRBM_EINVAL),
                      (dict(params=params, n_chains=31, chain_param=cp[:31]), crbm.CRBM_EINVAL),
-                     (dict(params=params, n_chains=32, layout=crbm.CRBM_LAYOUT_STREAM),
+                     (dict(params=params, n_chains=32, layout=crbm.CRBM_LAYOUT_STREAM, rng=crbm.CRBM_RNG_BITPLANE),
                       crbm.CRBM_EUNSUPPORTED)):
         kw.setdefault("chain_param", cp)
         with pytest.raises(crbm.CrbmError) as e:

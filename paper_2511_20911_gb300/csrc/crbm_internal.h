@@ -210,7 +210,6 @@ struct SweepArgs {
     const uint32_t* segmask;
     int n_words;
     int n_chains_padded;
-    int n_chains;  // real chains (replica-exchange ladders: n_chains / 32)
     uint32_t key0, key1;
     uint32_t rk[20];      // Philox round keys: rk[2r] = key0 + r W0, rk[2r+1] = key1 + r W1
     uint32_t t0;          // first global sweep index of this launch
@@ -219,6 +218,9 @@ struct SweepArgs {
     int64_t meas0;        // measurements recorded before this launch (series index)
     int series_len;
     int sq_every;         // 0 = never
+    // (kept last: the fields above keep the offsets the sweep kernels were tuned with; rk is
+    // read as 8-byte constant pairs)
+    int n_chains;         // real chains (replica-exchange ladders: n_chains / 32)
 };
 
 // Host model helpers (crbm_host.cpp): Q.4 rounding of a coupling, and the

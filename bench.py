@@ -827,17 +827,17 @@ def measure_sampler(args, workload, rank, ws, with_e2e=True, sq_every=0):
 
     e2e = None
     if with_e2e:
-        # end to end through the C ABI with host buffers: set spins (H2D),
-        # sweep, read observables (D2H), every step
-        spins_h = s.get_spins()
-        obs_h = np.zeros((w["n_chains"], crbm.CRBM_NSUM), np.int64)
+        # end to end through the C ABI with host buffers in pinned memory: set
+        # spins (H2D), sweep, read observables (D2H), every step
+        spins_h = torch.from_numpy(s.get_spins()).pin_memory().numpy()
+        obs_h = torch.zeros((w["n_chains"], crbm.CRBM_NSUM), dtype=torch.int64).pin_memory().numpy()
         torch.cuda.synchronize()
         t0 = time.perf_counter()
         e2e_steps = max(1, K // 2)
         for k in range(e2e_steps):
             s.set_spins(spins_h)
             s.sweep(S)
-            obs_h[:] = s.observables()
+            s.observables(out=obs_h)
         e2e_t = time.perf_counter() - t0
         e2e = {"value": w["n_chains"] * w["L"] ** 2 * S * e2e_steps * ws / e2e_t, "unit": UNIT,
                "h2d_bytes_per_step": int(spins_h.nbytes), "d2h_bytes_per_step": int(obs_h.nbytes)}

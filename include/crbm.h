@@ -223,7 +223,10 @@ int crbm_structure_factor(crbm_ctx* ctx, double* out, size_t n_out);
 /* Zero every accumulator (sums, series, correlations). */
 int crbm_reset_observables(crbm_ctx* ctx);
 
-/* Spins as int8 +-1, host array [n_chains][L][L]. */
+/* Spins as int8 +-1, host array [n_chains][L][L] (pinned host memory makes
+ * the copies direct).  crbm_set_spins checks the values on the device and
+ * sets the chains only when every one is +1 or -1 (else CRBM_EINVAL, chains
+ * unchanged).  Both synchronise the stream. */
 int crbm_get_spins(crbm_ctx* ctx, int8_t* out, size_t n_out);
 int crbm_set_spins(crbm_ctx* ctx, const int8_t* in, size_t n_in);
 

@@ -238,8 +238,13 @@ class Sampler:
     def layout(self):
         return int(self._lib.crbm_layout(self._ctx))
 
-    def observables(self):
-        out = np.zeros((self.n_chains, CRBM_NSUM), np.int64)
+    def observables(self, out=None):
+        """Per-chain sums [n_chains][CRBM_NSUM]; `out` (C-contiguous int64 of that
+        shape, e.g. in pinned memory) receives them in place when given."""
+        if out is None:
+            out = np.zeros((self.n_chains, CRBM_NSUM), np.int64)
+        elif out.dtype != np.int64 or out.shape != (self.n_chains, CRBM_NSUM) or not out.flags.c_contiguous:
+            raise ValueError("out must be a C-contiguous int64 array of shape (n_chains, CRBM_NSUM)")
         _check(self._lib.crbm_observables(self._ctx, _ptr(out, ctypes.c_int64), out.size), self._ctx)
         return out
 

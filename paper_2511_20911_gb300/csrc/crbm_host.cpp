@@ -231,7 +231,7 @@ int dalloc(crbm_ctx* ctx, T*& ptr, size_t count) {
 void free_device(DeviceState& d) {
     void* ptrs[] = {d.v, d.tab, d.ctab, d.crec, d.sneg, d.gep, d.sums, d.series, d.corr,
                     d.seg, d.segmask, d.spins8, d.h, d.cnt, d.sob, d.swap_tab, d.swap_off,
-                    d.swap_len, d.wq, d.chain_bh, d.chain_q, d.sched, d.hit, d.hit_q};
+                    d.swap_len, d.wq, d.chain_bh, d.chain_q, d.sched, d.hit, d.hit_q, d.flag};
     for (void* p : ptrs)
         if (p) cudaFree(p);
     d = DeviceState{};
@@ -729,7 +729,7 @@ int crbm_create(crbm_ctx** out, const crbm_params* p) {
         (rc = dalloc(ctx, d.corr, p->sq_every > 0 ? static_cast<size_t>(p->n_params) * N : 1)) ||
         (rc = dalloc(ctx, d.seg, seg.size())) || (rc = dalloc(ctx, d.segmask, segmask.size())) ||
         (rc = dalloc(ctx, d.spins8, static_cast<size_t>(npad) * N)) ||
-        (rc = dalloc(ctx, d.sob, static_cast<size_t>(npad))) ||
+        (rc = dalloc(ctx, d.sob, static_cast<size_t>(npad))) || (rc = dalloc(ctx, d.flag, 1)) ||
         (rc = dalloc(ctx, d.sched, 4 + static_cast<size_t>(nw))) ||
         (rc = dalloc(ctx, d.swap_tab, swap_tab.size())) || (rc = dalloc(ctx, d.swap_off, swap_off.size())) ||
         (rc = dalloc(ctx, d.swap_len, swap_len.size())) || (rc = dalloc(ctx, d.wq, wq.size())) ||
@@ -928,14 +928,18 @@ int crbm_set_spins(crbm_ctx* ctx, const int8_t* in, size_t n_in) {
     if (!ctx || !in) return CRBM_EINVAL;
     const size_t need = static_cast<size_t>(ctx->n_chains) * ctx->g.N;
     if (n_in < need) return fail(ctx, CRBM_EINVAL, "input buffer too small");
-    for (size_t x = 0; x < need; ++x)
-        if (in[x] != 1 && in[x] != -1) return fail(ctx, CRBM_EINVAL, "spins must be +1 or -1");
+    // the values are checked on the device, and the spins packed only when all are +-1
+    int bad = 0;
     cudaError_t e = cudaMemcpyAsync(ctx->d.spins8, in, need, cudaMemcpyHostToDevice, ctx->stream);
-    if (e == cudaSuccess) e = launch_pack(ctx->g, ctx->d.spins8, ctx->d.v, ctx->n_words, ctx->stream);
-    ++ctx->launches;
+    if (e == cudaSuccess) e = launch_check_spins(ctx->d.spins8, need, ctx->d.flag, ctx->stream);
+    if (e == cudaSuccess)
+        e = launch_pack(ctx->g, ctx->d.spins8, ctx->d.v, ctx->n_words, ctx->d.flag, ctx->stream);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(&bad, ctx->d.flag, sizeof(int), cudaMemcpyDeviceToHost, ctx->stream);
+    ctx->launches += 2;
     // the caller may free `in` on return
     if (e == cudaSuccess) e = cudaStreamSynchronize(ctx->stream);
-    return e == cudaSuccess ? CRBM_OK : cuda_fail(ctx, e, "crbm_set_spins");
+    if (e != cudaSuccess) return cuda_fail(ctx, e, "crbm_set_spins");
+    return bad ? fail(ctx, CRBM_EINVAL, "spins must be +1 or -1") : CRBM_OK;
 }
 
 int crbm_get_permutation(crbm_ctx* ctx, int32_t* out, size_t n_out) {

@@ -181,6 +181,7 @@ struct DeviceState {
     int* sched = nullptr;         // persistent scheduler: [n_words + 4] word states (chunks done, held)
     int64_t* hit = nullptr;       // time to solution: [n_words * 32][2] target energy, first hitting sweep
     int32_t* hit_q = nullptr;     // [n_words * 32][4] Q.4 J, J', h of each chain's point
+    int* flag = nullptr;          // [1] crbm_set_spins: set when an input spin is not +-1
 };
 
 struct SweepArgs {
@@ -274,7 +275,11 @@ cudaError_t launch_philox_stream(uint32_t* sink, int n_blocks, int threads, int 
                                  uint32_t k1, cudaStream_t st);
 cudaError_t launch_unpack(const Geometry& g, const uint32_t* v, int8_t* out, int n_words,
                           cudaStream_t st);
-cudaError_t launch_pack(const Geometry& g, const int8_t* in, uint32_t* v, int n_words,
+// Sets *flag (zeroed first) when any of the n bytes at `in` is not +1 or -1.
+cudaError_t launch_check_spins(const int8_t* in, size_t n, int* flag, cudaStream_t st);
+// Packs the staged int8 spins into the packed words, unless skip is non-null
+// and *skip is set (an invalid input found by launch_check_spins).
+cudaError_t launch_pack(const Geometry& g, const int8_t* in, uint32_t* v, int n_words, const int* skip,
                         cudaStream_t st);
 
 }  // namespace crbm

@@ -48,7 +48,8 @@ __global__ void k_unpack(const Geometry g, const uint32_t* v, int8_t* out, int n
     }
 }
 
-__global__ void k_pack(const Geometry g, const int8_t* in, uint32_t* v, int n_words) {
+__global__ void k_pack(const Geometry g, const int8_t* in, uint32_t* v, int n_words, const int* skip) {
+    if (skip && *skip) return;
     const int lane = threadIdx.x & 31;
     const long long nw = static_cast<long long>(gridDim.x) * (blockDim.x >> 5);
     for (long long x = blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
@@ -59,6 +60,23 @@ __global__ void k_pack(const Geometry g, const int8_t* in, uint32_t* v, int n_wo
         const uint32_t b = __ballot_sync(0xffffffffu, val > 0);
         if (lane == 0) v[word_index(g.vil, static_cast<int>(word), g.N, s)] = b;
     }
+}
+
+// *flag = 1 when a byte of in[0 .. n) is neither +1 (0x01) nor -1 (0xFF):
+// four bytes per load (the staging buffer is 256-byte aligned), a byte is
+// valid iff its bits 1..7 all equal its bit 7 and its bit 0 is set.
+__global__ void k_check_spins(const int8_t* in, size_t n, int* flag) {
+    const size_t words = n / 4, stride = static_cast<size_t>(gridDim.x) * blockDim.x;
+    const uint32_t* w4 = reinterpret_cast<const uint32_t*>(in);
+    bool bad = false;
+    for (size_t x = blockIdx.x * static_cast<size_t>(blockDim.x) + threadIdx.x; x < words; x += stride) {
+        const uint32_t w = w4[x];
+        const uint32_t sign = (w >> 7) & 0x01010101u;      // bit 7 of each byte
+        bad |= w != ((sign * 0xFEu) | 0x01010101u);        // 0xFF where the sign is set, else 0x01
+    }
+    for (size_t x = 4 * words + blockIdx.x * static_cast<size_t>(blockDim.x) + threadIdx.x; x < n; x += stride)
+        bad |= in[x] != 1 && in[x] != -1;
+    if (__any_sync(0xffffffffu, bad) && (threadIdx.x & 31) == 0) *flag = 1;
 }
 
 __global__ void k_philox(const uint32_t* in, uint32_t* out, int n) {
@@ -133,11 +151,21 @@ cudaError_t launch_unpack(const Geometry& g, const uint32_t* v, int8_t* out, int
     return cudaGetLastError();
 }
 
-cudaError_t launch_pack(const Geometry& g, const int8_t* in, uint32_t* v, int n_words,
+cudaError_t launch_pack(const Geometry& g, const int8_t* in, uint32_t* v, int n_words, const int* skip,
                         cudaStream_t st) {
     const long long work = static_cast<long long>(n_words) * g.N;
     const int blocks = static_cast<int>((work + 7) / 8 < 152 * 64 ? (work + 7) / 8 : 152 * 64);
-    k_pack<<<blocks, 256, 0, st>>>(g, in, v, n_words);
+    k_pack<<<blocks, 256, 0, st>>>(g, in, v, n_words, skip);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_check_spins(const int8_t* in, size_t n, int* flag, cudaStream_t st) {
+    cudaError_t e = cudaMemsetAsync(flag, 0, sizeof(int), st);
+    if (e != cudaSuccess) return e;
+    const size_t words = n / 4;  // 4 spins per 32-bit load, the tail bytes one at a time
+    const size_t want = (words + 255) / 256 + 1;
+    const int blocks = static_cast<int>(want < 152 * 16 ? want : 152 * 16);
+    k_check_spins<<<blocks, 256, 0, st>>>(in, n, flag);
     return cudaGetLastError();
 }
 

@@ -211,6 +211,25 @@ def test_host_side_errors():
         s.set_spins(np.zeros((4, 6, 6), np.int8))
 
 
+def test_set_spins_checks_values_on_the_device():
+    """crbm_set_spins checks its input on the device (four bytes per load and
+    the tail one at a time) and packs only when every value is +1 or -1: an
+    invalid byte at the start, in the middle or in the tail is rejected with
+    CRBM_EINVAL and leaves the chains as they were."""
+    ok = dict(J=[1.0], Jp=[1.0], h=[0.5], beta=[1.0])
+    s = crbm.Sampler(5, ok, 3, periodic=False, seed=4)      # 75 spin bytes: 18 words and a 3-byte tail
+    before = s.get_spins()
+    for pos, val in ((0, 0), (37, 2), (74, -3), (73, 127)):
+        bad = before.copy().reshape(-1)
+        bad[pos] = val
+        with pytest.raises(crbm.CrbmError) as e:
+            s.set_spins(bad.reshape(before.shape))
+        assert e.value.code == crbm.CRBM_EINVAL
+        assert np.array_equal(s.get_spins(), before), pos
+    s.set_spins(-before)
+    assert np.array_equal(s.get_spins(), -before)
+
+
 def test_device_memory_exhaustion_returns_enomem(orc):
     """A context whose device state exceeds the GPU's memory (L=4096 streamed,
     32768 chains: 69 GB of packed spins, then 550 GB of int8 staging) fails

@@ -32,12 +32,14 @@ namespace {
 using namespace dev;
 using namespace bp;
 
-constexpr int kBpMaxThreads = CRBM_SWEEP_MAX_THREADS;  // 64 registers a thread
+constexpr int kBpMaxThreads = CRBM_SWEEP_MAX_THREADS;  // largest CTA the launch takes
 
 // Persistent grid over (word, chunk of sweeps) items (claim_word): the node
 // records are staged once per CTA, then each claimed chunk runs the body.
+// At most 56 registers a thread, so that three CTAs of 12 warps (the shape
+// the L=18 grid tunes to) fit on an SM; CTAs of up to kBpMaxThreads threads.
 template <bool kSmemRec, bool kSwap>
-__global__ void __launch_bounds__(kBpMaxThreads) k_sweep_bitplane(const SweepArgs a, int chunk, int* state) {
+__global__ void __maxnreg__(56) k_sweep_bitplane(const SweepArgs a, int chunk, int* state) {
     extern __shared__ __align__(16) uint32_t smem[];
     __shared__ int s_word, s_chunk;
     const Geometry& g = a.g;

@@ -178,9 +178,11 @@ __device__ __forceinline__ void sweep_bitplane_body(const SweepArgs& a, const ui
         };
         const uint32_t* tv = s_tab + kBpVisPlanes;  // [count][J' bit][32]
         auto vis_planes = [&](const Vis& vn, const U4& q, uint32_t j, uint32_t& lt, uint32_t& eq) {
-            const uint32_t u[4] = {q.x, q.y, q.z, q.w};
-#pragma unroll
-            for (int i = 0; i < 4; ++i) bp::plane_step(u[i], bp::visible_plane(tv + 4u * j + i, vn.hp, vn.n4), lt, eq);
+            const uint4 T = bp::visible_planes(tv + 4u * j, vn.hp, vn.n4);
+            bp::plane_step(q.x, T.x, lt, eq);
+            bp::plane_step(q.y, T.y, lt, eq);
+            bp::plane_step(q.z, T.z, lt, eq);
+            bp::plane_step(q.w, T.w, lt, eq);
         };
         for (int base = warp * 32; base < N; base += nwarp * 32) {
             const int sx = base + lane;

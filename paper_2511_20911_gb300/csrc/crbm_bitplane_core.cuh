@@ -19,16 +19,22 @@ __device__ __forceinline__ void plane_step(uint32_t U, uint32_t T, uint32_t& lt,
     eq &= ~(T ^ U);
 }
 
+// Four consecutive threshold planes of one row: the planes of one Philox
+// call, read with one 16-byte shared-memory load (rows start on a 16-byte
+// boundary and calls on a multiple of four planes).
+__device__ __forceinline__ uint4 planes4(const uint32_t* p) { return *reinterpret_cast<const uint4*>(p); }
+
 // The four planes of one Philox call of a hidden node: P, M select the chains
 // with m = 2 and m = -2, tb points at the call's first plane of the m = -2 row
 // (m = 2 row 64 words further); Z0 = the chains with m = 0 on the first call
 // (their threshold 2^31 has only its top plane set), 0 on later calls.
 __device__ __forceinline__ void hidden_planes(const U4& q, const uint32_t* tb, uint32_t P, uint32_t M, uint32_t Z0,
                                               uint32_t& lt, uint32_t& eq) {
-    plane_step(q.x, (P & tb[64]) | (M & tb[0]) | Z0, lt, eq);
-    plane_step(q.y, (P & tb[65]) | (M & tb[1]), lt, eq);
-    plane_step(q.z, (P & tb[66]) | (M & tb[2]), lt, eq);
-    plane_step(q.w, (P & tb[67]) | (M & tb[3]), lt, eq);
+    const uint4 tm = planes4(tb), tp = planes4(tb + 64);
+    plane_step(q.x, (P & tp.x) | (M & tm.x) | Z0, lt, eq);
+    plane_step(q.y, (P & tp.y) | (M & tm.y), lt, eq);
+    plane_step(q.z, (P & tp.z) | (M & tm.z), lt, eq);
+    plane_step(q.w, (P & tp.w) | (M & tm.w), lt, eq);
 }
 
 // Count of set bits among h0..h3 per chain, c0 + 2 c1 + 4 c2, bit-sliced.
@@ -41,13 +47,19 @@ __device__ __forceinline__ Count4 count4(uint32_t h0, uint32_t h1, uint32_t h2, 
     return {s01 ^ s23, a01 ^ a23 ^ cy, (a01 & a23) | (cy & (a01 | a23))};
 }
 
-// The threshold plane of a spin: tb points at the plane in the [count][J' bit]
-// rows (32 words apart); hp is the J' bit, n the count of the J incidences.
-// A mux tree: the J' bit, then count bits 0, 1, 2.
-__device__ __forceinline__ uint32_t visible_plane(const uint32_t* tb, uint32_t hp, const Count4& n) {
-    auto sel = [&](int c) { return (hp & tb[(2 * c + 1) * 32]) | (~hp & tb[2 * c * 32]); };
-    const uint32_t m01 = (n.c0 & sel(1)) | (~n.c0 & sel(0)), m23 = (n.c0 & sel(3)) | (~n.c0 & sel(2));
-    return (n.c2 & sel(4)) | (~n.c2 & ((n.c1 & m23) | (~n.c1 & m01)));
+// The four threshold planes of one Philox call of a spin: tb points at the
+// call's first plane in the [count][J' bit] rows (32 words apart); hp is the
+// J' bit, n the count of the J incidences.  A mux tree per plane: the J' bit,
+// then count bits 0, 1, 2 (a count of 4 has bits 0 and 1 clear).
+__device__ __forceinline__ uint4 visible_planes(const uint32_t* tb, uint32_t hp, const Count4& n) {
+    auto mux = [](uint32_t s, const uint4& x1, const uint4& x0) {
+        return make_uint4((s & x1.x) | (~s & x0.x), (s & x1.y) | (~s & x0.y), (s & x1.z) | (~s & x0.z),
+                          (s & x1.w) | (~s & x0.w));
+    };
+    auto sel = [&](int c) { return mux(hp, planes4(tb + (2 * c + 1) * 32), planes4(tb + 2 * c * 32)); };
+    const uint4 m01 = mux(n.c0, sel(1), sel(0));
+    const uint4 m23 = mux(n.c0, sel(3), sel(2));
+    return mux(n.c2, sel(4), mux(n.c1, m23, m01));
 }
 
 // 32 x 32 bit transpose across a warp: lane c returns the word whose bit l is

@@ -34,6 +34,8 @@ constexpr uint32_t kTagBitplane = 256u;
 // [2 classes][3 m = -2, 0, 2][32 planes] hidden, [5 counts][2 J' bits][32
 // planes] visible, [2] chains whose class coupling has a negative sign.
 constexpr int kBpHidPlanes = 0, kBpVisPlanes = 192, kBpFlip = 512, kBpTab = 516;
+static_assert(kBpHidPlanes % 4 == 0 && kBpVisPlanes % 4 == 0 && kBpTab % 4 == 0 && (kNSum * 64) % 4 == 0,
+              "the sweeps read four threshold planes with one 16-byte load");
 
 // Canonical fast-path tables per packed word: hidden [2 cls][4 idx][32 lanes]
 // then visible [4 spin positions][32 idx][32 lanes] (see crbm_canon.cu).

@@ -249,7 +249,7 @@ __global__ void __launch_bounds__(kStreamVisThreads, CRBM_STREAM_VIS_MIN_BLOCKS)
 // hidden words out.
 __global__ void __launch_bounds__(kStreamThreads) k_stream_bp_hidden(const SweepArgs a, uint32_t t) {
     constexpr int kCap = kTI * kTJ * 10 / 4;  // straggler list: a quarter of the tile's nodes
-    __shared__ uint32_t s_tab[kBpTab];
+    __shared__ __align__(16) uint32_t s_tab[kBpTab];
     __shared__ uint32_t s_v[(2 * kTI + 1) * (2 * kTJ + 1)];
     __shared__ uint32_t s_h[kTI * kTJ * 10];
     __shared__ uint2 s_list[kCap];
@@ -348,7 +348,7 @@ __global__ void __launch_bounds__(kStreamThreads) k_stream_bp_hidden(const Sweep
 // the row above and the column to the left (wrapped) in, new spins out.
 __global__ void __launch_bounds__(kStreamVisThreads, CRBM_STREAM_MIN_BLOCKS) k_stream_bp_visible(const SweepArgs a, uint32_t t) {
     constexpr int HS = kTJ + 1;
-    __shared__ uint32_t s_tab[kBpTab];
+    __shared__ __align__(16) uint32_t s_tab[kBpTab];
     __shared__ uint32_t s_h[(kTI + 1) * HS * 10];
     __shared__ uint32_t s_o[2 * kTI * 2 * kTJ];
     constexpr int kCap = 2 * kTI * 2 * kTJ / 4;  // straggler list: a quarter of the tile's spins
@@ -426,9 +426,11 @@ __global__ void __launch_bounds__(kStreamVisThreads, CRBM_STREAM_MIN_BLOCKS) k_s
                    bp::count4(h0, h1, h2, h3), round2_cell(rs.hik ^ static_cast<uint32_t>(pc)), R * VO + C};
     };
     auto planes = [&](const Vis& vn, const U4& q, uint32_t j, uint32_t& lt, uint32_t& eq) {
-        const uint32_t u[4] = {q.x, q.y, q.z, q.w};
-#pragma unroll
-        for (int i = 0; i < 4; ++i) bp::plane_step(u[i], bp::visible_plane(tv + 4u * j + i, vn.hp, vn.n4), lt, eq);
+        const uint4 T = bp::visible_planes(tv + 4u * j, vn.hp, vn.n4);
+        bp::plane_step(q.x, T.x, lt, eq);
+        bp::plane_step(q.y, T.y, lt, eq);
+        bp::plane_step(q.z, T.z, lt, eq);
+        bp::plane_step(q.w, T.w, lt, eq);
     };
     for (int base = warp * 32; base < nn; base += nwarp * 32) {
         const int sx = base + lane;

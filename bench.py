@@ -53,8 +53,8 @@ MEASURED_TRAFFIC = {
     "stream": (56.74e6 + 392.31e6 + 454.82e6 + 48.83e6, "per sweep (two launches); profiles/k_stream_L384.md"),
     "grid_paper": (8.78e6 + 0.83e6, "per launch; profiles/k_sweep_canon_persistent_L18_grid_paper.md"),
     "stream_paper": (56.76e6 + 390.29e6 + 454.76e6 + 45.71e6, "per sweep (two launches); profiles/k_stream_L384.md"),
-    "grid_bitplane": (2.53e6 + 0.56e6, "per launch; profiles/k_sweep_bitplane_L18_grid.md"),
-    "stream_bitplane": (56.86e6 + 82.62e6 + 141.80e6 + 29.18e6, "per sweep (two launches); profiles/k_stream_bp_L384.md"),
+    "grid_bitplane": (2.51e6 + 0.72e6, "per launch; profiles/k_sweep_bitplane_L18_grid.md"),
+    "stream_bitplane": (56.98e6 + 83.06e6 + 141.93e6 + 29.42e6, "per sweep (two launches); profiles/k_stream_bp_L384.md"),
 }
 
 
@@ -113,6 +113,9 @@ def parse():
     ap.add_argument("--rng", default="lane", choices=["lane", "bitplane"],
                     help="bitplane: uniforms from bit-plane words shared by the 32 chains of a word, compared "
                          "most significant bit first (grid workload)")
+    ap.add_argument("--warps", type=int, default=0,
+                    help="grid workload: CTAs of this many warps instead of the autotuner's choice (0), so that "
+                         "a profile captures one known shape")
     args = ap.parse_args()
     if args.rng == "bitplane" and (args.workload not in ("grid", "stream", "phase") or args.precision != "exact"):
         ap.error("--rng bitplane runs the grid, stream and phase workloads in exact precision")
@@ -773,11 +776,25 @@ def measure_sampler(args, workload, rank, ws, with_e2e=True, sq_every=0):
     layout = crbm.CRBM_LAYOUT_SMEM if workload == "grid" else crbm.CRBM_LAYOUT_STREAM
     paper = args.precision == "paper"
     bitplane = args.rng == "bitplane"
-    s = crbm.Sampler(w["L"], w["params"], w["n_chains"], chain_param=w["chain_param"], seed=w["seed"],
-                     measure_every=args.measure_every, series_len=n_meas, layout=layout, sq_every=sq_every,
-                     precision=crbm.CRBM_PRECISION_PAPER if paper else crbm.CRBM_PRECISION_EXACT,
-                     rng=crbm.CRBM_RNG_BITPLANE if bitplane else crbm.CRBM_RNG_LANE)
-    tuned_warps = s.autotune(200) if workload == "grid" else None  # CTA shape, on scratch copies
+    fixed_warps = args.warps if workload == "grid" and args.warps > 0 else 0
+    env_warps = os.environ.get("CRBM_WARPS")
+    if fixed_warps:
+        os.environ["CRBM_WARPS"] = str(fixed_warps)  # read when the context is created
+    try:
+        s = crbm.Sampler(w["L"], w["params"], w["n_chains"], chain_param=w["chain_param"], seed=w["seed"],
+                         measure_every=args.measure_every, series_len=n_meas, layout=layout, sq_every=sq_every,
+                         precision=crbm.CRBM_PRECISION_PAPER if paper else crbm.CRBM_PRECISION_EXACT,
+                         rng=crbm.CRBM_RNG_BITPLANE if bitplane else crbm.CRBM_RNG_LANE)
+    finally:
+        if fixed_warps:
+            if env_warps is None:
+                del os.environ["CRBM_WARPS"]
+            else:
+                os.environ["CRBM_WARPS"] = env_warps
+    if fixed_warps:
+        assert s.warps == fixed_warps, (s.warps, fixed_warps)
+    # CTA shape, on scratch copies
+    tuned_warps = s.autotune(200) if workload == "grid" and not fixed_warps else None
     stream = torch.cuda.current_stream()
     flush = torch.empty(256 * 1024 * 1024, dtype=torch.uint8, device="cuda")
     for _ in range(W):
@@ -877,6 +894,8 @@ def measure_sampler(args, workload, rank, ws, with_e2e=True, sq_every=0):
         cfg["sq_every"] = sq_every
     if tuned_warps:
         cfg["warps_per_cta_autotuned"] = tuned_warps
+    if fixed_warps:
+        cfg["warps_per_cta"] = fixed_warps
     out = {
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws, "steps": K, "warmup": W,
         "ms_per_step": t_total / K * 1e3, "higher_is_better": True, "scaling": "weak",

@@ -243,8 +243,8 @@ int crbm_get_permutation(crbm_ctx* ctx, int32_t* out, size_t n_out);
 /* Which layout the context runs (CRBM_LAYOUT_SMEM or CRBM_LAYOUT_STREAM). */
 int crbm_layout(const crbm_ctx* ctx);
 
-/* Autotuner: time the CTA shapes of the SMEM sweep (2..16 warps per packed
- * word) for probe_sweeps sweeps each on scratch copies of the context's
+/* Autotuner: time the CTA shapes of the SMEM sweep (2..32 warps per CTA; at
+ * most 16 for the generic kernel, at most one per cell) for probe_sweeps sweeps each on scratch copies of the context's
  * spins (its chains, counters and observables are untouched), keep the
  * fastest for this context and append it to the cache file
  * ($CRBM_AUTOTUNE_CACHE, default $HOME/.cache/crbm_autotune.txt), which

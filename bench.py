@@ -114,8 +114,8 @@ def parse():
                     help="bitplane: uniforms from bit-plane words shared by the 32 chains of a word, compared "
                          "most significant bit first (grid workload)")
     ap.add_argument("--warps", type=int, default=0,
-                    help="grid workload: CTAs of this many warps instead of the autotuner's choice (0), so that "
-                         "a profile captures one known shape")
+                    help="grid and batch workloads: CTAs of this many warps instead of the autotuners' choice "
+                         "(0), so that a profile captures one known shape")
     args = ap.parse_args()
     if args.rng == "bitplane" and (args.workload not in ("grid", "stream", "phase") or args.precision != "exact"):
         ap.error("--rng bitplane runs the grid, stream and phase workloads in exact precision")
@@ -137,7 +137,8 @@ def dist_setup(args):
 
 
 class ClockSampler:
-    """nvidia-smi clock/throttle samples every 200 ms while running."""
+    """nvidia-smi clock/throttle samples every 50 ms while running (a timed region of a quarter of a
+    second still gets several)."""
 
     Q = ("clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.hw_slowdown,"
          "clocks_event_reasons.hw_thermal_slowdown,clocks_event_reasons.sw_thermal_slowdown,"
@@ -149,7 +150,7 @@ class ClockSampler:
     def __enter__(self):
         try:
             self.proc = subprocess.Popen(["nvidia-smi", "-i", str(self.index), f"--query-gpu={self.Q}",
-                                          "--format=csv,noheader,nounits", "-lms", "200"],
+                                          "--format=csv,noheader,nounits", "-lms", "50"],
                                          stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
             self.t = threading.Thread(target=self._read, daemon=True)
             self.t.start()
@@ -500,19 +501,33 @@ def run_batch(args, rank, ws, quiet=False):
     S = args.sweeps_per_step if args.workload == "batch" else DEFAULT_SWEEPS["batch"]
     K, W = args.steps, args.warmup
     members = []
-    for sp in specs:
-        sp = dict(sp, seed=replica_seed(sp["seed"], rank), measure_every=args.measure_every)
-        m = crbm.Sampler(**sp)
-        m.autotune(50)
-        members.append(m)
+    env_warps = os.environ.get("CRBM_WARPS")
+    if args.warps > 0:
+        os.environ["CRBM_WARPS"] = str(args.warps)  # every member, read when it is created
+    try:
+        for sp in specs:
+            sp = dict(sp, seed=replica_seed(sp["seed"], rank), measure_every=args.measure_every)
+            m = crbm.Sampler(**sp)
+            if args.warps <= 0:
+                m.autotune(50)
+            members.append(m)
+    finally:
+        if args.warps > 0:
+            if env_warps is None:
+                del os.environ["CRBM_WARPS"]
+            else:
+                os.environ["CRBM_WARPS"] = env_warps
     batch = crbm.Batch(members)
+    if args.warps <= 0:
+        batch.autotune(200)  # the batched launch's own CTA shape (members' state put back)
+    else:
+        assert batch.threads == 32 * args.warps, (batch.threads, args.warps)
     stream = torch.cuda.current_stream()
     flush = torch.empty(256 * 1024 * 1024, dtype=torch.uint8, device="cuda")
     for _ in range(W):
         batch.sweep(S)
     torch.cuda.synchronize()
     ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(K)]
-    l0 = sum(m.launch_count for m in members)
     if ws > 1:
         torch.distributed.barrier()
     with ClockSampler(torch.cuda.current_device()) as clk:
@@ -544,7 +559,8 @@ def run_batch(args, rank, ws, quiet=False):
                                   "geometric beta in [0.2,10], J'/J=1.5, h=1, swaps every 10 sweeps, "
                                   "one graph-captured launch per step",
                       "n_chains": sum(sp["n_chains"] for sp in specs), "sweeps_per_step": S,
-                      "threads_per_cta": batch.threads, "warps_tuned": [m.warps for m in members],
+                      "threads_per_cta": batch.threads, "threads_autotuned": args.warps <= 0,
+                      "warps_tuned": [m.warps for m in members],
                       "l2": "flushed between steps (256 MiB write outside the step events)",
                       "parallelism": f"replicas x{ws}"},
            "sweeps_per_s": S * K / t_total,
@@ -552,7 +568,8 @@ def run_batch(args, rank, ws, quiet=False):
            "e2e": {"value": per_sweep * S / e2e_t, "unit": UNIT,
                    "h2d_bytes_per_step": int(sum(h.nbytes for h in host)),
                    "d2h_bytes_per_step": int(sum(o.nbytes for o in obs))},
-           "gpu_launches": int(sum(m.launch_count for m in members) - l0),
+           # each step replays one captured graph of two kernels: the batched sweep and the clock update
+           "gpu_launches": 2 * K,
            "roofline": {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "Tops/s",
                         "frac": achieved / peak, "traffic": None}}
     for m in members:

@@ -304,6 +304,16 @@ int crbm_batch_create(crbm_batch** out, crbm_ctx* const* ctxs, int32_t n_ctx);
 /* Asynchronous on the members' stream.  n_sweeps in 0..2^20. */
 int crbm_batch_sweep(crbm_batch* batch, int64_t n_sweeps);
 int crbm_batch_threads(const crbm_batch* batch);
+/* Batch autotuner: time the batched launch with CTAs of 8, 12, ..., 32 warps
+ * (the shapes whose clusters can be resident) for probe_sweeps sweeps each
+ * and keep the fastest for this batch.  The members' chains, counters,
+ * observables, series, correlations, replica permutations and first-hit
+ * records are checkpointed to host memory first and put back after every
+ * probe, so a tuned batch continues bit-identically.  Synchronises the
+ * stream.  best_threads (threads per CTA) may be NULL.  Errors: CRBM_EINVAL
+ * (probe_sweeps outside 1..100000, or a member's 32-bit sweep counter would
+ * overflow), CRBM_ECUDA (the shape in use before the call is kept). */
+int crbm_batch_autotune(crbm_batch* batch, int64_t probe_sweeps, int32_t* best_threads);
 /* Cluster size C of the batched launch (1: no clusters, no word split). */
 int crbm_batch_cluster(const crbm_batch* batch);
 /* Message for the last failed call on batch (or crbm_batch_create if NULL). */

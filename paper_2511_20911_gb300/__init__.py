@@ -34,7 +34,7 @@ ABI_FUNCTIONS = (
     "crbm_series", "crbm_correlations", "crbm_structure_factor", "crbm_reset_observables",
     "crbm_get_spins", "crbm_set_spins", "crbm_get_tables", "crbm_get_permutation", "crbm_layout",
     "crbm_launch_count", "crbm_autotune", "crbm_warps", "crbm_set_targets", "crbm_first_hits", "crbm_batch_create", "crbm_batch_sweep",
-    "crbm_batch_threads", "crbm_batch_cluster", "crbm_batch_last_error", "crbm_batch_destroy",
+    "crbm_batch_threads", "crbm_batch_autotune", "crbm_batch_cluster", "crbm_batch_last_error", "crbm_batch_destroy",
     "crbm_proposal_create", "crbm_proposal_destroy", "crbm_proposal_set_weights",
     "crbm_proposal_get_weights", "crbm_proposal_train", "crbm_proposal_loss_grad",
     "crbm_proposal_pass", "crbm_sweep_mixed", "crbm_sweep_mixed_every", "crbm_proposal_inspect",
@@ -104,6 +104,7 @@ def load_library(path: str | None = None):
         "crbm_batch_create": (c.c_int, [c.POINTER(vp), c.POINTER(vp), c.c_int32]),
         "crbm_batch_sweep": (c.c_int, [vp, c.c_int64]),
         "crbm_batch_threads": (c.c_int, [vp]),
+        "crbm_batch_autotune": (c.c_int, [vp, c.c_int64, c.POINTER(c.c_int32)]),
         "crbm_batch_cluster": (c.c_int, [vp]),
         "crbm_set_targets": (c.c_int, [vp, c.POINTER(c.c_int64), c.c_int32]),
         "crbm_first_hits": (c.c_int, [vp, c.POINTER(c.c_int64), c.c_size_t]),
@@ -351,6 +352,15 @@ class Batch:
     @property
     def threads(self):
         return int(self._lib.crbm_batch_threads(self._b))
+
+    def autotune(self, probe_sweeps=200):
+        """Time the batched launch's CTA shapes (crbm_batch_autotune; the
+        members' state is put back); returns the threads per CTA kept."""
+        best = ctypes.c_int32(0)
+        rc = self._lib.crbm_batch_autotune(self._b, int(probe_sweeps), ctypes.byref(best))
+        if rc != CRBM_OK:
+            raise CrbmError(rc, (self._lib.crbm_batch_last_error(self._b) or b"").decode())
+        return best.value
 
     @property
     def cluster(self):

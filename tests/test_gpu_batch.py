@@ -164,3 +164,58 @@ def test_autotune_keeps_chains_and_writes_cache(tmp_path, monkeypatch):
     assert text.strip().endswith(f" {w}")
     c = make(spec)                          # same shape on the same GPU: taken from the cache
     assert c.warps == w
+
+
+def test_batch_autotune_keeps_state():
+    """The batch autotuner probes CTA shapes on the members' own state and puts
+    it back: spins, counters, sums, series, correlations, permutations, launch
+    counts and first-hit records (targets set just before, so the probes do
+    record hits) are as before, and the tuned batch continues bit-identically
+    to twins advanced on their own."""
+    specs = members()
+    batched = [make(s) for s in specs]
+    twins = [make(s) for s in specs]
+    batch = crbm.Batch(batched)
+    batch.sweep(6)
+    for t in twins:
+        t.sweep(6)
+    big = np.full(len(specs[0]["params"]["J"]), 10 ** 9, np.int64)   # reached at the next measurement
+    batched[0].set_targets(big)
+    twins[0].set_targets(big)
+    launches = [m.launch_count for m in batched]
+    threads = batch.autotune(20)
+    assert threads in [32 * w for w in (8, 12, 16, 20, 24, 28, 32)] and batch.threads == threads
+    assert [m.launch_count for m in batched] == launches
+    assert (batched[0].first_hits() == -1).all()
+    for a, b in zip(batched, twins):
+        same(a, b)
+    batch.sweep(5)
+    for t in twins:
+        t.sweep(5)
+    for a, b in zip(batched, twins):
+        same(a, b)
+    hits = batched[0].first_hits()
+    assert np.array_equal(hits, twins[0].first_hits()) and (hits == 8).all()
+    with pytest.raises(crbm.CrbmError) as e:
+        batch.autotune(0)
+    assert e.value.code == crbm.CRBM_EINVAL
+    batch.close()
+
+
+def test_batch_sees_targets_set_after_capture():
+    """Targets set on a member after the batch captured its graph (the same
+    sweep count, so the graph would otherwise be replayed) are recorded."""
+    specs = members()[:2]
+    batched = [make(s) for s in specs]
+    twin = make(specs[0])
+    batch = crbm.Batch(batched)
+    batch.sweep(4)
+    twin.sweep(4)
+    big = np.full(len(specs[0]["params"]["J"]), 10 ** 9, np.int64)
+    batched[0].set_targets(big)
+    twin.set_targets(big)
+    batch.sweep(4)
+    twin.sweep(4)
+    hits = batched[0].first_hits()
+    assert np.array_equal(hits, twin.first_hits()) and (hits == 6).all()
+    batch.close()

@@ -92,6 +92,7 @@ __device__ __forceinline__ void sweep_bitplane_body(const SweepArgs& a, const ui
     const uint64_t pw = static_cast<uint64_t>(kPhiloxM1) * static_cast<uint32_t>(word);
     const uint32_t Yw = static_cast<uint32_t>(pw), hiW = static_cast<uint32_t>(pw >> 32) ^ a.rk[0];
 
+    EveryCounter every_meas(t0, a.measure_every), every_swap(t0, kSwap ? a.swap_every : 0);
     for (int it = 0; it < n_sweeps; ++it) {
         const uint32_t t = t0 + static_cast<uint32_t>(it);
         const Round1Sweep rs = round1_sweep(hiW ^ t, a.rk);  // round 1's sweep-wide product
@@ -218,8 +219,8 @@ __device__ __forceinline__ void sweep_bitplane_body(const SweepArgs& a, const ui
         }
         __syncthreads();
         if (threadIdx.x == 0) s_nst[1] = 0;
-        const bool do_meas = measuring && (t + 1u) % static_cast<uint32_t>(a.measure_every) == 0u;
-        const bool do_swap = kSwap && (t + 1u) % static_cast<uint32_t>(a.swap_every) == 0u;
+        const bool do_meas = every_meas.step();
+        const bool do_swap = kSwap && every_swap.step();
         if (do_meas || do_swap) {
             // per chain: anti-aligned J and J' filters, +1 spins.  A warp takes 32 nodes (spins) at
             // a time, lane = node, and a bit transpose turns their 32 chain words into one word per

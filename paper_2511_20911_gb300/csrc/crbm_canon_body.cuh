@@ -152,6 +152,7 @@ __device__ __forceinline__ void sweep_canon_body(const SweepArgs& a, int word, u
     const int rstep = nwarp * kCellRec;
     const int last_row = c_end - Wc, first_row_end = c_begin + Wc;
 
+    EveryCounter every_meas(t0, a.measure_every), every_swap(t0, a.swap_every), every_sq(t0, kCluster ? 0 : a.sq_every);
     for (int it = 0; it < n_sweeps; ++it) {
         const uint32_t t = t0 + static_cast<uint32_t>(it);
         const Round1Sweep rs = round1_sweep(r0l.hi ^ t ^ a.rk[0], a.rk);
@@ -232,8 +233,8 @@ __device__ __forceinline__ void sweep_canon_body(const SweepArgs& a, int word, u
         }
         body_sync<kCluster>();
         }
-        const bool do_meas = measuring && (t + 1u) % static_cast<uint32_t>(a.measure_every) == 0u;
-        const bool do_swap = a.swap_every > 0 && (t + 1u) % static_cast<uint32_t>(a.swap_every) == 0u;
+        const bool do_meas = every_meas.step();
+        const bool do_swap = every_swap.step();
         if (do_meas || do_swap) {
             if (active) {
                 int anti0 = 0, anti1 = 0, pos = 0;
@@ -251,7 +252,7 @@ __device__ __forceinline__ void sweep_canon_body(const SweepArgs& a, int word, u
             body_sync<kCluster>();
             if (do_swap && active) lc.lb = 4u * static_cast<uint32_t>(bos0[lane]);
         }
-        if (!kCluster && a.sq_every > 0 && (t + 1u) % static_cast<uint32_t>(a.sq_every) == 0u) {
+        if (every_sq.step()) {
             accumulate_correlations_any(a, s_v, s_w, s_seg, s_segmask, warp, nwarp, lane);  // s_w: dead here
             __syncthreads();
         }

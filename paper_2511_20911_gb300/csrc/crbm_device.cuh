@@ -196,6 +196,23 @@ __device__ __forceinline__ void claim_word(int* state, int nw, int n_chunks, uns
     }
 }
 
+// Countdown to the sweeps t with (t + 1) % k == 0 (the sweeps after which a
+// measurement, a swap round or a correlation sample is taken), started at
+// sweep t0, so that the sweep loop needs no integer division per sweep.
+// k <= 0: never.  step() answers for the current sweep and moves on to the
+// next; every thread calls it once per sweep.
+struct EveryCounter {
+    int left, k;  // sweeps after the current one before the next hit (k <= 0: negative, never 0)
+    __device__ __forceinline__ EveryCounter(uint32_t t0, int k_)
+        : left(k_ > 0 ? static_cast<int>(static_cast<uint32_t>(k_) - 1u - t0 % static_cast<uint32_t>(k_)) : -1),
+          k(k_) {}
+    __device__ __forceinline__ bool step() {
+        const bool hit = left == 0;
+        left = hit ? k - 1 : left - 1;
+        return hit;
+    }
+};
+
 __device__ __forceinline__ int warp_sum(int x) {
 #pragma unroll
     for (int o = 16; o > 0; o >>= 1) x += __shfl_xor_sync(0xffffffffu, x, o);

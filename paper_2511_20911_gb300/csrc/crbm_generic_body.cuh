@@ -197,6 +197,7 @@ __device__ __forceinline__ void sweep_generic_body(const SweepArgs& a, int word)
     int64_t meas = a.clock ? a.clock[1] : a.meas0;
 
     const Round0Lane r0l = round0_lane(chain);
+    EveryCounter every_meas(t0, a.measure_every), every_swap(t0, a.swap_every), every_sq(t0, a.sq_every);
     for (int it = 0; it < a.n_sweeps; ++it) {
         const uint32_t t = t0 + static_cast<uint32_t>(it);
         const Round1Sweep rs = round1_sweep(r0l.hi ^ t ^ a.rk[0], a.rk);
@@ -206,8 +207,8 @@ __device__ __forceinline__ void sweep_generic_body(const SweepArgs& a, int word)
         for (int cell = warp; cell < g.n_cells; cell += nwarp)
             visible_cell_generic<kPaper>(sm, rv, cell, rs, r0l.lo, a.rk, sflip, stepJ, lb, lane);
         __syncthreads();
-        const bool do_meas = measuring && (t + 1u) % static_cast<uint32_t>(a.measure_every) == 0u;
-        const bool do_swap = a.swap_every > 0 && (t + 1u) % static_cast<uint32_t>(a.swap_every) == 0u;
+        const bool do_meas = every_meas.step();
+        const bool do_swap = every_swap.step();
         if (do_meas || do_swap) {
             int anti0 = 0, anti1 = 0, pos = 0;
             for (int cell = warp; cell < g.n_cells; cell += nwarp) count_cell(g, s_v, a.gep, cell, lane, anti0, anti1);
@@ -221,7 +222,7 @@ __device__ __forceinline__ void sweep_generic_body(const SweepArgs& a, int word)
             __syncthreads();
             if (do_swap) lb = 4u * static_cast<uint32_t>(s_bos[lane]);
         }
-        if (a.sq_every > 0 && (t + 1u) % static_cast<uint32_t>(a.sq_every) == 0u) {
+        if (every_sq.step()) {
             accumulate_correlations_any(a, s_v, nullptr, s_seg, s_segmask, warp, nwarp, lane);
             __syncthreads();
         }

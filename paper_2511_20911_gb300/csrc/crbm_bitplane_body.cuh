@@ -50,6 +50,10 @@ __device__ __forceinline__ void sweep_bitplane_body(const SweepArgs& a, const ui
     extern __shared__ __align__(16) uint32_t smem[];
     const Geometry& g = a.g;
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nwarp = blockDim.x >> 5;
+    // the warp that keeps the running sums and finishes each measurement: the last, which has the
+    // fewest node groups when they do not divide evenly, so that it can finish a measurement while
+    // the others start the next sweep
+    const int post_warp = nwarp - 1;
     const int N = g.N, nh = g.n_cells * kBpNodes;
     int64_t* s_acc = reinterpret_cast<int64_t*>(smem);          // [kNSum][32] running sums
     uint32_t* s_tab0 = smem + kAccWords;                         // [kBpTab] planes, sign masks by rung
@@ -68,7 +72,7 @@ __device__ __forceinline__ void sweep_bitplane_body(const SweepArgs& a, const ui
     for (int x = threadIdx.x; x < N; x += blockDim.x) s_v[x] = __ldcg(gv + x);
     for (int x = threadIdx.x; x < 96; x += blockDim.x) s_cnt[x] = 0;
     if (threadIdx.x < 2) s_nst[threadIdx.x] = 0;
-    if (warp == 0) {  // replica permutation (identity without replica exchange)
+    if (warp == post_warp) {  // replica permutation (identity without replica exchange)
         const int sob = kSwap ? __ldcg(a.sob + word * 32 + lane) : lane;
         s_sob[lane] = sob;
         s_bos[sob] = lane;
@@ -84,7 +88,7 @@ __device__ __forceinline__ void sweep_bitplane_body(const SweepArgs& a, const ui
     }
     const bool measuring = a.measure_every > 0;
     const uint32_t chain = static_cast<uint32_t>(word) * 32u + lane;
-    if (measuring && warp == 0)
+    if (measuring && warp == post_warp)
         for (int x = 0; x < kNSum; ++x) s_acc[x * 32 + lane] = __ldcg(a.sums + static_cast<size_t>(chain) * kNSum + x);
     __syncthreads();
     uint32_t fl0 = s_tab[kBpFlip], fl1 = s_tab[kBpFlip + 1];
@@ -244,19 +248,21 @@ __device__ __forceinline__ void sweep_bitplane_body(const SweepArgs& a, const ui
             atomicAdd(&s_cnt[32 + lane], anti1);
             atomicAdd(&s_cnt[64 + lane], pos);
             __syncthreads();
-            if (warp == 0) post_sweep_warp0(a, s_cnt, s_sob, s_bos, lane, word, t, do_meas, do_swap, meas, s_acc);
+            if (warp == post_warp) post_sweep_warp0(a, s_cnt, s_sob, s_bos, lane, word, t, do_meas, do_swap, meas, s_acc);
             if (do_meas) ++meas;
-            __syncthreads();
+            // a measurement alone touches only warp post_warp's sums and the counts, which the next
+            // measurement reaches after the next sweep's barriers; a swap round re-permutes the planes
             if (do_swap) {
+                __syncthreads();
                 permute_planes();
                 __syncthreads();
             }
         }
     }
-    if (kSwap && warp == 0) a.sob[word * 32 + lane] = s_sob[lane];
+    if (kSwap && warp == post_warp) a.sob[word * 32 + lane] = s_sob[lane];
     uint32_t* gvo = a.v + static_cast<size_t>(word) * N;
     for (int x = threadIdx.x; x < N; x += blockDim.x) gvo[x] = s_v[x];
-    if (measuring && warp == 0)
+    if (measuring && warp == post_warp)
         for (int x = 0; x < kNSum; ++x) a.sums[static_cast<size_t>(chain) * kNSum + x] = s_acc[x * 32 + lane];
 }
 

@@ -76,6 +76,10 @@ __device__ __forceinline__ void sweep_canon_body(const SweepArgs& a, int word, u
     const Geometry& g = a.g;
     const int W = g.W, Wc = g.Wc;  // rows and columns of cells
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nwarp = blockDim.x >> 5;
+    // The warp that keeps the running sums and finishes each measurement: the
+    // last, which has the fewest cells when they do not divide evenly, so that
+    // it can finish a measurement while the others start the next sweep.
+    const int post_warp = nwarp - 1;
     const int nb = kCluster ? a.n_bands : 1;
     const bool active = band < nb;
     const int row0 = active ? band * W / nb : 0, row1 = active ? (band + 1) * W / nb : 0;
@@ -129,7 +133,7 @@ __device__ __forceinline__ void sweep_canon_body(const SweepArgs& a, int word, u
             for (int x = threadIdx.x; x < 33; x += blockDim.x) s_seg[x] = a.seg[word * 33 + x];
             for (int x = threadIdx.x; x < 32; x += blockDim.x) s_segmask[x] = a.segmask[word * 32 + x];
         }
-        if (warp == 0) {  // replica permutation (identity without tempering)
+        if (warp == post_warp) {  // replica permutation (identity without tempering)
             const int sob = a.swap_every > 0 ? __ldcg(a.sob + word * 32 + lane) : lane;
             s_sob[lane] = sob;
             s_bos[sob] = lane;
@@ -137,7 +141,7 @@ __device__ __forceinline__ void sweep_canon_body(const SweepArgs& a, int word, u
     }
     __syncthreads();
     lc.lb = 4u * static_cast<uint32_t>(s_bos[lane]);  // lane reads the column of its rung
-    if (active && band == 0 && warp == 0 && measuring) {
+    if (active && band == 0 && warp == post_warp && measuring) {
         for (int x = 0; x < kNSum; ++x)
             s_acc[x * 32 + lane] = __ldcg(a.sums + static_cast<size_t>(chain) * kNSum + x);
     }
@@ -246,11 +250,16 @@ __device__ __forceinline__ void sweep_canon_body(const SweepArgs& a, int word, u
                 atomicAdd(&cnt0[64 + lane], pos);
             }
             body_sync<kCluster>();
-            if (band == 0 && warp == 0)
+            if (band == 0 && warp == post_warp)
                 post_sweep_warp0(a, s_cnt, s_sob, s_bos, lane, word, t, do_meas, do_swap, meas, s_acc);
             if (do_meas) ++meas;
-            body_sync<kCluster>();
-            if (do_swap && active) lc.lb = 4u * static_cast<uint32_t>(bos0[lane]);
+            // A swap round changes the permutation every warp reads next; a
+            // measurement alone touches only warp post_warp's sums and the counts, which
+            // the next measurement reaches after the next sweep's barriers.
+            if (do_swap) {
+                body_sync<kCluster>();
+                if (active) lc.lb = 4u * static_cast<uint32_t>(bos0[lane]);
+            }
         }
         if (every_sq.step()) {
             accumulate_correlations_any(a, s_v, s_w, s_seg, s_segmask, warp, nwarp, lane);  // s_w: dead here
@@ -263,8 +272,8 @@ __device__ __forceinline__ void sweep_canon_body(const SweepArgs& a, int word, u
     const int s_begin = kCluster ? 2 * row0 * g.Lc : 0;  // own spin rows
     const int s_end = kCluster ? min(2 * row1, g.L) * g.Lc : g.N;
     for (int x = s_begin + static_cast<int>(threadIdx.x); x < s_end; x += blockDim.x) gv[x] = s_v[x];
-    if (band == 0 && warp == 0 && a.swap_every > 0) a.sob[word * 32 + lane] = s_sob[lane];
-    if (band == 0 && warp == 0 && measuring) {
+    if (band == 0 && warp == post_warp && a.swap_every > 0) a.sob[word * 32 + lane] = s_sob[lane];
+    if (band == 0 && warp == post_warp && measuring) {
         for (int x = 0; x < kNSum; ++x) a.sums[static_cast<size_t>(chain) * kNSum + x] = s_acc[x * 32 + lane];
     }
 }

@@ -19,7 +19,8 @@ OUT_DIR = os.path.join(PKG, "_build")
 LIB = os.path.join(OUT_DIR, "libcrbm.so")
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 SOURCES = ["crbm_host.cpp", "crbm_runtime.cpp", "crbm_kernels.cu", "crbm_canon.cu",
-           "crbm_stream.cu", "crbm_noalloc.cu", "crbm_batch.cu", "crbm_proposal.cu", "crbm_bitplane.cu"]
+           "crbm_stream.cu", "crbm_noalloc.cu", "crbm_batch.cu", "crbm_batch_small.cu", "crbm_proposal.cu",
+           "crbm_bitplane.cu"]
 
 
 def nvcc_path() -> str:

@@ -6,71 +6,20 @@
 // value in the kernel parameters.  Sweep and measurement counters come from a device
 // clock per context, advanced by a one-thread epilogue, so the pair of
 // launches can be captured once in a CUDA graph and replayed.
-#include "crbm_bitplane_body.cuh"
-#include "crbm_canon_body.cuh"
-#include "crbm_generic_body.cuh"
+#include "crbm_batch_kernel.cuh"
 
 namespace crbm {
+
+// CTAs of up to 512 threads: the instantiations of crbm_batch_small.cu.
+BatchKernel batch_kernel_small(bool cluster, int modes);
+
 namespace {
 
-namespace cg = cooperative_groups;
-
-// One CTA per task (descriptor, word, band, bands).  kCluster: the launch
-// has thread-block clusters.  A word split into bands > 1 occupies
-// consecutive ranks of a cluster that holds only words of its context (and
-// padding ranks of that context, band >= bands), all synchronising with
-// cluster barriers; every other cluster holds whole words, one per CTA,
-// which synchronise within their CTA only; tasks with descriptor -1 return
-// at once.  kModes: the member kinds besides exact lane-uniform and generic
-// ones that the batch holds (kBatchPaper, kBatchBitplane), so that a batch
-// without them runs code that carries neither body.
-template <bool kCluster, int kModes>
-__global__ void __launch_bounds__(CRBM_SWEEP_MAX_THREADS, CRBM_SWEEP_MAX_THREADS <= 512 ? 2 : 1) k_sweep_batch(const __grid_constant__ BatchArgs b) {
-    const int4 task = b.items[blockIdx.x];
-    if (task.x < 0) return;
-    const SweepArgs& a = b.d[task.x];
-    const uint32_t t0 = static_cast<uint32_t>(a.clock[0]);
-    if (!a.g.canonical) {
-        if ((kModes & kBatchPaper) && a.g.paper)
-            generic::sweep_generic_body<true>(a, task.y);
-        else
-            generic::sweep_generic_body<false>(a, task.y);
-    } else if ((kModes & kBatchBitplane) && a.g.bitplane) {  // whole words; node records from global memory
-        const uint32_t* hrec = reinterpret_cast<const uint32_t*>(a.crec);
-        const uint32_t* vrec = hrec + static_cast<size_t>(a.g.n_cells) * bp::kBpNodes;
-        if (a.swap_every > 0)
-            bp::sweep_bitplane_body<true>(a, hrec, vrec, task.y, t0, a.n_sweeps, a.clock[1]);
-        else
-            bp::sweep_bitplane_body<false>(a, hrec, vrec, task.y, t0, a.n_sweeps, a.clock[1]);
-    } else if ((kModes & kBatchPaper) && a.g.paper) {  // whole words
-        if (b.smem_rec)
-            canon::sweep_canon_body<true, false, true>(a, task.y, t0, a.n_sweeps, a.clock[1]);
-        else
-            canon::sweep_canon_body<false, false, true>(a, task.y, t0, a.n_sweeps, a.clock[1]);
-    } else if (kCluster && task.w > 1) {
-        const int rank = static_cast<int>(cg::this_cluster().block_rank());
-        const int rank0 = task.z < task.w ? rank - task.z : 0;
-        if (b.smem_rec)
-            canon::sweep_canon_body<true, true>(a, task.y, t0, a.n_sweeps, a.clock[1], task.z, rank0);
-        else
-            canon::sweep_canon_body<false, true>(a, task.y, t0, a.n_sweeps, a.clock[1], task.z, rank0);
-    } else if (b.smem_rec) {
-        canon::sweep_canon_body<true, false>(a, task.y, t0, a.n_sweeps, a.clock[1]);
-    } else {
-        canon::sweep_canon_body<false, false>(a, task.y, t0, a.n_sweeps, a.clock[1]);
-    }
-}
-
-// The instantiation for a cluster flag and a set of member kinds.
-using BatchKernel = void (*)(const BatchArgs);
-template <bool kCluster>
-BatchKernel batch_kernel(int modes) {
-    switch (modes & (kBatchPaper | kBatchBitplane)) {
-        case kBatchPaper: return k_sweep_batch<kCluster, kBatchPaper>;
-        case kBatchBitplane: return k_sweep_batch<kCluster, kBatchBitplane>;
-        case kBatchPaper | kBatchBitplane: return k_sweep_batch<kCluster, kBatchPaper | kBatchBitplane>;
-        default: return k_sweep_batch<kCluster, 0>;
-    }
+// The kernel for a launch: the 512-thread instantiation for CTAs that fit it.
+BatchKernel batch_kernel(bool cluster, int modes, int threads) {
+    if (threads <= 512) return batch_kernel_small(cluster, modes);
+    return cluster ? batch_kernel_for<true, CRBM_SWEEP_MAX_THREADS>(modes)
+                   : batch_kernel_for<false, CRBM_SWEEP_MAX_THREADS>(modes);
 }
 
 // clocks[c] = {sweep, measurements}; every[c] = measure_every of context c.
@@ -87,7 +36,7 @@ __global__ void k_batch_advance(int64_t* clocks, const int* every, int n_ctx, in
 
 cudaError_t launch_sweep_batch(const BatchArgs& b, int n_tasks, int cluster, int threads, size_t smem, int modes,
                                cudaStream_t st) {
-    const BatchKernel kernel = cluster <= 1 ? batch_kernel<false>(modes) : batch_kernel<true>(modes);
+    const BatchKernel kernel = batch_kernel(cluster > 1, modes, threads);
     if (smem > 48 * 1024) {
         const cudaError_t e =
             cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, static_cast<int>(smem));
@@ -113,7 +62,7 @@ cudaError_t launch_sweep_batch(const BatchArgs& b, int n_tasks, int cluster, int
 }
 
 int batch_max_active_clusters(int cluster, int threads, size_t smem, int modes) {
-    const BatchKernel kernel = batch_kernel<true>(modes);
+    const BatchKernel kernel = batch_kernel(true, modes, threads);
     if (smem > 48 * 1024 &&
         cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, static_cast<int>(smem)) !=
             cudaSuccess)

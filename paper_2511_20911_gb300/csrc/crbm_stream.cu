@@ -53,6 +53,23 @@ __device__ __forceinline__ void stage_rungs(const SweepArgs& a, int w, int* s_bo
 // thread is issued before its first shared store.  kOneWrap: L >= 2 TI and
 // Lc >= 2 TJ, so 2 i0 + r <= L + 30 (2 j0 + c <= Lc + 30) needs at most one
 // subtraction of L (Lc).
+// n / d for 1 <= d <= 32 and 0 <= n < 2^16 (the tile-local indices) without a
+// division: one high multiply by m = ceil(2^32 / d), exact because
+// n (m d - 2^32) < 2^32 keeps the fraction below the next integer (d = 1,
+// whose m does not fit 32 bits, passes n through).
+struct SmallDiv {
+    uint32_t m;
+    int d;
+    __device__ __forceinline__ explicit SmallDiv(int d_)
+        : m(d_ > 1 ? static_cast<uint32_t>((0x100000000ull + static_cast<uint64_t>(d_) - 1u) /
+                                           static_cast<uint64_t>(d_))
+                   : 0u),
+          d(d_) {}
+    __device__ __forceinline__ int operator()(int n) const {
+        return d > 1 ? static_cast<int>(__umulhi(static_cast<uint32_t>(n), m)) : n;
+    }
+};
+
 template <bool kOneWrap>
 __device__ __forceinline__ void stage_spin_tile(const SweepArgs& a, int w, int i0, int j0, uint32_t* s_v) {
     constexpr int VS = 2 * kTJ + 1, NV = (2 * kTI + 1) * VS;
@@ -274,6 +291,7 @@ __global__ void __launch_bounds__(kStreamThreads) k_stream_bp_hidden(const Sweep
     __syncthreads();
     const uint32_t fl0 = s_tab[kBpFlip], fl1 = s_tab[kBpFlip + 1];
     const int ni = min(kTI, W - i0), nj = min(kTJ, Wc - j0), nn = ni * nj * 10;
+    const SmallDiv div_nj(nj);
     const uint64_t pw = static_cast<uint64_t>(kPhiloxM1) * static_cast<uint32_t>(w);
     const uint32_t Yw = static_cast<uint32_t>(pw);
     const Round1Sweep rs = round1_sweep(static_cast<uint32_t>(pw >> 32) ^ a.rk[0] ^ t, a.rk);
@@ -287,7 +305,7 @@ __global__ void __launch_bounds__(kStreamThreads) k_stream_bp_hidden(const Sweep
     };
     auto hidden_node = [&](int nd) {
         const int lc = nd / 10, k = nd - lc * 10;
-        const int li = lc / nj, lj = lc - li * nj;
+        const int li = div_nj(lc), lj = lc - li * nj;
         const uint32_t cls = k >= 8 ? 1u : 0u;
         const uint32_t* v = s_v + 2 * li * VS + 2 * lj;
         const uint32_t e1 = v[s_off[0][k]];
@@ -391,12 +409,16 @@ __global__ void __launch_bounds__(kStreamVisThreads, CRBM_STREAM_MIN_BLOCKS) k_s
         const int lc = x / 10, k = x - lc * 10;
         const int li = lc / HS, lj = lc - li * HS;
         if (li > ni || lj > nj) continue;
-        const int gi = (i0 - 1 + li + W) % W, gj = (j0 - 1 + lj + Wc) % Wc;
+        // li <= ni <= W - i0 (and lj <= nj <= Wc - j0): i0 - 1 + li lies in [-1, W - 1]
+        int gi = i0 - 1 + li, gj = j0 - 1 + lj;
+        gi += gi < 0 ? W : 0;
+        gj += gj < 0 ? Wc : 0;
         s_h[x] = hw[(gi * Wc + gj) * 10 + k];
     }
     __syncthreads();
     const uint32_t fl0 = s_tab[kBpFlip], fl1 = s_tab[kBpFlip + 1];
     const int nr = 2 * ni, nc = 2 * nj, nn = nr * nc;
+    const SmallDiv div_nc(nc);
     constexpr int VO = 2 * kTJ;
     const uint64_t pw = static_cast<uint64_t>(kPhiloxM1) * static_cast<uint32_t>(w);
     const uint32_t Yw = static_cast<uint32_t>(pw);
@@ -411,7 +433,7 @@ __global__ void __launch_bounds__(kStreamVisThreads, CRBM_STREAM_MIN_BLOCKS) k_s
         int out;
     };
     auto visible_node = [&](int sd) {
-        const int R = sd / nc, C = sd - R * nc;  // tile-local spin row and column
+        const int R = div_nc(sd), C = sd - R * nc;  // tile-local spin row and column
         const int x = 2 * (R & 1) + (C & 1);
         const uint32_t* hc = s_h + (((R >> 1) + 1) * HS + (C >> 1) + 1) * 10;  // own cell's words
         auto hin = [&](int v, uint32_t fl) {

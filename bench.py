@@ -56,7 +56,7 @@ MEASURED_TRAFFIC = {
                       "per launch with S(q) every 100 sweeps; profiles/k_sweep_canon_persistent_L18_grid_paper.md"),
     "stream_paper": (56.76e6 + 390.29e6 + 454.76e6 + 45.71e6, "per sweep (two launches); profiles/k_stream_L384.md"),
     "grid_bitplane": (2.48e6 + 0.78e6, "per launch; profiles/k_sweep_bitplane_L18_grid.md"),
-    "stream_bitplane": (56.98e6 + 83.06e6 + 141.93e6 + 29.42e6, "per sweep (two launches); profiles/k_stream_bp_L384.md"),
+    "stream_bitplane": (56.88e6 + 82.96e6 + 141.80e6 + 29.02e6, "per sweep (two launches); profiles/k_stream_bp_L384.md"),
 }
 
 

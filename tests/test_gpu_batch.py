@@ -219,3 +219,23 @@ def test_batch_sees_targets_set_after_capture():
     hits = batched[0].first_hits()
     assert np.array_equal(hits, twin.first_hits()) and (hits == 6).all()
     batch.close()
+
+
+def test_batch_wide_ctas_match_individual_sweeps(monkeypatch):
+    """CTAs of more than 512 threads run the kernel's 1024-thread instantiation
+    (64 registers a thread); smaller ones the 512-thread one.  Both stay
+    bit-identical to twins advanced on their own."""
+    specs = members()
+    monkeypatch.setenv("CRBM_WARPS", "24")
+    batched = [make(s) for s in specs]
+    monkeypatch.delenv("CRBM_WARPS")
+    twins = [make(s) for s in specs]
+    batch = crbm.Batch(batched)
+    assert batch.threads == 768
+    for n in (5, 8):
+        batch.sweep(n)
+        for t in twins:
+            t.sweep(n)
+    for a, b in zip(batched, twins):
+        same(a, b)
+    batch.close()

@@ -211,7 +211,7 @@ def workload_config(name, rank):
     return w
 
 
-DEFAULT_SWEEPS = {"grid": 2000, "stream": 20, "batch": 500, "proposal": 250, "tts": 50000, "phase": 4000}
+DEFAULT_SWEEPS = {"grid": 2000, "stream": 20, "batch": 500, "proposal": 250, "tts": 200000, "phase": 4000}
 
 
 def cpu_model():
@@ -329,12 +329,16 @@ def config_dict(w, args, workload=None):
 # the times it prints for its FPGA (lattice sizes not stated in the text).
 TTS_PHASES = (("FM", 1.0, 1.0, 7.0, 33e-9), ("dimer", 1.0, 2.5, 0.0, 5e-6), ("Neel", 1.0, 1.0, 0.0, 200e-6),
               ("1/3 plateau", 1.0, 0.5, 4.0, 120e-3))
+# beta range of each phase's replica-exchange ladders (geometric, 32 rungs): the paper tunes its
+# temperatures per phase too.  The 1/3 plateau freezes into domain walls above beta ~ 5 and is never
+# reached by rungs up to beta = 8 at L = 18; a ladder over [2, 5] reaches it in every run of 2x10^5 sweeps.
+TTS_LADDERS = ((0.25, 8.0), (0.25, 8.0), (0.25, 8.0), (2.0, 5.0))
 
 
 def run_tts(args, rank, ws):
     """Time to solution at the paper's four phase points, L in {6, 12, 18}.
     Per point, 32 independent replica-exchange ladders of 32 rungs (beta
-    geometric in [0.25, 8], swaps every 2 sweeps) and, for comparison, 1024
+    geometric in the phase's range of TTS_LADDERS, swaps every 2 sweeps) and, for comparison, 1024
     independent chains at fixed beta = 4; every chain's first sweep at its
     point's brute-force supercell ground-state energy is recorded on the
     device (measured every sweep).  A run is a ladder (first hit of any rung)
@@ -346,7 +350,7 @@ def run_tts(args, rank, ws):
     from paper_2511_20911_gb300 import analysis
     S = args.sweeps_per_step
     R, ladders, beta_fixed = 32, 32, 4.0
-    betas = 0.25 * (8.0 / 0.25) ** (np.arange(R) / (R - 1))
+    ladder_betas = [lo * (hi / lo) ** (np.arange(R) / (R - 1)) for lo, hi in TTS_LADDERS]
     rows, total_updates, total_s = [], 0, 0.0
     with ClockSampler(torch.cuda.current_device()) as clk:
         for L in (6, 12, 18):
@@ -354,7 +358,7 @@ def run_tts(args, rank, ws):
             for mode in ("tempering", "fixed"):
                 if mode == "tempering":
                     params = dict(J=[], Jp=[], h=[], beta=[])
-                    for _, J, Jp, h, _ in TTS_PHASES:
+                    for (_, J, Jp, h, _), betas in zip(TTS_PHASES, ladder_betas):
                         for _ in range(ladders):
                             params["J"] += [J] * R
                             params["Jp"] += [Jp] * R
@@ -395,7 +399,7 @@ def run_tts(args, rank, ws):
                 for k, (name, J, Jp, h_, paper) in enumerate(TTS_PHASES):
                     pg, T, tts = analysis.time_to_solution(runs[run_point == k], S)
                     rows.append({"phase": name, "L": L, "mode": mode, "J": J, "Jp": Jp, "h": h_,
-                                 "beta": [0.25, 8.0] if mode == "tempering" else beta_fixed,
+                                 "beta": list(TTS_LADDERS[k]) if mode == "tempering" else beta_fixed,
                                  "runs": int((run_point == k).sum()), "p_gnd": pg, "T_sweeps": T,
                                  "tts99_sweeps": tts, "tts99_s": None if tts is None else tts * sec / S,
                                  "context_s_per_sweep": sec / S, "paper_fpga_s": paper,
@@ -407,7 +411,8 @@ def run_tts(args, rank, ws):
            "vs_baseline": None, "dtype": "u32", "data": "synthetic",
            "config": {"workload": "time to solution at the paper's FM, dimer, Neel and 1/3-plateau points, "
                                   f"L in {{6,12,18}}: {ladders} replica-exchange ladders of {R} rungs (beta "
-                                  f"geometric in [0.25, 8], swaps every 2 sweeps) per point, and {ladders * R} "
+                                  f"geometric in [0.25, 8]; [2, 5] for the 1/3 plateau; swaps every 2 sweeps) per "
+                                  f"point, and {ladders * R} "
                                   f"chains at fixed beta = {beta_fixed} per point; {S} sweeps; ground states by "
                                   "brute force over even supercells of <= 16 sites",
                       "parallelism": f"replicas x{ws}"},

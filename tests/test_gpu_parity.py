@@ -137,7 +137,8 @@ def test_custom_filters_bitexact(orc, bonds):
 
 
 @pytest.mark.parametrize("L,interleaved", [(8, False), (6, False), (9, False), (36, False), (4, False),
-                                           (18, False), (32, False), (18, True), (10, True)])
+                                           (18, False), (32, False), (18, True), (10, True), (22, False),
+                                           (26, True)])
 def test_structure_factor_matches_oracle(orc, L, interleaved):
     """S(q) against the oracle: even sides up to 32 take the bit-transposed
     accumulation (lane = chain, one warp reduction per parameter point), odd

@@ -294,7 +294,8 @@ int crbm_philox_stream(uint32_t* sink, int32_t n_blocks, int32_t threads, int32_
  * boundary rows through distributed shared memory.  Members keep their own state, counters and getters; each
  * batched call advances every member by n_sweeps sweeps, bit-identical to
  * calling crbm_sweep on each.  The CTA shape is the largest warps count of
- * the members (see crbm_autotune). */
+ * the members (see crbm_autotune) until crbm_batch_autotune picks one for
+ * the batch itself. */
 #define CRBM_BATCH_MAX 16
 typedef struct crbm_batch crbm_batch;
 /* Errors: CRBM_EINVAL (0 or more than CRBM_BATCH_MAX members, a repeated

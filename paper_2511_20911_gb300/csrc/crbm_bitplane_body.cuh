@@ -248,7 +248,7 @@ __device__ __forceinline__ void sweep_bitplane_body(const SweepArgs& a, const ui
             atomicAdd(&s_cnt[32 + lane], anti1);
             atomicAdd(&s_cnt[64 + lane], pos);
             __syncthreads();
-            if (warp == post_warp) post_sweep_warp0(a, s_cnt, s_sob, s_bos, lane, word, t, do_meas, do_swap, meas, s_acc);
+            if (warp == post_warp) post_sweep_warp(a, s_cnt, s_sob, s_bos, lane, word, t, do_meas, do_swap, meas, s_acc);
             if (do_meas) ++meas;
             // a measurement alone touches only warp post_warp's sums and the counts, which the next
             // measurement reaches after the next sweep's barriers; a swap round re-permutes the planes

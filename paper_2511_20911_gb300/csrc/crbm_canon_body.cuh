@@ -251,7 +251,7 @@ __device__ __forceinline__ void sweep_canon_body(const SweepArgs& a, int word, u
             }
             body_sync<kCluster>();
             if (band == 0 && warp == post_warp)
-                post_sweep_warp0(a, s_cnt, s_sob, s_bos, lane, word, t, do_meas, do_swap, meas, s_acc);
+                post_sweep_warp(a, s_cnt, s_sob, s_bos, lane, word, t, do_meas, do_swap, meas, s_acc);
             if (do_meas) ++meas;
             // A swap round changes the permutation every warp reads next; a
             // measurement alone touches only warp post_warp's sums and the counts, which

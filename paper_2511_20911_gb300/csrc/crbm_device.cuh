@@ -230,8 +230,8 @@ static __device__ __noinline__ void record_first_hit(int64_t* hit, const int32_t
     if (ht[1] < 0 && E <= ht[0]) ht[1] = static_cast<int64_t>(t) + 1;
 }
 
-// Post-sweep step of the SMEM kernels, run by warp 0 after every warp has
-// added its per-lane counts to s_cnt ([0..31] anti-aligned J filters, [32..63]
+// Post-sweep step of the SMEM kernels, run by one warp (the one that keeps
+// the running sums) after every warp has added its per-lane counts to s_cnt ([0..31] anti-aligned J filters, [32..63]
 // anti-aligned J' filters, [64..95] +1 spins; lane = replica slot).  Lane k
 // then stands for temperature rung k, held by slot s_sob[k] (the identity
 // without tempering):
@@ -241,7 +241,7 @@ static __device__ __noinline__ void record_first_hit(int64_t* hit, const int32_t
 //  - replica exchange (round m): pairs (k, k+1) with k = m (mod 2) swap rungs
 //    when E_k <= E_{k+1}, else when a Philox word (k, m, word, swap tag) is
 //    below the host-built threshold of nearbyint(2^32 exp((b_k - b_{k+1}) dE / 16)).
-__device__ __forceinline__ void post_sweep_warp0(const SweepArgs& a, int* s_cnt, int* s_sob,
+__device__ __forceinline__ void post_sweep_warp(const SweepArgs& a, int* s_cnt, int* s_sob,
                                                  int* s_bos, int lane, int word, uint32_t t,
                                                  bool do_meas, bool do_swap, int64_t meas,
                                                  int64_t* s_acc) {

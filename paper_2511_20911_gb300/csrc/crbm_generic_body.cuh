@@ -217,7 +217,7 @@ __device__ __forceinline__ void sweep_generic_body(const SweepArgs& a, int word)
             atomicAdd(&s_cnt[32 + lane], anti1);
             atomicAdd(&s_cnt[64 + lane], pos);
             __syncthreads();
-            if (warp == 0) post_sweep_warp0(a, s_cnt, s_sob, s_bos, lane, word, t, do_meas, do_swap, meas, s_acc);
+            if (warp == 0) post_sweep_warp(a, s_cnt, s_sob, s_bos, lane, word, t, do_meas, do_swap, meas, s_acc);
             if (do_meas) ++meas;
             __syncthreads();
             if (do_swap) lb = 4u * static_cast<uint32_t>(s_bos[lane]);

@@ -564,7 +564,7 @@ __global__ void k_stream_finalize(const SweepArgs a, int64_t meas, int64_t sweep
 
 // Post-sweep step with replica exchange: one warp per 32-chain half-word w
 // (a ladder), lane = slot for the counts and rung for the rest, exactly the
-// SMEM kernels' step (post_sweep_warp0): rung k's measurement from the slot
+// SMEM kernels' step (post_sweep_warp): rung k's measurement from the slot
 // that holds it into row 32 w + k of the sums and series, then the
 // exchange round, and the new slot-of-rung array back to sob.  Half-words
 // past the last ladder (padding of the 64-chain groups) only clear their
@@ -587,7 +587,7 @@ __global__ void __launch_bounds__(32) k_stream_post_pt(const SweepArgs a, int64_
     if (do_meas)
         for (int x = 0; x < kNSum; ++x) s_acc[x * 32 + lane] = a.sums[row * kNSum + x];
     __syncwarp();
-    post_sweep_warp0(a, s_cnt, s_sob, s_bos, lane, w, t, do_meas != 0, do_swap != 0, meas, s_acc);
+    post_sweep_warp(a, s_cnt, s_sob, s_bos, lane, w, t, do_meas != 0, do_swap != 0, meas, s_acc);
     __syncwarp();
     if (do_meas)
         for (int x = 0; x < kNSum; ++x) a.sums[row * kNSum + x] = s_acc[x * 32 + lane];

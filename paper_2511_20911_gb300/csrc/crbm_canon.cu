@@ -27,8 +27,15 @@ using namespace canon;
 // again.  A CTA that finds no free unfinished word exits: every unfinished
 // word is then held by a running CTA, which claims again after its chunk, so
 // no work is left behind and nothing waits.
-template <bool kSmemRec, bool kPaper>
-__global__ void __launch_bounds__(CRBM_SWEEP_MAX_THREADS, CRBM_SWEEP_MIN_BLOCKS)
+//
+// Two instantiations per variant: one for CTAs of at most kSmallCta threads
+// (12 warps, the shape the L=18 grid tunes to) at two CTAs per SM, which may
+// take 80 registers a thread and keeps the sweep loop free of spills, and one
+// for any CTA, at 64 registers.  A launch takes the first wherever its CTA
+// fits it and it holds as many CTAs per SM as the second.
+constexpr int kSmallCta = 384;
+template <bool kSmemRec, bool kPaper, int kMaxThreads>
+__global__ void __launch_bounds__(kMaxThreads, kMaxThreads <= kSmallCta ? 2 : CRBM_SWEEP_MIN_BLOCKS)
     k_sweep_canon_persistent(const SweepArgs a, int chunk, int* state) {
     __shared__ int s_word, s_chunk;
     const int n_chunks = (a.n_sweeps + chunk - 1) / chunk;
@@ -122,14 +129,23 @@ namespace {
 template <bool kSmemRec, bool kPaper>
 cudaError_t launch_persistent(const SweepArgs& a, int warps_per_cta, int chunk, int* sched, cudaStream_t st) {
     const size_t smem = smem_bytes_canon_launch(a.g);
-    if (smem > 48 * 1024) {
-        const cudaError_t e = cudaFuncSetAttribute(k_sweep_canon_persistent<kSmemRec, kPaper>,
-                                                   cudaFuncAttributeMaxDynamicSharedMemorySize, static_cast<int>(smem));
+    using Kernel = void (*)(const SweepArgs, int, int*);
+    const Kernel big = k_sweep_canon_persistent<kSmemRec, kPaper, CRBM_SWEEP_MAX_THREADS>;
+    const Kernel small = k_sweep_canon_persistent<kSmemRec, kPaper, kSmallCta>;
+    const int threads = warps_per_cta * 32;
+    // the spill-free instantiation where the CTA fits it and it keeps as many CTAs per SM
+    int per_sm = 0, per_sm_small = 0, dev = 0, sms = 0;
+    cudaError_t e = cudaSuccess;
+    for (const Kernel k : {big, small}) {
+        if (k == small && threads > kSmallCta) break;
+        if (smem > 48 * 1024)
+            e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, static_cast<int>(smem));
+        if (e == cudaSuccess)
+            e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(k == big ? &per_sm : &per_sm_small, k, threads, smem);
         if (e != cudaSuccess) return e;
     }
-    int per_sm = 0, dev = 0, sms = 0;
-    cudaError_t e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_sweep_canon_persistent<kSmemRec, kPaper>,
-                                                                  warps_per_cta * 32, smem);
+    const Kernel kernel = per_sm_small >= per_sm && per_sm_small > 0 ? small : big;
+    if (kernel == small) per_sm = per_sm_small;
     if (e == cudaSuccess) e = cudaGetDevice(&dev);
     if (e == cudaSuccess) e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
     if (e != cudaSuccess) return e;
@@ -138,7 +154,7 @@ cudaError_t launch_persistent(const SweepArgs& a, int warps_per_cta, int chunk, 
     const int grid = std::min(std::min(n_items, a.n_words), per_sm * sms);
     e = cudaMemsetAsync(sched, 0, sizeof(int) * (4 + static_cast<size_t>(a.n_words)), st);
     if (e != cudaSuccess) return e;
-    k_sweep_canon_persistent<kSmemRec, kPaper><<<grid, warps_per_cta * 32, smem, st>>>(a, chunk, sched);
+    kernel<<<grid, warps_per_cta * 32, smem, st>>>(a, chunk, sched);
     return cudaGetLastError();
 }
 

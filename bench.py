@@ -48,11 +48,11 @@ CALLS_PER_CELL_PAPER_STREAM = 3  # streamed paper precision: the visible half-st
 # launch of k_sweep_canon_persistent (2000 sweeps of the L=18 grid), and one
 # streamed sweep of the L=384 lattice (k_stream_hidden + k_stream_visible).
 MEASURED_TRAFFIC = {
-    "grid": (8.35e6 + 0.83e6, "per launch; profiles/launches_L18_grid.md"),
-    "grid_sq": (10.67e6 + 0.90e6, "per launch with S(q) every 100 sweeps; profiles/launches_L18_grid.md"),
+    "grid": (8.73e6 + 0.84e6, "per launch; profiles/launches_L18_grid.md"),
+    "grid_sq": (10.91e6 + 0.87e6, "per launch with S(q) every 100 sweeps; profiles/launches_L18_grid.md"),
     "stream": (56.74e6 + 392.31e6 + 454.82e6 + 48.83e6, "per sweep (two launches); profiles/k_stream_L384.md"),
-    "grid_paper": (8.79e6 + 0.91e6, "per launch; profiles/k_sweep_canon_persistent_L18_grid_paper.md"),
-    "grid_paper_sq": (10.79e6 + 0.90e6,
+    "grid_paper": (8.34e6 + 0.78e6, "per launch; profiles/k_sweep_canon_persistent_L18_grid_paper.md"),
+    "grid_paper_sq": (10.46e6 + 0.77e6,
                       "per launch with S(q) every 100 sweeps; profiles/k_sweep_canon_persistent_L18_grid_paper.md"),
     "stream_paper": (56.76e6 + 390.29e6 + 454.76e6 + 45.71e6, "per sweep (two launches); profiles/k_stream_L384.md"),
     "grid_bitplane": (2.48e6 + 0.78e6, "per launch; profiles/k_sweep_bitplane_L18_grid.md"),

@@ -293,3 +293,33 @@ def test_stream_rejects_unsupported():
         with pytest.raises(crbm.CrbmError) as e:
             crbm.Sampler(params=ok, n_chains=4, layout=crbm.CRBM_LAYOUT_STREAM, **kw)
         assert e.value.code == crbm.CRBM_EUNSUPPORTED
+
+
+@pytest.mark.parametrize("warps,precision", [("4", 0), ("12", 0), ("13", 0), ("32", 0), ("12", 1), ("16", 1)])
+def test_persistent_cta_shapes(orc, warps, precision, monkeypatch):
+    """The persistent sweep runs one instantiation for CTAs of up to 12 warps
+    (80 registers a thread) and another for larger ones (64): every shape
+    bit-exact against the oracle (exact precision) or against a 12-warp twin
+    (paper precision), with S(q) samples and measurements inside the chunks."""
+    monkeypatch.setenv("CRBM_WARPS", warps)
+    L, n = 18, 70
+    rng = np.random.default_rng(int(warps) + 7 * precision)
+    params = workloads.random_params(rng, 3)
+    cp = rng.integers(0, 3, n).astype(np.int32)
+    if precision == 0:
+        s, _, _, _ = run_pair(orc, L, params, n, cp, 5, splits=[9, 24], measure_every=2, series_len=6,
+                              sq_every=4)
+        assert s.warps == int(warps)
+        return
+    s = crbm.Sampler(L, params, n, chain_param=cp, seed=5, measure_every=2, sq_every=4,
+                     precision=crbm.CRBM_PRECISION_PAPER)
+    monkeypatch.setenv("CRBM_WARPS", "12")
+    ref = crbm.Sampler(L, params, n, chain_param=cp, seed=5, measure_every=2, sq_every=4,
+                       precision=crbm.CRBM_PRECISION_PAPER)
+    assert s.warps == int(warps) and ref.warps == 12
+    for k in (9, 24):
+        s.sweep(k)
+        ref.sweep(k)
+    assert np.array_equal(s.get_spins(), ref.get_spins())
+    assert np.array_equal(s.observables(), ref.observables())
+    assert np.array_equal(s.correlations()[0], ref.correlations()[0])

@@ -956,7 +956,21 @@ int crbm_set_targets(crbm_ctx* ctx, const int64_t* e_target, int32_t n) {
     const size_t np = static_cast<size_t>(ctx->n_words) * 32;
     DeviceState& d = ctx->d;
     int rc = CRBM_OK;
-    if (!d.hit && ((rc = dalloc(ctx, d.hit, 2 * np)) || (rc = dalloc(ctx, d.hit_q, 4 * np)))) return rc;
+    // the sweeps record first hits only where both buffers exist and hold targets: a failed
+    // call leaves neither behind
+    auto drop = [&]() {
+        cudaFree(d.hit);
+        cudaFree(d.hit_q);
+        d.hit = nullptr;
+        d.hit_q = nullptr;
+    };
+    if (!d.hit) {
+        if ((rc = dalloc(ctx, d.hit, 2 * np))) return rc;
+        if ((rc = dalloc(ctx, d.hit_q, 4 * np))) {
+            drop();
+            return rc;
+        }
+    }
     std::vector<int64_t> ht(2 * np);
     std::vector<int32_t> hq(4 * np, 0);
     for (size_t c = 0; c < np; ++c) {
@@ -972,7 +986,11 @@ int crbm_set_targets(crbm_ctx* ctx, const int64_t* e_target, int32_t n) {
     if (e == cudaSuccess)
         e = cudaMemcpyAsync(d.hit_q, hq.data(), hq.size() * 4, cudaMemcpyHostToDevice, ctx->stream);
     if (e == cudaSuccess) e = cudaStreamSynchronize(ctx->stream);
-    return e == cudaSuccess ? CRBM_OK : cuda_fail(ctx, e, "crbm_set_targets");
+    if (e != cudaSuccess) {
+        drop();
+        return cuda_fail(ctx, e, "crbm_set_targets");
+    }
+    return CRBM_OK;
 }
 
 int crbm_first_hits(crbm_ctx* ctx, int64_t* out, size_t n_out) {

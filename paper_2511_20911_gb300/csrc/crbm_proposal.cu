@@ -883,7 +883,14 @@ int ensure_chain_params(crbm_ctx* ctx) {
     if (e == cudaSuccess) e = cudaMalloc(reinterpret_cast<void**>(&ctx->d.chain_q), cq.size() * 4);
     if (e == cudaSuccess) e = cudaMemcpy(ctx->d.chain_bh, bh.data(), bh.size() * 4, cudaMemcpyHostToDevice);
     if (e == cudaSuccess) e = cudaMemcpy(ctx->d.chain_q, cq.data(), cq.size() * 4, cudaMemcpyHostToDevice);
-    if (e != cudaSuccess) return prop_fail(CRBM_ECUDA, std::string("chain parameters: ") + cudaGetErrorString(e));
+    if (e != cudaSuccess) {  // leave neither buffer behind: the next call builds both again
+        cudaFree(ctx->d.chain_bh);
+        cudaFree(ctx->d.chain_q);
+        ctx->d.chain_bh = nullptr;
+        ctx->d.chain_q = nullptr;
+        cudaGetLastError();  // an allocation error is not sticky; clear it for later launch checks
+        return prop_fail(CRBM_ECUDA, std::string("chain parameters: ") + cudaGetErrorString(e));
+    }
     return CRBM_OK;
 }
 

@@ -910,8 +910,11 @@ int ensure_examples(crbm_proposal* p, int n) {
     cudaFree(p->ex);
     p->ex = nullptr;
     p->ex_cap = 0;
-    if (cudaMalloc(reinterpret_cast<void**>(&p->ex), static_cast<size_t>(n) * sizeof(Example)) != cudaSuccess)
+    if (cudaMalloc(reinterpret_cast<void**>(&p->ex), static_cast<size_t>(n) * sizeof(Example)) != cudaSuccess) {
+        p->ex = nullptr;
+        cudaGetLastError();  // not sticky: clear it for later launch checks
         return prop_fail(CRBM_ENOMEM, "examples");
+    }
     p->ex_cap = n;
     return CRBM_OK;
 }

@@ -203,8 +203,9 @@ int crbm_observables(crbm_ctx* ctx, int64_t* out, size_t n_out);
  * records; crbm_first_hits writes host out[n_chains] int64, -1 for a chain
  * that has not reached its target.  With replica exchange the records belong
  * to rungs.  Not part of checkpoints.  Errors: CRBM_EINVAL (n_params not the
- * context's), CRBM_ENOMEM, CRBM_ECUDA; a failed call leaves the context
- * without targets (nothing is recorded until a call succeeds). */
+ * context's; the targets in force stay), CRBM_ENOMEM, CRBM_ECUDA (either of
+ * these leaves the context without targets: nothing is recorded until a
+ * call succeeds). */
 int crbm_set_targets(crbm_ctx* ctx, const int64_t* e_target, int32_t n_params);
 int crbm_first_hits(crbm_ctx* ctx, int64_t* out, size_t n_out);
 
